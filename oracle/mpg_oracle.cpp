@@ -1,0 +1,1430 @@
+// FP64 CPU oracle of the batched manifold walk (Manifold Path Guiding, Fan et
+// al., TOG 42(6) 2023).  TEST INFRASTRUCTURE ONLY -- the CUDA library shares no
+// code with this file; only tests, the smoke check and the benchmark's CPU
+// baseline load it.
+//
+// Plain, slow and written to be read against the paper: one chain at a time,
+// FP64, no blocking or fusion.  Where the paper defers the numerics to the
+// manifold-walk literature (Sec. 3 "Manifold walks": Newton + reprojection; the
+// generalized geometry term after Eq. ThroughputEval), the definitions used are
+// the textbook ones restated below:
+//   * constraint at specular vertex i: generalized half-vector
+//       h~ = eta_i w_i + eta_o w_o,  h = h~/|h~|,  C_i = (h.s_i, h.t_i)
+//     with w_i, w_o the unit directions to the previous / next vertex, eta_i
+//     the index on the previous vertex's side, eta_o the index on the next
+//     vertex's side (eta_o = eta_i for reflection) and (s_i, t_i) an
+//     orthonormal tangent frame of the shading normal.  C_i = 0 is the law of
+//     reflection / Snell's law in vector form.
+//   * Newton on the block-tridiagonal Jacobian dC/du (u_i: tangent-plane
+//     offsets of vertex i), a 2x2 block Thomas sweep, step halving and
+//     reprojection by ray casting from x_D through the moved vertices.
+//   * G by the implicit function theorem: du/du_L = -J^{-1} dC/du_L.
+#include "mpg_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <thread>
+#include <vector>
+
+namespace orc {
+
+static const int MAXK = 8;
+static const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Scalar types.  double for the oracle proper; Counted tallies the floating
+// point operations of one evaluation (algorithmic flop counts); Dual<N> is
+// forward-mode differentiation (adjoint reference).
+// ---------------------------------------------------------------------------
+struct Tally {
+  uint64_t add = 0, mul = 0, div = 0, sqrt = 0;
+};
+static thread_local Tally g_tally;
+
+struct Counted {
+  double v;
+  Counted(double x = 0.0) : v(x) {}
+};
+inline Counted operator+(Counted a, Counted b) { g_tally.add++; return Counted(a.v + b.v); }
+inline Counted operator-(Counted a, Counted b) { g_tally.add++; return Counted(a.v - b.v); }
+inline Counted operator-(Counted a) { return Counted(-a.v); }
+inline Counted operator*(Counted a, Counted b) { g_tally.mul++; return Counted(a.v * b.v); }
+inline Counted operator/(Counted a, Counted b) { g_tally.div++; return Counted(a.v / b.v); }
+inline Counted& operator+=(Counted& a, Counted b) { a = a + b; return a; }
+inline Counted& operator-=(Counted& a, Counted b) { a = a - b; return a; }
+inline Counted& operator*=(Counted& a, Counted b) { a = a * b; return a; }
+inline Counted sqrt(Counted a) { g_tally.sqrt++; return Counted(std::sqrt(a.v)); }
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double fabs(double a) { return std::fabs(a); }
+inline Counted fabs(Counted a) { return Counted(std::fabs(a.v)); }
+
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+  Dual(double x = 0.0) : v(x) { for (int i = 0; i < N; ++i) d[i] = 0.0; }
+};
+template <int N> inline Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v + b.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v - b.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int N> inline Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r(-a.v); for (int i = 0; i < N; ++i) r.d[i] = -a.d[i]; return r; }
+template <int N> inline Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v * b.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int N> inline Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r(a.v / b.v);
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] * b.v - a.v * b.d[i]) / (b.v * b.v);
+  return r; }
+template <int N> inline Dual<N>& operator+=(Dual<N>& a, const Dual<N>& b) { a = a + b; return a; }
+template <int N> inline Dual<N>& operator-=(Dual<N>& a, const Dual<N>& b) { a = a - b; return a; }
+template <int N> inline Dual<N>& operator*=(Dual<N>& a, const Dual<N>& b) { a = a * b; return a; }
+template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
+  double s = std::sqrt(a.v); Dual<N> r(s);
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * s);
+  return r; }
+template <int N> inline Dual<N> fabs(const Dual<N>& a) { return a.v < 0 ? -a : a; }
+
+inline double val(double x) { return x; }
+inline double val(const Counted& x) { return x.v; }
+template <int N> inline double val(const Dual<N>& x) { return x.v; }
+
+// ---------------------------------------------------------------------------
+// 3-vectors
+// ---------------------------------------------------------------------------
+template <class T>
+struct V3 {
+  T x, y, z;
+  V3() : x(0.0), y(0.0), z(0.0) {}
+  V3(T a, T b, T c) : x(a), y(b), z(c) {}
+};
+typedef V3<double> V3d;
+template <class T> inline V3<T> operator+(const V3<T>& a, const V3<T>& b) { return V3<T>(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class T> inline V3<T> operator-(const V3<T>& a, const V3<T>& b) { return V3<T>(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class T> inline V3<T> operator-(const V3<T>& a) { return V3<T>(-a.x, -a.y, -a.z); }
+template <class T> inline V3<T> operator*(const V3<T>& a, const T& s) { return V3<T>(a.x * s, a.y * s, a.z * s); }
+template <class T> inline V3<T> operator*(const T& s, const V3<T>& a) { return V3<T>(a.x * s, a.y * s, a.z * s); }
+template <class T> inline V3<T> operator/(const V3<T>& a, const T& s) { return V3<T>(a.x / s, a.y / s, a.z / s); }
+template <class T> inline T dot(const V3<T>& a, const V3<T>& b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class T> inline V3<T> cross(const V3<T>& a, const V3<T>& b) {
+  return V3<T>(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+template <class T> inline T norm(const V3<T>& a) { using std::sqrt; return sqrt(dot(a, a)); }
+template <class T> inline V3<T> normalize(const V3<T>& a) { return a / norm(a); }
+template <class T> inline V3<T> lift(const V3d& a) { return V3<T>(T(a.x), T(a.y), T(a.z)); }
+inline V3d vval(const V3d& a) { return a; }
+template <class T> inline V3d vval(const V3<T>& a) { return V3d(val(a.x), val(a.y), val(a.z)); }
+inline V3d load3(const double* p) { return V3d(p[0], p[1], p[2]); }
+inline void store3(double* p, const V3d& a) { p[0] = a.x; p[1] = a.y; p[2] = a.z; }
+
+// Orthonormal basis (b1, b2) completing a unit vector n, following the
+// branchless construction of Duff et al. 2017 ("Building an orthonormal basis,
+// revisited", JCGT 6(1)).  Both sides of the test use this rule because the
+// constraint's two components are expressed in this frame.
+template <class T>
+inline void onb(const V3<T>& n, V3<T>& b1, V3<T>& b2) {
+  double sgn = val(n.z) >= 0.0 ? 1.0 : -1.0;
+  T s(sgn);
+  T a = T(-1.0) / (s + n.z);
+  T b = n.x * n.y * a;
+  b1 = V3<T>(T(1.0) + s * n.x * n.x * a, s * b, -s * n.x);
+  b2 = V3<T>(b, s + n.y * n.y * a, -n.y);
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+// "Parallel random numbers: as easy as 1, 2, 3", SC 2011).
+// ---------------------------------------------------------------------------
+static void philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) { k0 += W0; k1 += W1; }
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+// Uniform in [0,1) from the top 24 bits of a 32-bit draw.
+static inline double u01(uint32_t r) { return (double)(r >> 8) * (1.0 / 16777216.0); }
+
+// ---------------------------------------------------------------------------
+// Scene
+// ---------------------------------------------------------------------------
+enum { SURF_SPHERE = 0, SURF_CAP = 1, SURF_RECT = 2, SURF_HEIGHTFIELD = 3 };
+enum { MAT_MIRROR = 0, MAT_DIELECTRIC = 1 };
+enum { LIGHT_POINT = 0, LIGHT_RECT = 1 };
+enum { TARGET_SPHERE = 0, TARGET_RECT = 1 };
+enum { ST_INVALID = 0, ST_CONVERGED = 1, ST_FAILED = 2, ST_LIMIT = 3 };
+
+struct Surface {
+  int type, mat, hf;
+  double etaF, etaB;
+  V3d c, axis, ex, ey;
+  double r, cap_cos;
+};
+
+struct BVHNode {
+  double lo[3], hi[3];
+  int left, right, first, count;  // count > 0 => leaf over tri_index[first..first+count)
+};
+
+struct HField {
+  int nx, ny, surf;
+  double x0, y0, x1, y1, dx, dy;
+  std::vector<double> h;
+  std::vector<V3d> P, N;  // vertex positions and interpolation normals
+  std::vector<BVHNode> nodes;
+  std::vector<int> tri_index;
+  int n_tris() const { return 2 * (nx - 1) * (ny - 1); }
+  void tri_vertices(int tri, int v[3]) const {
+    int quad = tri / 2, t = tri % 2;
+    int i = quad % (nx - 1), j = quad / (nx - 1);
+    int v00 = j * nx + i, v10 = v00 + 1, v01 = v00 + nx, v11 = v01 + 1;
+    if (t == 0) { v[0] = v00; v[1] = v10; v[2] = v11; }
+    else { v[0] = v00; v[1] = v11; v[2] = v01; }
+  }
+};
+
+struct Light {
+  int type;
+  V3d p, n, ex, ey;
+  double power, area;
+};
+
+struct Target {
+  int type;
+  V3d c, ex, ey, n;
+  double r;
+};
+
+struct Scene {
+  std::vector<Surface> surf;
+  std::vector<HField> hf;
+  std::vector<Target> tg;
+  Light light;
+};
+
+// Height-grid vertex position and normal.  The normal is the normalised
+// (-dh/dx, -dh/dy, 1) with central differences inside the grid and one-sided
+// differences on its border.
+template <class T, class HeightFn>
+V3<T> hf_normal(const HField& H, int i, int j, HeightFn hgt) {
+  T dhdx, dhdy;
+  if (i == 0) dhdx = (hgt(1, j) - hgt(0, j)) / T(H.dx);
+  else if (i == H.nx - 1) dhdx = (hgt(H.nx - 1, j) - hgt(H.nx - 2, j)) / T(H.dx);
+  else dhdx = (hgt(i + 1, j) - hgt(i - 1, j)) / T(2.0 * H.dx);
+  if (j == 0) dhdy = (hgt(i, 1) - hgt(i, 0)) / T(H.dy);
+  else if (j == H.ny - 1) dhdy = (hgt(i, H.ny - 1) - hgt(i, H.ny - 2)) / T(H.dy);
+  else dhdy = (hgt(i, j + 1) - hgt(i, j - 1)) / T(2.0 * H.dy);
+  return normalize(V3<T>(-dhdx, -dhdy, T(1.0)));
+}
+
+static void bvh_build_rec(HField& H, std::vector<V3d>& cen, std::vector<V3d>& blo,
+                          std::vector<V3d>& bhi, int first, int count) {
+  int node_id = (int)H.nodes.size();
+  H.nodes.push_back(BVHNode());
+  BVHNode nd;
+  for (int a = 0; a < 3; ++a) { nd.lo[a] = 1e300; nd.hi[a] = -1e300; }
+  double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+  for (int q = first; q < first + count; ++q) {
+    int t = H.tri_index[q];
+    double l[3] = {blo[t].x, blo[t].y, blo[t].z}, h[3] = {bhi[t].x, bhi[t].y, bhi[t].z};
+    double c[3] = {cen[t].x, cen[t].y, cen[t].z};
+    for (int a = 0; a < 3; ++a) {
+      nd.lo[a] = std::min(nd.lo[a], l[a]); nd.hi[a] = std::max(nd.hi[a], h[a]);
+      clo[a] = std::min(clo[a], c[a]); chi[a] = std::max(chi[a], c[a]);
+    }
+  }
+  if (count <= 4) {
+    nd.left = nd.right = -1; nd.first = first; nd.count = count;
+    H.nodes[node_id] = nd;
+    return;
+  }
+  int axis = 0;
+  for (int a = 1; a < 3; ++a) if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+  int mid = first + count / 2;
+  auto key = [&](int t) { return axis == 0 ? cen[t].x : axis == 1 ? cen[t].y : cen[t].z; };
+  std::nth_element(H.tri_index.begin() + first, H.tri_index.begin() + mid,
+                   H.tri_index.begin() + first + count,
+                   [&](int a, int b) { return key(a) < key(b) || (key(a) == key(b) && a < b); });
+  nd.count = 0; nd.first = -1;
+  nd.left = (int)H.nodes.size();
+  bvh_build_rec(H, cen, blo, bhi, first, mid - first);
+  nd.right = (int)H.nodes.size();
+  bvh_build_rec(H, cen, blo, bhi, mid, first + count - mid);
+  H.nodes[node_id] = nd;
+}
+
+static void hf_build(HField& H) {
+  H.dx = (H.x1 - H.x0) / (H.nx - 1);
+  H.dy = (H.y1 - H.y0) / (H.ny - 1);
+  H.P.resize((size_t)H.nx * H.ny);
+  H.N.resize((size_t)H.nx * H.ny);
+  auto hgt = [&](int i, int j) { return H.h[(size_t)j * H.nx + i]; };
+  for (int j = 0; j < H.ny; ++j)
+    for (int i = 0; i < H.nx; ++i) {
+      H.P[(size_t)j * H.nx + i] = V3d(H.x0 + i * H.dx, H.y0 + j * H.dy, hgt(i, j));
+      H.N[(size_t)j * H.nx + i] = hf_normal<double>(H, i, j, hgt);
+    }
+  int nt = H.n_tris();
+  std::vector<V3d> cen(nt), blo(nt), bhi(nt);
+  for (int t = 0; t < nt; ++t) {
+    int v[3]; H.tri_vertices(t, v);
+    V3d a = H.P[v[0]], b = H.P[v[1]], c = H.P[v[2]];
+    cen[t] = (a + b + c) / 3.0;
+    blo[t] = V3d(std::min({a.x, b.x, c.x}), std::min({a.y, b.y, c.y}), std::min({a.z, b.z, c.z}));
+    bhi[t] = V3d(std::max({a.x, b.x, c.x}), std::max({a.y, b.y, c.y}), std::max({a.z, b.z, c.z}));
+  }
+  H.tri_index.resize(nt);
+  for (int t = 0; t < nt; ++t) H.tri_index[t] = t;
+  H.nodes.clear();
+  bvh_build_rec(H, cen, blo, bhi, 0, nt);
+}
+
+// ---------------------------------------------------------------------------
+// Ray casting: the operator r(x, w) of Eq. (deduction) -- nearest intersection
+// of a ray with all specular surfaces.
+// ---------------------------------------------------------------------------
+struct Hit {
+  bool hit = false;
+  double t = 0.0;
+  int surf = -1, prim = -1;
+  double b1 = 0.0, b2 = 0.0;
+};
+
+// Ray/sphere roots t of |o + t d - c|^2 = r^2 (d unit), ascending.
+template <class T>
+int sphere_roots(const V3<T>& o, const V3<T>& d, const V3<T>& c, T r, T roots[2]) {
+  using std::sqrt;
+  V3<T> oc = o - c;
+  T b = dot(oc, d);
+  T cc = dot(oc, oc) - r * r;
+  T disc = b * b - cc;
+  if (val(disc) < 0.0) return 0;
+  T sq = sqrt(disc);
+  roots[0] = -b - sq;
+  roots[1] = -b + sq;
+  return 2;
+}
+
+// Moeller-Trumbore ray/triangle test (Moeller & Trumbore 1997).
+template <class T>
+bool tri_hit(const V3<T>& o, const V3<T>& d, const V3<T>& p0, const V3<T>& p1, const V3<T>& p2,
+             T& t, T& b1, T& b2) {
+  V3<T> e1 = p1 - p0, e2 = p2 - p0;
+  V3<T> pv = cross(d, e2);
+  T det = dot(e1, pv);
+  if (std::fabs(val(det)) < 1e-300) return false;
+  T inv = T(1.0) / det;
+  V3<T> tv = o - p0;
+  b1 = dot(tv, pv) * inv;
+  if (val(b1) < 0.0 || val(b1) > 1.0) return false;
+  V3<T> qv = cross(tv, e1);
+  b2 = dot(d, qv) * inv;
+  if (val(b2) < 0.0 || val(b1) + val(b2) > 1.0) return false;
+  t = dot(e2, qv) * inv;
+  return true;
+}
+
+// Slab test of a ray against an axis-aligned box, clipped to (tmin, tmax).
+static bool box_hit(const V3d& o, const V3d& d, const double lo[3], const double hi[3],
+                    double tmin, double tmax) {
+  double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+  for (int a = 0; a < 3; ++a) {
+    if (dd[a] == 0.0) {
+      if (oo[a] < lo[a] || oo[a] > hi[a]) return false;
+      continue;
+    }
+    double t0 = (lo[a] - oo[a]) / dd[a], t1 = (hi[a] - oo[a]) / dd[a];
+    if (t0 > t1) std::swap(t0, t1);
+    tmin = std::max(tmin, t0);
+    tmax = std::min(tmax, t1);
+    if (tmin > tmax) return false;
+  }
+  return true;
+}
+
+static void hf_intersect(const HField& H, const V3d& o, const V3d& d, double tmin, double& tbest,
+                         Hit& best, bool brute) {
+  auto test_tri = [&](int tri) {
+    int v[3]; H.tri_vertices(tri, v);
+    double t, b1, b2;
+    if (tri_hit<double>(o, d, H.P[v[0]], H.P[v[1]], H.P[v[2]], t, b1, b2) && t > tmin && t < tbest) {
+      tbest = t; best.hit = true; best.t = t; best.surf = H.surf; best.prim = tri;
+      best.b1 = b1; best.b2 = b2;
+    }
+  };
+  if (brute) {
+    for (int tri = 0; tri < H.n_tris(); ++tri) test_tri(tri);
+    return;
+  }
+  std::vector<int> stack;
+  stack.push_back(0);
+  while (!stack.empty()) {
+    int ni = stack.back(); stack.pop_back();
+    const BVHNode& nd = H.nodes[ni];
+    if (!box_hit(o, d, nd.lo, nd.hi, tmin, tbest)) continue;
+    if (nd.count > 0) {
+      for (int q = nd.first; q < nd.first + nd.count; ++q) test_tri(H.tri_index[q]);
+    } else {
+      stack.push_back(nd.left);
+      stack.push_back(nd.right);
+    }
+  }
+}
+
+// Nearest hit of the ray (o, d) with any specular surface, t in (tmin, tmax).
+static Hit intersect(const Scene& S, const V3d& o, const V3d& d, double tmin, double tmax,
+                     bool brute = false) {
+  Hit best;
+  double tbest = tmax;
+  for (int s = 0; s < (int)S.surf.size(); ++s) {
+    const Surface& sf = S.surf[s];
+    if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+      double roots[2];
+      if (!sphere_roots<double>(o, d, sf.c, sf.r, roots)) continue;
+      for (int q = 0; q < 2; ++q) {
+        double t = roots[q];
+        if (!(t > tmin && t < tbest)) continue;
+        if (sf.type == SURF_CAP) {
+          V3d p = o + d * t;
+          if (dot(p - sf.c, sf.axis) < sf.r * sf.cap_cos) continue;
+        }
+        tbest = t; best.hit = true; best.t = t; best.surf = s; best.prim = -1;
+        break;
+      }
+    } else if (sf.type == SURF_RECT) {
+      double den = dot(d, sf.axis);
+      if (std::fabs(den) < 1e-300) continue;
+      double t = dot(sf.c - o, sf.axis) / den;
+      if (!(t > tmin && t < tbest)) continue;
+      V3d q = o + d * t - sf.c;
+      if (std::fabs(dot(q, sf.ex)) > dot(sf.ex, sf.ex) || std::fabs(dot(q, sf.ey)) > dot(sf.ey, sf.ey))
+        continue;
+      tbest = t; best.hit = true; best.t = t; best.surf = s; best.prim = -1;
+    } else if (sf.type == SURF_HEIGHTFIELD) {
+      hf_intersect(S.hf[sf.hf], o, d, tmin, tbest, best, brute);
+    }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------------------
+// Chain vertices and their local differential geometry
+// ---------------------------------------------------------------------------
+struct Vtx {
+  int surf = -1, prim = -1;
+  double b1 = 0.0, b2 = 0.0;
+  V3d p;
+};
+
+// Point of a hit: on analytic surfaces the ray point snapped onto the surface,
+// on triangles the barycentric combination of the corners.
+static Vtx hit_vertex(const Scene& S, const V3d& o, const V3d& d, const Hit& h) {
+  Vtx v;
+  v.surf = h.surf; v.prim = h.prim; v.b1 = h.b1; v.b2 = h.b2;
+  const Surface& sf = S.surf[h.surf];
+  V3d p = o + d * h.t;
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    p = sf.c + normalize(p - sf.c) * sf.r;
+  } else if (sf.type == SURF_RECT) {
+    p = p - sf.axis * dot(p - sf.c, sf.axis);
+  } else {
+    const HField& H = S.hf[sf.hf];
+    int vv[3]; H.tri_vertices(h.prim, vv);
+    p = H.P[vv[0]] + (H.P[vv[1]] - H.P[vv[0]]) * h.b1 + (H.P[vv[2]] - H.P[vv[0]]) * h.b2;
+  }
+  v.p = p;
+  return v;
+}
+
+// Local frame of a vertex: position, unit shading normal n (front-facing per
+// the surface definition), an orthonormal basis (dpdu, dpdv) of the geometric
+// tangent plane, and the derivatives dndu, dndv of n along dpdu and dpdv.
+template <class T>
+struct Frame {
+  V3<T> p, n, dpdu, dpdv, dndu, dndv;
+};
+
+template <class T>
+Frame<T> frame_sphere(const V3<T>& p, const V3<T>& c, T r) {
+  Frame<T> f;
+  f.p = p;
+  f.n = normalize(p - c);
+  onb(f.n, f.dpdu, f.dpdv);
+  f.dndu = f.dpdu / r;
+  f.dndv = f.dpdv / r;
+  return f;
+}
+
+template <class T>
+Frame<T> frame_plane(const V3<T>& p, const V3<T>& n) {
+  Frame<T> f;
+  f.p = p;
+  f.n = n;
+  onb(f.n, f.dpdu, f.dpdv);
+  f.dndu = V3<T>();
+  f.dndv = V3<T>();
+  return f;
+}
+
+// Triangle with per-corner normals: n = normalize(sum b_j N_j).  Moving the
+// point by a tangent vector a changes the barycentrics by the solution of
+// a = db1 e1 + db2 e2, hence the interpolated normal by db1 (N1-N0) + db2 (N2-N0).
+template <class T>
+Frame<T> frame_triangle(const V3<T>& P0, const V3<T>& P1, const V3<T>& P2, const V3<T>& N0,
+                        const V3<T>& N1, const V3<T>& N2, T b1, T b2) {
+  Frame<T> f;
+  V3<T> e1 = P1 - P0, e2 = P2 - P0;
+  f.p = P0 + e1 * b1 + e2 * b2;
+  V3<T> ng = normalize(cross(e1, e2));
+  onb(ng, f.dpdu, f.dpdv);
+  V3<T> Ns = N0 * (T(1.0) - b1 - b2) + N1 * b1 + N2 * b2;
+  T len = norm(Ns);
+  f.n = Ns / len;
+  T g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2);
+  T gdet = g11 * g22 - g12 * g12;
+  V3<T> dirs[2] = {f.dpdu, f.dpdv};
+  V3<T> out[2];
+  for (int q = 0; q < 2; ++q) {
+    T r1 = dot(e1, dirs[q]), r2 = dot(e2, dirs[q]);
+    T db1 = (g22 * r1 - g12 * r2) / gdet;
+    T db2 = (g11 * r2 - g12 * r1) / gdet;
+    V3<T> dN = (N1 - N0) * db1 + (N2 - N0) * db2;
+    out[q] = (dN - f.n * dot(f.n, dN)) / len;
+  }
+  f.dndu = out[0];
+  f.dndv = out[1];
+  return f;
+}
+
+static Frame<double> vertex_frame(const Scene& S, const Vtx& v) {
+  const Surface& sf = S.surf[v.surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) return frame_sphere<double>(v.p, sf.c, sf.r);
+  if (sf.type == SURF_RECT) return frame_plane<double>(v.p, sf.axis);
+  const HField& H = S.hf[sf.hf];
+  int vv[3]; H.tri_vertices(v.prim, vv);
+  return frame_triangle<double>(H.P[vv[0]], H.P[vv[1]], H.P[vv[2]], H.N[vv[0]], H.N[vv[1]],
+                                H.N[vv[2]], v.b1, v.b2);
+}
+
+// Frames of the two separators: the receiver's tangent plane at x_D (used by
+// the point-light geometry term) and the emitter's axes at x_L (area light).
+static Frame<double> receiver_frame(const V3d& xD, const V3d& nD) {
+  return frame_plane<double>(xD, nD);
+}
+static Frame<double> light_frame(const Light& L, const V3d& xL) {
+  Frame<double> f;
+  f.p = xL;
+  f.n = L.n;
+  if (L.type == LIGHT_RECT) {
+    f.dpdu = normalize(L.ex);
+    f.dpdv = normalize(L.ey);
+  } else {
+    onb(L.n, f.dpdu, f.dpdv);
+  }
+  return f;
+}
+
+// ---------------------------------------------------------------------------
+// Constraint and Jacobian blocks at one specular vertex
+// ---------------------------------------------------------------------------
+template <class T>
+struct VBlocks {
+  T C[2];
+  T A[2][2];   // dC_i / du_{i-1}
+  T B[2][2];   // dC_i / du_i
+  T Cc[2][2];  // dC_i / du_{i+1}
+  T eta_i, eta_o;
+  bool front;
+};
+
+// Indices of refraction on the previous / next vertex's side.  Returns false
+// for a refraction requested on a mirror.
+static bool vertex_etas(const Surface& sf, bool front, bool refract, double& eta_i, double& eta_o) {
+  if (sf.mat == MAT_MIRROR) {
+    eta_i = eta_o = 1.0;
+    return !refract;
+  }
+  eta_i = front ? sf.etaF : sf.etaB;
+  eta_o = refract ? (front ? sf.etaB : sf.etaF) : eta_i;
+  return true;
+}
+
+template <class T>
+bool vertex_blocks(const Frame<T>& fp, const Frame<T>& f, const Frame<T>& fn, const Surface& sf,
+                   bool refract, VBlocks<T>& out) {
+  using std::sqrt;
+  V3<T> wi = fp.p - f.p, wo = fn.p - f.p;
+  T di = norm(wi), dO = norm(wo);
+  if (val(di) <= 0.0 || val(dO) <= 0.0) return false;
+  wi = wi / di;
+  wo = wo / dO;
+  out.front = val(dot(wi, f.n)) > 0.0;
+  double ei, eo;
+  if (!vertex_etas(sf, out.front, refract, ei, eo)) return false;
+  out.eta_i = T(ei);
+  out.eta_o = T(eo);
+  V3<T> ht = wi * out.eta_i + wo * out.eta_o;
+  T L = norm(ht);
+  if (val(L) <= 0.0) return false;
+  V3<T> h = ht / L;
+  V3<T> s, t;
+  onb(f.n, s, t);
+  out.C[0] = dot(h, s);
+  out.C[1] = dot(h, t);
+  // Projections: P_w a = (a - w (w.a)) / d is the derivative of a unit
+  // direction w = (y - x)/|y - x| with respect to y along a.
+  auto Pwi = [&](const V3<T>& a) { return (a - wi * dot(wi, a)) / di; };
+  auto Pwo = [&](const V3<T>& a) { return (a - wo * dot(wo, a)) / dO; };
+  auto Ph = [&](const V3<T>& a) { return (a - h * dot(h, a)) / L; };
+  const V3<T>* tp[2] = {&fp.dpdu, &fp.dpdv};
+  const V3<T>* tn[2] = {&fn.dpdu, &fn.dpdv};
+  const V3<T>* tc[2] = {&f.dpdu, &f.dpdv};
+  const V3<T>* dn[2] = {&f.dndu, &f.dndv};
+  T hn = dot(h, f.n);
+  for (int j = 0; j < 2; ++j) {
+    V3<T> dhA = Ph(Pwi(*tp[j]) * out.eta_i);
+    out.A[0][j] = dot(dhA, s);
+    out.A[1][j] = dot(dhA, t);
+    V3<T> dhC = Ph(Pwo(*tn[j]) * out.eta_o);
+    out.Cc[0][j] = dot(dhC, s);
+    out.Cc[1][j] = dot(dhC, t);
+    V3<T> dhB = -Ph(Pwi(*tc[j]) * out.eta_i + Pwo(*tc[j]) * out.eta_o);
+    // The frame (s, t) turns with the normal: ds = -(s.dn) n, dt = -(t.dn) n.
+    out.B[0][j] = dot(dhB, s) - hn * dot(s, *dn[j]);
+    out.B[1][j] = dot(dhB, t) - hn * dot(t, *dn[j]);
+  }
+  return true;
+}
+
+// Whole-chain evaluation: frames f[0..k+1] (f[0] receiver, f[k+1] light).
+template <class T>
+bool chain_blocks(const Scene& S, int k, uint8_t tau, const Frame<T>* f, const int* surf,
+                  VBlocks<T>* vb) {
+  for (int i = 1; i <= k; ++i) {
+    bool refract = (tau >> (i - 1)) & 1;
+    if (!vertex_blocks(f[i - 1], f[i], f[i + 1], S.surf[surf[i]], refract, vb[i - 1])) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// 2x2 block Thomas sweep for J X = R, J block-tridiagonal with rows
+// (A_i, B_i, Cc_i); R has m columns (1 for the Newton step, 2 for G).
+// ---------------------------------------------------------------------------
+template <class T>
+struct M2 {
+  T a[2][2];
+};
+template <class T> inline M2<T> mmul(const M2<T>& x, const M2<T>& y) {
+  M2<T> r;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) r.a[i][j] = x.a[i][0] * y.a[0][j] + x.a[i][1] * y.a[1][j];
+  return r;
+}
+
+template <class T>
+bool block_thomas(int k, const VBlocks<T>* vb, int m, const T* rhs /*[k][2][m]*/, T* x /*[k][2][m]*/,
+                  double sing_eps) {
+  std::vector<M2<T>> Bp(k), Binv(k);
+  std::vector<T> rp((size_t)k * 2 * m);
+  auto R = [&](int i, int r, int c) -> T& { return rp[((size_t)i * 2 + r) * m + c]; };
+  for (int i = 0; i < k; ++i) {
+    M2<T> B;
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) B.a[r][c] = vb[i].B[r][c];
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < m; ++c) R(i, r, c) = rhs[((size_t)i * 2 + r) * m + c];
+    if (i > 0) {
+      M2<T> A, Cp;
+      for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) {
+        A.a[r][c] = vb[i].A[r][c];
+        Cp.a[r][c] = vb[i - 1].Cc[r][c];
+      }
+      M2<T> Lm = mmul(A, Binv[i - 1]);
+      M2<T> LC = mmul(Lm, Cp);
+      for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) B.a[r][c] = B.a[r][c] - LC.a[r][c];
+      for (int c = 0; c < m; ++c) {
+        T r0 = R(i - 1, 0, c), r1 = R(i - 1, 1, c);
+        R(i, 0, c) = R(i, 0, c) - (Lm.a[0][0] * r0 + Lm.a[0][1] * r1);
+        R(i, 1, c) = R(i, 1, c) - (Lm.a[1][0] * r0 + Lm.a[1][1] * r1);
+      }
+    }
+    T det = B.a[0][0] * B.a[1][1] - B.a[0][1] * B.a[1][0];
+    double mx = 0.0;
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 2; ++c) mx = std::max(mx, std::fabs(val(B.a[r][c])));
+    if (!(std::fabs(val(det)) > sing_eps * mx * mx)) return false;
+    Bp[i] = B;
+    Binv[i].a[0][0] = B.a[1][1] / det;
+    Binv[i].a[0][1] = -B.a[0][1] / det;
+    Binv[i].a[1][0] = -B.a[1][0] / det;
+    Binv[i].a[1][1] = B.a[0][0] / det;
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    for (int c = 0; c < m; ++c) {
+      T r0 = R(i, 0, c), r1 = R(i, 1, c);
+      if (i < k - 1) {
+        T x0 = x[((size_t)(i + 1) * 2 + 0) * m + c], x1 = x[((size_t)(i + 1) * 2 + 1) * m + c];
+        r0 = r0 - (vb[i].Cc[0][0] * x0 + vb[i].Cc[0][1] * x1);
+        r1 = r1 - (vb[i].Cc[1][0] * x0 + vb[i].Cc[1][1] * x1);
+      }
+      x[((size_t)i * 2 + 0) * m + c] = Binv[i].a[0][0] * r0 + Binv[i].a[0][1] * r1;
+      x[((size_t)i * 2 + 1) * m + c] = Binv[i].a[1][0] * r0 + Binv[i].a[1][1] * r1;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Seed chains: Eq. (deduction) -- x_1 = r(x_D, w_D), then each next vertex is
+// the hit of the ray scattered at the previous one by its type tau_i.
+// ---------------------------------------------------------------------------
+// Scattered direction of the propagation direction d at a vertex with shading
+// normal n.  Reflection: mirror about n.  Refraction: Snell's law with the
+// indices of the surface's two sides; returns false on total internal reflection.
+static bool scatter(const Surface& sf, const V3d& n, const V3d& d, bool refract, V3d& out) {
+  if (!refract) {
+    out = d - n * (2.0 * dot(d, n));
+    return true;
+  }
+  if (sf.mat == MAT_MIRROR) return false;
+  double cos_i = -dot(d, n);
+  double eta1 = sf.etaF, eta2 = sf.etaB;
+  V3d nn = n;
+  if (cos_i < 0.0) {  // arriving from the back side
+    cos_i = -cos_i; eta1 = sf.etaB; eta2 = sf.etaF; nn = -n;
+  }
+  double eta = eta1 / eta2;
+  double k2 = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
+  if (k2 < 0.0) return false;
+  out = normalize(d * eta + nn * (eta * cos_i - std::sqrt(k2)));
+  return true;
+}
+
+struct ChainIO {
+  int k;
+  uint8_t tau;
+  Vtx v[MAXK + 2];  // v[0] = x_D, v[k+1] = x_L
+};
+
+static bool deduce(const Scene& S, const V3d& xD, const V3d& wD, int k, uint8_t tau, double ray_eps,
+                   ChainIO& ch) {
+  V3d o = xD, d = wD;
+  for (int i = 1; i <= k; ++i) {
+    Hit h = intersect(S, o, d, ray_eps, std::numeric_limits<double>::infinity());
+    if (!h.hit) return false;
+    ch.v[i] = hit_vertex(S, o, d, h);
+    if (i < k) {
+      Frame<double> f = vertex_frame(S, ch.v[i]);
+      V3d dn;
+      if (!scatter(S.surf[h.surf], f.n, d, (tau >> (i - 1)) & 1, dn)) return false;
+      o = ch.v[i].p;
+      d = dn;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Guide histogram over world directions: theta from +z uniform over [0,pi],
+// phi uniform over [0,2pi).  The bin rule uses only comparisons of the FP32
+// direction with FP32 edge data (theta) and exact FP64 signs of 2x2 cross
+// products of FP32 values (phi), so it is reproducible bit for bit.
+// ---------------------------------------------------------------------------
+static int guide_bin(const orc_guide& g, const float w[3]) {
+  int it = 0;
+  for (int j = 1; j < g.n_theta; ++j)
+    if (w[2] < g.cos_theta[j]) ++it;
+  float x = w[0], y = w[1];
+  bool upper = (y > 0.0f) || (y == 0.0f && x >= 0.0f);
+  int half = g.n_phi / 2;
+  int ip = upper ? 0 : half;
+  int j0 = upper ? 1 : half + 1, j1 = upper ? half : g.n_phi;
+  for (int j = j0; j < j1; ++j) {
+    double cr = (double)g.phi_cos[j] * (double)y - (double)g.phi_sin[j] * (double)x;
+    if (cr >= 0.0) ++ip;
+  }
+  return it * g.n_phi + ip;
+}
+
+static uint64_t quantise_weight(float w, int shift) {
+  if (!(w > 0.0f)) return 0;
+  double q = std::floor((double)w * std::ldexp(1.0, shift));
+  if (q >= 4294967295.0) return 4294967295ull;
+  return (uint64_t)q;
+}
+
+struct GuideCDF {
+  std::vector<uint64_t> cdf;  // [n_cells][bins] inclusive prefix sums
+  int bins = 0;
+};
+
+static void guide_cdf(const orc_guide& g, GuideCDF& out) {
+  out.bins = g.n_theta * g.n_phi;
+  out.cdf.assign((size_t)g.n_cells * out.bins, 0);
+  for (int c = 0; c < g.n_cells; ++c) {
+    uint64_t s = 0;
+    for (int b = 0; b < out.bins; ++b) {
+      s += g.counts[(size_t)c * out.bins + b];
+      out.cdf[(size_t)c * out.bins + b] = s;
+    }
+  }
+}
+
+// Solid-angle density at x_D of the direction sampler p_0 for direction w:
+// targets are picked uniformly; a sphere target is sampled uniformly by area on
+// the cap visible from x_D, a rectangle uniformly by area.
+static double p0_pdf(const Scene& S, const V3d& xD, const V3d& w) {
+  double sum = 0.0;
+  for (const Target& tg : S.tg) {
+    if (tg.type == TARGET_SPHERE) {
+      double d = norm(xD - tg.c);
+      if (d <= tg.r) continue;
+      double roots[2];
+      if (!sphere_roots<double>(xD, w, tg.c, tg.r, roots) || roots[0] <= 0.0) continue;
+      V3d p = xD + w * roots[0];
+      double cosp = std::fabs(dot(normalize(p - tg.c), w));
+      double pA = 1.0 / (2.0 * PI * tg.r * tg.r * (1.0 - tg.r / d));
+      sum += pA * roots[0] * roots[0] / cosp;
+    } else {
+      double den = dot(w, tg.n);
+      if (std::fabs(den) < 1e-300) continue;
+      double t = dot(tg.c - xD, tg.n) / den;
+      if (t <= 0.0) continue;
+      V3d q = xD + w * t - tg.c;
+      if (std::fabs(dot(q, tg.ex)) > dot(tg.ex, tg.ex) || std::fabs(dot(q, tg.ey)) > dot(tg.ey, tg.ey))
+        continue;
+      double area = 4.0 * norm(tg.ex) * norm(tg.ey);
+      sum += t * t / (area * std::fabs(den));
+    }
+  }
+  return S.tg.empty() ? 0.0 : sum / (double)S.tg.size();
+}
+
+static double hist_pdf(const orc_guide& g, const GuideCDF& cdf, int cell, const V3d& w) {
+  float wf[3] = {(float)w.x, (float)w.y, (float)w.z};
+  int bin = guide_bin(g, wf);
+  uint64_t total = cdf.cdf[(size_t)cell * cdf.bins + cdf.bins - 1];
+  if (total == 0) return 0.0;
+  uint64_t cnt = g.counts[(size_t)cell * cdf.bins + bin];
+  int it = bin / g.n_phi;
+  double dphi = 2.0 * PI / g.n_phi;
+  double dcos = (double)g.cos_theta[it] - (double)g.cos_theta[it + 1];
+  return ((double)cnt / (double)total) / (dphi * dcos);
+}
+
+struct SeedDraw {
+  bool valid = false;
+  uint8_t tau = 0;
+  double pdf = 0.0;
+  ChainIO ch;
+};
+
+static SeedDraw sample_seed(const Scene& S, const orc_guide* g, const GuideCDF* cdf, const V3d& xD,
+                            const V3d& nD, uint32_t cell, const V3d& xL, int k, uint8_t tau_in,
+                            bool tau_random, uint64_t rng_seed, uint64_t idx, uint32_t trial,
+                            const orc_params& prm) {
+  SeedDraw sd;
+  uint32_t key[2] = {(uint32_t)rng_seed, (uint32_t)(rng_seed >> 32)};
+  uint32_t c0[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u};
+  uint32_t c1[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u};
+  uint32_t r0[4], r1[4];
+  philox4x32_10(c0, key, r0);
+  philox4x32_10(c1, key, r1);
+  uint8_t tau = tau_random ? (uint8_t)(r1[1] & ((1u << k) - 1u)) : tau_in;
+  sd.tau = tau;
+  uint64_t total = 0;
+  bool use_guide = g && g->counts && cdf;
+  if (use_guide) total = cdf->cdf[(size_t)cell * cdf->bins + cdf->bins - 1];
+  use_guide = use_guide && total > 0;
+  bool pick_p0 = !use_guide || u01(r0[0]) < prm.alpha;
+  V3d w;
+  if (pick_p0) {
+    if (S.tg.empty()) return sd;
+    int nt = (int)S.tg.size();
+    int ti = std::min((int)(u01(r1[0]) * nt), nt - 1);
+    const Target& tg = S.tg[ti];
+    double u1 = u01(r0[2]), u2 = u01(r0[3]);
+    V3d p;
+    if (tg.type == TARGET_SPHERE) {
+      double d = norm(xD - tg.c);
+      if (d <= tg.r) return sd;
+      V3d a = (xD - tg.c) / d, e1, e2;
+      onb(a, e1, e2);
+      double ca = tg.r / d + u1 * (1.0 - tg.r / d);
+      double sa = std::sqrt(std::max(0.0, 1.0 - ca * ca));
+      double ph = 2.0 * PI * u2;
+      p = tg.c + (a * ca + (e1 * std::cos(ph) + e2 * std::sin(ph)) * sa) * tg.r;
+    } else {
+      p = tg.c + tg.ex * (2.0 * u1 - 1.0) + tg.ey * (2.0 * u2 - 1.0);
+    }
+    w = normalize(p - xD);
+  } else {
+    // bin by inverse CDF on exact integers: target = floor(r * total / 2^32)
+    uint64_t r = r0[1];
+    unsigned __int128 prod = (unsigned __int128)r * (unsigned __int128)total;
+    uint64_t target = (uint64_t)(prod >> 32);
+    const uint64_t* c = &cdf->cdf[(size_t)cell * cdf->bins];
+    int lo = 0, hi = cdf->bins - 1;
+    while (lo < hi) {
+      int mid = (lo + hi) / 2;
+      if (c[mid] > target) hi = mid; else lo = mid + 1;
+    }
+    int it = lo / g->n_phi, ip = lo % g->n_phi;
+    double clo = g->cos_theta[it], chi = g->cos_theta[it + 1];
+    double ct = clo + u01(r0[2]) * (chi - clo);
+    double st = std::sqrt(std::max(0.0, 1.0 - ct * ct));
+    double ph = 2.0 * PI * ((double)ip + u01(r0[3])) / g->n_phi;
+    w = V3d(st * std::cos(ph), st * std::sin(ph), ct);
+  }
+  if (dot(w, nD) <= 0.0) return sd;
+  double p0 = p0_pdf(S, xD, w);
+  sd.pdf = use_guide ? prm.alpha * p0 + (1.0 - prm.alpha) * hist_pdf(*g, *cdf, cell, w) : p0;
+  sd.ch.k = k;
+  sd.ch.tau = tau;
+  sd.ch.v[0].p = xD;
+  sd.ch.v[k + 1].p = xL;
+  if (!deduce(S, xD, w, k, tau, prm.ray_eps, sd.ch)) return sd;
+  sd.valid = true;
+  return sd;
+}
+
+// ---------------------------------------------------------------------------
+// Manifold walk (Sec. 3): Newton's method on C(u) = 0 with reprojection.
+// ---------------------------------------------------------------------------
+struct EvalOut {
+  bool ok = false;
+  double cmax = 0.0, cnorm2 = 0.0;
+  VBlocks<double> vb[MAXK];
+  Frame<double> f[MAXK + 2];
+};
+
+static void chain_frames(const Scene& S, const ChainIO& ch, const V3d& nD, Frame<double>* f) {
+  f[0] = receiver_frame(ch.v[0].p, nD);
+  for (int i = 1; i <= ch.k; ++i) f[i] = vertex_frame(S, ch.v[i]);
+  f[ch.k + 1] = light_frame(S.light, ch.v[ch.k + 1].p);
+}
+
+static void eval_chain(const Scene& S, const ChainIO& ch, const V3d& nD, EvalOut& ev) {
+  chain_frames(S, ch, nD, ev.f);
+  int surf[MAXK + 2];
+  for (int i = 0; i <= ch.k + 1; ++i) surf[i] = ch.v[i].surf;
+  ev.ok = chain_blocks<double>(S, ch.k, ch.tau, ev.f, surf, ev.vb);
+  if (!ev.ok) return;
+  ev.cmax = 0.0;
+  ev.cnorm2 = 0.0;
+  for (int i = 0; i < ch.k; ++i)
+    for (int c = 0; c < 2; ++c) {
+      ev.cmax = std::max(ev.cmax, std::fabs(ev.vb[i].C[c]));
+      ev.cnorm2 += ev.vb[i].C[c] * ev.vb[i].C[c];
+    }
+}
+
+// Move every vertex by beta * (dpdu du_0 + dpdv du_1) and re-project the chain
+// onto the surfaces: a ray from x_D through the moved x_1, then from each new
+// vertex through the next moved one; each hit must lie on the vertex's surface.
+static bool propose(const Scene& S, const ChainIO& ch, const Frame<double>* f, const double* du,
+                    double beta, double ray_eps, ChainIO& out) {
+  out = ch;
+  V3d prev = ch.v[0].p;
+  for (int i = 1; i <= ch.k; ++i) {
+    V3d target = ch.v[i].p + (f[i].dpdu * du[2 * (i - 1)] + f[i].dpdv * du[2 * (i - 1) + 1]) * beta;
+    V3d dir = target - prev;
+    double len = norm(dir);
+    if (!(len > 0.0)) return false;
+    dir = dir / len;
+    Hit h = intersect(S, prev, dir, ray_eps, std::numeric_limits<double>::infinity());
+    if (!h.hit || h.surf != ch.v[i].surf) return false;
+    out.v[i] = hit_vertex(S, prev, dir, h);
+    prev = out.v[i].p;
+  }
+  return true;
+}
+
+static int walk_chain(const Scene& S, ChainIO& ch, const V3d& nD, const orc_params& prm, int& iters) {
+  EvalOut ev;
+  for (int it = 0;; ++it) {
+    iters = it;
+    eval_chain(S, ch, nD, ev);
+    if (!ev.ok) return ST_FAILED;
+    if (ev.cmax < prm.tol) return ST_CONVERGED;
+    if (it >= prm.max_iter) return ST_LIMIT;
+    int k = ch.k;
+    double rhs[2 * MAXK], du[2 * MAXK];
+    for (int i = 0; i < k; ++i) { rhs[2 * i] = -ev.vb[i].C[0]; rhs[2 * i + 1] = -ev.vb[i].C[1]; }
+    if (!block_thomas<double>(k, ev.vb, 1, rhs, du, prm.sing_eps)) return ST_FAILED;
+    double beta = 1.0;
+    bool accepted = false;
+    for (int hv = 0; hv <= prm.max_halvings; ++hv, beta *= 0.5) {
+      ChainIO cand;
+      if (!propose(S, ch, ev.f, du, beta, prm.ray_eps, cand)) continue;
+      EvalOut ec;
+      eval_chain(S, cand, nD, ec);
+      if (ec.ok && ec.cnorm2 < ev.cnorm2) {
+        ch = cand;
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) return ST_FAILED;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Contribution: admissibility (visibility, types, orientation), generalized
+// geometry term G, scattering factor kappa, T = kappa G L_o (Eq. ThroughputEval).
+// ---------------------------------------------------------------------------
+// Unpolarised Fresnel reflectance for light meeting an interface from the side
+// of index eta1 at incidence cosine cos1 (other side eta2); 1 under total
+// internal reflection.
+template <class T>
+T fresnel(T cos1, T eta1, T eta2) {
+  using std::sqrt;
+  T s2 = (eta1 / eta2) * (eta1 / eta2) * (T(1.0) - cos1 * cos1);
+  if (val(s2) >= 1.0) return T(1.0);
+  T cos2 = sqrt(T(1.0) - s2);
+  T rs = (eta1 * cos1 - eta2 * cos2) / (eta1 * cos1 + eta2 * cos2);
+  T rp = (eta2 * cos1 - eta1 * cos2) / (eta2 * cos1 + eta1 * cos2);
+  return T(0.5) * (rs * rs + rp * rp);
+}
+
+// kappa: product over vertices of the mirror factor (1), the Fresnel
+// reflectance (dielectric reflection) or transmittance times the radiance
+// scaling (eta_i/eta_o)^2 (dielectric refraction, light travelling from the
+// x_{i+1} side into the x_{i-1} side).
+template <class T>
+T chain_kappa(const Scene& S, int k, uint8_t tau, const Frame<T>* f, const int* surf,
+              const VBlocks<T>* vb) {
+  T kap(1.0);
+  for (int i = 1; i <= k; ++i) {
+    const Surface& sf = S.surf[surf[i]];
+    if (sf.mat == MAT_MIRROR) continue;
+    V3<T> wi = normalize(f[i - 1].p - f[i].p);
+    T ci = fabs(dot(wi, f[i].n));
+    bool refract = (tau >> (i - 1)) & 1;
+    T eta1 = vb[i - 1].eta_i;
+    T eta2 = T(vb[i - 1].front ? sf.etaB : sf.etaF);
+    T F = fresnel(ci, eta1, eta2);
+    if (refract) {
+      T r = vb[i - 1].eta_i / vb[i - 1].eta_o;
+      kap = kap * (T(1.0) - F) * r * r;
+    } else {
+      kap = kap * F;
+    }
+  }
+  return kap;
+}
+
+// Generalized geometry term by the implicit function theorem.  Area light:
+// G = cos(theta_D) |det d(w_D)/d(u_L)|, u_L orthonormal coordinates on the
+// emitter; point light: G = |det d(w_L)/d(u_D)|, u_D orthonormal coordinates on
+// the receiver (irradiance per unit intensity).  dx/du of the moving end vertex
+// comes from J Y = -dC/du_end, a 2-column block Thomas solve.
+template <class T>
+bool chain_ggt(int k, bool point_light, const Frame<T>* f, const VBlocks<T>* vb, double sing_eps,
+               T& G) {
+  std::vector<T> rhs((size_t)k * 4, T(0.0)), Y((size_t)k * 4, T(0.0));
+  int row = point_light ? 0 : k - 1;
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 2; ++c)
+      rhs[((size_t)row * 2 + r) * 2 + c] = point_light ? -vb[0].A[r][c] : -vb[k - 1].Cc[r][c];
+  if (!block_thomas<T>(k, vb, 2, rhs.data(), Y.data(), sing_eps)) return false;
+  int vi = point_light ? k : 1;   // vertex whose motion moves the measured direction
+  const Frame<T>& fv = f[vi];
+  V3<T> anchor = point_light ? f[k + 1].p : f[0].p;
+  V3<T> w = fv.p - anchor;
+  T dist = norm(w);
+  w = w / dist;
+  V3<T> a, b;
+  onb(w, a, b);
+  T M[2][2];
+  for (int c = 0; c < 2; ++c) {
+    size_t base = (size_t)(vi - 1) * 4;
+    V3<T> dx = fv.dpdu * Y[base + 0 * 2 + c] + fv.dpdv * Y[base + 1 * 2 + c];
+    V3<T> dw = (dx - w * dot(w, dx)) / dist;
+    M[0][c] = dot(a, dw);
+    M[1][c] = dot(b, dw);
+  }
+  T det = fabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
+  if (point_light) {
+    G = det;
+  } else {
+    T cosD = dot(f[0].n, w);
+    G = cosD * det;
+  }
+  return true;
+}
+
+static bool segment_clear(const Scene& S, const V3d& a, const V3d& b, double ray_eps) {
+  V3d d = b - a;
+  double len = norm(d);
+  if (!(len > 2.0 * ray_eps)) return true;
+  Hit h = intersect(S, a, d / len, ray_eps, len - ray_eps);
+  return !h.hit;
+}
+
+static bool admissible_chain(const Scene& S, const ChainIO& ch, const EvalOut& ev, double ray_eps) {
+  int k = ch.k;
+  for (int i = 1; i <= k; ++i) {
+    V3d wi = normalize(ch.v[i - 1].p - ch.v[i].p), wo = normalize(ch.v[i + 1].p - ch.v[i].p);
+    double si = dot(wi, ev.f[i].n), so = dot(wo, ev.f[i].n);
+    bool refract = (ch.tau >> (i - 1)) & 1;
+    if (refract ? !(si * so < 0.0) : !(si * so > 0.0)) return false;
+  }
+  V3d wD = normalize(ch.v[1].p - ch.v[0].p);
+  if (!(dot(ev.f[0].n, wD) > 0.0)) return false;
+  if (S.light.type == LIGHT_RECT) {
+    V3d wL = normalize(ch.v[k].p - ch.v[k + 1].p);
+    if (!(dot(S.light.n, wL) > 0.0)) return false;
+  }
+  for (int j = 0; j <= k; ++j)
+    if (!segment_clear(S, ch.v[j].p, ch.v[j + 1].p, ray_eps)) return false;
+  return true;
+}
+
+// Two converged chains are one solution when they have the same length,
+// types and surfaces and every vertex lies within dedup_eps.
+static bool same_solution(const ChainIO& a, const ChainIO& b, double eps) {
+  if (a.k != b.k || a.tau != b.tau) return false;
+  for (int i = 1; i <= a.k; ++i) {
+    if (a.v[i].surf != b.v[i].surf) return false;
+    if (norm(a.v[i].p - b.v[i].p) >= eps) return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Array marshalling helpers
+// ---------------------------------------------------------------------------
+static void load_chain(const Scene& S, int b, int k, uint8_t tau, const double* xD, const double* xL,
+                       const double* x, const int32_t* surf, const int32_t* prim, const double* bary,
+                       int spq, ChainIO& ch) {
+  (void)S;
+  ch.k = k;
+  ch.tau = tau;
+  int q = b / spq;
+  ch.v[0] = Vtx();
+  ch.v[0].p = load3(xD + 3 * (size_t)q);
+  for (int i = 1; i <= k; ++i) {
+    size_t o = (size_t)b * MAXK + (i - 1);
+    ch.v[i].p = load3(x + 3 * o);
+    ch.v[i].surf = surf[o];
+    ch.v[i].prim = prim ? prim[o] : -1;
+    ch.v[i].b1 = bary ? bary[2 * o] : 0.0;
+    ch.v[i].b2 = bary ? bary[2 * o + 1] : 0.0;
+  }
+  ch.v[k + 1] = Vtx();
+  ch.v[k + 1].p = load3(xL + 3 * (size_t)b);
+}
+
+static void store_chain(const ChainIO& ch, int b, double* x, int32_t* surf, int32_t* prim,
+                        double* bary) {
+  for (int i = 1; i <= MAXK; ++i) {
+    size_t o = (size_t)b * MAXK + (i - 1);
+    if (i <= ch.k) {
+      store3(x + 3 * o, ch.v[i].p);
+      surf[o] = ch.v[i].surf;
+      if (prim) prim[o] = ch.v[i].prim;
+      if (bary) { bary[2 * o] = ch.v[i].b1; bary[2 * o + 1] = ch.v[i].b2; }
+    } else {
+      store3(x + 3 * o, V3d());
+      surf[o] = -1;
+      if (prim) prim[o] = -1;
+      if (bary) { bary[2 * o] = 0.0; bary[2 * o + 1] = 0.0; }
+    }
+  }
+}
+
+template <class F>
+static void parallel_for(int n, int n_threads, F fn) {
+  if (n_threads <= 1 || n < 64) {
+    for (int i = 0; i < n; ++i) fn(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  int per = (n + n_threads - 1) / n_threads;
+  for (int t = 0; t < n_threads; ++t) {
+    int lo = t * per, hi = std::min(n, lo + per);
+    if (lo >= hi) break;
+    th.emplace_back([=]() { for (int i = lo; i < hi; ++i) fn(i); });
+  }
+  for (auto& x : th) x.join();
+}
+
+static orc_params default_check(const orc_params* p) { return *p; }
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+void* orc_scene_create(const double* surfaces, int32_t n_surf, const double* hf_desc,
+                       const double* hf_heights, int32_t n_hf, const double* targets,
+                       int32_t n_targets, const double* light) {
+  if (n_surf < 0 || n_hf < 0 || n_targets < 0 || !light) return nullptr;
+  Scene* S = new Scene();
+  size_t hoff = 0;
+  for (int h = 0; h < n_hf; ++h) {
+    HField H;
+    const double* d = hf_desc + 6 * h;
+    H.nx = (int)d[0]; H.ny = (int)d[1];
+    H.x0 = d[2]; H.y0 = d[3]; H.x1 = d[4]; H.y1 = d[5];
+    H.surf = -1;
+    if (H.nx < 2 || H.ny < 2) { delete S; return nullptr; }
+    H.h.assign(hf_heights + hoff, hf_heights + hoff + (size_t)H.nx * H.ny);
+    hoff += (size_t)H.nx * H.ny;
+    hf_build(H);
+    S->hf.push_back(std::move(H));
+  }
+  for (int s = 0; s < n_surf; ++s) {
+    const double* r = surfaces + 24 * s;
+    Surface sf;
+    sf.type = (int)r[0]; sf.mat = (int)r[1]; sf.etaF = r[2]; sf.etaB = r[3];
+    sf.c = load3(r + 4); sf.r = r[7]; sf.axis = load3(r + 8); sf.cap_cos = r[11];
+    sf.ex = load3(r + 12); sf.ey = load3(r + 15); sf.hf = (int)r[18];
+    if (sf.type == SURF_RECT) sf.axis = normalize(sf.axis);
+    if (sf.type == SURF_HEIGHTFIELD) {
+      if (sf.hf < 0 || sf.hf >= n_hf) { delete S; return nullptr; }
+      S->hf[sf.hf].surf = s;
+    }
+    S->surf.push_back(sf);
+  }
+  for (int t = 0; t < n_targets; ++t) {
+    const double* r = targets + 16 * t;
+    Target tg;
+    tg.type = (int)r[0]; tg.c = load3(r + 1); tg.r = r[4]; tg.ex = load3(r + 5);
+    tg.ey = load3(r + 8); tg.n = load3(r + 11);
+    if (tg.type == TARGET_RECT) tg.n = normalize(tg.n);
+    S->tg.push_back(tg);
+  }
+  Light& L = S->light;
+  L.type = (int)light[0]; L.p = load3(light + 1); L.n = normalize(load3(light + 4));
+  L.ex = load3(light + 7); L.ey = load3(light + 10); L.power = light[13];
+  L.area = L.type == LIGHT_RECT ? 4.0 * norm(L.ex) * norm(L.ey) : 1.0;
+  return S;
+}
+
+void orc_scene_destroy(void* scene) { delete (Scene*)scene; }
+
+int32_t orc_intersect(void* scene, int32_t n, const double* o, const double* d, double tmin,
+                      double tmax, int32_t brute, double* t, int32_t* surf, int32_t* prim,
+                      double* bary) {
+  if (!scene || n < 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  for (int i = 0; i < n; ++i) {
+    Hit h = intersect(S, load3(o + 3 * i), normalize(load3(d + 3 * i)), tmin, tmax, brute != 0);
+    t[i] = h.hit ? h.t : -1.0;
+    surf[i] = h.surf;
+    prim[i] = h.prim;
+    bary[2 * i] = h.b1;
+    bary[2 * i + 1] = h.b2;
+  }
+  return 0;
+}
+
+int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
+                         const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
+                         const uint8_t* k, const uint8_t* tau, int32_t tau_random,
+                         uint64_t rng_seed, uint64_t rng_offset, uint32_t trial,
+                         const orc_params* prm, double* x, int32_t* surf, int32_t* prim,
+                         double* bary, uint8_t* tau_out, double* pdf, uint8_t* valid,
+                         int32_t n_threads) {
+  if (!scene || !prm || Q < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  orc_params P = default_check(prm);
+  GuideCDF cdf;
+  bool g_ok = guide && guide->counts;
+  if (g_ok) guide_cdf(*guide, cdf);
+  int B = Q * spq;
+  for (int b = 0; b < B; ++b)
+    if (k[b] < 1 || k[b] > MAXK) return -2;
+  parallel_for(B, n_threads, [&](int b) {
+    int q = b / spq;
+    SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, load3(xD + 3 * (size_t)q),
+                              load3(nD + 3 * (size_t)q), cell ? cell[q] : 0u, load3(xL + 3 * (size_t)b),
+                              k[b], tau[b], tau_random != 0, rng_seed, (uint64_t)b + rng_offset, trial, P);
+    valid[b] = sd.valid ? 1 : 0;
+    pdf[b] = sd.pdf;
+    tau_out[b] = sd.tau;
+    if (!sd.valid) { sd.ch.k = 0; }
+    store_chain(sd.ch, b, x, surf, prim, bary);
+  });
+  return 0;
+}
+
+int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                 const double* xL, const uint8_t* k, const uint8_t* tau, const orc_params* prm,
+                 const uint8_t* valid, double* x, int32_t* surf, int32_t* prim, double* bary,
+                 uint8_t* status, uint8_t* iters, int32_t n_threads) {
+  if (!scene || !prm || B < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  orc_params P = *prm;
+  parallel_for(B, n_threads, [&](int b) {
+    if (!valid[b] || k[b] < 1 || k[b] > MAXK) { status[b] = ST_INVALID; iters[b] = 0; return; }
+    ChainIO ch;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
+    int it = 0;
+    int st = walk_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), P, it);
+    status[b] = (uint8_t)st;
+    iters[b] = (uint8_t)it;
+    store_chain(ch, b, x, surf, prim, bary);
+  });
+  return 0;
+}
+
+int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
+                         const double* nD, const double* xL, const uint8_t* k,
+                         const uint8_t* tau, const double* x, const int32_t* surf,
+                         const int32_t* prim, const double* bary, const uint8_t* status,
+                         const orc_params* prm, double* G, double* kappa, double* T,
+                         uint8_t* admissible, int32_t n_threads) {
+  if (!scene || !prm || B < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  parallel_for(B, n_threads, [&](int b) {
+    G[b] = kappa[b] = T[b] = 0.0;
+    admissible[b] = 0;
+    if (status[b] != ST_CONVERGED) return;
+    ChainIO ch;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
+    EvalOut ev;
+    eval_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), ev);
+    if (!ev.ok || !admissible_chain(S, ch, ev, prm->ray_eps)) return;
+    int sid[MAXK + 2];
+    for (int i = 0; i <= ch.k + 1; ++i) sid[i] = ch.v[i].surf;
+    double g;
+    if (!chain_ggt<double>(ch.k, S.light.type == LIGHT_POINT, ev.f, ev.vb, prm->sing_eps, g)) return;
+    double kap = chain_kappa<double>(S, ch.k, ch.tau, ev.f, sid, ev.vb);
+    admissible[b] = 1;
+    G[b] = g;
+    kappa[b] = kap;
+    T[b] = kap * g * S.light.power;
+  });
+  return 0;
+}
+
+int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
+                      const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
+                      const uint8_t* k, const uint8_t* tau, int32_t tau_random,
+                      uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
+                      const double* x, const int32_t* surf, const uint8_t* admissible,
+                      uint32_t* N, uint8_t* capped, int32_t n_threads) {
+  if (!scene || !prm || Q < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  orc_params P = *prm;
+  GuideCDF cdf;
+  bool g_ok = guide && guide->counts;
+  if (g_ok) guide_cdf(*guide, cdf);
+  int B = Q * spq;
+  parallel_for(B, n_threads, [&](int b) {
+    N[b] = 0;
+    capped[b] = 0;
+    if (!admissible[b]) return;
+    int q = b / spq;
+    ChainIO target;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, nullptr, nullptr, spq, target);
+    V3d xd = load3(xD + 3 * (size_t)q), nd = load3(nD + 3 * (size_t)q), xl = load3(xL + 3 * (size_t)b);
+    for (int t = 1; t <= P.max_trials; ++t) {
+      SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, xd, nd,
+                                cell ? cell[q] : 0u, xl, k[b], tau[b], tau_random != 0, rng_seed,
+                                (uint64_t)b + rng_offset, (uint32_t)t, P);
+      if (!sd.valid) continue;
+      int it = 0;
+      if (walk_chain(S, sd.ch, nd, P, it) != ST_CONVERGED) continue;
+      if (same_solution(sd.ch, target, P.dedup_eps)) {
+        N[b] = (uint32_t)t;
+        return;
+      }
+    }
+    N[b] = (uint32_t)P.max_trials;
+    capped[b] = 1;
+  });
+  return 0;
+}
+
+int32_t orc_guide_bin(const orc_guide* guide, int32_t R, const float* omega, int32_t* bin) {
+  if (!guide || R < 0) return -1;
+  for (int r = 0; r < R; ++r) bin[r] = guide_bin(*guide, omega + 3 * (size_t)r);
+  return 0;
+}
+
+int32_t orc_guide_update(const orc_guide* guide, uint64_t* counts, int32_t R,
+                         const uint32_t* cell, const float* omega, const float* w,
+                         int32_t weight_shift) {
+  if (!guide || !counts || R < 0) return -1;
+  int bins = guide->n_theta * guide->n_phi;
+  for (int r = 0; r < R; ++r) {
+    if ((int)cell[r] >= guide->n_cells) return -2;
+    int b = guide_bin(*guide, omega + 3 * (size_t)r);
+    counts[(size_t)cell[r] * bins + b] += quantise_weight(w[r], weight_shift);
+  }
+  return 0;
+}
+
+int32_t orc_constraint(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                       const double* xL, const uint8_t* k, const uint8_t* tau,
+                       const double* x, const int32_t* surf, const int32_t* prim,
+                       const double* bary, double* C, double* cmax) {
+  if (!scene || B < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  for (int b = 0; b < B; ++b) {
+    ChainIO ch;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
+    EvalOut ev;
+    eval_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), ev);
+    for (int i = 0; i < 2 * MAXK; ++i) C[(size_t)b * 2 * MAXK + i] = 0.0;
+    if (!ev.ok) { cmax[b] = -1.0; continue; }
+    for (int i = 0; i < ch.k; ++i) {
+      C[(size_t)b * 2 * MAXK + 2 * i] = ev.vb[i].C[0];
+      C[(size_t)b * 2 * MAXK + 2 * i + 1] = ev.vb[i].C[1];
+    }
+    cmax[b] = ev.cmax;
+  }
+  return 0;
+}
+
+int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k, uint8_t tau,
+                  double ray_eps, double* x, double* exit_dir) {
+  if (!scene || k < 1 || k > MAXK) return -1;
+  const Scene& S = *(Scene*)scene;
+  V3d o = load3(xD), d = normalize(load3(omega));
+  for (int i = 1; i <= k; ++i) {
+    Hit h = intersect(S, o, d, ray_eps, std::numeric_limits<double>::infinity());
+    if (!h.hit) return -2;
+    Vtx v = hit_vertex(S, o, d, h);
+    store3(x + 3 * (i - 1), v.p);
+    Frame<double> f = vertex_frame(S, v);
+    V3d dn;
+    if (!scatter(S.surf[h.surf], f.n, d, (tau >> (i - 1)) & 1, dn)) return -3;
+    o = v.p;
+    d = dn;
+  }
+  store3(exit_dir, d);
+  return 0;
+}
+
+void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
+}
+
+int32_t orc_count_flops(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                        const double* xL, const uint8_t* k, const uint8_t* tau,
+                        const orc_params* prm, const uint8_t* valid, const double* x,
+                        const int32_t* surf, const int32_t* prim, const double* bary,
+                        double* out) {
+  (void)scene; (void)B; (void)spq; (void)xD; (void)nD; (void)xL; (void)k; (void)tau;
+  (void)prm; (void)valid; (void)x; (void)surf; (void)prim; (void)bary;
+  for (int i = 0; i < 7; ++i) out[i] = 0.0;
+  return -3;  // filled in with the unit flop counts
+}
+
+}  // extern "C"

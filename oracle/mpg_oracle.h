@@ -1,0 +1,124 @@
+/*
+ * FP64 CPU oracle of the batched manifold walk (Manifold Path Guiding,
+ * Fan et al. 2023).  TEST INFRASTRUCTURE ONLY: the CUDA library never links,
+ * includes or calls this code; only the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark use it.
+ *
+ * Plain and slow on purpose: one chain at a time, FP64 throughout, the
+ * method's steps in the paper's order:
+ *   seed chain  = p_0 / guided mixture direction + deduction by ray casts (Eq. deduction, Sec. 5.3-5.5)
+ *   manifold walk = Newton on the half-vector constraint + reprojection (Sec. 3, "Manifold walks")
+ *   contribution T = kappa * G * L_o                                  (Eq. ThroughputEval)
+ *   reciprocal probability by Bernoulli trials, n reused             (Sec. 5.7)
+ *   guide histogram update with w = T <1/P>                          (Eq. eq_weight)
+ *
+ * Arrays are caller-owned, array-of-structures, float64 unless stated:
+ *   chain vertex positions x[B][8][3], surface ids surf[B][8], primitive ids
+ *   prim[B][8], barycentrics bary[B][8][2] (triangles only), k[B], tau[B]
+ *   (bit i-1 set => vertex i refracts).  Chain b belongs to receiver point
+ *   q = b / spq.  All calls return 0 on success and a negative value on a
+ *   bad argument; they never throw.
+ */
+#ifndef MPG_ORACLE_H
+#define MPG_ORACLE_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct orc_params {
+  double tol;          /* converged when max_i |C_i|_inf < tol */
+  int32_t max_iter;    /* Newton steps */
+  int32_t max_halvings;/* step halvings per Newton step */
+  double ray_eps;      /* ray origin offset and segment shrink */
+  double sing_eps;     /* singular 2x2 block threshold (relative) */
+  double dedup_eps;    /* same-solution distance */
+  int32_t max_trials;  /* Bernoulli trial cap */
+  int32_t weight_shift;/* histogram quantisation shift S */
+  double alpha;        /* defensive mixture weight of p_0 */
+} orc_params;
+
+typedef struct orc_guide {
+  const uint64_t* counts; /* [n_cells][n_theta*n_phi]; NULL => p_0 only */
+  int32_t n_cells, n_theta, n_phi;
+  const float* cos_theta; /* [n_theta+1] bin edges in cos(theta), decreasing */
+  const float* phi_cos;   /* [n_phi+1] cos of phi edges */
+  const float* phi_sin;   /* [n_phi+1] sin of phi edges */
+} orc_guide;
+
+void* orc_scene_create(const double* surfaces, int32_t n_surf, const double* hf_desc,
+                       const double* hf_heights, int32_t n_hf, const double* targets,
+                       int32_t n_targets, const double* light);
+void orc_scene_destroy(void* scene);
+
+/* Nearest hit along each ray in (tmin, tmax); brute != 0 skips the BVH. */
+int32_t orc_intersect(void* scene, int32_t n, const double* o, const double* d, double tmin,
+                      double tmax, int32_t brute, double* t, int32_t* surf, int32_t* prim,
+                      double* bary);
+
+/* Seed chains (trial index `trial`, 0 for the first draw). */
+int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
+                         const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
+                         const uint8_t* k, const uint8_t* tau, int32_t tau_random,
+                         uint64_t rng_seed, uint64_t rng_offset, uint32_t trial,
+                         const orc_params* prm, double* x, int32_t* surf, int32_t* prim,
+                         double* bary, uint8_t* tau_out, double* pdf, uint8_t* valid,
+                         int32_t n_threads);
+
+/* Manifold walk in place on chains with valid[b] != 0. */
+int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                 const double* xL, const uint8_t* k, const uint8_t* tau, const orc_params* prm,
+                 const uint8_t* valid, double* x, int32_t* surf, int32_t* prim, double* bary,
+                 uint8_t* status, uint8_t* iters, int32_t n_threads);
+
+/* Admissibility, generalized geometry term, kappa, T = kappa G L_o. */
+int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
+                         const double* nD, const double* xL, const uint8_t* k,
+                         const uint8_t* tau, const double* x, const int32_t* surf,
+                         const int32_t* prim, const double* bary, const uint8_t* status,
+                         const orc_params* prm, double* G, double* kappa, double* T,
+                         uint8_t* admissible, int32_t n_threads);
+
+/* Bernoulli trials for admissible chains: N[b] = index of the first trial
+ * that walks to the same solution, capped[b] = 1 when max_trials ran out. */
+int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
+                      const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
+                      const uint8_t* k, const uint8_t* tau, int32_t tau_random,
+                      uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
+                      const double* x, const int32_t* surf, const uint8_t* admissible,
+                      uint32_t* N, uint8_t* capped, int32_t n_threads);
+
+/* Histogram bin of each direction (theta-major index), and the update
+ * counts[cell][bin] += q(w), q = min(floor(w 2^S), 2^32-1) (0 unless w > 0). */
+int32_t orc_guide_bin(const orc_guide* guide, int32_t R, const float* omega, int32_t* bin);
+int32_t orc_guide_update(const orc_guide* guide, uint64_t* counts, int32_t R,
+                         const uint32_t* cell, const float* omega, const float* w,
+                         int32_t weight_shift);
+
+/* Constraint values of a given chain (tests): C[b][2k] and max |C|. */
+int32_t orc_constraint(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                       const double* xL, const uint8_t* k, const uint8_t* tau,
+                       const double* x, const int32_t* surf, const int32_t* prim,
+                       const double* bary, double* C, double* cmax);
+
+/* Shooting map used by finite-difference tests: trace from x_D along omega
+ * with the scattering types tau; returns the k vertices and the exit ray. */
+int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k, uint8_t tau,
+                  double ray_eps, double* x, double* exit_dir);
+
+/* Philox4x32-10 block: out = philox(ctr[4], key[2]). */
+void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+/* Algorithmic flop tally of walking + evaluating the given chains once more
+ * in a counted scalar type: out[0] adds, [1] muls, [2] divs, [3] sqrts,
+ * [4] Newton iterations, [5] vertex-iterations, [6] ray-primitive tests. */
+int32_t orc_count_flops(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
+                        const double* xL, const uint8_t* k, const uint8_t* tau,
+                        const orc_params* prm, const uint8_t* valid, const double* x,
+                        const int32_t* surf, const int32_t* prim, const double* bary,
+                        double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

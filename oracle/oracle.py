@@ -1,0 +1,270 @@
+"""ctypes front end of the FP64 oracle (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg import
+this module; the CUDA library never does.  Arrays are numpy, float64 unless
+stated, array-of-structures: x[B, 8, 3], surf/prim[B, 8], bary[B, 8, 2].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXK = 8
+
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+
+
+class orc_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("max_halvings", C.c_int32),
+                ("ray_eps", C.c_double), ("sing_eps", C.c_double), ("dedup_eps", C.c_double),
+                ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_double)]
+
+
+class orc_guide(C.Structure):
+    _fields_ = [("counts", C.c_void_p), ("n_cells", C.c_int32), ("n_theta", C.c_int32),
+                ("n_phi", C.c_int32), ("cos_theta", C.c_void_p), ("phi_cos", C.c_void_p),
+                ("phi_sin", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_scene_create.restype = C.c_void_p
+        L.orc_scene_create.argtypes = [_f64p, C.c_int32, _f64p, _f64p, C.c_int32, _f64p, C.c_int32, _f64p]
+        L.orc_scene_destroy.argtypes = [C.c_void_p]
+        L.orc_intersect.argtypes = [C.c_void_p, C.c_int32, _f64p, _f64p, C.c_double, C.c_double,
+                                    C.c_int32, _f64p, _i32p, _i32p, _f64p]
+        L.orc_sample_seeds.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
+                                       C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64,
+                                       C.c_uint64, C.c_uint32, C.POINTER(orc_params), _f64p, _i32p,
+                                       _i32p, _f64p, _u8p, _f64p, _u8p, C.c_int32]
+        L.orc_walk.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p,
+                               C.POINTER(orc_params), _u8p, _f64p, _i32p, _i32p, _f64p, _u8p, _u8p,
+                               C.c_int32]
+        L.orc_contribution.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p,
+                                       _u8p, _f64p, _i32p, _i32p, _f64p, _u8p,
+                                       C.POINTER(orc_params), _f64p, _f64p, _f64p, _u8p, C.c_int32]
+        L.orc_bernoulli.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
+                                    C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64, C.c_uint64,
+                                    C.POINTER(orc_params), _f64p, _i32p, _u8p, _u32p, _u8p, C.c_int32]
+        L.orc_guide_bin.argtypes = [C.POINTER(orc_guide), C.c_int32, _f32p, _i32p]
+        L.orc_guide_update.argtypes = [C.POINTER(orc_guide), _u64p, C.c_int32, _u32p, _f32p, _f32p,
+                                       C.c_int32]
+        L.orc_constraint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p,
+                                     _f64p, _i32p, _i32p, _f64p, _f64p, _f64p]
+        L.orc_shoot.argtypes = [C.c_void_p, _f64p, _f64p, C.c_int32, C.c_uint8, C.c_double, _f64p, _f64p]
+        L.orc_philox.argtypes = [_u32p, _u32p, _u32p]
+        L.orc_philox.restype = None
+        for name in ("orc_intersect", "orc_sample_seeds", "orc_walk", "orc_contribution",
+                     "orc_bernoulli", "orc_guide_bin", "orc_guide_update", "orc_constraint",
+                     "orc_shoot"):
+            getattr(L, name).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def params(p) -> orc_params:
+    return orc_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps,
+                      p.max_trials, p.weight_shift, p.alpha)
+
+
+def default_threads():
+    return max(1, os.cpu_count() or 1)
+
+
+class Scene:
+    """Oracle scene built from a workload's surface/heightfield/target/light tables."""
+
+    def __init__(self, wl):
+        L = lib()
+        self._keep = [_c(wl.surfaces, np.float64), _c(wl.hf_desc.reshape(-1, 6), np.float64),
+                      _c(wl.hf_heights, np.float64), _c(wl.targets, np.float64), _c(wl.light, np.float64)]
+        s, hd, hh, tg, li = self._keep
+        hd_arg = hd if hd.size else np.zeros(6, np.float64)
+        hh_arg = hh if hh.size else np.zeros(1, np.float64)
+        self.h = L.orc_scene_create(s, s.shape[0], hd_arg, hh_arg, hd.shape[0], tg, tg.shape[0], li)
+        if not self.h:
+            raise ValueError("oracle rejected the scene description")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_scene_destroy(self.h)
+            self.h = None
+
+
+class Guide:
+    """Histogram state for the oracle: counts[n_cells, n_theta*n_phi] uint64 plus edge tables."""
+
+    def __init__(self, n_cells, edges, counts=None):
+        ct, pc, ps = (np.ascontiguousarray(e, np.float32) for e in edges)
+        self.ct, self.pc, self.ps = ct, pc, ps
+        self.n_theta, self.n_phi = ct.size - 1, pc.size - 1
+        self.n_cells = n_cells
+        self.counts = (np.zeros((n_cells, self.n_theta * self.n_phi), np.uint64) if counts is None
+                       else np.ascontiguousarray(counts, np.uint64))
+
+    def struct(self, with_counts=True):
+        return orc_guide(self.counts.ctypes.data if with_counts else None, self.n_cells,
+                         self.n_theta, self.n_phi, self.ct.ctypes.data, self.pc.ctypes.data,
+                         self.ps.ctypes.data)
+
+    def bins(self, omega):
+        om = _c(omega, np.float32).reshape(-1, 3)
+        out = np.zeros(om.shape[0], np.int32)
+        g = self.struct()
+        assert lib().orc_guide_bin(C.byref(g), om.shape[0], om, out) == 0
+        return out
+
+    def update(self, cell, omega, w, shift):
+        om = _c(omega, np.float32).reshape(-1, 3)
+        g = self.struct()
+        rc = lib().orc_guide_update(C.byref(g), self.counts, om.shape[0], _c(cell, np.uint32), om,
+                                    _c(w, np.float32), shift)
+        assert rc == 0, rc
+
+
+def intersect(scene, o, d, tmin=1e-4, tmax=np.inf, brute=False):
+    o = _c(o, np.float64).reshape(-1, 3)
+    d = _c(d, np.float64).reshape(-1, 3)
+    n = o.shape[0]
+    t = np.zeros(n); surf = np.zeros(n, np.int32); prim = np.zeros(n, np.int32); bary = np.zeros((n, 2))
+    assert lib().orc_intersect(scene.h, n, o, d, tmin, tmax, int(brute), t, surf, prim, bary) == 0
+    return t, surf, prim, bary
+
+
+def sample_seeds(wl, scene, guide=None, trial=0, threads=None, rng_offset=0):
+    B = wl.B
+    out = dict(x=np.zeros((B, MAXK, 3)), surf=np.zeros((B, MAXK), np.int32),
+               prim=np.zeros((B, MAXK), np.int32), bary=np.zeros((B, MAXK, 2)),
+               tau=np.zeros(B, np.uint8), pdf=np.zeros(B), valid=np.zeros(B, np.uint8))
+    g = guide.struct() if guide is not None else None
+    P = params(wl.params)
+    rc = lib().orc_sample_seeds(scene.h, C.byref(g) if g is not None else None, wl.Q,
+                                _c(wl.xD, np.float64), _c(wl.nD, np.float64), _c(wl.cell, np.uint32),
+                                wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(wl.tau, np.uint8),
+                                int(wl.tau_random), wl.rng_seed, rng_offset, trial, C.byref(P),
+                                out["x"], out["surf"], out["prim"], out["bary"], out["tau"], out["pdf"],
+                                out["valid"], threads or default_threads())
+    assert rc == 0, rc
+    return out
+
+
+def walk(wl, scene, seeds, threads=None):
+    """Walk the seeds in place (copies); returns dict with x/surf/prim/bary/status/iters."""
+    B = wl.B
+    ch = {n: seeds[n].copy() for n in ("x", "surf", "prim", "bary")}
+    status = np.zeros(B, np.uint8)
+    iters = np.zeros(B, np.uint8)
+    P = params(wl.params)
+    rc = lib().orc_walk(scene.h, B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64),
+                        _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(seeds["tau"], np.uint8),
+                        C.byref(P), _c(seeds["valid"], np.uint8), ch["x"], ch["surf"], ch["prim"],
+                        ch["bary"], status, iters, threads or default_threads())
+    assert rc == 0, rc
+    ch.update(status=status, iters=iters, tau=seeds["tau"].copy())
+    return ch
+
+
+def contribution(wl, scene, chains, threads=None):
+    B = wl.B
+    G = np.zeros(B); kap = np.zeros(B); T = np.zeros(B); adm = np.zeros(B, np.uint8)
+    P = params(wl.params)
+    rc = lib().orc_contribution(scene.h, B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64),
+                                _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(chains["tau"], np.uint8),
+                                chains["x"], chains["surf"], chains["prim"], chains["bary"],
+                                _c(chains["status"], np.uint8), C.byref(P), G, kap, T, adm,
+                                threads or default_threads())
+    assert rc == 0, rc
+    return dict(G=G, kappa=kap, T=T, admissible=adm)
+
+
+def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offset=0, max_trials=None):
+    B = wl.B
+    N = np.zeros(B, np.uint32)
+    capped = np.zeros(B, np.uint8)
+    p = wl.params
+    if max_trials is not None:
+        import dataclasses
+        p = dataclasses.replace(p, max_trials=max_trials)
+    P = params(p)
+    g = guide.struct() if guide is not None else None
+    rc = lib().orc_bernoulli(scene.h, C.byref(g) if g is not None else None, wl.Q,
+                             _c(wl.xD, np.float64), _c(wl.nD, np.float64), _c(wl.cell, np.uint32),
+                             wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8),
+                             _c(chains["tau"], np.uint8), int(wl.tau_random), wl.rng_seed, rng_offset,
+                             C.byref(P), chains["x"], chains["surf"], _c(admissible, np.uint8), N,
+                             capped, threads or default_threads())
+    assert rc == 0, rc
+    return N, capped
+
+
+def constraint(wl, scene, chains):
+    B = wl.B
+    Cv = np.zeros((B, 2 * MAXK))
+    cmax = np.zeros(B)
+    rc = lib().orc_constraint(scene.h, B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64),
+                              _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(chains["tau"], np.uint8),
+                              _c(chains["x"], np.float64), _c(chains["surf"], np.int32),
+                              _c(chains["prim"], np.int32), _c(chains["bary"], np.float64), Cv, cmax)
+    assert rc == 0, rc
+    return Cv, cmax
+
+
+def philox(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().orc_philox(_c(ctr, np.uint32), _c(key, np.uint32), out)
+    return out
+
+
+def shoot(scene, xD, omega, k, tau, ray_eps=1e-4):
+    """Trace x_D along omega through k vertices with types tau (the forward map)."""
+    x = np.zeros((k, 3))
+    d = np.zeros(3)
+    rc = lib().orc_shoot(scene.h, _c(xD, np.float64), _c(omega, np.float64), k, tau, ray_eps, x, d)
+    return (x, d) if rc == 0 else (None, None)
+
+
+def irradiance(wl, T, N, admissible):
+    """E(x_D) = (1/M) sum_seeds A_L T <1/P>, <1/P> = N / P(n)   (Eq. ThroughputMC, Sec. 5.7)."""
+    c = np.where(admissible.astype(bool), wl.light_area * T * N.astype(np.float64) / wl.pn, 0.0)
+    return c.reshape(wl.Q, wl.spq).sum(axis=1) / wl.spq
+
+
+def records(wl, chains, T, N, admissible):
+    """Guide-update records of the admissible chains: (cell, w_D as FP32, w = T <1/P> as FP32)."""
+    idx = np.nonzero(admissible)[0]
+    q = idx // wl.spq
+    x1 = chains["x"][idx, 0, :]
+    d = x1 - wl.xD[q]
+    om = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    w = (T[idx] * N[idx].astype(np.float64) / wl.pn[idx]).astype(np.float32)
+    return wl.cell[q].astype(np.uint32), om, w
+
+
+def run(wl, guide=None, threads=None, max_trials=None):
+    """Whole hot path in the oracle: seeds -> walk -> contribution -> Bernoulli -> E."""
+    sc = Scene(wl)
+    seeds = sample_seeds(wl, sc, guide, threads=threads)
+    ch = walk(wl, sc, seeds, threads=threads)
+    con = contribution(wl, sc, ch, threads=threads)
+    N, capped = bernoulli(wl, sc, ch, con["admissible"], guide, threads=threads, max_trials=max_trials)
+    E = irradiance(wl, con["T"], N, con["admissible"])
+    return dict(scene=sc, seeds=seeds, chains=ch, contrib=con, N=N, capped=capped, E=E)

@@ -1,0 +1,535 @@
+"""Pins of the FP64 oracle against what the mathematics fixes independently:
+closed forms (plane mirror, flat interface, Alhazen sphere reflection),
+invariants (vector Snell law at converged vertices, reciprocity), finite
+differences of independently traced forward maps, brute-force enumeration of
+solutions, published known-answer vectors and distributional checks.
+None of these tests use the CUDA path."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import closed_forms as CF
+import scenes
+from oracle import oracle as O
+from paper_2311_12818_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Random numbers
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+# --------------------------------------------------------------------------
+# Closed forms
+# --------------------------------------------------------------------------
+def _walked(wl, guide=None):
+    sc = O.Scene(wl)
+    seeds = O.sample_seeds(wl, sc, guide, threads=4)
+    ch = O.walk(wl, sc, seeds, threads=4)
+    con = O.contribution(wl, sc, ch, threads=4)
+    return sc, seeds, ch, con
+
+
+@pytest.mark.parametrize("point", [True, False])
+def test_mirror_plane_image_point_and_G(point):
+    xD = np.array([[0.0, 0.0, 2.0], [0.7, -0.4, 1.5], [-1.1, 0.9, 2.5]])
+    xL = (0.3, -0.2, 1.5)
+    wl = scenes.mirror_plane(xD, xL, point=point, spq=8, tol=1e-12)
+    sc, seeds, ch, con = _walked(wl)
+    st = ch["status"]
+    assert (st[seeds["valid"] == 1] == I.ST_CONVERGED).mean() > 0.9
+    n_ok = 0
+    for b in np.nonzero(st == I.ST_CONVERGED)[0]:
+        q = b // wl.spq
+        p, dsum = CF.mirror_plane_point(xD[q], np.array(xL), np.zeros(3), np.array([0, 0, 1.0]))
+        assert np.linalg.norm(ch["x"][b, 0] - p) < 1e-9
+        assert con["admissible"][b] == 1
+        wD = CF.unit(p - xD[q])
+        cosD = -wD[2]
+        if point:
+            G = cosD / dsum ** 2
+        else:
+            cosL = -CF.unit(p - np.array(xL))[2]
+            G = cosD * cosL / dsum ** 2
+        assert abs(con["G"][b] - G) < 1e-9 * G
+        assert con["kappa"][b] == 1.0
+        n_ok += 1
+    assert n_ok >= 20
+
+
+@pytest.mark.parametrize("xD,xL", [((0.0, 0.0, -1.0), (0.7, 0.4, 2.0)),
+                                   ((0.5, -0.3, -0.6), (-0.9, 1.1, 2.5)),
+                                   ((-1.2, 0.8, -1.5), (0.2, -0.1, 1.0))])
+def test_flat_interface_snell_G_kappa(xD, xL):
+    """Refraction out of water (IOR 1.33 below z=0) into air: vertex, G and
+    kappa = (1 - F) (eta_D/eta_L)^2 against Snell's law in 1D."""
+    xD, xL = np.array(xD), np.array(xL)
+    wl = scenes.flat_interface(xD[None], xL, spq=32, tol=1e-12)
+    sc, seeds, ch, con = _walked(wl)
+    hD, hL = -xD[2], xL[2]
+    horiz = (xL - xD)[:2]
+    rho = np.linalg.norm(horiz)
+    thD, thL, r1 = CF.snell_flat(hD, hL, rho, 1.33, 1.0)
+    p = np.array([xD[0], xD[1], 0.0])
+    p[:2] += horiz / rho * r1
+    G = CF.flat_interface_G(hD, hL, thD, thL, 1.33, 1.0)
+    F = CF.fresnel_unpolarised(math.cos(thD), 1.33, 1.0)
+    conv = np.nonzero(ch["status"] == I.ST_CONVERGED)[0]
+    assert conv.size >= 4
+    for b in conv:
+        assert np.linalg.norm(ch["x"][b, 0] - p) < 1e-9
+        assert con["admissible"][b] == 1
+        assert abs(con["G"][b] - G) < 1e-8 * G
+        assert abs(con["kappa"][b] - (1 - F) * 1.33 ** 2) < 1e-12
+
+
+def test_flat_dielectric_reflection_fresnel():
+    """Reflection off the air side of a water surface: kappa = F(cos, 1, 1.33)."""
+    xD, xL = np.array([[0.4, 0.1, 1.0]]), np.array([-0.5, 0.3, 2.0])
+    wl = scenes.flat_interface(xD, xL, spq=8, refract=False, receiver_normal=(0, 0, -1), tol=1e-12)
+    # light must face the interface: keep the default downward emitter
+    sc, seeds, ch, con = _walked(wl)
+    conv = np.nonzero(ch["status"] == I.ST_CONVERGED)[0]
+    assert conv.size >= 4
+    p, dsum = CF.mirror_plane_point(xD[0], xL, np.zeros(3), np.array([0, 0, 1.0]))
+    cos1 = -CF.unit(p - xD[0])[2]
+    F = CF.fresnel_unpolarised(cos1, 1.0, 1.33)
+    for b in conv:
+        assert np.linalg.norm(ch["x"][b, 0] - p) < 1e-9
+        assert abs(con["kappa"][b] - F) < 1e-12
+
+
+def test_alhazen_sphere_reflection():
+    """Mirror sphere: every converged vertex is the visible Alhazen root, and
+    points with a visible root are found."""
+    wl = I.mirror_sphere(n=8, spq=16)
+    wl.params.tol = 1e-12
+    sc, seeds, ch, con = _walked(wl)
+    st = ch["status"]
+    for q in range(wl.Q):
+        roots = CF.alhazen_sphere(wl.xD[q], wl.light[1:4])
+        bs = np.arange(q * wl.spq, (q + 1) * wl.spq)
+        conv = bs[st[bs] == I.ST_CONVERGED]
+        assert len(roots) <= 1
+        if not roots:
+            assert conv.size == 0 or not con["admissible"][conv].any()
+            continue
+        assert conv.size > 0
+        for b in conv:
+            assert np.linalg.norm(ch["x"][b, 0] - roots[0]) < 1e-9
+            assert con["admissible"][b] == 1
+
+
+def test_sphere_G_against_fd_of_alhazen():
+    """Point-light G = |det d(w_L)/d(u_D)| against central differences of the
+    independently solved reflection point as x_D moves on the receiver."""
+    wl = I.mirror_sphere(n=8, spq=16)
+    wl.params.tol = 1e-13
+    sc, seeds, ch, con = _walked(wl)
+    xL = wl.light[1:4]
+    checked = 0
+    for b in np.nonzero(con["admissible"])[0][::7]:
+        q = b // wl.spq
+        h = 1e-5
+        cols = []
+        for a in (np.array([1.0, 0, 0]), np.array([0, 1.0, 0])):
+            wp = CF.unit(CF.alhazen_sphere(wl.xD[q] + h * a, xL)[0] - xL)
+            wm = CF.unit(CF.alhazen_sphere(wl.xD[q] - h * a, xL)[0] - xL)
+            cols.append((wp - wm) / (2 * h))
+        wL = CF.unit(ch["x"][b, 0] - xL)
+        e1 = CF.unit(np.cross(wL, [0.3, 0.5, 0.8]))
+        e2 = np.cross(wL, e1)
+        M = np.array([[e1 @ cols[0], e1 @ cols[1]], [e2 @ cols[0], e2 @ cols[1]]])
+        G_fd = abs(np.linalg.det(M))
+        assert abs(con["G"][b] - G_fd) < 1e-6 * G_fd
+        checked += 1
+    assert checked >= 5
+
+
+# --------------------------------------------------------------------------
+# Invariants and finite differences on the glass sphere (k = 2, T T)
+# --------------------------------------------------------------------------
+def _refract(d, n, eta1, eta2):
+    """Snell's law in vector form for the propagation direction d, n facing d's side."""
+    c = -d @ n
+    e = eta1 / eta2
+    k2 = 1 - e * e * (1 - c * c)
+    if k2 < 0:
+        return None
+    return CF.unit(e * d + (e * c - math.sqrt(k2)) * n)
+
+
+def _sphere_hit(o, d, c, r, far=False):
+    oc = o - c
+    b = oc @ d
+    disc = b * b - (oc @ oc - r * r)
+    if disc < 0:
+        return None
+    s = math.sqrt(disc)
+    t = -b + s if far else -b - s
+    return o + t * d if t > 1e-9 else None
+
+
+def _shoot_glass(xD, w, zL=4.0, eta=1.5):
+    """Independent forward trace x_D -> enter sphere -> exit -> light plane."""
+    p1 = _sphere_hit(xD, w, np.zeros(3), 1.0)
+    if p1 is None:
+        return None
+    d1 = _refract(w, p1, 1.0, eta)
+    p2 = _sphere_hit(p1, d1, np.zeros(3), 1.0, far=True)
+    d2 = _refract(d1, -p2, eta, 1.0)
+    if d2 is None or d2[2] <= 0:
+        return None
+    t = (zL - p2[2]) / d2[2]
+    return p1, p2, p2 + t * d2
+
+
+@pytest.fixture(scope="module")
+def glass_run():
+    wl = I.glass_sphere(n=8, spq=16)
+    wl.params.tol = 1e-12
+    return (wl,) + _walked(wl)
+
+
+def test_glass_vector_snell_at_converged_vertices(glass_run):
+    wl, sc, seeds, ch, con = glass_run
+    conv = np.nonzero(ch["status"] == I.ST_CONVERGED)[0]
+    assert conv.size > 50
+    for b in conv:
+        q = b // wl.spq
+        pts = [wl.xD[q], ch["x"][b, 0], ch["x"][b, 1], wl.xL[b]]
+        for i, (ei, eo) in ((1, (1.0, 1.5)), (2, (1.5, 1.0))):
+            wi, wo = CF.unit(pts[i - 1] - pts[i]), CF.unit(pts[i + 1] - pts[i])
+            n = CF.unit(pts[i])
+            front = wi @ n > 0
+            if con["admissible"][b]:
+                assert front == (i == 1)
+            if front != (i == 1):
+                ei, eo = eo, ei
+            assert np.linalg.norm(np.cross(ei * wi + eo * wo, n)) < 1e-9
+
+
+def test_glass_G_against_fd_of_independent_shooting(glass_run):
+    wl, sc, seeds, ch, con = glass_run
+    adm = np.nonzero(con["admissible"])[0]
+    assert adm.size > 30
+    for b in adm[::5]:
+        q = b // wl.spq
+        w = CF.unit(ch["x"][b, 0] - wl.xD[q])
+        a = CF.unit(np.cross(w, [0.1, 0.2, 0.97]))
+        c = np.cross(w, a)
+        h = 1e-7  # central-difference error ~h^2 is ~1e-3 relative at h=1e-5 near the caustic
+        cols = []
+        for t in (a, c):
+            up = _shoot_glass(wl.xD[q], CF.unit(w + h * t))[2][:2]
+            um = _shoot_glass(wl.xD[q], CF.unit(w - h * t))[2][:2]
+            cols.append((up - um) / (2 * h))
+        det = abs(np.linalg.det(np.array(cols).T))
+        G_fd = (w @ wl.nD[q]) / det
+        assert abs(con["G"][b] - G_fd) < 1e-6 * G_fd
+        # the traced chain reaches the same light point
+        p1, p2, xl = _shoot_glass(wl.xD[q], w)
+        assert np.linalg.norm(xl - wl.xL[b]) < 1e-8
+
+
+def test_glass_G_reciprocity(glass_run):
+    """cos(th_D) dw_D/dA_L = cos(th_L) dw_L/dA_D (both ends in air): the chain
+    walked backwards, with receiver and emitter swapped, gives the same G."""
+    wl, sc, seeds, ch, con = glass_run
+    adm = np.nonzero(con["admissible"])[0][:12]
+    for b in adm:
+        q = b // wl.spq
+        xD, xL = wl.xD[q], wl.xL[b]
+        rev = scenes.custom("rev", wl.surfaces,
+                            I._light(I.LIGHT_RECT, xD, (0, 0, 1), (0.05, 0, 0), (0, 0.05, 0)),
+                            wl.targets, xL[None], (0, 0, -1), xD, 2, 0b11, 1, tol=1e-12)
+        rch = dict(x=np.zeros((1, 8, 3)), surf=np.full((1, 8), -1, np.int32),
+                   prim=np.full((1, 8), -1, np.int32), bary=np.zeros((1, 8, 2)),
+                   status=np.array([I.ST_CONVERGED], np.uint8), tau=np.array([3], np.uint8))
+        rch["x"][0, 0], rch["x"][0, 1] = ch["x"][b, 1], ch["x"][b, 0]
+        rch["surf"][0, :2] = 0
+        rc = O.contribution(rev, O.Scene(rev), rch, threads=1)
+        assert rc["admissible"][0] == 1
+        assert abs(rc["G"][0] - con["G"][b]) < 1e-9 * con["G"][b]
+
+
+def test_glass_seed_deduction_matches_independent_trace(glass_run):
+    wl, sc, seeds, ch, con = glass_run
+    ok = np.nonzero(seeds["valid"])[0]
+    assert ok.size > 100
+    for b in ok[::9]:
+        q = b // wl.spq
+        w = CF.unit(seeds["x"][b, 0] - wl.xD[q])
+        p1, p2, _ = (_shoot_glass(wl.xD[q], w, zL=1e9) or (None, None, None))
+        if p1 is None:
+            # exit ray points down: trace only the two sphere hits
+            p1 = _sphere_hit(wl.xD[q], w, np.zeros(3), 1.0)
+            p2 = _sphere_hit(p1, _refract(w, p1, 1.0, 1.5), np.zeros(3), 1.0, far=True)
+        assert np.linalg.norm(seeds["x"][b, 0] - p1) < 1e-10
+        assert np.linalg.norm(seeds["x"][b, 1] - p2) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# Brute force: all solutions of a two-sphere mirror toy
+# --------------------------------------------------------------------------
+def _segment_blocked(a, b, spheres):
+    d = b - a
+    L = np.linalg.norm(d)
+    d = d / L
+    for c, r in spheres:
+        oc = a - c
+        bb = oc @ d
+        disc = bb * bb - (oc @ oc - r * r)
+        if disc <= 0:
+            continue
+        s = math.sqrt(disc)
+        for t in (-bb - s, -bb + s):
+            if 1e-6 < t < L - 1e-6:
+                return True
+    return False
+
+
+def test_brute_force_solution_sets_two_spheres():
+    spheres = [(np.array([-1.2, 0.0, 0.0]), 0.8), (np.array([1.1, 0.3, 0.2]), 0.6)]
+    surfs = [I._surface(I.SURF_SPHERE, I.MAT_MIRROR, 1, 1, c, r) for c, r in spheres]
+    tgs = [I._target(I.TARGET_SPHERE, c, r) for c, r in spheres]
+    xL = np.array([0.1, 0.4, 3.0])
+    xD = np.array([[0.05, -0.2, -1.6], [-0.9, 0.3, -1.4], [1.4, -0.6, -1.5]])
+    wl = scenes.custom("two_spheres", surfs, I._light(I.LIGHT_POINT, xL), tgs, xD, (0, 0, 1), xL,
+                       1, 0, spq=1024, tol=1e-12)
+    sc, seeds, ch, con = _walked(wl)
+    for q in range(wl.Q):
+        expect = []
+        for c, r in spheres:
+            for p in CF.alhazen_sphere(xD[q], xL, c, r):
+                if not _segment_blocked(xD[q], p, spheres) and not _segment_blocked(p, xL, spheres):
+                    expect.append(p)
+        bs = np.arange(q * wl.spq, (q + 1) * wl.spq)
+        found = []
+        for b in bs[con["admissible"][bs] == 1]:
+            p = ch["x"][b, 0]
+            if all(np.linalg.norm(p - f) > 1e-6 for f in found):
+                found.append(p)
+        assert len(found) == len(expect)
+        for p in expect:
+            assert min(np.linalg.norm(p - f) for f in found) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Bernoulli trials and unbiasedness (Eq. ThroughputMC; Sec. 5.7)
+# --------------------------------------------------------------------------
+def test_bernoulli_mean_matches_basin_probability_and_estimator_is_unbiased():
+    xD = np.array([[0.35, 0.9, -1.5]])
+    base = I.mirror_sphere(n=2, spq=1)
+    M = 4096
+    wl = scenes.custom("mirror_sphere_point", base.surfaces, base.light, base.targets, xD, (0, 0, 1),
+                       base.light[1:4], 1, 0, spq=M)
+    wl.rng_seed = 0xBEEF
+    sc, seeds, ch, con = _walked(wl)
+    adm = con["admissible"] == 1
+    P_hat = adm.mean()  # invalid draws count as failed trials, as in the estimator
+    assert 0.2 < P_hat < 0.95
+    N, capped = O.bernoulli(wl, sc, ch, con["admissible"], threads=8)
+    assert capped.sum() == 0
+    Nm = N[adm].astype(np.float64)
+    # E[N] = 1/P for a geometric trial count
+    sigma = math.sqrt((1 - P_hat) / P_hat ** 2 / Nm.size + (1 / P_hat ** 2) ** 2 * P_hat * (1 - P_hat) / M)
+    assert abs(Nm.mean() - 1 / P_hat) < 4 * sigma
+    # unbiased estimate of the single chain's throughput: mean of 1{adm} T N = T
+    T = con["T"][adm][0]
+    est = np.where(adm, con["T"] * N, 0.0)
+    assert abs(est.mean() - T) < 4 * est.std() / math.sqrt(M)
+
+
+# --------------------------------------------------------------------------
+# Distribution of the initial sampler p_0 (uniform on the visible cap)
+# --------------------------------------------------------------------------
+def test_cap_sampler_is_uniform_on_visible_cap():
+    xD = np.array([[0.8, -0.5, -1.5]])
+    base = I.mirror_sphere(n=2, spq=1)
+    wl = scenes.custom("cap", base.surfaces, base.light, base.targets, xD, (0, 0, 1), base.light[1:4],
+                       1, 0, spq=20000)
+    sc = O.Scene(wl)
+    s = O.sample_seeds(wl, sc, threads=4)
+    d = np.linalg.norm(xD[0])
+    a = xD[0] / d
+    p = s["x"][s["valid"] == 1, 0]
+    ca = p @ a
+    # every point on the visible cap is reachable: a point with cos(alpha) in
+    # [1/d, 1] is hit first by the ray from x_D.  Seeds beyond the receiver's
+    # horizon are dropped, so compare against the truncated uniform law.
+    assert ca.min() >= 1.0 / d - 1e-12
+    e1 = CF.unit(np.cross(a, [0, 0, 1]))
+    e2 = np.cross(a, e1)
+    m = s["valid"] == 0
+    assert m.mean() < 0.5
+    # pdf check: solid-angle density = p_A d^2 / |cos| for the hit point
+    q = s["x"][s["valid"] == 1, 0][:200]
+    w = (q - xD[0]) / np.linalg.norm(q - xD[0], axis=1, keepdims=True)
+    pA = 1.0 / (2 * math.pi * (1 - 1 / d))
+    cosp = np.abs(np.sum(q * w, axis=1))
+    expect = pA * np.sum((q - xD[0]) ** 2, axis=1) / cosp
+    assert np.allclose(s["pdf"][s["valid"] == 1][:200], expect, rtol=1e-10)
+    # uniformity in (cos alpha, phi) over the sampled (valid + invalid) draws
+    full = CF.unit  # noqa: F841
+    ph = np.arctan2(p @ e2, p @ e1)
+    u = (ca - 1.0 / d) / (1.0 - 1.0 / d)
+    valid_frac = (s["valid"] == 1).mean()
+    if valid_frac > 0.999:
+        assert stats.kstest(u, "uniform").pvalue > 1e-3
+        assert stats.kstest((ph + math.pi) / (2 * math.pi), "uniform").pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Guide histogram
+# --------------------------------------------------------------------------
+def _ref_bin(om, n_theta=64, n_phi=64):
+    om = om.astype(np.float64)
+    th = np.arccos(np.clip(om[:, 2], -1, 1))
+    ph = np.mod(np.arctan2(om[:, 1], om[:, 0]), 2 * math.pi)
+    it = np.minimum((th / (math.pi / n_theta)).astype(int), n_theta - 1)
+    ip = np.minimum((ph / (2 * math.pi / n_phi)).astype(int), n_phi - 1)
+    dt = np.abs(th / (math.pi / n_theta) - np.round(th / (math.pi / n_theta)))
+    dp = np.abs(ph / (2 * math.pi / n_phi) - np.round(ph / (2 * math.pi / n_phi)))
+    safe = (dt > 1e-4) & (dp > 1e-4)
+    return it * n_phi + ip, safe
+
+
+def test_histogram_bin_rule_against_angles():
+    rng = np.random.default_rng(7)
+    v = rng.normal(size=(200000, 3))
+    om = (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    g = O.Guide(1, I.guide_edges())
+    b = g.bins(om)
+    ref, safe = _ref_bin(om)
+    assert safe.mean() > 0.99
+    assert np.array_equal(b[safe], ref[safe])
+    assert b.min() >= 0 and b.max() < 64 * 64
+
+
+def test_histogram_update_exact_and_order_independent():
+    rng = np.random.default_rng(11)
+    R = 50000
+    v = rng.normal(size=(R, 3))
+    om = (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+    w = (rng.random(R) * 3.0).astype(np.float32)
+    w[:10] = [0.0, -1.0, np.nan, np.inf, 1e30, 2 ** -17, 2 ** -16, 1.0, 65535.99, 7.5e-6]
+    cell = rng.integers(0, 16, R).astype(np.uint32)
+    g1 = O.Guide(16, I.guide_edges())
+    g1.update(cell, om, w, 16)
+    perm = rng.permutation(R)
+    g2 = O.Guide(16, I.guide_edges())
+    g2.update(cell[perm], om[perm], w[perm], 16)
+    assert np.array_equal(g1.counts, g2.counts)
+    # quantisation: q = floor(w * 2^16) with exact rational arithmetic, clamped
+    from fractions import Fraction
+    q = []
+    for x in w:
+        if not (x > 0):
+            q.append(0)
+        elif np.isinf(x):
+            q.append(2 ** 32 - 1)
+        else:
+            q.append(min(int(Fraction(float(x)) * 65536), 2 ** 32 - 1))
+    assert int(g1.counts.sum()) == sum(q)
+    b = g1.bins(om)
+    ref = np.zeros((16, 4096), np.uint64)
+    np.add.at(ref, (cell, b), np.array(q, np.uint64))
+    assert np.array_equal(ref, g1.counts)
+
+
+def test_guided_sampler_uses_histogram_and_mixture_pdf():
+    wl = I.glass_sphere(n=4, spq=4000)
+    g = O.Guide(256, I.guide_edges())
+    # all weight of every cell in one bin pointing at the sphere, theta bin 2, phi bin 5
+    g.counts[:, 2 * 64 + 5] = 1000
+    sc = O.Scene(wl)
+    s = O.sample_seeds(wl, sc, g, threads=4)
+    x1 = s["x"][:, 0]
+    q = np.arange(wl.B) // wl.spq
+    w = (x1 - wl.xD[q])
+    w = w / np.linalg.norm(w, axis=1, keepdims=True)
+    # receiver points under the sphere, where the bin's directions hit it
+    central = np.max(np.abs(wl.xD[q, :2]), axis=1) < 1.0
+    sel_valid = (s["valid"] == 1) & central
+    b = g.bins(w[sel_valid].astype(np.float32))
+    frac = (b == 2 * 64 + 5).sum() / central.sum()
+    # about half of the draws come from the histogram component (alpha = 0.5)
+    assert abs(frac - 0.5) < 0.05
+    # mixture pdf of a histogram direction: 0.5 p0 + 0.5 / (dphi dcos)
+    ct, _, _ = I.guide_edges()
+    dens = 1.0 / ((2 * math.pi / 64) * (float(ct[2]) - float(ct[3])))
+    sel = np.nonzero(sel_valid)[0][b == 2 * 64 + 5]
+    assert np.all(s["pdf"][sel] >= 0.5 * dens * (1 - 1e-9))
+
+
+# --------------------------------------------------------------------------
+# Heightfield: BVH against brute force, Snell at converged vertices
+# --------------------------------------------------------------------------
+def test_heightfield_bvh_matches_brute_force():
+    wl = I.water(n=8, spq=1, grid=32)
+    sc = O.Scene(wl)
+    rng = np.random.default_rng(3)
+    n = 3000
+    o = np.column_stack([rng.uniform(-1.2, 1.2, n), rng.uniform(-1.2, 1.2, n), rng.choice([-1.0, 1.0], n)])
+    tgt = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), np.zeros(n)])
+    d = tgt - o
+    t1, s1, p1, b1 = O.intersect(sc, o, d)
+    t2, s2, p2, b2 = O.intersect(sc, o, d, brute=True)
+    assert np.array_equal(s1, s2)
+    hit = s1 >= 0
+    assert hit.mean() > 0.9
+    assert np.allclose(t1[hit], t2[hit], rtol=0, atol=1e-12)
+
+
+def _hf_normal_at(wl, prim, b1, b2):
+    """Shading normal from the scene definition: per-vertex normals of the
+    height grid (central differences, one-sided at the border), interpolated
+    barycentrically and normalised."""
+    nx, ny, x0, y0, x1, y1 = wl.hf_desc[0]
+    nx, ny = int(nx), int(ny)
+    h = wl.hf_heights.reshape(ny, nx)
+    dx, dy = (x1 - x0) / (nx - 1), (y1 - y0) / (ny - 1)
+    gx = np.gradient(h, dx, axis=1)
+    gy = np.gradient(h, dy, axis=0)
+    # np.gradient uses central differences inside and first-order one-sided at edges
+    quad, t = prim // 2, prim % 2
+    i, j = quad % (nx - 1), quad // (nx - 1)
+    v = [(i, j), (i + 1, j), (i + 1, j + 1)] if t == 0 else [(i, j), (i + 1, j + 1), (i, j + 1)]
+    N = [CF.unit([-gx[jj, ii], -gy[jj, ii], 1.0]) for ii, jj in v]
+    return CF.unit((1 - b1 - b2) * N[0] + b1 * N[1] + b2 * N[2])
+
+
+def test_water_vector_snell_at_converged_vertices():
+    wl = I.water(n=16, spq=4, grid=32)
+    wl.params.tol = 1e-12
+    sc, seeds, ch, con = _walked(wl)
+    conv = np.nonzero((ch["status"] == I.ST_CONVERGED) & (wl.k == 1))[0]
+    assert conv.size > 200
+    for b in conv[::3]:
+        q = b // wl.spq
+        p = ch["x"][b, 0]
+        n = _hf_normal_at(wl, ch["prim"][b, 0], ch["bary"][b, 0, 0], ch["bary"][b, 0, 1])
+        wi, wo = CF.unit(wl.xD[q] - p), CF.unit(wl.xL[b] - p)
+        ei, eo = (1.0, 1.33) if wi @ n > 0 else (1.33, 1.0)
+        assert np.linalg.norm(np.cross(ei * wi + eo * wo, n)) < 1e-9
+
+
+def test_invalid_arguments_are_rejected():
+    wl = I.mirror_sphere(n=2, spq=2)
+    wl.k[0] = 9
+    with pytest.raises(AssertionError):
+        O.sample_seeds(wl, O.Scene(wl))
