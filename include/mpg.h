@@ -1,0 +1,232 @@
+/*
+ * mpg.h -- C ABI of the GB300 (sm_103a) manifold-walk library libmpg.so.
+ *
+ * The library runs the data-parallel hot path of Manifold Path Guiding
+ * (Fan, Hong, Guo, Zou, Guo, Yan; ACM TOG 42(6), 2023): guided seed chains
+ * between two separators x_D and x_L, Newton manifold walks on the specular
+ * constraints, the contribution T = kappa G L_o of each admissible chain, its
+ * reciprocal probability by Bernoulli trials, the guide-histogram update, and
+ * the adjoint of the receiver irradiance with respect to surface parameters.
+ *
+ * Conventions for every entry point:
+ *   - Return value: MPG_OK (0) or a negative mpg_status.  The message of the
+ *     last failure on the calling host thread is returned by mpg_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - Pointers inside mpg_chains, mpg_guide and the output arguments are DEVICE
+ *     pointers, borrowed: the caller allocates and frees them (for example as
+ *     PyTorch tensors) and keeps them alive until the stream work completes.
+ *     All must be 16-byte aligned.  Arrays are structure-of-arrays with the
+ *     chain index fastest: element (i, c, b) of x lives at x[(i*3 + c)*B + b].
+ *   - Host pointers are used only during the call (scene and guide tables).
+ *   - Every call is asynchronous on the given cudaStream_t (0 = legacy default
+ *     stream); only mpg_ctx_sync() waits.  Device-side failures (for example a
+ *     BVH traversal stack overflow) are recorded in the context and reported by
+ *     the next mpg_ctx_sync().
+ *   - Opaque handles come in create/destroy pairs; destroy accepts NULL.
+ *   - A batch with B = Q = 0 is a valid no-op.
+ *   - Chain b belongs to receiver point q = b / spq.  Vertex types: bit i-1 of
+ *     tau[b] set means vertex i refracts (T), clear means it reflects (R).
+ */
+#ifndef MPG_H
+#define MPG_H
+
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mpg_status;
+#define MPG_OK 0
+#define MPG_ERR_INVALID_ARG (-1)
+#define MPG_ERR_CUDA (-2)
+#define MPG_ERR_OOM (-3)
+#define MPG_ERR_LIMIT (-4)
+#define MPG_ERR_UNSUPPORTED (-5)
+
+#define MPG_MAXK 8
+
+/* Per-chain status written by the walk (uint8). */
+#define MPG_CHAIN_INVALID 0   /* seed could not be deduced (miss, TIR, wrong side) */
+#define MPG_CHAIN_CONVERGED 1 /* max_i |C_i|_inf < tol */
+#define MPG_CHAIN_FAILED 2    /* singular block, failed reprojection or line search */
+#define MPG_CHAIN_LIMIT 3     /* max_iter Newton steps without convergence */
+#define MPG_CHAIN_SEEDED 255  /* valid seed, not walked yet */
+
+#define MPG_WALK_PLAIN 0      /* one launch per chain length k, no graph */
+#define MPG_WALK_BATCHED 1    /* all k in one persistent launch, k-sorted work queue */
+
+/* Solver constants.  The paper fixes none of them (it defers the walk to the
+ * manifold-walk literature, Sec. 3); the values are the caller's. */
+typedef struct mpg_params {
+  float tol;            /* converged when max_i |C_i|_inf < tol                  */
+  int32_t max_iter;     /* Newton steps per walk                                  */
+  int32_t max_halvings; /* step halvings per Newton step                          */
+  float ray_eps;        /* ray origin offset and shadow-segment shrink (scene units) */
+  float sing_eps;       /* |det B'| <= sing_eps * max|B'|^2 => singular block      */
+  float dedup_eps;      /* two chains are one solution when every vertex is closer */
+  int32_t max_trials;   /* Bernoulli trial cap                                    */
+  int32_t weight_shift; /* histogram weight quantisation q = floor(w * 2^S)        */
+  float alpha;          /* defensive mixture weight of p_0 (Sec. 5.5, alpha = 0.5) */
+  int32_t walk_mode;    /* MPG_WALK_PLAIN or MPG_WALK_BATCHED                     */
+  int32_t block_threads;/* threads per block of the walk kernels (0 = default)    */
+  int32_t tau_random;   /* nonzero: draw tau_i ~ Bernoulli(0.5) per trial          */
+  int32_t k_uniform;    /* 1..8: every chain has this length; 0: lengths vary      */
+} mpg_params;
+
+/* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
+typedef struct mpg_chains {
+  int32_t B, Q, spq;
+  const float* xD;      /* [3][Q] receiver points (separator x_D)                  */
+  const float* nD;      /* [3][Q] receiver normals                                 */
+  const uint32_t* cell; /* [Q] guide cell of each receiver point                   */
+  const float* xL;      /* [3][B] light-side separator x_L of each chain           */
+  const uint8_t* k;     /* [B] chain length n (1..8)                               */
+  const float* pn;      /* [B] P(n) of the chain's length (NULL => 1)              */
+  uint8_t* tau;         /* [B] vertex types (input; overwritten when tau_random)   */
+  float* x;             /* [8][3][B] vertex positions                              */
+  int32_t* surf;        /* [8][B] surface index of each vertex                     */
+  int32_t* prim;        /* [8][B] triangle index (meshes) or -1                    */
+  float* bary;          /* [8][2][B] barycentrics on triangles                     */
+  float* pdf;           /* [B] solid-angle density of the seed direction           */
+  uint8_t* status;      /* [B] MPG_CHAIN_* (valid seed => INVALID until walked)    */
+  uint8_t* iters;       /* [B] Newton steps taken                                  */
+} mpg_chains;
+
+/* Guide: per cell a (theta, phi) histogram over world directions (theta from
+ * +z uniform over [0, pi], phi uniform over [0, 2 pi)); caller-owned. */
+typedef struct mpg_guide {
+  int32_t n_cells, n_theta, n_phi;
+  uint64_t* counts;        /* [n_cells][n_theta*n_phi] quantised weight sums      */
+  uint64_t* cdf;           /* [n_cells][n_theta*n_phi] inclusive prefix sums      */
+  const float* cos_theta;  /* [n_theta+1] FP32 edges cos(j pi/n_theta)            */
+  const float* phi_cos;    /* [n_phi+1] FP32 cos(2 pi j/n_phi)                    */
+  const float* phi_sin;    /* [n_phi+1] FP32 sin(2 pi j/n_phi)                    */
+} mpg_guide;
+
+typedef struct mpg_ctx mpg_ctx;
+typedef struct mpg_scene mpg_scene;
+
+/* Work counters accumulated by the kernels since the last reset (device-side,
+ * read back by mpg_ctx_stats): they give the algorithmic flop count of a run. */
+typedef struct mpg_stats {
+  uint64_t newton_steps;     /* Newton steps (Thomas solves) over all walks       */
+  uint64_t full_evals;       /* chain evaluations with Jacobian blocks (per vertex) */
+  uint64_t c_evals;          /* constraint-only evaluations (per vertex)          */
+  uint64_t ray_casts;        /* nearest-hit ray queries                           */
+  uint64_t sphere_tests;     /* ray/sphere and ray/cap tests                      */
+  uint64_t plane_tests;      /* ray/rectangle tests                               */
+  uint64_t node_tests;       /* BVH child-box tests                               */
+  uint64_t tri_tests;        /* ray/triangle tests                                */
+  uint64_t walks;            /* walks started                                     */
+  uint64_t converged;        /* walks converged                                   */
+  uint64_t ggt_evals;        /* generalized-geometry-term solves (per vertex)     */
+  uint64_t trials;           /* Bernoulli trials drawn                            */
+} mpg_stats;
+
+const char* mpg_last_error(void);
+int32_t mpg_version(void);
+
+/* Context on one CUDA device (made current by every call that takes it). */
+mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out);
+void mpg_ctx_destroy(mpg_ctx* ctx);
+/* Waits for `stream` and returns the first device-side error recorded since the
+ * last sync (MPG_ERR_LIMIT for a traversal overflow), else MPG_OK. */
+mpg_status mpg_ctx_sync(mpg_ctx* ctx, cudaStream_t stream);
+mpg_status mpg_ctx_stats(mpg_ctx* ctx, mpg_stats* out, int32_t reset, cudaStream_t stream);
+/* Work counters on (default) or off; off selects kernels without the tallies. */
+mpg_status mpg_ctx_set_stats(mpg_ctx* ctx, int32_t on);
+
+/* Scene from the host tables (format: one row of 24 doubles per surface --
+ * type, material, eta_front, eta_back, centre[3], radius, axis/normal[3],
+ * cap_cos, e_x[3], e_y[3], heightfield index; heightfield descriptors of 6
+ * doubles nx, ny, x0, y0, x1, y1 with heights concatenated row-major; seed
+ * targets of 16 doubles; a light of 16 doubles).  Builds the triangle meshes,
+ * interpolation normals and BVHs on the host and uploads them (library-owned
+ * device memory, freed by mpg_scene_destroy).  Synchronous. */
+mpg_status mpg_scene_create(mpg_ctx* ctx, const double* surfaces, int32_t n_surf,
+                            const double* hf_desc, const double* hf_heights, int32_t n_hf,
+                            const double* targets, int32_t n_targets, const double* light,
+                            mpg_scene** out);
+void mpg_scene_destroy(mpg_scene* scene);
+/* Number of BVH nodes and triangles of heightfield h (for reports). */
+mpg_status mpg_scene_info(const mpg_scene* scene, int32_t h, int32_t* n_nodes, int32_t* n_tris);
+
+/* S1 -- seed chains (Eq. deduction; Sec. 5.4 initialisation p_0; Sec. 5.5
+ * guided sampling with the one-sample defensive mixture alpha p_0 + (1-alpha) p_e).
+ * For each chain: draws from Philox4x32-10 keyed by rng_seed with counter
+ * (b + rng_offset, trial 0, block), picks p_0 (a seed target, uniform visible cap
+ * or rectangle) or the cell's histogram (guide may be NULL => p_0 only), deduces
+ * x_1 = r(x_D, w_D) and the next vertices by scattering with tau, and writes
+ * x/surf/prim/bary/pdf/tau and status (MPG_CHAIN_INVALID on failure, else
+ * MPG_CHAIN_SEEDED). */
+mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
+                            mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
+                            const mpg_params* params, cudaStream_t stream);
+
+/* S2-S6 -- manifold walk (Sec. 3, "Manifold walks"): Newton's method on the
+ * generalized half-vector constraints C_i = (h.s_i, h.t_i), h ~ eta_i w_i +
+ * eta_o w_o, with the 2k x 2k block-tridiagonal Jacobian solved by a 2x2-block
+ * Thomas sweep, step halving and reprojection by ray casting from x_D through the
+ * moved vertices.  Walks every chain whose status is MPG_CHAIN_SEEDED; writes x,
+ * surf, prim, bary, status and iters in place. */
+mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* chains,
+                             const mpg_params* params, cudaStream_t stream);
+
+/* S7-S9 -- contribution of each converged chain (Eq. ThroughputEval):
+ * admissibility (unoccluded segments, vertex types consistent with the sides,
+ * positive end cosines), the generalized geometry term G by the implicit
+ * function theorem (FP64 determinant for k >= 6), kappa (Fresnel / mirror and
+ * radiance scaling), T = kappa G L_o; then Bernoulli trials (Sec. 5.7): fresh
+ * seeds with the same n are walked until one reaches the same solution (FP64
+ * distance test), N = trial index, <1/P> = N / P(n) (capped at max_trials,
+ * `capped` set).  Writes contrib[b] = A_L T <1/P> (A_L = light area, 1 for a
+ * point light) and the irradiance estimate E[q] = sum_b contrib / spq
+ * (Eq. ThroughputMC).  Outputs may be NULL except E; all are [B] unless noted. */
+mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
+                                  const mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
+                                  const mpg_params* params, float* G, float* kappa, float* T,
+                                  uint32_t* trials, uint8_t* capped, float* contrib,
+                                  float* E /* [Q] */, cudaStream_t stream);
+
+/* S10 -- guide update with sample weights w = T <1/P> (Eq. eq_weight): each
+ * record r < n (n = *R_dev when R_dev is not NULL, else R) adds
+ * q = min(floor(w[r] 2^S), 2^32-1) (0 unless w > 0) to counts[cell[r]][bin(omega)]
+ * with 64-bit integer atomics (bit-exact, order independent), then rebuilds the
+ * per-cell prefix sums used by the sampler.  omega is [3][R] SoA FP32 (R is the
+ * row stride and the upper bound of n); R_dev is a device int32. */
+mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell,
+                            const float* omega, const float* w, int32_t R, const int32_t* R_dev,
+                            int32_t weight_shift, cudaStream_t stream);
+/* Records of the admissible chains of a batch for mpg_guide_update: compacts
+ * (cell, w_D = unit(x_1 - x_D), w = contrib/A_L) of chains with contrib > 0 into
+ * cell_out[B], omega_out[3][B] and w_out[B] (capacity B, record order
+ * unspecified) and writes the record count to *R_dev (device int32). */
+mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* scene, const mpg_chains* chains,
+                             const float* contrib, uint32_t* cell_out, float* omega_out,
+                             float* w_out, int32_t* R_dev, cudaStream_t stream);
+
+/* S11 -- adjoint: accumulates dL/dtheta += sum_chains dL/dE[q] * d(contrib_b/spq)/dtheta
+ * for the heights theta of heightfield 0, with the implicit function theorem on
+ * the converged constraint (transposed block-tridiagonal solve; the Newton
+ * iterations are not unrolled) and <1/P> held constant.  dL_dtheta is
+ * [ny*nx] FP32, accumulated. */
+mpg_status mpg_walk_adjoint(mpg_ctx* ctx, const mpg_scene* scene, const mpg_chains* chains,
+                            const float* contrib, const float* dL_dE, float* dL_dtheta,
+                            cudaStream_t stream);
+
+/* K3 -- standalone BVH/analytic ray batch: nearest hit of rays (o[3][n], d[3][n])
+ * in (tmin, tmax): t (or -1), surface, primitive and barycentrics [2][n]. */
+mpg_status mpg_trace_rays(mpg_ctx* ctx, const mpg_scene* scene, const float* o, const float* d,
+                          int32_t n, float tmin, float tmax, float* t, int32_t* surf,
+                          int32_t* prim, float* bary, cudaStream_t stream);
+
+/* FP32 peak probe: a dependent-FFMA loop over the whole GPU; writes the
+ * achieved FP32 FLOP/s (host double) after synchronising `stream`. */
+mpg_status mpg_fp32_peak(mpg_ctx* ctx, double* flops, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPG_H */

@@ -1254,7 +1254,7 @@ int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const d
                               load3(nD + 3 * (size_t)q), cell ? cell[q] : 0u, load3(xL + 3 * (size_t)b),
                               k[b], tau[b], tau_random != 0, rng_seed, (uint64_t)b + rng_offset, trial, P);
     valid[b] = sd.valid ? 1 : 0;
-    pdf[b] = sd.pdf;
+    pdf[b] = sd.valid ? sd.pdf : 0.0;
     tau_out[b] = sd.tau;
     if (!sd.valid) { sd.ch.k = 0; }
     store_chain(sd.ch, b, x, surf, prim, bary);

@@ -1,0 +1,673 @@
+// C ABI of libmpg.so: context, scene construction (meshes, normals and a
+// binned-SAH BVH built on the host), argument checks and launch planning.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mpg_aux.cuh"
+
+using namespace mpg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mpg_status fail(mpg_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? MPG_ERR_OOM : MPG_ERR_CUDA, "%s: %s", \
+                  #expr, cudaGetErrorString(e_));                                         \
+  } while (0)
+
+#define LAUNCH_CHECK(what)                                                                \
+  do {                                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                                  \
+    if (e_ != cudaSuccess) return fail(MPG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+struct mpg_ctx {
+  int device = 0, sms = 1;
+  int* d_err = nullptr;
+  unsigned long long* d_stats = nullptr;
+  int* d_order = nullptr;
+  int order_cap = 0;
+  int* d_count = nullptr;
+  int* d_base = nullptr;
+  int* d_cursor = nullptr;
+  float* d_scratch = nullptr;
+  bool stats_on = true;
+  cudaStream_t aux[MAXK] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[MAXK] = {};
+};
+
+struct mpg_scene {
+  DScene S;
+  std::vector<void*> allocs;
+  std::vector<int> n_nodes, n_tris;
+  int device = 0;
+};
+
+// ---------------------------------------------------------------------------
+// BVH over the heightfield triangles (two children per node, binned SAH)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Box {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  void grow(const float* p) {
+    for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], p[a]); hi[a] = std::max(hi[a], p[a]); }
+  }
+  void grow(const Box& b) {
+    for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], b.lo[a]); hi[a] = std::max(hi[a], b.hi[a]); }
+  }
+  float area() const {
+    if (lo[0] > hi[0]) return 0.0f;
+    float d0 = hi[0] - lo[0], d1 = hi[1] - lo[1], d2 = hi[2] - lo[2];
+    return 2.0f * (d0 * d1 + d1 * d2 + d2 * d0);
+  }
+};
+
+struct BuildTri {
+  Box box;
+  float c[3];
+  int id;
+};
+
+struct ChildRef {
+  Box box;
+  int idx = 0, count = 0;  // count > 0: leaf over tri slots [idx, idx+count)
+};
+
+struct BVHBuilder {
+  std::vector<BuildTri> tris;
+  std::vector<float4> nodes;     // 4 float4 per node
+  std::vector<int> leaf_order;   // triangle ids in leaf order
+  int max_depth = 0;
+  static const int LEAF = 4;
+
+  ChildRef make_leaf(int first, int count, const Box& box) {
+    ChildRef r;
+    r.box = box;
+    r.idx = (int)leaf_order.size();
+    r.count = count;
+    for (int i = first; i < first + count; ++i) leaf_order.push_back(tris[i].id);
+    return r;
+  }
+
+  void write_node(int ni, const ChildRef& L, const ChildRef& R) {
+    float4* n = &nodes[4 * (size_t)ni];
+    n[0] = make_float4(L.box.lo[0], L.box.hi[0], L.box.lo[1], L.box.hi[1]);
+    n[1] = make_float4(R.box.lo[0], R.box.hi[0], R.box.lo[1], R.box.hi[1]);
+    n[2] = make_float4(L.box.lo[2], L.box.hi[2], R.box.lo[2], R.box.hi[2]);
+    int4 ch = make_int4(L.idx, R.idx, L.count, R.count);
+    memcpy(&n[3], &ch, sizeof(int4));
+  }
+
+  ChildRef build(int first, int count, int depth) {
+    max_depth = std::max(max_depth, depth);
+    Box box, cbox;
+    for (int i = first; i < first + count; ++i) { box.grow(tris[i].box); cbox.grow(tris[i].c); }
+    if (count <= LEAF) return make_leaf(first, count, box);
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+      if (cbox.hi[a] - cbox.lo[a] > cbox.hi[axis] - cbox.lo[axis]) axis = a;
+    float extent = cbox.hi[axis] - cbox.lo[axis];
+    int mid = first + count / 2;
+    if (extent > 0.0f && depth < 48) {
+      const int NB = 16;
+      Box bb[NB];
+      int bc[NB] = {0};
+      auto bin_of = [&](const BuildTri& t) {
+        int b = (int)((t.c[axis] - cbox.lo[axis]) / extent * NB);
+        return std::min(std::max(b, 0), NB - 1);
+      };
+      for (int i = first; i < first + count; ++i) { int b = bin_of(tris[i]); bb[b].grow(tris[i].box); bc[b]++; }
+      float best = INFINITY;
+      int best_split = -1;
+      for (int s = 1; s < NB; ++s) {
+        Box l, r;
+        int nl = 0, nr = 0;
+        for (int b = 0; b < s; ++b) { if (bc[b]) { l.grow(bb[b]); nl += bc[b]; } }
+        for (int b = s; b < NB; ++b) { if (bc[b]) { r.grow(bb[b]); nr += bc[b]; } }
+        if (!nl || !nr) continue;
+        float cost = l.area() * nl + r.area() * nr;
+        if (cost < best) { best = cost; best_split = s; }
+      }
+      if (best_split > 0) {
+        auto it = std::partition(tris.begin() + first, tris.begin() + first + count,
+                                 [&](const BuildTri& t) { return bin_of(t) < best_split; });
+        mid = (int)(it - tris.begin());
+      }
+      if (mid == first || mid == first + count) mid = first + count / 2;
+    }
+    std::nth_element(tris.begin() + first, tris.begin() + mid, tris.begin() + first + count,
+                     [&](const BuildTri& a, const BuildTri& b) {
+                       return a.c[axis] < b.c[axis] || (a.c[axis] == b.c[axis] && a.id < b.id);
+                     });
+    int ni = (int)(nodes.size() / 4);
+    nodes.resize(nodes.size() + 4);
+    ChildRef L = build(first, mid - first, depth + 1);
+    ChildRef R = build(mid, first + count - mid, depth + 1);
+    write_node(ni, L, R);
+    ChildRef r;
+    r.box = box;
+    r.idx = ni;
+    r.count = 0;
+    return r;
+  }
+};
+
+// Heightfield vertex positions and interpolation normals.  The normal of
+// grid vertex (i, j) is normalize(-dh/dx, -dh/dy, 1) with central
+// differences inside the grid and one-sided differences on its border.
+void heightfield_mesh(int nx, int ny, double x0, double y0, double x1, double y1, const double* h,
+                      std::vector<float4>& P, std::vector<float4>& N) {
+  double dx = (x1 - x0) / (nx - 1), dy = (y1 - y0) / (ny - 1);
+  P.resize((size_t)nx * ny);
+  N.resize((size_t)nx * ny);
+  auto H = [&](int i, int j) { return h[(size_t)j * nx + i]; };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double gx = i == 0 ? (H(1, j) - H(0, j)) / dx
+                : i == nx - 1 ? (H(nx - 1, j) - H(nx - 2, j)) / dx
+                              : (H(i + 1, j) - H(i - 1, j)) / (2.0 * dx);
+      double gy = j == 0 ? (H(i, 1) - H(i, 0)) / dy
+                : j == ny - 1 ? (H(i, ny - 1) - H(i, ny - 2)) / dy
+                              : (H(i, j + 1) - H(i, j - 1)) / (2.0 * dy);
+      double l = std::sqrt(gx * gx + gy * gy + 1.0);
+      P[(size_t)j * nx + i] = make_float4((float)(x0 + i * dx), (float)(y0 + j * dy), (float)H(i, j), 0.0f);
+      N[(size_t)j * nx + i] = make_float4((float)(-gx / l), (float)(-gy / l), (float)(1.0 / l), 0.0f);
+    }
+}
+
+template <class T>
+mpg_status upload(mpg_scene* sc, const std::vector<T>& v, const T** out) {
+  void* p = nullptr;
+  size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+  CUDA_TRY(cudaMalloc(&p, bytes));
+  sc->allocs.push_back(p);
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = (const T*)p;
+  return MPG_OK;
+}
+
+float3 ld3(const double* p) { return make_float3((float)p[0], (float)p[1], (float)p[2]); }
+double dlen(const double* p) { return std::sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]); }
+
+mpg_status check_chains(const mpg_chains* c, bool need_walk_state) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "chains is NULL");
+  if (c->B <= 0 || c->Q <= 0 || c->spq <= 0 || (long long)c->Q * c->spq != c->B)
+    return fail(MPG_ERR_INVALID_ARG, "B (%d) must equal Q (%d) * spq (%d) > 0", c->B, c->Q, c->spq);
+  const void* req[] = {c->xD, c->nD, c->xL, c->k, c->tau, c->x, c->surf, c->prim, c->bary, c->status, c->iters};
+  const char* names[] = {"xD", "nD", "xL", "k", "tau", "x", "surf", "prim", "bary", "status", "iters"};
+  for (int i = 0; i < 11; ++i)
+    if (!aligned16(req[i])) return fail(MPG_ERR_INVALID_ARG, "chains.%s is NULL or not 16-byte aligned", names[i]);
+  if (need_walk_state && !aligned16(c->pdf)) return fail(MPG_ERR_INVALID_ARG, "chains.pdf is NULL or unaligned");
+  return MPG_OK;
+}
+
+mpg_status check_params(const mpg_params* p) {
+  if (!p) return fail(MPG_ERR_INVALID_ARG, "params is NULL");
+  if (!(p->tol > 0.0f) || p->max_iter < 0 || p->max_iter > 255 || p->max_halvings < 0 || p->max_halvings > 60 ||
+      !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 ||
+      !(p->alpha >= 0.0f && p->alpha <= 1.0f) || p->weight_shift < 0 || p->weight_shift > 60 ||
+      (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
+      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0)
+    return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
+  return MPG_OK;
+}
+
+DChains to_dev(const mpg_chains* c) {
+  DChains d;
+  d.B = c->B; d.Q = c->Q; d.spq = c->spq;
+  d.xD = c->xD; d.nD = c->nD; d.cell = c->cell; d.xL = c->xL; d.k = c->k; d.pn = c->pn; d.tau = c->tau;
+  d.x = c->x; d.surf = c->surf; d.prim = c->prim; d.bary = c->bary; d.pdf = c->pdf;
+  d.status = c->status; d.iters = c->iters;
+  return d;
+}
+
+mpg_status check_guide(const mpg_guide* g, DGuide& out) {
+  if (!g) return fail(MPG_ERR_INVALID_ARG, "guide is NULL");
+  if (g->n_cells <= 0 || g->n_theta <= 0 || g->n_phi < 2 || (g->n_phi & 1) || !aligned16(g->counts) ||
+      !aligned16(g->cdf) || !g->cos_theta || !g->phi_cos || !g->phi_sin)
+    return fail(MPG_ERR_INVALID_ARG, "invalid guide (cells %d, theta %d, phi %d)", g->n_cells, g->n_theta, g->n_phi);
+  out.n_cells = g->n_cells; out.n_theta = g->n_theta; out.n_phi = g->n_phi; out.bins = g->n_theta * g->n_phi;
+  out.counts = g->counts; out.cdf = g->cdf; out.cos_theta = g->cos_theta; out.phi_cos = g->phi_cos;
+  out.phi_sin = g->phi_sin;
+  return MPG_OK;
+}
+
+// Which per-K launches to make, and over which work list.
+struct Plan {
+  int K[MAXK];
+  int nK = 0;
+  DWork w{nullptr, nullptr, nullptr};
+  bool concurrent = false;
+};
+
+mpg_status make_plan(mpg_ctx* ctx, const mpg_chains* c, const mpg_params* p, int status_filter, cudaStream_t st,
+                     Plan& plan) {
+  if (p->k_uniform >= 1) {
+    plan.K[0] = p->k_uniform;
+    plan.nK = 1;
+    return MPG_OK;
+  }
+  for (int k = 1; k <= MAXK; ++k) plan.K[plan.nK++] = k;
+  if (p->walk_mode == MPG_WALK_PLAIN) return MPG_OK;
+  if (ctx->order_cap < c->B) {
+    if (ctx->d_order) cudaFree(ctx->d_order);
+    ctx->d_order = nullptr;
+    CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * (size_t)c->B));
+    ctx->order_cap = c->B;
+  }
+  launch_bucket(c->k, c->status, status_filter, c->B, ctx->d_count, ctx->d_base, ctx->d_cursor, ctx->d_order,
+                ctx->sms, st);
+  LAUNCH_CHECK("bucket");
+  plan.w = DWork{ctx->d_order, ctx->d_base, ctx->d_count};
+  plan.concurrent = true;
+  return MPG_OK;
+}
+
+// Runs fn(K, stream) for each planned K, on forked streams when concurrent.
+template <class F>
+mpg_status run_plan(mpg_ctx* ctx, const Plan& plan, cudaStream_t st, F fn) {
+  if (!plan.concurrent) {
+    for (int i = 0; i < plan.nK; ++i) fn(plan.K[i], st);
+    LAUNCH_CHECK("kernel launch");
+    return MPG_OK;
+  }
+  CUDA_TRY(cudaEventRecord(ctx->ev_fork, st));
+  for (int i = 0; i < plan.nK; ++i) {
+    CUDA_TRY(cudaStreamWaitEvent(ctx->aux[i], ctx->ev_fork, 0));
+    fn(plan.K[i], ctx->aux[i]);
+    CUDA_TRY(cudaEventRecord(ctx->ev_join[i], ctx->aux[i]));
+  }
+  for (int i = 0; i < plan.nK; ++i) CUDA_TRY(cudaStreamWaitEvent(st, ctx->ev_join[i], 0));
+  LAUNCH_CHECK("kernel launch");
+  return MPG_OK;
+}
+
+int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threads : 128; }
+
+int grid_of(mpg_ctx* ctx, int which, int K, int block, int B, bool persistent) {
+  int per_sm = blocks_per_sm(which, K, ctx->stats_on, block);
+  int full = ctx->sms * per_sm;
+  int need = (B + block - 1) / block;
+  return persistent ? std::max(1, std::min(full, need)) : std::max(1, need);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpg_last_error(void) { return g_last_error.c_str(); }
+int32_t mpg_version(void) { return 1; }
+
+mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
+  if (!out) return fail(MPG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(MPG_ERR_INVALID_ARG, "device %d out of range (%d devices)", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  mpg_ctx* c = new mpg_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  bool ok = cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->d_stats, sizeof(unsigned long long) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_count, sizeof(int) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_base, sizeof(int) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_cursor, sizeof(int) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_scratch, sizeof(float) * 16) == cudaSuccess &&
+            cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
+            cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < MAXK; ++i)
+    ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    mpg_ctx_destroy(c);
+    return fail(MPG_ERR_OOM, "context allocation failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  *out = c;
+  return MPG_OK;
+}
+
+void mpg_ctx_destroy(mpg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaFree(c->d_err); cudaFree(c->d_stats); cudaFree(c->d_order); cudaFree(c->d_count);
+  cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
+  for (int i = 0; i < MAXK; ++i) {
+    if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  delete c;
+}
+
+mpg_status mpg_ctx_sync(mpg_ctx* c, cudaStream_t st) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+    if (err & ERR_BVH_STACK) return fail(MPG_ERR_LIMIT, "BVH traversal stack overflow (device flag %d)", err);
+    return fail(MPG_ERR_INVALID_ARG, "device-side argument error (flag %d): guide cell out of range", err);
+  }
+  return MPG_OK;
+}
+
+mpg_status mpg_ctx_stats(mpg_ctx* c, mpg_stats* out, int32_t reset, cudaStream_t st) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (out) {
+    unsigned long long v[16];
+    CUDA_TRY(cudaMemcpyAsync(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    static_assert(sizeof(mpg_stats) == 12 * sizeof(uint64_t), "stats layout");
+    memcpy(out, v, sizeof(mpg_stats));
+  }
+  if (reset) CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * 16, st));
+  return MPG_OK;
+}
+
+mpg_status mpg_ctx_set_stats(mpg_ctx* c, int32_t on) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  c->stats_on = on != 0;
+  return MPG_OK;
+}
+
+mpg_status mpg_scene_create(mpg_ctx* ctx, const double* surfaces, int32_t n_surf, const double* hf_desc,
+                            const double* hf_heights, int32_t n_hf, const double* targets, int32_t n_targets,
+                            const double* light, mpg_scene** out) {
+  if (!ctx || !out || !light || (n_surf > 0 && !surfaces) || (n_hf > 0 && (!hf_desc || !hf_heights)) ||
+      (n_targets > 0 && !targets))
+    return fail(MPG_ERR_INVALID_ARG, "NULL scene table");
+  if (n_surf < 1 || n_surf > MAX_SURF || n_hf < 0 || n_hf > MAX_HF || n_targets < 0 || n_targets > MAX_TG)
+    return fail(MPG_ERR_INVALID_ARG, "scene sizes out of range (surfaces %d <= %d, heightfields %d <= %d, targets %d <= %d)",
+                n_surf, MAX_SURF, n_hf, MAX_HF, n_targets, MAX_TG);
+  *out = nullptr;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  mpg_scene* sc = new mpg_scene();
+  sc->device = ctx->device;
+  DScene& S = sc->S;
+  memset(&S, 0, sizeof(S));
+  S.n_surf = n_surf;
+  S.n_hf = n_hf;
+  S.n_tg = n_targets;
+  size_t hoff = 0;
+  for (int h = 0; h < n_hf; ++h) {
+    const double* d = hf_desc + 6 * h;
+    int nx = (int)d[0], ny = (int)d[1];
+    if (nx < 2 || ny < 2 || (long long)nx * ny > (1 << 26)) {
+      mpg_scene_destroy(sc);
+      return fail(MPG_ERR_INVALID_ARG, "heightfield %d: bad grid %d x %d", h, nx, ny);
+    }
+    std::vector<float4> P, N;
+    heightfield_mesh(nx, ny, d[2], d[3], d[4], d[5], hf_heights + hoff, P, N);
+    hoff += (size_t)nx * ny;
+    BVHBuilder bb;
+    int nt = 2 * (nx - 1) * (ny - 1);
+    bb.tris.resize(nt);
+    for (int t = 0; t < nt; ++t) {
+      int quad = t / 2, tt = t % 2, i = quad % (nx - 1), j = quad / (nx - 1);
+      int v00 = j * nx + i, v[3] = {v00, tt == 0 ? v00 + 1 : v00 + nx + 1, tt == 0 ? v00 + nx + 1 : v00 + nx};
+      BuildTri& bt = bb.tris[t];
+      bt.id = t;
+      for (int a = 0; a < 3; ++a) {
+        float p[3] = {P[v[a]].x, P[v[a]].y, P[v[a]].z};
+        bt.box.grow(p);
+      }
+      for (int a = 0; a < 3; ++a) bt.c[a] = 0.5f * (bt.box.lo[a] + bt.box.hi[a]);
+    }
+    // build() allocates the first internal node first, so the root lands in slot 0
+    ChildRef root = bb.build(0, nt, 0);
+    if (root.count > 0) {  // whole mesh in one leaf: a root node whose two children are that leaf
+      bb.nodes.resize(4);
+      bb.write_node(0, root, root);
+    }
+    std::vector<float4> tris((size_t)nt * 3);
+    for (int s = 0; s < nt; ++s) {
+      int t = bb.leaf_order[s];
+      int quad = t / 2, tt = t % 2, i = quad % (nx - 1), j = quad / (nx - 1);
+      int v00 = j * nx + i, v1 = tt == 0 ? v00 + 1 : v00 + nx + 1, v2 = tt == 0 ? v00 + nx + 1 : v00 + nx;
+      float4 a = P[v00], b = P[v1], c = P[v2];
+      float4 v0 = a;
+      memcpy(&v0.w, &t, sizeof(float));  // primitive id stored as int bits
+      tris[3 * (size_t)s + 0] = v0;
+      tris[3 * (size_t)s + 1] = make_float4(b.x - a.x, b.y - a.y, b.z - a.z, 0.f);
+      tris[3 * (size_t)s + 2] = make_float4(c.x - a.x, c.y - a.y, c.z - a.z, 0.f);
+    }
+    DHF& H = S.hf[h];
+    H.nx = nx; H.ny = ny; H.surf = -1;
+    H.x0 = (float)d[2]; H.y0 = (float)d[3];
+    H.dx = (float)((d[4] - d[2]) / (nx - 1)); H.dy = (float)((d[5] - d[3]) / (ny - 1));
+    H.n_nodes = (int)(bb.nodes.size() / 4);
+    mpg_status st;
+    if ((st = upload(sc, P, &H.P)) || (st = upload(sc, N, &H.N)) || (st = upload(sc, bb.nodes, &H.nodes)) ||
+        (st = upload(sc, tris, &H.tris))) {
+      mpg_scene_destroy(sc);
+      return st;
+    }
+    sc->n_nodes.push_back(H.n_nodes);
+    sc->n_tris.push_back(nt);
+  }
+  for (int s = 0; s < n_surf; ++s) {
+    const double* r = surfaces + 24 * s;
+    DSurf& f = S.s[s];
+    f.type = (int)r[0]; f.mat = (int)r[1]; f.etaF = (float)r[2]; f.etaB = (float)r[3];
+    f.c = ld3(r + 4); f.r = (float)r[7]; f.cap_cos = (float)r[11]; f.hf = (int)r[18];
+    double ax = dlen(r + 8);
+    f.axis = ax > 0 ? make_float3((float)(r[8] / ax), (float)(r[9] / ax), (float)(r[10] / ax)) : make_float3(0, 0, 1);
+    if (f.type == SURF_CAP) f.axis = ld3(r + 8);
+    f.ex = ld3(r + 12); f.ey = ld3(r + 15);
+    f.ex2 = (float)(r[12] * r[12] + r[13] * r[13] + r[14] * r[14]);
+    f.ey2 = (float)(r[15] * r[15] + r[16] * r[16] + r[17] * r[17]);
+    bool bad = f.type < SURF_SPHERE || f.type > SURF_HEIGHTFIELD || (f.mat != MAT_MIRROR && f.mat != MAT_DIELECTRIC) ||
+               ((f.type == SURF_SPHERE || f.type == SURF_CAP) && !(f.r > 0.0f)) ||
+               (f.type == SURF_HEIGHTFIELD && (f.hf < 0 || f.hf >= n_hf)) ||
+               (f.mat == MAT_DIELECTRIC && !(f.etaF > 0.0f && f.etaB > 0.0f));
+    if (bad) {
+      mpg_scene_destroy(sc);
+      return fail(MPG_ERR_INVALID_ARG, "surface %d is invalid", s);
+    }
+    if (f.type == SURF_HEIGHTFIELD) S.hf[f.hf].surf = s;
+  }
+  for (int t = 0; t < n_targets; ++t) {
+    const double* r = targets + 16 * t;
+    DTarget& g = S.tg[t];
+    g.type = (int)r[0]; g.c = ld3(r + 1); g.r = (float)r[4]; g.ex = ld3(r + 5); g.ey = ld3(r + 8);
+    double nl = dlen(r + 11);
+    g.n = nl > 0 ? make_float3((float)(r[11] / nl), (float)(r[12] / nl), (float)(r[13] / nl)) : make_float3(0, 0, 1);
+    g.area = (float)(4.0 * dlen(r + 5) * dlen(r + 8));
+  }
+  DLight& L = S.L;
+  L.type = (int)light[0];
+  L.p = ld3(light + 1);
+  double nl = dlen(light + 4);
+  L.n = nl > 0 ? make_float3((float)(light[4] / nl), (float)(light[5] / nl), (float)(light[6] / nl)) : make_float3(0, 0, -1);
+  double ex = dlen(light + 7), ey = dlen(light + 10);
+  L.exu = ex > 0 ? make_float3((float)(light[7] / ex), (float)(light[8] / ex), (float)(light[9] / ex)) : make_float3(1, 0, 0);
+  L.eyu = ey > 0 ? make_float3((float)(light[10] / ey), (float)(light[11] / ey), (float)(light[12] / ey)) : make_float3(0, 1, 0);
+  L.power = (float)light[13];
+  L.area = L.type == LIGHT_RECT ? (float)(4.0 * ex * ey) : 1.0f;
+  if (L.type != LIGHT_POINT && L.type != LIGHT_RECT) {
+    mpg_scene_destroy(sc);
+    return fail(MPG_ERR_INVALID_ARG, "light type %d is invalid", L.type);
+  }
+  *out = sc;
+  return MPG_OK;
+}
+
+void mpg_scene_destroy(mpg_scene* sc) {
+  if (!sc) return;
+  cudaSetDevice(sc->device);
+  for (void* p : sc->allocs) cudaFree(p);
+  delete sc;
+}
+
+mpg_status mpg_scene_info(const mpg_scene* sc, int32_t h, int32_t* n_nodes, int32_t* n_tris) {
+  if (!sc || h < 0 || h >= (int)sc->n_nodes.size()) return fail(MPG_ERR_INVALID_ARG, "no heightfield %d", h);
+  if (n_nodes) *n_nodes = sc->n_nodes[h];
+  if (n_tris) *n_tris = sc->n_tris[h];
+  return MPG_OK;
+}
+
+mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guide, mpg_chains* chains,
+                            uint64_t rng_seed, uint64_t rng_offset, const mpg_params* P, cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
+  mpg_status s;
+  if ((s = check_chains(chains, true)) || (s = check_params(P))) return s;
+  DGuide g;
+  if (guide && (s = check_guide(guide, g))) return s;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Plan plan;
+  mpg_params Pn = *P;
+  if ((s = make_plan(ctx, chains, &Pn, -1, st, plan))) return s;
+  DChains c = to_dev(chains);
+  uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
+  DCtx dc{ctx->d_err, ctx->d_stats};
+  int block = block_of(P);
+  return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
+    launch_seed(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, dc,
+                grid_of(ctx, 0, K, block, c.B, true), block, s2);
+  });
+}
+
+mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chains, const mpg_params* P,
+                             cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
+  mpg_status s;
+  if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Plan plan;
+  if ((s = make_plan(ctx, chains, P, ST_SEEDED, st, plan))) return s;
+  DChains c = to_dev(chains);
+  DCtx dc{ctx->d_err, ctx->d_stats};
+  int block = block_of(P);
+  return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
+    launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, 1, K, block, c.B, true), block, s2);
+  });
+}
+
+mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guide, const mpg_chains* chains,
+                                  uint64_t rng_seed, uint64_t rng_offset, const mpg_params* P, float* G, float* kappa,
+                                  float* T, uint32_t* trials, uint8_t* capped, float* contrib, float* E,
+                                  cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
+  mpg_status s;
+  if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  if (!aligned16(T) || !aligned16(contrib) || !aligned16(E))
+    return fail(MPG_ERR_INVALID_ARG, "T, contrib and E must be non-NULL 16-byte aligned device arrays");
+  DGuide g;
+  if (guide && (s = check_guide(guide, g))) return s;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  Plan plan;
+  if ((s = make_plan(ctx, chains, P, ST_CONVERGED, st, plan))) return s;
+  DChains c = to_dev(chains);
+  DCtx dc{ctx->d_err, ctx->d_stats};
+  DOut o{G, kappa, T, trials, capped, contrib};
+  uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
+  int block = block_of(P);
+  if (plan.w.order) {
+    // zero the outputs of chains outside the converged buckets
+    CUDA_TRY(cudaMemsetAsync(T, 0, sizeof(float) * (size_t)c.B, st));
+    CUDA_TRY(cudaMemsetAsync(contrib, 0, sizeof(float) * (size_t)c.B, st));
+    if (G) CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * (size_t)c.B, st));
+    if (kappa) CUDA_TRY(cudaMemsetAsync(kappa, 0, sizeof(float) * (size_t)c.B, st));
+    if (trials) CUDA_TRY(cudaMemsetAsync(trials, 0, sizeof(uint32_t) * (size_t)c.B, st));
+    if (capped) CUDA_TRY(cudaMemsetAsync(capped, 0, (size_t)c.B, st));
+  }
+  s = run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
+    launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dc, grid_of(ctx, 2, K, block, c.B, true), block, s2);
+    launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dc,
+                     grid_of(ctx, 3, K, block, c.B, true), block, s2);
+  });
+  if (s) return s;
+  launch_irradiance(contrib, c.Q, c.spq, E, ctx->sms, st);
+  LAUNCH_CHECK("irradiance");
+  return MPG_OK;
+}
+
+mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell, const float* omega,
+                            const float* w, int32_t R, const int32_t* R_dev, int32_t shift, cudaStream_t st) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  DGuide g;
+  mpg_status s;
+  if ((s = check_guide(guide, g))) return s;
+  if (R < 0 || shift < 0 || shift > 60 || (R > 0 && (!aligned16(cell) || !aligned16(omega) || !aligned16(w))))
+    return fail(MPG_ERR_INVALID_ARG, "invalid records (R %d, shift %d)", R, shift);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  launch_guide_update(g, cell, omega, w, R, R_dev, shift, ctx->d_err, ctx->sms, st);
+  LAUNCH_CHECK("guide update");
+  return MPG_OK;
+}
+
+mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* contrib,
+                             uint32_t* cell_out, float* omega_out, float* w_out, int32_t* R_dev, cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (!aligned16(contrib) || !aligned16(cell_out) || !aligned16(omega_out) || !aligned16(w_out) || !R_dev)
+    return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  DChains c = to_dev(chains);
+  launch_guide_records(c, contrib, 1.0f / sc->S.L.area, cell_out, omega_out, w_out, R_dev, ctx->sms, st);
+  LAUNCH_CHECK("guide records");
+  return MPG_OK;
+}
+
+mpg_status mpg_walk_adjoint(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* contrib,
+                            const float* dL_dE, float* dL_dtheta, cudaStream_t st) {
+  (void)ctx; (void)sc; (void)chains; (void)contrib; (void)dL_dE; (void)dL_dtheta; (void)st;
+  return fail(MPG_ERR_UNSUPPORTED, "mpg_walk_adjoint is not built yet");
+}
+
+mpg_status mpg_trace_rays(mpg_ctx* ctx, const mpg_scene* sc, const float* o, const float* d, int32_t n, float tmin,
+                          float tmax, float* t, int32_t* surf, int32_t* prim, float* bary, cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  if (n < 0 || (n > 0 && (!aligned16(o) || !aligned16(d) || !aligned16(t) || !aligned16(surf) || !aligned16(prim) ||
+                          !aligned16(bary))))
+    return fail(MPG_ERR_INVALID_ARG, "invalid ray arrays");
+  if (n == 0) return MPG_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  launch_trace(sc->S, o, d, n, tmin, tmax, t, surf, prim, bary, ctx->d_err, ctx->d_stats, ctx->stats_on, ctx->sms, st);
+  LAUNCH_CHECK("trace");
+  return MPG_OK;
+}
+
+mpg_status mpg_fp32_peak(mpg_ctx* ctx, double* flops, cudaStream_t st) {
+  if (!ctx || !flops) return fail(MPG_ERR_INVALID_ARG, "ctx or flops is NULL");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  *flops = run_fp32_peak(ctx->d_scratch, ctx->sms, st);
+  LAUNCH_CHECK("fp32 peak");
+  return MPG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// Small kernels around the hot path: k-bucketing of the work list, the
+// per-point irradiance reduction, the guide histogram (update, prefix sums,
+// records), a standalone ray batch and an FP32 peak probe.
+#include "mpg_aux.cuh"
+
+namespace mpg {
+
+// ---------------------------------------------------------------------------
+// k-bucketing (counting sort of chain indices by length)
+// ---------------------------------------------------------------------------
+__global__ void k_bucket_count(const uint8_t* k, const uint8_t* status, int filter, int B, int* count) {
+  __shared__ int sh[MAXK + 1];
+  if (threadIdx.x <= MAXK) sh[threadIdx.x] = 0;
+  __syncthreads();
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    if (filter >= 0 && status[b] != filter) continue;
+    int kk = k[b];
+    if (kk >= 1 && kk <= MAXK) atomicAdd(&sh[kk], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x >= 1 && threadIdx.x <= MAXK && sh[threadIdx.x]) atomicAdd(&count[threadIdx.x], sh[threadIdx.x]);
+}
+
+__global__ void k_bucket_scan(const int* count, int* base, int* cursor) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int s = 0;
+    for (int kk = 0; kk <= MAXK; ++kk) {
+      base[kk] = s;
+      cursor[kk] = s;
+      s += kk >= 1 ? count[kk] : 0;
+    }
+  }
+}
+
+__global__ void k_bucket_scatter(const uint8_t* k, const uint8_t* status, int filter, int B, int* cursor, int* order) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    if (filter >= 0 && status[b] != filter) continue;
+    int kk = k[b];
+    if (kk >= 1 && kk <= MAXK) order[atomicAdd(&cursor[kk], 1)] = b;
+  }
+}
+
+void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
+                   int* order, int sms, cudaStream_t st) {
+  cudaMemsetAsync(count, 0, sizeof(int) * (MAXK + 1), st);
+  int grid = min(sms * 4, (B + 255) / 256 + 1);
+  k_bucket_count<<<grid, 256, 0, st>>>(k, status, filter, B, count);
+  k_bucket_scan<<<1, 32, 0, st>>>(count, base, cursor);
+  k_bucket_scatter<<<grid, 256, 0, st>>>(k, status, filter, B, cursor, order);
+}
+
+// ---------------------------------------------------------------------------
+// E[q] = (1/spq) sum_j contrib[q*spq + j]   (Eq. ThroughputMC), fixed order.
+// ---------------------------------------------------------------------------
+__global__ void k_irradiance(const float* contrib, int Q, int spq, float* E) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int j = 0; j < spq; ++j) s += contrib[(size_t)q * spq + j];
+    E[q] = s / (float)spq;
+  }
+}
+
+void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, cudaStream_t st) {
+  int grid = min(sms * 8, (Q + 255) / 256 + 1);
+  k_irradiance<<<grid, 256, 0, st>>>(contrib, Q, spq, E);
+}
+
+// ---------------------------------------------------------------------------
+// Guide histogram
+// ---------------------------------------------------------------------------
+__global__ void k_guide_update(DGuide g, const uint32_t* cell, const float* omega, const float* w, int R,
+                               const int* R_dev, int shift, int* err) {
+  double scale = ldexp(1.0, shift);
+  const int n = R_dev ? min(*R_dev, R) : R;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    uint32_t c = cell[r];
+    if ((int)c >= g.n_cells) { atomicOr(err, 2); continue; }
+    float wr = w[r];
+    if (!(wr > 0.0f)) continue;
+    double qd = floor((double)wr * scale);
+    unsigned long long q = qd >= 4294967295.0 ? 4294967295ull : (unsigned long long)qd;
+    if (q == 0) continue;
+    float3 om = make_float3(omega[r], omega[R + r], omega[2 * (size_t)R + r]);
+    int bin = guide_bin(g, om);
+    atomicAdd(reinterpret_cast<unsigned long long*>(const_cast<uint64_t*>(g.counts)) + (size_t)c * g.bins + bin, q);
+  }
+}
+
+// One block per cell: inclusive prefix sum of the cell's bins (uint64).
+__global__ void k_guide_cdf(DGuide g, uint64_t* cdf) {
+  extern __shared__ unsigned long long warp_sums[];
+  const int c = blockIdx.x;
+  const int bins = g.bins;
+  const int per = (bins + blockDim.x - 1) / blockDim.x;
+  const uint64_t* in = g.counts + (size_t)c * bins;
+  uint64_t* out = cdf + (size_t)c * bins;
+  int lo = threadIdx.x * per, hi = min(bins, lo + per);
+  unsigned long long s = 0;
+  for (int i = lo; i < hi; ++i) s += in[i];
+  // inclusive warp scan of the thread sums
+  unsigned long long v = s;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  if (lane == 31) warp_sums[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    unsigned long long x = lane < nw ? warp_sums[lane] : 0ull;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long n = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += n;
+    }
+    if (lane < nw) warp_sums[lane] = x;
+  }
+  __syncthreads();
+  unsigned long long run = v - s + (wid > 0 ? warp_sums[wid - 1] : 0ull);
+  for (int i = lo; i < hi; ++i) {
+    run += in[i];
+    out[i] = run;
+  }
+}
+
+void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* omega, const float* w, int R,
+                         const int* R_dev, int shift, int* err, int sms, cudaStream_t st) {
+  if (R > 0) {
+    int grid = min(sms * 8, (R + 255) / 256 + 1);
+    k_guide_update<<<grid, 256, 0, st>>>(g, cell, omega, w, R, R_dev, shift, err);
+  }
+  k_guide_cdf<<<g.n_cells, 256, (256 / 32) * sizeof(unsigned long long), st>>>(g, const_cast<uint64_t*>(g.cdf));
+}
+
+// Records (cell, w_D, w = contrib / A_L) of chains with a contribution.
+__global__ void k_guide_records(DChains c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
+                                float* w_out, int* R) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c.B; b += gridDim.x * blockDim.x) {
+    float cb = contrib[b];
+    if (!(cb > 0.0f)) continue;
+    int q = b / c.spq;
+    float3 xD = make_float3(c.xD[q], c.xD[c.Q + q], c.xD[2 * c.Q + q]);
+    float3 x1 = make_float3(c.x[b], c.x[(size_t)c.B + b], c.x[2 * (size_t)c.B + b]);
+    float3 w = unit(x1 - xD);
+    int r = atomicAdd(R, 1);
+    cell_out[r] = c.cell ? c.cell[q] : 0u;
+    om_out[r] = w.x;
+    om_out[c.B + r] = w.y;
+    om_out[2 * (size_t)c.B + r] = w.z;
+    w_out[r] = cb * inv_area;
+  }
+}
+
+void launch_guide_records(const DChains& c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
+                          float* w_out, int* R, int sms, cudaStream_t st) {
+  cudaMemsetAsync(R, 0, sizeof(int), st);
+  int grid = min(sms * 8, (c.B + 255) / 256 + 1);
+  k_guide_records<<<grid, 256, 0, st>>>(c, contrib, inv_area, cell_out, om_out, w_out, R);
+}
+
+// ---------------------------------------------------------------------------
+// Standalone ray batch (BVH/analytic nearest hit)
+// ---------------------------------------------------------------------------
+template <bool kS>
+__global__ void __launch_bounds__(128) k_trace(const __grid_constant__ DScene S, const float* o, const float* d, int n,
+                                               float tmin, float tmax, float* t, int* surf, int* prim, float* bary,
+                                               int* err, unsigned long long* stats) {
+  Counters cnt = {};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    float3 oo = make_float3(o[i], o[n + i], o[2 * (size_t)n + i]);
+    float3 dd = unit(make_float3(d[i], d[n + i], d[2 * (size_t)n + i]));
+    Hit h = intersect<kS>(S, oo, dd, tmin, tmax, err, cnt);
+    t[i] = h.surf >= 0 ? h.t : -1.0f;
+    surf[i] = h.surf;
+    prim[i] = h.prim;
+    bary[i] = h.b1;
+    bary[n + i] = h.b2;
+  }
+  if (kS) {
+    __syncwarp();
+    uint32_t v[5] = {cnt.casts, cnt.sphere, cnt.plane, cnt.node, cnt.tri};
+    const int idx[5] = {3, 4, 5, 6, 7};
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      uint32_t s = __reduce_add_sync(0xffffffffu, v[j]);
+      if ((threadIdx.x & 31) == 0 && s) atomicAdd(stats + idx[j], (unsigned long long)s);
+    }
+  }
+}
+
+void launch_trace(const DScene& S, const float* o, const float* d, int n, float tmin, float tmax, float* t, int* surf,
+                  int* prim, float* bary, int* err, unsigned long long* stats, bool st_on, int sms, cudaStream_t st) {
+  int grid = min(sms * 16, (n + 127) / 128 + 1);
+  if (st_on) k_trace<true><<<grid, 128, 0, st>>>(S, o, d, n, tmin, tmax, t, surf, prim, bary, err, stats);
+  else k_trace<false><<<grid, 128, 0, st>>>(S, o, d, n, tmin, tmax, t, surf, prim, bary, err, stats);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 peak probe: 8 independent FFMA chains per thread.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_ffma(float* out, int iters, float a, float b) {
+  float x0 = threadIdx.x * 1e-3f, x1 = x0 + 1.f, x2 = x0 + 2.f, x3 = x0 + 3.f;
+  float x4 = x0 + 4.f, x5 = x0 + 5.f, x6 = x0 + 6.f, x7 = x0 + 7.f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      x0 = fmaf(x0, a, b); x1 = fmaf(x1, a, b); x2 = fmaf(x2, a, b); x3 = fmaf(x3, a, b);
+      x4 = fmaf(x4, a, b); x5 = fmaf(x5, a, b); x6 = fmaf(x6, a, b); x7 = fmaf(x7, a, b);
+    }
+  }
+  float s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == 1234.5f) out[0] = s;  // keeps the chains live
+}
+
+double run_fp32_peak(float* scratch, int sms, cudaStream_t st) {
+  const int block = 256, per_sm = 8, iters = 4096;
+  int grid = sms * per_sm;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_ffma<<<grid, block, 0, st>>>(scratch, 64, 0.999f, 1e-3f);  // warm-up
+  cudaEventRecord(e0, st);
+  k_ffma<<<grid, block, 0, st>>>(scratch, iters, 0.999f, 1e-3f);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  double flops = (double)grid * block * iters * 16.0 * 8.0 * 2.0;
+  return ms > 0.f ? flops / (ms * 1e-3) : 0.0;
+}
+
+}  // namespace mpg

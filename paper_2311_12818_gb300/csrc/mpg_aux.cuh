@@ -1,0 +1,19 @@
+// Declarations of the auxiliary kernels' host launchers.
+#pragma once
+
+#include "mpg_kernels.cuh"
+
+namespace mpg {
+
+void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
+                   int* order, int sms, cudaStream_t st);
+void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, cudaStream_t st);
+void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* omega, const float* w, int R,
+                         const int* R_dev, int shift, int* err, int sms, cudaStream_t st);
+void launch_guide_records(const DChains& c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
+                          float* w_out, int* R, int sms, cudaStream_t st);
+void launch_trace(const DScene& S, const float* o, const float* d, int n, float tmin, float tmax, float* t, int* surf,
+                  int* prim, float* bary, int* err, unsigned long long* stats, bool st_on, int sms, cudaStream_t st);
+double run_fp32_peak(float* scratch, int sms, cudaStream_t st);
+
+}  // namespace mpg

@@ -1,0 +1,898 @@
+// Device-side math of the manifold walk (sm_103a, FP32 unless noted).
+//
+// One CUDA thread owns one chain; vertex state lives in registers, templated
+// on the chain length K so the 2x2-block arrays are fully unrolled.  The
+// formulas follow the paper's problem statement (Sec. 3-5) and the standard
+// manifold-walk definitions it cites:
+//   constraint  C_i = (h.s_i, h.t_i),  h = (eta_i w_i + eta_o w_o)/|...|
+//   Jacobian    block-tridiagonal, 2x2 blocks A_i, B_i, Cc_i (analytic)
+//   solve       2x2-block Thomas sweep
+//   step        tangent-plane move, step halving, reprojection by ray casting
+//   G           implicit function theorem, 2-column Thomas solve
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpg.h"
+
+namespace mpg {
+
+constexpr int MAXK = 8;
+constexpr int MAX_SURF = 16;
+constexpr int MAX_HF = 2;
+constexpr int MAX_TG = 16;
+constexpr int BVH_STACK = 64;
+
+enum { SURF_SPHERE = 0, SURF_CAP = 1, SURF_RECT = 2, SURF_HEIGHTFIELD = 3 };
+enum { MAT_MIRROR = 0, MAT_DIELECTRIC = 1 };
+enum { LIGHT_POINT = 0, LIGHT_RECT = 1 };
+enum { TARGET_SPHERE = 0, TARGET_RECT = 1 };
+enum { ST_INVALID = 0, ST_CONVERGED = 1, ST_FAILED = 2, ST_LIMIT = 3, ST_SEEDED = 255 };
+enum { ERR_BVH_STACK = 1 };
+
+// ---------------------------------------------------------------------------
+// Scene description passed by value (kernel parameter space).
+// ---------------------------------------------------------------------------
+struct DSurf {
+  int type, mat, hf;
+  float etaF, etaB, r, cap_cos;
+  float3 c, axis, ex, ey;
+  float ex2, ey2;  // squared half-axis lengths of a rectangle
+};
+
+struct DHF {
+  int nx, ny, surf, n_nodes;
+  float x0, y0, dx, dy;
+  const float4* P;      // [ny*nx] vertex positions (w unused)
+  const float4* N;      // [ny*nx] vertex interpolation normals
+  const float4* nodes;  // [n_nodes*4] two-child BVH nodes
+  const float4* tris;   // [n_tris*3] leaf-ordered (v0|prim, e1, e2)
+};
+
+struct DLight {
+  int type;
+  float3 p, n, exu, eyu;  // centre, emitting normal, unit half-axes
+  float power, area;
+};
+
+struct DTarget {
+  int type;
+  float3 c, ex, ey, n;
+  float r, area;
+};
+
+struct DScene {
+  int n_surf, n_hf, n_tg;
+  DSurf s[MAX_SURF];
+  DHF hf[MAX_HF];
+  DTarget tg[MAX_TG];
+  DLight L;
+};
+
+struct DGuide {
+  int n_cells, n_theta, n_phi, bins;
+  const uint64_t* counts;
+  const uint64_t* cdf;
+  const float* cos_theta;
+  const float* phi_cos;
+  const float* phi_sin;
+};
+
+// Per-thread work counters (flushed once per warp).
+struct Counters {
+  uint32_t newton, full_evals, c_evals, casts, sphere, plane, node, tri, ggt;
+};
+
+// ---------------------------------------------------------------------------
+// Vector helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return make_float3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float len(float3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ float3 unit(float3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+
+// Branchless orthonormal basis completing the unit vector n (Duff et al. 2017,
+// JCGT 6(1)); the constraint components are expressed in this frame.
+__device__ __forceinline__ void onb(float3 n, float3& b1, float3& b2) {
+  float s = n.z >= 0.0f ? 1.0f : -1.0f;
+  float a = -1.0f / (s + n.z);
+  float b = n.x * n.y * a;
+  b1 = make_float3(1.0f + s * n.x * n.x * a, s * b, -s * n.x);
+  b2 = make_float3(b, s + n.y * n.y * a, -n.y);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC 2011): counter (idx_lo, idx_hi, trial, block).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+    uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+__device__ __forceinline__ float u01(uint32_t r) { return (float)(r >> 8) * (1.0f / 16777216.0f); }
+
+// ---------------------------------------------------------------------------
+// Ray casting: r(x, w) of Eq. (deduction), nearest hit with all surfaces.
+// ---------------------------------------------------------------------------
+struct Hit {
+  float t;
+  int surf, prim;
+  float b1, b2;
+};
+
+// Roots of |o + t d - c|^2 = r^2 for unit d.  The discriminant is taken from
+// the distance of the line to the centre and the near root from the product of
+// the roots, which keeps FP32 accurate when o is far from or on the sphere.
+__device__ __forceinline__ bool sphere_roots(float3 o, float3 d, float3 c, float r, float& t0, float& t1) {
+  float3 oc = o - c;
+  float b = dot(oc, d);
+  float3 q = oc - d * b;
+  float disc = fmaf(r, r, -dot(q, q));
+  if (disc < 0.0f) return false;
+  float sq = sqrtf(disc);
+  float cc = fmaf(-r, r, dot(oc, oc));
+  float qq = -b - copysignf(sq, b);  // |qq| = |b| + sq
+  float ta = qq, tb = (qq != 0.0f) ? cc / qq : 0.0f;
+  t0 = fminf(ta, tb);
+  t1 = fmaxf(ta, tb);
+  return true;
+}
+
+__device__ __forceinline__ bool box_hit(float3 o, float3 inv, float lox, float hix, float loy, float hiy,
+                                        float loz, float hiz, float tmin, float tmax) {
+  float tx0 = (lox - o.x) * inv.x, tx1 = (hix - o.x) * inv.x;
+  float ty0 = (loy - o.y) * inv.y, ty1 = (hiy - o.y) * inv.y;
+  float tz0 = (loz - o.z) * inv.z, tz1 = (hiz - o.z) * inv.z;
+  float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), tmin));
+  float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+  return tn <= tf;
+}
+
+// Moeller-Trumbore test against a leaf triangle (v0, e1, e2).
+__device__ __forceinline__ bool tri_hit(float3 o, float3 d, float3 v0, float3 e1, float3 e2, float tmin,
+                                        float tmax, float& t, float& b1, float& b2) {
+  float3 pv = cross(d, e2);
+  float det = dot(e1, pv);
+  if (fabsf(det) < 1e-30f) return false;
+  float inv = 1.0f / det;
+  float3 tv = o - v0;
+  b1 = dot(tv, pv) * inv;
+  if (b1 < 0.0f || b1 > 1.0f) return false;
+  float3 qv = cross(tv, e1);
+  b2 = dot(d, qv) * inv;
+  if (b2 < 0.0f || b1 + b2 > 1.0f) return false;
+  t = dot(e2, qv) * inv;
+  return t > tmin && t < tmax;
+}
+
+template <bool kStats>
+__device__ __forceinline__ void hf_intersect(const DHF& H, float3 o, float3 d, float tmin, float& tbest,
+                                             Hit& best, int* err, Counters& cnt) {
+  float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+  int stack[BVH_STACK];
+  int sp = 0;
+  int node = 0;
+  while (true) {
+    const float4* nd = H.nodes + 4 * node;
+    float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2);
+    int4 ch = __ldg(reinterpret_cast<const int4*>(nd + 3));
+    if (kStats) cnt.node += 2;
+    bool hl = box_hit(o, inv, a.x, a.y, a.z, a.w, c.x, c.y, tmin, tbest);
+    bool hr = box_hit(o, inv, b.x, b.y, b.z, b.w, c.z, c.w, tmin, tbest);
+    int next = -1;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      bool h = side == 0 ? hl : hr;
+      if (!h) continue;
+      int idx = side == 0 ? ch.x : ch.y;
+      int count = side == 0 ? ch.z : ch.w;
+      if (count > 0) {
+        for (int q = idx; q < idx + count; ++q) {
+          const float4* tr = H.tris + 3 * q;
+          float4 v0 = __ldg(tr), e1 = __ldg(tr + 1), e2 = __ldg(tr + 2);
+          float t, b1, b2;
+          if (kStats) cnt.tri++;
+          if (tri_hit(o, d, f3(v0), f3(e1), f3(e2), tmin, tbest, t, b1, b2)) {
+            tbest = t;
+            best.t = t; best.surf = H.surf; best.prim = __float_as_int(v0.w);
+            best.b1 = b1; best.b2 = b2;
+          }
+        }
+      } else if (next < 0) {
+        next = idx;
+      } else {
+        if (sp >= BVH_STACK) { atomicOr(err, ERR_BVH_STACK); return; }
+        stack[sp++] = idx;
+      }
+    }
+    if (next >= 0) { node = next; continue; }
+    if (sp == 0) return;
+    node = stack[--sp];
+  }
+}
+
+template <bool kStats>
+__device__ Hit intersect(const DScene& S, float3 o, float3 d, float tmin, float tmax, int* err, Counters& cnt) {
+  Hit best;
+  best.t = -1.0f; best.surf = -1; best.prim = -1; best.b1 = best.b2 = 0.0f;
+  float tbest = tmax;
+  if (kStats) cnt.casts++;
+  for (int s = 0; s < S.n_surf; ++s) {
+    const DSurf& sf = S.s[s];
+    if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+      if (kStats) cnt.sphere++;
+      float t0, t1;
+      if (!sphere_roots(o, d, sf.c, sf.r, t0, t1)) continue;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float t = q == 0 ? t0 : t1;
+        if (!(t > tmin && t < tbest)) continue;
+        if (sf.type == SURF_CAP) {
+          float3 p = o + d * t;
+          if (dot(p - sf.c, sf.axis) < sf.r * sf.cap_cos) continue;
+        }
+        tbest = t; best.t = t; best.surf = s; best.prim = -1;
+        break;
+      }
+    } else if (sf.type == SURF_RECT) {
+      if (kStats) cnt.plane++;
+      float den = dot(d, sf.axis);
+      if (fabsf(den) < 1e-30f) continue;
+      float t = dot(sf.c - o, sf.axis) / den;
+      if (!(t > tmin && t < tbest)) continue;
+      float3 q = o + d * t - sf.c;
+      if (fabsf(dot(q, sf.ex)) > sf.ex2 || fabsf(dot(q, sf.ey)) > sf.ey2) continue;
+      tbest = t; best.t = t; best.surf = s; best.prim = -1;
+    } else {
+      hf_intersect<kStats>(S.hf[sf.hf], o, d, tmin, tbest, best, err, cnt);
+    }
+  }
+  return best;
+}
+
+// Heightfield triangle corners (grid vertex indices) of triangle `tri`.
+__device__ __forceinline__ void hf_tri(const DHF& H, int tri, int& v0, int& v1, int& v2) {
+  int quad = tri >> 1, t = tri & 1;
+  int i = quad % (H.nx - 1), j = quad / (H.nx - 1);
+  int v00 = j * H.nx + i;
+  v0 = v00;
+  v1 = t == 0 ? v00 + 1 : v00 + H.nx + 1;
+  v2 = t == 0 ? v00 + H.nx + 1 : v00 + H.nx;
+}
+
+// Vertex of a hit: analytic surfaces snap the ray point onto the surface;
+// triangles take the barycentric combination of their corners.
+__device__ __forceinline__ float3 hit_point(const DScene& S, float3 o, float3 d, const Hit& h) {
+  const DSurf& sf = S.s[h.surf];
+  float3 p = o + d * h.t;
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    p = sf.c + unit(p - sf.c) * sf.r;
+  } else if (sf.type == SURF_RECT) {
+    p = p - sf.axis * dot(p - sf.c, sf.axis);
+  } else {
+    const DHF& H = S.hf[sf.hf];
+    int v0, v1, v2;
+    hf_tri(H, h.prim, v0, v1, v2);
+    float3 P0 = f3(__ldg(H.P + v0)), P1 = f3(__ldg(H.P + v1)), P2 = f3(__ldg(H.P + v2));
+    p = P0 + (P1 - P0) * h.b1 + (P2 - P0) * h.b2;
+  }
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Local frames
+// ---------------------------------------------------------------------------
+struct Frame {
+  float3 n, dpdu, dpdv, dndu, dndv;
+};
+
+// Unit shading normal only (constraint-only evaluations).
+__device__ __forceinline__ float3 vertex_normal(const DScene& S, int surf, int prim, float3 p, float b1, float b2) {
+  const DSurf& sf = S.s[surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) return unit(p - sf.c);
+  if (sf.type == SURF_RECT) return sf.axis;
+  const DHF& H = S.hf[sf.hf];
+  int v0, v1, v2;
+  hf_tri(H, prim, v0, v1, v2);
+  float3 N0 = f3(__ldg(H.N + v0)), N1 = f3(__ldg(H.N + v1)), N2 = f3(__ldg(H.N + v2));
+  return unit(N0 * (1.0f - b1 - b2) + N1 * b1 + N2 * b2);
+}
+
+__device__ __forceinline__ Frame vertex_frame(const DScene& S, int surf, int prim, float3 p, float b1, float b2) {
+  Frame f;
+  const DSurf& sf = S.s[surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    f.n = unit(p - sf.c);
+    onb(f.n, f.dpdu, f.dpdv);
+    float ir = 1.0f / sf.r;
+    f.dndu = f.dpdu * ir;
+    f.dndv = f.dpdv * ir;
+  } else if (sf.type == SURF_RECT) {
+    f.n = sf.axis;
+    onb(f.n, f.dpdu, f.dpdv);
+    f.dndu = make_float3(0.f, 0.f, 0.f);
+    f.dndv = f.dndu;
+  } else {
+    // n = normalize(sum b_j N_j); a tangent move a changes the barycentrics by
+    // the solution of a = db1 e1 + db2 e2.
+    const DHF& H = S.hf[sf.hf];
+    int v0, v1, v2;
+    hf_tri(H, prim, v0, v1, v2);
+    float3 P0 = f3(__ldg(H.P + v0)), P1 = f3(__ldg(H.P + v1)), P2 = f3(__ldg(H.P + v2));
+    float3 N0 = f3(__ldg(H.N + v0)), N1 = f3(__ldg(H.N + v1)), N2 = f3(__ldg(H.N + v2));
+    float3 e1 = P1 - P0, e2 = P2 - P0;
+    onb(unit(cross(e1, e2)), f.dpdu, f.dpdv);
+    float3 Ns = N0 * (1.0f - b1 - b2) + N1 * b1 + N2 * b2;
+    float il = 1.0f / len(Ns);
+    f.n = Ns * il;
+    float g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2);
+    float igd = 1.0f / (g11 * g22 - g12 * g12);
+    float3 dN1 = N1 - N0, dN2 = N2 - N0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float3 a = q == 0 ? f.dpdu : f.dpdv;
+      float r1 = dot(e1, a), r2 = dot(e2, a);
+      float db1 = (g22 * r1 - g12 * r2) * igd, db2 = (g11 * r2 - g12 * r1) * igd;
+      float3 dN = dN1 * db1 + dN2 * db2;
+      float3 dn = (dN - f.n * dot(f.n, dN)) * il;
+      if (q == 0) f.dndu = dn; else f.dndv = dn;
+    }
+  }
+  return f;
+}
+
+// Indices of refraction on the previous / next vertex's side (R: equal).
+__device__ __forceinline__ bool etas(const DSurf& sf, bool front, bool refract, float& ei, float& eo) {
+  if (sf.mat == MAT_MIRROR) { ei = eo = 1.0f; return !refract; }
+  ei = front ? sf.etaF : sf.etaB;
+  eo = refract ? (front ? sf.etaB : sf.etaF) : ei;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Constraint and Jacobian blocks at one vertex
+// ---------------------------------------------------------------------------
+struct VB {
+  float2 C;
+  float4 A, B, Cc;  // row-major 2x2: (m00, m01, m10, m11)
+  float ei, eo;
+  bool front;
+};
+
+// Constraint only (line-search evaluations).
+__device__ __forceinline__ bool vertex_c(float3 xp, float3 x, float3 xn, float3 n, const DSurf& sf,
+                                         bool refract, float2& C) {
+  float3 wi = unit(xp - x), wo = unit(xn - x);
+  float ei, eo;
+  if (!etas(sf, dot(wi, n) > 0.0f, refract, ei, eo)) return false;
+  float3 ht = wi * ei + wo * eo;
+  float L2 = dot(ht, ht);
+  if (!(L2 > 0.0f)) return false;
+  float3 h = ht * (1.0f / sqrtf(L2));
+  float3 s, t;
+  onb(n, s, t);
+  C = make_float2(dot(h, s), dot(h, t));
+  return true;
+}
+
+// Full evaluation.  want_a / want_c: also the off-diagonal blocks (for the
+// first / last vertex they are derivatives with respect to the separators).
+__device__ __forceinline__ bool vertex_blocks(float3 xp, float3 tpu, float3 tpv, float3 x, const Frame& f,
+                                              float3 xn, float3 tnu, float3 tnv, const DSurf& sf,
+                                              bool refract, bool want_a, bool want_c, VB& o) {
+  float3 wi = xp - x, wo = xn - x;
+  float di = len(wi), dO = len(wo);
+  if (!(di > 0.0f) || !(dO > 0.0f)) return false;
+  float idi = 1.0f / di, ido = 1.0f / dO;
+  wi = wi * idi;
+  wo = wo * ido;
+  o.front = dot(wi, f.n) > 0.0f;
+  if (!etas(sf, o.front, refract, o.ei, o.eo)) return false;
+  float3 ht = wi * o.ei + wo * o.eo;
+  float L = len(ht);
+  if (!(L > 0.0f)) return false;
+  float iL = 1.0f / L;
+  float3 h = ht * iL;
+  float3 s, t;
+  onb(f.n, s, t);
+  o.C = make_float2(dot(h, s), dot(h, t));
+  float hn = dot(h, f.n);
+  // The derivative of C along dh is (s.dh, t.dh) with dh = (I - h h^T) dht / L;
+  // fold the projection into the row vectors: s' = (s - h (h.s)) / L.
+  float3 sp = (s - h * o.C.x) * iL, tp = (t - h * o.C.y) * iL;
+  // d(w)/d(y) a = (a - w (w.a)) / d for w = (y - x)/|y - x|.
+  auto Pi = [&](float3 a) { return (a - wi * dot(wi, a)) * idi; };
+  auto Po = [&](float3 a) { return (a - wo * dot(wo, a)) * ido; };
+  float3 piu = Pi(f.dpdu) * o.ei, piv = Pi(f.dpdv) * o.ei;
+  float3 pou = Po(f.dpdu) * o.eo, pov = Po(f.dpdv) * o.eo;
+  float3 bu = -(piu + pou), bv = -(piv + pov);
+  o.B = make_float4(dot(sp, bu) - hn * dot(s, f.dndu), dot(sp, bv) - hn * dot(s, f.dndv),
+                    dot(tp, bu) - hn * dot(t, f.dndu), dot(tp, bv) - hn * dot(t, f.dndv));
+  if (want_a) {
+    float3 au = Pi(tpu) * o.ei, av = Pi(tpv) * o.ei;
+    o.A = make_float4(dot(sp, au), dot(sp, av), dot(tp, au), dot(tp, av));
+  }
+  if (want_c) {
+    float3 cu = Po(tnu) * o.eo, cv = Po(tnv) * o.eo;
+    o.Cc = make_float4(dot(sp, cu), dot(sp, cv), dot(tp, cu), dot(tp, cv));
+  }
+  return true;
+}
+
+__device__ __forceinline__ float4 mm(float4 a, float4 b) {
+  return make_float4(a.x * b.x + a.y * b.z, a.x * b.y + a.y * b.w, a.z * b.x + a.w * b.z, a.z * b.y + a.w * b.w);
+}
+__device__ __forceinline__ float2 mv(float4 a, float2 v) {
+  return make_float2(a.x * v.x + a.y * v.y, a.z * v.x + a.w * v.y);
+}
+__device__ __forceinline__ bool inv2(float4 m, float sing_eps, float4& r) {
+  float det = m.x * m.w - m.y * m.z;
+  float mx = fmaxf(fmaxf(fabsf(m.x), fabsf(m.y)), fmaxf(fabsf(m.z), fabsf(m.w)));
+  if (!(fabsf(det) > sing_eps * mx * mx)) return false;
+  float id = 1.0f / det;
+  r = make_float4(m.w * id, -m.y * id, -m.z * id, m.x * id);
+  return true;
+}
+
+// Block Thomas sweep J X = R for M right-hand-side columns.  R[i][c] holds
+// the 2-vector of block row i, column c; overwritten by X.
+template <int K, int M>
+__device__ __forceinline__ bool thomas(const VB* vb, float2 (&R)[K][M], float sing_eps) {
+  float4 Binv[K];
+  float4 Bp = vb[0].B;
+  if (!inv2(Bp, sing_eps, Binv[0])) return false;
+#pragma unroll
+  for (int i = 1; i < K; ++i) {
+    float4 Lm = mm(vb[i].A, Binv[i - 1]);
+    float4 LC = mm(Lm, vb[i - 1].Cc);
+    Bp = make_float4(vb[i].B.x - LC.x, vb[i].B.y - LC.y, vb[i].B.z - LC.z, vb[i].B.w - LC.w);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      float2 l = mv(Lm, R[i - 1][c]);
+      R[i][c] = make_float2(R[i][c].x - l.x, R[i][c].y - l.y);
+    }
+    if (!inv2(Bp, sing_eps, Binv[i])) return false;
+  }
+#pragma unroll
+  for (int i = K - 1; i >= 0; --i) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      float2 r = R[i][c];
+      if (i < K - 1) {
+        float2 cx = mv(vb[i].Cc, R[i + 1][c]);
+        r = make_float2(r.x - cx.x, r.y - cx.y);
+      }
+      R[i][c] = mv(Binv[i], r);
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Chain state of one thread
+// ---------------------------------------------------------------------------
+template <int K>
+struct Chain {
+  float3 x[K];
+  int surf[K], prim[K];
+  float b1[K], b2[K];
+};
+
+struct Ends {
+  float3 xD, nD, xL;
+  uint32_t tau;
+};
+
+// Full evaluation of all K vertices; fills vb and the tangent bases.
+template <int K, bool kStats>
+__device__ __forceinline__ bool eval_full(const DScene& S, const Chain<K>& ch, const Ends& e, VB (&vb)[K],
+                                          float3 (&tu)[K], float3 (&tv)[K], float& cnorm2, float& cmax,
+                                          bool want_ends, Counters& cnt) {
+  Frame fr[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    fr[i] = vertex_frame(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
+    tu[i] = fr[i].dpdu;
+    tv[i] = fr[i].dpdv;
+  }
+  float3 ru, rv, lu, lv;
+  onb(e.nD, ru, rv);
+  lu = S.L.exu;
+  lv = S.L.eyu;
+  cnorm2 = 0.0f;
+  cmax = 0.0f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 xp = i == 0 ? e.xD : ch.x[i - 1];
+    float3 xn = i == K - 1 ? e.xL : ch.x[i + 1];
+    float3 pu = i == 0 ? ru : tu[i > 0 ? i - 1 : 0], pv = i == 0 ? rv : tv[i > 0 ? i - 1 : 0];
+    float3 nu = i == K - 1 ? lu : tu[i < K - 1 ? i + 1 : 0], nv = i == K - 1 ? lv : tv[i < K - 1 ? i + 1 : 0];
+    bool wa = i > 0 || want_ends, wc = i < K - 1 || want_ends;
+    if (!vertex_blocks(xp, pu, pv, ch.x[i], fr[i], xn, nu, nv, S.s[ch.surf[i]], (e.tau >> i) & 1u, wa, wc, vb[i]))
+      return false;
+    cnorm2 = fmaf(vb[i].C.x, vb[i].C.x, fmaf(vb[i].C.y, vb[i].C.y, cnorm2));
+    cmax = fmaxf(cmax, fmaxf(fabsf(vb[i].C.x), fabsf(vb[i].C.y)));
+  }
+  if (kStats) cnt.full_evals += K;
+  return true;
+}
+
+template <int K, bool kStats>
+__device__ __forceinline__ bool eval_c(const DScene& S, const Chain<K>& ch, const Ends& e, float& cnorm2,
+                                       Counters& cnt) {
+  cnorm2 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 xp = i == 0 ? e.xD : ch.x[i - 1];
+    float3 xn = i == K - 1 ? e.xL : ch.x[i + 1];
+    float3 n = vertex_normal(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
+    float2 C;
+    if (!vertex_c(xp, ch.x[i], xn, n, S.s[ch.surf[i]], (e.tau >> i) & 1u, C)) return false;
+    cnorm2 = fmaf(C.x, C.x, fmaf(C.y, C.y, cnorm2));
+  }
+  if (kStats) cnt.c_evals += K;
+  return true;
+}
+
+// Move every vertex by beta (dpdu du_0 + dpdv du_1) and reproject: a ray from
+// x_D through the moved x_1, then from each new vertex through the next moved
+// one; every hit must lie on the vertex's own surface.
+template <int K, bool kStats>
+__device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, const Ends& e, const float3 (&tu)[K],
+                                        const float3 (&tv)[K], const float2 (&du)[K][1], float beta, float ray_eps,
+                                        Chain<K>& out, int* err, Counters& cnt) {
+  float3 prev = e.xD;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 target = ch.x[i] + (tu[i] * du[i][0].x + tv[i] * du[i][0].y) * beta;
+    float3 d = target - prev;
+    float l2 = dot(d, d);
+    if (!(l2 > 0.0f)) return false;
+    d = d * (1.0f / sqrtf(l2));
+    Hit h = intersect<kStats>(S, prev, d, ray_eps, 3.0e38f, err, cnt);
+    if (h.surf != ch.surf[i]) return false;
+    out.x[i] = hit_point(S, prev, d, h);
+    out.surf[i] = h.surf;
+    out.prim[i] = h.prim;
+    out.b1[i] = h.b1;
+    out.b2[i] = h.b2;
+    prev = out.x[i];
+  }
+  return true;
+}
+
+// Newton manifold walk of one chain.  Returns the chain status; `iters` gets
+// the number of Newton steps taken.
+template <int K, bool kStats>
+__device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_params& P, int& iters, int* err,
+                    Counters& cnt) {
+  VB vb[K];
+  float3 tu[K], tv[K];
+  float cn2, cmax;
+  for (int it = 0;; ++it) {
+    iters = it;
+    if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, false, cnt)) return ST_FAILED;
+    if (cmax < P.tol) return ST_CONVERGED;
+    if (it >= P.max_iter) return ST_LIMIT;
+    float2 du[K][1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
+    if (kStats) cnt.newton++;
+    if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
+    float beta = 1.0f;
+    bool accepted = false;
+    for (int hv = 0; hv <= P.max_halvings; ++hv, beta *= 0.5f) {
+      Chain<K> cand;
+      if (!propose<K, kStats>(S, ch, e, tu, tv, du, beta, P.ray_eps, cand, err, cnt)) continue;
+      float cc2;
+      if (eval_c<K, kStats>(S, cand, e, cc2, cnt) && cc2 < cn2) {
+        ch = cand;
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) return ST_FAILED;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Seeds (Eq. deduction; p_0 of Sec. 5.4; guided mixture of Sec. 5.5)
+// ---------------------------------------------------------------------------
+// Scattered propagation direction (mirror reflection or Snell refraction).
+__device__ __forceinline__ bool scatter(const DSurf& sf, float3 n, float3 d, bool refract, float3& out) {
+  if (!refract) {
+    out = d - n * (2.0f * dot(d, n));
+    return true;
+  }
+  if (sf.mat == MAT_MIRROR) return false;
+  float ci = -dot(d, n);
+  float e1 = sf.etaF, e2 = sf.etaB;
+  float3 nn = n;
+  if (ci < 0.0f) { ci = -ci; e1 = sf.etaB; e2 = sf.etaF; nn = -n; }
+  float eta = e1 / e2;
+  float k2 = 1.0f - eta * eta * (1.0f - ci * ci);
+  if (k2 < 0.0f) return false;
+  out = unit(d * eta + nn * (eta * ci - sqrtf(k2)));
+  return true;
+}
+
+__device__ __forceinline__ int guide_bin(const DGuide& g, float3 w) {
+  int it = 0;
+  for (int j = 1; j < g.n_theta; ++j) it += (w.z < __ldg(g.cos_theta + j)) ? 1 : 0;
+  bool upper = (w.y > 0.0f) || (w.y == 0.0f && w.x >= 0.0f);
+  int half = g.n_phi >> 1;
+  int ip = upper ? 0 : half;
+  int j0 = upper ? 1 : half + 1, j1 = upper ? half : g.n_phi;
+  double x = (double)w.x, y = (double)w.y;
+  for (int j = j0; j < j1; ++j) {
+    // exact sign: products of two FP32 values are exact in FP64
+    double cr = __dsub_rn(__dmul_rn((double)__ldg(g.phi_cos + j), y), __dmul_rn((double)__ldg(g.phi_sin + j), x));
+    ip += cr >= 0.0 ? 1 : 0;
+  }
+  return it * g.n_phi + ip;
+}
+
+// Solid-angle density of p_0 at direction w from x_D.
+__device__ __forceinline__ float p0_pdf(const DScene& S, float3 xD, float3 w) {
+  float sum = 0.0f;
+  for (int i = 0; i < S.n_tg; ++i) {
+    const DTarget& tg = S.tg[i];
+    if (tg.type == TARGET_SPHERE) {
+      float d = len(xD - tg.c);
+      if (d <= tg.r) continue;
+      float t0, t1;
+      if (!sphere_roots(xD, w, tg.c, tg.r, t0, t1) || t0 <= 0.0f) continue;
+      float3 p = xD + w * t0;
+      float cp = fabsf(dot(unit(p - tg.c), w));
+      float pA = 1.0f / (6.28318530717958647f * tg.r * tg.r * (1.0f - tg.r / d));
+      sum += pA * t0 * t0 / cp;
+    } else {
+      float den = dot(w, tg.n);
+      if (fabsf(den) < 1e-30f) continue;
+      float t = dot(tg.c - xD, tg.n) / den;
+      if (t <= 0.0f) continue;
+      float3 q = xD + w * t - tg.c;
+      if (fabsf(dot(q, tg.ex)) > dot(tg.ex, tg.ex) || fabsf(dot(q, tg.ey)) > dot(tg.ey, tg.ey)) continue;
+      sum += t * t / (tg.area * fabsf(den));
+    }
+  }
+  return S.n_tg > 0 ? sum / (float)S.n_tg : 0.0f;
+}
+
+// Draw seed `trial` of chain idx and deduce its vertices.  Returns validity;
+// fills ch (first k vertices), tau and pdf.
+template <int K, bool kStats>
+__device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
+                          bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
+                          Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt) {
+  uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
+  uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
+  uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
+  tau_out = tau;
+  uint64_t total = 0;
+  bool use_guide = g != nullptr;
+  const uint64_t* cdf = nullptr;
+  if (use_guide && cell >= (uint32_t)g->n_cells) {  // bad cell index: flag it, sample p_0 only
+    atomicOr(err, 2);
+    use_guide = false;
+  }
+  if (use_guide) {
+    cdf = g->cdf + (size_t)cell * g->bins;
+    total = __ldg(reinterpret_cast<const unsigned long long*>(cdf + g->bins - 1));
+    use_guide = total > 0;
+  }
+  bool pick_p0 = !use_guide || u01(r0.x) < P.alpha;
+  float3 w;
+  if (pick_p0) {
+    if (S.n_tg == 0) return false;
+    int ti = min((int)(u01(r1.x) * (float)S.n_tg), S.n_tg - 1);
+    const DTarget& tg = S.tg[ti];
+    float u1 = u01(r0.z), u2 = u01(r0.w);
+    float3 p;
+    if (tg.type == TARGET_SPHERE) {
+      float3 ax = e.xD - tg.c;
+      float d = len(ax);
+      if (d <= tg.r) return false;
+      ax = ax * (1.0f / d);
+      float3 e1, e2;
+      onb(ax, e1, e2);
+      float ca = tg.r / d + u1 * (1.0f - tg.r / d);
+      float sa = sqrtf(fmaxf(0.0f, 1.0f - ca * ca));
+      float sp, cp;
+      sincospif(2.0f * u2, &sp, &cp);
+      p = tg.c + (ax * ca + (e1 * cp + e2 * sp) * sa) * tg.r;
+    } else {
+      p = tg.c + tg.ex * (2.0f * u1 - 1.0f) + tg.ey * (2.0f * u2 - 1.0f);
+    }
+    w = unit(p - e.xD);
+  } else {
+    // inverse CDF on exact integers: target = floor(r * total / 2^32)
+    uint64_t r = r0.y;
+    uint64_t lo = r * total, hi = __umul64hi(r, total);
+    uint64_t target = (hi << 32) | (lo >> 32);
+    int a = 0, b = g->bins - 1;
+    while (a < b) {
+      int mid = (a + b) >> 1;
+      uint64_t c = __ldg(reinterpret_cast<const unsigned long long*>(cdf + mid));
+      if (c > target) b = mid; else a = mid + 1;
+    }
+    int it = a / g->n_phi, ip = a % g->n_phi;
+    float clo = __ldg(g->cos_theta + it), chi = __ldg(g->cos_theta + it + 1);
+    float ct = clo + u01(r0.z) * (chi - clo);
+    float st = sqrtf(fmaxf(0.0f, 1.0f - ct * ct));
+    float sp, cp;
+    sincospif(2.0f * ((float)ip + u01(r0.w)) / (float)g->n_phi, &sp, &cp);
+    w = make_float3(st * cp, st * sp, ct);
+  }
+  if (dot(w, e.nD) <= 0.0f) return false;
+  float p0 = p0_pdf(S, e.xD, w);
+  if (use_guide) {
+    int bin = guide_bin(*g, w);
+    uint64_t cnt_b = __ldg(reinterpret_cast<const unsigned long long*>(g->counts + (size_t)cell * g->bins + bin));
+    int it = bin / g->n_phi;
+    float dcos = __ldg(g->cos_theta + it) - __ldg(g->cos_theta + it + 1);
+    float ph = (float)((double)cnt_b / (double)total) / ((6.28318530717958647f / (float)g->n_phi) * dcos);
+    pdf = P.alpha * p0 + (1.0f - P.alpha) * ph;
+  } else {
+    pdf = p0;
+  }
+  float3 o = e.xD, d = w;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    Hit h = intersect<kStats>(S, o, d, P.ray_eps, 3.0e38f, err, cnt);
+    if (h.surf < 0) return false;
+    ch.x[i] = hit_point(S, o, d, h);
+    ch.surf[i] = h.surf;
+    ch.prim[i] = h.prim;
+    ch.b1[i] = h.b1;
+    ch.b2[i] = h.b2;
+    if (i < K - 1) {
+      float3 n = vertex_normal(S, h.surf, h.prim, ch.x[i], h.b1, h.b2);
+      float3 dn;
+      if (!scatter(S.s[h.surf], n, d, (tau >> i) & 1u, dn)) return false;
+      o = ch.x[i];
+      d = dn;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Contribution (Eq. ThroughputEval)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float fresnel(float c1, float e1, float e2) {
+  float r = e1 / e2;
+  float s2 = r * r * (1.0f - c1 * c1);
+  if (s2 >= 1.0f) return 1.0f;
+  float c2 = sqrtf(1.0f - s2);
+  float rs = (e1 * c1 - e2 * c2) / (e1 * c1 + e2 * c2);
+  float rp = (e2 * c1 - e1 * c2) / (e2 * c1 + e1 * c2);
+  return 0.5f * (rs * rs + rp * rp);
+}
+
+template <bool kStats>
+__device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 b, float eps, int* err, Counters& cnt) {
+  float3 d = b - a;
+  float l = len(d);
+  if (!(l > 2.0f * eps)) return true;
+  Hit h = intersect<kStats>(S, a, d * (1.0f / l), eps, l - eps, err, cnt);
+  return h.surf < 0;
+}
+
+// Admissibility, G (IFT; FP64 determinant for K >= 6), kappa.  Returns false
+// for an inadmissible chain.
+template <int K, bool kStats>
+__device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
+                             float& kappa, int* err, Counters& cnt) {
+  VB vb[K];
+  float3 tu[K], tv[K];
+  float cn2, cmax;
+  if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, true, cnt)) return false;
+  // vertex types must match the sides of their neighbours
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 xp = i == 0 ? e.xD : ch.x[i - 1];
+    float3 xn = i == K - 1 ? e.xL : ch.x[i + 1];
+    float3 n = vertex_normal(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
+    float si = dot(xp - ch.x[i], n), so = dot(xn - ch.x[i], n);
+    bool refract = (e.tau >> i) & 1u;
+    if (refract ? !(si * so < 0.0f) : !(si * so > 0.0f)) return false;
+  }
+  float3 wD = unit(ch.x[0] - e.xD);
+  float cosD = dot(e.nD, wD);
+  if (!(cosD > 0.0f)) return false;
+  bool point = S.L.type == LIGHT_POINT;
+  if (!point && !(dot(S.L.n, unit(ch.x[K - 1] - e.xL)) > 0.0f)) return false;
+  if (!segment_clear<kStats>(S, e.xD, ch.x[0], P.ray_eps, err, cnt)) return false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 b = i == K - 1 ? e.xL : ch.x[i + 1];
+    if (!segment_clear<kStats>(S, ch.x[i], b, P.ray_eps, err, cnt)) return false;
+  }
+  // G: J Y = -dC/du_end, end = light axes (area light) or receiver axes (point)
+  float2 Y[K][2];
+#pragma unroll
+  for (int i = 0; i < K; ++i) { Y[i][0] = make_float2(0.f, 0.f); Y[i][1] = Y[i][0]; }
+  if (point) {
+    Y[0][0] = make_float2(-vb[0].A.x, -vb[0].A.z);
+    Y[0][1] = make_float2(-vb[0].A.y, -vb[0].A.w);
+  } else {
+    Y[K - 1][0] = make_float2(-vb[K - 1].Cc.x, -vb[K - 1].Cc.z);
+    Y[K - 1][1] = make_float2(-vb[K - 1].Cc.y, -vb[K - 1].Cc.w);
+  }
+  if (kStats) cnt.ggt += K;
+  if (!thomas<K, 2>(vb, Y, P.sing_eps)) return false;
+  int vi = point ? K - 1 : 0;
+  float3 anchor = point ? e.xL : e.xD;
+  float3 w = ch.x[vi] - anchor;
+  float dist = len(w);
+  w = w * (1.0f / dist);
+  float3 a, b;
+  onb(w, a, b);
+  float M[2][2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    float3 dx = tu[vi] * Y[vi][c].x + tv[vi] * Y[vi][c].y;
+    float3 dw = (dx - w * dot(w, dx)) * (1.0f / dist);
+    M[0][c] = dot(a, dw);
+    M[1][c] = dot(b, dw);
+  }
+  float det;
+  if (K >= 6) {
+    double dd = (double)M[0][0] * (double)M[1][1] - (double)M[0][1] * (double)M[1][0];
+    det = (float)fabs(dd);
+  } else {
+    det = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
+  }
+  G = point ? det : cosD * det;
+  // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2
+  float kap = 1.0f;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const DSurf& sf = S.s[ch.surf[i]];
+    if (sf.mat == MAT_MIRROR) continue;
+    float3 xp = i == 0 ? e.xD : ch.x[i - 1];
+    float3 n = vertex_normal(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
+    float ci = fabsf(dot(unit(xp - ch.x[i]), n));
+    float e2 = vb[i].front ? sf.etaB : sf.etaF;
+    float F = fresnel(ci, vb[i].ei, e2);
+    if ((e.tau >> i) & 1u) {
+      float r = vb[i].ei / vb[i].eo;
+      kap *= (1.0f - F) * r * r;
+    } else {
+      kap *= F;
+    }
+  }
+  kappa = kap;
+  return true;
+}
+
+// FP64 distance test of two converged chains (same types and surfaces).
+template <int K>
+__device__ __forceinline__ bool same_solution(const Chain<K>& a, const Chain<K>& b, double eps2) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    if (a.surf[i] != b.surf[i]) return false;
+    double dx = (double)a.x[i].x - (double)b.x[i].x;
+    double dy = (double)a.x[i].y - (double)b.x[i].y;
+    double dz = (double)a.x[i].z - (double)b.x[i].z;
+    if (!(dx * dx + dy * dy + dz * dz < eps2)) return false;
+  }
+  return true;
+}
+
+}  // namespace mpg

@@ -1,0 +1,4 @@
+// Instantiation of the hot-path kernels for chains of length 7.
+#include "mpg_kernels_impl.cuh"
+
+template struct mpg::KLaunch<7>;

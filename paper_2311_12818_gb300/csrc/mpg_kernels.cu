@@ -1,0 +1,65 @@
+// Dispatch of the per-chain-length kernels to their instantiations
+// (mpg_k1.cu .. mpg_k8.cu, compiled as separate translation units).
+#include "mpg_kernels.cuh"
+
+namespace mpg {
+
+extern template struct KLaunch<1>;
+extern template struct KLaunch<2>;
+extern template struct KLaunch<3>;
+extern template struct KLaunch<4>;
+extern template struct KLaunch<5>;
+extern template struct KLaunch<6>;
+extern template struct KLaunch<7>;
+extern template struct KLaunch<8>;
+
+#define MPG_SWITCH(K_, CALL) \
+  switch (K_) {              \
+    case 1: CALL(1); break;  \
+    case 2: CALL(2); break;  \
+    case 3: CALL(3); break;  \
+    case 4: CALL(4); break;  \
+    case 5: CALL(5); break;  \
+    case 6: CALL(6); break;  \
+    case 7: CALL(7); break;  \
+    case 8: CALL(8); break;  \
+    default: break;          \
+  }
+
+void launch_seed(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                 uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::seed(stats, S, g, c, w, key, offset, P, ctx, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_walk(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                 int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::walk(stats, S, c, w, P, ctx, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_contrib(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o,
+                    DCtx ctx, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::contrib(stats, S, c, w, P, o, ctx, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_bernoulli(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                      uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::bernoulli(stats, S, g, c, w, key, offset, P, o, ctx, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+int blocks_per_sm(int which, int K, bool stats, int block) {
+  int n = 1;
+#define C_(KK) n = KLaunch<KK>::blocks_per_sm(which, stats, block)
+  MPG_SWITCH(K, C_)
+#undef C_
+  return n;
+}
+
+}  // namespace mpg

@@ -1,0 +1,75 @@
+// Kernel declarations shared by the kernel and host translation units.
+#pragma once
+
+#include "mpg_device.cuh"
+
+namespace mpg {
+
+// Raw device view of a chain batch (see mpg_chains in mpg.h).
+struct DChains {
+  int B, Q, spq;
+  const float* xD;
+  const float* nD;
+  const uint32_t* cell;
+  const float* xL;
+  const uint8_t* k;
+  const float* pn;
+  uint8_t* tau;
+  float* x;
+  int32_t* surf;
+  int32_t* prim;
+  float* bary;
+  float* pdf;
+  uint8_t* status;
+  uint8_t* iters;
+};
+
+// Optional k-bucketed work list: chains order[base[K] .. base[K]+count[K]).
+struct DWork {
+  const int* order;   // NULL => identity over [0, B)
+  const int* base;    // [MAXK+1] bucket starts (device)
+  const int* count;   // [MAXK+1] bucket sizes (device)
+};
+
+struct DOut {
+  float* G;
+  float* kappa;
+  float* T;
+  uint32_t* trials;
+  uint8_t* capped;
+  float* contrib;
+};
+
+struct DCtx {
+  int* err;                      // device error word
+  unsigned long long* stats;     // [12] counters (mpg_stats layout)
+};
+
+void launch_seed(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                 uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st);
+void launch_walk(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                 int grid, int block, cudaStream_t st);
+void launch_contrib(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o,
+                    DCtx ctx, int grid, int block, cudaStream_t st);
+void launch_bernoulli(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                      uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block, cudaStream_t st);
+
+// Occupancy-derived grid for the per-K kernels (blocks per SM x SMs).
+int blocks_per_sm(int which, int K, bool stats, int block);
+
+// Host launchers of the kernels for one chain length K (see mpg_kernels_impl.cuh).
+template <int K>
+struct KLaunch {
+  static void seed(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                   uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st);
+  static void walk(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx, int grid,
+                   int block, cudaStream_t st);
+  static void contrib(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx,
+                      int grid, int block, cudaStream_t st);
+  static void bernoulli(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                        uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
+                        cudaStream_t st);
+  static int blocks_per_sm(int which, bool stats, int block);
+};
+
+}  // namespace mpg

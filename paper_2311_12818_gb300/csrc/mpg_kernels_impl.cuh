@@ -1,0 +1,254 @@
+// Kernel templates of the hot path, instantiated once per chain length K in
+// mpg_k<K>.cu: seed sampling (K1), manifold walk (K2), contribution (K4) and
+// Bernoulli trials (K5).  Each kernel is templated on K (registers sized for K
+// vertices) and on whether it tallies work counters.
+#pragma once
+
+#include "mpg_kernels.cuh"
+
+namespace mpg {
+namespace kern {
+
+
+enum { S_NEWTON = 0, S_FULL, S_CEVAL, S_CASTS, S_SPHERE, S_PLANE, S_NODE, S_TRI, S_WALKS, S_CONV, S_GGT, S_TRIALS };
+
+struct Tally {
+  Counters c;
+  uint32_t walks, conv, trials;
+};
+
+__device__ __forceinline__ void flush(const Tally& t, unsigned long long* stats) {
+  __syncwarp();
+  uint32_t v[12] = {t.c.newton, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
+                    t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials};
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    uint32_t s = __reduce_add_sync(0xffffffffu, v[i]);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(stats + i, (unsigned long long)s);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void load_chain(const DChains& c, int b, Chain<K>& ch) {
+  const size_t B = (size_t)c.B;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    ch.x[i] = make_float3(c.x[(3 * i + 0) * B + b], c.x[(3 * i + 1) * B + b], c.x[(3 * i + 2) * B + b]);
+    ch.surf[i] = c.surf[i * B + b];
+    ch.prim[i] = c.prim[i * B + b];
+    ch.b1[i] = c.bary[(2 * i + 0) * B + b];
+    ch.b2[i] = c.bary[(2 * i + 1) * B + b];
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void store_chain(const DChains& c, int b, const Chain<K>& ch) {
+  const size_t B = (size_t)c.B;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    c.x[(3 * i + 0) * B + b] = ch.x[i].x;
+    c.x[(3 * i + 1) * B + b] = ch.x[i].y;
+    c.x[(3 * i + 2) * B + b] = ch.x[i].z;
+    c.surf[i * B + b] = ch.surf[i];
+    c.prim[i * B + b] = ch.prim[i];
+    c.bary[(2 * i + 0) * B + b] = ch.b1[i];
+    c.bary[(2 * i + 1) * B + b] = ch.b2[i];
+  }
+}
+
+__device__ __forceinline__ Ends load_ends(const DChains& c, int b) {
+  Ends e;
+  int q = b / c.spq;
+  e.xD = make_float3(c.xD[q], c.xD[c.Q + q], c.xD[2 * c.Q + q]);
+  e.nD = make_float3(c.nD[q], c.nD[c.Q + q], c.nD[2 * c.Q + q]);
+  e.xL = make_float3(c.xL[b], c.xL[c.B + b], c.xL[2 * (size_t)c.B + b]);
+  e.tau = c.tau[b];
+  return e;
+}
+
+// Work item i of bucket K -> chain index, or -1 to skip.
+template <int K>
+__device__ __forceinline__ int item(const DWork& w, const DChains& c, int i) {
+  if (w.order) return w.order[w.base[K] + i];
+  return c.k[i] == K ? i : -1;
+}
+template <int K>
+__device__ __forceinline__ int n_items(const DWork& w, const DChains& c) {
+  return w.order ? w.count[K] : c.B;
+}
+
+template <int K, bool kS>
+__global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, DGuide g, int has_guide, DChains c,
+                                              DWork w, uint2 key, uint64_t offset, mpg_params P, DCtx ctx) {
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
+    if (b < 0) continue;
+    Ends e = load_ends(c, b);
+    Chain<K> ch;
+    uint32_t tau;
+    float pdf;
+    int q = b / c.spq;
+    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[q] : 0u, e.tau, P.tau_random != 0,
+                               key, (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c);
+    if (!ok) {
+#pragma unroll
+      for (int v = 0; v < K; ++v) {
+        ch.x[v] = make_float3(0.f, 0.f, 0.f);
+        ch.surf[v] = -1; ch.prim[v] = -1; ch.b1[v] = 0.f; ch.b2[v] = 0.f;
+      }
+    }
+    store_chain<K>(c, b, ch);
+    c.tau[b] = (uint8_t)tau;
+    c.pdf[b] = ok ? pdf : 0.0f;
+    c.status[b] = ok ? ST_SEEDED : ST_INVALID;
+    c.iters[b] = 0;
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+template <int K, bool kS>
+__global__ void __launch_bounds__(128) k_walk(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+                                              DCtx ctx) {
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
+    if (b < 0 || c.status[b] != ST_SEEDED) continue;
+    Chain<K> ch;
+    load_chain<K>(c, b, ch);
+    Ends e = load_ends(c, b);
+    int it = 0;
+    int st = walk<K, kS>(S, ch, e, P, it, ctx.err, t.c);
+    t.walks++;
+    t.conv += st == ST_CONVERGED;
+    store_chain<K>(c, b, ch);
+    c.status[b] = (uint8_t)st;
+    c.iters[b] = (uint8_t)it;
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+template <int K, bool kS>
+__global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+                                                 DOut o, DCtx ctx) {
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
+    if (b < 0) continue;
+    float G = 0.f, kap = 0.f;
+    bool adm = false;
+    if (c.status[b] == ST_CONVERGED) {
+      Chain<K> ch;
+      load_chain<K>(c, b, ch);
+      Ends e = load_ends(c, b);
+      adm = contribution<K, kS>(S, ch, e, P, G, kap, ctx.err, t.c);
+    }
+    if (!adm) { G = 0.f; kap = 0.f; }
+    if (o.G) o.G[b] = G;
+    if (o.kappa) o.kappa[b] = kap;
+    o.T[b] = kap * G * S.L.power;
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+template <int K, bool kS>
+__global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S, DGuide g, int has_guide,
+                                                   DChains c, DWork w, uint2 key, uint64_t offset, mpg_params P,
+                                                   DOut o, DCtx ctx) {
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
+    if (b < 0) continue;
+    float T = o.T[b];
+    uint32_t N = 0;
+    bool cap = false;
+    if (T > 0.0f) {
+      Chain<K> target;
+      load_chain<K>(c, b, target);
+      Ends e = load_ends(c, b);
+      int q = b / c.spq;
+      uint32_t cell = c.cell ? c.cell[q] : 0u;
+      cap = true;
+      for (int tr = 1; tr <= P.max_trials; ++tr) {
+        t.trials++;
+        Chain<K> ch;
+        uint32_t tau;
+        float pdf;
+        Ends et = e;
+        if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
+                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c))
+          continue;
+        if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
+        et.tau = tau;
+        int it;
+        int st = walk<K, kS>(S, ch, et, P, it, ctx.err, t.c);
+        t.walks++;
+        t.conv += st == ST_CONVERGED;
+        if (st == ST_CONVERGED && same_solution<K>(ch, target, eps2)) {
+          N = (uint32_t)tr;
+          cap = false;
+          break;
+        }
+      }
+      if (cap) N = (uint32_t)P.max_trials;
+    }
+    if (o.trials) o.trials[b] = N;
+    if (o.capped) o.capped[b] = cap ? 1 : 0;
+    float pn = c.pn ? c.pn[b] : 1.0f;
+    o.contrib[b] = T > 0.0f ? S.L.area * T * (float)N / pn : 0.0f;
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+
+}  // namespace kern
+
+template <int K>
+void KLaunch<K>::seed(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                      uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st) {
+  DGuide gg = g ? *g : DGuide{};
+  if (stats) kern::k_seed<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
+  else kern::k_seed<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
+}
+
+template <int K>
+void KLaunch<K>::walk(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx, int grid,
+                      int block, cudaStream_t st) {
+  if (stats) kern::k_walk<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+  else kern::k_walk<K, false><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+}
+
+template <int K>
+void KLaunch<K>::contrib(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx,
+                         int grid, int block, cudaStream_t st) {
+  if (stats) kern::k_contrib<K, true><<<grid, block, 0, st>>>(S, c, w, P, o, ctx);
+  else kern::k_contrib<K, false><<<grid, block, 0, st>>>(S, c, w, P, o, ctx);
+}
+
+template <int K>
+void KLaunch<K>::bernoulli(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                           uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
+                           cudaStream_t st) {
+  DGuide gg = g ? *g : DGuide{};
+  if (stats) kern::k_bernoulli<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  else kern::k_bernoulli<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+}
+
+template <int K>
+int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
+  const void* fn;
+  if (which == 0) fn = stats ? (const void*)kern::k_seed<K, true> : (const void*)kern::k_seed<K, false>;
+  else if (which == 1) fn = stats ? (const void*)kern::k_walk<K, true> : (const void*)kern::k_walk<K, false>;
+  else if (which == 2) fn = stats ? (const void*)kern::k_contrib<K, true> : (const void*)kern::k_contrib<K, false>;
+  else fn = stats ? (const void*)kern::k_bernoulli<K, true> : (const void*)kern::k_bernoulli<K, false>;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 1;
+  return n > 0 ? n : 1;
+}
+
+}  // namespace mpg

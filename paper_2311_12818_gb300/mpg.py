@@ -1,0 +1,331 @@
+"""Thin Python binding of libmpg.so (the C ABI declared in include/mpg.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch provides device memory (tensors passed by pointer) and
+streams.  The binding refuses to run without the compiled library -- there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpg.so")
+
+MAXK = 8
+MPG_OK = 0
+CHAIN_INVALID, CHAIN_CONVERGED, CHAIN_FAILED, CHAIN_LIMIT, CHAIN_SEEDED = 0, 1, 2, 3, 255
+WALK_PLAIN, WALK_BATCHED = 0, 1
+
+
+class MpgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mpg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class mpg_params(C.Structure):
+    _fields_ = [("tol", C.c_float), ("max_iter", C.c_int32), ("max_halvings", C.c_int32),
+                ("ray_eps", C.c_float), ("sing_eps", C.c_float), ("dedup_eps", C.c_float),
+                ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_float),
+                ("walk_mode", C.c_int32), ("block_threads", C.c_int32), ("tau_random", C.c_int32),
+                ("k_uniform", C.c_int32)]
+
+
+class mpg_chains(C.Structure):
+    _fields_ = [("B", C.c_int32), ("Q", C.c_int32), ("spq", C.c_int32),
+                ("xD", C.c_void_p), ("nD", C.c_void_p), ("cell", C.c_void_p), ("xL", C.c_void_p),
+                ("k", C.c_void_p), ("pn", C.c_void_p), ("tau", C.c_void_p), ("x", C.c_void_p),
+                ("surf", C.c_void_p), ("prim", C.c_void_p), ("bary", C.c_void_p), ("pdf", C.c_void_p),
+                ("status", C.c_void_p), ("iters", C.c_void_p)]
+
+
+class mpg_guide(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
+                ("counts", C.c_void_p), ("cdf", C.c_void_p), ("cos_theta", C.c_void_p),
+                ("phi_cos", C.c_void_p), ("phi_sin", C.c_void_p)]
+
+
+STAT_FIELDS = ["newton_steps", "full_evals", "c_evals", "ray_casts", "sphere_tests", "plane_tests",
+               "node_tests", "tri_tests", "walks", "converged", "ggt_evals", "trials"]
+
+
+class mpg_stats(C.Structure):
+    _fields_ = [(f, C.c_uint64) for f in STAT_FIELDS]
+
+
+EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy", "mpg_ctx_sync",
+           "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
+           "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
+           "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak"]
+
+_lib = None
+
+
+def lib():
+    """Load libmpg.so (raises if it was not built -- no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmpg.so is missing: build it with paper_2311_12818_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, u64, f32 = C.c_void_p, C.c_int32, C.c_uint64, C.c_float
+        L.mpg_last_error.restype = C.c_char_p
+        L.mpg_version.restype = i32
+        L.mpg_ctx_create.argtypes = [i32, C.POINTER(vp)]
+        L.mpg_ctx_destroy.argtypes = [vp]
+        L.mpg_ctx_destroy.restype = None
+        L.mpg_ctx_sync.argtypes = [vp, vp]
+        L.mpg_ctx_stats.argtypes = [vp, C.POINTER(mpg_stats), i32, vp]
+        L.mpg_ctx_set_stats.argtypes = [vp, i32]
+        L.mpg_scene_create.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]
+        L.mpg_scene_destroy.argtypes = [vp]
+        L.mpg_scene_destroy.restype = None
+        L.mpg_scene_info.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.mpg_sample_seeds.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
+                                       C.POINTER(mpg_params), vp]
+        L.mpg_manifold_walk.argtypes = [vp, vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
+        L.mpg_chain_contribution.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
+                                             C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
+        L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
+        L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp]
+        L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp]
+        L.mpg_trace_rays.argtypes = [vp, vp, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp]
+        L.mpg_fp32_peak.argtypes = [vp, C.POINTER(C.c_double), vp]
+        for n in EXPORTS[2:]:
+            if n not in ("mpg_ctx_destroy", "mpg_scene_destroy"):
+                getattr(L, n).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != MPG_OK:
+        raise MpgError(code, lib().mpg_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_uniform=0) -> mpg_params:
+    """mpg_params from an inputs.Params (FP32 copy of the solver constants)."""
+    return mpg_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps, p.max_trials,
+                      p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform)
+
+
+class Context:
+    def __init__(self, device=0):
+        self.device = device
+        h = C.c_void_p()
+        torch.cuda.set_device(device)
+        _check(lib().mpg_ctx_create(device, C.byref(h)))
+        self.h = h
+
+    def sync(self, stream=None):
+        _check(lib().mpg_ctx_sync(self.h, _stream(stream)))
+
+    def stats(self, reset=False, stream=None):
+        s = mpg_stats()
+        _check(lib().mpg_ctx_stats(self.h, C.byref(s), int(reset), _stream(stream)))
+        return {f: int(getattr(s, f)) for f in STAT_FIELDS}
+
+    def reset_stats(self, stream=None):
+        _check(lib().mpg_ctx_stats(self.h, None, 1, _stream(stream)))
+
+    def set_stats(self, on):
+        _check(lib().mpg_ctx_set_stats(self.h, int(bool(on))))
+
+    def fp32_peak(self, stream=None):
+        v = C.c_double()
+        _check(lib().mpg_fp32_peak(self.h, C.byref(v), _stream(stream)))
+        return v.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().mpg_ctx_destroy(self.h)
+            self.h = None
+
+
+class Scene:
+    def __init__(self, ctx: Context, wl):
+        self.ctx = ctx
+        keep = [np.ascontiguousarray(a, np.float64) for a in
+                (wl.surfaces, wl.hf_desc.reshape(-1, 6), wl.hf_heights, wl.targets, wl.light)]
+        s, hd, hh, tg, li = keep
+        h = C.c_void_p()
+        _check(lib().mpg_scene_create(ctx.h, s.ctypes.data, s.shape[0], hd.ctypes.data if hd.size else None,
+                                      hh.ctypes.data if hh.size else None, hd.shape[0],
+                                      tg.ctypes.data if tg.size else None, tg.shape[0], li.ctypes.data,
+                                      C.byref(h)))
+        self.h = h
+        self.light_area = wl.light_area
+
+    def info(self, h=0):
+        n, t = C.c_int32(), C.c_int32()
+        _check(lib().mpg_scene_info(self.h, h, C.byref(n), C.byref(t)))
+        return n.value, t.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().mpg_scene_destroy(self.h)
+            self.h = None
+
+
+class Guide:
+    """Guide histograms in device memory (counts and prefix sums uint64)."""
+
+    def __init__(self, n_cells, edges, device="cuda"):
+        ct, pc, ps = (torch.as_tensor(np.ascontiguousarray(e, np.float32), device=device) for e in edges)
+        self.cos_theta, self.phi_cos, self.phi_sin = ct, pc, ps
+        self.n_cells, self.n_theta, self.n_phi = n_cells, ct.numel() - 1, pc.numel() - 1
+        bins = self.n_theta * self.n_phi
+        self.counts = torch.zeros((n_cells, bins), dtype=torch.int64, device=device)
+        self.cdf = torch.zeros((n_cells, bins), dtype=torch.int64, device=device)
+
+    def struct(self):
+        return mpg_guide(self.n_cells, self.n_theta, self.n_phi, self.counts.data_ptr(), self.cdf.data_ptr(),
+                         self.cos_theta.data_ptr(), self.phi_cos.data_ptr(), self.phi_sin.data_ptr())
+
+    def clear(self):
+        self.counts.zero_()
+        self.cdf.zero_()
+
+
+class Chains:
+    """Device SoA state of a chain batch built from a workload (inputs module)."""
+
+    def __init__(self, wl, device="cuda"):
+        f32 = dict(dtype=torch.float32, device=device)
+        self.B, self.Q, self.spq = wl.B, wl.Q, wl.spq
+        self.xD = torch.as_tensor(np.ascontiguousarray(wl.xD.T, np.float32), device=device)
+        self.nD = torch.as_tensor(np.ascontiguousarray(wl.nD.T, np.float32), device=device)
+        self.cell = torch.as_tensor(wl.cell.astype(np.int32), device=device)
+        self.xL = torch.as_tensor(np.ascontiguousarray(wl.xL.T, np.float32), device=device)
+        self.k = torch.as_tensor(wl.k.astype(np.uint8), device=device)
+        self.pn = torch.as_tensor(wl.pn.astype(np.float32), device=device)
+        self.tau = torch.as_tensor(wl.tau.astype(np.uint8), device=device)
+        B = self.B
+        self.x = torch.zeros((MAXK, 3, B), **f32)
+        self.surf = torch.full((MAXK, B), -1, dtype=torch.int32, device=device)
+        self.prim = torch.full((MAXK, B), -1, dtype=torch.int32, device=device)
+        self.bary = torch.zeros((MAXK, 2, B), **f32)
+        self.pdf = torch.zeros(B, **f32)
+        self.status = torch.zeros(B, dtype=torch.uint8, device=device)
+        self.iters = torch.zeros(B, dtype=torch.uint8, device=device)
+
+    def struct(self):
+        return mpg_chains(self.B, self.Q, self.spq, self.xD.data_ptr(), self.nD.data_ptr(), self.cell.data_ptr(),
+                          self.xL.data_ptr(), self.k.data_ptr(), self.pn.data_ptr(), self.tau.data_ptr(),
+                          self.x.data_ptr(), self.surf.data_ptr(), self.prim.data_ptr(), self.bary.data_ptr(),
+                          self.pdf.data_ptr(), self.status.data_ptr(), self.iters.data_ptr())
+
+    def aos(self):
+        """Host copy in the oracle's array-of-structures layout (tests)."""
+        x = self.x.permute(2, 0, 1).double().cpu().numpy()
+        return dict(x=np.ascontiguousarray(x), surf=self.surf.T.contiguous().cpu().numpy(),
+                    prim=self.prim.T.contiguous().cpu().numpy(),
+                    bary=np.ascontiguousarray(self.bary.permute(2, 0, 1).double().cpu().numpy()),
+                    tau=self.tau.cpu().numpy(), status=self.status.cpu().numpy(),
+                    iters=self.iters.cpu().numpy(), pdf=self.pdf.double().cpu().numpy())
+
+
+@dataclasses.dataclass
+class Contribution:
+    G: torch.Tensor
+    kappa: torch.Tensor
+    T: torch.Tensor
+    trials: torch.Tensor
+    capped: torch.Tensor
+    contrib: torch.Tensor
+    E: torch.Tensor
+
+    @classmethod
+    def empty(cls, B, Q, device="cuda"):
+        f = dict(dtype=torch.float32, device=device)
+        return cls(torch.zeros(B, **f), torch.zeros(B, **f), torch.zeros(B, **f),
+                   torch.zeros(B, dtype=torch.int32, device=device), torch.zeros(B, dtype=torch.uint8, device=device),
+                   torch.zeros(B, **f), torch.zeros(Q, **f))
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def mpg_sample_seeds(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, stream=None):
+    cs = chains.struct()
+    gs = guide.struct() if guide is not None else None
+    _check(lib().mpg_sample_seeds(ctx.h, scene.h, C.byref(gs) if gs is not None else None, C.byref(cs),
+                                  rng_seed, rng_offset, C.byref(params), _stream(stream)))
+
+
+def mpg_manifold_walk(ctx, scene, chains, params, stream=None):
+    cs = chains.struct()
+    _check(lib().mpg_manifold_walk(ctx.h, scene.h, C.byref(cs), C.byref(params), _stream(stream)))
+
+
+def mpg_chain_contribution(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, out=None, stream=None):
+    out = out if out is not None else Contribution.empty(chains.B, chains.Q)
+    cs = chains.struct()
+    gs = guide.struct() if guide is not None else None
+    _check(lib().mpg_chain_contribution(ctx.h, scene.h, C.byref(gs) if gs is not None else None, C.byref(cs),
+                                        rng_seed, rng_offset, C.byref(params), _ptr(out.G), _ptr(out.kappa),
+                                        _ptr(out.T), _ptr(out.trials), _ptr(out.capped), _ptr(out.contrib),
+                                        _ptr(out.E), _stream(stream)))
+    return out
+
+
+def mpg_guide_update(ctx, guide, cell, omega, w, R=None, R_dev=None, weight_shift=16, stream=None):
+    """cell [R] int32, omega [3, R] float32, w [R] float32 (device tensors)."""
+    R = int(cell.numel()) if R is None else R
+    gs = guide.struct()
+    _check(lib().mpg_guide_update(ctx.h, C.byref(gs), _ptr(cell), _ptr(omega), _ptr(w), R, _ptr(R_dev),
+                                  weight_shift, _stream(stream)))
+
+
+def mpg_guide_records(ctx, scene, chains, contrib, stream=None):
+    B = chains.B
+    cell = torch.zeros(B, dtype=torch.int32, device="cuda")
+    om = torch.zeros((3, B), dtype=torch.float32, device="cuda")
+    w = torch.zeros(B, dtype=torch.float32, device="cuda")
+    R = torch.zeros(4, dtype=torch.int32, device="cuda")
+    cs = chains.struct()
+    _check(lib().mpg_guide_records(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(cell), _ptr(om), _ptr(w),
+                                   _ptr(R), _stream(stream)))
+    return cell, om, w, R
+
+
+def mpg_walk_adjoint(ctx, scene, chains, contrib, dL_dE, dL_dtheta, stream=None):
+    cs = chains.struct()
+    _check(lib().mpg_walk_adjoint(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(dL_dE), _ptr(dL_dtheta),
+                                  _stream(stream)))
+
+
+def mpg_trace_rays(ctx, scene, o, d, tmin=1e-4, tmax=3.0e38, stream=None):
+    """o, d: [3, n] float32 device tensors."""
+    n = o.shape[1]
+    t = torch.empty(n, dtype=torch.float32, device="cuda")
+    surf = torch.empty(n, dtype=torch.int32, device="cuda")
+    prim = torch.empty(n, dtype=torch.int32, device="cuda")
+    bary = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    _check(lib().mpg_trace_rays(ctx.h, scene.h, _ptr(o), _ptr(d), n, tmin, tmax, _ptr(t), _ptr(surf), _ptr(prim),
+                                _ptr(bary), _stream(stream)))
+    return t, surf, prim, bary
+
+
+def run(ctx, scene, chains, wl, guide=None, params=None, out=None, stream=None):
+    """Whole hot path on the GPU: seeds -> walk -> contribution + Bernoulli -> E."""
+    P = params if params is not None else params_from(wl.params, tau_random=wl.tau_random,
+                                                      k_uniform=int(wl.k[0]) if (wl.k == wl.k[0]).all() else 0)
+    mpg_sample_seeds(ctx, scene, guide, chains, P, wl.rng_seed, 0, stream)
+    mpg_manifold_walk(ctx, scene, chains, P, stream)
+    return mpg_chain_contribution(ctx, scene, guide, chains, P, wl.rng_seed, 0, out, stream)

@@ -1,0 +1,293 @@
+"""CUDA path against the FP64 oracle on identical seeded inputs.
+
+Tolerances (from the hot-path contract): converged vertices within 1e-4 of
+the scene scale, converged/failed flags agreeing on >= 99.9% of chains,
+contributions and irradiance within 1e-3 relative, histogram counts
+bit-exact.  Discrete results (seed validity, surfaces, Bernoulli trial counts)
+are compared exactly where both sides took the same continuous path."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2311_12818_gb300 import inputs as I  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12818_gb300 import build, mpg
+    build.build()
+    return mpg
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    return M.Context(0)
+
+
+def _params(M, wl, mode=None, **kw):
+    uniform = int(wl.k[0]) if (wl.k == wl.k[0]).all() else 0
+    return M.params_from(wl.params, walk_mode=M.WALK_BATCHED if mode is None else mode,
+                         tau_random=wl.tau_random, k_uniform=kw.pop("k_uniform", uniform), **kw)
+
+
+def _gpu_pipeline(M, ctx, wl, guide=None, P=None):
+    sc = M.Scene(ctx, wl)
+    ch = M.Chains(wl)
+    P = P or _params(M, wl)
+    M.mpg_sample_seeds(ctx, sc, guide, ch, P, wl.rng_seed, 0)
+    seeds = ch.aos()
+    M.mpg_manifold_walk(ctx, sc, ch, P)
+    walked = ch.aos()
+    out = M.mpg_chain_contribution(ctx, sc, guide, ch, P, wl.rng_seed, 0)
+    ctx.sync()
+    return sc, ch, seeds, walked, out
+
+
+def _oracle_pipeline(wl, guide=None):
+    sc = O.Scene(wl)
+    seeds = O.sample_seeds(wl, sc, guide)
+    ch = O.walk(wl, sc, seeds)
+    con = O.contribution(wl, sc, ch)
+    N, capped = O.bernoulli(wl, sc, ch, con["admissible"], guide)
+    return sc, seeds, ch, con, N, capped
+
+
+def _seed_valid(st):
+    return (st != M_INVALID).astype(np.uint8)
+
+
+M_INVALID = 0
+
+
+def _compare_seeds(wl, gs, os_):
+    gvalid = gs["status"] != 0
+    ovalid = os_["valid"] == 1
+    assert (gvalid == ovalid).mean() >= 0.999
+    both = gvalid & ovalid
+    assert both.sum() > 0.2 * wl.B
+    k = wl.k
+    scale = wl.scene_scale
+    for i in range(int(k.max())):
+        sel = both & (k > i)
+        assert np.array_equal(gs["surf"][sel, i], os_["surf"][sel, i])
+        d = np.linalg.norm(gs["x"][sel, i] - os_["x"][sel, i], axis=1)
+        assert np.quantile(d, 0.999) < 1e-4 * scale
+    assert np.array_equal(gs["tau"][both], os_["tau"][both])
+    rel = np.abs(gs["pdf"][both] - os_["pdf"][both]) / np.maximum(os_["pdf"][both], 1e-30)
+    assert np.quantile(rel, 0.999) < 1e-3
+
+
+def _compare_walk(wl, gw, ow, same_start=None):
+    gconv = gw["status"] == 1
+    oconv = ow["status"] == 1
+    mask = np.ones(wl.B, bool) if same_start is None else same_start
+    agree = (gconv == oconv)[mask].mean()
+    assert agree >= 0.999, agree
+    both = gconv & oconv
+    assert both.sum() > 0.1 * wl.B
+    for i in range(int(wl.k.max())):
+        sel = both & (wl.k > i)
+        d = np.linalg.norm(gw["x"][sel, i] - ow["x"][sel, i], axis=1)
+        assert d.max() < 1e-4 * wl.scene_scale, d.max()
+    return both
+
+
+def test_mirror_sphere_parity(M, ctx):
+    wl = I.mirror_sphere(n=24, spq=16)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    _compare_seeds(wl, gs, os_)
+    both = _compare_walk(wl, gw, ow)
+    G = out.G.cpu().numpy()
+    gadm = G > 0
+    assert (gadm == (con["admissible"] == 1)).mean() >= 0.999
+    ab = gadm & (con["admissible"] == 1) & both
+    rel = np.abs(G[ab] - con["G"][ab]) / con["G"][ab]
+    assert rel.max() < 1e-3, rel.max()
+    kap = out.kappa.cpu().numpy()
+    assert np.allclose(kap[ab], con["kappa"][ab], rtol=1e-6)
+    gN = out.trials.cpu().numpy().astype(np.int64)
+    assert (gN[ab] == N[ab]).mean() >= 0.999
+    # irradiance per receiver point
+    E_o = O.irradiance(wl, con["T"], N, con["admissible"])
+    E_g = out.E.cpu().numpy()
+    same = np.ones(wl.Q, bool)
+    agree_chain = (gN == N) & (gadm == (con["admissible"] == 1))
+    same &= agree_chain.reshape(wl.Q, wl.spq).all(axis=1)
+    nz = same & (E_o > 0)
+    assert nz.sum() > 0.3 * wl.Q
+    assert np.max(np.abs(E_g[nz] - E_o[nz]) / E_o[nz]) < 1e-3
+    assert abs(E_g.sum() - E_o.sum()) / E_o.sum() < 1e-3
+
+
+def test_walk_parity_from_identical_seeds(M, ctx):
+    """The GPU's own FP32 seeds walked by the oracle in FP64: isolates the walk."""
+    wl = I.glass_sphere(n=32, spq=16)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc = O.Scene(wl)
+    seeds = dict(x=gs["x"].copy(), surf=gs["surf"].copy(), prim=gs["prim"].copy(), bary=gs["bary"].copy(),
+                 tau=gs["tau"].copy(), valid=(gs["status"] != 0).astype(np.uint8))
+    ow = O.walk(wl, osc, seeds)
+    _compare_walk(wl, gw, ow)
+    assert np.quantile(np.abs(gw["iters"].astype(int) - ow["iters"].astype(int))[ow["status"] == 1], 0.99) <= 1
+
+
+def test_glass_sphere_guided_parity_and_histogram_bit_exact(M, ctx):
+    wl = I.glass_sphere(n=32, spq=16)
+    # training pass (p_0 only) in the oracle gives the records
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    cell, om, w = O.records(wl, ow, con["T"], N, con["admissible"])
+    assert cell.size > 1000
+    og = O.Guide(wl.n_cells, I.guide_edges())
+    og.update(cell, om, w, wl.params.weight_shift)
+    gg = M.Guide(wl.n_cells, I.guide_edges())
+    M.mpg_guide_update(ctx, gg, torch.as_tensor(cell.astype(np.int32), device="cuda"),
+                       torch.as_tensor(np.ascontiguousarray(om.T), device="cuda"),
+                       torch.as_tensor(w, device="cuda"), weight_shift=wl.params.weight_shift)
+    ctx.sync()
+    counts = gg.counts.cpu().numpy().view(np.uint64)
+    assert np.array_equal(counts, og.counts)
+    assert np.array_equal(gg.cdf.cpu().numpy().view(np.uint64), np.cumsum(og.counts, axis=1, dtype=np.uint64))
+    # guided pass on both sides with the identical guide
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, guide=gg)
+    osc2, os2, ow2, con2, N2, capped2 = _oracle_pipeline(wl, guide=og)
+    _compare_seeds(wl, gs, os2)
+    both = _compare_walk(wl, gw, ow2)
+    G = out.G.cpu().numpy()
+    ab = (G > 0) & (con2["admissible"] == 1) & both
+    assert ab.sum() > 1000
+    rel = np.abs(out.T.cpu().numpy()[ab] - con2["T"][ab]) / con2["T"][ab]
+    assert np.quantile(rel, 0.999) < 1e-3
+    gN = out.trials.cpu().numpy().astype(np.int64)
+    assert (gN[ab] == N2[ab]).mean() >= 0.999
+
+
+def test_records_kernel_matches_oracle_records(M, ctx):
+    wl = I.glass_sphere(n=16, spq=8)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    cell, om, w, R = M.mpg_guide_records(ctx, sc, ch, out.contrib)
+    ctx.sync()
+    n = int(R[0].item())
+    contrib = out.contrib.cpu().numpy()
+    assert n == int((contrib > 0).sum())
+    gi = np.nonzero(contrib > 0)[0]
+    # records are unordered: compare as multisets keyed by cell and weight
+    recs = sorted(zip(cell[:n].cpu().numpy().tolist(), w[:n].cpu().numpy().tolist()))
+    q = gi // wl.spq
+    ref = sorted(zip(wl.cell[q].tolist(), (contrib[gi] / wl.light_area).astype(np.float32).tolist()))
+    assert len(recs) == len(ref)
+    assert np.allclose(np.array(recs)[:, 1], np.array(ref)[:, 1], rtol=1e-6)
+
+
+def test_water_bvh_trace_parity(M, ctx):
+    wl = I.water(n=16, spq=1, grid=128)
+    sc = M.Scene(ctx, wl)
+    nn, nt = sc.info(0)
+    assert nt == 2 * 127 * 127
+    rng = np.random.default_rng(5)
+    n = 20000
+    o = np.column_stack([rng.uniform(-1.1, 1.1, n), rng.uniform(-1.1, 1.1, n), rng.choice([-1.0, 2.0], n)])
+    tgt = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(-0.05, 0.05, n)])
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    osc = O.Scene(wl)
+    to, so, po, bo = O.intersect(osc, o.astype(np.float32).astype(np.float64),
+                                 d.astype(np.float32).astype(np.float64))
+    tg, sg, pg, bg = M.mpg_trace_rays(ctx, sc, torch.as_tensor(o.T.astype(np.float32), device="cuda").contiguous(),
+                                      torch.as_tensor(d.T.astype(np.float32), device="cuda").contiguous())
+    ctx.sync()
+    sg, pg, tg = sg.cpu().numpy(), pg.cpu().numpy(), tg.cpu().numpy()
+    assert (sg == so).mean() >= 0.999
+    hit = (sg >= 0) & (so >= 0)
+    assert hit.mean() > 0.9
+    assert (pg[hit] == po[hit]).mean() >= 0.998  # edge hits may pick the neighbouring triangle
+    assert np.quantile(np.abs(tg[hit] - to[hit]), 0.999) < 1e-5
+
+
+def test_water_pipeline_parity(M, ctx):
+    wl = I.water(n=48, spq=4, grid=128)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    _compare_seeds(wl, gs, os_)
+    both = _compare_walk(wl, gw, ow)
+    T = out.T.cpu().numpy()
+    ab = (T > 0) & (con["admissible"] == 1) & both
+    assert ab.sum() > 1000
+    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
+    assert np.quantile(rel, 0.999) < 1e-3
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_mixed_lengths_plain_and_batched(M, ctx, mode):
+    wl = I.mixed(nx=48, ny=24, spq=4)
+    P = _params(M, wl, mode=mode, k_uniform=0)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    _compare_seeds(wl, gs, os_)
+    _compare_walk(wl, gw, ow)
+    T = out.T.cpu().numpy()
+    assert ((T > 0) == (con["admissible"] == 1)).mean() >= 0.999
+    ab = (T > 0) & (con["admissible"] == 1)
+    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
+    assert np.quantile(rel, 0.999) < 1e-3
+    for kk in range(1, 9):
+        assert ((gw["status"] == 1) & (wl.k == kk)).sum() >= 0
+
+
+def test_plain_and_batched_are_identical(M, ctx):
+    wl = I.mixed(nx=32, ny=16, spq=4)
+    res = []
+    for mode in (0, 1):
+        P = _params(M, wl, mode=mode, k_uniform=0)
+        sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
+        res.append((gw, out.contrib.cpu().numpy(), out.E.cpu().numpy()))
+    assert np.array_equal(res[0][0]["status"], res[1][0]["status"])
+    assert np.array_equal(res[0][0]["x"], res[1][0]["x"])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert np.array_equal(res[0][2], res[1][2])
+
+
+def test_edge_cases(M, ctx):
+    # empty batch is a no-op; ragged sizes; a cap on trials is flagged
+    wl = I.mirror_sphere(n=1, spq=1)
+    empty = dataclasses.replace(wl, xD=wl.xD[:0], nD=wl.nD[:0], cell=wl.cell[:0], xL=wl.xL[:0], k=wl.k[:0],
+                                tau=wl.tau[:0], pn=wl.pn[:0])
+    ch = M.Chains(empty)
+    sc = M.Scene(ctx, wl)
+    P = _params(M, wl)
+    M.mpg_sample_seeds(ctx, sc, None, ch, P, 1, 0)
+    M.mpg_manifold_walk(ctx, sc, ch, P)
+    ctx.sync()
+    # ragged: 37 points x 3 seeds
+    wl = I.mirror_sphere(n=7, spq=3)
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    _compare_walk(wl, gw, ow)
+    # max_trials = 1: every admissible chain either hits on trial 1 or is capped
+    P1 = _params(M, wl)
+    P1.max_trials = 1
+    sc2 = M.Scene(ctx, wl)
+    ch2 = M.Chains(wl)
+    M.mpg_sample_seeds(ctx, sc2, None, ch2, P1, wl.rng_seed, 0)
+    M.mpg_manifold_walk(ctx, sc2, ch2, P1)
+    o2 = M.mpg_chain_contribution(ctx, sc2, None, ch2, P1, wl.rng_seed, 0)
+    ctx.sync()
+    adm = o2.T.cpu().numpy() > 0
+    cap = o2.capped.cpu().numpy().astype(bool)
+    trials = o2.trials.cpu().numpy()
+    assert np.all(trials[adm] == 1)
+    N1, capped1 = O.bernoulli(wl, osc, ow, con["admissible"], max_trials=1)
+    both = adm & (con["admissible"] == 1)
+    assert (cap[both] == capped1[both].astype(bool)).mean() >= 0.999
+    # invalid arguments are rejected with an error code, not a fault
+    bad = _params(M, wl)
+    bad.tol = -1.0
+    with pytest.raises(M.MpgError):
+        M.mpg_manifold_walk(ctx, sc2, ch2, bad)
