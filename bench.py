@@ -1,0 +1,374 @@
+#!/usr/bin/env python
+"""Benchmark of the manifold-walk hot path on GB300.
+
+A step is one pass of the whole hot path over one batch: guided seed chains
+(Eq. deduction with the alpha-mixture of Sec. 5.5), Newton manifold walks,
+contributions T = kappa G L_o with Bernoulli-trial reciprocal probabilities
+(Sec. 5.7) and the irradiance estimate (Eq. ThroughputMC), then the guide
+records and histogram update (Eq. eq_weight).  The workload is the refractive
+caustic through a glass sphere (radius 1, IOR 1.5, k = 2, 0.2 x 0.2 area light
+at z = 4, 256 x 256 receiver points x 16 seeds = 1,048,576 chains, guide of
+16 x 16 cells x 64 x 64 bins trained by one untimed p_0 pass).
+
+Metric: converged manifold walks per second (every Newton walk that reached
+max|C| < tol: the first walks and the Bernoulli trial walks).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "converged manifold walks/sec and FP32 % of peak at 1 GB300, batched vs plain, at oracle tol"
+UNIT = "walks/s"
+WORKLOAD = "glass_sphere_k2_guided: r=1 IOR 1.5, 256x256 points x 16 seeds = 1,048,576 chains, 16x16x64x64 guide"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="receiver points per side")
+    ap.add_argument("--spq", type=int, default=16)
+    ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
+    ap.add_argument("--no-flush", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), f[5:9]))
+                except ValueError:
+                    pass
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def unit_flops():
+    with open(os.path.join(ROOT, "paper_2311_12818_gb300", "unit_flops.json")) as f:
+        return json.load(f)["flops"]
+
+
+def algorithmic_flops(st, F, surface="sphere"):
+    """Flops of the work a kernel family did, from its counters and the
+    per-primitive operation counts of the counted-scalar oracle."""
+    frame = F["frame_" + surface]
+    normal = F["normal_" + surface]
+    return (st["full_evals"] * (frame + F["vertex_blocks"]) + st["c_evals"] * (normal + F["vertex_constraint"])
+            + st["newton_steps"] * F["thomas_first_row"] + (st["thomas_rows"] - st["newton_steps"]) * F["thomas_row"]
+            + st["ggt_rows"] * F["ggt_row"] + st["sphere_tests"] * F["ray_sphere"]
+            + st["plane_tests"] * F["ray_rect"] + st["tri_tests"] * F["ray_triangle"] + st["node_tests"] * F["ray_box"])
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    wl = I.glass_sphere(n=args.n, spq=args.spq)
+    B, Q = wl.B, wl.Q
+    off = rank * B  # each rank draws its own seeds (weak scaling)
+    ctx = mpg.Context(local)
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    mode = mpg.WALK_BATCHED if args.mode == "batched" else mpg.WALK_PLAIN
+    P = mpg.params_from(wl.params, walk_mode=mode, k_uniform=2)
+    guide = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+    nxt = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+    out = mpg.Contribution.empty(B, Q, device=dev)
+    rec = (torch.zeros(B, dtype=torch.int32, device=dev), torch.zeros((3, B), dtype=torch.float32, device=dev),
+           torch.zeros(B, dtype=torch.float32, device=dev), torch.zeros(4, dtype=torch.int32, device=dev))
+
+    # untimed fixture: one p_0 training pass builds the guide
+    mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, off + (1 << 40))
+    mpg.mpg_manifold_walk(ctx, sc, ch, P)
+    mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, off + (1 << 40), out=out)
+    mpg.mpg_guide_records(ctx, sc, ch, out.contrib, out=rec)
+    mpg.mpg_guide_update(ctx, guide, rec[0], rec[1], rec[2], R=B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
+    ctx.sync()
+
+    def step(i):
+        o = off + i * B * world
+        mpg.mpg_sample_seeds(ctx, sc, guide, ch, P, wl.rng_seed, o)
+        mpg.mpg_manifold_walk(ctx, sc, ch, P)
+        mpg.mpg_chain_contribution(ctx, sc, guide, ch, P, wl.rng_seed, o, out=out)
+        mpg.mpg_guide_records(ctx, sc, ch, out.contrib, out=rec)
+        nxt.counts.zero_()
+        mpg.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=B, R_dev=rec[3],
+                             weight_shift=wl.params.weight_shift)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+    for i in range(args.warmup):
+        step(1000 + i)
+    ctx.sync()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-timed steps (inputs resident in HBM)
+    ctx.reset_stats()
+    ctx.profile(reset=True)
+    ctx.set_profile(True)
+    n_launch0 = ctx.launches()
+    clocks = Clocks(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        ev[i][0].record(stream)
+        step(i)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ctx.set_profile(False)
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launches = ctx.launches() - n_launch0
+    fam = {}
+    F = unit_flops()
+    for k, name in enumerate(mpg.KERNEL_NAMES):
+        ms, n = ctx.profile(k)
+        st = ctx.stats(k)
+        fam[name] = dict(ms=ms, launches=n, stats=st, flops=algorithmic_flops(st, F))
+    total = ctx.stats()
+    conv = total["converged"]
+    t_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_ms, float(conv)], dtype=torch.float64, device=dev)
+        t_max = tt[:1].clone()
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        c_sum = tt[1:].clone()
+        dist.all_reduce(c_sum, op=dist.ReduceOp.SUM)
+        t_ms, conv_all = float(t_max.item()), float(c_sum.item())
+    else:
+        conv_all = float(conv)
+    value = conv_all / (t_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
+    host_in = [(ch.xD, pin(np.ascontiguousarray(wl.xD.T, np.float32))),
+               (ch.nD, pin(np.ascontiguousarray(wl.nD.T, np.float32))),
+               (ch.cell, pin(wl.cell.astype(np.int32))), (ch.xL, pin(np.ascontiguousarray(wl.xL.T, np.float32))),
+               (ch.k, pin(wl.k.astype(np.uint8))), (ch.tau, pin(wl.tau.astype(np.uint8))),
+               (ch.pn, pin(wl.pn.astype(np.float32)))]
+    h2d = sum(h.numel() * h.element_size() for _, h in host_in)
+    E_host = torch.empty(Q, dtype=torch.float32).pin_memory()
+    n_host = torch.empty(4, dtype=torch.int32).pin_memory()
+    d2h = E_host.numel() * 4 + n_host.numel() * 4
+    e2e_conv = 0
+    e2e_ms = 0.0
+    for i in range(max(1, args.steps // 2)):
+        if not args.no_flush:
+            flush.zero_()
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for d, h in host_in:
+            d.copy_(h, non_blocking=True)
+        step(500 + i)
+        E_host.copy_(out.E, non_blocking=True)
+        n_host.copy_(rec[3], non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+        e2e_conv += ctx.stats()["converged"]
+    e2e_value = e2e_conv / (e2e_ms * 1e-3) if world == 1 else None
+
+    # ---- roofline of the dominant kernel family (FP32 ALU bound)
+    dom = max((n for n in fam if n != "aux"), key=lambda n: fam[n]["ms"])
+    d = fam[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) if d["ms"] > 0 else 0.0
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_nominal = props.multi_processor_count * 128 * 2 * sm_max * 1e6
+    peak_ffma = ctx.fp32_peak()
+    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved / 1e12, "peak": peak_nominal / 1e12,
+                "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": None,
+                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (props.multi_processor_count, sm_max),
+                "peak_ffma_measured": peak_ffma / 1e12, "frac_of_ffma_measured": achieved / peak_ffma if peak_ffma else None,
+                "algorithmic_flops_per_launch": d["flops"] / max(1, d["launches"]),
+                "avg_launch_ms": d["ms"] / max(1, d["launches"])}
+    step_flops = sum(f["flops"] for f in fam.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural scene, no dataset)",
+        "config": {"workload": WORKLOAD, "chains_per_step": B, "receiver_points": Q, "seeds_per_point": wl.spq,
+                   "k": 2, "walk_mode": args.mode, "l2": "flushed between steps (256 MiB write)" if not args.no_flush
+                   else "not flushed", "parallelism": "replicas x%d" % world,
+                   "counted_walks": "first walks + Bernoulli trial walks that converged"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clk,
+        "detail": {"converged_per_step": conv / args.steps, "walks_per_step": total["walks"] / args.steps,
+                   "trials_per_step": total["trials"] / args.steps,
+                   "step_ms": [round(x, 4) for x in step_ms],
+                   "step_fp32_tflops": step_flops / (t_ms * 1e-3) / 1e12 if world == 1 else None,
+                   "families": {n: {"ms_per_step": f["ms"] / args.steps, "launches": f["launches"],
+                                    "gflop_per_step": f["flops"] / args.steps / 1e9,
+                                    "tflops": f["flops"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] > 0 else None}
+                                for n, f in fam.items() if f["launches"]}},
+    }
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_sample(n=256, spq=16):
+    """Sample of the same workload for the oracle: an n x n receiver grid over
+    the same extent with 16 seeds per point (n = 256 is the whole workload)."""
+    from paper_2311_12818_gb300 import inputs as I
+    return I.glass_sphere(n=n, spq=spq)
+
+
+def oracle_step(wl, threads):
+    """One oracle pass of the hot path (guide trained untimed first); returns
+    (seconds, converged walks)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    from paper_2311_12818_gb300 import inputs as I
+    sc = O.Scene(wl)
+    s0 = O.sample_seeds(wl, sc, None, threads=threads, rng_offset=1 << 40)
+    c0 = O.walk(wl, sc, s0, threads=threads)
+    k0 = O.contribution(wl, sc, c0, threads=threads)
+    N0, _ = O.bernoulli(wl, sc, c0, k0["admissible"], threads=threads, rng_offset=1 << 40)
+    g = O.Guide(wl.n_cells, I.guide_edges())
+    g.update(*O.records(wl, c0, k0["T"], N0, k0["admissible"]), wl.params.weight_shift)
+    t0 = time.perf_counter()
+    s = O.sample_seeds(wl, sc, g, threads=threads)
+    c = O.walk(wl, sc, s, threads=threads)
+    k = O.contribution(wl, sc, c, threads=threads)
+    tw = np.zeros(wl.B, np.uint32)
+    N, _ = O.bernoulli(wl, sc, c, k["admissible"], g, threads=threads, trial_walks=tw)
+    E = O.irradiance(wl, k["T"], N, k["admissible"])
+    g2 = O.Guide(wl.n_cells, I.guide_edges())
+    g2.update(*O.records(wl, c, k["T"], N, k["admissible"]), wl.params.weight_shift)
+    dt = time.perf_counter() - t0
+    conv = int((c["status"] == 1).sum() + tw.sum())
+    del E
+    return dt, conv
+
+
+def cpu_baseline(wl_full):
+    threads = os.cpu_count() or 1
+    wl = cpu_sample()
+    dt, conv = oracle_step(wl, threads)
+    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "the whole workload (%d chains), one guided step after an untimed training pass, %.1f s"
+                      % (wl.B, dt)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    wl = cpu_sample(n=128)
+    times, convs = [], []
+    for i in range(args.warmup + args.steps):
+        dt, conv = oracle_step(wl, threads)
+        if i >= args.warmup:
+            times.append(dt)
+            convs.append(conv)
+    value = sum(convs) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded procedural scene, no dataset)",
+            "config": {"workload": WORKLOAD, "sample": "%d chains per step (128x128 points x 16 seeds over the same "
+                                                       "receiver extent)" % wl.B},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d chains per step, %d steps" % (wl.B, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,11 +109,13 @@ typedef struct mpg_ctx mpg_ctx;
 typedef struct mpg_scene mpg_scene;
 
 /* Work counters accumulated by the kernels since the last reset (device-side,
- * read back by mpg_ctx_stats): they give the algorithmic flop count of a run. */
+ * read back by mpg_ctx_stats): multiplied by per-unit operation counts they
+ * give the algorithmic flop count of a run. */
 typedef struct mpg_stats {
-  uint64_t newton_steps;     /* Newton steps (Thomas solves) over all walks       */
-  uint64_t full_evals;       /* chain evaluations with Jacobian blocks (per vertex) */
-  uint64_t c_evals;          /* constraint-only evaluations (per vertex)          */
+  uint64_t newton_steps;     /* Newton steps (one Thomas solve each)              */
+  uint64_t thomas_rows;      /* block rows of those Thomas solves (k per step)    */
+  uint64_t full_evals;       /* vertex evaluations with Jacobian blocks           */
+  uint64_t c_evals;          /* constraint-only vertex evaluations (line search)  */
   uint64_t ray_casts;        /* nearest-hit ray queries                           */
   uint64_t sphere_tests;     /* ray/sphere and ray/cap tests                      */
   uint64_t plane_tests;      /* ray/rectangle tests                               */
@@ -121,9 +123,19 @@ typedef struct mpg_stats {
   uint64_t tri_tests;        /* ray/triangle tests                                */
   uint64_t walks;            /* walks started                                     */
   uint64_t converged;        /* walks converged                                   */
-  uint64_t ggt_evals;        /* generalized-geometry-term solves (per vertex)     */
+  uint64_t ggt_rows;         /* block rows of the 2-column geometry-term solves   */
   uint64_t trials;           /* Bernoulli trials drawn                            */
+  uint64_t seeds;            /* seed directions drawn (first draws and trials)    */
 } mpg_stats;
+
+/* Kernel families, for per-family counters and launch timings. */
+#define MPG_KERNEL_SEED 0
+#define MPG_KERNEL_WALK 1
+#define MPG_KERNEL_CONTRIB 2
+#define MPG_KERNEL_BERNOULLI 3
+#define MPG_KERNEL_TRACE 4
+#define MPG_KERNEL_AUX 5   /* bucketing, irradiance reduction, guide update/prefix sums/records */
+#define MPG_KERNEL_KINDS 6
 
 const char* mpg_last_error(void);
 int32_t mpg_version(void);
@@ -134,9 +146,19 @@ void mpg_ctx_destroy(mpg_ctx* ctx);
 /* Waits for `stream` and returns the first device-side error recorded since the
  * last sync (MPG_ERR_LIMIT for a traversal overflow), else MPG_OK. */
 mpg_status mpg_ctx_sync(mpg_ctx* ctx, cudaStream_t stream);
-mpg_status mpg_ctx_stats(mpg_ctx* ctx, mpg_stats* out, int32_t reset, cudaStream_t stream);
+/* Counters of one kernel family (kind = MPG_KERNEL_*) or of all (kind = -1);
+ * waits for `stream`; reset != 0 clears them afterwards.  out may be NULL. */
+mpg_status mpg_ctx_stats(mpg_ctx* ctx, int32_t kind, mpg_stats* out, int32_t reset, cudaStream_t stream);
 /* Work counters on (default) or off; off selects kernels without the tallies. */
 mpg_status mpg_ctx_set_stats(mpg_ctx* ctx, int32_t on);
+/* Launch timing: when on, every kernel launch of the library is bracketed by
+ * CUDA events recorded on the stream it is launched on.  mpg_ctx_profile sums
+ * the elapsed times (ms) and counts the launches of a family (kind) since the
+ * last reset; it synchronises on the recorded events. */
+mpg_status mpg_ctx_set_profile(mpg_ctx* ctx, int32_t on);
+mpg_status mpg_ctx_profile(mpg_ctx* ctx, int32_t kind, double* ms, int64_t* launches, int32_t reset);
+/* Total kernel launches issued by the library on this context. */
+mpg_status mpg_ctx_launches(mpg_ctx* ctx, int64_t* count);
 
 /* Scene from the host tables (format: one row of 24 doubles per surface --
  * type, material, eta_front, eta_back, centre[3], radius, axis/normal[3],

@@ -563,7 +563,7 @@ static bool vertex_etas(const Surface& sf, bool front, bool refract, double& eta
 
 template <class T>
 bool vertex_blocks(const Frame<T>& fp, const Frame<T>& f, const Frame<T>& fn, const Surface& sf,
-                   bool refract, VBlocks<T>& out) {
+                   bool refract, VBlocks<T>& out, bool c_only = false) {
   using std::sqrt;
   V3<T> wi = fp.p - f.p, wo = fn.p - f.p;
   T di = norm(wi), dO = norm(wo);
@@ -583,6 +583,7 @@ bool vertex_blocks(const Frame<T>& fp, const Frame<T>& f, const Frame<T>& fn, co
   onb(f.n, s, t);
   out.C[0] = dot(h, s);
   out.C[1] = dot(h, t);
+  if (c_only) return true;
   // Projections: P_w a = (a - w (w.a)) / d is the derivative of a unit
   // direction w = (y - x)/|y - x| with respect to y along a.
   auto Pwi = [&](const V3<T>& a) { return (a - wi * dot(wi, a)) / di; };
@@ -1317,7 +1318,7 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
-                      uint32_t* N, uint8_t* capped, int32_t n_threads) {
+                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads) {
   if (!scene || !prm || Q < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   orc_params P = *prm;
@@ -1328,6 +1329,7 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
   parallel_for(B, n_threads, [&](int b) {
     N[b] = 0;
     capped[b] = 0;
+    if (trial_walks) trial_walks[b] = 0;
     if (!admissible[b]) return;
     int q = b / spq;
     ChainIO target;
@@ -1340,6 +1342,7 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
       if (!sd.valid) continue;
       int it = 0;
       if (walk_chain(S, sd.ch, nd, P, it) != ST_CONVERGED) continue;
+      if (trial_walks) trial_walks[b]++;
       if (same_solution(sd.ch, target, P.dedup_eps)) {
         N[b] = (uint32_t)t;
         return;
@@ -1414,6 +1417,73 @@ int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k,
 
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
   philox4x32_10(ctr, key, out);
+}
+
+static double tally_flops(const Tally& t) { return (double)(t.add + t.mul + t.div + t.sqrt); }
+
+// Floating-point operations (add, mul, div, sqrt: one flop each) of one
+// execution of each primitive, counted with the Counted scalar type on a
+// representative configuration.  out[]: 0 sphere frame, 1 plane frame,
+// 2 triangle frame, 3 sphere normal, 4 triangle normal, 5 vertex blocks (C and
+// the three Jacobian blocks), 6 vertex constraint only, 7 Thomas first row,
+// 8 Thomas further row (1 column), 9 geometry-term Thomas row (2 columns),
+// 10 geometry-term projection and determinant, 11 ray/sphere roots,
+// 12 ray/rectangle test, 13 ray/triangle test, 14 ray/box slab test,
+// 15 kappa per dielectric vertex.
+int32_t orc_unit_flops(double* out) {
+  typedef Counted C;
+  auto run = [](auto fn) { g_tally = Tally(); fn(); return tally_flops(g_tally); };
+  V3<C> p(0.3, -0.4, 0.86602540378), c(0.0, 0.0, 0.0);
+  out[0] = run([&] { frame_sphere<C>(p, c, C(1.0)); });
+  out[1] = run([&] { frame_plane<C>(p, V3<C>(0.0, 0.0, 1.0)); });
+  V3<C> P0(0.0, 0.0, 0.01), P1(0.02, 0.0, 0.012), P2(0.02, 0.02, 0.008);
+  V3<C> N0(0.01, 0.02, 0.9997), N1(-0.01, 0.0, 0.99995), N2(0.0, -0.02, 0.9998);
+  out[2] = run([&] { frame_triangle<C>(P0, P1, P2, N0, N1, N2, C(0.3), C(0.2)); });
+  out[3] = run([&] { normalize(p - c); });
+  out[4] = run([&] { normalize(N0 * (C(1.0) - C(0.3) - C(0.2)) + N1 * C(0.3) + N2 * C(0.2)); });
+  Surface sf;
+  sf.type = SURF_SPHERE; sf.mat = MAT_DIELECTRIC; sf.etaF = 1.0; sf.etaB = 1.5; sf.hf = -1;
+  sf.r = 1.0; sf.cap_cos = -1.0;
+  Frame<C> fp = frame_plane<C>(V3<C>(0.1, 0.2, -1.5), V3<C>(0.0, 0.0, 1.0));
+  Frame<C> f = frame_sphere<C>(normalize(V3<C>(0.1, 0.1, -1.0)), c, C(1.0));
+  Frame<C> fn = frame_sphere<C>(normalize(V3<C>(0.0, -0.2, 1.0)), c, C(1.0));
+  VBlocks<C> vb;
+  out[5] = run([&] { vertex_blocks<C>(fp, f, fn, sf, true, vb); });
+  out[6] = run([&] { vertex_blocks<C>(fp, f, fn, sf, true, vb, true); });
+  VBlocks<C> v8[8];
+  for (int i = 0; i < 8; ++i) vertex_blocks<C>(fp, f, fn, sf, true, v8[i]);
+  C rhs[32], x[32];
+  for (int i = 0; i < 32; ++i) rhs[i] = C(0.01 * (i + 1));
+  double t1 = run([&] { block_thomas<C>(1, v8, 1, rhs, x, 0.0); });
+  double t8 = run([&] { block_thomas<C>(8, v8, 1, rhs, x, 0.0); });
+  out[7] = t1;
+  out[8] = (t8 - t1) / 7.0;
+  double g1 = run([&] { block_thomas<C>(1, v8, 2, rhs, x, 0.0); });
+  double g8 = run([&] { block_thomas<C>(8, v8, 2, rhs, x, 0.0); });
+  out[9] = (g8 - g1) / 7.0;
+  Frame<C> ff[3] = {fp, f, fn};
+  double gg = run([&] { C G; chain_ggt<C>(1, false, ff, v8, 0.0, G); });
+  out[10] = gg - g1;
+  C r0[2];
+  out[11] = run([&] { sphere_roots<C>(V3<C>(0.1, 0.2, -1.5), normalize(V3<C>(0.0, 0.1, 1.0)), c, C(1.0), r0); });
+  out[12] = run([&] {  // plane t, hit point and two in-rectangle projections
+    V3<C> o(0.1, 0.2, 1.0), d(0.0, 0.1, -1.0), n(0.0, 0.0, 1.0), ex(1.0, 0.0, 0.0), ey(0.0, 1.0, 0.0);
+    C t = dot(c - o, n) / dot(d, n);
+    V3<C> q = o + d * t - c;
+    dot(q, ex); dot(q, ey); dot(ex, ex); dot(ey, ey);
+  });
+  C tt, bb1, bb2;
+  out[13] = run([&] { tri_hit<C>(V3<C>(0.01, 0.005, -1.0), normalize(V3<C>(0.0, 0.0, 1.0)), P0, P1, P2, tt, bb1, bb2); });
+  out[14] = 12.0;  // 6 subtractions and 6 divisions (or reciprocal products) of the slab test
+  out[15] = run([&] {
+    V3<C> wi = normalize(fp.p - f.p);
+    C ci = fabs(dot(wi, f.n));
+    C F = fresnel<C>(ci, C(1.0), C(1.5));
+    C r = C(1.0) / C(1.5);
+    C k = (C(1.0) - F) * r * r;
+    (void)k;
+  });
+  return 0;
 }
 
 int32_t orc_count_flops(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,

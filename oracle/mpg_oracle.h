@@ -80,13 +80,14 @@ int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
                          uint8_t* admissible, int32_t n_threads);
 
 /* Bernoulli trials for admissible chains: N[b] = index of the first trial
- * that walks to the same solution, capped[b] = 1 when max_trials ran out. */
+ * that walks to the same solution, capped[b] = 1 when max_trials ran out,
+ * trial_walks[b] (may be NULL) = trial walks that converged. */
 int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
                       const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
-                      uint32_t* N, uint8_t* capped, int32_t n_threads);
+                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads);
 
 /* Histogram bin of each direction (theta-major index), and the update
  * counts[cell][bin] += q(w), q = min(floor(w 2^S), 2^32-1) (0 unless w > 0). */
@@ -108,6 +109,10 @@ int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k,
 
 /* Philox4x32-10 block: out = philox(ctr[4], key[2]). */
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+/* Flops of one execution of each primitive in the counted scalar type (16
+ * values; the order is documented in the implementation). */
+int32_t orc_unit_flops(double* out);
 
 /* Algorithmic flop tally of walking + evaluating the given chains once more
  * in a counted scalar type: out[0] adds, [1] muls, [2] divs, [3] sqrts,

@@ -60,7 +60,8 @@ def lib():
                                        C.POINTER(orc_params), _f64p, _f64p, _f64p, _u8p, C.c_int32]
         L.orc_bernoulli.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
                                     C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64, C.c_uint64,
-                                    C.POINTER(orc_params), _f64p, _i32p, _u8p, _u32p, _u8p, C.c_int32]
+                                    C.POINTER(orc_params), _f64p, _i32p, _u8p, _u32p, _u8p, C.c_void_p,
+                                    C.c_int32]
         L.orc_guide_bin.argtypes = [C.POINTER(orc_guide), C.c_int32, _f32p, _i32p]
         L.orc_guide_update.argtypes = [C.POINTER(orc_guide), _u64p, C.c_int32, _u32p, _f32p, _f32p,
                                        C.c_int32]
@@ -196,10 +197,12 @@ def contribution(wl, scene, chains, threads=None):
     return dict(G=G, kappa=kap, T=T, admissible=adm)
 
 
-def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offset=0, max_trials=None):
+def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offset=0, max_trials=None,
+              trial_walks=None):
     B = wl.B
     N = np.zeros(B, np.uint32)
     capped = np.zeros(B, np.uint8)
+    tw = None if trial_walks is None else trial_walks.ctypes.data
     p = wl.params
     if max_trials is not None:
         import dataclasses
@@ -211,7 +214,7 @@ def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offse
                              wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8),
                              _c(chains["tau"], np.uint8), int(wl.tau_random), wl.rng_seed, rng_offset,
                              C.byref(P), chains["x"], chains["surf"], _c(admissible, np.uint8), N,
-                             capped, threads or default_threads())
+                             capped, tw, threads or default_threads())
     assert rc == 0, rc
     return N, capped
 

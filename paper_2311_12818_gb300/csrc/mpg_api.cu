@@ -45,7 +45,17 @@ bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
 }  // namespace
 
 struct mpg_ctx {
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
   int device = 0, sms = 1;
+  bool profile = false;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[MPG_KERNEL_KINDS] = {};
+  int64_t prof_n[MPG_KERNEL_KINDS] = {};
+  int64_t launches = 0;
   int* d_err = nullptr;
   unsigned long long* d_stats = nullptr;
   int* d_order = nullptr;
@@ -257,6 +267,10 @@ mpg_status check_guide(const mpg_guide* g, DGuide& out) {
   return MPG_OK;
 }
 
+cudaEvent_t pooled_event(mpg_ctx* ctx);
+template <class F>
+void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn);
+
 // Which per-K launches to make, and over which work list.
 struct Plan {
   int K[MAXK];
@@ -280,13 +294,46 @@ mpg_status make_plan(mpg_ctx* ctx, const mpg_chains* c, const mpg_params* p, int
     CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * (size_t)c->B));
     ctx->order_cap = c->B;
   }
-  launch_bucket(c->k, c->status, status_filter, c->B, ctx->d_count, ctx->d_base, ctx->d_cursor, ctx->d_order,
-                ctx->sms, st);
+  timed(ctx, MPG_KERNEL_AUX, st, 3, [&] {
+    launch_bucket(c->k, c->status, status_filter, c->B, ctx->d_count, ctx->d_base, ctx->d_cursor, ctx->d_order,
+                  ctx->sms, st);
+  });
   LAUNCH_CHECK("bucket");
   plan.w = DWork{ctx->d_order, ctx->d_base, ctx->d_count};
   plan.concurrent = true;
   return MPG_OK;
 }
+
+cudaEvent_t pooled_event(mpg_ctx* ctx) {
+  if (!ctx->pool.empty()) {
+    cudaEvent_t e = ctx->pool.back();
+    ctx->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launches `n` kernels through fn() on stream st, bracketed by events when
+// launch profiling is on.
+template <class F>
+void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn) {
+  mpg_ctx::ProfRec r{kind, nullptr, nullptr};
+  if (ctx->profile) {
+    r.a = pooled_event(ctx);
+    cudaEventRecord(r.a, st);
+  }
+  fn();
+  ctx->launches += n;
+  if (ctx->profile) {
+    r.b = pooled_event(ctx);
+    cudaEventRecord(r.b, st);
+    ctx->prof.push_back(r);
+  }
+}
+
+DCtx dctx(mpg_ctx* ctx, int kind) { return DCtx{ctx->d_err, ctx->d_stats + 16 * kind}; }
 
 // Runs fn(K, stream) for each planned K, on forked streams when concurrent.
 template <class F>
@@ -334,13 +381,13 @@ mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
   c->device = device;
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
   bool ok = cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&c->d_stats, sizeof(unsigned long long) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_stats, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS) == cudaSuccess &&
             cudaMalloc(&c->d_count, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_base, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_cursor, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_scratch, sizeof(float) * 16) == cudaSuccess &&
             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
-            cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16) == cudaSuccess &&
+            cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   for (int i = 0; ok && i < MAXK; ++i)
     ok = cudaStreamCreateWithFlags(&c->aux[i], cudaStreamNonBlocking) == cudaSuccess &&
@@ -363,6 +410,8 @@ void mpg_ctx_destroy(mpg_ctx* c) {
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
   }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -380,17 +429,62 @@ mpg_status mpg_ctx_sync(mpg_ctx* c, cudaStream_t st) {
   return MPG_OK;
 }
 
-mpg_status mpg_ctx_stats(mpg_ctx* c, mpg_stats* out, int32_t reset, cudaStream_t st) {
+mpg_status mpg_ctx_stats(mpg_ctx* c, int32_t kind, mpg_stats* out, int32_t reset, cudaStream_t st) {
   if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  if (kind < -1 || kind >= MPG_KERNEL_KINDS) return fail(MPG_ERR_INVALID_ARG, "kernel kind %d out of range", kind);
   CUDA_TRY(cudaSetDevice(c->device));
+  static_assert(sizeof(mpg_stats) == 14 * sizeof(uint64_t), "stats layout");
   if (out) {
-    unsigned long long v[16];
+    unsigned long long v[16 * MPG_KERNEL_KINDS];
     CUDA_TRY(cudaMemcpyAsync(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    static_assert(sizeof(mpg_stats) == 12 * sizeof(uint64_t), "stats layout");
-    memcpy(out, v, sizeof(mpg_stats));
+    uint64_t acc[14] = {0};
+    for (int k = 0; k < MPG_KERNEL_KINDS; ++k)
+      if (kind < 0 || kind == k)
+        for (int i = 0; i < 14; ++i) acc[i] += v[16 * k + i];
+    memcpy(out, acc, sizeof(mpg_stats));
   }
-  if (reset) CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * 16, st));
+  if (reset) {
+    if (kind < 0) CUDA_TRY(cudaMemsetAsync(c->d_stats, 0, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS, st));
+    else CUDA_TRY(cudaMemsetAsync(c->d_stats + 16 * kind, 0, sizeof(unsigned long long) * 16, st));
+  }
+  return MPG_OK;
+}
+
+mpg_status mpg_ctx_set_profile(mpg_ctx* c, int32_t on) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  c->profile = on != 0;
+  return MPG_OK;
+}
+
+mpg_status mpg_ctx_profile(mpg_ctx* c, int32_t kind, double* ms, int64_t* launches, int32_t reset) {
+  if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  if (kind < -1 || kind >= MPG_KERNEL_KINDS) return fail(MPG_ERR_INVALID_ARG, "kernel kind %d out of range", kind);
+  CUDA_TRY(cudaSetDevice(c->device));
+  for (auto& r : c->prof) {
+    CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    c->prof_ms[r.kind] += t;
+    c->prof_n[r.kind] += 1;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->prof.clear();
+  double m = 0.0;
+  int64_t n = 0;
+  for (int k = 0; k < MPG_KERNEL_KINDS; ++k)
+    if (kind < 0 || kind == k) { m += c->prof_ms[k]; n += c->prof_n[k]; }
+  if (ms) *ms = m;
+  if (launches) *launches = n;
+  if (reset)
+    for (int k = 0; k < MPG_KERNEL_KINDS; ++k) { c->prof_ms[k] = 0.0; c->prof_n[k] = 0; }
+  return MPG_OK;
+}
+
+mpg_status mpg_ctx_launches(mpg_ctx* c, int64_t* count) {
+  if (!c || !count) return fail(MPG_ERR_INVALID_ARG, "ctx or count is NULL");
+  *count = c->launches;
   return MPG_OK;
 }
 
@@ -550,11 +644,13 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* 
   if ((s = make_plan(ctx, chains, &Pn, -1, st, plan))) return s;
   DChains c = to_dev(chains);
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
-  DCtx dc{ctx->d_err, ctx->d_stats};
+  DCtx dc = dctx(ctx, MPG_KERNEL_SEED);
   int block = block_of(P);
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
-    launch_seed(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, dc,
-                grid_of(ctx, 0, K, block, c.B, true), block, s2);
+    timed(ctx, MPG_KERNEL_SEED, s2, 1, [&] {
+      launch_seed(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, dc,
+                  grid_of(ctx, 0, K, block, c.B, true), block, s2);
+    });
   });
 }
 
@@ -568,10 +664,12 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
   Plan plan;
   if ((s = make_plan(ctx, chains, P, ST_SEEDED, st, plan))) return s;
   DChains c = to_dev(chains);
-  DCtx dc{ctx->d_err, ctx->d_stats};
+  DCtx dc = dctx(ctx, MPG_KERNEL_WALK);
   int block = block_of(P);
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
-    launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, 1, K, block, c.B, true), block, s2);
+    timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
+      launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, 1, K, block, c.B, true), block, s2);
+    });
   });
 }
 
@@ -591,7 +689,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   Plan plan;
   if ((s = make_plan(ctx, chains, P, ST_CONVERGED, st, plan))) return s;
   DChains c = to_dev(chains);
-  DCtx dc{ctx->d_err, ctx->d_stats};
+  DCtx dcc = dctx(ctx, MPG_KERNEL_CONTRIB), dcb = dctx(ctx, MPG_KERNEL_BERNOULLI);
   DOut o{G, kappa, T, trials, capped, contrib};
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
   int block = block_of(P);
@@ -605,12 +703,17 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     if (capped) CUDA_TRY(cudaMemsetAsync(capped, 0, (size_t)c.B, st));
   }
   s = run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
-    launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dc, grid_of(ctx, 2, K, block, c.B, true), block, s2);
-    launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dc,
-                     grid_of(ctx, 3, K, block, c.B, true), block, s2);
+    timed(ctx, MPG_KERNEL_CONTRIB, s2, 1, [&] {
+      launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
+                     s2);
+    });
+    timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
+      launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb,
+                       grid_of(ctx, 3, K, block, c.B, true), block, s2);
+    });
   });
   if (s) return s;
-  launch_irradiance(contrib, c.Q, c.spq, E, ctx->sms, st);
+  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] { launch_irradiance(contrib, c.Q, c.spq, E, ctx->sms, st); });
   LAUNCH_CHECK("irradiance");
   return MPG_OK;
 }
@@ -624,7 +727,8 @@ mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t
   if (R < 0 || shift < 0 || shift > 60 || (R > 0 && (!aligned16(cell) || !aligned16(omega) || !aligned16(w))))
     return fail(MPG_ERR_INVALID_ARG, "invalid records (R %d, shift %d)", R, shift);
   CUDA_TRY(cudaSetDevice(ctx->device));
-  launch_guide_update(g, cell, omega, w, R, R_dev, shift, ctx->d_err, ctx->sms, st);
+  timed(ctx, MPG_KERNEL_AUX, st, R > 0 ? 2 : 1,
+        [&] { launch_guide_update(g, cell, omega, w, R, R_dev, shift, ctx->d_err, ctx->sms, st); });
   LAUNCH_CHECK("guide update");
   return MPG_OK;
 }
@@ -638,7 +742,9 @@ mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains
     return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
   CUDA_TRY(cudaSetDevice(ctx->device));
   DChains c = to_dev(chains);
-  launch_guide_records(c, contrib, 1.0f / sc->S.L.area, cell_out, omega_out, w_out, R_dev, ctx->sms, st);
+  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] {
+    launch_guide_records(c, contrib, 1.0f / sc->S.L.area, cell_out, omega_out, w_out, R_dev, ctx->sms, st);
+  });
   LAUNCH_CHECK("guide records");
   return MPG_OK;
 }
@@ -657,7 +763,10 @@ mpg_status mpg_trace_rays(mpg_ctx* ctx, const mpg_scene* sc, const float* o, con
     return fail(MPG_ERR_INVALID_ARG, "invalid ray arrays");
   if (n == 0) return MPG_OK;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  launch_trace(sc->S, o, d, n, tmin, tmax, t, surf, prim, bary, ctx->d_err, ctx->d_stats, ctx->stats_on, ctx->sms, st);
+  timed(ctx, MPG_KERNEL_TRACE, st, 1, [&] {
+    launch_trace(sc->S, o, d, n, tmin, tmax, t, surf, prim, bary, ctx->d_err, ctx->d_stats + 16 * MPG_KERNEL_TRACE,
+                 ctx->stats_on, ctx->sms, st);
+  });
   LAUNCH_CHECK("trace");
   return MPG_OK;
 }

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(128) k_trace(const __grid_constant__ DScene S,
   if (kS) {
     __syncwarp();
     uint32_t v[5] = {cnt.casts, cnt.sphere, cnt.plane, cnt.node, cnt.tri};
-    const int idx[5] = {3, 4, 5, 6, 7};
+    const int idx[5] = {4, 5, 6, 7, 8};
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
       uint32_t s = __reduce_add_sync(0xffffffffu, v[j]);

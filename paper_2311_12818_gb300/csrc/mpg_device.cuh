@@ -81,7 +81,7 @@ struct DGuide {
 
 // Per-thread work counters (flushed once per warp).
 struct Counters {
-  uint32_t newton, full_evals, c_evals, casts, sphere, plane, node, tri, ggt;
+  uint32_t newton, rows, full_evals, c_evals, casts, sphere, plane, node, tri, ggt, seeds;
 };
 
 // ---------------------------------------------------------------------------
@@ -591,7 +591,7 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
     float2 du[K][1];
 #pragma unroll
     for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
-    if (kStats) cnt.newton++;
+    if (kStats) { cnt.newton++; cnt.rows += K; }
     if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
     float beta = 1.0f;
     bool accepted = false;
@@ -656,8 +656,11 @@ __device__ __forceinline__ float p0_pdf(const DScene& S, float3 xD, float3 w) {
       if (d <= tg.r) continue;
       float t0, t1;
       if (!sphere_roots(xD, w, tg.c, tg.r, t0, t1) || t0 <= 0.0f) continue;
-      float3 p = xD + w * t0;
-      float cp = fabsf(dot(unit(p - tg.c), w));
+      // at the near hit (p - c).w = b + t0 = -sqrt(disc): the cosine is sqrt(disc)/r,
+      // well conditioned at grazing incidence where 1/cos makes the density steep
+      float3 oc = xD - tg.c;
+      float3 qd = oc - w * dot(oc, w);
+      float cp = sqrtf(fmaxf(fmaf(tg.r, tg.r, -dot(qd, qd)), 0.0f)) / tg.r;
       float pA = 1.0f / (6.28318530717958647f * tg.r * tg.r * (1.0f - tg.r / d));
       sum += pA * t0 * t0 / cp;
     } else {
@@ -679,6 +682,7 @@ template <int K, bool kStats>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
                           Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt) {
+  if (kStats) cnt.seeds++;
   uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;

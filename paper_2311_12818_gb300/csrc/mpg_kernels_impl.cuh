@@ -10,19 +10,18 @@ namespace mpg {
 namespace kern {
 
 
-enum { S_NEWTON = 0, S_FULL, S_CEVAL, S_CASTS, S_SPHERE, S_PLANE, S_NODE, S_TRI, S_WALKS, S_CONV, S_GGT, S_TRIALS };
-
 struct Tally {
   Counters c;
   uint32_t walks, conv, trials;
 };
 
+// Warp-reduced flush of the tallies into the family's counters (mpg_stats order).
 __device__ __forceinline__ void flush(const Tally& t, unsigned long long* stats) {
   __syncwarp();
-  uint32_t v[12] = {t.c.newton, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
-                    t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials};
+  uint32_t v[14] = {t.c.newton, t.c.rows, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
+                    t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials, t.c.seeds};
 #pragma unroll
-  for (int i = 0; i < 12; ++i) {
+  for (int i = 0; i < 14; ++i) {
     uint32_t s = __reduce_add_sync(0xffffffffu, v[i]);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(stats + i, (unsigned long long)s);
   }

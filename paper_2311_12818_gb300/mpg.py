@@ -51,8 +51,10 @@ class mpg_guide(C.Structure):
                 ("phi_cos", C.c_void_p), ("phi_sin", C.c_void_p)]
 
 
-STAT_FIELDS = ["newton_steps", "full_evals", "c_evals", "ray_casts", "sphere_tests", "plane_tests",
-               "node_tests", "tri_tests", "walks", "converged", "ggt_evals", "trials"]
+STAT_FIELDS = ["newton_steps", "thomas_rows", "full_evals", "c_evals", "ray_casts", "sphere_tests",
+               "plane_tests", "node_tests", "tri_tests", "walks", "converged", "ggt_rows", "trials", "seeds"]
+KERNEL_SEED, KERNEL_WALK, KERNEL_CONTRIB, KERNEL_BERNOULLI, KERNEL_TRACE, KERNEL_AUX = range(6)
+KERNEL_NAMES = ["seed", "walk", "contrib", "bernoulli", "trace", "aux"]
 
 
 class mpg_stats(C.Structure):
@@ -60,7 +62,7 @@ class mpg_stats(C.Structure):
 
 
 EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy", "mpg_ctx_sync",
-           "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
+           "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak"]
 
@@ -81,8 +83,11 @@ def lib():
         L.mpg_ctx_destroy.argtypes = [vp]
         L.mpg_ctx_destroy.restype = None
         L.mpg_ctx_sync.argtypes = [vp, vp]
-        L.mpg_ctx_stats.argtypes = [vp, C.POINTER(mpg_stats), i32, vp]
+        L.mpg_ctx_stats.argtypes = [vp, i32, C.POINTER(mpg_stats), i32, vp]
         L.mpg_ctx_set_stats.argtypes = [vp, i32]
+        L.mpg_ctx_set_profile.argtypes = [vp, i32]
+        L.mpg_ctx_profile.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(C.c_int64), i32]
+        L.mpg_ctx_launches.argtypes = [vp, C.POINTER(C.c_int64)]
         L.mpg_scene_create.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]
         L.mpg_scene_destroy.argtypes = [vp]
         L.mpg_scene_destroy.restype = None
@@ -135,13 +140,27 @@ class Context:
     def sync(self, stream=None):
         _check(lib().mpg_ctx_sync(self.h, _stream(stream)))
 
-    def stats(self, reset=False, stream=None):
+    def stats(self, kind=-1, reset=False, stream=None):
         s = mpg_stats()
-        _check(lib().mpg_ctx_stats(self.h, C.byref(s), int(reset), _stream(stream)))
+        _check(lib().mpg_ctx_stats(self.h, kind, C.byref(s), int(reset), _stream(stream)))
         return {f: int(getattr(s, f)) for f in STAT_FIELDS}
 
     def reset_stats(self, stream=None):
-        _check(lib().mpg_ctx_stats(self.h, None, 1, _stream(stream)))
+        _check(lib().mpg_ctx_stats(self.h, -1, None, 1, _stream(stream)))
+
+    def set_profile(self, on):
+        _check(lib().mpg_ctx_set_profile(self.h, int(bool(on))))
+
+    def profile(self, kind=-1, reset=False):
+        """(milliseconds, launches) of a kernel family since the last reset."""
+        ms, n = C.c_double(), C.c_int64()
+        _check(lib().mpg_ctx_profile(self.h, kind, C.byref(ms), C.byref(n), int(reset)))
+        return ms.value, n.value
+
+    def launches(self):
+        n = C.c_int64()
+        _check(lib().mpg_ctx_launches(self.h, C.byref(n)))
+        return n.value
 
     def set_stats(self, on):
         _check(lib().mpg_ctx_set_stats(self.h, int(bool(on))))
@@ -292,12 +311,13 @@ def mpg_guide_update(ctx, guide, cell, omega, w, R=None, R_dev=None, weight_shif
                                   weight_shift, _stream(stream)))
 
 
-def mpg_guide_records(ctx, scene, chains, contrib, stream=None):
+def mpg_guide_records(ctx, scene, chains, contrib, out=None, stream=None):
+    """Records (cell [B] int32, omega [3, B], w [B], count [1] int32) of chains with contrib > 0."""
     B = chains.B
-    cell = torch.zeros(B, dtype=torch.int32, device="cuda")
-    om = torch.zeros((3, B), dtype=torch.float32, device="cuda")
-    w = torch.zeros(B, dtype=torch.float32, device="cuda")
-    R = torch.zeros(4, dtype=torch.int32, device="cuda")
+    if out is None:
+        out = (torch.zeros(B, dtype=torch.int32, device="cuda"), torch.zeros((3, B), dtype=torch.float32, device="cuda"),
+               torch.zeros(B, dtype=torch.float32, device="cuda"), torch.zeros(4, dtype=torch.int32, device="cuda"))
+    cell, om, w, R = out
     cs = chains.struct()
     _check(lib().mpg_guide_records(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(cell), _ptr(om), _ptr(w),
                                    _ptr(R), _stream(stream)))
