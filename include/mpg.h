@@ -73,6 +73,9 @@ typedef struct mpg_params {
   int32_t block_threads;/* threads per block of the walk kernels (0 = default)    */
   int32_t tau_random;   /* nonzero: draw tau_i ~ Bernoulli(0.5) per trial          */
   int32_t k_uniform;    /* 1..8: every chain has this length; 0: lengths vary      */
+  float stall_tol;      /* FP32 resolution of C: a walk whose line search can no
+                           longer reduce |C| ends CONVERGED when max_i |C_i|_inf <
+                           stall_tol (0 disables; the FP64 oracle has no such rule) */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */

@@ -1380,11 +1380,18 @@ int32_t orc_constraint(void* scene, int32_t B, int32_t spq, const double* xD, co
   if (!scene || B < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   for (int b = 0; b < B; ++b) {
+    for (int i = 0; i < 2 * MAXK; ++i) C[(size_t)b * 2 * MAXK + i] = 0.0;
+    cmax[b] = -1.0;
+    bool ok = k[b] >= 1 && k[b] <= MAXK;
+    for (int i = 0; ok && i < k[b]; ++i) {
+      int s = surf[(size_t)b * MAXK + i];
+      ok = s >= 0 && s < (int)S.surf.size();
+    }
+    if (!ok) continue;  // chain without vertices (invalid seed)
     ChainIO ch;
     load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
     EvalOut ev;
     eval_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), ev);
-    for (int i = 0; i < 2 * MAXK; ++i) C[(size_t)b * 2 * MAXK + i] = 0.0;
     if (!ev.ok) { cmax[b] = -1.0; continue; }
     for (int i = 0; i < ch.k; ++i) {
       C[(size_t)b * 2 * MAXK + 2 * i] = ev.vb[i].C[0];

@@ -605,7 +605,10 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
         break;
       }
     }
-    if (!accepted) return ST_FAILED;
+    // FP32 resolution: C cannot be evaluated much below ~1e-6 at unit scene
+    // scale, so a step that no longer lowers |C| ends a walk already within
+    // stall_tol as converged.
+    if (!accepted) return cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   }
 }
 
