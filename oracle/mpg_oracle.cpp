@@ -17,7 +17,9 @@
 //     reflection / Snell's law in vector form.
 //   * Newton on the block-tridiagonal Jacobian dC/du (u_i: tangent-plane
 //     offsets of vertex i), a 2x2 block Thomas sweep, step halving and
-//     reprojection by ray casting from x_D through the moved vertices.
+//     reprojection of each moved vertex onto its own surface by a ray cast along
+//     the surface's projection direction (radial / normal / vertical); chain
+//     visibility is checked once the walk has converged (admissibility).
 //   * G by the implicit function theorem: du/du_L = -J^{-1} dC/du_L.
 #include "mpg_oracle.h"
 
@@ -930,23 +932,52 @@ static void eval_chain(const Scene& S, const ChainIO& ch, const V3d& nD, EvalOut
     }
 }
 
-// Move every vertex by beta * (dpdu du_0 + dpdv du_1) and re-project the chain
-// onto the surfaces: a ray from x_D through the moved x_1, then from each new
-// vertex through the next moved one; each hit must lie on the vertex's surface.
+// Vertical ray cast into a heightfield at (x, y): the triangle of the grid
+// cell containing (x, y) and the barycentrics of the point in it.
+static bool hf_vertical_hit(const HField& H, double x, double y, Vtx& v) {
+  double fx = (x - H.x0) / H.dx, fy = (y - H.y0) / H.dy;
+  if (!(fx >= 0.0 && fy >= 0.0 && fx <= H.nx - 1 && fy <= H.ny - 1)) return false;
+  int i = std::min((int)fx, H.nx - 2), j = std::min((int)fy, H.ny - 2);
+  double u = fx - i, w = fy - j;
+  int quad = j * (H.nx - 1) + i;
+  if (u >= w) { v.prim = 2 * quad; v.b1 = u - w; v.b2 = w; }       // triangle (v00, v10, v11)
+  else { v.prim = 2 * quad + 1; v.b1 = u; v.b2 = w - u; }          // triangle (v00, v11, v01)
+  int vv[3]; H.tri_vertices(v.prim, vv);
+  v.p = H.P[vv[0]] + (H.P[vv[1]] - H.P[vv[0]]) * v.b1 + (H.P[vv[2]] - H.P[vv[0]]) * v.b2;
+  return true;
+}
+
+// Reprojection of a moved vertex onto its own surface by a ray cast along the
+// surface's projection direction: from the centre (spheres and caps), along
+// the normal (rectangles), vertically (heightfields).  Fails when the point
+// leaves the surface (cap rim, rectangle border, heightfield domain).
+static bool reproject_vertex(const Scene& S, const Vtx& cur, const V3d& target, Vtx& out) {
+  const Surface& sf = S.surf[cur.surf];
+  out = cur;
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    V3d d = target - sf.c;
+    double l = norm(d);
+    if (!(l > 0.0)) return false;
+    out.p = sf.c + d * (sf.r / l);
+    return sf.type == SURF_SPHERE || dot(out.p - sf.c, sf.axis) >= sf.r * sf.cap_cos;
+  }
+  if (sf.type == SURF_RECT) {
+    out.p = target - sf.axis * dot(target - sf.c, sf.axis);
+    V3d q = out.p - sf.c;
+    return std::fabs(dot(q, sf.ex)) <= dot(sf.ex, sf.ex) && std::fabs(dot(q, sf.ey)) <= dot(sf.ey, sf.ey);
+  }
+  return hf_vertical_hit(S.hf[sf.hf], target.x, target.y, out);
+}
+
+// Move every vertex by beta * (dpdu du_0 + dpdv du_1) in its tangent plane and
+// reproject it onto its surface.  Visibility along the chain is not enforced
+// during the walk; the admissibility test of the converged chain checks it.
 static bool propose(const Scene& S, const ChainIO& ch, const Frame<double>* f, const double* du,
-                    double beta, double ray_eps, ChainIO& out) {
+                    double beta, ChainIO& out) {
   out = ch;
-  V3d prev = ch.v[0].p;
   for (int i = 1; i <= ch.k; ++i) {
     V3d target = ch.v[i].p + (f[i].dpdu * du[2 * (i - 1)] + f[i].dpdv * du[2 * (i - 1) + 1]) * beta;
-    V3d dir = target - prev;
-    double len = norm(dir);
-    if (!(len > 0.0)) return false;
-    dir = dir / len;
-    Hit h = intersect(S, prev, dir, ray_eps, std::numeric_limits<double>::infinity());
-    if (!h.hit || h.surf != ch.v[i].surf) return false;
-    out.v[i] = hit_vertex(S, prev, dir, h);
-    prev = out.v[i].p;
+    if (!reproject_vertex(S, ch.v[i], target, out.v[i])) return false;
   }
   return true;
 }
@@ -967,7 +998,7 @@ static int walk_chain(const Scene& S, ChainIO& ch, const V3d& nD, const orc_para
     bool accepted = false;
     for (int hv = 0; hv <= prm.max_halvings; ++hv, beta *= 0.5) {
       ChainIO cand;
-      if (!propose(S, ch, ev.f, du, beta, prm.ray_eps, cand)) continue;
+      if (!propose(S, ch, ev.f, du, beta, cand)) continue;
       EvalOut ec;
       eval_chain(S, cand, nD, ec);
       if (ec.ok && ec.cnorm2 < ev.cnorm2) {

@@ -15,12 +15,13 @@ def unit(v):
     return v / np.linalg.norm(v)
 
 
-def alhazen_sphere(xD, xL, c=(0.0, 0.0, 0.0), r=1.0, n_scan=20000):
+def alhazen_sphere(xD, xL, c=(0.0, 0.0, 0.0), r=1.0, n_scan=20000, visible_only=True):
     """Reflection points on a sphere between two external points (Alhazen's
     problem).  The reflection point lies in the plane through the centre, x_D
     and x_L; on the circle p(t) = c + r (cos t e1 + sin t e2) the normal bisects
     the two unit directions, i.e. cross2(p - c, u_D + u_L) = 0.  Returns the
-    roots seen from both points (in front of the tangent plane)."""
+    roots seen from both points (in front of the tangent plane), or all roots
+    of the equation with visible_only=False."""
     c = np.asarray(c, np.float64)
     D, L = np.asarray(xD, np.float64) - c, np.asarray(xL, np.float64) - c
     e1 = unit(D)
@@ -44,7 +45,7 @@ def alhazen_sphere(xD, xL, c=(0.0, 0.0, 0.0), r=1.0, n_scan=20000):
         if fs[i] == 0 or fs[i] * fs[i + 1] < 0:
             t = brentq(f, ts[i], ts[i + 1], xtol=1e-15, rtol=1e-15, maxiter=200)
             p2 = r * np.array([math.cos(t), math.sin(t)])
-            if (D2 - p2) @ p2 > 0 and (L2 - p2) @ p2 > 0:
+            if not visible_only or ((D2 - p2) @ p2 > 0 and (L2 - p2) @ p2 > 0):
                 roots.append(c + p2[0] * e1 + p2[1] * e2)
     # de-duplicate roots found on neighbouring intervals
     out = []
