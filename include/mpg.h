@@ -193,8 +193,11 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guid
 /* S2-S6 -- manifold walk (Sec. 3, "Manifold walks"): Newton's method on the
  * generalized half-vector constraints C_i = (h.s_i, h.t_i), h ~ eta_i w_i +
  * eta_o w_o, with the 2k x 2k block-tridiagonal Jacobian solved by a 2x2-block
- * Thomas sweep, step halving and reprojection by ray casting from x_D through the
- * moved vertices.  Walks every chain whose status is MPG_CHAIN_SEEDED; writes x,
+ * Thomas sweep, step halving and reprojection of each moved vertex onto its own
+ * surface by a ray cast along the surface's projection direction (from the
+ * centre of spheres and caps, along the normal of rectangles, vertically into
+ * heightfields).  Chain visibility is left to mpg_chain_contribution's
+ * admissibility test.  Walks every chain whose status is MPG_CHAIN_SEEDED; writes x,
  * surf, prim, bary, status and iters in place. */
 mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* chains,
                              const mpg_params* params, cudaStream_t stream);

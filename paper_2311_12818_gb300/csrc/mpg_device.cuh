@@ -7,7 +7,8 @@
 //   constraint  C_i = (h.s_i, h.t_i),  h = (eta_i w_i + eta_o w_o)/|...|
 //   Jacobian    block-tridiagonal, 2x2 blocks A_i, B_i, Cc_i (analytic)
 //   solve       2x2-block Thomas sweep
-//   step        tangent-plane move, step halving, reprojection by ray casting
+//   step        tangent-plane move, step halving, reprojection of each vertex
+//               onto its own surface (radial / normal / vertical ray cast)
 //   G           implicit function theorem, 2-column Thomas solve
 #pragma once
 
@@ -548,29 +549,59 @@ __device__ __forceinline__ bool eval_c(const DScene& S, const Chain<K>& ch, cons
   return true;
 }
 
-// Move every vertex by beta (dpdu du_0 + dpdv du_1) and reproject: a ray from
-// x_D through the moved x_1, then from each new vertex through the next moved
-// one; every hit must lie on the vertex's own surface.
-template <int K, bool kStats>
-__device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, const Ends& e, const float3 (&tu)[K],
-                                        const float3 (&tv)[K], const float2 (&du)[K][1], float beta, float ray_eps,
-                                        Chain<K>& out, int* err, Counters& cnt) {
-  float3 prev = e.xD;
+// Vertical ray cast into a heightfield at (x, y): the triangle of the grid
+// cell holding (x, y) and the barycentrics of the point in it (O(1): the
+// height grid is its own acceleration structure for vertical rays).
+__device__ __forceinline__ bool hf_vertical_hit(const DHF& H, float x, float y, float3& p, int& prim, float& b1,
+                                                float& b2) {
+  float fx = (x - H.x0) / H.dx, fy = (y - H.y0) / H.dy;
+  if (!(fx >= 0.0f && fy >= 0.0f && fx <= (float)(H.nx - 1) && fy <= (float)(H.ny - 1))) return false;
+  int i = min((int)fx, H.nx - 2), j = min((int)fy, H.ny - 2);
+  float u = fx - (float)i, w = fy - (float)j;
+  int quad = j * (H.nx - 1) + i;
+  if (u >= w) { prim = 2 * quad; b1 = u - w; b2 = w; }
+  else { prim = 2 * quad + 1; b1 = u; b2 = w - u; }
+  int v0, v1, v2;
+  hf_tri(H, prim, v0, v1, v2);
+  float3 P0 = f3(__ldg(H.P + v0)), P1 = f3(__ldg(H.P + v1)), P2 = f3(__ldg(H.P + v2));
+  p = P0 + (P1 - P0) * b1 + (P2 - P0) * b2;
+  return true;
+}
+
+// Reprojection of a moved vertex onto its own surface by a ray cast along the
+// surface's projection direction: from the centre (spheres and caps), along
+// the normal (rectangles), vertically (heightfields).
+__device__ __forceinline__ bool reproject(const DScene& S, int surf, float3 target, float3& p, int& prim, float& b1,
+                                          float& b2) {
+  const DSurf& sf = S.s[surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    float3 d = target - sf.c;
+    float l2 = dot(d, d);
+    if (!(l2 > 0.0f)) return false;
+    p = sf.c + d * (sf.r / sqrtf(l2));
+    return sf.type == SURF_SPHERE || dot(p - sf.c, sf.axis) >= sf.r * sf.cap_cos;
+  }
+  if (sf.type == SURF_RECT) {
+    p = target - sf.axis * dot(target - sf.c, sf.axis);
+    float3 q = p - sf.c;
+    return fabsf(dot(q, sf.ex)) <= sf.ex2 && fabsf(dot(q, sf.ey)) <= sf.ey2;
+  }
+  return hf_vertical_hit(S.hf[sf.hf], target.x, target.y, p, prim, b1, b2);
+}
+
+// Move every vertex by beta (dpdu du_0 + dpdv du_1) in its tangent plane and
+// reproject it onto its surface; chain visibility is checked once converged.
+template <int K>
+__device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, const float3 (&tu)[K],
+                                        const float3 (&tv)[K], const float2 (&du)[K][1], float beta, Chain<K>& out) {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     float3 target = ch.x[i] + (tu[i] * du[i][0].x + tv[i] * du[i][0].y) * beta;
-    float3 d = target - prev;
-    float l2 = dot(d, d);
-    if (!(l2 > 0.0f)) return false;
-    d = d * (1.0f / sqrtf(l2));
-    Hit h = intersect<kStats>(S, prev, d, ray_eps, 3.0e38f, err, cnt);
-    if (h.surf != ch.surf[i]) return false;
-    out.x[i] = hit_point(S, prev, d, h);
-    out.surf[i] = h.surf;
-    out.prim[i] = h.prim;
-    out.b1[i] = h.b1;
-    out.b2[i] = h.b2;
-    prev = out.x[i];
+    out.surf[i] = ch.surf[i];
+    out.prim[i] = ch.prim[i];
+    out.b1[i] = ch.b1[i];
+    out.b2[i] = ch.b2[i];
+    if (!reproject(S, ch.surf[i], target, out.x[i], out.prim[i], out.b1[i], out.b2[i])) return false;
   }
   return true;
 }
@@ -597,7 +628,7 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
     bool accepted = false;
     for (int hv = 0; hv <= P.max_halvings; ++hv, beta *= 0.5f) {
       Chain<K> cand;
-      if (!propose<K, kStats>(S, ch, e, tu, tv, du, beta, P.ray_eps, cand, err, cnt)) continue;
+      if (!propose<K>(S, ch, tu, tv, du, beta, cand)) continue;
       float cc2;
       if (eval_c<K, kStats>(S, cand, e, cc2, cnt) && cc2 < cn2) {
         ch = cand;
