@@ -242,7 +242,7 @@ mpg_status check_params(const mpg_params* p) {
       !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 ||
       !(p->alpha >= 0.0f && p->alpha <= 1.0f) || p->weight_shift < 0 || p->weight_shift > 60 ||
       (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
-      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f))
+      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) || !(p->fp64_cond >= 0.0f))
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -433,15 +433,15 @@ mpg_status mpg_ctx_stats(mpg_ctx* c, int32_t kind, mpg_stats* out, int32_t reset
   if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
   if (kind < -1 || kind >= MPG_KERNEL_KINDS) return fail(MPG_ERR_INVALID_ARG, "kernel kind %d out of range", kind);
   CUDA_TRY(cudaSetDevice(c->device));
-  static_assert(sizeof(mpg_stats) == 14 * sizeof(uint64_t), "stats layout");
+  static_assert(sizeof(mpg_stats) == 15 * sizeof(uint64_t), "stats layout");
   if (out) {
     unsigned long long v[16 * MPG_KERNEL_KINDS];
     CUDA_TRY(cudaMemcpyAsync(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    uint64_t acc[14] = {0};
+    uint64_t acc[15] = {0};
     for (int k = 0; k < MPG_KERNEL_KINDS; ++k)
       if (kind < 0 || kind == k)
-        for (int i = 0; i < 14; ++i) acc[i] += v[16 * k + i];
+        for (int i = 0; i < 15; ++i) acc[i] += v[16 * k + i];
     memcpy(out, acc, sizeof(mpg_stats));
   }
   if (reset) {

@@ -82,7 +82,7 @@ struct DGuide {
 
 // Per-thread work counters (flushed once per warp).
 struct Counters {
-  uint32_t newton, rows, full_evals, c_evals, casts, sphere, plane, node, tri, ggt, seeds;
+  uint32_t newton, rows, full_evals, c_evals, casts, sphere, plane, node, tri, ggt, seeds, ggt64;
 };
 
 // ---------------------------------------------------------------------------
@@ -833,9 +833,11 @@ __device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 
 
 // Admissibility, G (IFT; FP64 determinant for K >= 6), kappa.  Returns false
 // for an inadmissible chain.
+// condM (out) = |M|_F^2 / (2 |det M|) of the 2x2 direction Jacobian: 1 for a
+// conformal map, large near caustic folds where FP32 loses the determinant.
 template <int K, bool kStats>
 __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
-                             float& kappa, int* err, Counters& cnt) {
+                             float& kappa, float& condM, int* err, Counters& cnt) {
   VB vb[K];
   float3 tu[K], tv[K];
   float cn2, cmax;
@@ -889,13 +891,9 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
     M[0][c] = dot(a, dw);
     M[1][c] = dot(b, dw);
   }
-  float det;
-  if (K >= 6) {
-    double dd = (double)M[0][0] * (double)M[1][1] - (double)M[0][1] * (double)M[1][0];
-    det = (float)fabs(dd);
-  } else {
-    det = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
-  }
+  float det = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
+  float fro2 = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[1][0] * M[1][0] + M[1][1] * M[1][1];
+  condM = det > 0.0f ? 0.5f * fro2 / det : 3.0e38f;
   G = point ? det : cosD * det;
   // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2
   float kap = 1.0f;

@@ -4,6 +4,7 @@
 // vertices) and on whether it tallies work counters.
 #pragma once
 
+#include "mpg_ggt64.cuh"
 #include "mpg_kernels.cuh"
 
 namespace mpg {
@@ -18,10 +19,10 @@ struct Tally {
 // Warp-reduced flush of the tallies into the family's counters (mpg_stats order).
 __device__ __forceinline__ void flush(const Tally& t, unsigned long long* stats) {
   __syncwarp();
-  uint32_t v[14] = {t.c.newton, t.c.rows, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
-                    t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials, t.c.seeds};
+  uint32_t v[15] = {t.c.newton, t.c.rows, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
+                    t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials, t.c.seeds, t.c.ggt64};
 #pragma unroll
-  for (int i = 0; i < 14; ++i) {
+  for (int i = 0; i < 15; ++i) {
     uint32_t s = __reduce_add_sync(0xffffffffu, v[i]);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(stats + i, (unsigned long long)s);
   }
@@ -143,7 +144,16 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       Chain<K> ch;
       load_chain<K>(c, b, ch);
       Ends e = load_ends(c, b);
-      adm = contribution<K, kS>(S, ch, e, P, G, kap, ctx.err, t.c);
+      float condM = 1.0f;
+      adm = contribution<K, kS>(S, ch, e, P, G, kap, condM, ctx.err, t.c);
+      // FP32 leaves too few digits of G near caustic folds and for long
+      // chains: repeat the geometry term in FP64 there.
+      if (adm && (K >= 6 || condM > P.fp64_cond)) {
+        double g;
+        if (ggt64<K>(S, ch, e, (double)P.sing_eps, g)) G = (float)g;
+        else adm = false;
+        t.c.ggt64++;
+      }
     }
     if (!adm) { G = 0.f; kap = 0.f; }
     if (o.G) o.G[b] = G;

@@ -34,7 +34,7 @@ class mpg_params(C.Structure):
                 ("ray_eps", C.c_float), ("sing_eps", C.c_float), ("dedup_eps", C.c_float),
                 ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_float),
                 ("walk_mode", C.c_int32), ("block_threads", C.c_int32), ("tau_random", C.c_int32),
-                ("k_uniform", C.c_int32), ("stall_tol", C.c_float)]
+                ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_cond", C.c_float)]
 
 
 class mpg_chains(C.Structure):
@@ -52,7 +52,8 @@ class mpg_guide(C.Structure):
 
 
 STAT_FIELDS = ["newton_steps", "thomas_rows", "full_evals", "c_evals", "ray_casts", "sphere_tests",
-               "plane_tests", "node_tests", "tri_tests", "walks", "converged", "ggt_rows", "trials", "seeds"]
+               "plane_tests", "node_tests", "tri_tests", "walks", "converged", "ggt_rows", "trials", "seeds",
+               "ggt_fp64"]
 KERNEL_SEED, KERNEL_WALK, KERNEL_CONTRIB, KERNEL_BERNOULLI, KERNEL_TRACE, KERNEL_AUX = range(6)
 KERNEL_NAMES = ["seed", "walk", "contrib", "bernoulli", "trace", "aux"]
 
@@ -127,7 +128,7 @@ def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_
     """mpg_params from an inputs.Params (FP32 copy of the solver constants)."""
     return mpg_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps, p.max_trials,
                       p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform,
-                      p.stall_tol)
+                      p.stall_tol, p.fp64_cond)
 
 
 class Context:

@@ -59,7 +59,7 @@ def test_params_struct_layout_matches_header():
     from paper_2311_12818_gb300 import mpg
     src = open(os.path.join(ROOT, "include", "mpg.h")).read()
     body = src[src.index("typedef struct mpg_params"):src.index("} mpg_params;")]
-    fields = re.findall(r"\b(?:float|int32_t)\s+([a-z_]+);", body)
+    fields = re.findall(r"\b(?:float|int32_t)\s+([a-z_0-9]+);", body)
     assert fields == [f for f, _ in mpg.mpg_params._fields_]
     body = src[src.index("typedef struct mpg_chains"):src.index("} mpg_chains;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
