@@ -76,9 +76,11 @@ typedef struct mpg_params {
   float stall_tol;      /* FP32 resolution of C: a walk whose line search can no
                            longer reduce |C| ends CONVERGED when max_i |C_i|_inf <
                            stall_tol (0 disables; the FP64 oracle has no such rule) */
-  float fp64_cond;      /* the geometry term is recomputed in FP64 when the 2x2
-                           direction Jacobian's |M|_F^2/(2|det M|) exceeds this
-                           (0: always; chains with k >= 6 always)               */
+  float fp64_tol;       /* G is formed in FP32 from both chain ends (reciprocity);
+                           when the two differ by more than this relative amount,
+                           for k >= 6, or for a walk stopped by stall_tol, the
+                           vertices are polished and G recomputed in FP64
+                           (0: always FP64)                                     */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
@@ -210,7 +212,7 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* c
  * admissibility (unoccluded segments, vertex types consistent with the sides,
  * positive end cosines), the generalized geometry term G by the implicit
  * function theorem (in FP64 for k >= 6 and ill-conditioned chains, see
- * fp64_cond), kappa (Fresnel / mirror and
+ * fp64_tol), kappa (Fresnel / mirror and
  * radiance scaling), T = kappa G L_o; then Bernoulli trials (Sec. 5.7): fresh
  * seeds with the same n are walked until one reaches the same solution (FP64
  * distance test), N = trial index, <1/P> = N / P(n) (capped at max_trials,

@@ -242,7 +242,7 @@ mpg_status check_params(const mpg_params* p) {
       !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 ||
       !(p->alpha >= 0.0f && p->alpha <= 1.0f) || p->weight_shift < 0 || p->weight_shift > 60 ||
       (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
-      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) || !(p->fp64_cond >= 0.0f))
+      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) || !(p->fp64_tol >= 0.0f))
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }

@@ -833,14 +833,18 @@ __device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 
 
 // Admissibility, G (IFT; FP64 determinant for K >= 6), kappa.  Returns false
 // for an inadmissible chain.
-// condM (out) = |M|_F^2 / (2 |det M|) of the 2x2 direction Jacobian: 1 for a
-// conformal map, large near caustic folds where FP32 loses the determinant.
+// Admissibility, G (implicit function theorem) and kappa in FP32.  G is
+// formed twice from one 4-column Thomas sweep: X_L = cos_D |det d(w_D)/d(u_L)|
+// (light end moved) and X_D = |det d(w_L)/d(u_D)| (receiver moved).  By
+// reciprocity eta_D^2 X_L = eta_L^2 |n_L.w_L| X_D, so their relative mismatch
+// estimates the FP32 error of G (out: mismatch); cmax (out) is the chain's
+// FP32 residual.  Returns false for an inadmissible chain.
 template <int K, bool kStats>
 __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
-                             float& kappa, float& condM, int* err, Counters& cnt) {
+                             float& kappa, float& mismatch, float& cmax, int* err, Counters& cnt) {
   VB vb[K];
   float3 tu[K], tv[K];
-  float cn2, cmax;
+  float cn2;
   if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, true, cnt)) return false;
   // vertex types must match the sides of their neighbours
 #pragma unroll
@@ -856,45 +860,53 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   float cosD = dot(e.nD, wD);
   if (!(cosD > 0.0f)) return false;
   bool point = S.L.type == LIGHT_POINT;
-  if (!point && !(dot(S.L.n, unit(ch.x[K - 1] - e.xL)) > 0.0f)) return false;
+  float3 wL = unit(ch.x[K - 1] - e.xL);
+  if (!point && !(dot(S.L.n, wL) > 0.0f)) return false;
   if (!segment_clear<kStats>(S, e.xD, ch.x[0], P.ray_eps, err, cnt)) return false;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     float3 b = i == K - 1 ? e.xL : ch.x[i + 1];
     if (!segment_clear<kStats>(S, ch.x[i], b, P.ray_eps, err, cnt)) return false;
   }
-  // G: J Y = -dC/du_end, end = light axes (area light) or receiver axes (point)
-  float2 Y[K][2];
+  // J Y = -dC/du_end: columns 0,1 light end (block row K-1), 2,3 receiver end (row 0)
+  float2 Y[K][4];
 #pragma unroll
-  for (int i = 0; i < K; ++i) { Y[i][0] = make_float2(0.f, 0.f); Y[i][1] = Y[i][0]; }
-  if (point) {
-    Y[0][0] = make_float2(-vb[0].A.x, -vb[0].A.z);
-    Y[0][1] = make_float2(-vb[0].A.y, -vb[0].A.w);
-  } else {
-    Y[K - 1][0] = make_float2(-vb[K - 1].Cc.x, -vb[K - 1].Cc.z);
-    Y[K - 1][1] = make_float2(-vb[K - 1].Cc.y, -vb[K - 1].Cc.w);
-  }
-  if (kStats) cnt.ggt += K;
-  if (!thomas<K, 2>(vb, Y, P.sing_eps)) return false;
-  int vi = point ? K - 1 : 0;
-  float3 anchor = point ? e.xL : e.xD;
-  float3 w = ch.x[vi] - anchor;
-  float dist = len(w);
-  w = w * (1.0f / dist);
-  float3 a, b;
-  onb(w, a, b);
-  float M[2][2];
+  for (int i = 0; i < K; ++i)
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    float3 dx = tu[vi] * Y[vi][c].x + tv[vi] * Y[vi][c].y;
-    float3 dw = (dx - w * dot(w, dx)) * (1.0f / dist);
-    M[0][c] = dot(a, dw);
-    M[1][c] = dot(b, dw);
+    for (int c = 0; c < 4; ++c) Y[i][c] = make_float2(0.f, 0.f);
+  Y[K - 1][0] = make_float2(-vb[K - 1].Cc.x, -vb[K - 1].Cc.z);
+  Y[K - 1][1] = make_float2(-vb[K - 1].Cc.y, -vb[K - 1].Cc.w);
+  Y[0][2] = make_float2(-vb[0].A.x, -vb[0].A.z);
+  Y[0][3] = make_float2(-vb[0].A.y, -vb[0].A.w);
+  if (kStats) cnt.ggt += 2 * K;
+  if (!thomas<K, 4>(vb, Y, P.sing_eps)) return false;
+  float X[2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    int vi = side == 0 ? 0 : K - 1;
+    float3 w = side == 0 ? ch.x[0] - e.xD : ch.x[K - 1] - e.xL;
+    float dist = len(w);
+    w = w * (1.0f / dist);
+    float3 a, b;
+    onb(w, a, b);
+    float M[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float2 y = Y[vi][2 * side + c];
+      float3 dx = tu[vi] * y.x + tv[vi] * y.y;
+      float3 dw = (dx - w * dot(w, dx)) * (1.0f / dist);
+      M[0][c] = dot(a, dw);
+      M[1][c] = dot(b, dw);
+    }
+    X[side] = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
   }
-  float det = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
-  float fro2 = M[0][0] * M[0][0] + M[0][1] * M[0][1] + M[1][0] * M[1][0] + M[1][1] * M[1][1];
-  condM = det > 0.0f ? 0.5f * fro2 / det : 3.0e38f;
-  G = point ? det : cosD * det;
+  float XL = cosD * X[0], XD = X[1];
+  float3 nl = point ? cross(S.L.exu, S.L.eyu) : S.L.n;
+  float etaD = vb[0].ei, etaL = vb[K - 1].eo;
+  float rc = (etaL * etaL) / (etaD * etaD) * fabsf(dot(nl, wL));
+  float XDs = rc * XD;
+  mismatch = fabsf(XL - XDs) / fmaxf(fmaxf(XL, XDs), 1e-30f);
+  G = point ? XD : XL;
   // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2
   float kap = 1.0f;
 #pragma unroll

@@ -125,34 +125,153 @@ __device__ __forceinline__ bool blocks64(D3 xp, D3 tpu, D3 tpv, const Frame64& f
   return true;
 }
 
-// G in FP64 for the chain ch (vertices as stored by the walk).
+// Chain vertices in FP64 (positions on the surfaces, triangle ids, barycentrics).
 template <int K>
-__device__ bool ggt64(const DScene& S, const Chain<K>& ch, const Ends& e, double sing_eps, double& G) {
-  Frame64 f[K];
+struct Chain64 {
+  D3 x[K];
+  int surf[K], prim[K];
+  double b1[K], b2[K];
+};
+
+// FP64 local frame at a chain vertex (positions already on the surface).
+__device__ __forceinline__ Frame64 frame64_at(const DScene& S, int surf, int prim, D3 p, double b1, double b2) {
+  const DSurf& sf = S.s[surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP || sf.type == SURF_RECT) {
+    Frame64 f = frame64(S, surf, prim, make_float3((float)p.x, (float)p.y, (float)p.z), 0.f, 0.f);
+    if (sf.type != SURF_RECT) {
+      D3 c = d3(sf.c);
+      f.n = unit(p - c);
+      f.p = p;
+      onb(f.n, f.dpdu, f.dpdv);
+      f.dndu = f.dpdu * (1.0 / (double)sf.r);
+      f.dndv = f.dpdv * (1.0 / (double)sf.r);
+    } else {
+      f.p = p;
+    }
+    return f;
+  }
+  Frame64 f = frame64(S, surf, prim, make_float3(0.f, 0.f, 0.f), (float)b1, (float)b2);
+  // recompute with the FP64 barycentrics
+  const DHF& H = S.hf[sf.hf];
+  int v0, v1, v2;
+  hf_tri(H, prim, v0, v1, v2);
+  D3 P0 = d3(__ldg(H.P + v0)), P1 = d3(__ldg(H.P + v1)), P2 = d3(__ldg(H.P + v2));
+  D3 N0 = d3(__ldg(H.N + v0)), N1 = d3(__ldg(H.N + v1)), N2 = d3(__ldg(H.N + v2));
+  D3 e1 = P1 - P0, e2 = P2 - P0;
+  f.p = P0 + e1 * b1 + e2 * b2;
+  D3 Ns = N0 * (1.0 - b1 - b2) + N1 * b1 + N2 * b2;
+  double il = 1.0 / len(Ns);
+  f.n = Ns * il;
+  double g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2);
+  double igd = 1.0 / (g11 * g22 - g12 * g12);
+  for (int q = 0; q < 2; ++q) {
+    D3 a = q == 0 ? f.dpdu : f.dpdv;
+    double r1 = dot(e1, a), r2 = dot(e2, a);
+    double db1 = (g22 * r1 - g12 * r2) * igd, db2 = (g11 * r2 - g12 * r1) * igd;
+    D3 dN = (N1 - N0) * db1 + (N2 - N0) * db2;
+    D3 dn = (dN - f.n * dot(f.n, dN)) * il;
+    if (q == 0) f.dndu = dn; else f.dndv = dn;
+  }
+  return f;
+}
+
+// Constraint value at a vertex in FP64.
+__device__ __forceinline__ bool constraint64(D3 xp, const Frame64& f, D3 xn, const DSurf& sf, bool refract,
+                                             double& c0, double& c1) {
+  D3 wi = unit(xp - f.p), wo = unit(xn - f.p);
+  float eif, eof;
+  if (!etas(sf, dot(wi, f.n) > 0.0, refract, eif, eof)) return false;
+  D3 ht = wi * (double)eif + wo * (double)eof;
+  double L = len(ht);
+  if (!(L > 0.0)) return false;
+  D3 h = ht * (1.0 / L), s, t;
+  onb(f.n, s, t);
+  c0 = dot(h, s);
+  c1 = dot(h, t);
+  return true;
+}
+
+// Vertical ray cast into a heightfield in FP64.
+__device__ __forceinline__ bool hf_vertical64(const DHF& H, double x, double y, D3& p, int& prim, double& b1,
+                                              double& b2) {
+  double fx = (x - (double)H.x0) / (double)H.dx, fy = (y - (double)H.y0) / (double)H.dy;
+  if (!(fx >= 0.0 && fy >= 0.0 && fx <= (double)(H.nx - 1) && fy <= (double)(H.ny - 1))) return false;
+  int i = min((int)fx, H.nx - 2), j = min((int)fy, H.ny - 2);
+  double u = fx - i, w = fy - j;
+  int quad = j * (H.nx - 1) + i;
+  if (u >= w) { prim = 2 * quad; b1 = u - w; b2 = w; }
+  else { prim = 2 * quad + 1; b1 = u; b2 = w - u; }
+  int v0, v1, v2;
+  hf_tri(H, prim, v0, v1, v2);
+  D3 P0 = d3(__ldg(H.P + v0)), P1 = d3(__ldg(H.P + v1)), P2 = d3(__ldg(H.P + v2));
+  p = P0 + (P1 - P0) * b1 + (P2 - P0) * b2;
+  return true;
+}
+
+__device__ __forceinline__ bool reproject64(const DScene& S, int surf, D3 target, D3& p, int& prim, double& b1,
+                                            double& b2) {
+  const DSurf& sf = S.s[surf];
+  if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    D3 c = d3(sf.c), d = target - c;
+    double l = len(d);
+    if (!(l > 0.0)) return false;
+    p = c + d * ((double)sf.r / l);
+    return sf.type == SURF_SPHERE || dot(p - c, d3(sf.axis)) >= (double)sf.r * (double)sf.cap_cos;
+  }
+  if (sf.type == SURF_RECT) {
+    D3 ax = d3(sf.axis);
+    p = target - ax * dot(target - d3(sf.c), ax);
+    D3 q = p - d3(sf.c);
+    return fabs(dot(q, d3(sf.ex))) <= (double)sf.ex2 && fabs(dot(q, d3(sf.ey))) <= (double)sf.ey2;
+  }
+  return hf_vertical64(S.hf[sf.hf], target.x, target.y, p, prim, b1, b2);
+}
+
+template <int K>
+__device__ __forceinline__ void to64(const DScene& S, const Chain<K>& ch, Chain64<K>& c) {
 #pragma unroll
-  for (int i = 0; i < K; ++i) f[i] = frame64(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
-  D3 xD = d3(e.xD), xL = d3(e.xL), nD = d3(e.nD);
-  D3 ru, rv;
-  onb(nD, ru, rv);
+  for (int i = 0; i < K; ++i) {
+    c.surf[i] = ch.surf[i];
+    c.prim[i] = ch.prim[i];
+    c.b1[i] = ch.b1[i];
+    c.b2[i] = ch.b2[i];
+    const DSurf& sf = S.s[ch.surf[i]];
+    D3 p = d3(ch.x[i]);
+    if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) p = d3(sf.c) + unit(p - d3(sf.c)) * (double)sf.r;
+    c.x[i] = p;
+  }
+}
+
+// Frames and Jacobian blocks of the whole chain; C (2K) and max |C| optional.
+template <int K>
+__device__ bool chain64(const DScene& S, const Chain64<K>& ch, const Ends& e, Frame64 (&f)[K], VB64 (&vb)[K],
+                        double* C, double& cmax) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) f[i] = frame64_at(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
+  D3 xD = d3(e.xD), xL = d3(e.xL), ru, rv;
+  onb(d3(e.nD), ru, rv);
   D3 lu = d3(S.L.exu), lv = d3(S.L.eyu);
-  VB64 vb[K];
+  cmax = 0.0;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     D3 xp = i == 0 ? xD : f[i > 0 ? i - 1 : 0].p;
     D3 xn = i == K - 1 ? xL : f[i < K - 1 ? i + 1 : 0].p;
     D3 pu = i == 0 ? ru : f[i > 0 ? i - 1 : 0].dpdu, pv = i == 0 ? rv : f[i > 0 ? i - 1 : 0].dpdv;
     D3 nu = i == K - 1 ? lu : f[i < K - 1 ? i + 1 : 0].dpdu, nv = i == K - 1 ? lv : f[i < K - 1 ? i + 1 : 0].dpdv;
-    if (!blocks64(xp, pu, pv, f[i], xn, nu, nv, S.s[ch.surf[i]], (e.tau >> i) & 1u, vb[i])) return false;
+    const DSurf& sf = S.s[ch.surf[i]];
+    bool refract = (e.tau >> i) & 1u;
+    if (!blocks64(xp, pu, pv, f[i], xn, nu, nv, sf, refract, vb[i])) return false;
+    double c0, c1;
+    if (!constraint64(xp, f[i], xn, sf, refract, c0, c1)) return false;
+    if (C) { C[2 * i] = c0; C[2 * i + 1] = c1; }
+    cmax = fmax(cmax, fmax(fabs(c0), fabs(c1)));
   }
-  bool point = S.L.type == LIGHT_POINT;
-  // right-hand side: -dC/du_end in block row 0 (point light) or K-1 (area light)
-  double R[K][2][2];
-#pragma unroll
-  for (int i = 0; i < K; ++i) R[i][0][0] = R[i][0][1] = R[i][1][0] = R[i][1][1] = 0.0;
-  const double* E = point ? vb[0].A : vb[K - 1].Cc;
-  int row = point ? 0 : K - 1;
-  R[row][0][0] = -E[0]; R[row][0][1] = -E[1]; R[row][1][0] = -E[2]; R[row][1][1] = -E[3];
-  // block Thomas sweep, two columns
+  return true;
+}
+
+// Block Thomas sweep in FP64 for M columns; R[i][r][c].
+template <int K, int M>
+__device__ bool thomas64(const VB64 (&vb)[K], double (&R)[K][2][M], double sing_eps) {
   double Binv[K][4];
   double Bp[4] = {vb[0].B[0], vb[0].B[1], vb[0].B[2], vb[0].B[3]};
 #pragma unroll
@@ -166,7 +285,7 @@ __device__ bool ggt64(const DScene& S, const Chain<K>& ch, const Ends& e, double
       Bp[1] = vb[i].B[1] - (Lm[0] * Cp[1] + Lm[1] * Cp[3]);
       Bp[2] = vb[i].B[2] - (Lm[2] * Cp[0] + Lm[3] * Cp[2]);
       Bp[3] = vb[i].B[3] - (Lm[2] * Cp[1] + Lm[3] * Cp[3]);
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < M; ++c) {
         double r0 = R[i - 1][0][c], r1 = R[i - 1][1][c];
         R[i][0][c] -= Lm[0] * r0 + Lm[1] * r1;
         R[i][1][c] -= Lm[2] * r0 + Lm[3] * r1;
@@ -180,7 +299,7 @@ __device__ bool ggt64(const DScene& S, const Chain<K>& ch, const Ends& e, double
   }
 #pragma unroll
   for (int i = K - 1; i >= 0; --i) {
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < M; ++c) {
       double r0 = R[i][0][c], r1 = R[i][1][c];
       if (i < K - 1) {
         const double* Cc = vb[i].Cc;
@@ -191,8 +310,54 @@ __device__ bool ggt64(const DScene& S, const Chain<K>& ch, const Ends& e, double
       R[i][1][c] = Binv[i][2] * r0 + Binv[i][3] * r1;
     }
   }
+  return true;
+}
+
+// Newton polish in FP64 of a converged FP32 chain (a few steps, each accepted
+// only if it lowers |C|), then G in FP64.  Returns false if the chain is not a
+// solution in FP64 (no step brings max|C| under tol) or G cannot be formed.
+template <int K>
+__device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, double tol, double sing_eps, int steps,
+                             double& G) {
+  Frame64 f[K];
+  VB64 vb[K];
+  double C[2 * K], cmax;
+  if (!chain64<K>(S, ch, e, f, vb, C, cmax)) return false;
+  for (int it = 0; it < steps && cmax >= 1e-3 * tol; ++it) {
+    double R[K][2][1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) { R[i][0][0] = -C[2 * i]; R[i][1][0] = -C[2 * i + 1]; }
+    if (!thomas64<K, 1>(vb, R, sing_eps)) break;
+    Chain64<K> cand = ch;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < K && ok; ++i) {
+      D3 target = ch.x[i] + f[i].dpdu * R[i][0][0] + f[i].dpdv * R[i][1][0];
+      ok = reproject64(S, ch.surf[i], target, cand.x[i], cand.prim[i], cand.b1[i], cand.b2[i]);
+    }
+    if (!ok) break;
+    Frame64 fc[K];
+    VB64 vc[K];
+    double Cn[2 * K], cn;
+    if (!chain64<K>(S, cand, e, fc, vc, Cn, cn) || !(cn < cmax)) break;
+    ch = cand;
+#pragma unroll
+    for (int i = 0; i < K; ++i) { f[i] = fc[i]; vb[i] = vc[i]; }
+#pragma unroll
+    for (int i = 0; i < 2 * K; ++i) C[i] = Cn[i];
+    cmax = cn;
+  }
+  if (!(cmax < tol)) return false;
+  bool point = S.L.type == LIGHT_POINT;
+  double R[K][2][2];
+#pragma unroll
+  for (int i = 0; i < K; ++i) R[i][0][0] = R[i][0][1] = R[i][1][0] = R[i][1][1] = 0.0;
+  const double* E = point ? vb[0].A : vb[K - 1].Cc;
+  int row = point ? 0 : K - 1;
+  R[row][0][0] = -E[0]; R[row][0][1] = -E[1]; R[row][1][0] = -E[2]; R[row][1][1] = -E[3];
+  if (!thomas64<K, 2>(vb, R, sing_eps)) return false;
   int vi = point ? K - 1 : 0;
-  D3 anchor = point ? xL : xD;
+  D3 anchor = point ? d3(e.xL) : d3(e.xD);
   D3 w = f[vi].p - anchor;
   double dist = len(w);
   w = w * (1.0 / dist);
@@ -206,7 +371,7 @@ __device__ bool ggt64(const DScene& S, const Chain<K>& ch, const Ends& e, double
     M[1][c] = dot(b, dw);
   }
   double det = fabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
-  G = point ? det : dot(nD, w) * det;
+  G = point ? det : dot(d3(e.nD), w) * det;
   return true;
 }
 

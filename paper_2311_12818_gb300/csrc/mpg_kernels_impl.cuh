@@ -144,14 +144,29 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       Chain<K> ch;
       load_chain<K>(c, b, ch);
       Ends e = load_ends(c, b);
-      float condM = 1.0f;
-      adm = contribution<K, kS>(S, ch, e, P, G, kap, condM, ctx.err, t.c);
-      // FP32 leaves too few digits of G near caustic folds and for long
-      // chains: repeat the geometry term in FP64 there.
-      if (adm && (K >= 6 || condM > P.fp64_cond)) {
+      float mismatch = 0.0f, cmax = 0.0f;
+      adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, ctx.err, t.c);
+      // Escalate to FP64 where FP32 is not enough: long chains, a geometry term
+      // whose two reciprocal FP32 evaluations disagree, or a walk that stopped
+      // at the FP32 resolution of C.  The vertices are first polished by FP64
+      // Newton steps and written back.
+      if (adm && (K >= 6 || mismatch > P.fp64_tol || !(cmax < P.tol))) {
+        Chain64<K> c64;
+        to64<K>(S, ch, c64);
         double g;
-        if (ggt64<K>(S, ch, e, (double)P.sing_eps, g)) G = (float)g;
-        else adm = false;
+        if (polish_ggt64<K>(S, c64, e, (double)P.tol, (double)P.sing_eps, 3, g)) {
+          G = (float)g;
+#pragma unroll
+          for (int v = 0; v < K; ++v) {
+            ch.x[v] = make_float3((float)c64.x[v].x, (float)c64.x[v].y, (float)c64.x[v].z);
+            ch.prim[v] = c64.prim[v];
+            ch.b1[v] = (float)c64.b1[v];
+            ch.b2[v] = (float)c64.b2[v];
+          }
+          store_chain<K>(c, b, ch);
+        } else {
+          adm = false;
+        }
         t.c.ggt64++;
       }
     }

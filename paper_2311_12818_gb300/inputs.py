@@ -89,7 +89,7 @@ class Params:
     alpha: float = 0.5           # defensive mixture weight of p_0 (Sec. 5.5)
     weight_shift: int = 16       # histogram weight quantisation q = floor(w * 2^S)
     stall_tol: float = 2e-5      # FP32 walks only: stalled line search within this |C| counts as converged
-    fp64_cond: float = 4.0       # FP32 G is recomputed in FP64 above this 2x2 conditioning
+    fp64_tol: float = 1e-4       # FP32 G recomputed in FP64 when its two reciprocal forms differ by more
 
 
 @dataclasses.dataclass

@@ -34,7 +34,7 @@ class mpg_params(C.Structure):
                 ("ray_eps", C.c_float), ("sing_eps", C.c_float), ("dedup_eps", C.c_float),
                 ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_float),
                 ("walk_mode", C.c_int32), ("block_threads", C.c_int32), ("tau_random", C.c_int32),
-                ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_cond", C.c_float)]
+                ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float)]
 
 
 class mpg_chains(C.Structure):
@@ -128,7 +128,7 @@ def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_
     """mpg_params from an inputs.Params (FP32 copy of the solver constants)."""
     return mpg_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps, p.max_trials,
                       p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform,
-                      p.stall_tol, p.fp64_cond)
+                      p.stall_tol, p.fp64_tol)
 
 
 class Context:
