@@ -64,6 +64,12 @@ struct mpg_ctx {
   int* d_base = nullptr;
   int* d_cursor = nullptr;
   float* d_scratch = nullptr;
+  int* d_queue = nullptr;        // [MAXK+1][16] work-queue counters of the persistent launches
+  int* d_nlist = nullptr;        // [2][MAXK+1] overflow list lengths
+  int* d_zero = nullptr;         // [MAXK+1] zeros (list regions when chains are not bucketed)
+  int* d_list[2] = {nullptr, nullptr};
+  unsigned* d_nbest = nullptr;
+  int bern_cap = 0;
   bool stats_on = true;
   cudaStream_t aux[MAXK] = {};
   cudaEvent_t ev_fork = nullptr;
@@ -239,7 +245,7 @@ mpg_status check_chains(const mpg_chains* c, bool need_walk_state) {
 mpg_status check_params(const mpg_params* p) {
   if (!p) return fail(MPG_ERR_INVALID_ARG, "params is NULL");
   if (!(p->tol > 0.0f) || p->max_iter < 0 || p->max_iter > 255 || p->max_halvings < 0 || p->max_halvings > 60 ||
-      !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 ||
+      !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 || p->max_trials > (1 << 24) ||
       !(p->alpha >= 0.0f && p->alpha <= 1.0f) || p->weight_shift < 0 || p->weight_shift > 60 ||
       (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
       p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) || !(p->fp64_tol >= 0.0f))
@@ -386,6 +392,10 @@ mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
             cudaMalloc(&c->d_base, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_cursor, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_scratch, sizeof(float) * 16) == cudaSuccess &&
+            cudaMalloc(&c->d_queue, sizeof(int) * 16 * (MAXK + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_nlist, sizeof(int) * 2 * (MAXK + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_zero, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
+            cudaMemset(c->d_zero, 0, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
@@ -405,6 +415,8 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaSetDevice(c->device);
   cudaFree(c->d_err); cudaFree(c->d_stats); cudaFree(c->d_order); cudaFree(c->d_count);
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
+  cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero);
+  cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest);
   for (int i = 0; i < MAXK; ++i) {
     if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
@@ -666,6 +678,15 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
   DChains c = to_dev(chains);
   DCtx dc = dctx(ctx, MPG_KERNEL_WALK);
   int block = block_of(P);
+  if (P->walk_mode == MPG_WALK_BATCHED) {
+    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 16 * (MAXK + 1), st));
+    return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
+      timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
+        launch_walk_p(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, ctx->d_queue + 16 * K,
+                      grid_of(ctx, 4, K, block, c.B, true), block, s2);
+      });
+    });
+  }
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
       launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, 1, K, block, c.B, true), block, s2);
@@ -702,15 +723,65 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     if (trials) CUDA_TRY(cudaMemsetAsync(trials, 0, sizeof(uint32_t) * (size_t)c.B, st));
     if (capped) CUDA_TRY(cudaMemsetAsync(capped, 0, (size_t)c.B, st));
   }
+  const bool batched = P->walk_mode == MPG_WALK_BATCHED;
+  if (batched) {
+    if (ctx->bern_cap < c.B) {
+      cudaFree(ctx->d_list[0]); cudaFree(ctx->d_list[1]); cudaFree(ctx->d_nbest);
+      ctx->d_list[0] = ctx->d_list[1] = nullptr;
+      ctx->d_nbest = nullptr;
+      ctx->bern_cap = 0;
+      CUDA_TRY(cudaMalloc(&ctx->d_list[0], sizeof(int) * (size_t)c.B));
+      CUDA_TRY(cudaMalloc(&ctx->d_list[1], sizeof(int) * (size_t)c.B));
+      CUDA_TRY(cudaMalloc(&ctx->d_nbest, sizeof(unsigned) * (size_t)c.B));
+      ctx->bern_cap = c.B;
+    }
+    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 16 * (MAXK + 1), st));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_nlist, 0, sizeof(int) * 2 * (MAXK + 1), st));
+  }
   s = run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_CONTRIB, s2, 1, [&] {
       launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
                      s2);
     });
+    if (!batched) {
+      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
+        launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb,
+                         grid_of(ctx, 3, K, block, c.B, true), block, s2);
+      });
+      return;
+    }
+    // first pass: each lane runs trials 1..T1 of one chain; the rest go to
+    // rounds of TB = 8, 32, 128, ... parallel trials per remaining chain
+    DBernScratch bs;
+    bs.T1 = 8;
+    bs.list[0] = ctx->d_list[0];
+    bs.list[1] = ctx->d_list[1];
+    bs.n_list[0] = ctx->d_nlist + K;
+    bs.n_list[1] = ctx->d_nlist + (MAXK + 1) + K;
+    bs.base = plan.w.base ? plan.w.base + K : ctx->d_zero + K;
+    bs.nbest = ctx->d_nbest;
+    int* q = ctx->d_queue + 16 * K;
     timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-      launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb,
-                       grid_of(ctx, 3, K, block, c.B, true), block, s2);
+      launch_bern_p(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb, q + 1, bs,
+                    grid_of(ctx, 5, K, block, c.B, true), block, s2);
     });
+    int t0 = bs.T1 + 1, TB = 8, cur = 0;
+    for (int r = 0; t0 <= P->max_trials && r < 14; ++r) {
+      if (r == 13 || t0 + TB - 1 > P->max_trials) TB = P->max_trials - t0 + 1;  // the last round reaches the cap
+      int t_end = t0 + TB - 1;
+      int nxt = 1 - cur;
+      cudaMemsetAsync(bs.n_list[nxt], 0, sizeof(int), s2);
+      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
+        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q + 2 + r,
+                          bs.list[cur], bs.n_list[cur], bs.base, bs.nbest, t0, TB,
+                          grid_of(ctx, 6, K, block, c.B, true), block, s2);
+        launch_bern_finish(sc->S, c, o, bs.list[cur], bs.n_list[cur], bs.base, bs.nbest, t_end, P->max_trials,
+                           bs.list[nxt], bs.n_list[nxt], ctx->sms, s2);
+      });
+      t0 = t_end + 1;
+      TB *= 4;
+      cur = nxt;
+    }
   });
   if (s) return s;
   timed(ctx, MPG_KERNEL_AUX, st, 1, [&] { launch_irradiance(contrib, c.Q, c.spq, E, ctx->sms, st); });

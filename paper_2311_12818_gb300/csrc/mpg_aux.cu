@@ -159,6 +159,37 @@ void launch_guide_records(const DChains& c, const float* contrib, float inv_area
 }
 
 // ---------------------------------------------------------------------------
+// End of a Bernoulli trial round
+// ---------------------------------------------------------------------------
+__global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, const int* n_list, const int* base,
+                              unsigned* nbest, int t_end, int max_trials, int* next, int* n_next) {
+  const int n = *n_list;
+  const int* L = list + *base;
+  int* Nx = next + *base;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int b = L[j];
+    unsigned nb = nbest[b];
+    bool hit = nb != 0xffffffffu;
+    bool cap = !hit && t_end >= max_trials;
+    if (hit || cap) {
+      uint32_t N = hit ? nb : (uint32_t)max_trials;
+      if (o.trials) o.trials[b] = N;
+      if (o.capped) o.capped[b] = cap ? 1 : 0;
+      float pn = c.pn ? c.pn[b] : 1.0f;
+      o.contrib[b] = area * o.T[b] * (float)N / pn;
+    } else {
+      Nx[atomicAdd(n_next, 1)] = b;
+    }
+  }
+}
+
+void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
+                        const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
+                        int sms, cudaStream_t st) {
+  k_bern_finish<<<sms * 2, 256, 0, st>>>(S.L.area, c, o, list, n_list, base, nbest, t_end, max_trials, next, n_next);
+}
+
+// ---------------------------------------------------------------------------
 // Standalone ray batch (BVH/analytic nearest hit)
 // ---------------------------------------------------------------------------
 template <bool kS>

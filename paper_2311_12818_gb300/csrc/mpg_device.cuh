@@ -907,22 +907,31 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   float XDs = rc * XD;
   mismatch = fabsf(XL - XDs) / fmaxf(fmaxf(XL, XDs), 1e-30f);
   G = point ? XD : XL;
-  // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2
+  // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2.  The
+  // transmittance is formed directly, (1 - F) = (T_s + T_p)/2 with
+  // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
+  // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
+  // near total internal reflection.
   float kap = 1.0f;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const DSurf& sf = S.s[ch.surf[i]];
     if (sf.mat == MAT_MIRROR) continue;
     float3 xp = i == 0 ? e.xD : ch.x[i - 1];
+    float3 xn = i == K - 1 ? e.xL : ch.x[i + 1];
     float3 n = vertex_normal(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
     float ci = fabsf(dot(unit(xp - ch.x[i]), n));
-    float e2 = vb[i].front ? sf.etaB : sf.etaF;
-    float F = fresnel(ci, vb[i].ei, e2);
     if ((e.tau >> i) & 1u) {
-      float r = vb[i].ei / vb[i].eo;
-      kap *= (1.0f - F) * r * r;
+      float n1 = vb[i].ei, n2 = vb[i].eo;
+      float co = fabsf(dot(unit(xn - ch.x[i]), n));
+      float num = 4.0f * n1 * n2 * ci * co;
+      float ds = n1 * ci + n2 * co, dp = n2 * ci + n1 * co;
+      float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
+      float r = n1 / n2;
+      kap *= Tr * r * r;
     } else {
-      kap *= F;
+      float e2 = vb[i].front ? sf.etaB : sf.etaF;
+      kap *= fresnel(ci, vb[i].ei, e2);
     }
   }
   kappa = kap;

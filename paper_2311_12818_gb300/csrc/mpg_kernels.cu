@@ -54,6 +54,29 @@ void launch_bernoulli(int K, bool stats, const DScene& S, const DGuide* g, const
 #undef C_
 }
 
+void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                   int* queue, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::walk_p(stats, S, c, w, P, ctx, queue, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_bern_p(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                   uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
+                   int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::bern_p(stats, S, g, c, w, key, offset, P, o, ctx, queue, bs, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key,
+                       uint64_t offset, const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
+                       const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::bern_round(stats, S, g, c, key, offset, P, ctx, queue, list, n_list, base, nbest, t0, TB, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
 int blocks_per_sm(int which, int K, bool stats, int block) {
   int n = 1;
 #define C_(KK) n = KLaunch<KK>::blocks_per_sm(which, stats, block)

@@ -42,7 +42,16 @@ struct DOut {
 
 struct DCtx {
   int* err;                      // device error word
-  unsigned long long* stats;     // [12] counters (mpg_stats layout)
+  unsigned long long* stats;     // [16] counters of the kernel family (mpg_stats layout)
+};
+
+// Scratch of the persistent Bernoulli pass and its trial rounds.
+struct DBernScratch {
+  int T1;                  // trials of the first pass
+  int* list[2];            // overflow chain lists (ping-pong), region list + base
+  int* n_list[2];          // their lengths (device)
+  const int* base;         // start of this chain length's region (device)
+  unsigned* nbest;         // [B] first successful trial of the current round
 };
 
 void launch_seed(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
@@ -69,7 +78,30 @@ struct KLaunch {
   static void bernoulli(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                         uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
                         cudaStream_t st);
+  static void walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                     int* queue, int grid, int block, cudaStream_t st);
+  static void bern_p(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                     uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
+                     int block, cudaStream_t st);
+  static void bern_round(bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
+                         const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
+                         const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);
   static int blocks_per_sm(int which, bool stats, int block);
 };
+
+// Persistent-mode launchers by chain length (dispatch to KLaunch<K>).
+void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                   int* queue, int grid, int block, cudaStream_t st);
+void launch_bern_p(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                   uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
+                   int block, cudaStream_t st);
+void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key,
+                       uint64_t offset, const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
+                       const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);
+// Ends a trial round: chains with a success get N, chains past the cap are
+// capped, the rest move to the next list.
+void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
+                        const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
+                        int sms, cudaStream_t st);
 
 }  // namespace mpg

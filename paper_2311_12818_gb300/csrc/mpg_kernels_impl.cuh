@@ -231,6 +231,40 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
 
 
 }  // namespace kern
+}  // namespace mpg
+
+#include "mpg_persistent.cuh"
+
+namespace mpg {
+
+template <int K>
+void KLaunch<K>::walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                        int* queue, int grid, int block, cudaStream_t st) {
+  if (stats) kern::k_walk_p<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
+  else kern::k_walk_p<K, false><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
+}
+
+template <int K>
+void KLaunch<K>::bern_p(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
+                        uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
+                        int block, cudaStream_t st) {
+  DGuide gg = g ? *g : DGuide{};
+  if (stats) kern::k_bern_p<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
+  else kern::k_bern_p<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
+}
+
+template <int K>
+void KLaunch<K>::bern_round(bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
+                            const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
+                            const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st) {
+  DGuide gg = g ? *g : DGuide{};
+  if (stats)
+    kern::k_bern_round<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
+                                                         n_list, base, nbest, t0, TB);
+  else
+    kern::k_bern_round<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
+                                                          n_list, base, nbest, t0, TB);
+}
 
 template <int K>
 void KLaunch<K>::seed(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
@@ -269,7 +303,10 @@ int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   if (which == 0) fn = stats ? (const void*)kern::k_seed<K, true> : (const void*)kern::k_seed<K, false>;
   else if (which == 1) fn = stats ? (const void*)kern::k_walk<K, true> : (const void*)kern::k_walk<K, false>;
   else if (which == 2) fn = stats ? (const void*)kern::k_contrib<K, true> : (const void*)kern::k_contrib<K, false>;
-  else fn = stats ? (const void*)kern::k_bernoulli<K, true> : (const void*)kern::k_bernoulli<K, false>;
+  else if (which == 3) fn = stats ? (const void*)kern::k_bernoulli<K, true> : (const void*)kern::k_bernoulli<K, false>;
+  else if (which == 4) fn = stats ? (const void*)kern::k_walk_p<K, true> : (const void*)kern::k_walk_p<K, false>;
+  else if (which == 5) fn = stats ? (const void*)kern::k_bern_p<K, true> : (const void*)kern::k_bern_p<K, false>;
+  else fn = stats ? (const void*)kern::k_bern_round<K, true> : (const void*)kern::k_bern_round<K, false>;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 1;
   return n > 0 ? n : 1;
