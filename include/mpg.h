@@ -158,7 +158,7 @@ mpg_status mpg_ctx_sync(mpg_ctx* ctx, cudaStream_t stream);
 /* Counters of one kernel family (kind = MPG_KERNEL_*) or of all (kind = -1);
  * waits for `stream`; reset != 0 clears them afterwards.  out may be NULL. */
 mpg_status mpg_ctx_stats(mpg_ctx* ctx, int32_t kind, mpg_stats* out, int32_t reset, cudaStream_t stream);
-/* Work counters on (default) or off; off selects kernels without the tallies. */
+/* Work counters on (default) or off; off skips writing them. */
 mpg_status mpg_ctx_set_stats(mpg_ctx* ctx, int32_t on);
 /* Launch timing: when on, every kernel launch of the library is bracketed by
  * CUDA events recorded on the stream it is launched on.  mpg_ctx_profile sums

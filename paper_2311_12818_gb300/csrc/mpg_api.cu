@@ -339,7 +339,7 @@ void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn) {
   }
 }
 
-DCtx dctx(mpg_ctx* ctx, int kind) { return DCtx{ctx->d_err, ctx->d_stats + 16 * kind}; }
+DCtx dctx(mpg_ctx* ctx, int kind) { return DCtx{ctx->d_err, ctx->stats_on ? ctx->d_stats + 16 * kind : nullptr}; }
 
 // Runs fn(K, stream) for each planned K, on forked streams when concurrent.
 template <class F>

@@ -664,19 +664,29 @@ __device__ __forceinline__ bool scatter(const DSurf& sf, float3 n, float3 d, boo
   return true;
 }
 
+// Bin of a direction: the theta bin counts the FP32 edges cos(theta_j) above
+// w.z; the phi bin counts, within the half plane of w, the edge vectors
+// (c_j, s_j) that w is counter-clockwise of, by the exact FP64 sign of
+// c_j y - s_j x (a product of two FP32 values is exact in FP64).  Both
+// predicates are monotone in j, so each count is a binary search.
 __device__ __forceinline__ int guide_bin(const DGuide& g, float3 w) {
-  int it = 0;
-  for (int j = 1; j < g.n_theta; ++j) it += (w.z < __ldg(g.cos_theta + j)) ? 1 : 0;
+  int lo = 1, hi = g.n_theta;  // count of j in [1, n_theta) with w.z < cos_theta[j]
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (w.z < __ldg(g.cos_theta + mid)) lo = mid + 1; else hi = mid;
+  }
+  int it = lo - 1;
   bool upper = (w.y > 0.0f) || (w.y == 0.0f && w.x >= 0.0f);
   int half = g.n_phi >> 1;
-  int ip = upper ? 0 : half;
   int j0 = upper ? 1 : half + 1, j1 = upper ? half : g.n_phi;
   double x = (double)w.x, y = (double)w.y;
-  for (int j = j0; j < j1; ++j) {
-    // exact sign: products of two FP32 values are exact in FP64
-    double cr = __dsub_rn(__dmul_rn((double)__ldg(g.phi_cos + j), y), __dmul_rn((double)__ldg(g.phi_sin + j), x));
-    ip += cr >= 0.0 ? 1 : 0;
+  int a = j0, b = j1;  // first j in [j0, j1) where w is no longer counter-clockwise of edge j
+  while (a < b) {
+    int mid = (a + b) >> 1;
+    double cr = __dsub_rn(__dmul_rn((double)__ldg(g.phi_cos + mid), y), __dmul_rn((double)__ldg(g.phi_sin + mid), x));
+    if (cr >= 0.0) a = mid + 1; else b = mid;
   }
+  int ip = (upper ? 0 : half) + (a - j0);
   return it * g.n_phi + ip;
 }
 
@@ -715,7 +725,8 @@ __device__ __forceinline__ float p0_pdf(const DScene& S, float3 xD, float3 w) {
 template <int K, bool kStats>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
-                          Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt) {
+                          Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
+                          bool want_pdf = true) {
   if (kStats) cnt.seeds++;
   uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
@@ -777,8 +788,10 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     w = make_float3(st * cp, st * sp, ct);
   }
   if (dot(w, e.nD) <= 0.0f) return false;
-  float p0 = p0_pdf(S, e.xD, w);
-  if (use_guide) {
+  pdf = 0.0f;
+  if (!want_pdf) {
+  } else if (use_guide) {
+    float p0 = p0_pdf(S, e.xD, w);
     int bin = guide_bin(*g, w);
     uint64_t cnt_b = __ldg(reinterpret_cast<const unsigned long long*>(g->counts + (size_t)cell * g->bins + bin));
     int it = bin / g->n_phi;
@@ -786,7 +799,7 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     float ph = (float)((double)cnt_b / (double)total) / ((6.28318530717958647f / (float)g->n_phi) * dcos);
     pdf = P.alpha * p0 + (1.0f - P.alpha) * ph;
   } else {
-    pdf = p0;
+    pdf = p0_pdf(S, e.xD, w);
   }
   float3 o = e.xD, d = w;
 #pragma unroll
@@ -841,7 +854,7 @@ __device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 
 // FP32 residual.  Returns false for an inadmissible chain.
 template <int K, bool kStats>
 __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
-                             float& kappa, float& mismatch, float& cmax, int* err, Counters& cnt) {
+                             float& kappa, float& mismatch, float& cmax, float& kappa_err, int* err, Counters& cnt) {
   VB vb[K];
   float3 tu[K], tv[K];
   float cn2;
@@ -912,7 +925,11 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
   // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
   // near total internal reflection.
+  // kappa_err (out): FP32 relative error estimate of the transmittances, which
+  // lose digits like 1/c2^2 as the refracted cosine c2 goes to zero (grazing
+  // exit near total internal reflection).
   float kap = 1.0f;
+  kappa_err = 0.0f;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const DSurf& sf = S.s[ch.surf[i]];
@@ -929,6 +946,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
       float r = n1 / n2;
       kap *= Tr * r * r;
+      kappa_err = fmaxf(kappa_err, 2.4e-7f / fmaxf(fminf(ci, co) * fminf(ci, co), 1e-30f));
     } else {
       float e2 = vb[i].front ? sf.etaB : sf.etaF;
       kap *= fresnel(ci, vb[i].ei, e2);

@@ -318,7 +318,7 @@ __device__ bool thomas64(const VB64 (&vb)[K], double (&R)[K][2][M], double sing_
 // solution in FP64 (no step brings max|C| under tol) or G cannot be formed.
 template <int K>
 __device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, double tol, double sing_eps, int steps,
-                             double& G) {
+                             double& G, double& kappa) {
   Frame64 f[K];
   VB64 vb[K];
   double C[2 * K], cmax;
@@ -372,6 +372,37 @@ __device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, dou
   }
   double det = fabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
   G = point ? det : dot(d3(e.nD), w) * det;
+  // kappa in FP64: mirror 1, dielectric R -> F, T -> (T_s + T_p)/2 (eta_i/eta_o)^2
+  kappa = 1.0;
+  D3 xD = d3(e.xD), xL = d3(e.xL);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const DSurf& sf = S.s[ch.surf[i]];
+    if (sf.mat == MAT_MIRROR) continue;
+    D3 xp = i == 0 ? xD : f[i > 0 ? i - 1 : 0].p;
+    D3 xn = i == K - 1 ? xL : f[i < K - 1 ? i + 1 : 0].p;
+    D3 wi = unit(xp - f[i].p), wo = unit(xn - f[i].p);
+    double ci = fabs(dot(wi, f[i].n));
+    bool front = dot(wi, f[i].n) > 0.0;
+    double n1 = front ? sf.etaF : sf.etaB;
+    if ((e.tau >> i) & 1u) {
+      double n2 = front ? sf.etaB : sf.etaF;
+      double co = fabs(dot(wo, f[i].n));
+      double num = 4.0 * n1 * n2 * ci * co, ds = n1 * ci + n2 * co, dp = n2 * ci + n1 * co;
+      double r = n1 / n2;
+      kappa *= 0.5 * (num / (ds * ds) + num / (dp * dp)) * r * r;
+    } else {
+      double n2 = front ? sf.etaB : sf.etaF;
+      double s2 = (n1 / n2) * (n1 / n2) * (1.0 - ci * ci);
+      double F = 1.0;
+      if (s2 < 1.0) {
+        double c2 = sqrt(1.0 - s2);
+        double rs = (n1 * ci - n2 * c2) / (n1 * ci + n2 * c2), rp = (n2 * ci - n1 * c2) / (n2 * ci + n1 * c2);
+        F = 0.5 * (rs * rs + rp * rp);
+      }
+      kappa *= F;
+    }
+  }
   return true;
 }
 

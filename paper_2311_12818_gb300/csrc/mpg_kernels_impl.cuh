@@ -18,6 +18,7 @@ struct Tally {
 
 // Warp-reduced flush of the tallies into the family's counters (mpg_stats order).
 __device__ __forceinline__ void flush(const Tally& t, unsigned long long* stats) {
+  if (!stats) return;
   __syncwarp();
   uint32_t v[15] = {t.c.newton, t.c.rows, t.c.full_evals, t.c.c_evals, t.c.casts, t.c.sphere, t.c.plane,
                     t.c.node, t.c.tri, t.walks, t.conv, t.c.ggt, t.trials, t.c.seeds, t.c.ggt64};
@@ -144,18 +145,19 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       Chain<K> ch;
       load_chain<K>(c, b, ch);
       Ends e = load_ends(c, b);
-      float mismatch = 0.0f, cmax = 0.0f;
-      adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, ctx.err, t.c);
+      float mismatch = 0.0f, cmax = 0.0f, kerr = 0.0f;
+      adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, kerr, ctx.err, t.c);
       // Escalate to FP64 where FP32 is not enough: long chains, a geometry term
       // whose two reciprocal FP32 evaluations disagree, or a walk that stopped
       // at the FP32 resolution of C.  The vertices are first polished by FP64
       // Newton steps and written back.
-      if (adm && (K >= 6 || mismatch > P.fp64_tol || !(cmax < P.tol))) {
+      if (adm && (K >= 6 || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol))) {
         Chain64<K> c64;
         to64<K>(S, ch, c64);
-        double g;
-        if (polish_ggt64<K>(S, c64, e, (double)P.tol, (double)P.sing_eps, 3, g)) {
+        double g, k64;
+        if (polish_ggt64<K>(S, c64, e, (double)P.tol, (double)P.sing_eps, 3, g, k64)) {
           G = (float)g;
+          kap = (float)k64;
 #pragma unroll
           for (int v = 0; v < K; ++v) {
             ch.x[v] = make_float3((float)c64.x[v].x, (float)c64.x[v].y, (float)c64.x[v].z);
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
         float pdf;
         Ends et = e;
         if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c))
+                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c, false))
           continue;
         if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
         et.tau = tau;
@@ -240,8 +242,7 @@ namespace mpg {
 template <int K>
 void KLaunch<K>::walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                         int* queue, int grid, int block, cudaStream_t st) {
-  if (stats) kern::k_walk_p<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
-  else kern::k_walk_p<K, false><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
+  kern::k_walk_p<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
 }
 
 template <int K>
@@ -249,8 +250,7 @@ void KLaunch<K>::bern_p(bool stats, const DScene& S, const DGuide* g, const DCha
                         uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
                         int block, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (stats) kern::k_bern_p<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
-  else kern::k_bern_p<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
+  kern::k_bern_p<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
 }
 
 template <int K>
@@ -258,34 +258,27 @@ void KLaunch<K>::bern_round(bool stats, const DScene& S, const DGuide* g, const 
                             const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
                             const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (stats)
-    kern::k_bern_round<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
+  kern::k_bern_round<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
                                                          n_list, base, nbest, t0, TB);
-  else
-    kern::k_bern_round<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
-                                                          n_list, base, nbest, t0, TB);
 }
 
 template <int K>
 void KLaunch<K>::seed(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                       uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (stats) kern::k_seed<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
-  else kern::k_seed<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
+  kern::k_seed<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
 }
 
 template <int K>
 void KLaunch<K>::walk(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx, int grid,
                       int block, cudaStream_t st) {
-  if (stats) kern::k_walk<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx);
-  else kern::k_walk<K, false><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+  kern::k_walk<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx);
 }
 
 template <int K>
 void KLaunch<K>::contrib(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx,
                          int grid, int block, cudaStream_t st) {
-  if (stats) kern::k_contrib<K, true><<<grid, block, 0, st>>>(S, c, w, P, o, ctx);
-  else kern::k_contrib<K, false><<<grid, block, 0, st>>>(S, c, w, P, o, ctx);
+  kern::k_contrib<K, true><<<grid, block, 0, st>>>(S, c, w, P, o, ctx);
 }
 
 template <int K>
@@ -293,20 +286,19 @@ void KLaunch<K>::bernoulli(bool stats, const DScene& S, const DGuide* g, const D
                            uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
                            cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (stats) kern::k_bernoulli<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
-  else kern::k_bernoulli<K, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  kern::k_bernoulli<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
 }
 
 template <int K>
 int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   const void* fn;
-  if (which == 0) fn = stats ? (const void*)kern::k_seed<K, true> : (const void*)kern::k_seed<K, false>;
-  else if (which == 1) fn = stats ? (const void*)kern::k_walk<K, true> : (const void*)kern::k_walk<K, false>;
-  else if (which == 2) fn = stats ? (const void*)kern::k_contrib<K, true> : (const void*)kern::k_contrib<K, false>;
-  else if (which == 3) fn = stats ? (const void*)kern::k_bernoulli<K, true> : (const void*)kern::k_bernoulli<K, false>;
-  else if (which == 4) fn = stats ? (const void*)kern::k_walk_p<K, true> : (const void*)kern::k_walk_p<K, false>;
-  else if (which == 5) fn = stats ? (const void*)kern::k_bern_p<K, true> : (const void*)kern::k_bern_p<K, false>;
-  else fn = stats ? (const void*)kern::k_bern_round<K, true> : (const void*)kern::k_bern_round<K, false>;
+  if (which == 0) fn = (const void*)kern::k_seed<K, true>;
+  else if (which == 1) fn = (const void*)kern::k_walk<K, true>;
+  else if (which == 2) fn = (const void*)kern::k_contrib<K, true>;
+  else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true>;
+  else if (which == 4) fn = (const void*)kern::k_walk_p<K, true>;
+  else if (which == 5) fn = (const void*)kern::k_bern_p<K, true>;
+  else fn = (const void*)kern::k_bern_round<K, true>;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 1;
   return n > 0 ? n : 1;

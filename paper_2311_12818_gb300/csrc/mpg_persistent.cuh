@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(128) k_bern_p(const __grid_constant__ DScene S
       float pdf;
       Ends e = L.w.e;
       if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, L.cell, e.tau, P.tau_random != 0, key,
-                           (uint64_t)b + offset, (uint32_t)L.t, P, L.w.ch, tau, pdf, ctx.err, t.c) &&
+                           (uint64_t)b + offset, (uint32_t)L.t, P, L.w.ch, tau, pdf, ctx.err, t.c, false) &&
           tau == e.tau) {
         walk_begin(L.w);
         L.walking = true;
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
         float pdf;
         uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
         if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                             (uint64_t)bb + offset, (uint32_t)tt, P, L.ch, tau, pdf, ctx.err, t.c) &&
+                             (uint64_t)bb + offset, (uint32_t)tt, P, L.ch, tau, pdf, ctx.err, t.c, false) &&
             tau == e.tau) {
           b = bb;
           tr = tt;
