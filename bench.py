@@ -277,6 +277,7 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "detail": {"converged_per_step": conv / args.steps, "walks_per_step": total["walks"] / args.steps,
                    "trials_per_step": total["trials"] / args.steps,
+                   "fp64_geometry_terms_per_step": total["ggt_fp64"] / args.steps,
                    "step_ms": [round(x, 4) for x in step_ms],
                    "step_fp32_tflops": step_flops / (t_ms * 1e-3) / 1e12 if world == 1 else None,
                    "families": {n: {"ms_per_step": f["ms"] / args.steps, "launches": f["launches"],

@@ -925,9 +925,9 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
   // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
   // near total internal reflection.
-  // kappa_err (out): FP32 relative error estimate of the transmittances, which
-  // lose digits like 1/c2^2 as the refracted cosine c2 goes to zero (grazing
-  // exit near total internal reflection).
+  // kappa_err (out): FP32 relative error estimate of the transmittances.  The
+  // cosines come from the chain's own unit directions (absolute error ~1e-7),
+  // and T_s, T_p scale like the smaller cosine at grazing incidence or exit.
   float kap = 1.0f;
   kappa_err = 0.0f;
 #pragma unroll
@@ -946,7 +946,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
       float r = n1 / n2;
       kap *= Tr * r * r;
-      kappa_err = fmaxf(kappa_err, 2.4e-7f / fmaxf(fminf(ci, co) * fminf(ci, co), 1e-30f));
+      kappa_err = fmaxf(kappa_err, 1.2e-7f / fmaxf(fminf(ci, co), 1e-30f));
     } else {
       float e2 = vb[i].front ? sf.etaB : sf.etaF;
       kap *= fresnel(ci, vb[i].ei, e2);

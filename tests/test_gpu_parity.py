@@ -51,11 +51,24 @@ def _gpu_pipeline(M, ctx, wl, guide=None, P=None):
 
 
 def _oracle_pipeline(wl, guide=None):
+    """Oracle at the walk tolerance for flags and trial counts; the contribution
+    of each converged chain is evaluated after polishing it to max|C| < 1e-12,
+    since kappa and G at grazing or near-caustic chains change by up to 1e-3
+    relative between the tolerance and the solution itself."""
     sc = O.Scene(wl)
     seeds = O.sample_seeds(wl, sc, guide)
     ch = O.walk(wl, sc, seeds)
     con = O.contribution(wl, sc, ch)
     N, capped = O.bernoulli(wl, sc, ch, con["admissible"], guide)
+    tight = dataclasses.replace(wl, params=dataclasses.replace(wl.params, tol=1e-12))
+    conv = dict(x=ch["x"], surf=ch["surf"], prim=ch["prim"], bary=ch["bary"], tau=ch["tau"],
+                valid=(ch["status"] == 1).astype(np.uint8))
+    pol = O.walk(tight, sc, conv)
+    pol["status"] = np.where(pol["status"] == 1, ch["status"], 0).astype(np.uint8)
+    cp = O.contribution(wl, sc, pol)
+    # flags and trial counts stay those of the walk at the tolerance
+    con = dict(G=cp["G"], kappa=cp["kappa"], T=cp["T"],
+               admissible=(con["admissible"] & (cp["admissible"] | (ch["status"] != 1))).astype(np.uint8))
     return sc, seeds, ch, con, N, capped
 
 
