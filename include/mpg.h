@@ -208,6 +208,27 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guid
 mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* chains,
                              const mpg_params* params, cudaStream_t stream);
 
+/* Allocation-free variant of mpg_manifold_walk in the batched (persistent
+ * work-queue) form; the paper has no counterpart -- it exists for callers that
+ * must not allocate device memory during a call: renderers whose frame loop
+ * forbids cudaMalloc (it synchronises the device and can stall the frame),
+ * codes whose device memory is owned by their own pool allocator, and
+ * callers that cannot touch the runtime allocator while another thread holds a
+ * global-mode stream capture.  Same inputs, outputs and results as
+ * mpg_manifold_walk with walk_mode MPG_WALK_BATCHED on the current device, with
+ * no context: work counters and launch timing are not kept.
+ * Scratch: a fixed device array inside the library (about 4 MiB plus the
+ * counters, held by every GPU that loads the library until the process exits),
+ * so one call takes at most 1,048,576 chains; larger batches are rejected with
+ * MPG_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.  Every call shares the array and clears what must start at zero;
+ * calls that overlap on the GPU (two streams, or two host threads) race on it.
+ * The scene must live on the current device. */
+mpg_status mpg_manifold_walk_noalloc(const mpg_scene* scene, mpg_chains* chains,
+                                     const mpg_params* params, cudaStream_t stream);
+
 /* S7-S9 -- contribution of each converged chain (Eq. ThroughputEval):
  * admissibility (unoccluded segments, vertex types consistent with the sides,
  * positive end cosines), the generalized geometry term G by the implicit

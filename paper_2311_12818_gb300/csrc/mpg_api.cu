@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -851,3 +852,85 @@ mpg_status mpg_fp32_peak(mpg_ctx* ctx, double* flops, cudaStream_t st) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free manifold walk.  Its scratch (work-queue counters, length
+// buckets and the bucketed chain order) is a file-scope device array instead
+// of context memory, so a call needs no device allocation at all.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_CHAINS = 1 << 20;
+
+struct NoAllocScratch {
+  int queue[16 * (MAXK + 1)];
+  int count[MAXK + 1];
+  int base[MAXK + 1];
+  int cursor[MAXK + 1];
+  int err;
+  int order[NOALLOC_MAX_CHAINS];
+};
+
+// Held by every GPU that loads the library, for the life of the process.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+NoAllocScratch* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device.  In host code the
+// array's name only stands for it, so it is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached.
+mpg_status noalloc_scratch(int device, NoAllocScratch** out) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) return fail(MPG_ERR_UNSUPPORTED, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MPG_ERR_CUDA, "cudaGetSymbolAddress of the walk scratch: %s", cudaGetErrorString(e));
+    g_noalloc_addr[device] = (NoAllocScratch*)p;
+  }
+  *out = g_noalloc_addr[device];
+  return MPG_OK;
+}
+
+}  // namespace
+
+extern "C" mpg_status mpg_manifold_walk_noalloc(const mpg_scene* sc, mpg_chains* chains, const mpg_params* P,
+                                                cudaStream_t st) {
+  if (!sc) return fail(MPG_ERR_INVALID_ARG, "scene is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;
+  mpg_status s;
+  if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  if (chains->B > NOALLOC_MAX_CHAINS)
+    return fail(MPG_ERR_INVALID_ARG, "mpg_manifold_walk_noalloc takes at most %d chains per call (got %d)",
+                NOALLOC_MAX_CHAINS, chains->B);
+  int device = -1;
+  CUDA_TRY(cudaGetDevice(&device));
+  if (device != sc->device) return fail(MPG_ERR_INVALID_ARG, "the scene lives on device %d, current is %d", sc->device, device);
+  NoAllocScratch* scr = nullptr;
+  if ((s = noalloc_scratch(device, &scr))) return s;
+  int sms = 1;
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  // what must start at zero: the queue counters and the bucket sizes
+  CUDA_TRY(cudaMemsetAsync(scr->queue, 0, sizeof(scr->queue), st));
+  DChains c = to_dev(chains);
+  DWork w{nullptr, nullptr, nullptr};
+  int k_lo = 1, k_hi = MAXK;
+  if (P->k_uniform >= 1) {
+    k_lo = k_hi = P->k_uniform;
+  } else {
+    launch_bucket(c.k, c.status, ST_SEEDED, c.B, scr->count, scr->base, scr->cursor, scr->order, sms, st);
+    w = DWork{scr->order, scr->base, scr->count};
+  }
+  DCtx dc{&scr->err, nullptr};
+  int block = block_of(P);
+  for (int K = k_lo; K <= k_hi; ++K) {
+    int per_sm = blocks_per_sm(4, K, false, block);
+    int grid = std::max(1, std::min(sms * per_sm, (c.B + block - 1) / block));
+    launch_walk_p(K, false, sc->S, c, w, *P, dc, scr->queue + 16 * K, grid, block, st);
+  }
+  LAUNCH_CHECK("walk (no-alloc)");
+  return MPG_OK;
+}

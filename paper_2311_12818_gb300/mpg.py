@@ -65,7 +65,8 @@ class mpg_stats(C.Structure):
 EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy", "mpg_ctx_sync",
            "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
-           "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak"]
+           "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
+           "mpg_manifold_walk_noalloc"]
 
 _lib = None
 
@@ -96,6 +97,7 @@ def lib():
         L.mpg_sample_seeds.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                        C.POINTER(mpg_params), vp]
         L.mpg_manifold_walk.argtypes = [vp, vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
+        L.mpg_manifold_walk_noalloc.argtypes = [vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
         L.mpg_chain_contribution.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                              C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
@@ -292,6 +294,13 @@ def mpg_sample_seeds(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, 
 def mpg_manifold_walk(ctx, scene, chains, params, stream=None):
     cs = chains.struct()
     _check(lib().mpg_manifold_walk(ctx.h, scene.h, C.byref(cs), C.byref(params), _stream(stream)))
+
+
+def mpg_manifold_walk_noalloc(scene, chains, params, stream=None):
+    """Batched manifold walk that allocates no device memory (fixed library
+    scratch, at most 1,048,576 chains per call; overlapping calls race)."""
+    cs = chains.struct()
+    _check(lib().mpg_manifold_walk_noalloc(scene.h, C.byref(cs), C.byref(params), _stream(stream)))
 
 
 def mpg_chain_contribution(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, out=None, stream=None):
