@@ -65,12 +65,19 @@ struct mpg_ctx {
   int* d_base = nullptr;
   int* d_cursor = nullptr;
   float* d_scratch = nullptr;
-  int* d_queue = nullptr;        // [MAXK+1][16] work-queue counters of the persistent launches
+  int* d_queue = nullptr;        // [MAXK+1][32] work-queue counters of the persistent launches
   int* d_nlist = nullptr;        // [2][MAXK+1] overflow list lengths
   int* d_zero = nullptr;         // [MAXK+1] zeros (list regions when chains are not bucketed)
   int* d_list[2] = {nullptr, nullptr};
   unsigned* d_nbest = nullptr;
   int bern_cap = 0;
+  // trial chain state of the Bernoulli rounds (same layout as mpg_chains)
+  float* t_x = nullptr;
+  int32_t* t_surf = nullptr;
+  int32_t* t_prim = nullptr;
+  float* t_bary = nullptr;
+  uint8_t* t_status = nullptr;
+  uint8_t* t_iters = nullptr;
   bool stats_on = true;
   cudaStream_t aux[MAXK] = {};
   cudaEvent_t ev_fork = nullptr;
@@ -393,7 +400,7 @@ mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
             cudaMalloc(&c->d_base, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_cursor, sizeof(int) * 16) == cudaSuccess &&
             cudaMalloc(&c->d_scratch, sizeof(float) * 16) == cudaSuccess &&
-            cudaMalloc(&c->d_queue, sizeof(int) * 16 * (MAXK + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_queue, sizeof(int) * 32 * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_nlist, sizeof(int) * 2 * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_zero, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_zero, 0, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
@@ -418,6 +425,8 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
   cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero);
   cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest);
+  cudaFree(c->t_x); cudaFree(c->t_surf); cudaFree(c->t_prim); cudaFree(c->t_bary); cudaFree(c->t_status);
+  cudaFree(c->t_iters);
   for (int i = 0; i < MAXK; ++i) {
     if (c->aux[i]) cudaStreamDestroy(c->aux[i]);
     if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
@@ -680,10 +689,10 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
   DCtx dc = dctx(ctx, MPG_KERNEL_WALK);
   int block = block_of(P);
   if (P->walk_mode == MPG_WALK_BATCHED) {
-    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 16 * (MAXK + 1), st));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 32 * (MAXK + 1), st));
     return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
       timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
-        launch_walk_p(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, ctx->d_queue + 16 * K,
+        launch_walk_p(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, ctx->d_queue + 32 * K,
                       grid_of(ctx, 4, K, block, c.B, true), block, s2);
       });
     });
@@ -727,18 +736,29 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   const bool batched = P->walk_mode == MPG_WALK_BATCHED;
   if (batched) {
     if (ctx->bern_cap < c.B) {
-      cudaFree(ctx->d_list[0]); cudaFree(ctx->d_list[1]); cudaFree(ctx->d_nbest);
-      ctx->d_list[0] = ctx->d_list[1] = nullptr;
-      ctx->d_nbest = nullptr;
+      void** bufs[] = {(void**)&ctx->d_list[0], (void**)&ctx->d_list[1], (void**)&ctx->d_nbest, (void**)&ctx->t_x,
+                       (void**)&ctx->t_surf, (void**)&ctx->t_prim, (void**)&ctx->t_bary, (void**)&ctx->t_status,
+                       (void**)&ctx->t_iters};
+      for (void** b : bufs) { cudaFree(*b); *b = nullptr; }
       ctx->bern_cap = 0;
-      CUDA_TRY(cudaMalloc(&ctx->d_list[0], sizeof(int) * (size_t)c.B));
-      CUDA_TRY(cudaMalloc(&ctx->d_list[1], sizeof(int) * (size_t)c.B));
-      CUDA_TRY(cudaMalloc(&ctx->d_nbest, sizeof(unsigned) * (size_t)c.B));
+      size_t n = (size_t)c.B;
+      CUDA_TRY(cudaMalloc(&ctx->d_list[0], sizeof(int) * n));
+      CUDA_TRY(cudaMalloc(&ctx->d_list[1], sizeof(int) * n));
+      CUDA_TRY(cudaMalloc(&ctx->d_nbest, sizeof(unsigned) * n));
+      CUDA_TRY(cudaMalloc(&ctx->t_x, sizeof(float) * 3 * MAXK * n));
+      CUDA_TRY(cudaMalloc(&ctx->t_surf, sizeof(int32_t) * MAXK * n));
+      CUDA_TRY(cudaMalloc(&ctx->t_prim, sizeof(int32_t) * MAXK * n));
+      CUDA_TRY(cudaMalloc(&ctx->t_bary, sizeof(float) * 2 * MAXK * n));
+      CUDA_TRY(cudaMalloc(&ctx->t_status, n));
+      CUDA_TRY(cudaMalloc(&ctx->t_iters, n));
       ctx->bern_cap = c.B;
     }
-    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 16 * (MAXK + 1), st));
+    CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 32 * (MAXK + 1), st));
     CUDA_TRY(cudaMemsetAsync(ctx->d_nlist, 0, sizeof(int) * 2 * (MAXK + 1), st));
   }
+  DChains tc = c;  // trial chains: same separators and types, own vertex state
+  tc.x = ctx->t_x; tc.surf = ctx->t_surf; tc.prim = ctx->t_prim; tc.bary = ctx->t_bary;
+  tc.status = ctx->t_status; tc.iters = ctx->t_iters; tc.pdf = nullptr;
   s = run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_CONTRIB, s2, 1, [&] {
       launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
@@ -751,33 +771,44 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       return;
     }
-    // first pass: each lane runs trials 1..T1 of one chain; the rest go to
-    // rounds of TB = 8, 32, 128, ... parallel trials per remaining chain
-    DBernScratch bs;
-    bs.T1 = 8;
-    bs.list[0] = ctx->d_list[0];
-    bs.list[1] = ctx->d_list[1];
-    bs.n_list[0] = ctx->d_nlist + K;
-    bs.n_list[1] = ctx->d_nlist + (MAXK + 1) + K;
-    bs.base = plan.w.base ? plan.w.base + K : ctx->d_zero + K;
-    bs.nbest = ctx->d_nbest;
-    int* q = ctx->d_queue + 16 * K;
+    // Rounds t = 1..T1: every chain without a hit draws and walks trial t; the
+    // chains left after T1 go to rounds of TB = 8, 32, 128, ... parallel trials.
+    const int T1 = std::min(8, P->max_trials);
+    int* lists[2] = {ctx->d_list[0], ctx->d_list[1]};
+    int* counts[2] = {ctx->d_nlist, ctx->d_nlist + (MAXK + 1)};
+    const int* base = plan.w.base ? plan.w.base : ctx->d_zero;
+    int* q = ctx->d_queue + 32 * K;
+    int small_grid = ctx->sms * 4;
     timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-      launch_bern_p(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb, q + 1, bs,
-                    grid_of(ctx, 5, K, block, c.B, true), block, s2);
+      launch_trial_init(K, sc->S, c, plan.w, o, lists[0], base, counts[0], small_grid, s2);
     });
-    int t0 = bs.T1 + 1, TB = 8, cur = 0;
+    int cur = 0;
+    for (int t = 1; t <= T1; ++t) {
+      int nxt = 1 - cur;
+      cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
+      DWork tw{lists[cur], base, counts[cur]};
+      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 3, [&] {
+        launch_trial_seed(K, sc->S, guide ? &g : nullptr, c, tc, lists[cur], base, counts[cur], key, rng_offset, *P,
+                          dcb, t, grid_of(ctx, 5, K, block, c.B, true), block, s2);
+        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcb, q + t, grid_of(ctx, 4, K, block, c.B, true), block,
+                      s2);
+        launch_trial_check(K, sc->S, c, tc, o, lists[cur], base, counts[cur], t, t == T1, *P, lists[nxt], counts[nxt],
+                           ctx->d_nbest, small_grid, s2);
+      });
+      cur = nxt;
+    }
+    int t0 = T1 + 1, TB = 8;
     for (int r = 0; t0 <= P->max_trials && r < 14; ++r) {
       if (r == 13 || t0 + TB - 1 > P->max_trials) TB = P->max_trials - t0 + 1;  // the last round reaches the cap
       int t_end = t0 + TB - 1;
       int nxt = 1 - cur;
-      cudaMemsetAsync(bs.n_list[nxt], 0, sizeof(int), s2);
+      cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
-        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q + 2 + r,
-                          bs.list[cur], bs.n_list[cur], bs.base, bs.nbest, t0, TB,
+        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q + 10 + r,
+                          lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, TB,
                           grid_of(ctx, 6, K, block, c.B, true), block, s2);
-        launch_bern_finish(sc->S, c, o, bs.list[cur], bs.n_list[cur], bs.base, bs.nbest, t_end, P->max_trials,
-                           bs.list[nxt], bs.n_list[nxt], ctx->sms, s2);
+        launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
+                           lists[nxt], counts[nxt] + K, ctx->sms, s2);
       });
       t0 = t_end + 1;
       TB *= 4;

@@ -61,10 +61,25 @@ void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w
 #undef C_
 }
 
-void launch_bern_p(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
-                   uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
-                   int block, cudaStream_t st) {
-#define C_(KK) KLaunch<KK>::bern_p(stats, S, g, c, w, key, offset, P, o, ctx, queue, bs, grid, block, st)
+void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
+                       int* n_list, int grid, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::trial_init(S, c, w, o, list, base, n_list, grid, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_trial_seed(int K, const DScene& S, const DGuide* g, const DChains& c, const DChains& tc,
+                       const int* list, const int* base, const int* n_list, uint2 key, uint64_t offset,
+                       const mpg_params& P, DCtx ctx, int t, int grid, int block, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::trial_seed(S, g, c, tc, list, base, n_list, key, offset, P, ctx, t, grid, block, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
+void launch_trial_check(int K, const DScene& S, const DChains& c, const DChains& tc, DOut o, const int* list,
+                        const int* base, const int* n_list, int t, int last, const mpg_params& P, int* next,
+                        int* n_next, unsigned* nbest, int grid, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::trial_check(S, c, tc, o, list, base, n_list, t, last, P, next, n_next, nbest, grid, st)
   MPG_SWITCH(K, C_)
 #undef C_
 }

@@ -80,9 +80,14 @@ struct KLaunch {
                         cudaStream_t st);
   static void walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                      int* queue, int grid, int block, cudaStream_t st);
-  static void bern_p(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
-                     uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
-                     int block, cudaStream_t st);
+  static void trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base, int* n_list,
+                         int grid, cudaStream_t st);
+  static void trial_seed(const DScene& S, const DGuide* g, const DChains& c, const DChains& tc, const int* list,
+                         const int* base, const int* n_list, uint2 key, uint64_t offset, const mpg_params& P,
+                         DCtx ctx, int t, int grid, int block, cudaStream_t st);
+  static void trial_check(const DScene& S, const DChains& c, const DChains& tc, DOut o, const int* list,
+                          const int* base, const int* n_list, int t, int last, const mpg_params& P, int* next,
+                          int* n_next, unsigned* nbest, int grid, cudaStream_t st);
   static void bern_round(bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
                          const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
                          const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);
@@ -92,9 +97,14 @@ struct KLaunch {
 // Persistent-mode launchers by chain length (dispatch to KLaunch<K>).
 void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                    int* queue, int grid, int block, cudaStream_t st);
-void launch_bern_p(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
-                   uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
-                   int block, cudaStream_t st);
+void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
+                       int* n_list, int grid, cudaStream_t st);
+void launch_trial_seed(int K, const DScene& S, const DGuide* g, const DChains& c, const DChains& tc,
+                       const int* list, const int* base, const int* n_list, uint2 key, uint64_t offset,
+                       const mpg_params& P, DCtx ctx, int t, int grid, int block, cudaStream_t st);
+void launch_trial_check(int K, const DScene& S, const DChains& c, const DChains& tc, DOut o, const int* list,
+                        const int* base, const int* n_list, int t, int last, const mpg_params& P, int* next,
+                        int* n_next, unsigned* nbest, int grid, cudaStream_t st);
 void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key,
                        uint64_t offset, const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
                        const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);

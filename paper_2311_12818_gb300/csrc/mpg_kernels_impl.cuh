@@ -246,11 +246,25 @@ void KLaunch<K>::walk_p(bool stats, const DScene& S, const DChains& c, DWork w, 
 }
 
 template <int K>
-void KLaunch<K>::bern_p(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
-                        uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int* queue, DBernScratch bs, int grid,
-                        int block, cudaStream_t st) {
+void KLaunch<K>::trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
+                            int* n_list, int grid, cudaStream_t st) {
+  kern::k_trial_init<K><<<grid, 256, 0, st>>>(S, c, w, o, list, base, n_list);
+}
+
+template <int K>
+void KLaunch<K>::trial_seed(const DScene& S, const DGuide* g, const DChains& c, const DChains& tc, const int* list,
+                            const int* base, const int* n_list, uint2 key, uint64_t offset, const mpg_params& P,
+                            DCtx ctx, int t, int grid, int block, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  kern::k_bern_p<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx, queue, bs);
+  kern::k_trial_seed<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, tc, list, base, n_list, key, offset, P,
+                                                       ctx, t);
+}
+
+template <int K>
+void KLaunch<K>::trial_check(const DScene& S, const DChains& c, const DChains& tc, DOut o, const int* list,
+                             const int* base, const int* n_list, int t, int last, const mpg_params& P, int* next,
+                             int* n_next, unsigned* nbest, int grid, cudaStream_t st) {
+  kern::k_trial_check<K><<<grid, 256, 0, st>>>(S, c, tc, o, list, base, n_list, t, last, P, next, n_next, nbest);
 }
 
 template <int K>
@@ -297,7 +311,7 @@ int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   else if (which == 2) fn = (const void*)kern::k_contrib<K, true>;
   else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true>;
   else if (which == 4) fn = (const void*)kern::k_walk_p<K, true>;
-  else if (which == 5) fn = (const void*)kern::k_bern_p<K, true>;
+  else if (which == 5) fn = (const void*)kern::k_trial_seed<K, true>;
   else fn = (const void*)kern::k_bern_round<K, true>;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 1;

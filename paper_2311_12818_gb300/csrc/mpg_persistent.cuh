@@ -127,17 +127,12 @@ __global__ void __launch_bounds__(128) k_walk_p(const __grid_constant__ DScene S
 }
 
 // ---------------------------------------------------------------------------
-// Bernoulli trials (K5), first pass: one lane per admissible chain runs trials
-// 1..T1 in order; chains without a hit are appended to the overflow list.
+// Bernoulli trials (K5) in synchronous rounds: round t draws trial t for every
+// chain still without a hit (k_trial_seed), the persistent walk kernel walks
+// them all, and k_trial_check retires the hits and compacts the rest.  Each
+// kernel is uniform across lanes; the trial index of a chain's first hit is
+// the same as in a sequential loop over t.
 // ---------------------------------------------------------------------------
-template <int K>
-struct TrialLane {
-  WalkLane<K> w;
-  Chain<K> target;
-  uint32_t cell;
-  int t;           // current trial index
-  bool walking;    // a trial walk is in progress
-};
 
 // Final outputs of one chain.
 __device__ __forceinline__ void bern_write(const DScene& S, const DChains& c, const DOut& o, int b, float T, uint32_t N,
@@ -148,77 +143,74 @@ __device__ __forceinline__ void bern_write(const DScene& S, const DChains& c, co
   o.contrib[b] = (T > 0.0f && N > 0) ? S.L.area * T * (float)N / pn : 0.0f;
 }
 
-template <int K, bool kS>
-__global__ void __launch_bounds__(128) k_bern_p(const __grid_constant__ DScene S, DGuide g, int has_guide, DChains c,
-                                                DWork w, uint2 key, uint64_t offset, mpg_params P, DOut o, DCtx ctx,
-                                                int* queue, DBernScratch bern) {
-  Tally t = {};
+// Chains of this length with a contribution enter the rounds; the others get
+// their final (zero) outputs.
+template <int K>
+__global__ void __launch_bounds__(256) k_trial_init(const __grid_constant__ DScene S, DChains c, DWork w, DOut o,
+                                                    int* list, const int* base, int* n_list) {
   const int n = n_items<K>(w, c);
-  const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
-  const int T1 = min(bern.T1, P.max_trials);
-  TrialLane<K> L;
-  int b = -1;
-  bool done = false;
-  const unsigned FULL = 0xffffffffu;
-  while (true) {
-    int i = take_item(b < 0, queue, n, done);
-    if (i >= 0) {
-      int bb = item<K>(w, c, i);
-      if (bb >= 0) {
-        float T = o.T[bb];
-        if (T > 0.0f) {
-          b = bb;
-          load_chain<K>(c, b, L.target);
-          L.w.e = load_ends(c, b);
-          L.cell = c.cell ? c.cell[b / c.spq] : 0u;
-          L.t = 0;
-          L.walking = false;
-        } else {
-          bern_write(S, c, o, bb, 0.0f, 0, false);
-        }
-      }
-    }
-    bool any = __any_sync(FULL, b >= 0);
-    if (!any && done) break;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
     if (b < 0) continue;
-    if (!L.walking) {
-      // next trial: fresh seed from the same distribution, same n
-      L.t++;
-      t.trials++;
-      uint32_t tau;
-      float pdf;
-      Ends e = L.w.e;
-      if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, L.cell, e.tau, P.tau_random != 0, key,
-                           (uint64_t)b + offset, (uint32_t)L.t, P, L.w.ch, tau, pdf, ctx.err, t.c, false) &&
-          tau == e.tau) {
-        walk_begin(L.w);
-        L.walking = true;
-      }
-    } else {
-      int st = walk_pass<K, kS>(S, L.w, P, t.c);
-      if (st != RUNNING) {
-        L.walking = false;
-        t.walks++;
-        t.conv += st == ST_CONVERGED;
-        if (st == ST_CONVERGED && same_solution<K>(L.w.ch, L.target, eps2)) {
-          bern_write(S, c, o, b, o.T[b], (uint32_t)L.t, false);
-          b = -1;
-          continue;
-        }
-      }
+    if (o.T[b] > 0.0f) list[base[K] + atomicAdd(n_list + K, 1)] = b;
+    else bern_write(S, c, o, b, 0.0f, 0, false);
+  }
+}
+
+// Trial t of every listed chain: a fresh seed from the same distribution and
+// length (Sec. 5.7), written to the trial state; a seed with another type
+// sequence cannot reach the same solution and is marked invalid.
+template <int K, bool kS>
+__global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DScene S, DGuide g, int has_guide,
+                                                    DChains c, DChains tc, const int* list, const int* base,
+                                                    const int* n_list, uint2 key, uint64_t offset, mpg_params P,
+                                                    DCtx ctx, int t) {
+  Tally tl = {};
+  const int n = n_list[K];
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int b = list[base[K] + j];
+    Ends e = load_ends(c, b);
+    Chain<K> ch;
+    uint32_t tau;
+    float pdf;
+    tl.trials++;
+    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[b / c.spq] : 0u, e.tau,
+                               P.tau_random != 0, key, (uint64_t)b + offset, (uint32_t)t, P, ch, tau, pdf, ctx.err,
+                               tl.c, false) &&
+              tau == e.tau;
+    if (ok) store_chain<K>(tc, b, ch);
+    tc.status[b] = ok ? ST_SEEDED : ST_INVALID;
+  }
+  if (kS) flush(tl, ctx.stats);
+}
+
+// Retire the chains whose trial t walked to their own solution (FP64 distance
+// test); the others move to the next list.  After the last sequential round
+// the next list feeds the speculative rounds (nbest reset).
+template <int K>
+__global__ void __launch_bounds__(256) k_trial_check(const __grid_constant__ DScene S, DChains c, DChains tc, DOut o,
+                                                     const int* list, const int* base, const int* n_list, int t,
+                                                     int last, mpg_params P, int* next, int* n_next, unsigned* nbest) {
+  const int n = n_list[K];
+  const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int b = list[base[K] + j];
+    bool hit = false;
+    if (tc.status[b] == ST_CONVERGED) {
+      Chain<K> a, ref;
+      load_chain<K>(tc, b, a);
+      load_chain<K>(c, b, ref);
+      hit = same_solution<K>(a, ref, eps2);
     }
-    if (!L.walking && b >= 0 && L.t >= T1) {
-      if (T1 >= P.max_trials) {
-        bern_write(S, c, o, b, o.T[b], (uint32_t)P.max_trials, true);
-      } else {
-        int slot = atomicAdd(bern.n_list[0], 1);
-        bern.list[0][*bern.base + slot] = b;
-        bern.nbest[b] = 0xffffffffu;
-      }
-      b = -1;
+    if (hit) {
+      bern_write(S, c, o, b, o.T[b], (uint32_t)t, false);
+    } else if (t >= P.max_trials) {
+      bern_write(S, c, o, b, o.T[b], (uint32_t)P.max_trials, true);
+    } else {
+      next[base[K] + atomicAdd(n_next + K, 1)] = b;
+      if (last) nbest[b] = 0xffffffffu;
     }
   }
-  if (kS) flush(t, ctx.stats);
 }
 
 // ---------------------------------------------------------------------------
