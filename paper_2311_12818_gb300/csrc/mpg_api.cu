@@ -68,6 +68,9 @@ struct mpg_ctx {
   int* d_queue = nullptr;        // [MAXK+1][32] work-queue counters of the persistent launches
   int* d_nlist = nullptr;        // [2][MAXK+1] overflow list lengths
   int* d_zero = nullptr;         // [MAXK+1] zeros (list regions when chains are not bucketed)
+  int* d_fp64 = nullptr;         // [B] chains queued for the FP64 geometry term
+  int* d_fp64_count = nullptr;   // [MAXK+1] queue lengths per chain length
+  int fp64_cap = 0;
   int* d_list[2] = {nullptr, nullptr};
   unsigned* d_nbest = nullptr;
   int bern_cap = 0;
@@ -403,6 +406,7 @@ mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
             cudaMalloc(&c->d_queue, sizeof(int) * 32 * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_nlist, sizeof(int) * 2 * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_zero, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_fp64_count, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_zero, 0, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS) == cudaSuccess &&
@@ -423,7 +427,7 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaSetDevice(c->device);
   cudaFree(c->d_err); cudaFree(c->d_stats); cudaFree(c->d_order); cudaFree(c->d_count);
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
-  cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero);
+  cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero); cudaFree(c->d_fp64); cudaFree(c->d_fp64_count);
   cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest);
   cudaFree(c->t_x); cudaFree(c->t_surf); cudaFree(c->t_prim); cudaFree(c->t_bary); cudaFree(c->t_status);
   cudaFree(c->t_iters);
@@ -721,7 +725,15 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   if ((s = make_plan(ctx, chains, P, ST_CONVERGED, st, plan))) return s;
   DChains c = to_dev(chains);
   DCtx dcc = dctx(ctx, MPG_KERNEL_CONTRIB), dcb = dctx(ctx, MPG_KERNEL_BERNOULLI);
-  DOut o{G, kappa, T, trials, capped, contrib};
+  if (ctx->fp64_cap < c.B) {
+    cudaFree(ctx->d_fp64);
+    ctx->d_fp64 = nullptr;
+    ctx->fp64_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->d_fp64, sizeof(int) * (size_t)c.B));
+    ctx->fp64_cap = c.B;
+  }
+  CUDA_TRY(cudaMemsetAsync(ctx->d_fp64_count, 0, sizeof(int) * (MAXK + 1), st));
+  DOut o{G, kappa, T, trials, capped, contrib, ctx->d_fp64, nullptr, nullptr};
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
   int block = block_of(P);
   if (plan.w.order) {
@@ -760,9 +772,14 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   tc.x = ctx->t_x; tc.surf = ctx->t_surf; tc.prim = ctx->t_prim; tc.bary = ctx->t_bary;
   tc.status = ctx->t_status; tc.iters = ctx->t_iters; tc.pdf = nullptr;
   s = run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
-    timed(ctx, MPG_KERNEL_CONTRIB, s2, 1, [&] {
-      launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, o, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
+    // each length queues its FP64 chains in its own bucket region of the list
+    DOut oK = o;
+    oK.fp64_count = ctx->d_fp64_count + K;
+    oK.fp64_base = (plan.w.base ? plan.w.base : ctx->d_zero) + K;
+    timed(ctx, MPG_KERNEL_CONTRIB, s2, 2, [&] {
+      launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
                      s2);
+      launch_contrib64(K, sc->S, c, *P, oK, ctx->sms * 2, s2);
     });
     if (!batched) {
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
@@ -771,9 +788,11 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       return;
     }
-    // Rounds t = 1..T1: every chain without a hit draws and walks trial t; the
-    // chains left after T1 go to rounds of TB = 8, 32, 128, ... parallel trials.
-    const int T1 = std::min(8, P->max_trials);
+    // Rounds t = 1..T1 (T1 = 2): every chain without a hit draws and walks
+    // trial t; the chains left after T1 go to rounds of TB = 8, 32, 128, ...
+    // parallel trials.  Each round lasts as long as its slowest walk, so few
+    // rounds keep the pass short.
+    const int T1 = std::min(2, P->max_trials);
     int* lists[2] = {ctx->d_list[0], ctx->d_list[1]};
     int* counts[2] = {ctx->d_nlist, ctx->d_nlist + (MAXK + 1)};
     const int* base = plan.w.base ? plan.w.base : ctx->d_zero;

@@ -61,6 +61,13 @@ void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w
 #undef C_
 }
 
+void launch_contrib64(int K, const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid,
+                      cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::contrib64(S, c, P, o, grid, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
 void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
                        int* n_list, int grid, cudaStream_t st) {
 #define C_(KK) KLaunch<KK>::trial_init(S, c, w, o, list, base, n_list, grid, st)

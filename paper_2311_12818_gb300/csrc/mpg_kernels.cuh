@@ -38,6 +38,9 @@ struct DOut {
   uint32_t* trials;
   uint8_t* capped;
   float* contrib;
+  int* fp64_list;        // chains queued for the FP64 geometry term
+  int* fp64_count;       // length of this chain length's queue
+  const int* fp64_base;  // start of this chain length's region of fp64_list
 };
 
 struct DCtx {
@@ -82,6 +85,7 @@ struct KLaunch {
                      int* queue, int grid, int block, cudaStream_t st);
   static void trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base, int* n_list,
                          int grid, cudaStream_t st);
+  static void contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st);
   static void trial_seed(const DScene& S, const DGuide* g, const DChains& c, const DChains& tc, const int* list,
                          const int* base, const int* n_list, uint2 key, uint64_t offset, const mpg_params& P,
                          DCtx ctx, int t, int grid, int block, cudaStream_t st);
@@ -97,6 +101,8 @@ struct KLaunch {
 // Persistent-mode launchers by chain length (dispatch to KLaunch<K>).
 void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                    int* queue, int grid, int block, cudaStream_t st);
+void launch_contrib64(int K, const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid,
+                      cudaStream_t st);
 void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
                        int* n_list, int grid, cudaStream_t st);
 void launch_trial_seed(int K, const DScene& S, const DGuide* g, const DChains& c, const DChains& tc,

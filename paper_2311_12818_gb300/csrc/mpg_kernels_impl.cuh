@@ -148,27 +148,12 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       float mismatch = 0.0f, cmax = 0.0f, kerr = 0.0f;
       adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, kerr, ctx.err, t.c);
       // Escalate to FP64 where FP32 is not enough: long chains, a geometry term
-      // whose two reciprocal FP32 evaluations disagree, or a walk that stopped
-      // at the FP32 resolution of C.  The vertices are first polished by FP64
-      // Newton steps and written back.
-      if (adm && (K >= 6 || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol))) {
-        Chain64<K> c64;
-        to64<K>(S, ch, c64);
-        double g, k64;
-        if (polish_ggt64<K>(S, c64, e, (double)P.tol, (double)P.sing_eps, 3, g, k64)) {
-          G = (float)g;
-          kap = (float)k64;
-#pragma unroll
-          for (int v = 0; v < K; ++v) {
-            ch.x[v] = make_float3((float)c64.x[v].x, (float)c64.x[v].y, (float)c64.x[v].z);
-            ch.prim[v] = c64.prim[v];
-            ch.b1[v] = (float)c64.b1[v];
-            ch.b2[v] = (float)c64.b2[v];
-          }
-          store_chain<K>(c, b, ch);
-        } else {
-          adm = false;
-        }
+      // whose two reciprocal FP32 evaluations disagree, a transmittance at a
+      // grazing cosine, or a walk that stopped at the FP32 resolution of C.
+      // The chain is queued for k_contrib64, which polishes it and recomputes
+      // G and kappa in FP64.
+      if (adm && (K >= 6 || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol)) && o.fp64_list) {
+        o.fp64_list[*o.fp64_base + atomicAdd(o.fp64_count, 1)] = b;
         t.c.ggt64++;
       }
     }
@@ -178,6 +163,40 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
     o.T[b] = kap * G * S.L.power;
   }
   if (kS) flush(t, ctx.stats);
+}
+
+// FP64 polish, G and kappa of the chains k_contrib queued (rare: near caustic
+// folds, grazing transmission, stalled walks, k >= 6).  Writes back the
+// polished vertices and the final G, kappa and T.
+template <int K>
+__global__ void __launch_bounds__(64) k_contrib64(const __grid_constant__ DScene S, DChains c, mpg_params P, DOut o) {
+  const int n = *o.fp64_count;
+  const int* list = o.fp64_list + *o.fp64_base;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    int b = list[j];
+    Chain<K> ch;
+    load_chain<K>(c, b, ch);
+    Ends e = load_ends(c, b);
+    Chain64<K> c64;
+    to64<K>(S, ch, c64);
+    double g, k64;
+    float G = 0.f, kap = 0.f;
+    if (polish_ggt64<K>(S, c64, e, (double)P.tol, (double)P.sing_eps, 3, g, k64)) {
+      G = (float)g;
+      kap = (float)k64;
+#pragma unroll
+      for (int v = 0; v < K; ++v) {
+        ch.x[v] = make_float3((float)c64.x[v].x, (float)c64.x[v].y, (float)c64.x[v].z);
+        ch.prim[v] = c64.prim[v];
+        ch.b1[v] = (float)c64.b1[v];
+        ch.b2[v] = (float)c64.b2[v];
+      }
+      store_chain<K>(c, b, ch);
+    }
+    if (o.G) o.G[b] = G;
+    if (o.kappa) o.kappa[b] = kap;
+    o.T[b] = kap * G * S.L.power;
+  }
 }
 
 template <int K, bool kS>
@@ -243,6 +262,11 @@ template <int K>
 void KLaunch<K>::walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                         int* queue, int grid, int block, cudaStream_t st) {
   kern::k_walk_p<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx, queue);
+}
+
+template <int K>
+void KLaunch<K>::contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st) {
+  kern::k_contrib64<K><<<grid, 64, 0, st>>>(S, c, P, o);
 }
 
 template <int K>

@@ -201,7 +201,7 @@ def glass_sphere(n: int = 256, spq: int = 16, seed: int = 0x4D50470002) -> Workl
     scale = 2.0 * math.sqrt(3.0)
     return Workload("glass_sphere_k2", surfaces, np.zeros((0, 6)), np.zeros(0), targets, light,
                     xD, nD, cell, spq, xL, np.full(B, 2, np.uint8), np.full(B, 0b11, np.uint8),
-                    False, np.ones(B), 256, seed, scale, Params(dedup_eps=1e-4 * scale, max_iter=40), (n, n))
+                    False, np.ones(B), 256, seed, scale, Params(dedup_eps=1e-4 * scale), (n, n))
 
 
 def water_heights(grid: int = 128, seed: int = 0x4D50470003, n_waves: int = 8):
@@ -240,7 +240,7 @@ def water(n: int = 512, spq: int = 4, grid: int = 128, seed: int = 0x4D50470003)
     scale = float(math.sqrt(8.0 + (heights.max() - heights.min()) ** 2))
     pn = np.where(k == 1, 0.75, 0.25)
     return Workload("water_heightfield", surfaces, hf_desc, heights, targets, light, xD, nD, cell,
-                    spq, xL, k, tau, False, pn, 256, seed, scale, Params(dedup_eps=1e-4 * scale, max_iter=40),
+                    spq, xL, k, tau, False, pn, 256, seed, scale, Params(dedup_eps=1e-4 * scale),
                     (n, n))
 
 
@@ -282,7 +282,7 @@ def mixed(nx: int = 1024, ny: int = 512, spq: int = 8, seed: int = 0x4D50470004)
     scale = float(math.sqrt(8.0 ** 2 + 4.0 ** 2 + 2.9 ** 2))
     return Workload("mixed_k1to8", surfaces, np.zeros((0, 6)), np.zeros(0), np.stack(targets), light,
                     xD, nD, cell, spq, xL, k, np.zeros(B, np.uint8), True, GEOMETRIC_K_PMF[k - 1],
-                    256, seed, scale, Params(dedup_eps=1e-4 * scale, max_iter=40), (ny, nx))
+                    256, seed, scale, Params(dedup_eps=1e-4 * scale), (ny, nx))
 
 
 def upstream_grad(Q: int, seed: int = 0x4D50470005):
