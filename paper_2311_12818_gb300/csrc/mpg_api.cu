@@ -827,7 +827,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
                           lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, TB,
                           grid_of(ctx, 6, K, block, c.B, true), block, s2);
         launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
-                           lists[nxt], counts[nxt] + K, ctx->sms, s2);
+                           lists[nxt], counts[nxt] + K, dcb.stats, ctx->sms, s2);
       });
       t0 = t_end + 1;
       TB *= 4;

@@ -162,7 +162,8 @@ void launch_guide_records(const DChains& c, const float* contrib, float inv_area
 // End of a Bernoulli trial round
 // ---------------------------------------------------------------------------
 __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, const int* n_list, const int* base,
-                              unsigned* nbest, int t_end, int max_trials, int* next, int* n_next) {
+                              unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
+                              unsigned long long* stats) {
   const int n = *n_list;
   const int* L = list + *base;
   int* Nx = next + *base;
@@ -171,6 +172,7 @@ __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, co
     unsigned nb = nbest[b];
     bool hit = nb != 0xffffffffu;
     bool cap = !hit && t_end >= max_trials;
+    if (hit && stats) atomicAdd(stats + 10, 1ull);  // the walk of trial N converged
     if (hit || cap) {
       uint32_t N = hit ? nb : (uint32_t)max_trials;
       if (o.trials) o.trials[b] = N;
@@ -185,8 +187,9 @@ __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, co
 
 void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
                         const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
-                        int sms, cudaStream_t st) {
-  k_bern_finish<<<sms * 2, 256, 0, st>>>(S.L.area, c, o, list, n_list, base, nbest, t_end, max_trials, next, n_next);
+                        unsigned long long* stats, int sms, cudaStream_t st) {
+  k_bern_finish<<<sms * 2, 256, 0, st>>>(S.L.area, c, o, list, n_list, base, nbest, t_end, max_trials, next, n_next,
+                                         stats);
 }
 
 // ---------------------------------------------------------------------------

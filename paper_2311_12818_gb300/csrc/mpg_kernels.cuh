@@ -48,14 +48,7 @@ struct DCtx {
   unsigned long long* stats;     // [16] counters of the kernel family (mpg_stats layout)
 };
 
-// Scratch of the persistent Bernoulli pass and its trial rounds.
-struct DBernScratch {
-  int T1;                  // trials of the first pass
-  int* list[2];            // overflow chain lists (ping-pong), region list + base
-  int* n_list[2];          // their lengths (device)
-  const int* base;         // start of this chain length's region (device)
-  unsigned* nbest;         // [B] first successful trial of the current round
-};
+
 
 void launch_seed(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                  uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st);
@@ -118,6 +111,6 @@ void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, cons
 // capped, the rest move to the next list.
 void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
                         const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
-                        int sms, cudaStream_t st);
+                        unsigned long long* stats, int sms, cudaStream_t st);
 
 }  // namespace mpg

@@ -262,10 +262,10 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
     int st = walk_pass<K, kS>(S, L, P, t.c);
     if (st != RUNNING) {
       t.walks++;
-      if (st == ST_CONVERGED && same_solution<K>(L.ch, target, eps2)) {
-        atomicMin(nbest + b, (unsigned)tr);
-        t.conv++;  // only the successful trial of a round counts as a converged walk
-      }
+      // converged walks of the trial sequence (t <= N) are counted by the
+      // round's finish kernel, once per chain: parallel trials past the first
+      // success are not part of the estimator
+      if (st == ST_CONVERGED && same_solution<K>(L.ch, target, eps2)) atomicMin(nbest + b, (unsigned)tr);
       b = -1;
     }
   }
