@@ -24,6 +24,7 @@
 #include "mpg_oracle.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -1194,6 +1195,163 @@ static void parallel_for(int n, int n_threads, F fn) {
 
 static orc_params default_check(const orc_params* p) { return *p; }
 
+// ---------------------------------------------------------------------------
+// Adjoint of the receiver irradiance with respect to heightfield heights
+// (implicit function theorem on the converged constraint; <1/P> held fixed).
+// For a converged chain with local coordinates u (2 per vertex) and heights
+// theta: C(u*, theta) = 0 defines u*(theta), so
+//   dT/dtheta = dT/dtheta|_u - lambda^T dC/dtheta,   J^T lambda = (dT/du)^T.
+// All partial derivatives come from forward-mode dual numbers evaluated
+// through the same primitives as the walk (frames, constraint blocks, G, kappa).
+// ---------------------------------------------------------------------------
+static const int ADJ_LANES = 8;
+typedef Dual<ADJ_LANES> DN;
+
+// Grid vertices whose heights move vertex `prim` of heightfield H (its three
+// corners and the stencils of their normals).
+static void triangle_params(const HField& H, int prim, std::vector<int>& out) {
+  int v[3]; H.tri_vertices(prim, v);
+  for (int c = 0; c < 3; ++c) {
+    int i = v[c] % H.nx, j = v[c] / H.nx;
+    int cand[5][2] = {{i, j}, {i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+    for (auto& q : cand)
+      if (q[0] >= 0 && q[0] < H.nx && q[1] >= 0 && q[1] < H.ny) {
+        int id = q[1] * H.nx + q[0];
+        if (std::find(out.begin(), out.end(), id) == out.end()) out.push_back(id);
+      }
+  }
+}
+
+// Throughput and constraints of the chain at local coordinates u and heights
+// theta, as dual numbers; lane l carries direction dir0 + l of the list
+// [u_1 .. u_2k, theta_params[0 .. m)].
+static bool chain_value_dual(const Scene& S, const ChainIO& ch, const V3d& nD, const std::vector<int>& params,
+                             const std::vector<std::array<double, 4>>& Dmat, int dir0, DN* C, DN& T) {
+  int k = ch.k;
+  const HField* H = nullptr;
+  for (int i = 1; i <= k; ++i) {
+    const Surface& sf = S.surf[ch.v[i].surf];
+    if (sf.type != SURF_HEIGHTFIELD) return false;
+    H = &S.hf[sf.hf];
+  }
+  auto seed_of = [&](int dir) { int l = dir - dir0; return (l >= 0 && l < ADJ_LANES) ? l : -1; };
+  auto hgt = [&](int i, int j) {
+    int id = j * H->nx + i;
+    DN h(H->h[(size_t)id]);
+    for (size_t p = 0; p < params.size(); ++p)
+      if (params[p] == id) { int l = seed_of(2 * k + (int)p); if (l >= 0) h.d[l] = 1.0; }
+    return h;
+  };
+  Frame<DN> f[MAXK + 2];
+  Frame<double> f0 = receiver_frame(ch.v[0].p, nD), fL = light_frame(S.light, ch.v[k + 1].p);
+  auto liftf = [](const Frame<double>& a) {
+    Frame<DN> r;
+    r.p = lift<DN>(a.p); r.n = lift<DN>(a.n); r.dpdu = lift<DN>(a.dpdu); r.dpdv = lift<DN>(a.dpdv);
+    r.dndu = lift<DN>(a.dndu); r.dndv = lift<DN>(a.dndv);
+    return r;
+  };
+  f[0] = liftf(f0);
+  f[k + 1] = liftf(fL);
+  for (int i = 1; i <= k; ++i) {
+    int v[3]; H->tri_vertices(ch.v[i].prim, v);
+    V3<DN> P[3], N[3];
+    for (int c = 0; c < 3; ++c) {
+      int gi = v[c] % H->nx, gj = v[c] / H->nx;
+      P[c] = V3<DN>(DN(H->x0 + gi * H->dx), DN(H->y0 + gj * H->dy), hgt(gi, gj));
+      N[c] = hf_normal<DN>(*H, gi, gj, hgt);
+    }
+    DN u0(0.0), u1(0.0);
+    int l0 = seed_of(2 * (i - 1)), l1 = seed_of(2 * (i - 1) + 1);
+    if (l0 >= 0) u0.d[l0] = 1.0;
+    if (l1 >= 0) u1.d[l1] = 1.0;
+    const std::array<double, 4>& D = Dmat[i - 1];
+    DN b1 = DN(ch.v[i].b1) + u0 * DN(D[0]) + u1 * DN(D[1]);
+    DN b2 = DN(ch.v[i].b2) + u0 * DN(D[2]) + u1 * DN(D[3]);
+    f[i] = frame_triangle<DN>(P[0], P[1], P[2], N[0], N[1], N[2], b1, b2);
+  }
+  int surf[MAXK + 2];
+  for (int i = 0; i <= k + 1; ++i) surf[i] = ch.v[i].surf;
+  VBlocks<DN> vb[MAXK];
+  if (!chain_blocks<DN>(S, k, ch.tau, f, surf, vb)) return false;
+  for (int i = 0; i < k; ++i) { C[2 * i] = vb[i].C[0]; C[2 * i + 1] = vb[i].C[1]; }
+  DN G;
+  if (!chain_ggt<DN>(k, S.light.type == LIGHT_POINT, f, vb, 0.0, G)) return false;
+  DN kap = chain_kappa<DN>(S, k, ch.tau, f, surf, vb);
+  T = kap * G * DN(S.light.power);
+  return true;
+}
+
+// Dense solve of A x = b (n <= 16) by Gaussian elimination with partial pivoting.
+static bool dense_solve(int n, std::vector<double> A, std::vector<double>& b) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r) if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (!(std::fabs(A[piv * n + c]) > 0.0)) return false;
+    if (piv != c) { for (int q = 0; q < n; ++q) std::swap(A[c * n + q], A[piv * n + q]); std::swap(b[c], b[piv]); }
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r * n + c] / A[c * n + c];
+      for (int q = c; q < n; ++q) A[r * n + q] -= f * A[c * n + q];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double v = b[r];
+    for (int q = r + 1; q < n; ++q) v -= A[r * n + q] * b[q];
+    b[r] = v / A[r * n + r];
+  }
+  return true;
+}
+
+// dT/dtheta of one converged heightfield chain; returns false if the chain is
+// not a heightfield chain or its Jacobian is singular.
+static bool chain_adjoint(const Scene& S, const ChainIO& ch, const V3d& nD, std::vector<int>& params,
+                          std::vector<double>& dT) {
+  int k = ch.k;
+  const HField* H = nullptr;
+  params.clear();
+  std::vector<std::array<double, 4>> Dmat(k);
+  for (int i = 1; i <= k; ++i) {
+    const Surface& sf = S.surf[ch.v[i].surf];
+    if (sf.type != SURF_HEIGHTFIELD) return false;
+    H = &S.hf[sf.hf];
+    triangle_params(*H, ch.v[i].prim, params);
+    // map from local coordinates (along dpdu, dpdv) to barycentric increments
+    Frame<double> f = vertex_frame(S, ch.v[i]);
+    int v[3]; H->tri_vertices(ch.v[i].prim, v);
+    V3d e1 = H->P[v[1]] - H->P[v[0]], e2 = H->P[v[2]] - H->P[v[0]];
+    double g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2), gd = g11 * g22 - g12 * g12;
+    V3d a[2] = {f.dpdu, f.dpdv};
+    for (int q = 0; q < 2; ++q) {
+      double r1 = dot(e1, a[q]), r2 = dot(e2, a[q]);
+      Dmat[i - 1][q] = (g22 * r1 - g12 * r2) / gd;      // db1 / du_q
+      Dmat[i - 1][2 + q] = (g11 * r2 - g12 * r1) / gd;  // db2 / du_q
+    }
+  }
+  int n = 2 * k, m = (int)params.size(), nd = n + m;
+  std::vector<double> dC((size_t)n * nd), dTd(nd);
+  for (int d0 = 0; d0 < nd; d0 += ADJ_LANES) {
+    DN C[2 * MAXK], T;
+    if (!chain_value_dual(S, ch, nD, params, Dmat, d0, C, T)) return false;
+    for (int l = 0; l < ADJ_LANES && d0 + l < nd; ++l) {
+      for (int r = 0; r < n; ++r) dC[(size_t)r * nd + d0 + l] = C[r].d[l];
+      dTd[d0 + l] = T.d[l];
+    }
+  }
+  // J^T lambda = dT/du
+  std::vector<double> JT((size_t)n * n), lam(n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) JT[(size_t)r * n + c] = dC[(size_t)c * nd + r];
+  for (int r = 0; r < n; ++r) lam[r] = dTd[r];
+  if (!dense_solve(n, JT, lam)) return false;
+  dT.assign(m, 0.0);
+  for (int p = 0; p < m; ++p) {
+    double v = dTd[n + p];
+    for (int r = 0; r < n; ++r) v -= lam[r] * dC[(size_t)r * nd + n + p];
+    dT[p] = v;
+  }
+  return true;
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -1450,6 +1608,30 @@ int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k,
     d = dn;
   }
   store3(exit_dir, d);
+  return 0;
+}
+
+int32_t orc_adjoint(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD, const double* xL,
+                    const uint8_t* k, const uint8_t* tau, const double* x, const int32_t* surf,
+                    const int32_t* prim, const double* bary, const double* weight, double* dL_dtheta,
+                    double* dT_out, int32_t n_threads) {
+  if (!scene || B < 0 || spq <= 0) return -1;
+  const Scene& S = *(Scene*)scene;
+  if (S.hf.empty()) return -2;
+  std::vector<std::vector<int>> P(B);
+  std::vector<std::vector<double>> D(B);
+  std::vector<uint8_t> ok(B, 0);
+  parallel_for(B, n_threads, [&](int b) {
+    if (weight[b] == 0.0) return;
+    ChainIO ch;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
+    ok[b] = chain_adjoint(S, ch, load3(nD + 3 * (size_t)(b / spq)), P[b], D[b]) ? 1 : 0;
+  });
+  for (int b = 0; b < B; ++b) {
+    if (dT_out) dT_out[b] = ok[b] ? 1.0 : 0.0;
+    if (!ok[b]) continue;
+    for (size_t p = 0; p < P[b].size(); ++p) dL_dtheta[P[b][p]] += weight[b] * D[b][p];
+  }
   return 0;
 }
 

@@ -107,6 +107,15 @@ int32_t orc_constraint(void* scene, int32_t B, int32_t spq, const double* xD, co
 int32_t orc_shoot(void* scene, const double* xD, const double* omega, int32_t k, uint8_t tau,
                   double ray_eps, double* x, double* exit_dir);
 
+/* Adjoint: dL_dtheta[height] += sum_b weight[b] * dT_b/dtheta for heightfield
+ * chains (T = kappa G L_o at the converged chain, implicit function theorem,
+ * heights of heightfield 0 on its grid).  dT_out[b] (may be NULL) = 1 where a
+ * gradient was formed. */
+int32_t orc_adjoint(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD, const double* xL,
+                    const uint8_t* k, const uint8_t* tau, const double* x, const int32_t* surf,
+                    const int32_t* prim, const double* bary, const double* weight, double* dL_dtheta,
+                    double* dT_out, int32_t n_threads);
+
 /* Philox4x32-10 block: out = philox(ctr[4], key[2]). */
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 

@@ -68,6 +68,9 @@ def lib():
         L.orc_constraint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p,
                                      _f64p, _i32p, _i32p, _f64p, _f64p, _f64p]
         L.orc_shoot.argtypes = [C.c_void_p, _f64p, _f64p, C.c_int32, C.c_uint8, C.c_double, _f64p, _f64p]
+        L.orc_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p, _f64p, _i32p,
+                                  _i32p, _f64p, _f64p, _f64p, _f64p, C.c_int32]
+        L.orc_adjoint.restype = C.c_int32
         L.orc_philox.argtypes = [_u32p, _u32p, _u32p]
         L.orc_philox.restype = None
         for name in ("orc_intersect", "orc_sample_seeds", "orc_walk", "orc_contribution",
@@ -243,6 +246,21 @@ def shoot(scene, xD, omega, k, tau, ray_eps=1e-4):
     d = np.zeros(3)
     rc = lib().orc_shoot(scene.h, _c(xD, np.float64), _c(omega, np.float64), k, tau, ray_eps, x, d)
     return (x, d) if rc == 0 else (None, None)
+
+
+def adjoint(wl, scene, chains, weight, threads=None):
+    """dL/dtheta (heights of heightfield 0) for L = sum_b weight[b] T_b; also
+    the per-chain flag of a formed gradient."""
+    n_h = int(wl.hf_heights.size)
+    g = np.zeros(n_h)
+    okf = np.zeros(wl.B)
+    rc = lib().orc_adjoint(scene.h, wl.B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64),
+                           _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(chains["tau"], np.uint8),
+                           _c(chains["x"], np.float64), _c(chains["surf"], np.int32), _c(chains["prim"], np.int32),
+                           _c(chains["bary"], np.float64), _c(weight, np.float64), g, okf,
+                           threads or default_threads())
+    assert rc == 0, rc
+    return g, okf
 
 
 def irradiance(wl, T, N, admissible):
