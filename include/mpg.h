@@ -263,14 +263,20 @@ mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* scene, const mpg_cha
                              const float* contrib, uint32_t* cell_out, float* omega_out,
                              float* w_out, int32_t* R_dev, cudaStream_t stream);
 
-/* S11 -- adjoint: accumulates dL/dtheta += sum_chains dL/dE[q] * d(contrib_b/spq)/dtheta
- * for the heights theta of heightfield 0, with the implicit function theorem on
- * the converged constraint (transposed block-tridiagonal solve; the Newton
- * iterations are not unrolled) and <1/P> held constant.  dL_dtheta is
- * [ny*nx] FP32, accumulated. */
+/* S11 -- adjoint (the configuration's differentiable form, built on the
+ * continuity of the specular manifold, Sec. 5.2): accumulates
+ *   dL_dtheta[h] += sum_b dL_dE[q_b] * d(contrib_b / spq)/dtheta_h
+ * for the heights theta of heightfield 0 (grid index j*nx + i, FP32,
+ * accumulated with atomics), with <1/P> held constant so that
+ * d contrib_b/dtheta = (contrib_b / T_b) dT_b/dtheta.  dT/dtheta comes from the
+ * implicit function theorem on the converged constraint (J^T lambda = dT/du,
+ * dT/dtheta = dT/dtheta|_u - lambda^T dC/dtheta); the Newton iterations are not
+ * unrolled.  Chains of length 1..4 whose vertices all lie on heightfield 0 are
+ * differentiated; other chains are skipped.  T and contrib are the outputs of
+ * mpg_chain_contribution for the same chains. */
 mpg_status mpg_walk_adjoint(mpg_ctx* ctx, const mpg_scene* scene, const mpg_chains* chains,
-                            const float* contrib, const float* dL_dE, float* dL_dtheta,
-                            cudaStream_t stream);
+                            const float* T, const float* contrib, const float* dL_dE,
+                            float* dL_dtheta, cudaStream_t stream);
 
 /* K3 -- standalone BVH/analytic ray batch: nearest hit of rays (o[3][n], d[3][n])
  * in (tmin, tmax): t (or -1), surface, primitive and barycentrics [2][n]. */

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libmpg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mpg_kernels.cu", "mpg_aux.cu", "mpg_api.cu"] + ["mpg_k%d.cu" % k for k in range(1, 9)]
+SOURCES = ["mpg_kernels.cu", "mpg_aux.cu", "mpg_api.cu", "mpg_adjoint.cu"] + ["mpg_k%d.cu" % k for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -871,10 +871,23 @@ mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains
   return MPG_OK;
 }
 
-mpg_status mpg_walk_adjoint(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* contrib,
-                            const float* dL_dE, float* dL_dtheta, cudaStream_t st) {
-  (void)ctx; (void)sc; (void)chains; (void)contrib; (void)dL_dE; (void)dL_dtheta; (void)st;
-  return fail(MPG_ERR_UNSUPPORTED, "mpg_walk_adjoint is not built yet");
+mpg_status mpg_walk_adjoint(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* T,
+                            const float* contrib, const float* dL_dE, float* dL_dtheta, cudaStream_t st) {
+  if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (!aligned16(T) || !aligned16(contrib) || !aligned16(dL_dE) || !aligned16(dL_dtheta))
+    return fail(MPG_ERR_INVALID_ARG, "T, contrib, dL_dE and dL_dtheta must be non-NULL 16-byte aligned device arrays");
+  if (sc->S.n_hf < 1) return fail(MPG_ERR_UNSUPPORTED, "the adjoint differentiates heightfield heights: no heightfield");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  DChains c = to_dev(chains);
+  timed(ctx, MPG_KERNEL_AUX, st, 4, [&] {
+    for (int K = 1; K <= 4; ++K)
+      launch_adjoint(K, sc->S, c, T, contrib, dL_dE, dL_dtheta, ctx->d_err + 0, ctx->sms, st);
+  });
+  LAUNCH_CHECK("adjoint");
+  return MPG_OK;
 }
 
 mpg_status mpg_trace_rays(mpg_ctx* ctx, const mpg_scene* sc, const float* o, const float* d, int32_t n, float tmin,

@@ -59,6 +59,10 @@ void launch_contrib(int K, bool stats, const DScene& S, const DChains& c, DWork 
 void launch_bernoulli(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                       uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block, cudaStream_t st);
 
+// K7 adjoint for chains of length K (1..4) on heightfield 0.
+void launch_adjoint(int K, const DScene& S, const DChains& c, const float* T, const float* contrib,
+                    const float* dL_dE, float* dL_dtheta, int* skipped, int sms, cudaStream_t st);
+
 // Occupancy-derived grid for the per-K kernels (blocks per SM x SMs).
 int blocks_per_sm(int which, int K, bool stats, int block);
 

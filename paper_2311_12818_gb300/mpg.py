@@ -102,7 +102,7 @@ def lib():
                                              C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
         L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp]
-        L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp]
+        L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp]
         L.mpg_trace_rays.argtypes = [vp, vp, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp]
         L.mpg_fp32_peak.argtypes = [vp, C.POINTER(C.c_double), vp]
         for n in EXPORTS[2:]:
@@ -335,10 +335,11 @@ def mpg_guide_records(ctx, scene, chains, contrib, out=None, stream=None):
     return cell, om, w, R
 
 
-def mpg_walk_adjoint(ctx, scene, chains, contrib, dL_dE, dL_dtheta, stream=None):
+def mpg_walk_adjoint(ctx, scene, chains, T, contrib, dL_dE, dL_dtheta, stream=None):
+    """dL_dtheta (heights of heightfield 0, accumulated) += sum_b dL_dE[q] d(contrib_b/spq)/dtheta."""
     cs = chains.struct()
-    _check(lib().mpg_walk_adjoint(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(dL_dE), _ptr(dL_dtheta),
-                                  _stream(stream)))
+    _check(lib().mpg_walk_adjoint(ctx.h, scene.h, C.byref(cs), _ptr(T), _ptr(contrib), _ptr(dL_dE),
+                                  _ptr(dL_dtheta), _stream(stream)))
 
 
 def mpg_trace_rays(ctx, scene, o, d, tmin=1e-4, tmax=3.0e38, stream=None):
