@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--spq", type=int, default=16)
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the mixed-batch and adjoint measurements")
     return ap.parse_args()
 
 
@@ -285,12 +286,81 @@ def run_ours(args, rank, world, local):
                                     "tflops": f["flops"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] > 0 else None}
                                 for n, f in fam.items() if f["launches"]}},
     }
+    if rank == 0 and not args.no_secondary:
+        line["secondary"] = secondary(args, dev, flush, torch)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def timed_steps(fn, steps, warmup, flush, stream, torch):
+    for i in range(warmup):
+        fn(10_000 + i)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for i in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn(i)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    return ms / steps
+
+
+def secondary(args, dev, flush, torch):
+    """Two more configurations measured beside the headline: the mixed-length
+    batch (k = 1..8, 2^22 chains) in batched and plain mode, and the adjoint of
+    the water irradiance with respect to the heights (2^20 chains)."""
+    import numpy as np
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    stream = torch.cuda.current_stream()
+    out = {}
+    ctx = mpg.Context(dev.index or 0)
+    # mixed-length batch: seeds -> walk -> contribution with Bernoulli trials
+    wl = I.mixed()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    mixed = {"workload": "mixed_k1to8: nested spheres + 4 lenses + mirror, 1024x512 points x 8 = 4,194,304 chains"}
+    for mode, name in ((mpg.WALK_BATCHED, "batched"), (mpg.WALK_PLAIN, "plain")):
+        P = mpg.params_from(wl.params, walk_mode=mode, tau_random=True, k_uniform=0)
+
+        def step(i, P=P):
+            mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B)
+            mpg.mpg_manifold_walk(ctx, sc, ch, P)
+            mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B, out=res)
+        ctx.reset_stats()
+        ms = timed_steps(step, max(2, args.steps // 2), 2, flush, stream, torch)
+        st = ctx.stats()
+        n = max(2, args.steps // 2) + 2
+        mixed[name] = {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / n / (ms * 1e-3),
+                       "walks_per_s": st["walks"] / n / (ms * 1e-3)}
+    mixed["batched_over_plain"] = mixed["batched"]["converged_walks_per_s"] / mixed["plain"]["converged_walks_per_s"]
+    out["mixed_batch"] = mixed
+    del ch, res
+    # adjoint on the water heightfield
+    wl = I.water()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED)
+    res = mpg.run(ctx, sc, ch, wl, params=P)
+    dLdE = torch.as_tensor(I.upstream_grad(wl.Q), dtype=torch.float32, device=dev)
+    g = torch.zeros(wl.hf_heights.size, dtype=torch.float32, device=dev)
+    n_adj = int((res.contrib > 0).sum().item())
+
+    def adj(i):
+        g.zero_()
+        mpg.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE, g)
+    ms = timed_steps(adj, max(2, args.steps // 2), 2, flush, stream, torch)
+    out["adjoint"] = {"workload": "water_heightfield: 128x128 heights, 512x512 points x 4 = 1,048,576 chains",
+                      "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3)}
+    return out
 
 
 def cpu_sample(n=256, spq=16):

@@ -1706,15 +1706,5 @@ int32_t orc_unit_flops(double* out) {
   return 0;
 }
 
-int32_t orc_count_flops(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
-                        const double* xL, const uint8_t* k, const uint8_t* tau,
-                        const orc_params* prm, const uint8_t* valid, const double* x,
-                        const int32_t* surf, const int32_t* prim, const double* bary,
-                        double* out) {
-  (void)scene; (void)B; (void)spq; (void)xD; (void)nD; (void)xL; (void)k; (void)tau;
-  (void)prm; (void)valid; (void)x; (void)surf; (void)prim; (void)bary;
-  for (int i = 0; i < 7; ++i) out[i] = 0.0;
-  return -3;  // filled in with the unit flop counts
-}
 
 }  // extern "C"

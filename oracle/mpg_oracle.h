@@ -123,14 +123,7 @@ void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
  * values; the order is documented in the implementation). */
 int32_t orc_unit_flops(double* out);
 
-/* Algorithmic flop tally of walking + evaluating the given chains once more
- * in a counted scalar type: out[0] adds, [1] muls, [2] divs, [3] sqrts,
- * [4] Newton iterations, [5] vertex-iterations, [6] ray-primitive tests. */
-int32_t orc_count_flops(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
-                        const double* xL, const uint8_t* k, const uint8_t* tau,
-                        const orc_params* prm, const uint8_t* valid, const double* x,
-                        const int32_t* surf, const int32_t* prim, const double* bary,
-                        double* out);
+
 
 #ifdef __cplusplus
 }

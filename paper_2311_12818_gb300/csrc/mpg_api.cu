@@ -724,7 +724,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   Plan plan;
   if ((s = make_plan(ctx, chains, P, ST_CONVERGED, st, plan))) return s;
   DChains c = to_dev(chains);
-  DCtx dcc = dctx(ctx, MPG_KERNEL_CONTRIB), dcb = dctx(ctx, MPG_KERNEL_BERNOULLI);
+  DCtx dcc = dctx(ctx, MPG_KERNEL_CONTRIB), dcb = dctx(ctx, MPG_KERNEL_BERNOULLI), dcw = dctx(ctx, MPG_KERNEL_WALK);
   if (ctx->fp64_cap < c.B) {
     cudaFree(ctx->d_fp64);
     ctx->d_fp64 = nullptr;
@@ -806,11 +806,16 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       int nxt = 1 - cur;
       cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
       DWork tw{lists[cur], base, counts[cur]};
-      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 3, [&] {
+      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
         launch_trial_seed(K, sc->S, guide ? &g : nullptr, c, tc, lists[cur], base, counts[cur], key, rng_offset, *P,
                           dcb, t, grid_of(ctx, 5, K, block, c.B, true), block, s2);
-        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcb, q + t, grid_of(ctx, 4, K, block, c.B, true), block,
+      });
+      // trial walks run the walk kernel and are tallied with the walk family
+      timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
+        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t, grid_of(ctx, 4, K, block, c.B, true), block,
                       s2);
+      });
+      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
         launch_trial_check(K, sc->S, c, tc, o, lists[cur], base, counts[cur], t, t == T1, *P, lists[nxt], counts[nxt],
                            ctx->d_nbest, small_grid, s2);
       });
