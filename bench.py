@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--spq", type=int, default=16)
     ap.add_argument("--mode", default="batched", choices=["batched", "plain"])
     ap.add_argument("--no-flush", action="store_true")
-    ap.add_argument("--no-secondary", action="store_true", help="skip the mixed-batch and adjoint measurements")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the K3/K6, mixed-batch and adjoint measurements")
+    ap.add_argument("--no-graph", action="store_true", help="batched mode without graph capture")
+    ap.add_argument("--part", choices=["k3", "k6", "mixed", "adjoint"], help="run one secondary measurement only")
     return ap.parse_args()
 
 
@@ -159,15 +161,25 @@ def run_ours(args, rank, world, local):
         mpg.mpg_manifold_walk(ctx, sc, ch, P)
         mpg.mpg_chain_contribution(ctx, sc, guide, ch, P, wl.rng_seed, o, out=out)
         mpg.mpg_guide_records(ctx, sc, ch, out.contrib, out=rec)
-        nxt.counts.zero_()
+        mpg.mpg_guide_clear(ctx, nxt)
         mpg.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=B, R_dev=rec[3],
                              weight_shift=wl.params.weight_shift)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    for i in range(args.warmup):
+    for i in range(args.warmup):  # uncaptured: sizes the context's buffers
         step(1000 + i)
     ctx.sync()
+    graph = None
+    if args.mode == "batched" and not args.no_graph:
+        # the whole step as one graph; replay r draws at the offsets of step 2000 + r
+        graph = mpg.Graph(ctx, rng_advance=B * world)
+        with graph:
+            step(2000)
+        for i in range(args.warmup):
+            graph.launch()
+        ctx.sync()
+    run = (lambda i: graph.launch()) if graph is not None else step
 
     def barrier():
         if world > 1:
@@ -176,8 +188,6 @@ def run_ours(args, rank, world, local):
 
     # ---- device-timed steps (inputs resident in HBM)
     ctx.reset_stats()
-    ctx.profile(reset=True)
-    ctx.set_profile(True)
     n_launch0 = ctx.launches()
     clocks = Clocks(local)
     barrier()
@@ -188,21 +198,14 @@ def run_ours(args, rank, world, local):
         if not args.no_flush:
             flush.zero_()
         ev[i][0].record(stream)
-        step(i)
+        run(i)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ctx.set_profile(False)
     ctx.sync()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     launches = ctx.launches() - n_launch0
-    fam = {}
-    F = unit_flops()
-    for k, name in enumerate(mpg.KERNEL_NAMES):
-        ms, n = ctx.profile(k)
-        st = ctx.stats(k)
-        fam[name] = dict(ms=ms, launches=n, stats=st, flops=algorithmic_flops(st, F))
     total = ctx.stats()
     conv = total["converged"]
     t_ms = sum(step_ms)
@@ -217,6 +220,29 @@ def run_ours(args, rank, world, local):
     else:
         conv_all = float(conv)
     value = conv_all / (t_ms * 1e-3)
+
+    # ---- attribution: the same steps uncaptured, each launch bracketed by
+    # CUDA events on its own stream (per-family time, counters and flops)
+    ctx.reset_stats()
+    ctx.profile(reset=True)
+    ctx.set_profile(True)
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        if not args.no_flush:
+            flush.zero_()
+        ev2[i][0].record(stream)
+        step(3000 + i)
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.set_profile(False)
+    ctx.sync()
+    attr_ms = sum(a.elapsed_time(b) for a, b in ev2)
+    fam = {}
+    F = unit_flops()
+    for k, name in enumerate(mpg.KERNEL_NAMES):
+        ms, n = ctx.profile(k)
+        st = ctx.stats(k)
+        fam[name] = dict(ms=ms, launches=n, stats=st, flops=algorithmic_flops(st, F))
 
     # ---- end to end through the public API with host buffers
     pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
@@ -240,7 +266,7 @@ def run_ours(args, rank, world, local):
         a.record(stream)
         for d, h in host_in:
             d.copy_(h, non_blocking=True)
-        step(500 + i)
+        run(500 + i)
         E_host.copy_(out.E, non_blocking=True)
         n_host.copy_(rec[3], non_blocking=True)
         b.record(stream)
@@ -257,20 +283,25 @@ def run_ours(args, rank, world, local):
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_nominal = props.multi_processor_count * 128 * 2 * sm_max * 1e6
     peak_ffma = ctx.fp32_peak()
-    roofline = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved / 1e12, "peak": peak_nominal / 1e12,
+    peak_dfma = ctx.fp64_peak()
+    kname = {"walk": "k_walk_p" if args.mode == "batched" else "k_walk", "bernoulli": "k_bern_round"}.get(dom, "k_" + dom)
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_nominal / 1e12,
                 "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": None,
                 "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (props.multi_processor_count, sm_max),
                 "peak_ffma_measured": peak_ffma / 1e12, "frac_of_ffma_measured": achieved / peak_ffma if peak_ffma else None,
+                "peak_fp64_dfma_measured": peak_dfma / 1e12,
                 "algorithmic_flops_per_launch": d["flops"] / max(1, d["launches"]),
-                "avg_launch_ms": d["ms"] / max(1, d["launches"])}
+                "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                "timing": "per-launch CUDA events in an uncaptured pass of the same steps"}
     step_flops = sum(f["flops"] for f in fam.values())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural scene, no dataset)",
         "config": {"workload": WORKLOAD, "chains_per_step": B, "receiver_points": Q, "seeds_per_point": wl.spq,
-                   "k": 2, "walk_mode": args.mode, "l2": "flushed between steps (256 MiB write)" if not args.no_flush
-                   else "not flushed", "parallelism": "replicas x%d" % world,
+                   "k": 2, "walk_mode": args.mode, "graph": graph is not None,
+                   "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
+                   "parallelism": "replicas x%d" % world,
                    "counted_walks": "first walks + Bernoulli trial walks that converged"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -280,14 +311,17 @@ def run_ours(args, rank, world, local):
                    "trials_per_step": total["trials"] / args.steps,
                    "fp64_geometry_terms_per_step": total["ggt_fp64"] / args.steps,
                    "step_ms": [round(x, 4) for x in step_ms],
-                   "step_fp32_tflops": step_flops / (t_ms * 1e-3) / 1e12 if world == 1 else None,
+                   "graph_kernels_per_step": graph.kernels() if graph is not None else None,
+                   "uncaptured_profiled_ms_per_step": attr_ms / args.steps,
+                   "step_fp32_tflops": step_flops / (attr_ms * 1e-3) / 1e12 if world == 1 else None,
                    "families": {n: {"ms_per_step": f["ms"] / args.steps, "launches": f["launches"],
                                     "gflop_per_step": f["flops"] / args.steps / 1e9,
                                     "tflops": f["flops"] / (f["ms"] * 1e-3) / 1e12 if f["ms"] > 0 else None}
                                 for n, f in fam.items() if f["launches"]}},
     }
+    del graph
     if rank == 0 and not args.no_secondary:
-        line["secondary"] = secondary(args, dev, flush, torch)
+        line["secondary"] = secondary(args, dev, flush, torch, peak_nominal)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(line))
@@ -296,7 +330,8 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def timed_steps(fn, steps, warmup, flush, stream, torch):
+def timed_loop(fn, steps, warmup, flush, stream, torch):
+    """Mean ms of fn(i) over `steps` calls after `warmup`, L2 flushed before each."""
     for i in range(warmup):
         fn(10_000 + i)
     torch.cuda.synchronize()
@@ -312,55 +347,182 @@ def timed_steps(fn, steps, warmup, flush, stream, torch):
     return ms / steps
 
 
-def secondary(args, dev, flush, torch):
-    """Two more configurations measured beside the headline: the mixed-length
-    batch (k = 1..8, 2^22 chains) in batched and plain mode, and the adjoint of
-    the water irradiance with respect to the heights (2^20 chains)."""
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+PARTS = ("k3", "k6", "mixed", "adjoint")
+
+
+def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
+    """The other configurations, measured beside the headline:
+    - k3: the standalone BVH ray batch on the water heightfield (GB/s);
+    - k6: the guide-histogram update of one glass-sphere pass (GB/s);
+    - mixed: the mixed-length batch (k = 1..8, 2^22 chains) plain (one launch
+      per k), batched (one graph replay) and batched with the autotuned schedule;
+    - adjoint: the adjoint of the water irradiance with respect to the heights."""
     import numpy as np
     from paper_2311_12818_gb300 import inputs as I
     from paper_2311_12818_gb300 import mpg
     stream = torch.cuda.current_stream()
+    hbm, hbm_src = measured_hbm()
+    steps = max(2, args.steps // 2)
+    F = unit_flops()
     out = {}
     ctx = mpg.Context(dev.index or 0)
-    # mixed-length batch: seeds -> walk -> contribution with Bernoulli trials
+    if "k3" in parts:
+        out["k3_bvh_trace"] = part_k3(ctx, dev, flush, torch, stream, steps, F, hbm, hbm_src)
+    if "k6" in parts:
+        out["k6_guide_update"] = part_k6(ctx, dev, flush, torch, stream, steps, hbm, hbm_src)
+    if "mixed" in parts:
+        out["mixed_batch"] = part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
+    if "adjoint" in parts:
+        out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
+    return out
+
+
+def part_k3(ctx, dev, flush, torch, stream, steps, F, hbm, hbm_src):
+    import numpy as np
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.water()
+    sc = mpg.Scene(ctx, wl)
+    n = 1 << 22
+    o, d = I.water_rays(n)
+    o = torch.as_tensor(o.T.astype(np.float32), device=dev).contiguous()
+    d = torch.as_tensor(d.T.astype(np.float32), device=dev).contiguous()
+    res = (torch.empty(n, dtype=torch.float32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+           torch.empty(n, dtype=torch.int32, device=dev), torch.empty((2, n), dtype=torch.float32, device=dev))
+    mpg.mpg_trace_rays(ctx, sc, o, d, out=res)
+    ctx.reset_stats()
+    ms = timed_loop(lambda i: mpg.mpg_trace_rays(ctx, sc, o, d, out=res), steps, 2, flush, stream, torch)
+    st = ctx.stats(mpg.KERNEL_TRACE)
+    per = steps + 2
+    nodes, tris = st["node_tests"] / per, st["tri_tests"] / per
+    byts = n * (24 + 20) + nodes * 32 + tris * 48
+    nn, nt = sc.info(0)
+    return {
+        "workload": "water heightfield 128x128 (%d triangles, %d BVH nodes), %d rays" % (nt, nn, n),
+        "ms": ms, "rays_per_s": n / (ms * 1e-3), "node_tests_per_ray": nodes / n, "tri_tests_per_ray": tris / n,
+        "algorithmic_bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm, "peak_source": hbm_src,
+        "frac": byts / (ms * 1e-3) / 1e9 / hbm,
+        "bytes_rule": "44 B of ray in/out + 32 B per child-box test + 48 B per triangle test (nodes and triangles are"
+                      " L2-resident: the figure is L2+DRAM traffic against the HBM peak)",
+        "fp32_tflops": algorithmic_flops(st, F, "sphere") / per / (ms * 1e-3) / 1e12}
+
+
+def part_k6(ctx, dev, flush, torch, stream, steps, hbm, hbm_src):
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.glass_sphere()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, k_uniform=2)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, 0)
+    mpg.mpg_manifold_walk(ctx, sc, ch, P)
+    mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 0, out=res)
+    rec = (torch.zeros(wl.B, dtype=torch.int32, device=dev), torch.zeros((3, wl.B), dtype=torch.float32, device=dev),
+           torch.zeros(wl.B, dtype=torch.float32, device=dev), torch.zeros(4, dtype=torch.int32, device=dev))
+    mpg.mpg_guide_records(ctx, sc, ch, res.contrib, out=rec)
+    g = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+    R = int(rec[3][0].item())
+
+    def upd(i):
+        mpg.mpg_guide_clear(ctx, g)
+        mpg.mpg_guide_update(ctx, g, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
+    ms = timed_loop(upd, steps, 2, flush, stream, torch)
+    hist = g.counts.numel() * 8
+    byts = R * (4 + 12 + 4 + 8) + 2 * hist + 2 * hist  # records + atomics, clear, prefix-sum read + write
+    return {
+        "workload": "glass sphere pass: %d records into 256 cells x 64x64 bins (uint64)" % R,
+        "ms": ms, "records_per_s": R / (ms * 1e-3), "algorithmic_bytes": byts, "gbs": byts / (ms * 1e-3) / 1e9,
+        "hbm_peak_gbs": hbm, "peak_source": hbm_src, "frac": byts / (ms * 1e-3) / 1e9 / hbm,
+        "bytes_rule": "20 B per record + 8 B atomic, clear of counts and prefix sums (16 B/bin), prefix sums"
+                      " (8 B/bin read + 8 B/bin written)"}
+
+
+def part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
     wl = I.mixed()
     sc = mpg.Scene(ctx, wl)
     ch = mpg.Chains(wl, device=dev)
     res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
     mixed = {"workload": "mixed_k1to8: nested spheres + 4 lenses + mirror, 1024x512 points x 8 = 4,194,304 chains"}
-    for mode, name in ((mpg.WALK_BATCHED, "batched"), (mpg.WALK_PLAIN, "plain")):
-        P = mpg.params_from(wl.params, walk_mode=mode, tau_random=True, k_uniform=0)
 
-        def step(i, P=P):
-            mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B)
+    def measure(P, use_graph):
+        def step(i, o=0):
+            mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B + o)
             mpg.mpg_manifold_walk(ctx, sc, ch, P)
-            mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B, out=res)
+            mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B + o, out=res)
+        step(0)
+        ctx.sync()
+        fn, gr = step, None
+        if use_graph:
+            gr = mpg.Graph(ctx, rng_advance=wl.B)
+            with gr:
+                step(0, 7 << 32)
+            fn = lambda i: gr.launch()  # noqa: E731
         ctx.reset_stats()
-        ms = timed_steps(step, max(2, args.steps // 2), 2, flush, stream, torch)
+        n0 = ctx.launches()
+        ms = timed_loop(fn, steps, 2, flush, stream, torch)
         st = ctx.stats()
-        n = max(2, args.steps // 2) + 2
-        mixed[name] = {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / n / (ms * 1e-3),
-                       "walks_per_s": st["walks"] / n / (ms * 1e-3)}
-    mixed["batched_over_plain"] = mixed["batched"]["converged_walks_per_s"] / mixed["plain"]["converged_walks_per_s"]
-    out["mixed_batch"] = mixed
-    del ch, res
-    # adjoint on the water heightfield
+        per = steps + 2
+        fl = algorithmic_flops(st, F) / per
+        r = {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+             "walks_per_s": st["walks"] / per / (ms * 1e-3), "fp32_tflops": fl / (ms * 1e-3) / 1e12,
+             "fp32_frac": fl / (ms * 1e-3) / peak_fp32, "launches_per_step": (ctx.launches() - n0) / per,
+             "graph": use_graph}
+        return r
+
+    base = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=True, k_uniform=0)
+    mixed["plain"] = measure(mpg.params_from(wl.params, walk_mode=mpg.WALK_PLAIN, tau_random=True, k_uniform=0), False)
+    mixed["batched"] = measure(base, True)
+    t0 = time.perf_counter()
+    tuned, tms = mpg.mpg_autotune(ctx, sc, None, ch, base, wl.rng_seed, 0, repeats=1)
+    tune_s = time.perf_counter() - t0
+    mixed["batched_autotuned"] = measure(tuned, True)
+    mixed["batched_autotuned"]["schedule"] = {f: getattr(tuned, f) for f in mpg.SCHEDULE_FIELDS}
+    mixed["batched_autotuned"]["tuning_s"] = tune_s
+    mixed["batched_over_plain"] = (mixed["batched_autotuned"]["converged_walks_per_s"]
+                                   / mixed["plain"]["converged_walks_per_s"])
+    return mixed
+
+
+def part_adjoint(ctx, dev, flush, torch, stream, steps):
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
     wl = I.water()
     sc = mpg.Scene(ctx, wl)
     ch = mpg.Chains(wl, device=dev)
     P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED)
     res = mpg.run(ctx, sc, ch, wl, params=P)
     dLdE = torch.as_tensor(I.upstream_grad(wl.Q), dtype=torch.float32, device=dev)
-    g = torch.zeros(wl.hf_heights.size, dtype=torch.float32, device=dev)
+    gr = torch.zeros(wl.hf_heights.size, dtype=torch.float32, device=dev)
     n_adj = int((res.contrib > 0).sum().item())
 
     def adj(i):
-        g.zero_()
-        mpg.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE, g)
-    ms = timed_steps(adj, max(2, args.steps // 2), 2, flush, stream, torch)
-    out["adjoint"] = {"workload": "water_heightfield: 128x128 heights, 512x512 points x 4 = 1,048,576 chains",
-                      "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3)}
-    return out
+        gr.zero_()
+        mpg.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE, gr)
+    ms = timed_loop(adj, steps, 2, flush, stream, torch)
+    return {"workload": "water_heightfield: 128x128 heights, 512x512 points x 4 = 1,048,576 chains",
+            "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3)}
+
+
+def run_part(args):
+    """One secondary measurement alone (--part), for profiling a single kernel."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * 2 * 2070.0 * 1e6
+    print(json.dumps({"part": args.part, **secondary(args, dev, flush, torch, peak, parts=(args.part,))}))
 
 
 def cpu_sample(n=256, spq=16):
@@ -437,6 +599,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.part:
+        run_part(args)
     else:
         run_ours(args, rank, world, local)
 

@@ -70,7 +70,8 @@ typedef struct mpg_params {
   int32_t weight_shift; /* histogram weight quantisation q = floor(w * 2^S)        */
   float alpha;          /* defensive mixture weight of p_0 (Sec. 5.5, alpha = 0.5) */
   int32_t walk_mode;    /* MPG_WALK_PLAIN or MPG_WALK_BATCHED                     */
-  int32_t block_threads;/* threads per block of the walk kernels (0 = default)    */
+  int32_t block_threads;/* threads per block of the walk kernels (0 = 128; 32..128,
+                           a multiple of 32)                                      */
   int32_t tau_random;   /* nonzero: draw tau_i ~ Bernoulli(0.5) per trial          */
   int32_t k_uniform;    /* 1..8: every chain has this length; 0: lengths vary      */
   float stall_tol;      /* FP32 resolution of C: a walk whose line search can no
@@ -81,6 +82,21 @@ typedef struct mpg_params {
                            for k >= 6, or for a walk stopped by stall_tol, the
                            vertices are polished and G recomputed in FP64
                            (0: always FP64)                                     */
+  /* Schedule of the batched mode.  None of these changes a result: every chain
+   * is walked, and every trial drawn, with the same arithmetic whatever the
+   * schedule (mpg_autotune picks them by timing). */
+  int32_t fp64_k;       /* chains of this length or longer always take the FP64
+                           geometry term (0 = 6; 1..6 allowed, so the split can
+                           only move toward more FP64)                         */
+  int32_t ctas_per_sm;  /* resident CTAs per SM of the persistent kernels
+                           (0 = the occupancy maximum)                          */
+  int32_t refill_every; /* passes between work-queue refills of idle lanes in the
+                           persistent kernels (0 or 1 = every pass; a warp whose
+                           lanes are all idle refills at once)                  */
+  int32_t trial_sync_rounds; /* Bernoulli: rounds that draw one trial per chain
+                           before the parallel rounds (0 = 2; 1..8)              */
+  int32_t trial_batch;  /* Bernoulli: parallel trials per chain in the first
+                           parallel round (0 = 8; 1..4096), x4 each round after */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
@@ -255,6 +271,9 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* scene, const mp
 mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell,
                             const float* omega, const float* w, int32_t R, const int32_t* R_dev,
                             int32_t weight_shift, cudaStream_t stream);
+/* Empties the guide (counts and prefix sums to zero) on `stream`, for a new
+ * training pass (Sec. 5.6: each pass builds its guide from its own samples). */
+mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t stream);
 /* Records of the admissible chains of a batch for mpg_guide_update: compacts
  * (cell, w_D = unit(x_1 - x_D), w = contrib/A_L) of chains with contrib > 0 into
  * cell_out[B], omega_out[3][B] and w_out[B] (capacity B, record order
@@ -287,6 +306,51 @@ mpg_status mpg_trace_rays(mpg_ctx* ctx, const mpg_scene* scene, const float* o, 
 /* FP32 peak probe: a dependent-FFMA loop over the whole GPU; writes the
  * achieved FP32 FLOP/s (host double) after synchronising `stream`. */
 mpg_status mpg_fp32_peak(mpg_ctx* ctx, double* flops, cudaStream_t stream);
+/* FP64 peak probe: the same loop with DFMA (FP64 FLOP/s). */
+mpg_status mpg_fp64_peak(mpg_ctx* ctx, double* flops, cudaStream_t stream);
+
+/* Captured steps.  The paper runs its chains one by one on CPU threads; on the
+ * GPU a whole batched step (seeds, walk, contribution with its Bernoulli rounds,
+ * records, guide update: several dozen launches over up to eight concurrent
+ * streams) is recorded once as a CUDA graph and replayed with one launch.
+ *
+ * mpg_graph_begin starts a thread-local stream capture on `stream`: the library
+ * calls that follow on that stream (from this thread, on this context) are
+ * recorded, not run, until mpg_graph_end, which instantiates the graph.  Calls
+ * recorded this way add the graph's device counter to their rng_offset; the
+ * counter starts at 0 and the graph adds `rng_advance` to it at the end of each
+ * replay, so replay r draws with rng_offset + r * rng_advance and a replayed
+ * loop never repeats its random numbers.  Launch timing (mpg_ctx_set_profile)
+ * is suspended while recording.  Capacity: the library's context buffers
+ * grow only outside a capture, so run the same sequence once uncaptured first;
+ * a recorded call that would have to grow them fails with MPG_ERR_INVALID_ARG.
+ * After a failed recorded call, still end the capture with mpg_graph_end and
+ * destroy the (incomplete) graph it returns.  The device pointers of the
+ * recorded calls are baked into the graph: keep them alive and in place.
+ * Synchronous (allocates the counter). */
+typedef struct mpg_graph mpg_graph;
+mpg_status mpg_graph_begin(mpg_ctx* ctx, cudaStream_t stream, uint64_t rng_advance);
+mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t stream, mpg_graph** out);
+/* Replays the graph on `stream` (asynchronous, one graph launch). */
+mpg_status mpg_graph_launch(mpg_graph* graph, cudaStream_t stream);
+/* Kernel launches inside one replay. */
+mpg_status mpg_graph_kernels(const mpg_graph* graph, int64_t* count);
+void mpg_graph_destroy(mpg_graph* graph);
+
+/* Autotuner of the batched schedule (block_threads, ctas_per_sm, refill_every,
+ * trial_sync_rounds, trial_batch, fp64_k).  Times candidate schedules by
+ * running the step seeds -> walk -> contribution on the given batch (same
+ * rng_seed and rng_offset for every candidate, so each one does identical
+ * work; the chain arrays are overwritten) and returns in *out the input
+ * parameters with the fastest schedule, and in *best_ms its time.  Coordinate
+ * descent over one group at a time (tile shape, refill cadence, Bernoulli
+ * rounds, FP64 split); each candidate is timed `repeats` times (minimum).
+ * The outputs of the step go to scratch the call allocates and frees.
+ * Synchronous; walk_mode must be MPG_WALK_BATCHED. */
+mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
+                        mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
+                        const mpg_params* in, int32_t repeats, mpg_params* out,
+                        double* best_ms, cudaStream_t stream);
 
 #ifdef __cplusplus
 }

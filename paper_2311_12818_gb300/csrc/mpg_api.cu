@@ -82,6 +82,12 @@ struct mpg_ctx {
   uint8_t* t_status = nullptr;
   uint8_t* t_iters = nullptr;
   bool stats_on = true;
+  // stream capture in progress (mpg_graph_begin .. mpg_graph_end)
+  bool capturing = false;
+  bool profile_saved = false;
+  unsigned long long* cap_rng = nullptr;  // the recorded graph's random-number counter
+  uint64_t cap_advance = 0;
+  int64_t cap_launch0 = 0;
   cudaStream_t aux[MAXK] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[MAXK] = {};
@@ -259,7 +265,10 @@ mpg_status check_params(const mpg_params* p) {
       !(p->ray_eps > 0.0f) || !(p->sing_eps >= 0.0f) || !(p->dedup_eps > 0.0f) || p->max_trials < 1 || p->max_trials > (1 << 24) ||
       !(p->alpha >= 0.0f && p->alpha <= 1.0f) || p->weight_shift < 0 || p->weight_shift > 60 ||
       (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
-      p->block_threads < 0 || p->block_threads > 1024 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) || !(p->fp64_tol >= 0.0f))
+      p->block_threads < 0 || p->block_threads > 128 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) ||
+      !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
+      p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < 0 || p->trial_sync_rounds > 8 ||
+      p->trial_batch < 0 || p->trial_batch > 4096)
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -288,6 +297,13 @@ cudaEvent_t pooled_event(mpg_ctx* ctx);
 template <class F>
 void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn);
 
+// A call recorded into a graph cannot grow the context's buffers.
+mpg_status capture_grow_error() {
+  return fail(MPG_ERR_INVALID_ARG,
+              "the context's buffers are too small for this batch and cannot grow during a capture: "
+              "run the same calls once uncaptured first");
+}
+
 // Which per-K launches to make, and over which work list.
 struct Plan {
   int K[MAXK];
@@ -306,6 +322,7 @@ mpg_status make_plan(mpg_ctx* ctx, const mpg_chains* c, const mpg_params* p, int
   for (int k = 1; k <= MAXK; ++k) plan.K[plan.nK++] = k;
   if (p->walk_mode == MPG_WALK_PLAIN) return MPG_OK;
   if (ctx->order_cap < c->B) {
+    if (ctx->capturing) return capture_grow_error();
     if (ctx->d_order) cudaFree(ctx->d_order);
     ctx->d_order = nullptr;
     CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * (size_t)c->B));
@@ -350,7 +367,9 @@ void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn) {
   }
 }
 
-DCtx dctx(mpg_ctx* ctx, int kind) { return DCtx{ctx->d_err, ctx->stats_on ? ctx->d_stats + 16 * kind : nullptr}; }
+DCtx dctx(mpg_ctx* ctx, int kind) {
+  return DCtx{ctx->d_err, ctx->stats_on ? ctx->d_stats + 16 * kind : nullptr, ctx->capturing ? ctx->cap_rng : nullptr};
+}
 
 // Runs fn(K, stream) for each planned K, on forked streams when concurrent.
 template <class F>
@@ -373,8 +392,9 @@ mpg_status run_plan(mpg_ctx* ctx, const Plan& plan, cudaStream_t st, F fn) {
 
 int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threads : 128; }
 
-int grid_of(mpg_ctx* ctx, int which, int K, int block, int B, bool persistent) {
+int grid_of(mpg_ctx* ctx, const mpg_params* P, int which, int K, int block, int B, bool persistent) {
   int per_sm = blocks_per_sm(which, K, ctx->stats_on, block);
+  if (P->ctas_per_sm > 0) per_sm = std::min(per_sm, P->ctas_per_sm);
   int full = ctx->sms * per_sm;
   int need = (B + block - 1) / block;
   return persistent ? std::max(1, std::min(full, need)) : std::max(1, need);
@@ -675,7 +695,7 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* 
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_SEED, s2, 1, [&] {
       launch_seed(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, dc,
-                  grid_of(ctx, 0, K, block, c.B, true), block, s2);
+                  grid_of(ctx, P, 0, K, block, c.B, true), block, s2);
     });
   });
 }
@@ -697,13 +717,13 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
     return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
       timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
         launch_walk_p(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, ctx->d_queue + 32 * K,
-                      grid_of(ctx, 4, K, block, c.B, true), block, s2);
+                      grid_of(ctx, P, 4, K, block, c.B, true), block, s2);
       });
     });
   }
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
-      launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, 1, K, block, c.B, true), block, s2);
+      launch_walk(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, grid_of(ctx, P, 1, K, block, c.B, true), block, s2);
     });
   });
 }
@@ -726,6 +746,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   DChains c = to_dev(chains);
   DCtx dcc = dctx(ctx, MPG_KERNEL_CONTRIB), dcb = dctx(ctx, MPG_KERNEL_BERNOULLI), dcw = dctx(ctx, MPG_KERNEL_WALK);
   if (ctx->fp64_cap < c.B) {
+    if (ctx->capturing) return capture_grow_error();
     cudaFree(ctx->d_fp64);
     ctx->d_fp64 = nullptr;
     ctx->fp64_cap = 0;
@@ -748,6 +769,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
   const bool batched = P->walk_mode == MPG_WALK_BATCHED;
   if (batched) {
     if (ctx->bern_cap < c.B) {
+      if (ctx->capturing) return capture_grow_error();
       void** bufs[] = {(void**)&ctx->d_list[0], (void**)&ctx->d_list[1], (void**)&ctx->d_nbest, (void**)&ctx->t_x,
                        (void**)&ctx->t_surf, (void**)&ctx->t_prim, (void**)&ctx->t_bary, (void**)&ctx->t_status,
                        (void**)&ctx->t_iters};
@@ -777,14 +799,14 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     oK.fp64_count = ctx->d_fp64_count + K;
     oK.fp64_base = (plan.w.base ? plan.w.base : ctx->d_zero) + K;
     timed(ctx, MPG_KERNEL_CONTRIB, s2, 2, [&] {
-      launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, 2, K, block, c.B, true), block,
+      launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, P, 2, K, block, c.B, true), block,
                      s2);
       launch_contrib64(K, sc->S, c, *P, oK, ctx->sms * 2, s2);
     });
     if (!batched) {
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
         launch_bernoulli(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, plan.w, key, rng_offset, *P, o, dcb,
-                         grid_of(ctx, 3, K, block, c.B, true), block, s2);
+                         grid_of(ctx, P, 3, K, block, c.B, true), block, s2);
       });
       return;
     }
@@ -792,7 +814,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     // trial t; the chains left after T1 go to rounds of TB = 8, 32, 128, ...
     // parallel trials.  Each round lasts as long as its slowest walk, so few
     // rounds keep the pass short.
-    const int T1 = std::min(2, P->max_trials);
+    const int T1 = std::min(P->trial_sync_rounds > 0 ? P->trial_sync_rounds : 2, P->max_trials);
     int* lists[2] = {ctx->d_list[0], ctx->d_list[1]};
     int* counts[2] = {ctx->d_nlist, ctx->d_nlist + (MAXK + 1)};
     const int* base = plan.w.base ? plan.w.base : ctx->d_zero;
@@ -808,11 +830,11 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       DWork tw{lists[cur], base, counts[cur]};
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
         launch_trial_seed(K, sc->S, guide ? &g : nullptr, c, tc, lists[cur], base, counts[cur], key, rng_offset, *P,
-                          dcb, t, grid_of(ctx, 5, K, block, c.B, true), block, s2);
+                          dcb, t, grid_of(ctx, P, 5, K, block, c.B, true), block, s2);
       });
       // trial walks run the walk kernel and are tallied with the walk family
       timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
-        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t, grid_of(ctx, 4, K, block, c.B, true), block,
+        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t, grid_of(ctx, P, 4, K, block, c.B, true), block,
                       s2);
       });
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
@@ -821,7 +843,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       cur = nxt;
     }
-    int t0 = T1 + 1, TB = 8;
+    int t0 = T1 + 1, TB = P->trial_batch > 0 ? P->trial_batch : 8;
     for (int r = 0; t0 <= P->max_trials && r < 14; ++r) {
       if (r == 13 || t0 + TB - 1 > P->max_trials) TB = P->max_trials - t0 + 1;  // the last round reaches the cap
       int t_end = t0 + TB - 1;
@@ -830,7 +852,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
         launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q + 10 + r,
                           lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, TB,
-                          grid_of(ctx, 6, K, block, c.B, true), block, s2);
+                          grid_of(ctx, P, 6, K, block, c.B, true), block, s2);
         launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
                            lists[nxt], counts[nxt] + K, dcb.stats, ctx->sms, s2);
       });
@@ -857,6 +879,18 @@ mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t
   timed(ctx, MPG_KERNEL_AUX, st, R > 0 ? 2 : 1,
         [&] { launch_guide_update(g, cell, omega, w, R, R_dev, shift, ctx->d_err, ctx->sms, st); });
   LAUNCH_CHECK("guide update");
+  return MPG_OK;
+}
+
+mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t st) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  DGuide g;
+  mpg_status s;
+  if ((s = check_guide(guide, g))) return s;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t bytes = sizeof(uint64_t) * (size_t)guide->n_cells * (size_t)guide->n_theta * (size_t)guide->n_phi;
+  CUDA_TRY(cudaMemsetAsync(guide->counts, 0, bytes, st));
+  CUDA_TRY(cudaMemsetAsync(guide->cdf, 0, bytes, st));
   return MPG_OK;
 }
 
@@ -916,6 +950,236 @@ mpg_status mpg_fp32_peak(mpg_ctx* ctx, double* flops, cudaStream_t st) {
   CUDA_TRY(cudaSetDevice(ctx->device));
   *flops = run_fp32_peak(ctx->d_scratch, ctx->sms, st);
   LAUNCH_CHECK("fp32 peak");
+  return MPG_OK;
+}
+
+mpg_status mpg_fp64_peak(mpg_ctx* ctx, double* flops, cudaStream_t st) {
+  if (!ctx || !flops) return fail(MPG_ERR_INVALID_ARG, "ctx or flops is NULL");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  *flops = run_fp64_peak(ctx->d_scratch, ctx->sms, st);
+  LAUNCH_CHECK("fp64 peak");
+  return MPG_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Captured steps (CUDA graphs).
+// ---------------------------------------------------------------------------
+struct mpg_graph {
+  mpg_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long* counter = nullptr;
+  int64_t kernels = 0;
+};
+
+extern "C" {
+
+mpg_status mpg_graph_begin(mpg_ctx* ctx, cudaStream_t st, uint64_t rng_advance) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  if (ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "a capture is already in progress on this context");
+  if (st == 0 || st == cudaStreamLegacy || st == cudaStreamPerThread)
+    return fail(MPG_ERR_INVALID_ARG, "capture needs a created (non-default) stream");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  unsigned long long* counter = nullptr;
+  CUDA_TRY(cudaMalloc(&counter, sizeof(unsigned long long)));
+  cudaError_t e = cudaMemset(counter, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaFree(counter);
+    return fail(MPG_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  }
+  ctx->capturing = true;
+  ctx->cap_rng = counter;
+  ctx->profile_saved = ctx->profile;
+  ctx->profile = false;
+  ctx->cap_launch0 = ctx->launches;
+  // the advance is recorded now and runs last: it is the final node on the
+  // capture stream, after every recorded call has joined back onto it
+  ctx->cap_advance = rng_advance;
+  return MPG_OK;
+}
+
+mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t st, mpg_graph** out) {
+  if (!ctx || !out) return fail(MPG_ERR_INVALID_ARG, "ctx or out is NULL");
+  *out = nullptr;
+  if (!ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "no capture in progress on this context");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  launch_rng_advance(ctx->cap_rng, ctx->cap_advance, st);
+  cudaError_t le = cudaGetLastError();
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  mpg_graph* g = new mpg_graph();
+  g->ctx = ctx;
+  g->counter = ctx->cap_rng;
+  g->kernels = ctx->launches - ctx->cap_launch0 + 1;
+  ctx->launches = ctx->cap_launch0;
+  ctx->capturing = false;
+  ctx->cap_rng = nullptr;
+  ctx->profile = ctx->profile_saved;
+  if (le == cudaSuccess && e == cudaSuccess && graph) {
+    g->graph = graph;
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+  } else if (e == cudaSuccess) {
+    e = le != cudaSuccess ? le : cudaErrorStreamCaptureInvalidated;
+  }
+  if (e != cudaSuccess || !g->exec) {
+    if (graph) cudaGraphDestroy(graph);
+    g->graph = nullptr;
+    cudaFree(g->counter);
+    delete g;
+    return fail(MPG_ERR_CUDA, "capture failed: %s", cudaGetErrorString(e));
+  }
+  *out = g;
+  return MPG_OK;
+}
+
+mpg_status mpg_graph_launch(mpg_graph* g, cudaStream_t st) {
+  if (!g || !g->exec) return fail(MPG_ERR_INVALID_ARG, "graph is NULL");
+  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  CUDA_TRY(cudaGraphLaunch(g->exec, st));
+  g->ctx->launches += g->kernels;
+  return MPG_OK;
+}
+
+mpg_status mpg_graph_kernels(const mpg_graph* g, int64_t* count) {
+  if (!g || !count) return fail(MPG_ERR_INVALID_ARG, "graph or count is NULL");
+  *count = g->kernels;
+  return MPG_OK;
+}
+
+void mpg_graph_destroy(mpg_graph* g) {
+  if (!g) return;
+  cudaSetDevice(g->ctx->device);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  cudaFree(g->counter);
+  delete g;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the batched schedule.
+// ---------------------------------------------------------------------------
+mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guide, mpg_chains* chains,
+                        uint64_t rng_seed, uint64_t rng_offset, const mpg_params* in, int32_t repeats,
+                        mpg_params* out, double* best_ms, cudaStream_t st) {
+  if (!ctx || !sc || !in || !out || !chains) return fail(MPG_ERR_INVALID_ARG, "NULL argument");
+  mpg_status s;
+  if ((s = check_chains(chains, true)) || (s = check_params(in))) return s;
+  if (in->walk_mode != MPG_WALK_BATCHED) return fail(MPG_ERR_INVALID_ARG, "the autotuner tunes the batched mode");
+  if (ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "cannot tune during a capture");
+  if (repeats < 1 || repeats > 16) return fail(MPG_ERR_INVALID_ARG, "repeats %d out of 1..16", repeats);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  const size_t B = (size_t)chains->B, Q = (size_t)chains->Q;
+  auto up = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t oG = 0, oK = oG + up(4 * B), oT = oK + up(4 * B), oN = oT + up(4 * B), oC = oN + up(4 * B),
+               oW = oC + up(B), oE = oW + up(4 * B), total = oE + up(4 * Q);
+  char* scratch = nullptr;
+  CUDA_TRY(cudaMalloc(&scratch, total));
+  // the tuner's own work is kept out of the caller's counters and timings
+  unsigned long long saved[16 * MPG_KERNEL_KINDS];
+  cudaError_t e = cudaMemcpy(saved, ctx->d_stats, sizeof(saved), cudaMemcpyDeviceToHost);
+  const bool prof = ctx->profile;
+  const int64_t launches = ctx->launches;
+  ctx->profile = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto time_one = [&](const mpg_params& P, double& ms) -> mpg_status {
+    ms = 1e300;
+    for (int r = 0; r <= repeats; ++r) {  // the first run is a warm-up
+      mpg_status rs;
+      CUDA_TRY(cudaEventRecord(e0, st));
+      if ((rs = mpg_sample_seeds(ctx, sc, guide, chains, rng_seed, rng_offset, &P, st)) ||
+          (rs = mpg_manifold_walk(ctx, sc, chains, &P, st)) ||
+          (rs = mpg_chain_contribution(ctx, sc, guide, chains, rng_seed, rng_offset, &P, (float*)(scratch + oG),
+                                       (float*)(scratch + oK), (float*)(scratch + oT), (uint32_t*)(scratch + oN),
+                                       (uint8_t*)(scratch + oC), (float*)(scratch + oW), (float*)(scratch + oE), st)))
+        return rs;
+      CUDA_TRY(cudaEventRecord(e1, st));
+      CUDA_TRY(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+      if (r > 0) ms = std::min(ms, (double)t);
+    }
+    return MPG_OK;
+  };
+  mpg_params best = *in;
+  double bms = 0.0;
+  if (e == cudaSuccess) s = time_one(best, bms);
+  // Coordinate descent, one group of schedule fields at a time.
+  auto group = [&](const std::vector<mpg_params>& cands) -> mpg_status {
+    for (const mpg_params& P : cands) {
+      double ms;
+      mpg_status rs = time_one(P, ms);
+      if (rs) return rs;
+      if (ms < bms) { bms = ms; best = P; }
+    }
+    return MPG_OK;
+  };
+  if (e == cudaSuccess && !s) {  // tile shape: threads per CTA x resident CTAs per SM
+    std::vector<mpg_params> c;
+    const int cur_block = best.block_threads ? best.block_threads : 128;
+    for (int block : {32, 64, 128}) {
+      // resident CTAs: the occupancy maximum (0) or half of it, from the k = 2 walk kernel
+      int occ = blocks_per_sm(4, 2, ctx->stats_on, block);
+      for (int ctas : {0, occ / 2}) {
+        if (ctas != 0 && (ctas < 1 || ctas >= occ)) continue;
+        if (block == cur_block && ctas == best.ctas_per_sm) continue;  // the starting point
+        mpg_params P = best;
+        P.block_threads = block;
+        P.ctas_per_sm = ctas;
+        c.push_back(P);
+      }
+    }
+    s = group(c);
+  }
+  if (e == cudaSuccess && !s) {  // refill cadence of the persistent kernels
+    std::vector<mpg_params> c;
+    for (int r : {1, 2, 4, 8}) {
+      if (r == std::max(1, best.refill_every)) continue;
+      mpg_params P = best;
+      P.refill_every = r;
+      c.push_back(P);
+    }
+    s = group(c);
+  }
+  if (e == cudaSuccess && !s) {  // Bernoulli rounds: synchronous rounds x first parallel batch
+    std::vector<mpg_params> c;
+    for (int t1 : {1, 2, 3})
+      for (int tb : {4, 8, 16, 32}) {
+        if (t1 == (best.trial_sync_rounds ? best.trial_sync_rounds : 2) && tb == (best.trial_batch ? best.trial_batch : 8))
+          continue;
+        mpg_params P = best;
+        P.trial_sync_rounds = t1;
+        P.trial_batch = tb;
+        c.push_back(P);
+      }
+    s = group(c);
+  }
+  if (e == cudaSuccess && !s) {  // FP32/FP64 split: only toward more FP64
+    std::vector<mpg_params> c;
+    for (int k : {5, 4}) {
+      if (k >= fp64_k_of(best)) continue;
+      mpg_params P = best;
+      P.fp64_k = k;
+      c.push_back(P);
+    }
+    s = group(c);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e2 == cudaSuccess) e2 = cudaMemcpy(ctx->d_stats, saved, sizeof(saved), cudaMemcpyHostToDevice);
+  cudaFree(scratch);
+  ctx->profile = prof;
+  ctx->launches = launches;
+  if (e != cudaSuccess) return fail(MPG_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+  if (s) return s;
+  if (e2 != cudaSuccess) return fail(MPG_ERR_CUDA, "autotune: %s", cudaGetErrorString(e2));
+  *out = best;
+  if (best_ms) *best_ms = bms;
   return MPG_OK;
 }
 

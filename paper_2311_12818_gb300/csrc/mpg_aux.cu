@@ -246,6 +246,47 @@ __global__ void __launch_bounds__(256) k_ffma(float* out, int iters, float a, fl
   if (s == 1234.5f) out[0] = s;  // keeps the chains live
 }
 
+// FP64 peak probe: the same loop with DFMA.
+__global__ void __launch_bounds__(256) k_dfma(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x * 1e-3, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+      x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+  }
+  double s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+  if (s == 1234.5) out[0] = s;
+}
+
+double run_fp64_peak(float* scratch, int sms, cudaStream_t st) {
+  const int block = 256, per_sm = 8, iters = 256;
+  int grid = sms * per_sm;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_dfma<<<grid, block, 0, st>>>((double*)scratch, 8, 0.999, 1e-3);  // warm-up
+  cudaEventRecord(e0, st);
+  k_dfma<<<grid, block, 0, st>>>((double*)scratch, iters, 0.999, 1e-3);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  double flops = (double)grid * block * iters * 16.0 * 8.0 * 2.0;
+  return ms > 0.f ? flops / (ms * 1e-3) : 0.0;
+}
+
+// Advances a captured graph's random-number counter at the end of a replay.
+__global__ void k_rng_advance(unsigned long long* counter, unsigned long long delta) { *counter += delta; }
+
+void launch_rng_advance(unsigned long long* counter, unsigned long long delta, cudaStream_t st) {
+  k_rng_advance<<<1, 1, 0, st>>>(counter, delta);
+}
+
 double run_fp32_peak(float* scratch, int sms, cudaStream_t st) {
   const int block = 256, per_sm = 8, iters = 4096;
   int grid = sms * per_sm;

@@ -15,5 +15,7 @@ void launch_guide_records(const DChains& c, const float* contrib, float inv_area
 void launch_trace(const DScene& S, const float* o, const float* d, int n, float tmin, float tmax, float* t, int* surf,
                   int* prim, float* bary, int* err, unsigned long long* stats, bool st_on, int sms, cudaStream_t st);
 double run_fp32_peak(float* scratch, int sms, cudaStream_t st);
+double run_fp64_peak(float* scratch, int sms, cudaStream_t st);  // scratch: 8-byte aligned
+void launch_rng_advance(unsigned long long* counter, unsigned long long delta, cudaStream_t st);
 
 }  // namespace mpg

@@ -44,9 +44,19 @@ struct DOut {
 };
 
 struct DCtx {
-  int* err;                      // device error word
-  unsigned long long* stats;     // [16] counters of the kernel family (mpg_stats layout)
+  int* err;                          // device error word
+  unsigned long long* stats;         // [16] counters of the kernel family (mpg_stats layout)
+  const unsigned long long* rng_add; // NULL, or a device counter added to rng offsets (captured graphs)
 };
+
+// Random-number offset of a launch: the host value plus, inside a replayed
+// graph, the graph's device counter.
+__device__ __forceinline__ uint64_t rng_offset(uint64_t offset, const DCtx& ctx) {
+  return ctx.rng_add ? offset + *ctx.rng_add : offset;
+}
+
+// Length from which the geometry term is always formed in FP64.
+__host__ __device__ __forceinline__ int fp64_k_of(const mpg_params& P) { return P.fp64_k > 0 ? P.fp64_k : 6; }
 
 
 

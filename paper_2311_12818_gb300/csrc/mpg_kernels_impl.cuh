@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
                                               DWork w, uint2 key, uint64_t offset, mpg_params P, DCtx ctx) {
   Tally t = {};
   const int n = n_items<K>(w, c);
+  offset = rng_offset(offset, ctx);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int b = item<K>(w, c, i);
     if (b < 0) continue;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       // grazing cosine, or a walk that stopped at the FP32 resolution of C.
       // The chain is queued for k_contrib64, which polishes it and recomputes
       // G and kappa in FP64.
-      if (adm && (K >= 6 || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol)) && o.fp64_list) {
+      if (adm && (K >= fp64_k_of(P) || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol)) && o.fp64_list) {
         o.fp64_list[*o.fp64_base + atomicAdd(o.fp64_count, 1)] = b;
         t.c.ggt64++;
       }
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
   Tally t = {};
   const int n = n_items<K>(w, c);
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
+  offset = rng_offset(offset, ctx);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int b = item<K>(w, c, i);
     if (b < 0) continue;

@@ -98,8 +98,13 @@ __global__ void __launch_bounds__(128) k_walk_p(const __grid_constant__ DScene S
   int b = -1;
   bool done = false;
   const unsigned FULL = 0xffffffffu;
+  const int refill = P.refill_every > 1 ? P.refill_every : 1;
+  int pass = 0;
   while (true) {
-    int i = take_item(b < 0, queue, n, done);
+    // idle lanes refill every `refill` passes, or at once when the whole warp is idle
+    bool idle_warp = __all_sync(FULL, b < 0);
+    int i = take_item(b < 0 && (idle_warp || pass % refill == 0), queue, n, done);
+    ++pass;
     if (i >= 0) {
       int bb = item<K>(w, c, i);
       if (bb >= 0 && c.status[bb] == ST_SEEDED) {
@@ -167,6 +172,7 @@ __global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DSce
                                                     DCtx ctx, int t) {
   Tally tl = {};
   const int n = n_list[K];
+  offset = rng_offset(offset, ctx);
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     int b = list[base[K] + j];
     Ends e = load_ends(c, b);
@@ -228,6 +234,9 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
   const int* over = list + *base;
   const long long n = (long long)(*n_list) * TB;
+  offset = rng_offset(offset, ctx);
+  const int refill = P.refill_every > 1 ? P.refill_every : 1;
+  int pass = 0;
   const int n_items_i = n > 0x7fffffff ? 0x7fffffff : (int)n;
   WalkLane<K> L;
   Chain<K> target;
@@ -235,7 +244,10 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
   bool done = false;
   const unsigned FULL = 0xffffffffu;
   while (true) {
-    int i = take_item(b < 0, queue, n_items_i, done);
+    // idle lanes refill every `refill` passes, or at once when the whole warp is idle
+    bool idle_warp = __all_sync(FULL, b < 0);
+    int i = take_item(b < 0 && (idle_warp || pass % refill == 0), queue, n_items_i, done);
+    ++pass;
     if (i >= 0) {
       int bb = over[i / TB];
       int tt = t0 + i % TB;

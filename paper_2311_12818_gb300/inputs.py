@@ -285,6 +285,19 @@ def mixed(nx: int = 1024, ny: int = 512, spq: int = 8, seed: int = 0x4D50470004)
                     256, seed, scale, Params(dedup_eps=1e-4 * scale), (ny, nx))
 
 
+def water_rays(n: int, seed: int = 0x4D50470013):
+    """Ray batch for the standalone BVH pass on the water heightfield: origins
+    above (z = 2) or below (z = -1) the surface over [-1.1, 1.1]^2, aimed at
+    uniform points of the surface's bounding slab (|z| < 0.05).  Returns
+    (o, d) as [n, 3] float64."""
+    rng = np.random.default_rng(seed)
+    o = np.column_stack([rng.uniform(-1.1, 1.1, n), rng.uniform(-1.1, 1.1, n), rng.choice([-1.0, 2.0], n)])
+    tgt = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(-0.05, 0.05, n)])
+    d = tgt - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return o, d
+
+
 def upstream_grad(Q: int, seed: int = 0x4D50470005):
     """dL/dE per receiver point, U(0,1), for the adjoint workload."""
     return np.random.default_rng(seed).random(Q)

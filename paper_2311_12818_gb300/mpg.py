@@ -34,7 +34,11 @@ class mpg_params(C.Structure):
                 ("ray_eps", C.c_float), ("sing_eps", C.c_float), ("dedup_eps", C.c_float),
                 ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_float),
                 ("walk_mode", C.c_int32), ("block_threads", C.c_int32), ("tau_random", C.c_int32),
-                ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float)]
+                ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float),
+                ("fp64_k", C.c_int32), ("ctas_per_sm", C.c_int32), ("refill_every", C.c_int32),
+                ("trial_sync_rounds", C.c_int32), ("trial_batch", C.c_int32)]
+
+SCHEDULE_FIELDS = ["block_threads", "ctas_per_sm", "refill_every", "trial_sync_rounds", "trial_batch", "fp64_k"]
 
 
 class mpg_chains(C.Structure):
@@ -66,7 +70,8 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
-           "mpg_manifold_walk_noalloc"]
+           "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_end",
+           "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune"]
 
 _lib = None
 
@@ -93,6 +98,7 @@ def lib():
         L.mpg_scene_create.argtypes = [vp, vp, i32, vp, vp, i32, vp, i32, vp, C.POINTER(vp)]
         L.mpg_scene_destroy.argtypes = [vp]
         L.mpg_scene_destroy.restype = None
+        L.mpg_graph_destroy.restype = None
         L.mpg_scene_info.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.mpg_sample_seeds.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                        C.POINTER(mpg_params), vp]
@@ -105,8 +111,17 @@ def lib():
         L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp]
         L.mpg_trace_rays.argtypes = [vp, vp, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp]
         L.mpg_fp32_peak.argtypes = [vp, C.POINTER(C.c_double), vp]
+        L.mpg_fp64_peak.argtypes = [vp, C.POINTER(C.c_double), vp]
+        L.mpg_guide_clear.argtypes = [vp, C.POINTER(mpg_guide), vp]
+        L.mpg_graph_begin.argtypes = [vp, vp, u64]
+        L.mpg_graph_end.argtypes = [vp, vp, C.POINTER(vp)]
+        L.mpg_graph_launch.argtypes = [vp, vp]
+        L.mpg_graph_kernels.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.mpg_graph_destroy.argtypes = [vp]
+        L.mpg_autotune.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
+                                   C.POINTER(mpg_params), i32, C.POINTER(mpg_params), C.POINTER(C.c_double), vp]
         for n in EXPORTS[2:]:
-            if n not in ("mpg_ctx_destroy", "mpg_scene_destroy"):
+            if n not in ("mpg_ctx_destroy", "mpg_scene_destroy", "mpg_graph_destroy"):
                 getattr(L, n).restype = i32
         _lib = L
     return _lib
@@ -126,11 +141,17 @@ def _stream(stream=None):
     return C.c_void_p(s.cuda_stream)
 
 
-def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_uniform=0) -> mpg_params:
-    """mpg_params from an inputs.Params (FP32 copy of the solver constants)."""
-    return mpg_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps, p.max_trials,
-                      p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform,
-                      p.stall_tol, p.fp64_tol)
+def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_uniform=0, **schedule) -> mpg_params:
+    """mpg_params from an inputs.Params (FP32 copy of the solver constants);
+    `schedule` sets fields of SCHEDULE_FIELDS (0 = the library's default)."""
+    P = mpg_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps, p.max_trials,
+                   p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform,
+                   p.stall_tol, p.fp64_tol)
+    for f, v in schedule.items():
+        if f not in SCHEDULE_FIELDS:
+            raise TypeError("unknown schedule field %r" % f)
+        setattr(P, f, int(v))
+    return P
 
 
 class Context:
@@ -172,6 +193,11 @@ class Context:
     def fp32_peak(self, stream=None):
         v = C.c_double()
         _check(lib().mpg_fp32_peak(self.h, C.byref(v), _stream(stream)))
+        return v.value
+
+    def fp64_peak(self, stream=None):
+        v = C.c_double()
+        _check(lib().mpg_fp64_peak(self.h, C.byref(v), _stream(stream)))
         return v.value
 
     def __del__(self):
@@ -220,9 +246,8 @@ class Guide:
         return mpg_guide(self.n_cells, self.n_theta, self.n_phi, self.counts.data_ptr(), self.cdf.data_ptr(),
                          self.cos_theta.data_ptr(), self.phi_cos.data_ptr(), self.phi_sin.data_ptr())
 
-    def clear(self):
-        self.counts.zero_()
-        self.cdf.zero_()
+    def clear(self, ctx, stream=None):
+        mpg_guide_clear(ctx, self, stream)
 
 
 class Chains:
@@ -291,6 +316,65 @@ def mpg_sample_seeds(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, 
                                   rng_seed, rng_offset, C.byref(params), _stream(stream)))
 
 
+def mpg_guide_clear(ctx, guide, stream=None):
+    gs = guide.struct()
+    _check(lib().mpg_guide_clear(ctx.h, C.byref(gs), _stream(stream)))
+
+
+def mpg_autotune(ctx, scene, guide, chains, params, rng_seed, rng_offset=0, repeats=2, stream=None):
+    """Fastest batched schedule for this batch: (tuned mpg_params, ms per step)."""
+    cs = chains.struct()
+    gs = guide.struct() if guide is not None else None
+    out, ms = mpg_params(), C.c_double()
+    _check(lib().mpg_autotune(ctx.h, scene.h, C.byref(gs) if gs is not None else None, C.byref(cs), rng_seed,
+                              rng_offset, C.byref(params), repeats, C.byref(out), C.byref(ms), _stream(stream)))
+    return out, ms.value
+
+
+class Graph:
+    """Library calls recorded once on a side stream and replayed with one graph
+    launch (mpg_graph_*).  Use as a context manager around the calls; they are
+    recorded, not run.  Replay r draws its random numbers at rng_offset +
+    r * rng_advance."""
+
+    def __init__(self, ctx, rng_advance=0):
+        self.ctx, self.rng_advance, self.h = ctx, int(rng_advance), None
+        self.stream = torch.cuda.Stream(device=ctx.device)
+
+    def __enter__(self):
+        self._outer = torch.cuda.current_stream()
+        self.stream.wait_stream(self._outer)
+        self._ctx_mgr = torch.cuda.stream(self.stream)
+        self._ctx_mgr.__enter__()
+        _check(lib().mpg_graph_begin(self.ctx.h, _stream(self.stream), self.rng_advance))
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = C.c_void_p()
+        code = lib().mpg_graph_end(self.ctx.h, _stream(self.stream), C.byref(h))
+        self._ctx_mgr.__exit__(et, ev, tb)
+        self._outer.wait_stream(self.stream)
+        if et is None:
+            _check(code)
+            self.h = h
+        elif code == MPG_OK and h:
+            lib().mpg_graph_destroy(h)  # a recorded call failed: the graph is incomplete
+        return False
+
+    def launch(self, stream=None):
+        _check(lib().mpg_graph_launch(self.h, _stream(stream)))
+
+    def kernels(self):
+        n = C.c_int64()
+        _check(lib().mpg_graph_kernels(self.h, C.byref(n)))
+        return n.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().mpg_graph_destroy(self.h)
+            self.h = None
+
+
 def mpg_manifold_walk(ctx, scene, chains, params, stream=None):
     cs = chains.struct()
     _check(lib().mpg_manifold_walk(ctx.h, scene.h, C.byref(cs), C.byref(params), _stream(stream)))
@@ -342,13 +426,13 @@ def mpg_walk_adjoint(ctx, scene, chains, T, contrib, dL_dE, dL_dtheta, stream=No
                                   _ptr(dL_dtheta), _stream(stream)))
 
 
-def mpg_trace_rays(ctx, scene, o, d, tmin=1e-4, tmax=3.0e38, stream=None):
-    """o, d: [3, n] float32 device tensors."""
+def mpg_trace_rays(ctx, scene, o, d, tmin=1e-4, tmax=3.0e38, out=None, stream=None):
+    """o, d: [3, n] float32 device tensors; out: optional (t, surf, prim, bary)."""
     n = o.shape[1]
-    t = torch.empty(n, dtype=torch.float32, device="cuda")
-    surf = torch.empty(n, dtype=torch.int32, device="cuda")
-    prim = torch.empty(n, dtype=torch.int32, device="cuda")
-    bary = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    if out is None:
+        out = (torch.empty(n, dtype=torch.float32, device=o.device), torch.empty(n, dtype=torch.int32, device=o.device),
+               torch.empty(n, dtype=torch.int32, device=o.device), torch.empty((2, n), dtype=torch.float32, device=o.device))
+    t, surf, prim, bary = out
     _check(lib().mpg_trace_rays(ctx.h, scene.h, _ptr(o), _ptr(d), n, tmin, tmax, _ptr(t), _ptr(surf), _ptr(prim),
                                 _ptr(bary), _stream(stream)))
     return t, surf, prim, bary
