@@ -285,8 +285,11 @@ def run_ours(args, rank, world, local):
     peak_ffma = ctx.fp32_peak()
     peak_dfma = ctx.fp64_peak()
     kname = {"walk": "k_walk_p" if args.mode == "batched" else "k_walk", "bernoulli": "k_bern_round"}.get(dom, "k_" + dom)
+    traffic = profiled_traffic("k_walk_p__glass_sphere_1M.md") if kname == "k_walk_p" else None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_nominal / 1e12,
-                "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_nominal, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one primary-walk launch"
+                                  " (profiles/k_walk_p__glass_sphere_1M.md); null when the kernels changed since",
                 "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % (props.multi_processor_count, sm_max),
                 "peak_ffma_measured": peak_ffma / 1e12, "frac_of_ffma_measured": achieved / peak_ffma if peak_ffma else None,
                 "peak_fp64_dfma_measured": peak_dfma / 1e12,
@@ -345,6 +348,35 @@ def timed_loop(fn, steps, warmup, flush, stream, torch):
         b.synchronize()
         ms += a.elapsed_time(b)
     return ms / steps
+
+
+def kernel_digest():
+    """sha256 over the CUDA sources (file names and contents, sorted)."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2311_12818_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(summary):
+    """DRAM bytes per launch from a committed ncu summary under profiles/, or
+    None when the summary was taken on other kernel sources than these."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", summary)) as f:
+            text = f.read()
+    except OSError:
+        return None
+    dg = re.search(r"Kernel source digest: ([0-9a-f]{64})", text)
+    tb = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    if not dg or not tb or dg.group(1) != kernel_digest():
+        return None
+    return int(tb.group(1))
 
 
 def measured_hbm():
