@@ -4,7 +4,7 @@
 A step is one pass of the whole hot path over one batch: guided seed chains
 (Eq. deduction with the alpha-mixture of Sec. 5.5), Newton manifold walks,
 contributions T = kappa G L_o with Bernoulli-trial reciprocal probabilities
-(Sec. 5.7) and the irradiance estimate (Eq. ThroughputMC), then the guide
+(Sec. 5.8, reciprocal probability estimation) and the irradiance estimate (Eq. ThroughputMC), then the guide
 records and histogram update (Eq. eq_weight).  The workload is the refractive
 caustic through a glass sphere (radius 1, IOR 1.5, k = 2, 0.2 x 0.2 area light
 at z = 4, 256 x 256 receiver points x 16 seeds = 1,048,576 chains, guide of
@@ -209,16 +209,8 @@ def run_ours(args, rank, world, local):
     total = ctx.stats()
     conv = total["converged"]
     t_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_ms, float(conv)], dtype=torch.float64, device=dev)
-        t_max = tt[:1].clone()
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        c_sum = tt[1:].clone()
-        dist.all_reduce(c_sum, op=dist.ReduceOp.SUM)
-        t_ms, conv_all = float(t_max.item()), float(c_sum.item())
-    else:
-        conv_all = float(conv)
+    from paper_2311_12818_gb300 import dist as D
+    t_ms, conv_all = D.job_throughput(t_ms, float(conv), device=dev)  # max time, summed walks
     value = conv_all / (t_ms * 1e-3)
 
     # ---- attribution: the same steps uncaptured, each launch bracketed by
@@ -305,7 +297,8 @@ def run_ours(args, rank, world, local):
                    "k": 2, "walk_mode": args.mode, "graph": graph is not None,
                    "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
                    "parallelism": "replicas x%d" % world,
-                   "counted_walks": "first walks + Bernoulli trial walks that converged"},
+                   "counted_walks": "walks that converged: the first walks and the trial walks of each chain's"
+                                    " sequential Bernoulli loop up to its first recurrence"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roofline,

@@ -94,9 +94,11 @@ typedef struct mpg_params {
                            persistent kernels (0 or 1 = every pass; a warp whose
                            lanes are all idle refills at once)                  */
   int32_t trial_sync_rounds; /* Bernoulli: rounds that draw one trial per chain
-                           before the parallel rounds (0 = 2; 1..8)              */
+                           before the parallel rounds (0 = 2; -1 = none; 1..8)   */
   int32_t trial_batch;  /* Bernoulli: parallel trials per chain in the first
-                           parallel round (0 = 8; 1..4096), x4 each round after */
+                           parallel round (0 = 64; 1..4096), x4 each round after;
+                           issued trial-major, so trials past a chain's first
+                           success are mostly skipped                          */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
@@ -146,11 +148,16 @@ typedef struct mpg_stats {
   uint64_t node_tests;       /* BVH child-box tests                               */
   uint64_t tri_tests;        /* ray/triangle tests                                */
   uint64_t walks;            /* walks started                                     */
-  uint64_t converged;        /* walks converged                                   */
+  uint64_t converged;        /* walks converged: first walks, and the trial walks
+                                a sequential Bernoulli loop runs (up to each
+                                chain's first recurrence), whatever the schedule */
   uint64_t ggt_rows;         /* block rows of the 2-column geometry-term solves   */
   uint64_t trials;           /* Bernoulli trials drawn                            */
   uint64_t seeds;            /* seed directions drawn (first draws and trials)    */
   uint64_t ggt_fp64;         /* geometry terms recomputed in FP64                 */
+  uint64_t uncounted;        /* converged trial walks of the parallel Bernoulli
+                                rounds left out of `converged` (their record
+                                buffer of 8 entries per chain overflowed)      */
 } mpg_stats;
 
 /* Kernel families, for per-family counters and launch timings. */
@@ -250,7 +257,7 @@ mpg_status mpg_manifold_walk_noalloc(const mpg_scene* scene, mpg_chains* chains,
  * positive end cosines), the generalized geometry term G by the implicit
  * function theorem (in FP64 for k >= 6 and ill-conditioned chains, see
  * fp64_tol), kappa (Fresnel / mirror and
- * radiance scaling), T = kappa G L_o; then Bernoulli trials (Sec. 5.7): fresh
+ * radiance scaling), T = kappa G L_o; then Bernoulli trials (Sec. 5.8, reciprocal probability estimation): fresh
  * seeds with the same n are walked until one reaches the same solution (FP64
  * distance test), N = trial index, <1/P> = N / P(n) (capped at max_trials,
  * `capped` set).  Writes contrib[b] = A_L T <1/P> (A_L = light area, 1 for a
@@ -272,7 +279,7 @@ mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t
                             const float* omega, const float* w, int32_t R, const int32_t* R_dev,
                             int32_t weight_shift, cudaStream_t stream);
 /* Empties the guide (counts and prefix sums to zero) on `stream`, for a new
- * training pass (Sec. 5.6: each pass builds its guide from its own samples). */
+ * training pass (Sec. 5.8: the distributions are built from the last training iteration's samples only). */
 mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t stream);
 /* Records of the admissible chains of a batch for mpg_guide_update: compacts
  * (cell, w_D = unit(x_1 - x_D), w = contrib/A_L) of chains with contrib > 0 into

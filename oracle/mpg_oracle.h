@@ -9,7 +9,7 @@
  *   seed chain  = p_0 / guided mixture direction + deduction by ray casts (Eq. deduction, Sec. 5.3-5.5)
  *   manifold walk = Newton on the half-vector constraint + reprojection (Sec. 3, "Manifold walks")
  *   contribution T = kappa * G * L_o                                  (Eq. ThroughputEval)
- *   reciprocal probability by Bernoulli trials, n reused             (Sec. 5.7)
+ *   reciprocal probability by Bernoulli trials, n reused             (Sec. 5.8, reciprocal probability estimation)
  *   guide histogram update with w = T <1/P>                          (Eq. eq_weight)
  *
  * Arrays are caller-owned, array-of-structures, float64 unless stated:

@@ -264,7 +264,7 @@ def adjoint(wl, scene, chains, weight, threads=None):
 
 
 def irradiance(wl, T, N, admissible):
-    """E(x_D) = (1/M) sum_seeds A_L T <1/P>, <1/P> = N / P(n)   (Eq. ThroughputMC, Sec. 5.7)."""
+    """E(x_D) = (1/M) sum_seeds A_L T <1/P>, <1/P> = N / P(n)   (Eq. ThroughputMC; Sec. 5.8)."""
     c = np.where(admissible.astype(bool), wl.light_area * T * N.astype(np.float64) / wl.pn, 0.0)
     return c.reshape(wl.Q, wl.spq).sum(axis=1) / wl.spq
 

@@ -73,6 +73,8 @@ struct mpg_ctx {
   int fp64_cap = 0;
   int* d_list[2] = {nullptr, nullptr};
   unsigned* d_nbest = nullptr;
+  uint2* d_pairs = nullptr;      // [8B] converged trial walks of the parallel rounds (chain, trial)
+  int* d_npairs = nullptr;       // [MAXK+1] pair counts per chain length
   int bern_cap = 0;
   // trial chain state of the Bernoulli rounds (same layout as mpg_chains)
   float* t_x = nullptr;
@@ -267,7 +269,7 @@ mpg_status check_params(const mpg_params* p) {
       (p->walk_mode != MPG_WALK_PLAIN && p->walk_mode != MPG_WALK_BATCHED) || p->k_uniform < 0 || p->k_uniform > MAXK ||
       p->block_threads < 0 || p->block_threads > 128 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) ||
       !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
-      p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < 0 || p->trial_sync_rounds > 8 ||
+      p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
       p->trial_batch < 0 || p->trial_batch > 4096)
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
@@ -392,6 +394,9 @@ mpg_status run_plan(mpg_ctx* ctx, const Plan& plan, cudaStream_t st, F fn) {
 
 int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threads : 128; }
 
+// Synchronous Bernoulli rounds before the parallel ones (-1: none, 0: default).
+int sync_rounds_of(const mpg_params* p) { return p->trial_sync_rounds < 0 ? 0 : p->trial_sync_rounds > 0 ? p->trial_sync_rounds : 2; }
+
 int grid_of(mpg_ctx* ctx, const mpg_params* P, int which, int K, int block, int B, bool persistent) {
   int per_sm = blocks_per_sm(which, K, ctx->stats_on, block);
   if (P->ctas_per_sm > 0) per_sm = std::min(per_sm, P->ctas_per_sm);
@@ -427,6 +432,7 @@ mpg_status mpg_ctx_create(int32_t device, mpg_ctx** out) {
             cudaMalloc(&c->d_nlist, sizeof(int) * 2 * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_zero, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMalloc(&c->d_fp64_count, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
+            cudaMalloc(&c->d_npairs, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_zero, 0, sizeof(int) * (MAXK + 1)) == cudaSuccess &&
             cudaMemset(c->d_err, 0, sizeof(int)) == cudaSuccess &&
             cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * 16 * MPG_KERNEL_KINDS) == cudaSuccess &&
@@ -448,7 +454,7 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaFree(c->d_err); cudaFree(c->d_stats); cudaFree(c->d_order); cudaFree(c->d_count);
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
   cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero); cudaFree(c->d_fp64); cudaFree(c->d_fp64_count);
-  cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest);
+  cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest); cudaFree(c->d_pairs); cudaFree(c->d_npairs);
   cudaFree(c->t_x); cudaFree(c->t_surf); cudaFree(c->t_prim); cudaFree(c->t_bary); cudaFree(c->t_status);
   cudaFree(c->t_iters);
   for (int i = 0; i < MAXK; ++i) {
@@ -479,15 +485,15 @@ mpg_status mpg_ctx_stats(mpg_ctx* c, int32_t kind, mpg_stats* out, int32_t reset
   if (!c) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
   if (kind < -1 || kind >= MPG_KERNEL_KINDS) return fail(MPG_ERR_INVALID_ARG, "kernel kind %d out of range", kind);
   CUDA_TRY(cudaSetDevice(c->device));
-  static_assert(sizeof(mpg_stats) == 15 * sizeof(uint64_t), "stats layout");
+  static_assert(sizeof(mpg_stats) == 16 * sizeof(uint64_t), "stats layout");
   if (out) {
     unsigned long long v[16 * MPG_KERNEL_KINDS];
     CUDA_TRY(cudaMemcpyAsync(v, c->d_stats, sizeof(v), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    uint64_t acc[15] = {0};
+    uint64_t acc[16] = {0};
     for (int k = 0; k < MPG_KERNEL_KINDS; ++k)
       if (kind < 0 || kind == k)
-        for (int i = 0; i < 15; ++i) acc[i] += v[16 * k + i];
+        for (int i = 0; i < 16; ++i) acc[i] += v[16 * k + i];
     memcpy(out, acc, sizeof(mpg_stats));
   }
   if (reset) {
@@ -772,7 +778,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       if (ctx->capturing) return capture_grow_error();
       void** bufs[] = {(void**)&ctx->d_list[0], (void**)&ctx->d_list[1], (void**)&ctx->d_nbest, (void**)&ctx->t_x,
                        (void**)&ctx->t_surf, (void**)&ctx->t_prim, (void**)&ctx->t_bary, (void**)&ctx->t_status,
-                       (void**)&ctx->t_iters};
+                       (void**)&ctx->t_iters, (void**)&ctx->d_pairs};
       for (void** b : bufs) { cudaFree(*b); *b = nullptr; }
       ctx->bern_cap = 0;
       size_t n = (size_t)c.B;
@@ -785,6 +791,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       CUDA_TRY(cudaMalloc(&ctx->t_bary, sizeof(float) * 2 * MAXK * n));
       CUDA_TRY(cudaMalloc(&ctx->t_status, n));
       CUDA_TRY(cudaMalloc(&ctx->t_iters, n));
+      CUDA_TRY(cudaMalloc(&ctx->d_pairs, sizeof(uint2) * PAIRS_PER_CHAIN * n));
       ctx->bern_cap = c.B;
     }
     CUDA_TRY(cudaMemsetAsync(ctx->d_queue, 0, sizeof(int) * 32 * (MAXK + 1), st));
@@ -810,18 +817,18 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       return;
     }
-    // Rounds t = 1..T1 (T1 = 2): every chain without a hit draws and walks
-    // trial t; the chains left after T1 go to rounds of TB = 8, 32, 128, ...
-    // parallel trials.  Each round lasts as long as its slowest walk, so few
-    // rounds keep the pass short.
-    const int T1 = std::min(P->trial_sync_rounds > 0 ? P->trial_sync_rounds : 2, P->max_trials);
+    // Synchronous rounds t = 1..T1: every chain without a hit draws and walks
+    // trial t; then parallel rounds of TB = TB0, 4 TB0, 16 TB0, ... trials per
+    // remaining chain, issued trial-major.  Each round lasts at least as long
+    // as its slowest walk, so few rounds keep the pass short.
+    const int T1 = std::min(sync_rounds_of(P), P->max_trials);
     int* lists[2] = {ctx->d_list[0], ctx->d_list[1]};
     int* counts[2] = {ctx->d_nlist, ctx->d_nlist + (MAXK + 1)};
     const int* base = plan.w.base ? plan.w.base : ctx->d_zero;
     int* q = ctx->d_queue + 32 * K;
     int small_grid = ctx->sms * 4;
     timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-      launch_trial_init(K, sc->S, c, plan.w, o, lists[0], base, counts[0], small_grid, s2);
+      launch_trial_init(K, sc->S, c, plan.w, o, lists[0], base, counts[0], ctx->d_nbest, small_grid, s2);
     });
     int cur = 0;
     for (int t = 1; t <= T1; ++t) {
@@ -843,18 +850,24 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       cur = nxt;
     }
-    int t0 = T1 + 1, TB = P->trial_batch > 0 ? P->trial_batch : 8;
-    for (int r = 0; t0 <= P->max_trials && r < 14; ++r) {
-      if (r == 13 || t0 + TB - 1 > P->max_trials) TB = P->max_trials - t0 + 1;  // the last round reaches the cap
-      int t_end = t0 + TB - 1;
+    long long TB = P->trial_batch > 0 ? P->trial_batch : 64;
+    int t0 = T1 + 1;
+    // 64-bit queue counter of the parallel rounds (two int slots, 8-byte aligned)
+    int* q64 = q + 10;
+    for (int r = 0; t0 <= P->max_trials; ++r) {
+      TB = std::min<long long>(TB, (long long)P->max_trials - t0 + 1);  // the last round reaches the cap
+      int t_end = t0 + (int)TB - 1;
       int nxt = 1 - cur;
       cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
+      cudaMemsetAsync(ctx->d_npairs + K, 0, sizeof(int), s2);
+      cudaMemsetAsync(q64, 0, sizeof(unsigned long long), s2);
+      DPairs pr{ctx->d_pairs, ctx->d_npairs + K, plan.w.count ? plan.w.count + K : nullptr, c.B};
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
-        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q + 10 + r,
-                          lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, TB,
+        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q64,
+                          lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, (int)TB, pr,
                           grid_of(ctx, P, 6, K, block, c.B, true), block, s2);
         launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
-                           lists[nxt], counts[nxt] + K, dcb.stats, ctx->sms, s2);
+                           lists[nxt], counts[nxt] + K, pr, dcb.stats, ctx->sms, s2);
       });
       t0 = t_end + 1;
       TB *= 4;
@@ -1148,9 +1161,8 @@ mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guid
   if (e == cudaSuccess && !s) {  // Bernoulli rounds: synchronous rounds x first parallel batch
     std::vector<mpg_params> c;
     for (int t1 : {1, 2, 3})
-      for (int tb : {4, 8, 16, 32}) {
-        if (t1 == (best.trial_sync_rounds ? best.trial_sync_rounds : 2) && tb == (best.trial_batch ? best.trial_batch : 8))
-          continue;
+      for (int tb : {4, 16, 64, 256}) {
+        if (t1 == sync_rounds_of(&best) && tb == (best.trial_batch ? best.trial_batch : 64)) continue;
         mpg_params P = best;
         P.trial_sync_rounds = t1;
         P.trial_batch = tb;

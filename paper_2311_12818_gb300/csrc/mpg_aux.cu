@@ -32,11 +32,25 @@ __global__ void k_bucket_scan(const int* count, int* base, int* cursor) {
   }
 }
 
+// Lanes of a warp with the same length share one atomic (match + popc), so
+// the eight bucket cursors see one update per warp and length, not per chain.
 __global__ void k_bucket_scatter(const uint8_t* k, const uint8_t* status, int filter, int B, int* cursor, int* order) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-    if (filter >= 0 && status[b] != filter) continue;
-    int kk = k[b];
-    if (kk >= 1 && kk <= MAXK) order[atomicAdd(&cursor[kk], 1)] = b;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int stride = gridDim.x * blockDim.x;
+  for (int b0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); b0 < B; b0 += stride) {  // warp-uniform
+    int b = b0 + lane;
+    int kk = 0;
+    if (b < B && (filter < 0 || status[b] == filter)) {
+      kk = k[b];
+      if (kk < 1 || kk > MAXK) kk = 0;
+    }
+    unsigned same = __match_any_sync(FULL, kk);
+    int leader = __ffs(same) - 1;
+    int off = 0;
+    if (kk && lane == leader) off = atomicAdd(&cursor[kk], __popc(same));
+    off = __shfl_sync(FULL, off, leader);
+    if (kk) order[off + __popc(same & ((1u << lane) - 1u))] = b;
   }
 }
 
@@ -162,8 +176,20 @@ void launch_guide_records(const DChains& c, const float* contrib, float inv_area
 // End of a Bernoulli trial round
 // ---------------------------------------------------------------------------
 __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, const int* n_list, const int* base,
-                              unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
+                              unsigned* nbest, int t_end, int max_trials, int* next, int* n_next, DPairs pr,
                               unsigned long long* stats) {
+  // converged walks to other solutions below each chain's first success
+  const int cap = pairs_cap(pr);
+  const int np = *pr.n;
+  const uint2* P = pr.buf + (size_t)PAIRS_PER_CHAIN * *base;
+  uint32_t below = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < min(np, cap); j += gridDim.x * blockDim.x) {
+    uint2 p = P[j];
+    below += p.y < nbest[p.x];
+  }
+  below = __reduce_add_sync(0xffffffffu, below);
+  if (stats && (threadIdx.x & 31) == 0 && below) atomicAdd(stats + 10, (unsigned long long)below);
+  if (stats && blockIdx.x == 0 && threadIdx.x == 0 && np > cap) atomicAdd(stats + 15, (unsigned long long)(np - cap));
   const int n = *n_list;
   const int* L = list + *base;
   int* Nx = next + *base;
@@ -187,9 +213,9 @@ __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, co
 
 void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
                         const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
-                        unsigned long long* stats, int sms, cudaStream_t st) {
+                        DPairs pr, unsigned long long* stats, int sms, cudaStream_t st) {
   k_bern_finish<<<sms * 2, 256, 0, st>>>(S.L.area, c, o, list, n_list, base, nbest, t_end, max_trials, next, n_next,
-                                         stats);
+                                         pr, stats);
 }
 
 // ---------------------------------------------------------------------------

@@ -726,12 +726,15 @@ template <int K, bool kStats>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
                           Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
-                          bool want_pdf = true) {
+                          bool want_pdf = true, bool need_tau_in = false) {
   if (kStats) cnt.seeds++;
-  uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
   tau_out = tau;
+  // a Bernoulli trial must sample the chain's own types: when it drew others it
+  // has failed already, before any ray is cast
+  if (need_tau_in && tau != tau_in) return false;
+  uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
   uint64_t total = 0;
   bool use_guide = g != nullptr;
   const uint64_t* cdf = nullptr;

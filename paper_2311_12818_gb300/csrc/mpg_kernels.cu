@@ -69,8 +69,8 @@ void launch_contrib64(int K, const DScene& S, const DChains& c, const mpg_params
 }
 
 void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
-                       int* n_list, int grid, cudaStream_t st) {
-#define C_(KK) KLaunch<KK>::trial_init(S, c, w, o, list, base, n_list, grid, st)
+                       int* n_list, unsigned* nbest, int grid, cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::trial_init(S, c, w, o, list, base, n_list, nbest, grid, st)
   MPG_SWITCH(K, C_)
 #undef C_
 }
@@ -93,8 +93,9 @@ void launch_trial_check(int K, const DScene& S, const DChains& c, const DChains&
 
 void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key,
                        uint64_t offset, const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
-                       const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st) {
-#define C_(KK) KLaunch<KK>::bern_round(stats, S, g, c, key, offset, P, ctx, queue, list, n_list, base, nbest, t0, TB, grid, block, st)
+                       const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
+                       cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::bern_round(stats, S, g, c, key, offset, P, ctx, queue, list, n_list, base, nbest, t0, TB, pr, grid, block, st)
   MPG_SWITCH(K, C_)
 #undef C_
 }

@@ -49,6 +49,22 @@ struct DCtx {
   const unsigned long long* rng_add; // NULL, or a device counter added to rng offsets (captured graphs)
 };
 
+// Trial walks of a parallel Bernoulli round that converged to another
+// solution, as (chain, trial) pairs; the round's finish counts those below the
+// chain's first recurrence, which a sequential loop over the trials would have
+// walked.  Region of chain length K: PAIRS_PER_CHAIN entries per chain of the
+// bucket, buf[PAIRS_PER_CHAIN * *base ..), PAIRS_PER_CHAIN * bucket size long.
+constexpr int PAIRS_PER_CHAIN = 8;
+struct DPairs {
+  uint2* buf;
+  int* n;              // pairs recorded in this round (device counter of length K)
+  const int* cap_dev;  // bucket size, or NULL => cap_host
+  int cap_host;
+};
+__device__ __forceinline__ int pairs_cap(const DPairs& p) {
+  return PAIRS_PER_CHAIN * (p.cap_dev ? *p.cap_dev : p.cap_host);
+}
+
 // Random-number offset of a launch: the host value plus, inside a replayed
 // graph, the graph's device counter.
 __device__ __forceinline__ uint64_t rng_offset(uint64_t offset, const DCtx& ctx) {
@@ -91,7 +107,7 @@ struct KLaunch {
   static void walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                      int* queue, int grid, int block, cudaStream_t st);
   static void trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base, int* n_list,
-                         int grid, cudaStream_t st);
+                         unsigned* nbest, int grid, cudaStream_t st);
   static void contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st);
   static void trial_seed(const DScene& S, const DGuide* g, const DChains& c, const DChains& tc, const int* list,
                          const int* base, const int* n_list, uint2 key, uint64_t offset, const mpg_params& P,
@@ -101,7 +117,8 @@ struct KLaunch {
                           int* n_next, unsigned* nbest, int grid, cudaStream_t st);
   static void bern_round(bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
                          const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
-                         const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);
+                         const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
+                         cudaStream_t st);
   static int blocks_per_sm(int which, bool stats, int block);
 };
 
@@ -111,7 +128,7 @@ void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w
 void launch_contrib64(int K, const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid,
                       cudaStream_t st);
 void launch_trial_init(int K, const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
-                       int* n_list, int grid, cudaStream_t st);
+                       int* n_list, unsigned* nbest, int grid, cudaStream_t st);
 void launch_trial_seed(int K, const DScene& S, const DGuide* g, const DChains& c, const DChains& tc,
                        const int* list, const int* base, const int* n_list, uint2 key, uint64_t offset,
                        const mpg_params& P, DCtx ctx, int t, int grid, int block, cudaStream_t st);
@@ -120,11 +137,12 @@ void launch_trial_check(int K, const DScene& S, const DChains& c, const DChains&
                         int* n_next, unsigned* nbest, int grid, cudaStream_t st);
 void launch_bern_round(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key,
                        uint64_t offset, const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
-                       const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st);
+                       const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
+                       cudaStream_t st);
 // Ends a trial round: chains with a success get N, chains past the cap are
 // capped, the rest move to the next list.
 void launch_bern_finish(const DScene& S, const DChains& c, DOut o, const int* list, const int* n_list,
                         const int* base, unsigned* nbest, int t_end, int max_trials, int* next, int* n_next,
-                        unsigned long long* stats, int sms, cudaStream_t st);
+                        DPairs pr, unsigned long long* stats, int sms, cudaStream_t st);
 
 }  // namespace mpg

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
         float pdf;
         Ends et = e;
         if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c, false))
+                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c, false, true))
           continue;
         if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
         et.tau = tau;
@@ -273,8 +273,8 @@ void KLaunch<K>::contrib64(const DScene& S, const DChains& c, const mpg_params& 
 
 template <int K>
 void KLaunch<K>::trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base,
-                            int* n_list, int grid, cudaStream_t st) {
-  kern::k_trial_init<K><<<grid, 256, 0, st>>>(S, c, w, o, list, base, n_list);
+                            int* n_list, unsigned* nbest, int grid, cudaStream_t st) {
+  kern::k_trial_init<K><<<grid, 256, 0, st>>>(S, c, w, o, list, base, n_list, nbest);
 }
 
 template <int K>
@@ -296,10 +296,11 @@ void KLaunch<K>::trial_check(const DScene& S, const DChains& c, const DChains& t
 template <int K>
 void KLaunch<K>::bern_round(bool stats, const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
                             const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
-                            const int* base, unsigned* nbest, int t0, int TB, int grid, int block, cudaStream_t st) {
+                            const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
+                            cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
   kern::k_bern_round<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
-                                                         n_list, base, nbest, t0, TB);
+                                                         n_list, base, nbest, t0, TB, pr);
 }
 
 template <int K>

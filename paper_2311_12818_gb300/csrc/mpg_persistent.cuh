@@ -86,11 +86,26 @@ __device__ __forceinline__ int take_item(bool want, int* queue, int n, bool& don
   return i < n ? i : -1;
 }
 
+// The same over a 64-bit item space (parallel Bernoulli rounds: chains x trials).
+__device__ __forceinline__ long long take_item64(bool want, unsigned long long* queue, long long n, bool& done) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned need = __ballot_sync(FULL, want);
+  if (!need || done) return -1;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(queue, (unsigned long long)__popc(need));
+  base = __shfl_sync(FULL, base, 0);
+  if ((long long)base + __popc(need) >= n) done = true;
+  if (!want) return -1;
+  long long i = (long long)base + __popc(need & ((1u << lane) - 1u));
+  return i < n ? i : -1;
+}
+
 // ---------------------------------------------------------------------------
 // Walk (K2): one lane per chain, refilled from the bucket's queue.
 // ---------------------------------------------------------------------------
 template <int K, bool kS>
-__global__ void __launch_bounds__(128) k_walk_p(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+__global__ void __launch_bounds__(128, 5) k_walk_p(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
                                                 DCtx ctx, int* queue) {
   Tally t = {};
   const int n = n_items<K>(w, c);
@@ -152,18 +167,22 @@ __device__ __forceinline__ void bern_write(const DScene& S, const DChains& c, co
 // their final (zero) outputs.
 template <int K>
 __global__ void __launch_bounds__(256) k_trial_init(const __grid_constant__ DScene S, DChains c, DWork w, DOut o,
-                                                    int* list, const int* base, int* n_list) {
+                                                    int* list, const int* base, int* n_list, unsigned* nbest) {
   const int n = n_items<K>(w, c);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int b = item<K>(w, c, i);
     if (b < 0) continue;
-    if (o.T[b] > 0.0f) list[base[K] + atomicAdd(n_list + K, 1)] = b;
-    else bern_write(S, c, o, b, 0.0f, 0, false);
+    if (o.T[b] > 0.0f) {
+      list[base[K] + atomicAdd(n_list + K, 1)] = b;
+      nbest[b] = 0xffffffffu;  // no success yet
+    } else {
+      bern_write(S, c, o, b, 0.0f, 0, false);
+    }
   }
 }
 
 // Trial t of every listed chain: a fresh seed from the same distribution and
-// length (Sec. 5.7), written to the trial state; a seed with another type
+// length (Sec. 5.8, n reused), written to the trial state; a seed with another type
 // sequence cannot reach the same solution and is marked invalid.
 template <int K, bool kS>
 __global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DScene S, DGuide g, int has_guide,
@@ -182,7 +201,7 @@ __global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DSce
     tl.trials++;
     bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[b / c.spq] : 0u, e.tau,
                                P.tau_random != 0, key, (uint64_t)b + offset, (uint32_t)t, P, ch, tau, pdf, ctx.err,
-                               tl.c, false) &&
+                               tl.c, false, true) &&
               tau == e.tau;
     if (ok) store_chain<K>(tc, b, ch);
     tc.status[b] = ok ? ST_SEEDED : ST_INVALID;
@@ -220,24 +239,28 @@ __global__ void __launch_bounds__(256) k_trial_check(const __grid_constant__ DSc
 }
 
 // ---------------------------------------------------------------------------
-// Bernoulli trial rounds for the overflow chains: trials t0 .. t0+TB-1 of every
-// listed chain run in parallel as independent items; the first success is the
-// smallest successful index (atomicMin), exactly as a sequential loop would
-// find.  Items above a chain's best success so far are skipped.
+// Parallel Bernoulli rounds: trials t0 .. t0+TB-1 of every listed chain run as
+// independent items; the first success is the smallest successful index
+// (atomicMin), exactly as a sequential loop would find.  Items are issued
+// trial-major (trial t0 of every chain, then trial t0+1, ...), so by the time a
+// chain's later trials are taken its earlier ones have mostly finished, and
+// items above a chain's best success so far are skipped: the speculative work
+// is bounded by the items in flight, not by TB.
 // ---------------------------------------------------------------------------
 template <int K, bool kS>
-__global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
+__global__ void __launch_bounds__(128, 5) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                     DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
                                                     int* queue, const int* list, const int* n_list, const int* base,
-                                                    unsigned* nbest, int t0, int TB) {
+                                                    unsigned* nbest, int t0, int TB, DPairs pr) {
   Tally t = {};
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
   const int* over = list + *base;
-  const long long n = (long long)(*n_list) * TB;
+  const int nl = *n_list;
+  const long long n = (long long)nl * TB;
+  unsigned long long* queue64 = reinterpret_cast<unsigned long long*>(queue);
   offset = rng_offset(offset, ctx);
   const int refill = P.refill_every > 1 ? P.refill_every : 1;
   int pass = 0;
-  const int n_items_i = n > 0x7fffffff ? 0x7fffffff : (int)n;
   WalkLane<K> L;
   Chain<K> target;
   int b = -1, tr = 0;
@@ -246,11 +269,11 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
   while (true) {
     // idle lanes refill every `refill` passes, or at once when the whole warp is idle
     bool idle_warp = __all_sync(FULL, b < 0);
-    int i = take_item(b < 0 && (idle_warp || pass % refill == 0), queue, n_items_i, done);
+    long long i = take_item64(b < 0 && (idle_warp || pass % refill == 0), queue64, n, done);
     ++pass;
     if (i >= 0) {
-      int bb = over[i / TB];
-      int tt = t0 + i % TB;
+      int bb = over[i % nl];
+      int tt = t0 + (int)(i / nl);
       if (tt <= P.max_trials && (unsigned)tt < *((volatile unsigned*)(nbest + bb))) {
         t.trials++;
         Ends e = load_ends(c, bb);
@@ -258,7 +281,7 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
         float pdf;
         uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
         if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                             (uint64_t)bb + offset, (uint32_t)tt, P, L.ch, tau, pdf, ctx.err, t.c, false) &&
+                             (uint64_t)bb + offset, (uint32_t)tt, P, L.ch, tau, pdf, ctx.err, t.c, false, true) &&
             tau == e.tau) {
           b = bb;
           tr = tt;
@@ -275,9 +298,17 @@ __global__ void __launch_bounds__(128) k_bern_round(const __grid_constant__ DSce
     if (st != RUNNING) {
       t.walks++;
       // converged walks of the trial sequence (t <= N) are counted by the
-      // round's finish kernel, once per chain: parallel trials past the first
-      // success are not part of the estimator
-      if (st == ST_CONVERGED && same_solution<K>(L.ch, target, eps2)) atomicMin(nbest + b, (unsigned)tr);
+      // round's finish kernel: the success itself once per chain, and the
+      // walks to other solutions that lie below the first success (parallel
+      // trials past it are not part of the estimator)
+      if (st == ST_CONVERGED) {
+        if (same_solution<K>(L.ch, target, eps2)) {
+          atomicMin(nbest + b, (unsigned)tr);
+        } else {
+          int j = atomicAdd(pr.n, 1);
+          if (j < pairs_cap(pr)) pr.buf[PAIRS_PER_CHAIN * *base + j] = make_uint2((unsigned)b, (unsigned)tr);
+        }
+      }
       b = -1;
     }
   }

@@ -57,7 +57,7 @@ class mpg_guide(C.Structure):
 
 STAT_FIELDS = ["newton_steps", "thomas_rows", "full_evals", "c_evals", "ray_casts", "sphere_tests",
                "plane_tests", "node_tests", "tri_tests", "walks", "converged", "ggt_rows", "trials", "seeds",
-               "ggt_fp64"]
+               "ggt_fp64", "uncounted"]
 KERNEL_SEED, KERNEL_WALK, KERNEL_CONTRIB, KERNEL_BERNOULLI, KERNEL_TRACE, KERNEL_AUX = range(6)
 KERNEL_NAMES = ["seed", "walk", "contrib", "bernoulli", "trace", "aux"]
 

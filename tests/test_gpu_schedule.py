@@ -47,9 +47,13 @@ def _run(M, ctx, wl, P, off=0):
     sc = M.Scene(ctx, wl)
     ch = M.Chains(wl)
     res = M.Contribution.empty(wl.B, wl.Q)
+    ctx.reset_stats()
     _step(M, ctx, sc, ch, res, wl, P, off)
     ctx.sync()
-    return _snapshot(ch, res)
+    snap = _snapshot(ch, res)
+    st = ctx.stats()
+    snap["converged_walks"] = np.array([st["converged"], st["uncounted"]])
+    return snap
 
 
 def _mixed():
@@ -67,9 +71,15 @@ def test_schedules_give_identical_results(M, ctx):
     ref = _run(M, ctx, wl, base)
     assert (ref["status"] == 1).sum() > 1000
     assert ref["trials"].max() > 8  # the parallel Bernoulli rounds ran
+    assert ref["converged_walks"][1] == 0
+    # the count of converged walks is the sequential loop's, whatever the schedule:
+    # the plain mode runs each chain's trials one after another
+    plain = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_PLAIN, tau_random=True))
+    assert abs(int(plain["converged_walks"][0]) - int(ref["converged_walks"][0])) <= 1e-3 * ref["converged_walks"][0]
     for sched in ({"block_threads": 64, "ctas_per_sm": 2}, {"block_threads": 32, "refill_every": 4},
                   {"refill_every": 2, "trial_sync_rounds": 1, "trial_batch": 4},
-                  {"trial_sync_rounds": 3, "trial_batch": 32, "ctas_per_sm": 1}):
+                  {"trial_sync_rounds": 3, "trial_batch": 32, "ctas_per_sm": 1},
+                  {"trial_sync_rounds": -1, "trial_batch": 1}, {"trial_sync_rounds": -1, "trial_batch": 4096}):
         P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True, **sched)
         _bitwise_equal(ref, _run(M, ctx, wl, P))
 
@@ -150,10 +160,10 @@ def test_autotune_picks_a_valid_schedule(M, ctx):
     assert ctx.stats()["walks"] == 0 and ctx.launches() == n0  # tuning left the caller's counters alone
     assert tuned.block_threads in (0, 32, 64, 128)
     assert tuned.refill_every in (0, 1, 2, 4, 8)
-    assert tuned.trial_sync_rounds in (0, 1, 2, 3) and tuned.trial_batch in (0, 4, 8, 16, 32)
+    assert tuned.trial_sync_rounds in (0, 1, 2, 3) and tuned.trial_batch in (0, 4, 16, 64, 256)
     assert tuned.fp64_k in (0, 4, 5)
     for f in ("tol", "max_iter", "max_halvings", "max_trials", "dedup_eps", "walk_mode", "tau_random"):
         assert getattr(tuned, f) == getattr(base, f)
     ref = _run(M, ctx, wl, base)
     got = _run(M, ctx, wl, tuned)
-    _bitwise_equal(ref, got, ["status", "surf", "trials"] if tuned.fp64_k else None)
+    _bitwise_equal(ref, got, ["status", "surf", "trials", "converged_walks"] if tuned.fp64_k else None)

@@ -338,7 +338,7 @@ def test_brute_force_solution_sets_two_spheres():
 
 
 # --------------------------------------------------------------------------
-# Bernoulli trials and unbiasedness (Eq. ThroughputMC; Sec. 5.7)
+# Bernoulli trials and unbiasedness (Eq. ThroughputMC; Sec. 5.8)
 # --------------------------------------------------------------------------
 def test_bernoulli_mean_matches_basin_probability_and_estimator_is_unbiased():
     xD = np.array([[0.35, 0.9, -1.5]])
