@@ -39,7 +39,7 @@ WORKLOAD = "glass_sphere_k2_guided: r=1 IOR 1.5, 256x256 points x 16 seeds = 1,0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="receiver points per side")
@@ -75,7 +75,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -344,12 +344,13 @@ def timed_loop(fn, steps, warmup, flush, stream, torch):
 
 
 def kernel_digest():
-    """sha256 over the CUDA sources (file names and contents, sorted)."""
+    """sha256 over the CUDA sources (file names and contents, sorted) and the build script."""
     import glob
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2311_12818_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+    files = sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh")))
+    for f in files + [os.path.join(ROOT, "paper_2311_12818_gb300", "build.py")]:  # sources and flags
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

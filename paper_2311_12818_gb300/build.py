@@ -13,8 +13,10 @@ OUT = os.path.join(HERE, "libmpg.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["mpg_kernels.cu", "mpg_aux.cu", "mpg_api.cu", "mpg_adjoint.cu"] + ["mpg_k%d.cu" % k for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# FP32 division at <= 2 ulp (hardware reciprocal) instead of the IEEE-rounded
+# sequence; square roots stay IEEE; FP64 and denormals are untouched.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I" + INCLUDE, "-I" + CSRC]
+         "--prec-div=false", "--prec-sqrt=true", "-I" + INCLUDE, "-I" + CSRC]
 
 
 def _nvcc():

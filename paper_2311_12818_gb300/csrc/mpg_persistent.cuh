@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(128, 5) k_bern_round(const __grid_constant__ D
       if (st == ST_CONVERGED) {
         if (same_solution<K>(L.ch, target, eps2)) {
           atomicMin(nbest + b, (unsigned)tr);
-        } else {
+        } else if ((unsigned)tr < *((volatile unsigned*)(nbest + b))) {  // not past a known success
           int j = atomicAdd(pr.n, 1);
           if (j < pairs_cap(pr)) pr.buf[PAIRS_PER_CHAIN * *base + j] = make_uint2((unsigned)b, (unsigned)tr);
         }
