@@ -193,6 +193,7 @@ def run_ours(args, rank, world, local):
     barrier()
     torch.cuda.synchronize()
     clocks.start()
+    time.sleep(0.5)  # let the sampler come up before the timed region
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     for i in range(args.steps):
         if not args.no_flush:
@@ -366,7 +367,7 @@ def profiled_traffic(summary):
             text = f.read()
     except OSError:
         return None
-    dg = re.search(r"Kernel source digest: ([0-9a-f]{64})", text)
+    dg = re.search(r"Kernel source digest[^:]*: ([0-9a-f]{64})", text)
     tb = re.search(r"dram_bytes_per_launch: (\d+)", text)
     if not dg or not tb or dg.group(1) != kernel_digest():
         return None
