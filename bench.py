@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the K3/K6, mixed-batch and adjoint measurements")
     ap.add_argument("--no-graph", action="store_true", help="batched mode without graph capture")
-    ap.add_argument("--part", choices=["k3", "k6", "mixed", "adjoint"], help="run one secondary measurement only")
+    ap.add_argument("--part", choices=list(PARTS), help="run one secondary measurement only")
     return ap.parse_args()
 
 
@@ -382,7 +382,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("k3", "k6", "mixed", "adjoint")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -401,6 +401,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     F = unit_flops()
     out = {}
     ctx = mpg.Context(dev.index or 0)
+    if "plain" in parts:
+        out["glass_plain"] = part_plain(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "k3" in parts:
         out["k3_bvh_trace"] = part_k3(ctx, dev, flush, torch, stream, steps, F, hbm, hbm_src)
     if "k6" in parts:
@@ -409,6 +411,37 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["mixed_batch"] = part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "adjoint" in parts:
         out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
+    return out
+
+
+def part_plain(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
+    """The benchmark step (seeds -> walk -> contribution with Bernoulli trials)
+    on the same glass-sphere inputs in plain mode: one launch per chain length,
+    one thread per chain, each chain's trials as a sequential loop; no graph."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.glass_sphere()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    out = {"workload": "glass_sphere_k2 (p_0 seeds), 1,048,576 chains: seeds -> walk -> contribution + trials"}
+    for name, mode in (("plain", mpg.WALK_PLAIN), ("batched", mpg.WALK_BATCHED)):
+        P = mpg.params_from(wl.params, walk_mode=mode, k_uniform=2)
+
+        def step(i, P=P):
+            mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B)
+            mpg.mpg_manifold_walk(ctx, sc, ch, P)
+            mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B, out=res)
+        step(0)
+        ctx.sync()
+        ctx.reset_stats()
+        ms = timed_loop(step, steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        per = steps + 2
+        fl = algorithmic_flops(st, F) / per
+        out[name] = {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+                     "fp32_tflops": fl / (ms * 1e-3) / 1e12, "fp32_frac": fl / (ms * 1e-3) / peak_fp32}
+    out["batched_over_plain"] = out["batched"]["converged_walks_per_s"] / out["plain"]["converged_walks_per_s"]
     return out
 
 

@@ -38,10 +38,13 @@ __device__ __forceinline__ void walk_begin(WalkLane<K>& w) {
 
 // One pass of the walk: Jacobian and Newton direction when the previous
 // attempt was accepted (or at the start), then one reprojection attempt.
-// Same decisions, in the same order, as walk<K>().
+// Same decisions, in the same order, as walk<K>().  In a pass without the
+// evaluation phase (eval_phase false) a lane that needs the Jacobian waits.
 template <int K, bool kS>
-__device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const mpg_params& P, Counters& cnt) {
+__device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const mpg_params& P, Counters& cnt,
+                                         bool eval_phase) {
   if (w.need_eval) {
+    if (!eval_phase) return RUNNING;
     VB vb[K];
     if (!eval_full<K, kS>(S, w.ch, w.e, vb, w.tu, w.tv, w.cn2, w.cmax, false, cnt)) return ST_FAILED;
     if (w.cmax < P.tol) return ST_CONVERGED;
@@ -67,6 +70,19 @@ __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const 
   w.beta *= 0.5f;
   if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   return RUNNING;
+}
+
+// Phase vote of a warp: the Jacobian evaluation (about four times the work of
+// a line-search attempt) runs when at least as many active lanes need it as
+// are between halvings; otherwise the pass runs the line-search attempts only
+// and the lanes that need the Jacobian wait for the next evaluation pass.
+// Without it, a lane whose last step was rejected idles through the other
+// lanes' evaluation in every pass.
+__device__ __forceinline__ bool eval_vote(bool active, bool need_eval) {
+  const unsigned FULL = 0xffffffffu;
+  unsigned e = __ballot_sync(FULL, active && need_eval);
+  unsigned l = __ballot_sync(FULL, active && !need_eval);
+  return __popc(e) >= __popc(l);
 }
 
 // Warp-aggregated take of one queue item per lane that asks for one.  Returns
@@ -110,6 +126,7 @@ __global__ void __launch_bounds__(128, 5) k_walk_p(const __grid_constant__ DScen
   Tally t = {};
   const int n = n_items<K>(w, c);
   WalkLane<K> L;
+  L.need_eval = false;
   int b = -1;
   bool done = false;
   const unsigned FULL = 0xffffffffu;
@@ -131,8 +148,9 @@ __global__ void __launch_bounds__(128, 5) k_walk_p(const __grid_constant__ DScen
     }
     bool any = __any_sync(FULL, b >= 0);
     if (!any && done) break;
+    const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b >= 0) {
-      int st = walk_pass<K, kS>(S, L, P, t.c);
+      int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase);
       if (st != RUNNING) {
         t.walks++;
         t.conv += st == ST_CONVERGED;
@@ -262,6 +280,7 @@ __global__ void __launch_bounds__(128, 5) k_bern_round(const __grid_constant__ D
   const int refill = P.refill_every > 1 ? P.refill_every : 1;
   int pass = 0;
   WalkLane<K> L;
+  L.need_eval = false;
   Chain<K> target;
   int b = -1, tr = 0;
   bool done = false;
@@ -293,8 +312,9 @@ __global__ void __launch_bounds__(128, 5) k_bern_round(const __grid_constant__ D
     }
     bool any = __any_sync(FULL, b >= 0);
     if (!any && done) break;
+    const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b < 0) continue;
-    int st = walk_pass<K, kS>(S, L, P, t.c);
+    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase);
     if (st != RUNNING) {
       t.walks++;
       // converged walks of the trial sequence (t <= N) are counted by the
