@@ -84,15 +84,16 @@ void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, 
 // ---------------------------------------------------------------------------
 __global__ void k_guide_update(DGuide g, const uint32_t* cell, const float* omega, const float* w, int R,
                                const int* R_dev, int shift, int* err) {
-  double scale = ldexp(1.0, shift);
   const int n = R_dev ? min(*R_dev, R) : R;
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
     uint32_t c = cell[r];
     if ((int)c >= g.n_cells) { atomicOr(err, 2); continue; }
     float wr = w[r];
     if (!(wr > 0.0f)) continue;
-    double qd = floor((double)wr * scale);
-    unsigned long long q = qd >= 4294967295.0 ? 4294967295ull : (unsigned long long)qd;
+    // w 2^S is exact in FP32 (a power-of-two scaling; +inf past the range) and
+    // so is its floor: q = min(floor(w 2^S), 2^32 - 1) with no rounding
+    float qf = floorf(ldexpf(wr, shift));
+    unsigned long long q = qf >= 4294967295.0f ? 4294967295ull : (unsigned long long)qf;
     if (q == 0) continue;
     float3 om = make_float3(omega[r], omega[R + r], omega[2 * (size_t)R + r]);
     int bin = guide_bin(g, om);

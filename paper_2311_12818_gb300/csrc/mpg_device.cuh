@@ -669,6 +669,27 @@ __device__ __forceinline__ bool scatter(const DSurf& sf, float3 n, float3 d, boo
 // (c_j, s_j) that w is counter-clockwise of, by the exact FP64 sign of
 // c_j y - s_j x (a product of two FP32 values is exact in FP64).  Both
 // predicates are monotone in j, so each count is a binary search.
+// Exact sign test c y - s x >= 0 for FP32 inputs.  The FP32 products p1, p2
+// are within max(|p1|,|p2|) 2^-24 + 2^-150 of the exact ones and the rounded
+// difference d within |d| 2^-24 of p1 - p2, so when |d| exceeds
+// max(|p1|,|p2|) 2^-21 + 2^-126 its sign is the sign of the exact value.
+// Otherwise (near ties, rare) the products are formed in FP64, where a product
+// of two FP32 values is exact and the one rounding of the difference keeps its
+// sign.  Either way the result is the exact predicate, the same on every
+// machine.
+// The FP64 form is a separate, non-inlined call so that the compiler cannot
+// turn the rare branch into straight-line code executed for every test.
+static __device__ __noinline__ bool ccw_or_on_fp64(float c, float s, float x, float y) {
+  return __dsub_rn(__dmul_rn((double)c, (double)y), __dmul_rn((double)s, (double)x)) >= 0.0;
+}
+__device__ __forceinline__ bool ccw_or_on(float c, float s, float x, float y) {
+  float p1 = __fmul_rn(c, y), p2 = __fmul_rn(s, x);
+  float d = __fsub_rn(p1, p2);
+  float m = fmaxf(fabsf(p1), fabsf(p2));
+  if (fabsf(d) > __fmaf_rn(m, 0x1p-21f, 0x1p-126f)) return d >= 0.0f;
+  return ccw_or_on_fp64(c, s, x, y);
+}
+
 __device__ __forceinline__ int guide_bin(const DGuide& g, float3 w) {
   int lo = 1, hi = g.n_theta;  // count of j in [1, n_theta) with w.z < cos_theta[j]
   while (lo < hi) {
@@ -679,12 +700,10 @@ __device__ __forceinline__ int guide_bin(const DGuide& g, float3 w) {
   bool upper = (w.y > 0.0f) || (w.y == 0.0f && w.x >= 0.0f);
   int half = g.n_phi >> 1;
   int j0 = upper ? 1 : half + 1, j1 = upper ? half : g.n_phi;
-  double x = (double)w.x, y = (double)w.y;
   int a = j0, b = j1;  // first j in [j0, j1) where w is no longer counter-clockwise of edge j
   while (a < b) {
     int mid = (a + b) >> 1;
-    double cr = __dsub_rn(__dmul_rn((double)__ldg(g.phi_cos + mid), y), __dmul_rn((double)__ldg(g.phi_sin + mid), x));
-    if (cr >= 0.0) a = mid + 1; else b = mid;
+    if (ccw_or_on(__ldg(g.phi_cos + mid), __ldg(g.phi_sin + mid), w.x, w.y)) a = mid + 1; else b = mid;
   }
   int ip = (upper ? 0 : half) + (a - j0);
   return it * g.n_phi + ip;
@@ -799,7 +818,7 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     uint64_t cnt_b = __ldg(reinterpret_cast<const unsigned long long*>(g->counts + (size_t)cell * g->bins + bin));
     int it = bin / g->n_phi;
     float dcos = __ldg(g->cos_theta + it) - __ldg(g->cos_theta + it + 1);
-    float ph = (float)((double)cnt_b / (double)total) / ((6.28318530717958647f / (float)g->n_phi) * dcos);
+    float ph = ((float)cnt_b / (float)total) / ((6.28318530717958647f / (float)g->n_phi) * dcos);
     pdf = P.alpha * p0 + (1.0f - P.alpha) * ph;
   } else {
     pdf = p0_pdf(S, e.xD, w);
