@@ -1,0 +1,194 @@
+"""Parity at the benchmark's full sizes, in the launch configuration it times.
+
+The glass-sphere step (1,048,576 chains, guided, batched, replayed from a
+captured graph) and the mixed-length batch (4,194,304 chains, batched graph)
+run whole on the GPU; the oracle then recomputes blocks of chains aligned to
+the receiver points -- at the start, in the middle and at the end of the batch.
+A block [b0, b0 + n) is a workload of its own whose random-number counters are
+those of the full run shifted by b0 (rng_offset + b0), so the oracle redraws
+the same seeds and trials and the comparison is chain by chain.  Full-size
+properties that need no oracle run are checked over the whole batch."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as O  # noqa: E402
+from paper_2311_12818_gb300 import inputs as I  # noqa: E402
+
+BLOCK = 1024
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_12818_gb300 import build, mpg
+    build.build()
+    return mpg
+
+
+@pytest.fixture(scope="module")
+def ctx(M):
+    return M.Context(0)
+
+
+def _block(wl, b0, n):
+    q0, nq = b0 // wl.spq, n // wl.spq
+    return dataclasses.replace(wl, xD=wl.xD[q0:q0 + nq], nD=wl.nD[q0:q0 + nq], cell=wl.cell[q0:q0 + nq],
+                               xL=wl.xL[b0:b0 + n], k=wl.k[b0:b0 + n], tau=wl.tau[b0:b0 + n],
+                               pn=wl.pn[b0:b0 + n], receiver_shape=(nq, 1))
+
+
+def _starts(wl):
+    B, s = wl.B, wl.spq
+    mid = (B // 2) // s * s
+    third = (B // 3) // s * s
+    return [0, third, mid, B - BLOCK]
+
+
+def _oracle_block(sub, guide, off):
+    """Oracle pipeline on one block: seeds, walk, contribution (of chains
+    polished to 1e-12, as in the reduced-size tests) and Bernoulli trials."""
+    sc = O.Scene(sub)
+    seeds = O.sample_seeds(sub, sc, guide, rng_offset=off)
+    ch = O.walk(sub, sc, seeds)
+    con = O.contribution(sub, sc, ch)
+    N, _ = O.bernoulli(sub, sc, ch, con["admissible"], guide, rng_offset=off)
+    tight = dataclasses.replace(sub, params=dataclasses.replace(sub.params, tol=1e-12))
+    conv = dict(x=ch["x"], surf=ch["surf"], prim=ch["prim"], bary=ch["bary"], tau=ch["tau"],
+                valid=(ch["status"] == 1).astype(np.uint8))
+    pol = O.walk(tight, sc, conv)
+    pol["status"] = np.where(pol["status"] == 1, ch["status"], 0).astype(np.uint8)
+    cp = O.contribution(sub, sc, pol)
+    adm = con["admissible"] & (cp["admissible"] | (ch["status"] != 1))
+    return seeds, ch, cp["T"], adm.astype(bool), N
+
+
+def _compare_blocks(M, wl, ch, res, guide_o, off):
+    st = ch.status.cpu().numpy()
+    x = ch.x.permute(2, 0, 1).double().cpu().numpy()
+    surf = ch.surf.T.contiguous().cpu().numpy()
+    T = res.T.cpu().numpy()
+    N = res.trials.cpu().numpy().astype(np.int64)
+    E = res.E.cpu().numpy()
+    flags, same_T, same_N, rel_T, rel_E, dx = [], [], [], [], [], []
+    for b0 in _starts(wl):
+        sl = slice(b0, b0 + BLOCK)
+        sub = _block(wl, b0, BLOCK)
+        seeds, och, oT, oadm, oN = _oracle_block(sub, guide_o, off + b0)
+        g1, o1 = st[sl] == 1, och["status"] == 1
+        flags.append(g1 == o1)
+        both = g1 & o1
+        for i in range(int(sub.k.max())):
+            sel = both & (sub.k > i) & np.all(surf[sl][:, :i + 1] == och["surf"][:, :i + 1], axis=1)
+            if sel.any():
+                dx.append(np.linalg.norm(x[sl][sel, i] - och["x"][sel, i], axis=1).max())
+        gadm = T[sl] > 0
+        same_T.append(gadm == oadm)
+        ab = gadm & oadm
+        rel_T.append(np.abs(T[sl][ab] - oT[ab]) / oT[ab])
+        same_N.append(N[sl][ab] == oN[ab])
+        # irradiance of the points whose every chain agrees in admissibility and N
+        ok = ((gadm == oadm) & ((N[sl] == oN) | ~oadm)).reshape(-1, wl.spq).all(axis=1)
+        oE = O.irradiance(sub, oT, oN, oadm)
+        q0 = b0 // wl.spq
+        nz = ok & (oE > 0)
+        rel_E.append(np.abs(E[q0:q0 + BLOCK // wl.spq][nz] - oE[nz]) / oE[nz])
+    flags, same_T, same_N = np.concatenate(flags), np.concatenate(same_T), np.concatenate(same_N)
+    rel_T, rel_E = np.concatenate(rel_T), np.concatenate(rel_E)
+    assert flags.mean() >= 0.999, flags.mean()
+    assert max(dx) < 1e-4 * wl.scene_scale, max(dx)
+    assert same_T.mean() >= 0.999, same_T.mean()
+    assert rel_T.size > 200 and np.quantile(rel_T, 0.999) < 1e-3
+    assert same_N.mean() >= 0.999, same_N.mean()
+    assert rel_E.size > 50 and rel_E.max() < 1e-3
+    # whole batch: E is the per-point mean of the contributions
+    c = res.contrib.cpu().numpy().astype(np.float64).reshape(wl.Q, wl.spq)
+    assert np.allclose(E, c.sum(axis=1) / wl.spq, rtol=1e-5, atol=0)
+    adm = T > 0
+    assert np.all(N[adm] >= 1) and np.all(N[~adm] == 0)
+
+
+def test_glass_sphere_full_size_captured_step(M, ctx):
+    wl = I.glass_sphere()
+    B = wl.B
+    sc = M.Scene(ctx, wl)
+    ch = M.Chains(wl)
+    P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, k_uniform=2)
+    res = M.Contribution.empty(B, wl.Q)
+    mk_rec = lambda: (torch.zeros(B, dtype=torch.int32, device="cuda"),  # noqa: E731
+                      torch.zeros((3, B), dtype=torch.float32, device="cuda"),
+                      torch.zeros(B, dtype=torch.float32, device="cuda"), torch.zeros(4, dtype=torch.int32, device="cuda"))
+    rec0, rec = mk_rec(), mk_rec()
+    guide = M.Guide(wl.n_cells, I.guide_edges())
+    nxt = M.Guide(wl.n_cells, I.guide_edges())
+    # training pass with p_0 (as the benchmark's fixture)
+    M.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40)
+    M.mpg_manifold_walk(ctx, sc, ch, P)
+    M.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40, out=res)
+    M.mpg_guide_records(ctx, sc, ch, res.contrib, out=rec0)
+    M.mpg_guide_update(ctx, guide, rec0[0], rec0[1], rec0[2], R=B, R_dev=rec0[3], weight_shift=wl.params.weight_shift)
+    ctx.sync()
+    counts = guide.counts.cpu().numpy().view(np.uint64)
+    R0 = int(rec0[3][0].item())
+    g_o = O.Guide(wl.n_cells, I.guide_edges())
+    g_o.update(rec0[0][:R0].cpu().numpy().astype(np.uint32), rec0[1][:, :R0].T.contiguous().cpu().numpy(),
+               rec0[2][:R0].cpu().numpy(), wl.params.weight_shift)
+    assert np.array_equal(counts, g_o.counts)  # the whole training pass, bit-exact
+
+    def step(off):
+        M.mpg_sample_seeds(ctx, sc, guide, ch, P, wl.rng_seed, off)
+        M.mpg_manifold_walk(ctx, sc, ch, P)
+        M.mpg_chain_contribution(ctx, sc, guide, ch, P, wl.rng_seed, off, out=res)
+        M.mpg_guide_records(ctx, sc, ch, res.contrib, out=rec)
+        M.mpg_guide_clear(ctx, nxt)
+        M.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
+
+    off = 3 * B
+    step(off)  # uncaptured first: sizes the buffers
+    ctx.sync()
+    g = M.Graph(ctx, rng_advance=B)
+    with g:
+        step(off)
+    g.launch()  # replay 0 draws at `off`
+    ctx.sync()
+    _compare_blocks(M, wl, ch, res, g_o, off)
+    # the step's own histogram update over every record, bit-exact
+    R = int(rec[3][0].item())
+    assert R == int((res.contrib > 0).sum().item())
+    g2 = O.Guide(wl.n_cells, I.guide_edges())
+    g2.update(rec[0][:R].cpu().numpy().astype(np.uint32), rec[1][:, :R].T.contiguous().cpu().numpy(),
+              rec[2][:R].cpu().numpy(), wl.params.weight_shift)
+    assert np.array_equal(nxt.counts.cpu().numpy().view(np.uint64), g2.counts)
+
+
+def test_mixed_batch_full_size_captured_step(M, ctx):
+    wl = I.mixed()
+    sc = M.Scene(ctx, wl)
+    ch = M.Chains(wl)
+    P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True)
+    res = M.Contribution.empty(wl.B, wl.Q)
+
+    def step(off):
+        M.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, off)
+        M.mpg_manifold_walk(ctx, sc, ch, P)
+        M.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, off, out=res)
+
+    off = 7 * wl.B
+    step(off)
+    ctx.sync()
+    g = M.Graph(ctx, rng_advance=wl.B)
+    with g:
+        step(off)
+    g.launch()
+    ctx.sync()
+    _compare_blocks(M, wl, ch, res, None, off)
+    # every chain length is present and walked
+    k = wl.k
+    st = ch.status.cpu().numpy()
+    for kk in range(1, 9):
+        assert ((k == kk) & (st == 1)).sum() > 0
