@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the K3/K6, mixed-batch and adjoint measurements")
     ap.add_argument("--no-graph", action="store_true", help="batched mode without graph capture")
+    ap.add_argument("--no-pipeline", action="store_true", help="one batch per graph replay (no double buffering)")
     ap.add_argument("--part", choices=list(PARTS), help="run one secondary measurement only")
     return ap.parse_args()
 
@@ -136,16 +137,25 @@ def run_ours(args, rank, world, local):
     wl = I.glass_sphere(n=args.n, spq=args.spq)
     B, Q = wl.B, wl.Q
     off = rank * B  # each rank draws its own seeds (weak scaling)
-    ctx = mpg.Context(local)
-    sc = mpg.Scene(ctx, wl)
-    ch = mpg.Chains(wl, device=dev)
     mode = mpg.WALK_BATCHED if args.mode == "batched" else mpg.WALK_PLAIN
     P = mpg.params_from(wl.params, walk_mode=mode, k_uniform=2)
+    graph_mode = args.mode == "batched" and not args.no_graph
+    # Batched mode replays a graph that advances two batches at once on two
+    # contexts and two streams (double buffering): consecutive steps are
+    # independent (each samples the trained guide and builds its own), so the
+    # latency-bound ends of one batch's kernels overlap the other batch's work.
+    n_buf = 2 if graph_mode and not args.no_pipeline else 1
+    ctxs = [mpg.Context(local) for _ in range(n_buf)]
+
+    def buffers(c):
+        return dict(sc=mpg.Scene(c, wl), ch=mpg.Chains(wl, device=dev), out=mpg.Contribution.empty(B, Q, device=dev),
+                    rec=(torch.zeros(B, dtype=torch.int32, device=dev),
+                         torch.zeros((3, B), dtype=torch.float32, device=dev),
+                         torch.zeros(B, dtype=torch.float32, device=dev), torch.zeros(4, dtype=torch.int32, device=dev)),
+                    nxt=mpg.Guide(wl.n_cells, I.guide_edges(), device=dev))
+    bufs = [buffers(c) for c in ctxs]
+    ctx, sc, ch, out, rec = ctxs[0], bufs[0]["sc"], bufs[0]["ch"], bufs[0]["out"], bufs[0]["rec"]
     guide = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
-    nxt = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
-    out = mpg.Contribution.empty(B, Q, device=dev)
-    rec = (torch.zeros(B, dtype=torch.int32, device=dev), torch.zeros((3, B), dtype=torch.float32, device=dev),
-           torch.zeros(B, dtype=torch.float32, device=dev), torch.zeros(4, dtype=torch.int32, device=dev))
 
     # untimed fixture: one p_0 training pass builds the guide
     mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, off + (1 << 40))
@@ -155,31 +165,57 @@ def run_ours(args, rank, world, local):
     mpg.mpg_guide_update(ctx, guide, rec[0], rec[1], rec[2], R=B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
     ctx.sync()
 
-    def step(i):
+    def step_on(j, i, stream=None):
+        c, bf = ctxs[j], bufs[j]
         o = off + i * B * world
-        mpg.mpg_sample_seeds(ctx, sc, guide, ch, P, wl.rng_seed, o)
-        mpg.mpg_manifold_walk(ctx, sc, ch, P)
-        mpg.mpg_chain_contribution(ctx, sc, guide, ch, P, wl.rng_seed, o, out=out)
-        mpg.mpg_guide_records(ctx, sc, ch, out.contrib, out=rec)
-        mpg.mpg_guide_clear(ctx, nxt)
-        mpg.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=B, R_dev=rec[3],
-                             weight_shift=wl.params.weight_shift)
+        mpg.mpg_sample_seeds(c, bf["sc"], guide, bf["ch"], P, wl.rng_seed, o, stream=stream)
+        mpg.mpg_manifold_walk(c, bf["sc"], bf["ch"], P, stream=stream)
+        mpg.mpg_chain_contribution(c, bf["sc"], guide, bf["ch"], P, wl.rng_seed, o, out=bf["out"], stream=stream)
+        mpg.mpg_guide_records(c, bf["sc"], bf["ch"], bf["out"].contrib, out=bf["rec"], stream=stream)
+        mpg.mpg_guide_clear(c, bf["nxt"], stream=stream)
+        r = bf["rec"]
+        mpg.mpg_guide_update(c, bf["nxt"], r[0], r[1], r[2], R=B, R_dev=r[3], weight_shift=wl.params.weight_shift,
+                             stream=stream)
+
+    def step(i):
+        step_on(0, i)
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > L2
     stream = torch.cuda.current_stream()
-    for i in range(args.warmup):  # uncaptured: sizes the context's buffers
-        step(1000 + i)
-    ctx.sync()
+    for j in range(n_buf):
+        for i in range(args.warmup):  # uncaptured: sizes each context's buffers
+            step_on(j, 1000 + 16 * i + j)
+    torch.cuda.synchronize()
     graph = None
-    if args.mode == "batched" and not args.no_graph:
-        # the whole step as one graph; replay r draws at the offsets of step 2000 + r
-        graph = mpg.Graph(ctx, rng_advance=B * world)
+    per_launch = 1
+    if graph_mode:
+        # replay r draws at the offsets of steps 2000 + n_buf r + j
+        graph = mpg.Graph(ctx, rng_advance=n_buf * B * world, join=ctxs[1:])
+        side = [torch.cuda.Stream(device=dev) for _ in range(n_buf)]
         with graph:
-            step(2000)
+            for j in range(n_buf):
+                side[j].wait_stream(graph.stream)
+                step_on(j, 2000 + j, stream=side[j])
+            for j in range(n_buf):
+                graph.stream.wait_stream(side[j])
         for i in range(args.warmup):
             graph.launch()
-        ctx.sync()
+        torch.cuda.synchronize()
+        per_launch = n_buf
+    n_launch = -(-args.steps // per_launch)  # steps rounded up to whole replays
+    steps_run = n_launch * per_launch
     run = (lambda i: graph.launch()) if graph is not None else step
+
+    def all_stats():
+        tot = None
+        for c in ctxs:
+            st = c.stats()
+            tot = st if tot is None else {k: tot[k] + st[k] for k in tot}
+        return tot
+
+    def reset_all():
+        for c in ctxs:
+            c.reset_stats()
 
     def barrier():
         if world > 1:
@@ -187,15 +223,15 @@ def run_ours(args, rank, world, local):
             dist.barrier()
 
     # ---- device-timed steps (inputs resident in HBM)
-    ctx.reset_stats()
+    reset_all()
     n_launch0 = ctx.launches()
     clocks = Clocks(local)
     barrier()
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.5)  # let the sampler come up before the timed region
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_launch)]
+    for i in range(n_launch):
         if not args.no_flush:
             flush.zero_()
         ev[i][0].record(stream)
@@ -204,10 +240,11 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ctx.sync()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    for c in ctxs:
+        c.sync()
+    step_ms = [a.elapsed_time(b) / per_launch for a, b in ev for _ in range(per_launch)]
     launches = ctx.launches() - n_launch0
-    total = ctx.stats()
+    total = all_stats()
     conv = total["converged"]
     t_ms = sum(step_ms)
     from paper_2311_12818_gb300 import dist as D
@@ -239,33 +276,37 @@ def run_ours(args, rank, world, local):
 
     # ---- end to end through the public API with host buffers
     pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
-    host_in = [(ch.xD, pin(np.ascontiguousarray(wl.xD.T, np.float32))),
-               (ch.nD, pin(np.ascontiguousarray(wl.nD.T, np.float32))),
-               (ch.cell, pin(wl.cell.astype(np.int32))), (ch.xL, pin(np.ascontiguousarray(wl.xL.T, np.float32))),
-               (ch.k, pin(wl.k.astype(np.uint8))), (ch.tau, pin(wl.tau.astype(np.uint8))),
-               (ch.pn, pin(wl.pn.astype(np.float32)))]
-    h2d = sum(h.numel() * h.element_size() for _, h in host_in)
-    E_host = torch.empty(Q, dtype=torch.float32).pin_memory()
-    n_host = torch.empty(4, dtype=torch.int32).pin_memory()
-    d2h = E_host.numel() * 4 + n_host.numel() * 4
+    host_in = []
+    for bf in bufs:
+        c_ = bf["ch"]
+        host_in += [(c_.xD, pin(np.ascontiguousarray(wl.xD.T, np.float32))),
+                    (c_.nD, pin(np.ascontiguousarray(wl.nD.T, np.float32))),
+                    (c_.cell, pin(wl.cell.astype(np.int32))), (c_.xL, pin(np.ascontiguousarray(wl.xL.T, np.float32))),
+                    (c_.k, pin(wl.k.astype(np.uint8))), (c_.tau, pin(wl.tau.astype(np.uint8))),
+                    (c_.pn, pin(wl.pn.astype(np.float32)))]
+    h2d = sum(h.numel() * h.element_size() for _, h in host_in) // per_launch
+    E_host = [torch.empty(Q, dtype=torch.float32).pin_memory() for _ in bufs]
+    n_host = [torch.empty(4, dtype=torch.int32).pin_memory() for _ in bufs]
+    d2h = (E_host[0].numel() * 4 + n_host[0].numel() * 4) * len(bufs) // per_launch
     e2e_conv = 0
     e2e_ms = 0.0
-    for i in range(max(1, args.steps // 2)):
+    for i in range(max(1, n_launch // 2)):
         if not args.no_flush:
             flush.zero_()
-        ctx.reset_stats()
+        reset_all()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for d, h in host_in:
             d.copy_(h, non_blocking=True)
         run(500 + i)
-        E_host.copy_(out.E, non_blocking=True)
-        n_host.copy_(rec[3], non_blocking=True)
+        for j, bf in enumerate(bufs[:per_launch]):
+            E_host[j].copy_(bf["out"].E, non_blocking=True)
+            n_host[j].copy_(bf["rec"][3], non_blocking=True)
         b.record(stream)
         b.synchronize()
         e2e_ms += a.elapsed_time(b)
-        e2e_conv += ctx.stats()["converged"]
+        e2e_conv += all_stats()["converged"]
     e2e_value = e2e_conv / (e2e_ms * 1e-3) if world == 1 else None
 
     # ---- roofline of the dominant kernel family (FP32 ALU bound)
@@ -291,11 +332,12 @@ def run_ours(args, rank, world, local):
                 "timing": "per-launch CUDA events in an uncaptured pass of the same steps"}
     step_flops = sum(f["flops"] for f in fam.values())
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps_run,
+        "warmup": args.warmup, "ms_per_step": t_ms / steps_run, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded procedural scene, no dataset)",
         "config": {"workload": WORKLOAD, "chains_per_step": B, "receiver_points": Q, "seeds_per_point": wl.spq,
                    "k": 2, "walk_mode": args.mode, "graph": graph is not None,
+                   "batches_in_flight": per_launch,
                    "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
                    "parallelism": "replicas x%d" % world,
                    "counted_walks": "walks that converged: the first walks and the trial walks of each chain's"
@@ -304,9 +346,9 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "clocks": clk,
-        "detail": {"converged_per_step": conv / args.steps, "walks_per_step": total["walks"] / args.steps,
-                   "trials_per_step": total["trials"] / args.steps,
-                   "fp64_geometry_terms_per_step": total["ggt_fp64"] / args.steps,
+        "detail": {"converged_per_step": conv / steps_run, "walks_per_step": total["walks"] / steps_run,
+                   "trials_per_step": total["trials"] / steps_run,
+                   "fp64_geometry_terms_per_step": total["ggt_fp64"] / steps_run,
                    "step_ms": [round(x, 4) for x in step_ms],
                    "graph_kernels_per_step": graph.kernels() if graph is not None else None,
                    "uncaptured_profiled_ms_per_step": attr_ms / args.steps,

@@ -337,10 +337,17 @@ mpg_status mpg_fp64_peak(mpg_ctx* ctx, double* flops, cudaStream_t stream);
  * Synchronous (allocates the counter). */
 typedef struct mpg_graph mpg_graph;
 mpg_status mpg_graph_begin(mpg_ctx* ctx, cudaStream_t stream, uint64_t rng_advance);
+/* Lets another context (same device) record into the capture begun on `ctx`:
+ * its calls on streams joined to the capture stream (by an event recorded on
+ * it) are recorded too and share the graph's random-number counter, until
+ * mpg_graph_end on `ctx`.  Two contexts with their own buffers make a graph
+ * that advances two independent batches at once, so that the latency-bound
+ * ends of one batch's kernels overlap the other's (double buffering). */
+mpg_status mpg_graph_join(mpg_ctx* ctx, mpg_ctx* other);
 mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t stream, mpg_graph** out);
 /* Replays the graph on `stream` (asynchronous, one graph launch). */
 mpg_status mpg_graph_launch(mpg_graph* graph, cudaStream_t stream);
-/* Kernel launches inside one replay. */
+/* Kernel launches inside one replay (of every context recorded). */
 mpg_status mpg_graph_kernels(const mpg_graph* graph, int64_t* count);
 void mpg_graph_destroy(mpg_graph* graph);
 

@@ -89,6 +89,7 @@ struct mpg_ctx {
   bool profile_saved = false;
   unsigned long long* cap_rng = nullptr;  // the recorded graph's random-number counter
   uint64_t cap_advance = 0;
+  std::vector<mpg_ctx*> cap_joined;       // other contexts recording into this capture
   int64_t cap_launch0 = 0;
   cudaStream_t aux[MAXK] = {};
   cudaEvent_t ev_fork = nullptr;
@@ -1014,10 +1015,24 @@ mpg_status mpg_graph_begin(mpg_ctx* ctx, cudaStream_t st, uint64_t rng_advance) 
   return MPG_OK;
 }
 
+mpg_status mpg_graph_join(mpg_ctx* ctx, mpg_ctx* other) {
+  if (!ctx || !other) return fail(MPG_ERR_INVALID_ARG, "ctx or other is NULL");
+  if (!ctx->capturing || !ctx->cap_rng) return fail(MPG_ERR_INVALID_ARG, "no capture begun on this context");
+  if (other == ctx || other->capturing) return fail(MPG_ERR_INVALID_ARG, "the other context is already recording");
+  if (other->device != ctx->device) return fail(MPG_ERR_INVALID_ARG, "contexts on different devices");
+  other->capturing = true;
+  other->cap_rng = ctx->cap_rng;
+  other->profile_saved = other->profile;
+  other->profile = false;
+  other->cap_launch0 = other->launches;
+  ctx->cap_joined.push_back(other);
+  return MPG_OK;
+}
+
 mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t st, mpg_graph** out) {
   if (!ctx || !out) return fail(MPG_ERR_INVALID_ARG, "ctx or out is NULL");
   *out = nullptr;
-  if (!ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "no capture in progress on this context");
+  if (!ctx->capturing || !ctx->cap_rng) return fail(MPG_ERR_INVALID_ARG, "no capture begun on this context");
   CUDA_TRY(cudaSetDevice(ctx->device));
   launch_rng_advance(ctx->cap_rng, ctx->cap_advance, st);
   cudaError_t le = cudaGetLastError();
@@ -1028,6 +1043,14 @@ mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t st, mpg_graph** out) {
   g->counter = ctx->cap_rng;
   g->kernels = ctx->launches - ctx->cap_launch0 + 1;
   ctx->launches = ctx->cap_launch0;
+  for (mpg_ctx* o : ctx->cap_joined) {  // their recorded launches replay with this graph
+    g->kernels += o->launches - o->cap_launch0;
+    o->launches = o->cap_launch0;
+    o->capturing = false;
+    o->cap_rng = nullptr;
+    o->profile = o->profile_saved;
+  }
+  ctx->cap_joined.clear();
   ctx->capturing = false;
   ctx->cap_rng = nullptr;
   ctx->profile = ctx->profile_saved;

@@ -70,7 +70,7 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
-           "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_end",
+           "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune"]
 
 _lib = None
@@ -115,6 +115,7 @@ def lib():
         L.mpg_guide_clear.argtypes = [vp, C.POINTER(mpg_guide), vp]
         L.mpg_graph_begin.argtypes = [vp, vp, u64]
         L.mpg_graph_end.argtypes = [vp, vp, C.POINTER(vp)]
+        L.mpg_graph_join.argtypes = [vp, vp]
         L.mpg_graph_launch.argtypes = [vp, vp]
         L.mpg_graph_kernels.argtypes = [vp, C.POINTER(C.c_int64)]
         L.mpg_graph_destroy.argtypes = [vp]
@@ -337,8 +338,8 @@ class Graph:
     recorded, not run.  Replay r draws its random numbers at rng_offset +
     r * rng_advance."""
 
-    def __init__(self, ctx, rng_advance=0):
-        self.ctx, self.rng_advance, self.h = ctx, int(rng_advance), None
+    def __init__(self, ctx, rng_advance=0, join=()):
+        self.ctx, self.rng_advance, self.h, self.join = ctx, int(rng_advance), None, list(join)
         self.stream = torch.cuda.Stream(device=ctx.device)
 
     def __enter__(self):
@@ -347,6 +348,15 @@ class Graph:
         self._ctx_mgr = torch.cuda.stream(self.stream)
         self._ctx_mgr.__enter__()
         _check(lib().mpg_graph_begin(self.ctx.h, _stream(self.stream), self.rng_advance))
+        for other in self.join:
+            code = lib().mpg_graph_join(self.ctx.h, other.h)
+            if code != MPG_OK:
+                h = C.c_void_p()
+                lib().mpg_graph_end(self.ctx.h, _stream(self.stream), C.byref(h))
+                if h:
+                    lib().mpg_graph_destroy(h)
+                self._ctx_mgr.__exit__(None, None, None)
+                _check(code)
         return self
 
     def __exit__(self, et, ev, tb):

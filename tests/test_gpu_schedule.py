@@ -167,3 +167,41 @@ def test_autotune_picks_a_valid_schedule(M, ctx):
     ref = _run(M, ctx, wl, base)
     got = _run(M, ctx, wl, tuned)
     _bitwise_equal(ref, got, ["status", "surf", "trials", "converged_walks"] if tuned.fp64_k else None)
+
+
+def test_two_context_graph_matches_uncaptured(M, ctx):
+    """Two contexts recording into one capture (double buffering): replay r of
+    batch j draws at offset + (2 r + j) B, bit-identical to the uncaptured calls."""
+    wl = I.glass_sphere(n=48, spq=8)
+    P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, k_uniform=2)
+    ctxs = [ctx, M.Context(0)]
+    parts = [(M.Scene(c, wl), M.Chains(wl), M.Contribution.empty(wl.B, wl.Q)) for c in ctxs]
+    off = 777
+    for j, c in enumerate(ctxs):  # size the buffers
+        _step(M, c, *parts[j], wl, P, off + j * wl.B)
+    torch.cuda.synchronize()
+    refs = []
+    for r in range(2):
+        for j, c in enumerate(ctxs):
+            _step(M, c, *parts[j], wl, P, off + (2 * r + j) * wl.B)
+            c.sync()
+            refs.append(_snapshot(parts[j][1], parts[j][2]))
+    g = M.Graph(ctx, rng_advance=2 * wl.B, join=[ctxs[1]])
+    side = [torch.cuda.Stream(), torch.cuda.Stream()]
+    with g:
+        for j, c in enumerate(ctxs):
+            side[j].wait_stream(g.stream)
+            sc, ch, res = parts[j]
+            M.mpg_sample_seeds(c, sc, None, ch, P, wl.rng_seed, off + j * wl.B, stream=side[j])
+            M.mpg_manifold_walk(c, sc, ch, P, stream=side[j])
+            M.mpg_chain_contribution(c, sc, None, ch, P, wl.rng_seed, off + j * wl.B, out=res, stream=side[j])
+        for s in side:
+            g.stream.wait_stream(s)
+    for r in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        for j in range(2):
+            _bitwise_equal(refs[2 * r + j], _snapshot(parts[j][1], parts[j][2]))
+    with pytest.raises(M.MpgError):  # a context cannot join a capture twice
+        with M.Graph(ctx, join=[ctxs[1], ctxs[1]]):
+            pass
