@@ -589,14 +589,22 @@ __device__ __forceinline__ bool reproject(const DScene& S, int surf, float3 targ
   return hf_vertical_hit(S.hf[sf.hf], target.x, target.y, p, prim, b1, b2);
 }
 
-// Move every vertex by beta (dpdu du_0 + dpdv du_1) in its tangent plane and
-// reproject it onto its surface; chain visibility is checked once converged.
+// Newton step of every vertex as a 3-D tangent vector dpdu du_0 + dpdv du_1.
 template <int K>
-__device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, const float3 (&tu)[K],
-                                        const float3 (&tv)[K], const float2 (&du)[K][1], float beta, Chain<K>& out) {
+__device__ __forceinline__ void step_vectors(const float3 (&tu)[K], const float3 (&tv)[K], const float2 (&du)[K][1],
+                                             float3 (&d)[K]) {
+#pragma unroll
+  for (int i = 0; i < K; ++i) d[i] = tu[i] * du[i][0].x + tv[i] * du[i][0].y;
+}
+
+// Move every vertex by beta d_i in its tangent plane and reproject it onto its
+// surface; chain visibility is checked once converged.
+template <int K>
+__device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, const float3 (&d)[K], float beta,
+                                        Chain<K>& out) {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    float3 target = ch.x[i] + (tu[i] * du[i][0].x + tv[i] * du[i][0].y) * beta;
+    float3 target = ch.x[i] + d[i] * beta;
     out.surf[i] = ch.surf[i];
     out.prim[i] = ch.prim[i];
     out.b1[i] = ch.b1[i];
@@ -624,11 +632,13 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
     for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
     if (kStats) { cnt.newton++; cnt.rows += K; }
     if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
+    float3 dstep[K];
+    step_vectors<K>(tu, tv, du, dstep);
     float beta = 1.0f;
     bool accepted = false;
     for (int hv = 0; hv <= P.max_halvings; ++hv, beta *= 0.5f) {
       Chain<K> cand;
-      if (!propose<K>(S, ch, tu, tv, du, beta, cand)) continue;
+      if (!propose<K>(S, ch, dstep, beta, cand)) continue;
       float cc2;
       if (eval_c<K, kStats>(S, cand, e, cc2, cnt) && cc2 < cn2) {
         ch = cand;

@@ -21,8 +21,7 @@ template <int K>
 struct WalkLane {
   Chain<K> ch;
   Ends e;
-  float3 tu[K], tv[K];
-  float2 du[K][1];
+  float3 d[K];  // Newton step of each vertex (tangent vector), kept through the halvings
   float cn2, cmax, beta;
   int it, hv;
   bool need_eval;
@@ -46,20 +45,23 @@ __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const 
   if (w.need_eval) {
     if (!eval_phase) return RUNNING;
     VB vb[K];
-    if (!eval_full<K, kS>(S, w.ch, w.e, vb, w.tu, w.tv, w.cn2, w.cmax, false, cnt)) return ST_FAILED;
+    float3 tu[K], tv[K];
+    if (!eval_full<K, kS>(S, w.ch, w.e, vb, tu, tv, w.cn2, w.cmax, false, cnt)) return ST_FAILED;
     if (w.cmax < P.tol) return ST_CONVERGED;
     if (w.it >= P.max_iter) return ST_LIMIT;
+    float2 du[K][1];
 #pragma unroll
-    for (int i = 0; i < K; ++i) w.du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
+    for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
     if (kS) { cnt.newton++; cnt.rows += K; }
-    if (!thomas<K, 1>(vb, w.du, P.sing_eps)) return ST_FAILED;
+    if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
+    step_vectors<K>(tu, tv, du, w.d);
     w.beta = 1.0f;
     w.hv = 0;
     w.need_eval = false;
   }
   Chain<K> cand;
   float cc2;
-  if (propose<K>(S, w.ch, w.tu, w.tv, w.du, w.beta, cand) && eval_c<K, kS>(S, cand, w.e, cc2, cnt) &&
+  if (propose<K>(S, w.ch, w.d, w.beta, cand) && eval_c<K, kS>(S, cand, w.e, cc2, cnt) &&
       cc2 < w.cn2) {
     w.ch = cand;
     w.it++;
