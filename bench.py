@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true", help="skip the K3/K6, mixed-batch and adjoint measurements")
     ap.add_argument("--no-graph", action="store_true", help="batched mode without graph capture")
     ap.add_argument("--no-pipeline", action="store_true", help="one batch per graph replay (no double buffering)")
+    ap.add_argument("--in-flight", type=int, default=4, help="batches advanced by one graph replay (own contexts)")
     ap.add_argument("--part", choices=list(PARTS), help="run one secondary measurement only")
     return ap.parse_args()
 
@@ -144,7 +145,7 @@ def run_ours(args, rank, world, local):
     # contexts and two streams (double buffering): consecutive steps are
     # independent (each samples the trained guide and builds its own), so the
     # latency-bound ends of one batch's kernels overlap the other batch's work.
-    n_buf = 2 if graph_mode and not args.no_pipeline else 1
+    n_buf = max(1, args.in_flight) if graph_mode and not args.no_pipeline else 1
     ctxs = [mpg.Context(local) for _ in range(n_buf)]
 
     def buffers(c):
@@ -187,24 +188,39 @@ def run_ours(args, rank, world, local):
             step_on(j, 1000 + 16 * i + j)
     torch.cuda.synchronize()
     graph = None
-    per_launch = 1
+    plan = [1] * args.steps  # batches advanced by each timed launch (sum = steps, exactly)
     if graph_mode:
-        # replay r draws at the offsets of steps 2000 + n_buf r + j
-        graph = mpg.Graph(ctx, rng_advance=n_buf * B * world, join=ctxs[1:])
-        side = [torch.cuda.Stream(device=dev) for _ in range(n_buf)]
-        with graph:
-            for j in range(n_buf):
-                side[j].wait_stream(graph.stream)
-                step_on(j, 2000 + j, stream=side[j])
-            for j in range(n_buf):
-                graph.stream.wait_stream(side[j])
+        def capture(nb, base):
+            # replay r of an nb-batch graph draws at the offsets of steps base + nb r + j
+            g = mpg.Graph(ctx, rng_advance=nb * B * world, join=ctxs[1:nb])
+            side = [torch.cuda.Stream(device=dev) for _ in range(nb)]
+            with g:
+                for j in range(nb):
+                    side[j].wait_stream(g.stream)
+                    step_on(j, base + j, stream=side[j])
+                for j in range(nb):
+                    g.stream.wait_stream(side[j])
+            return g
+        graph = capture(n_buf, 2000)
+        rem = args.steps % n_buf
+        graph_rem = capture(rem, 1 << 20) if rem else None
         for i in range(args.warmup):
             graph.launch()
+            if graph_rem is not None:
+                graph_rem.launch()
         torch.cuda.synchronize()
-        per_launch = n_buf
-    n_launch = -(-args.steps // per_launch)  # steps rounded up to whole replays
-    steps_run = n_launch * per_launch
-    run = (lambda i: graph.launch()) if graph is not None else step
+        plan = [n_buf] * (args.steps // n_buf) + ([rem] if rem else [])
+    n_launch = len(plan)
+    steps_run = sum(plan)
+    per_launch = max(plan)
+
+    def run(i):
+        if graph is None:
+            step(i)
+        elif plan[i] == n_buf:
+            graph.launch()
+        else:
+            graph_rem.launch()
 
     def all_stats():
         tot = None
@@ -242,7 +258,7 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     for c in ctxs:
         c.sync()
-    step_ms = [a.elapsed_time(b) / per_launch for a, b in ev for _ in range(per_launch)]
+    step_ms = [a.elapsed_time(b) / nb for (a, b), nb in zip(ev, plan) for _ in range(nb)]
     launches = ctx.launches() - n_launch0
     total = all_stats()
     conv = total["converged"]
@@ -299,7 +315,10 @@ def run_ours(args, rank, world, local):
         a.record(stream)
         for d, h in host_in:
             d.copy_(h, non_blocking=True)
-        run(500 + i)
+        if graph is not None:
+            graph.launch()
+        else:
+            step(500 + i)
         for j, bf in enumerate(bufs[:per_launch]):
             E_host[j].copy_(bf["out"].E, non_blocking=True)
             n_host[j].copy_(bf["rec"][3], non_blocking=True)
