@@ -90,34 +90,23 @@ __global__ void __launch_bounds__(64) k_adjoint(const __grid_constant__ DScene S
       }
     }
     if (!ok) { atomicAdd(skipped, 1); continue; }
-    // J^T lambda = dT/du (Gaussian elimination with partial pivoting, NU <= 8)
-    float A[NU][NU], lam[NU];
+    // J^T lambda = dT/du by the 2x2-block Thomas sweep on the transposed
+    // block-tridiagonal system: its diagonal blocks are B_i^T, its sub- and
+    // super-diagonal blocks Cc_{i-1}^T and A_{i+1}^T (J = dC/du, dC[r][d] for d < 2k).
+    VB vt[K];
+    float2 lam2[K][1];
 #pragma unroll
-    for (int r = 0; r < NU; ++r) {
+    for (int i = 0; i < K; ++i) {
+      const int r = 2 * i;
+      vt[i].B = make_float4(dC[r][r], dC[r + 1][r], dC[r][r + 1], dC[r + 1][r + 1]);
+      if (i > 0) vt[i].A = make_float4(dC[r - 2][r], dC[r - 1][r], dC[r - 2][r + 1], dC[r - 1][r + 1]);
+      if (i < K - 1) vt[i].Cc = make_float4(dC[r + 2][r], dC[r + 3][r], dC[r + 2][r + 1], dC[r + 3][r + 1]);
+      lam2[i][0] = make_float2(dT[r], dT[r + 1]);
+    }
+    if (!thomas<K, 1>(vt, lam2, 0.0f)) { atomicAdd(skipped, 1); continue; }
+    float lam[NU];
 #pragma unroll
-      for (int cc = 0; cc < NU; ++cc) A[r][cc] = dC[cc][r];
-      lam[r] = dT[r];
-    }
-    for (int col = 0; col < NU && ok; ++col) {
-      int piv = col;
-      for (int r = col + 1; r < NU; ++r) if (fabsf(A[r][col]) > fabsf(A[piv][col])) piv = r;
-      if (!(fabsf(A[piv][col]) > 0.0f)) { ok = false; break; }
-      if (piv != col) {
-        for (int cc = 0; cc < NU; ++cc) { float tmp = A[col][cc]; A[col][cc] = A[piv][cc]; A[piv][cc] = tmp; }
-        float tmp = lam[col]; lam[col] = lam[piv]; lam[piv] = tmp;
-      }
-      for (int r = col + 1; r < NU; ++r) {
-        float f = A[r][col] / A[col][col];
-        for (int cc = col; cc < NU; ++cc) A[r][cc] -= f * A[col][cc];
-        lam[r] -= f * lam[col];
-      }
-    }
-    if (!ok) { atomicAdd(skipped, 1); continue; }
-    for (int r = NU - 1; r >= 0; --r) {
-      float v = lam[r];
-      for (int cc = r + 1; cc < NU; ++cc) v -= A[r][cc] * lam[cc];
-      lam[r] = v / A[r][r];
-    }
+    for (int i = 0; i < K; ++i) { lam[2 * i] = lam2[i][0].x; lam[2 * i + 1] = lam2[i][0].y; }
     for (int p = 0; p < m; ++p) {
       float g = dT[NU + p];
 #pragma unroll
