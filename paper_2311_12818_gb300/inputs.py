@@ -78,7 +78,7 @@ def _target(type_, centre, radius=0.0, ex=(0, 0, 0), ey=(0, 0, 0), normal=(0, 0,
 
 @dataclasses.dataclass
 class Params:
-    """Solver constants (the paper fixes none of them; values are this build's reading)."""
+    """Solver constants (the paper fixes none of them; the values are a reading of it)."""
     tol: float = 1e-6            # converged when max_i |C_i|_inf < tol
     max_iter: int = 20           # Newton steps
     max_halvings: int = 8        # step halvings per Newton step

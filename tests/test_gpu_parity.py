@@ -89,7 +89,7 @@ def _compare_seeds(wl, gs, os_):
     scale = wl.scene_scale
     # The surface each deduced vertex lands on is a floating-point decision
     # (FP32 here, FP64 in the oracle) along a refraction chain that amplifies
-    # rounding; near a surface boundary the two may differ, so it is judged
+    # rounding; near a surface boundary the two may differ, so it is assessed
     # like the walk flags: agreement on >= 99.9 % of the seeds valid on both
     # sides, positions compared where every surface agrees.
     same = np.ones(wl.B, bool)
@@ -104,7 +104,7 @@ def _compare_seeds(wl, gs, os_):
     assert np.array_equal(gs["tau"][both], os_["tau"][both])
     # the seed density is a diagnostic output (the estimator uses Bernoulli
     # trials, not the density); near grazing it scales like 1/cos and FP32
-    # direction rounding is amplified, so judge the bulk and the median
+    # direction rounding is amplified, so compare the bulk and the median
     rel = np.abs(gs["pdf"][both] - os_["pdf"][both]) / np.maximum(os_["pdf"][both], 1e-30)
     assert np.quantile(rel, 0.95) < 1e-3
     assert np.median(rel) < 1e-5
