@@ -75,16 +75,18 @@ typedef struct mpg_params {
   int32_t tau_random;   /* nonzero: draw tau_i ~ Bernoulli(0.5) per trial          */
   int32_t k_uniform;    /* 1..8: every chain has this length; 0: lengths vary      */
   float stall_tol;      /* FP32 resolution of C: a walk whose line search can no
-                           longer reduce |C| ends CONVERGED when max_i |C_i|_inf <
-                           stall_tol (0 disables; the FP64 oracle has no such rule) */
+                           longer reduce |C|, or that reaches max_iter, ends
+                           CONVERGED when max_i |C_i|_inf < stall_tol (0 disables;
+                           the FP64 oracle has no such rule)                      */
   float fp64_tol;       /* G is formed in FP32 from both chain ends (reciprocity);
                            when the two differ by more than this relative amount,
                            for k >= 6, or for a walk stopped by stall_tol, the
                            vertices are polished and G recomputed in FP64
                            (0: always FP64)                                     */
-  /* Schedule of the batched mode.  None of these changes a result: every chain
-   * is walked, and every trial drawn, with the same arithmetic whatever the
-   * schedule (mpg_autotune picks them by timing). */
+  /* Schedule of the batched mode.  Apart from fp64_k and walk_group none of
+   * these changes a result: every chain is walked, and every trial drawn, with
+   * the same arithmetic whatever the schedule (mpg_autotune picks them by
+   * timing). */
   int32_t fp64_k;       /* chains of this length or longer always take the FP64
                            geometry term (0 = 6; 1..6 allowed, so the split can
                            only move toward more FP64)                         */
@@ -99,6 +101,12 @@ typedef struct mpg_params {
                            parallel round (0 = 64; 1..4096), x4 each round after;
                            issued trial-major, so trials past a chain's first
                            success are mostly skipped                          */
+  int32_t walk_group;   /* batched walk: 0 = one thread per chain; 1 = one chain per
+                           group of G lanes (G = 2, 4, 8 >= k; 128 threads per
+                           CTA), lane j owning vertex j, blocks staged in shared
+                           memory.  Same per-vertex arithmetic; the compiler may
+                           contract products differently in the two forms, so
+                           results agree to FP32 rounding, not bit for bit    */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */

@@ -271,7 +271,7 @@ mpg_status check_params(const mpg_params* p) {
       p->block_threads < 0 || p->block_threads > 128 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) ||
       !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
       p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
-      p->trial_batch < 0 || p->trial_batch > 4096)
+      p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 1)
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -394,6 +394,11 @@ mpg_status run_plan(mpg_ctx* ctx, const Plan& plan, cudaStream_t st, F fn) {
 }
 
 int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threads : 128; }
+
+// Persistent walk kernel of the batched mode: occupancy entry and block size
+// (the group form runs 128 threads per CTA).
+int walk_which(const mpg_params* p) { return p->walk_group ? 7 : 4; }
+int walk_block(const mpg_params* p) { return p->walk_group ? 128 : block_of(p); }
 
 // Synchronous Bernoulli rounds before the parallel ones (-1: none, 0: default).
 int sync_rounds_of(const mpg_params* p) { return p->trial_sync_rounds < 0 ? 0 : p->trial_sync_rounds > 0 ? p->trial_sync_rounds : 2; }
@@ -724,7 +729,7 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
     return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
       timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
         launch_walk_p(K, ctx->stats_on, sc->S, c, plan.w, *P, dc, ctx->d_queue + 32 * K,
-                      grid_of(ctx, P, 4, K, block, c.B, true), block, s2);
+                      grid_of(ctx, P, walk_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
       });
     });
   }
@@ -842,8 +847,8 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       });
       // trial walks run the walk kernel and are tallied with the walk family
       timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
-        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t, grid_of(ctx, P, 4, K, block, c.B, true), block,
-                      s2);
+        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t,
+                      grid_of(ctx, P, walk_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
       });
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
         launch_trial_check(K, sc->S, c, tc, o, lists[cur], base, counts[cur], t, t == T1, *P, lists[nxt], counts[nxt],
@@ -1170,6 +1175,11 @@ mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guid
       }
     }
     s = group(c);
+  }
+  if (e == cudaSuccess && !s) {  // walk form: one thread per chain or one chain per lane group
+    mpg_params P = best;
+    P.walk_group = best.walk_group ? 0 : 1;
+    s = group({P});
   }
   if (e == cudaSuccess && !s) {  // refill cadence of the persistent kernels
     std::vector<mpg_params> c;

@@ -626,7 +626,7 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
     iters = it;
     if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, false, cnt)) return ST_FAILED;
     if (cmax < P.tol) return ST_CONVERGED;
-    if (it >= P.max_iter) return ST_LIMIT;
+    if (it >= P.max_iter) return cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
     float2 du[K][1];
 #pragma unroll
     for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);

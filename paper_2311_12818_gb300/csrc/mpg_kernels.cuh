@@ -106,6 +106,9 @@ struct KLaunch {
                         cudaStream_t st);
   static void walk_p(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                      int* queue, int grid, int block, cudaStream_t st);
+  // one chain per group of G >= K lanes (128 threads per CTA)
+  static void walk_g(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                     int* queue, int grid, cudaStream_t st);
   static void trial_init(const DScene& S, const DChains& c, DWork w, DOut o, int* list, const int* base, int* n_list,
                          unsigned* nbest, int grid, cudaStream_t st);
   static void contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st);

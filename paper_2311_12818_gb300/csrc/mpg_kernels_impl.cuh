@@ -267,6 +267,17 @@ void KLaunch<K>::walk_p(bool stats, const DScene& S, const DChains& c, DWork w, 
 }
 
 template <int K>
+void KLaunch<K>::walk_g(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
+                        int* queue, int grid, cudaStream_t st) {
+  if constexpr (K == 1) {
+    kern::k_walk_p<K, true><<<grid, 128, 0, st>>>(S, c, w, P, ctx, queue);
+  } else {
+    constexpr int G = K <= 2 ? 2 : K <= 4 ? 4 : 8;
+    kern::k_walk_g<K, G, true><<<grid, 128, 0, st>>>(S, c, w, P, ctx, queue);
+  }
+}
+
+template <int K>
 void KLaunch<K>::contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st) {
   kern::k_contrib64<K><<<grid, 64, 0, st>>>(S, c, P, o);
 }
@@ -339,6 +350,10 @@ int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true>;
   else if (which == 4) fn = (const void*)kern::k_walk_p<K, true>;
   else if (which == 5) fn = (const void*)kern::k_trial_seed<K, true>;
+  else if (which == 7) {
+    if constexpr (K == 1) fn = (const void*)kern::k_walk_p<K, true>;
+    else fn = (const void*)kern::k_walk_g<K, (K <= 2 ? 2 : K <= 4 ? 4 : 8), true>;
+  }
   else fn = (const void*)kern::k_bern_round<K, true>;
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, block, 0) != cudaSuccess) return 1;

@@ -17,6 +17,23 @@ namespace kern {
 
 constexpr int RUNNING = -1;
 
+// Resident CTAs of 128 threads per SM the one-thread-per-chain kernels are
+// compiled for: the register need grows with K (about 128 registers at
+// K <= 2, 168 at K <= 4, the 255 maximum beyond), and a tighter bound spills.
+template <int K>
+constexpr int walk_min_ctas() { return K <= 2 ? 5 : K <= 4 ? 3 : 2; }
+
+// float3 from the previous / next lane of a segment of `width` lanes (the lane
+// itself at the segment's start / end); `mask` holds the segment's lanes.
+__device__ __forceinline__ float3 shfl_up3(unsigned mask, float3 v, int width) {
+  return make_float3(__shfl_up_sync(mask, v.x, 1, width), __shfl_up_sync(mask, v.y, 1, width),
+                     __shfl_up_sync(mask, v.z, 1, width));
+}
+__device__ __forceinline__ float3 shfl_down3(unsigned mask, float3 v, int width) {
+  return make_float3(__shfl_down_sync(mask, v.x, 1, width), __shfl_down_sync(mask, v.y, 1, width),
+                     __shfl_down_sync(mask, v.z, 1, width));
+}
+
 template <int K>
 struct WalkLane {
   Chain<K> ch;
@@ -48,7 +65,7 @@ __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const 
     float3 tu[K], tv[K];
     if (!eval_full<K, kS>(S, w.ch, w.e, vb, tu, tv, w.cn2, w.cmax, false, cnt)) return ST_FAILED;
     if (w.cmax < P.tol) return ST_CONVERGED;
-    if (w.it >= P.max_iter) return ST_LIMIT;
+    if (w.it >= P.max_iter) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
     float2 du[K][1];
 #pragma unroll
     for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
@@ -123,7 +140,7 @@ __device__ __forceinline__ long long take_item64(bool want, unsigned long long* 
 // Walk (K2): one lane per chain, refilled from the bucket's queue.
 // ---------------------------------------------------------------------------
 template <int K, bool kS>
-__global__ void __launch_bounds__(128, 5) k_walk_p(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
                                                 DCtx ctx, int* queue) {
   Tally t = {};
   const int n = n_items<K>(w, c);
@@ -159,6 +176,185 @@ __global__ void __launch_bounds__(128, 5) k_walk_p(const __grid_constant__ DScen
         store_chain<K>(c, b, L.ch);
         c.status[b] = (uint8_t)st;
         c.iters[b] = (uint8_t)L.it;
+        b = -1;
+      }
+    }
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+// ---------------------------------------------------------------------------
+// Walk (K2), one chain per thread group: lane j of a group of G >= K lanes
+// owns vertex j (its position, surface coordinates and step vector); the
+// neighbours' positions and tangent bases come by shuffles within the group,
+// and each lane stages its vertex's 2x2 blocks and constraint in shared
+// memory, where every lane of the group reads all of them and runs the same
+// block Thomas sweep.  Per vertex the arithmetic is that of walk_pass() and
+// the sums over vertices are taken in the same order (the compiler may still
+// contract some products differently, so the two forms agree to FP32
+// rounding); the group form cuts the latency of a pass by up to K, at the
+// price of idle lanes for K < G and of the staging.
+// ---------------------------------------------------------------------------
+template <int K>
+struct GroupLane {
+  float3 x, d;  // own vertex and its Newton step
+  int surf, prim;
+  float b1, b2;
+  Ends e;
+  float cn2, cmax, beta;
+  int it, hv;
+  bool need_eval;
+};
+
+template <int K, int G, bool kS>
+__device__ __forceinline__ int walk_pass_g(const DScene& S, GroupLane<K>& w, const mpg_params& P, Counters& cnt,
+                                           bool eval_phase, unsigned gmask, int j, float2* sC, float4* sA, float4* sB,
+                                           float4* sCc) {
+  const bool own = j < K;
+  if (w.need_eval) {
+    if (!eval_phase) return RUNNING;
+    Frame fr = {};
+    if (own) fr = vertex_frame(S, w.surf, w.prim, w.x, w.b1, w.b2);
+    float3 tu = fr.dpdu, tv = fr.dpdv;
+    float3 xp = shfl_up3(gmask, w.x, G), xn = shfl_down3(gmask, w.x, G);
+    float3 pu = shfl_up3(gmask, tu, G), pv = shfl_up3(gmask, tv, G);
+    float3 nu = shfl_down3(gmask, tu, G), nv = shfl_down3(gmask, tv, G);
+    if (j == 0) xp = w.e.xD;
+    if (j == K - 1) xn = w.e.xL;
+    VB vb;
+    bool ok = !own || vertex_blocks(xp, pu, pv, w.x, fr, xn, nu, nv, S.s[w.surf], (w.e.tau >> j) & 1u, j > 0,
+                                    j < K - 1, vb);
+    if (!__all_sync(gmask, ok)) return ST_FAILED;
+    if (own) { sC[j] = vb.C; sA[j] = vb.A; sB[j] = vb.B; sCc[j] = vb.Cc; }
+    __syncwarp(gmask);
+    VB blk[K];
+    float2 du[K][1];
+    float cn2 = 0.0f, cmax = 0.0f;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      blk[i].C = sC[i]; blk[i].A = sA[i]; blk[i].B = sB[i]; blk[i].Cc = sCc[i];
+      cn2 = fmaf(blk[i].C.x, blk[i].C.x, fmaf(blk[i].C.y, blk[i].C.y, cn2));
+      cmax = fmaxf(cmax, fmaxf(fabsf(blk[i].C.x), fabsf(blk[i].C.y)));
+      du[i][0] = make_float2(-blk[i].C.x, -blk[i].C.y);
+    }
+    __syncwarp(gmask);  // the staging area is rewritten by the next evaluation
+    if (kS && j == 0) cnt.full_evals += K;
+    w.cn2 = cn2;
+    w.cmax = cmax;
+    if (cmax < P.tol) return ST_CONVERGED;
+    if (w.it >= P.max_iter) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
+    if (kS && j == 0) { cnt.newton++; cnt.rows += K; }
+    if (!thomas<K, 1>(blk, du, P.sing_eps)) return ST_FAILED;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i == j) w.d = tu * du[i][0].x + tv * du[i][0].y;
+    w.beta = 1.0f;
+    w.hv = 0;
+    w.need_eval = false;
+  }
+  float3 cx = w.x;
+  int cprim = w.prim;
+  float cb1 = w.b1, cb2 = w.b2;
+  bool ok = !own || reproject(S, w.surf, w.x + w.d * w.beta, cx, cprim, cb1, cb2);
+  bool accept = false;
+  if (__all_sync(gmask, ok)) {
+    float3 xp = shfl_up3(gmask, cx, G), xn = shfl_down3(gmask, cx, G);
+    if (j == 0) xp = w.e.xD;
+    if (j == K - 1) xn = w.e.xL;
+    float2 C = make_float2(0.f, 0.f);
+    bool okc = true;
+    if (own) {
+      float3 n = vertex_normal(S, w.surf, cprim, cx, cb1, cb2);
+      okc = vertex_c(xp, cx, xn, n, S.s[w.surf], (w.e.tau >> j) & 1u, C);
+    }
+    if (__all_sync(gmask, okc)) {
+      if (kS && j == 0) cnt.c_evals += K;
+      const int leader = (threadIdx.x & 31) & ~(G - 1);
+      float cc2 = 0.0f;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        float cxv = __shfl_sync(gmask, C.x, leader + i), cyv = __shfl_sync(gmask, C.y, leader + i);
+        cc2 = fmaf(cxv, cxv, fmaf(cyv, cyv, cc2));
+      }
+      accept = cc2 < w.cn2;
+    }
+  }
+  if (accept) {
+    w.x = cx; w.prim = cprim; w.b1 = cb1; w.b2 = cb2;
+    w.it++;
+    w.need_eval = true;
+    return RUNNING;
+  }
+  w.hv++;
+  w.beta *= 0.5f;
+  if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
+  return RUNNING;
+}
+
+template <int K, int G, bool kS>
+__global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+                                                DCtx ctx, int* queue) {
+  static_assert(G >= K && G <= 32 && (G & (G - 1)) == 0, "group of a power of two >= K lanes");
+  constexpr int NG = 128 / G;
+  __shared__ float2 sC[NG][K];
+  __shared__ float4 sA[NG][K], sB[NG][K], sCc[NG][K];
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, j = threadIdx.x % G, grp = threadIdx.x / G;
+  const int leader = lane & ~(G - 1);
+  const unsigned gmask = (G == 32 ? FULL : ((1u << G) - 1u)) << leader;
+  const size_t Bz = (size_t)c.B;
+  GroupLane<K> L;
+  L.need_eval = false;
+  int b = -1;  // the group's chain (the same in every lane of the group)
+  bool done = false;
+  const int refill = P.refill_every > 1 ? P.refill_every : 1;
+  int pass = 0;
+  while (true) {
+    bool idle_warp = __all_sync(FULL, b < 0);
+    int i = take_item(j == 0 && b < 0 && (idle_warp || pass % refill == 0), queue, n, done);
+    i = __shfl_sync(FULL, i, leader);
+    ++pass;
+    if (i >= 0) {
+      int bb = item<K>(w, c, i);
+      if (bb >= 0 && c.status[bb] == ST_SEEDED) {
+        b = bb;
+        if (j < K) {
+          L.x = make_float3(c.x[(3 * j + 0) * Bz + b], c.x[(3 * j + 1) * Bz + b], c.x[(3 * j + 2) * Bz + b]);
+          L.surf = c.surf[j * Bz + b];
+          L.prim = c.prim[j * Bz + b];
+          L.b1 = c.bary[(2 * j + 0) * Bz + b];
+          L.b2 = c.bary[(2 * j + 1) * Bz + b];
+        }
+        L.e = load_ends(c, b);
+        L.it = 0;
+        L.hv = 0;
+        L.beta = 1.0f;
+        L.need_eval = true;
+      }
+    }
+    bool any = __any_sync(FULL, b >= 0);
+    if (!any && done) break;
+    const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
+    if (b >= 0) {
+      int st = walk_pass_g<K, G, kS>(S, L, P, t.c, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp], sCc[grp]);
+      if (st != RUNNING) {
+        if (j < K) {
+          c.x[(3 * j + 0) * Bz + b] = L.x.x;
+          c.x[(3 * j + 1) * Bz + b] = L.x.y;
+          c.x[(3 * j + 2) * Bz + b] = L.x.z;
+          c.surf[j * Bz + b] = L.surf;
+          c.prim[j * Bz + b] = L.prim;
+          c.bary[(2 * j + 0) * Bz + b] = L.b1;
+          c.bary[(2 * j + 1) * Bz + b] = L.b2;
+        }
+        if (j == 0) {
+          t.walks++;
+          t.conv += st == ST_CONVERGED;
+          c.status[b] = (uint8_t)st;
+          c.iters[b] = (uint8_t)L.it;
+        }
         b = -1;
       }
     }
@@ -268,7 +464,7 @@ __global__ void __launch_bounds__(256) k_trial_check(const __grid_constant__ DSc
 // is bounded by the items in flight, not by TB.
 // ---------------------------------------------------------------------------
 template <int K, bool kS>
-__global__ void __launch_bounds__(128, 5) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
+__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                     DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
                                                     int* queue, const int* list, const int* n_list, const int* base,
                                                     unsigned* nbest, int t0, int TB, DPairs pr) {

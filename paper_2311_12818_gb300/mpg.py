@@ -36,9 +36,10 @@ class mpg_params(C.Structure):
                 ("walk_mode", C.c_int32), ("block_threads", C.c_int32), ("tau_random", C.c_int32),
                 ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float),
                 ("fp64_k", C.c_int32), ("ctas_per_sm", C.c_int32), ("refill_every", C.c_int32),
-                ("trial_sync_rounds", C.c_int32), ("trial_batch", C.c_int32)]
+                ("trial_sync_rounds", C.c_int32), ("trial_batch", C.c_int32), ("walk_group", C.c_int32)]
 
-SCHEDULE_FIELDS = ["block_threads", "ctas_per_sm", "refill_every", "trial_sync_rounds", "trial_batch", "fp64_k"]
+SCHEDULE_FIELDS = ["block_threads", "ctas_per_sm", "refill_every", "trial_sync_rounds", "trial_batch", "fp64_k",
+                   "walk_group"]
 
 
 class mpg_chains(C.Structure):

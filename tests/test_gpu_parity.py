@@ -252,10 +252,11 @@ def test_water_pipeline_parity(M, ctx):
     assert np.quantile(rel, 0.999) < 1e-3
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_mixed_lengths_plain_and_batched(M, ctx, mode):
+    """mode 0: plain; 1: batched, one thread per chain; 2: batched, one chain per lane group."""
     wl = I.mixed(nx=48, ny=24, spq=4)
-    P = _params(M, wl, mode=mode, k_uniform=0)
+    P = _params(M, wl, mode=min(mode, 1), k_uniform=0, walk_group=int(mode == 2))
     sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
     osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
     _compare_seeds(wl, gs, os_)

@@ -162,11 +162,17 @@ def test_autotune_picks_a_valid_schedule(M, ctx):
     assert tuned.refill_every in (0, 1, 2, 4, 8)
     assert tuned.trial_sync_rounds in (0, 1, 2, 3) and tuned.trial_batch in (0, 4, 16, 64, 256)
     assert tuned.fp64_k in (0, 4, 5)
+    assert tuned.walk_group in (0, 1)
     for f in ("tol", "max_iter", "max_halvings", "max_trials", "dedup_eps", "walk_mode", "tau_random"):
         assert getattr(tuned, f) == getattr(base, f)
     ref = _run(M, ctx, wl, base)
     got = _run(M, ctx, wl, tuned)
-    _bitwise_equal(ref, got, ["status", "surf", "trials", "converged_walks"] if tuned.fp64_k else None)
+    if tuned.walk_group:  # same per-vertex arithmetic, contracted differently: compared like the oracle
+        assert (ref["status"] == got["status"]).mean() >= 0.999
+        ok = (ref["T"] > 0) & (got["T"] > 0)
+        assert np.quantile(np.abs(got["T"][ok] - ref["T"][ok]) / ref["T"][ok], 0.999) < 1e-3
+    else:
+        _bitwise_equal(ref, got, ["status", "surf", "trials", "converged_walks"] if tuned.fp64_k else None)
 
 
 def test_two_context_graph_matches_uncaptured(M, ctx):
