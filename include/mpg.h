@@ -340,7 +340,9 @@ mpg_status mpg_fp64_peak(mpg_ctx* ctx, double* flops, cudaStream_t stream);
  * grow only outside a capture, so run the same sequence once uncaptured first;
  * a recorded call that would have to grow them fails with MPG_ERR_INVALID_ARG.
  * After a failed recorded call, still end the capture with mpg_graph_end and
- * destroy the (incomplete) graph it returns.  The device pointers of the
+ * destroy the (incomplete) graph it returns.  Nothing may free device memory
+ * while the capture is open (no *_destroy of a context, scene or graph from
+ * this thread): cudaFree is not allowed then and invalidates the capture.  The device pointers of the
  * recorded calls are baked into the graph: keep them alive and in place.
  * Synchronous (allocates the counter). */
 typedef struct mpg_graph mpg_graph;

@@ -399,6 +399,7 @@ int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threa
 // (the group form runs 128 threads per CTA).
 int walk_which(const mpg_params* p) { return p->walk_group ? 7 : 4; }
 int walk_block(const mpg_params* p) { return p->walk_group ? 128 : block_of(p); }
+int round_which(const mpg_params* p) { return p->walk_group ? 8 : 6; }
 
 // Synchronous Bernoulli rounds before the parallel ones (-1: none, 0: default).
 int sync_rounds_of(const mpg_params* p) { return p->trial_sync_rounds < 0 ? 0 : p->trial_sync_rounds > 0 ? p->trial_sync_rounds : 2; }
@@ -871,7 +872,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
         launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q64,
                           lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, (int)TB, pr,
-                          grid_of(ctx, P, 6, K, block, c.B, true), block, s2);
+                          grid_of(ctx, P, round_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
         launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
                            lists[nxt], counts[nxt] + K, pr, dcb.stats, ctx->sms, s2);
       });

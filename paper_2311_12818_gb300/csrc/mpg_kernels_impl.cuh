@@ -310,6 +310,14 @@ void KLaunch<K>::bern_round(bool stats, const DScene& S, const DGuide* g, const 
                             const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
                             cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
+  if constexpr (K > 1) {
+    if (P.walk_group) {
+      constexpr int G = K <= 2 ? 2 : K <= 4 ? 4 : 8;
+      kern::k_bern_round_g<K, G, true><<<grid, 128, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
+                                                             n_list, base, nbest, t0, TB, pr);
+      return;
+    }
+  }
   kern::k_bern_round<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
                                                          n_list, base, nbest, t0, TB, pr);
 }
@@ -353,6 +361,9 @@ int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   else if (which == 7) {
     if constexpr (K == 1) fn = (const void*)kern::k_walk_p<K, true>;
     else fn = (const void*)kern::k_walk_g<K, (K <= 2 ? 2 : K <= 4 ? 4 : 8), true>;
+  } else if (which == 8) {
+    if constexpr (K == 1) fn = (const void*)kern::k_bern_round<K, true>;
+    else fn = (const void*)kern::k_bern_round_g<K, (K <= 2 ? 2 : K <= 4 ? 4 : 8), true>;
   }
   else fn = (const void*)kern::k_bern_round<K, true>;
   int n = 0;

@@ -533,5 +533,118 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
   if (kS) flush(t, ctx.stats);
 }
 
+// Parallel Bernoulli round, one chain per lane group (see k_walk_g): the
+// group's leader takes the (chain, trial) item, every lane draws the same trial
+// seed from the same counters and keeps its own vertex, the group walks it,
+// and the same-solution test is taken per vertex in FP64 and combined over the
+// group -- the decisions of k_bern_round.
+template <int K, int G, bool kS>
+__global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DScene S, DGuide g, int has_guide,
+                                                      DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
+                                                      int* queue, const int* list, const int* n_list, const int* base,
+                                                      unsigned* nbest, int t0, int TB, DPairs pr) {
+  static_assert(G >= K && G <= 32 && (G & (G - 1)) == 0, "group of a power of two >= K lanes");
+  constexpr int NG = 128 / G;
+  __shared__ float2 sC[NG][K];
+  __shared__ float4 sA[NG][K], sB[NG][K], sCc[NG][K];
+  Tally t = {};
+  Counters dummy = {};
+  const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
+  const int* over = list + *base;
+  const int nl = *n_list;
+  const long long n = (long long)nl * TB;
+  unsigned long long* queue64 = reinterpret_cast<unsigned long long*>(queue);
+  offset = rng_offset(offset, ctx);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31, j = threadIdx.x % G, grp = threadIdx.x / G;
+  const int leader = lane & ~(G - 1);
+  const unsigned gmask = (G == 32 ? FULL : ((1u << G) - 1u)) << leader;
+  const size_t Bz = (size_t)c.B;
+  GroupLane<K> L;
+  L.need_eval = false;
+  float3 tx = make_float3(0.f, 0.f, 0.f);  // own vertex of the chain's solution
+  int tsurf = -1;
+  int b = -1, tr = 0;
+  bool done = false;
+  const int refill = P.refill_every > 1 ? P.refill_every : 1;
+  int pass = 0;
+  while (true) {
+    bool idle_warp = __all_sync(FULL, b < 0);
+    long long i = take_item64(j == 0 && b < 0 && (idle_warp || pass % refill == 0), queue64, n, done);
+    i = __shfl_sync(FULL, i, leader);
+    ++pass;
+    // The leader alone reads the chain's best success (it changes under other
+    // groups' atomics) and decides for its group; every warp-wide shuffle below
+    // is executed by all 32 lanes.
+    int bb = -1, tt = 0;
+    bool take = false;
+    if (i >= 0) {
+      bb = over[i % nl];
+      tt = t0 + (int)(i / nl);
+      if (j == 0) take = tt <= P.max_trials && (unsigned)tt < *((volatile unsigned*)(nbest + bb));
+    }
+    take = __shfl_sync(FULL, take ? 1 : 0, leader) != 0;
+    bool drawn = false;
+    Chain<K> ch;
+    Ends e;
+    if (take) {
+      if (j == 0) t.trials++;
+      e = load_ends(c, bb);
+      uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
+      uint32_t tau;
+      float pdf;
+      drawn = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
+                               (uint64_t)bb + offset, (uint32_t)tt, P, ch, tau, pdf, ctx.err, j == 0 ? t.c : dummy,
+                               false, true) &&
+              tau == e.tau;
+    }
+    drawn = __shfl_sync(FULL, drawn ? 1 : 0, leader) != 0;
+    if (take && drawn) {
+#pragma unroll
+      for (int v = 0; v < K; ++v)
+        if (v == j) { L.x = ch.x[v]; L.surf = ch.surf[v]; L.prim = ch.prim[v]; L.b1 = ch.b1[v]; L.b2 = ch.b2[v]; }
+      if (j < K) {
+        tx = make_float3(c.x[(3 * j + 0) * Bz + bb], c.x[(3 * j + 1) * Bz + bb], c.x[(3 * j + 2) * Bz + bb]);
+        tsurf = c.surf[j * Bz + bb];
+      }
+      b = bb;
+      tr = tt;
+      L.e = e;
+      L.it = 0;
+      L.hv = 0;
+      L.beta = 1.0f;
+      L.need_eval = true;
+    }
+    bool any = __any_sync(FULL, b >= 0);
+    if (!any && done) break;
+    const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
+    if (b < 0) continue;
+    int st = walk_pass_g<K, G, kS>(S, L, P, j == 0 ? t.c : dummy, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp],
+                                   sCc[grp]);
+    if (st != RUNNING) {
+      if (j == 0) t.walks++;
+      if (st == ST_CONVERGED) {
+        bool same_v = true;
+        if (j < K) {
+          double dx = (double)L.x.x - (double)tx.x, dy = (double)L.x.y - (double)tx.y,
+                 dz = (double)L.x.z - (double)tx.z;
+          same_v = L.surf == tsurf && dx * dx + dy * dy + dz * dz < eps2;
+        }
+        bool same = __all_sync(gmask, same_v);
+        if (j == 0) {
+          if (same) {
+            atomicMin(nbest + b, (unsigned)tr);
+          } else if ((unsigned)tr < *((volatile unsigned*)(nbest + b))) {  // not past a known success
+            int q = atomicAdd(pr.n, 1);
+            if (q < pairs_cap(pr)) pr.buf[PAIRS_PER_CHAIN * *base + q] = make_uint2((unsigned)b, (unsigned)tr);
+          }
+        }
+      }
+      b = -1;
+    }
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
 }  // namespace kern
 }  // namespace mpg

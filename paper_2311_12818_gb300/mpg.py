@@ -8,6 +8,7 @@ no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import gc
 import dataclasses
 import os
 
@@ -344,6 +345,12 @@ class Graph:
         self.stream = torch.cuda.Stream(device=ctx.device)
 
     def __enter__(self):
+        # Objects whose destructors free device memory (contexts, scenes,
+        # graphs) must not be collected while the capture is open: cudaFree
+        # is not allowed then and would invalidate the capture.
+        gc.collect()
+        self._gc_was_enabled = gc.isenabled()
+        gc.disable()
         self._outer = torch.cuda.current_stream()
         self.stream.wait_stream(self._outer)
         self._ctx_mgr = torch.cuda.stream(self.stream)
@@ -357,12 +364,16 @@ class Graph:
                 if h:
                     lib().mpg_graph_destroy(h)
                 self._ctx_mgr.__exit__(None, None, None)
+                if self._gc_was_enabled:
+                    gc.enable()
                 _check(code)
         return self
 
     def __exit__(self, et, ev, tb):
         h = C.c_void_p()
         code = lib().mpg_graph_end(self.ctx.h, _stream(self.stream), C.byref(h))
+        if self._gc_was_enabled:
+            gc.enable()
         self._ctx_mgr.__exit__(et, ev, tb)
         self._outer.wait_stream(self.stream)
         if et is None:

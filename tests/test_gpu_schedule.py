@@ -211,3 +211,18 @@ def test_two_context_graph_matches_uncaptured(M, ctx):
     with pytest.raises(M.MpgError):  # a context cannot join a capture twice
         with M.Graph(ctx, join=[ctxs[1], ctxs[1]]):
             pass
+
+
+def test_group_walk_agrees_with_thread_walk(M, ctx):
+    """One chain per lane group (walk and parallel Bernoulli rounds) against one
+    thread per chain: the same per-vertex arithmetic, agreeing to FP32 rounding."""
+    wl = _mixed()
+    ref = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True))
+    got = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True, walk_group=1))
+    assert (ref["status"] == got["status"]).mean() >= 0.999
+    both = (ref["status"] == 1) & (got["status"] == 1)
+    assert np.abs(ref["x"][:, :, both] - got["x"][:, :, both]).max() < 1e-4 * wl.scene_scale
+    ok = (ref["T"] > 0) & (got["T"] > 0)
+    assert (ref["trials"][ok] == got["trials"][ok]).mean() >= 0.995
+    assert abs(int(got["converged_walks"][0]) - int(ref["converged_walks"][0])) <= 0.01 * ref["converged_walks"][0]
+    assert got["converged_walks"][1] == 0
