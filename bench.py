@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="batched mode without graph capture")
     ap.add_argument("--no-pipeline", action="store_true", help="one batch per graph replay (no double buffering)")
     ap.add_argument("--in-flight", type=int, default=4, help="batches advanced by one graph replay (own contexts)")
+    ap.add_argument("--no-autotune", action="store_true", help="library default schedule instead of the autotuned one")
     ap.add_argument("--part", choices=list(PARTS), help="run one secondary measurement only")
     return ap.parse_args()
 
@@ -165,6 +166,13 @@ def run_ours(args, rank, world, local):
     mpg.mpg_guide_records(ctx, sc, ch, out.contrib, out=rec)
     mpg.mpg_guide_update(ctx, guide, rec[0], rec[1], rec[2], R=B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
     ctx.sync()
+    tune_s = None
+    if args.mode == "batched" and not args.no_autotune:
+        # the batched schedule chosen once by the library's autotuner (untimed),
+        # on a guided batch of this workload
+        t0 = time.perf_counter()
+        P, _ = mpg.mpg_autotune(ctx, sc, guide, ch, P, wl.rng_seed, off + (1 << 41), repeats=2)
+        tune_s = time.perf_counter() - t0
 
     def step_on(j, i, stream=None):
         c, bf = ctxs[j], bufs[j]
@@ -357,6 +365,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD, "chains_per_step": B, "receiver_points": Q, "seeds_per_point": wl.spq,
                    "k": 2, "walk_mode": args.mode, "graph": graph is not None,
                    "batches_in_flight": per_launch,
+                   "schedule": {f: getattr(P, f) for f in mpg.SCHEDULE_FIELDS}, "autotune_s": tune_s,
                    "l2": "flushed between steps (256 MiB write)" if not args.no_flush else "not flushed",
                    "parallelism": "replicas x%d" % world,
                    "counted_walks": "walks that converged: the first walks and the trial walks of each chain's"

@@ -101,9 +101,11 @@ typedef struct mpg_params {
                            parallel round (0 = 64; 1..4096), x4 each round after;
                            issued trial-major, so trials past a chain's first
                            success are mostly skipped                          */
-  int32_t walk_group;   /* batched walk: 0 = one thread per chain; 1 = one chain per
-                           group of G lanes (G = 2, 4, 8 >= k; 128 threads per
-                           CTA), lane j owning vertex j, blocks staged in shared
+  int32_t walk_group;   /* one chain per group of G lanes (G = 2, 4, 8 >= k; 128
+                           threads per CTA) instead of one thread per chain:
+                           bit 0 in the walks (primary and synchronous trial
+                           walks), bit 1 in the parallel Bernoulli rounds.
+                           Lane j owns vertex j, the blocks are staged in shared
                            memory.  Same per-vertex arithmetic; the compiler may
                            contract products differently in the two forms, so
                            results agree to FP32 rounding, not bit for bit    */

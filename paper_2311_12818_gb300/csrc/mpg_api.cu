@@ -271,7 +271,7 @@ mpg_status check_params(const mpg_params* p) {
       p->block_threads < 0 || p->block_threads > 128 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) ||
       !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
       p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
-      p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 1)
+      p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 3)
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -397,9 +397,10 @@ int block_of(const mpg_params* p) { return p->block_threads > 0 ? p->block_threa
 
 // Persistent walk kernel of the batched mode: occupancy entry and block size
 // (the group form runs 128 threads per CTA).
-int walk_which(const mpg_params* p) { return p->walk_group ? 7 : 4; }
-int walk_block(const mpg_params* p) { return p->walk_group ? 128 : block_of(p); }
-int round_which(const mpg_params* p) { return p->walk_group ? 8 : 6; }
+int walk_which(const mpg_params* p) { return (p->walk_group & 1) ? 7 : 4; }
+int walk_block(const mpg_params* p) { return (p->walk_group & 1) ? 128 : block_of(p); }
+int round_which(const mpg_params* p) { return (p->walk_group & 2) ? 8 : 6; }
+int round_block(const mpg_params* p) { return (p->walk_group & 2) ? 128 : block_of(p); }
 
 // Synchronous Bernoulli rounds before the parallel ones (-1: none, 0: default).
 int sync_rounds_of(const mpg_params* p) { return p->trial_sync_rounds < 0 ? 0 : p->trial_sync_rounds > 0 ? p->trial_sync_rounds : 2; }
@@ -872,7 +873,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
         launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q64,
                           lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, (int)TB, pr,
-                          grid_of(ctx, P, round_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
+                          grid_of(ctx, P, round_which(P), K, round_block(P), c.B, true), round_block(P), s2);
         launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
                            lists[nxt], counts[nxt] + K, pr, dcb.stats, ctx->sms, s2);
       });
@@ -1177,10 +1178,15 @@ mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guid
     }
     s = group(c);
   }
-  if (e == cudaSuccess && !s) {  // walk form: one thread per chain or one chain per lane group
-    mpg_params P = best;
-    P.walk_group = best.walk_group ? 0 : 1;
-    s = group({P});
+  if (e == cudaSuccess && !s) {  // walk form: one thread or one lane group per chain, in walks / rounds
+    std::vector<mpg_params> c;
+    for (int wg = 0; wg < 4; ++wg) {
+      if (wg == best.walk_group) continue;
+      mpg_params P = best;
+      P.walk_group = wg;
+      c.push_back(P);
+    }
+    s = group(c);
   }
   if (e == cudaSuccess && !s) {  // refill cadence of the persistent kernels
     std::vector<mpg_params> c;

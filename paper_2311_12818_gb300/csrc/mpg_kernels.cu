@@ -56,7 +56,7 @@ void launch_bernoulli(int K, bool stats, const DScene& S, const DGuide* g, const
 
 void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                    int* queue, int grid, int block, cudaStream_t st) {
-  if (P.walk_group && K > 1) {
+  if ((P.walk_group & 1) && K > 1) {
 #define C_(KK) KLaunch<KK>::walk_g(stats, S, c, w, P, ctx, queue, grid, st)
     MPG_SWITCH(K, C_)
 #undef C_

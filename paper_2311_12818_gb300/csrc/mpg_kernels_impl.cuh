@@ -311,7 +311,7 @@ void KLaunch<K>::bern_round(bool stats, const DScene& S, const DGuide* g, const 
                             cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
   if constexpr (K > 1) {
-    if (P.walk_group) {
+    if (P.walk_group & 2) {
       constexpr int G = K <= 2 ? 2 : K <= 4 ? 4 : 8;
       kern::k_bern_round_g<K, G, true><<<grid, 128, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx, queue, list,
                                                              n_list, base, nbest, t0, TB, pr);

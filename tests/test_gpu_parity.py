@@ -256,7 +256,7 @@ def test_water_pipeline_parity(M, ctx):
 def test_mixed_lengths_plain_and_batched(M, ctx, mode):
     """mode 0: plain; 1: batched, one thread per chain; 2: batched, one chain per lane group."""
     wl = I.mixed(nx=48, ny=24, spq=4)
-    P = _params(M, wl, mode=min(mode, 1), k_uniform=0, walk_group=int(mode == 2))
+    P = _params(M, wl, mode=min(mode, 1), k_uniform=0, walk_group=3 * int(mode == 2))
     sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
     osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
     _compare_seeds(wl, gs, os_)

@@ -162,7 +162,7 @@ def test_autotune_picks_a_valid_schedule(M, ctx):
     assert tuned.refill_every in (0, 1, 2, 4, 8)
     assert tuned.trial_sync_rounds in (0, 1, 2, 3) and tuned.trial_batch in (0, 4, 16, 64, 256)
     assert tuned.fp64_k in (0, 4, 5)
-    assert tuned.walk_group in (0, 1)
+    assert tuned.walk_group in (0, 1, 2, 3)
     for f in ("tol", "max_iter", "max_halvings", "max_trials", "dedup_eps", "walk_mode", "tau_random"):
         assert getattr(tuned, f) == getattr(base, f)
     ref = _run(M, ctx, wl, base)
@@ -218,7 +218,7 @@ def test_group_walk_agrees_with_thread_walk(M, ctx):
     thread per chain: the same per-vertex arithmetic, agreeing to FP32 rounding."""
     wl = _mixed()
     ref = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True))
-    got = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True, walk_group=1))
+    got = _run(M, ctx, wl, M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True, walk_group=3))
     assert (ref["status"] == got["status"]).mean() >= 0.999
     both = (ref["status"] == 1) & (got["status"] == 1)
     assert np.abs(ref["x"][:, :, both] - got["x"][:, :, both]).max() < 1e-4 * wl.scene_scale
