@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -483,7 +483,29 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["mixed_batch"] = part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "adjoint" in parts:
         out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
+    if "mixed_group" in parts and parts == ("mixed_group",):
+        out["mixed_group"] = part_mixed_group(ctx, dev, flush, torch, stream, steps)
     return out
+
+
+def part_mixed_group(ctx, dev, flush, torch, stream, steps):
+    """The mixed-length step with one chain per lane group in walks and
+    parallel rounds (first parallel batch 4), uncaptured: for profiling the
+    group kernels (run alone with --part mixed_group)."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.mixed()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=True, walk_group=3, trial_batch=4)
+
+    def step(i):
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B)
+        mpg.mpg_manifold_walk(ctx, sc, ch, P)
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B, out=res)
+    ms = timed_loop(step, steps, 1, flush, stream, torch)
+    return {"workload": "mixed_k1to8, 4,194,304 chains, walk_group 3, trial_batch 4", "ms_per_step": ms}
 
 
 def part_plain(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
