@@ -363,14 +363,15 @@ mpg_status mpg_graph_launch(mpg_graph* graph, cudaStream_t stream);
 mpg_status mpg_graph_kernels(const mpg_graph* graph, int64_t* count);
 void mpg_graph_destroy(mpg_graph* graph);
 
-/* Autotuner of the batched schedule (block_threads, ctas_per_sm, refill_every,
- * trial_sync_rounds, trial_batch, fp64_k).  Times candidate schedules by
- * running the step seeds -> walk -> contribution on the given batch (same
- * rng_seed and rng_offset for every candidate, so each one does identical
- * work; the chain arrays are overwritten) and returns in *out the input
- * parameters with the fastest schedule, and in *best_ms its time.  Coordinate
- * descent over one group at a time (tile shape, refill cadence, Bernoulli
- * rounds, FP64 split); each candidate is timed `repeats` times (minimum).
+/* Autotuner of the batched schedule (block_threads, ctas_per_sm, walk_group,
+ * refill_every, trial_sync_rounds, trial_batch, fp64_k).  Times candidate
+ * schedules by running the step seeds -> walk -> contribution on the given
+ * batch (same rng_seed and rng_offset for every candidate, so each one does
+ * the same work; the chain arrays are overwritten) and returns in *out the
+ * input parameters with the fastest schedule, and in *best_ms its time.
+ * Coordinate descent over one group at a time (tile shape, walk form, refill
+ * cadence, Bernoulli rounds, FP64 split); each candidate is timed `repeats`
+ * times (minimum).
  * The outputs of the step go to scratch the call allocates and frees.
  * Synchronous; walk_mode must be MPG_WALK_BATCHED. */
 mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
