@@ -826,6 +826,83 @@ static double hist_pdf(const orc_guide& g, const GuideCDF& cdf, int cell, const 
   return ((double)cnt / (double)total) / (dphi * dcos);
 }
 
+// ---------------------------------------------------------------------------
+// vMF mixture guide (Sec. 5.5).  The samples of the last pass that share the
+// receiver cell stand for the neighbourhood S(x_D, x_L); grouped by chain
+// length n and types tau they give
+//   P_e(n)        = W(n) / W              (weights summed over the cell),
+//   P_e(tau | n)  = W(n, tau) / W(n),
+//   p_e(w | tau)  = sum_i (w_i / W(n, tau)) v(w; mu_i, kappa_i)   (Eq. vMF)
+// with mu_i the sample's direction w_D and kappa_i = sigma_i^-2, sigma_i the
+// angle between w_D and the nearest other direction of its group.  Weights
+// are the Eq. eq_weight weights quantised as for the histograms, so the
+// discrete choices are exact integer decisions.
+// ---------------------------------------------------------------------------
+static const double VMF_SIGMA_MIN = 1e-6;  // identical directions
+
+// Uniform in (0,1]: the draw of u01 shifted up by one step.
+static inline double u01c(uint32_t r) { return (double)((r >> 8) + 1u) * (1.0 / 16777216.0); }
+
+// v(w; mu, kappa) = kappa / (4 pi sinh kappa) e^{kappa mu.w}, written as
+// kappa / (2 pi (1 - e^{-2 kappa})) e^{-kappa (1 - mu.w)} with
+// 1 - mu.w = |w - mu|^2 / 2 for unit vectors.
+static double vmf_pdf(const V3d& mu, double kappa, const V3d& w) {
+  V3d d = w - mu;
+  double h = 0.5 * dot(d, d);
+  return kappa / (2.0 * PI * -std::expm1(-2.0 * kappa)) * std::exp(-kappa * h);
+}
+
+// t = 1 - mu.w has density kappa e^{-kappa t} / (1 - e^{-2 kappa}) on [0, 2]
+// and the azimuth is uniform; t by inverting its distribution function with
+// u1 in (0, 1], the azimuth 2 pi u2 in the Duff et al. frame of mu.
+static V3d vmf_sample(const V3d& mu, double kappa, double u1, double u2) {
+  double t = -std::log(u1 + (1.0 - u1) * std::exp(-2.0 * kappa)) / kappa;
+  t = std::min(std::max(t, 0.0), 2.0);
+  double ct = 1.0 - t, st = std::sqrt(std::max(0.0, t * (2.0 - t)));
+  V3d e1, e2;
+  onb(mu, e1, e2);
+  double ph = 2.0 * PI * u2;
+  return mu * ct + (e1 * std::cos(ph) + e2 * std::sin(ph)) * st;
+}
+
+// Lobes of `cell` whose key lies in [klo, khi): index range [a, b), the
+// cell-local prefix sum before a, and the range's total weight.
+struct LobeRange {
+  uint32_t a = 0, b = 0;
+  uint64_t base = 0, total = 0;
+};
+static LobeRange lobe_range(const orc_vmf& v, uint32_t cell, uint32_t klo, uint32_t khi) {
+  LobeRange r;
+  uint32_t c0 = v.cell_start[cell], c1 = v.cell_start[cell + 1];
+  r.a = c1;
+  r.b = c1;
+  for (uint32_t i = c0; i < c1; ++i)
+    if (v.key[i] >= klo) { r.a = i; break; }
+  for (uint32_t i = r.a; i < c1; ++i)
+    if (v.key[i] >= khi) { r.b = i; break; }
+  r.base = r.a > c0 ? v.prefix[r.a - 1] : 0;
+  r.total = r.b > r.a ? v.prefix[r.b - 1] - r.base : 0;
+  return r;
+}
+
+// Quantised weight of lobe i (difference of the cell-local prefix sums).
+static uint64_t lobe_weight(const orc_vmf& v, uint32_t cell, uint32_t i) {
+  return v.prefix[i] - (i > v.cell_start[cell] ? v.prefix[i - 1] : 0);
+}
+
+// First lobe of [a, b) whose cell-local prefix sum exceeds base + target.
+static uint32_t lobe_search(const orc_vmf& v, const LobeRange& r, uint64_t target) {
+  for (uint32_t i = r.a; i < r.b; ++i)
+    if (v.prefix[i] - r.base > target) return i;
+  return r.b - 1;
+}
+
+// floor(r * total / 2^32) in exact integer arithmetic.
+static uint64_t scaled_target(uint32_t r, uint64_t total) {
+  unsigned __int128 prod = (unsigned __int128)r * (unsigned __int128)total;
+  return (uint64_t)(prod >> 32);
+}
+
 struct SeedDraw {
   bool valid = false;
   uint8_t tau = 0;
@@ -845,14 +922,34 @@ static SeedDraw sample_seed(const Scene& S, const orc_guide* g, const GuideCDF* 
   philox4x32_10(c0, key, r0);
   philox4x32_10(c1, key, r1);
   uint8_t tau = tau_random ? (uint8_t)(r1[1] & ((1u << k) - 1u)) : tau_in;
-  sd.tau = tau;
   uint64_t total = 0;
-  bool use_guide = g && g->counts && cdf;
-  if (use_guide) total = cdf->cdf[(size_t)cell * cdf->bins + cdf->bins - 1];
-  use_guide = use_guide && total > 0;
+  const orc_vmf* vm = g ? g->vmf : nullptr;
+  LobeRange lr;
+  bool use_guide = false;
+  if (vm) {
+    // the guided component draws (w, tau) given n, or w given n and tau when
+    // the types are fixed
+    uint32_t klo = ((uint32_t)k << 8) | (tau_random ? 0u : tau_in);
+    uint32_t khi = tau_random ? ((uint32_t)(k + 1) << 8) : klo + 1;
+    lr = lobe_range(*vm, cell, klo, khi);
+    total = lr.total;
+    use_guide = total > 0;
+  } else {
+    use_guide = g && g->counts && cdf;
+    if (use_guide) total = cdf->cdf[(size_t)cell * cdf->bins + cdf->bins - 1];
+    use_guide = use_guide && total > 0;
+  }
   bool pick_p0 = !use_guide || u01(r0[0]) < prm.alpha;
   V3d w;
-  if (pick_p0) {
+  if (!pick_p0 && vm) {
+    uint32_t i = lobe_search(*vm, lr, scaled_target(r0[1], total));
+    tau = (uint8_t)(vm->key[i] & 255u);
+    const double* L = vm->lobe + 4 * (size_t)i;
+    w = vmf_sample(V3d(L[0], L[1], L[2]), L[3], u01c(r0[2]), u01(r0[3]));
+  }
+  sd.tau = tau;
+  if (!pick_p0 && vm) {
+  } else if (pick_p0) {
     if (S.tg.empty()) return sd;
     int nt = (int)S.tg.size();
     int ti = std::min((int)(u01(r1[0]) * nt), nt - 1);
@@ -892,7 +989,22 @@ static SeedDraw sample_seed(const Scene& S, const orc_guide* g, const GuideCDF* 
   }
   if (dot(w, nD) <= 0.0) return sd;
   double p0 = p0_pdf(S, xD, w);
-  sd.pdf = use_guide ? prm.alpha * p0 + (1.0 - prm.alpha) * hist_pdf(*g, *cdf, cell, w) : p0;
+  if (vm) {
+    // joint density of (w, tau) given n: p_0 draws the types uniformly
+    if (tau_random) p0 *= std::ldexp(1.0, -k);
+    double pe = 0.0;
+    if (use_guide) {
+      uint32_t kt = ((uint32_t)k << 8) | tau;
+      for (uint32_t i = lr.a; i < lr.b; ++i) {
+        if (vm->key[i] != kt) continue;
+        const double* L = vm->lobe + 4 * (size_t)i;
+        pe += (double)lobe_weight(*vm, cell, i) / (double)total * vmf_pdf(V3d(L[0], L[1], L[2]), L[3], w);
+      }
+    }
+    sd.pdf = use_guide ? prm.alpha * p0 + (1.0 - prm.alpha) * pe : p0;
+  } else {
+    sd.pdf = use_guide ? prm.alpha * p0 + (1.0 - prm.alpha) * hist_pdf(*g, *cdf, cell, w) : p0;
+  }
   sd.ch.k = k;
   sd.ch.tau = tau;
   sd.ch.v[0].p = xD;
@@ -1433,8 +1545,11 @@ int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const d
   const Scene& S = *(Scene*)scene;
   orc_params P = default_check(prm);
   GuideCDF cdf;
-  bool g_ok = guide && guide->counts;
-  if (g_ok) guide_cdf(*guide, cdf);
+  bool g_ok = guide && (guide->counts || guide->vmf);
+  if (g_ok && !guide->vmf) guide_cdf(*guide, cdf);
+  if (g_ok && guide->vmf && cell)
+    for (int q = 0; q < Q; ++q)
+      if ((int)cell[q] >= guide->vmf->n_cells) return -3;
   int B = Q * spq;
   for (int b = 0; b < B; ++b)
     if (k[b] < 1 || k[b] > MAXK) return -2;
@@ -1512,8 +1627,11 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
   const Scene& S = *(Scene*)scene;
   orc_params P = *prm;
   GuideCDF cdf;
-  bool g_ok = guide && guide->counts;
-  if (g_ok) guide_cdf(*guide, cdf);
+  bool g_ok = guide && (guide->counts || guide->vmf);
+  if (g_ok && !guide->vmf) guide_cdf(*guide, cdf);
+  if (g_ok && guide->vmf && cell)
+    for (int q = 0; q < Q; ++q)
+      if ((int)cell[q] >= guide->vmf->n_cells) return -3;
   int B = Q * spq;
   parallel_for(B, n_threads, [&](int b) {
     N[b] = 0;
@@ -1541,6 +1659,113 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
     capped[b] = 1;
   });
   return 0;
+}
+
+int32_t orc_vmf_build(int32_t n_cells, int32_t R, const uint32_t* cell, const float* omega,
+                      const float* w, const uint8_t* k, const uint8_t* tau, int32_t weight_shift,
+                      uint32_t* cell_start, uint32_t* key, double* lobe, uint64_t* prefix) {
+  if (n_cells <= 0 || R < 0 || !cell_start) return -1;
+  for (int r = 0; r < R; ++r) {
+    if ((int64_t)cell[r] >= n_cells || k[r] < 1 || k[r] > MAXK || tau[r] >= (1u << k[r])) return -2;
+  }
+  // order: cell, then key (n, tau), then record index
+  std::vector<int> ord(R);
+  for (int r = 0; r < R; ++r) ord[r] = r;
+  auto rkey = [&](int r) { return ((uint32_t)k[r] << 8) | tau[r]; };
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    if (cell[a] != cell[b]) return cell[a] < cell[b];
+    return rkey(a) < rkey(b);
+  });
+  for (int c = 0; c <= n_cells; ++c) cell_start[c] = 0;
+  for (int r = 0; r < R; ++r) cell_start[cell[r] + 1]++;
+  for (int c = 0; c < n_cells; ++c) cell_start[c + 1] += cell_start[c];
+  for (int i = 0; i < R; ++i) {
+    int r = ord[i];
+    key[i] = rkey(r);
+    for (int j = 0; j < 3; ++j) lobe[4 * (size_t)i + j] = (double)omega[3 * (size_t)r + j];
+  }
+  // kappa_i = sigma_i^-2, sigma_i the angle to the nearest other direction
+  // of the same group (same cell and key; groups are contiguous)
+  for (int i = 0; i < R; ++i) {
+    uint32_t ci = cell[ord[i]];
+    int g0 = i, g1 = i + 1;
+    while (g0 > 0 && cell[ord[g0 - 1]] == ci && key[g0 - 1] == key[i]) --g0;
+    while (g1 < R && cell[ord[g1]] == ci && key[g1] == key[i]) ++g1;
+    V3d mi(lobe[4 * (size_t)i], lobe[4 * (size_t)i + 1], lobe[4 * (size_t)i + 2]);
+    double sigma = PI;
+    if (g1 - g0 > 1) {
+      double best = std::numeric_limits<double>::infinity();
+      for (int j = g0; j < g1; ++j) {
+        if (j == i) continue;
+        V3d d = mi - V3d(lobe[4 * (size_t)j], lobe[4 * (size_t)j + 1], lobe[4 * (size_t)j + 2]);
+        best = std::min(best, dot(d, d));
+      }
+      sigma = 2.0 * std::asin(std::min(1.0, 0.5 * std::sqrt(best)));  // chord -> angle
+    }
+    sigma = std::max(sigma, VMF_SIGMA_MIN);
+    lobe[4 * (size_t)i + 3] = 1.0 / (sigma * sigma);
+  }
+  // prefix sums of the quantised weights within each cell
+  for (int c = 0; c < n_cells; ++c) {
+    uint64_t acc = 0;
+    for (uint32_t i = cell_start[c]; i < cell_start[c + 1]; ++i) {
+      acc += quantise_weight(w[ord[i]], weight_shift);
+      prefix[i] = acc;
+    }
+  }
+  return 0;
+}
+
+int32_t orc_sample_lengths(const orc_guide* guide, int32_t Q, const uint32_t* cell, int32_t spq,
+                           const uint32_t* p0w, uint64_t rng_seed, uint64_t rng_offset,
+                           const orc_params* prm, uint8_t* k_out, double* pn_out) {
+  if (Q < 0 || spq <= 0 || !p0w || !prm) return -1;
+  uint64_t W0 = 0;
+  for (int n = 1; n <= MAXK; ++n) W0 += p0w[n - 1];
+  if (W0 == 0) return -2;
+  const orc_vmf* vm = guide ? guide->vmf : nullptr;
+  uint32_t key[2] = {(uint32_t)rng_seed, (uint32_t)(rng_seed >> 32)};
+  for (int q = 0; q < Q; ++q) {
+    uint32_t c = cell ? cell[q] : 0u;
+    if (vm && (int)c >= vm->n_cells) return -3;
+    // W(n) of the cell, n = 1..8
+    uint64_t We[MAXK + 1] = {0}, Wc = 0;
+    if (vm) {
+      for (int n = 1; n <= MAXK; ++n) {
+        We[n] = lobe_range(*vm, c, (uint32_t)n << 8, (uint32_t)(n + 1) << 8).total;
+        Wc += We[n];
+      }
+    }
+    for (int s = 0; s < spq; ++s) {
+      size_t b = (size_t)q * spq + s;
+      uint64_t idx = (uint64_t)b + rng_offset;
+      uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), 0u, 2u}, r[4];
+      philox4x32_10(ctr, key, r);
+      bool pick_p0 = Wc == 0 || u01(r[0]) < prm->alpha;
+      const uint64_t* Wt = pick_p0 ? nullptr : We;
+      uint64_t total = pick_p0 ? W0 : Wc;
+      uint64_t target = scaled_target(r[1], total);
+      int n = 1;
+      uint64_t acc = 0;
+      for (; n <= MAXK; ++n) {
+        acc += Wt ? Wt[n] : p0w[n - 1];
+        if (acc > target) break;
+      }
+      n = std::min(n, MAXK);
+      double P0 = (double)p0w[n - 1] / (double)W0;
+      k_out[b] = (uint8_t)n;
+      pn_out[b] = Wc == 0 ? P0 : prm->alpha * P0 + (1.0 - prm->alpha) * (double)We[n] / (double)Wc;
+    }
+  }
+  return 0;
+}
+
+double orc_vmf_pdf(const double* mu, double kappa, const double* w) {
+  return vmf_pdf(load3(mu), kappa, load3(w));
+}
+
+void orc_vmf_sample(const double* mu, double kappa, double u1, double u2, double* w) {
+  store3(w, vmf_sample(load3(mu), kappa, u1, u2));
 }
 
 int32_t orc_guide_bin(const orc_guide* guide, int32_t R, const float* omega, int32_t* bin) {

@@ -11,6 +11,7 @@
  *   contribution T = kappa * G * L_o                                  (Eq. ThroughputEval)
  *   reciprocal probability by Bernoulli trials, n reused             (Sec. 5.8, reciprocal probability estimation)
  *   guide histogram update with w = T <1/P>                          (Eq. eq_weight)
+ *   vMF mixture guide, P_e(n), P_e(tau | n), one-sample MIS          (Sec. 5.5, Eq. vMF)
  *
  * Arrays are caller-owned, array-of-structures, float64 unless stated:
  *   chain vertex positions x[B][8][3], surface ids surf[B][8], primitive ids
@@ -38,12 +39,24 @@ typedef struct orc_params {
   double alpha;        /* defensive mixture weight of p_0 */
 } orc_params;
 
+/* vMF mixture guide (Sec. 5.5): one lobe per sample of the last pass.  The
+ * lobes of a cell are contiguous, ordered by key = (n << 8) | tau and, within
+ * a key, in record order. */
+typedef struct orc_vmf {
+  int32_t n_cells, n_lobes;
+  const uint32_t* cell_start; /* [n_cells+1] first lobe of each cell */
+  const uint32_t* key;        /* [n_lobes] (n << 8) | tau */
+  const double* lobe;         /* [n_lobes][4] mu_x, mu_y, mu_z, kappa */
+  const uint64_t* prefix;     /* [n_lobes] inclusive prefix sums of the quantised weights within the cell */
+} orc_vmf;
+
 typedef struct orc_guide {
   const uint64_t* counts; /* [n_cells][n_theta*n_phi]; NULL => p_0 only */
   int32_t n_cells, n_theta, n_phi;
   const float* cos_theta; /* [n_theta+1] bin edges in cos(theta), decreasing */
   const float* phi_cos;   /* [n_phi+1] cos of phi edges */
   const float* phi_sin;   /* [n_phi+1] sin of phi edges */
+  const orc_vmf* vmf;     /* non-NULL => the vMF mixture replaces the histograms */
 } orc_guide;
 
 void* orc_scene_create(const double* surfaces, int32_t n_surf, const double* hf_desc,
@@ -95,6 +108,27 @@ int32_t orc_guide_bin(const orc_guide* guide, int32_t R, const float* omega, int
 int32_t orc_guide_update(const orc_guide* guide, uint64_t* counts, int32_t R,
                          const uint32_t* cell, const float* omega, const float* w,
                          int32_t weight_shift);
+
+/* vMF mixture from guide records (cell, w_D [R][3], w, n, tau): lobes sorted
+ * by (cell, n, tau) and record order, mu = w_D, kappa = sigma^-2 with sigma
+ * the angle to the nearest other direction of the same cell, n and tau (pi
+ * when there is none; at least 1e-6), prefix sums of q(w) within each cell.
+ * Outputs are [n_cells+1], [R], [R][4] and [R]. */
+int32_t orc_vmf_build(int32_t n_cells, int32_t R, const uint32_t* cell, const float* omega,
+                      const float* w, const uint8_t* k, const uint8_t* tau, int32_t weight_shift,
+                      uint32_t* cell_start, uint32_t* key, double* lobe, uint64_t* prefix);
+
+/* Chain lengths from P(n) = alpha P_0(n) + (1 - alpha) P_e(n | cell) (Sec. 5.5,
+ * defensive one-sample MIS; P_e from the vMF guide's weights, absent => P_0
+ * only): k_out[b] and pn_out[b] = P(k_out[b]).  p0w[n-1] are integer weights
+ * of P_0(n), n = 1..8. */
+int32_t orc_sample_lengths(const orc_guide* guide, int32_t Q, const uint32_t* cell, int32_t spq,
+                           const uint32_t* p0w, uint64_t rng_seed, uint64_t rng_offset,
+                           const orc_params* prm, uint8_t* k_out, double* pn_out);
+
+/* vMF lobe density (Eq. vMF) and inverse-CDF draw, exposed for the tests. */
+double orc_vmf_pdf(const double* mu, double kappa, const double* w);
+void orc_vmf_sample(const double* mu, double kappa, double u1, double u2, double* w);
 
 /* Constraint values of a given chain (tests): C[b][2k] and max |C|. */
 int32_t orc_constraint(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,

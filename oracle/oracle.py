@@ -29,10 +29,15 @@ class orc_params(C.Structure):
                 ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_double)]
 
 
+class orc_vmf(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("n_lobes", C.c_int32), ("cell_start", C.c_void_p),
+                ("key", C.c_void_p), ("lobe", C.c_void_p), ("prefix", C.c_void_p)]
+
+
 class orc_guide(C.Structure):
     _fields_ = [("counts", C.c_void_p), ("n_cells", C.c_int32), ("n_theta", C.c_int32),
                 ("n_phi", C.c_int32), ("cos_theta", C.c_void_p), ("phi_cos", C.c_void_p),
-                ("phi_sin", C.c_void_p)]
+                ("phi_sin", C.c_void_p), ("vmf", C.c_void_p)]
 
 
 _lib = None
@@ -71,11 +76,19 @@ def lib():
         L.orc_adjoint.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p, _f64p, _i32p,
                                   _i32p, _f64p, _f64p, _f64p, _f64p, C.c_int32]
         L.orc_adjoint.restype = C.c_int32
+        L.orc_vmf_build.argtypes = [C.c_int32, C.c_int32, _u32p, _f32p, _f32p, _u8p, _u8p, C.c_int32, _u32p,
+                                    _u32p, _f64p, _u64p]
+        L.orc_sample_lengths.argtypes = [C.c_void_p, C.c_int32, _u32p, C.c_int32, _u32p, C.c_uint64, C.c_uint64,
+                                         C.POINTER(orc_params), _u8p, _f64p]
+        L.orc_vmf_pdf.argtypes = [_f64p, C.c_double, _f64p]
+        L.orc_vmf_pdf.restype = C.c_double
+        L.orc_vmf_sample.argtypes = [_f64p, C.c_double, C.c_double, C.c_double, _f64p]
+        L.orc_vmf_sample.restype = None
         L.orc_philox.argtypes = [_u32p, _u32p, _u32p]
         L.orc_philox.restype = None
         for name in ("orc_intersect", "orc_sample_seeds", "orc_walk", "orc_contribution",
                      "orc_bernoulli", "orc_guide_bin", "orc_guide_update", "orc_constraint",
-                     "orc_shoot"):
+                     "orc_shoot", "orc_vmf_build", "orc_sample_lengths"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -128,7 +141,7 @@ class Guide:
     def struct(self, with_counts=True):
         return orc_guide(self.counts.ctypes.data if with_counts else None, self.n_cells,
                          self.n_theta, self.n_phi, self.ct.ctypes.data, self.pc.ctypes.data,
-                         self.ps.ctypes.data)
+                         self.ps.ctypes.data, None)
 
     def bins(self, omega):
         om = _c(omega, np.float32).reshape(-1, 3)
@@ -143,6 +156,59 @@ class Guide:
         rc = lib().orc_guide_update(C.byref(g), self.counts, om.shape[0], _c(cell, np.uint32), om,
                                     _c(w, np.float32), shift)
         assert rc == 0, rc
+
+
+class VmfGuide:
+    """vMF mixture guide (Sec. 5.5) of the oracle: one lobe per record, lobes of
+    a cell contiguous and ordered by (n, tau) and record order.  Arrays:
+    cell_start[n_cells+1], key[L] = (n << 8) | tau, lobe[L, 4] = (mu, kappa),
+    prefix[L] = inclusive prefix sums of the quantised weights within the cell."""
+
+    def __init__(self, n_cells):
+        self.n_cells = n_cells
+        self.build(np.zeros(0, np.uint32), np.zeros((0, 3), np.float32), np.zeros(0, np.float32),
+                   np.zeros(0, np.uint8), np.zeros(0, np.uint8), 16)
+
+    def build(self, cell, omega, w, k, tau, shift):
+        om = _c(omega, np.float32).reshape(-1, 3)
+        R = om.shape[0]
+        self.cell_start = np.zeros(self.n_cells + 1, np.uint32)
+        self.key = np.zeros(max(R, 1), np.uint32)
+        self.lobe = np.zeros((max(R, 1), 4), np.float64)
+        self.prefix = np.zeros(max(R, 1), np.uint64)
+        rc = lib().orc_vmf_build(self.n_cells, R, _c(cell, np.uint32), om, _c(w, np.float32), _c(k, np.uint8),
+                                 _c(tau, np.uint8), shift, self.cell_start, self.key, self.lobe, self.prefix)
+        assert rc == 0, rc
+        self.n_lobes = R
+        self._v = orc_vmf(self.n_cells, R, self.cell_start.ctypes.data, self.key.ctypes.data,
+                          self.lobe.ctypes.data, self.prefix.ctypes.data)
+        return self
+
+    def struct(self):
+        return orc_guide(None, self.n_cells, 0, 0, None, None, None, C.addressof(self._v))
+
+
+def sample_lengths(wl, guide, p0w, rng_offset=0):
+    """Chain lengths and P(n) from the defensive mixture of P_0 (integer weights
+    p0w[n-1]) and the vMF guide's P_e(n | cell) (Sec. 5.5)."""
+    k = np.zeros(wl.B, np.uint8)
+    pn = np.zeros(wl.B)
+    g = guide.struct() if guide is not None else None
+    P = params(wl.params)
+    rc = lib().orc_sample_lengths(C.byref(g) if g is not None else None, wl.Q, _c(wl.cell, np.uint32), wl.spq,
+                                  _c(p0w, np.uint32), wl.rng_seed, rng_offset, C.byref(P), k, pn)
+    assert rc == 0, rc
+    return k, pn
+
+
+def vmf_pdf(mu, kappa, w):
+    return lib().orc_vmf_pdf(_c(mu, np.float64), float(kappa), _c(w, np.float64))
+
+
+def vmf_sample(mu, kappa, u1, u2):
+    out = np.zeros(3)
+    lib().orc_vmf_sample(_c(mu, np.float64), float(kappa), float(u1), float(u2), out)
+    return out
 
 
 def intersect(scene, o, d, tmin=1e-4, tmax=np.inf, brute=False):
@@ -269,14 +335,18 @@ def irradiance(wl, T, N, admissible):
     return c.reshape(wl.Q, wl.spq).sum(axis=1) / wl.spq
 
 
-def records(wl, chains, T, N, admissible):
-    """Guide-update records of the admissible chains: (cell, w_D as FP32, w = T <1/P> as FP32)."""
+def records(wl, chains, T, N, admissible, with_types=False):
+    """Guide-update records of the admissible chains in chain order: (cell, w_D
+    as FP32, w = T <1/P> as FP32), and with_types: also (n, tau)."""
     idx = np.nonzero(admissible)[0]
     q = idx // wl.spq
     x1 = chains["x"][idx, 0, :]
     d = x1 - wl.xD[q]
     om = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
     w = (T[idx] * N[idx].astype(np.float64) / wl.pn[idx]).astype(np.float32)
+    if with_types:
+        return (wl.cell[q].astype(np.uint32), om, w, wl.k[idx].astype(np.uint8),
+                chains["tau"][idx].astype(np.uint8))
     return wl.cell[q].astype(np.uint32), om, w
 
 

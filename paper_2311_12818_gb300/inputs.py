@@ -246,6 +246,9 @@ def water(n: int = 512, spq: int = 4, grid: int = 128, seed: int = 0x4D50470003)
 
 GEOMETRIC_K_PMF = np.array([0.35 * 0.65 ** (i - 1) for i in range(1, MAXK + 1)])
 GEOMETRIC_K_PMF = GEOMETRIC_K_PMF / GEOMETRIC_K_PMF.sum()
+# The same law as integer weights (sampled lengths draw n by exact integer
+# inverse CDF): round(pmf * 2^20).
+GEOMETRIC_K_WEIGHTS = np.round(GEOMETRIC_K_PMF * (1 << 20)).astype(np.uint32)
 
 
 def mixed(nx: int = 1024, ny: int = 512, spq: int = 8, seed: int = 0x4D50470004) -> Workload:
