@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -463,7 +463,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     - k6: the guide-histogram update of one glass-sphere pass (GB/s);
     - mixed: the mixed-length batch (k = 1..8, 2^22 chains) plain (one launch
       per k), batched (one graph replay) and batched with the autotuned schedule;
-    - adjoint: the adjoint of the water irradiance with respect to the heights."""
+    - adjoint: the adjoint of the water irradiance with respect to the heights;
+    - vmf: the vMF mixture guide with sampled chain lengths on the mixed batch."""
     import numpy as np
     from paper_2311_12818_gb300 import inputs as I
     from paper_2311_12818_gb300 import mpg
@@ -483,6 +484,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["mixed_batch"] = part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "adjoint" in parts:
         out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
+    if "vmf" in parts:
+        out["vmf_guide"] = part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "mixed_group" in parts and parts == ("mixed_group",):
         out["mixed_group"] = part_mixed_group(ctx, dev, flush, torch, stream, steps)
     return out
@@ -676,6 +679,85 @@ def part_adjoint(ctx, dev, flush, torch, stream, steps):
     ms = timed_loop(adj, steps, 2, flush, stream, torch)
     return {"workload": "water_heightfield: 128x128 heights, 512x512 points x 4 = 1,048,576 chains",
             "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3)}
+
+
+def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
+    """The paper's guiding distribution (Sec. 5.5) on the mixed-length batch.
+    A p_0 training pass gives the records (cell, w_D, w, n, tau) of its
+    admissible chains; the vMF lobes are built from them (timed); the guided
+    step draws n from alpha P_0 + (1 - alpha) P_e(n | cell) and (w_D, tau)
+    from alpha p_0 + (1 - alpha) p_e, walks and forms the contributions with
+    Bernoulli trials from the same mixture.  Both steps replay captured
+    graphs with the library's default schedule."""
+    import numpy as np
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.mixed()
+    sc = mpg.Scene(ctx, wl)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=True, k_uniform=0)
+    ch0, chv = mpg.Chains(wl, device=dev), mpg.Chains(wl, device=dev)
+    res0 = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    resv = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    p0w = I.GEOMETRIC_K_WEIGHTS
+    # training pass with p_0 and its records
+    mpg.mpg_sample_seeds(ctx, sc, None, ch0, P, wl.rng_seed, 1 << 40)
+    mpg.mpg_manifold_walk(ctx, sc, ch0, P)
+    mpg.mpg_chain_contribution(ctx, sc, None, ch0, P, wl.rng_seed, 1 << 40, out=res0)
+    rec = mpg.mpg_guide_records(ctx, sc, ch0, res0.contrib, with_types=True)
+    g = mpg.VmfGuide(wl.n_cells, wl.B)
+
+    def build(i):
+        mpg.mpg_vmf_build(ctx, g, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[5],
+                          weight_shift=wl.params.weight_shift)
+    build(0)
+    ctx.sync()
+    R = int(rec[5][0].item())
+    L = g.n_lobes
+    keys = (rec[0][:R].long().cpu().numpy() << 11) | ((rec[3][:R].long().cpu().numpy() - 1) << 8) | \
+        rec[4][:R].long().cpu().numpy()
+    sizes = np.unique(keys, return_counts=True)[1].astype(np.float64)
+    pairs = float((sizes * (sizes - 1)).sum())
+    b_ms = timed_loop(build, steps, 2, flush, stream, torch)
+    out = {"workload": "mixed_k1to8, 4,194,304 chains; vMF lobes from the %d records of a p_0 training pass" % R,
+           "lobes": L, "groups": int(sizes.size), "largest_group": int(sizes.max()),
+           "nearest_neighbour_pair_tests": pairs,
+           "build": {"ms": b_ms, "lobes_per_s": L / (b_ms * 1e-3), "pair_tests_per_s": pairs / (b_ms * 1e-3),
+                     "launches": 1 + 3 * 3 + 5}}
+
+    def measure(guided):
+        ch, res = (chv, resv) if guided else (ch0, res0)
+
+        def step(o, s=None):
+            gg = g if guided else None
+            if guided:
+                mpg.mpg_sample_lengths(ctx, g, ch, p0w, P, wl.rng_seed, o, out=(ch.k, ch.pn), stream=s)
+            mpg.mpg_sample_seeds(ctx, sc, gg, ch, P, wl.rng_seed, o, stream=s)
+            mpg.mpg_manifold_walk(ctx, sc, ch, P, stream=s)
+            mpg.mpg_chain_contribution(ctx, sc, gg, ch, P, wl.rng_seed, o, out=res, stream=s)
+        step(0)
+        torch.cuda.synchronize()
+        gr = mpg.Graph(ctx, rng_advance=wl.B)
+        with gr:
+            step(3 << 32)
+        ctx.reset_stats()
+        ms = timed_loop(lambda i: gr.launch(), steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        per = steps + 2
+        fl = algorithmic_flops(st, F) / per
+        c = res.contrib
+        adm = int((c > 0).sum().item())
+        return {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+                "walks_per_s": st["walks"] / per / (ms * 1e-3), "fp32_tflops": fl / (ms * 1e-3) / 1e12,
+                "fp32_frac": fl / (ms * 1e-3) / peak_fp32, "trials_per_step": st["trials"] / per,
+                "admissible_per_step": adm, "capped_per_step": int(res.capped.sum().item()),
+                "mean_E": float(res.E.double().mean().item()),
+                "mean_E_std_err": float(res.E.double().std().item() / np.sqrt(wl.Q)),
+                "graph_kernels": gr.kernels()}
+    out["p0_step"] = measure(False)
+    out["vmf_step"] = measure(True)
+    out["admissible_chains_per_ms"] = {k: out[k]["admissible_per_step"] / out[k]["ms_per_step"]
+                                       for k in ("p0_step", "vmf_step")}
+    return out
 
 
 def run_part(args):

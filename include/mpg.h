@@ -130,8 +130,23 @@ typedef struct mpg_chains {
   uint8_t* iters;       /* [B] Newton steps taken                                  */
 } mpg_chains;
 
-/* Guide: per cell a (theta, phi) histogram over world directions (theta from
- * +z uniform over [0, pi], phi uniform over [0, 2 pi)); caller-owned. */
+/* Guide kinds (mpg_guide.kind). */
+#define MPG_GUIDE_HISTOGRAM 0
+#define MPG_GUIDE_VMF 1
+
+/* Build scratch of a vMF guide of `capacity` lobes, in uint32 words. */
+#define MPG_VMF_SCRATCH_WORDS(capacity) (4 * (size_t)(capacity) + 256 * (((size_t)(capacity) + 1023) / 1024) + 64)
+
+/* Guide, caller-owned, one of two kinds.
+ * MPG_GUIDE_HISTOGRAM (0): per cell a (theta, phi) histogram over world
+ *   directions (theta from +z uniform over [0, pi], phi uniform over
+ *   [0, 2 pi)).  The vMF fields are unused (zero).
+ * MPG_GUIDE_VMF (1): the vMF mixture of Sec. 5.5 (Eq. vMF) built by
+ *   mpg_vmf_build from the records of the last pass: one lobe per record, the
+ *   lobes of a cell contiguous and ordered by key = (n << 8) | tau and, within
+ *   a key, by record order.  The receiver cell stands for the spatial
+ *   neighbourhood S(x_D, x_L).  Uses n_cells and the vMF fields; the histogram
+ *   pointers are unused. */
 typedef struct mpg_guide {
   int32_t n_cells, n_theta, n_phi;
   uint64_t* counts;        /* [n_cells][n_theta*n_phi] quantised weight sums      */
@@ -139,6 +154,14 @@ typedef struct mpg_guide {
   const float* cos_theta;  /* [n_theta+1] FP32 edges cos(j pi/n_theta)            */
   const float* phi_cos;    /* [n_phi+1] FP32 cos(2 pi j/n_phi)                    */
   const float* phi_sin;    /* [n_phi+1] FP32 sin(2 pi j/n_phi)                    */
+  int32_t kind;            /* MPG_GUIDE_HISTOGRAM or MPG_GUIDE_VMF                 */
+  int32_t capacity;        /* vMF: lobes the arrays hold                           */
+  uint32_t* cell_start;    /* vMF: [n_cells+1] first lobe of each cell             */
+  uint32_t* lobe_key;      /* vMF: [capacity] (n << 8) | tau                       */
+  float* lobe;             /* vMF: [capacity][4] mu_x, mu_y, mu_z, kappa           */
+  uint64_t* lobe_prefix;   /* vMF: [capacity] inclusive prefix sums of the
+                              quantised weights within the cell                    */
+  uint32_t* scratch;       /* vMF: MPG_VMF_SCRATCH_WORDS(capacity) build scratch   */
 } mpg_guide;
 
 typedef struct mpg_ctx mpg_ctx;
@@ -221,10 +244,18 @@ mpg_status mpg_scene_info(const mpg_scene* scene, int32_t h, int32_t* n_nodes, i
  * guided sampling with the one-sample defensive mixture alpha p_0 + (1-alpha) p_e).
  * For each chain: draws from Philox4x32-10 keyed by rng_seed with counter
  * (b + rng_offset, trial 0, block), picks p_0 (a seed target, uniform visible cap
- * or rectangle) or the cell's histogram (guide may be NULL => p_0 only), deduces
+ * or rectangle) or the cell's guide (guide may be NULL => p_0 only), deduces
  * x_1 = r(x_D, w_D) and the next vertices by scattering with tau, and writes
  * x/surf/prim/bary/pdf/tau and status (MPG_CHAIN_INVALID on failure, else
- * MPG_CHAIN_SEEDED). */
+ * MPG_CHAIN_SEEDED).
+ * Histogram guide: tau is the input (or uniform when tau_random) and pdf the
+ * solid-angle density of w_D.  vMF guide: given n = k[b], the guided component
+ * draws a lobe of the cell with probability proportional to its weight among
+ * the lobes of length n (of length n and type tau[b] unless tau_random) and
+ * takes (w_D, tau) from it; p_0 draws tau uniformly (tau_random) or keeps the
+ * input; pdf is the joint density p(w_D, tau | n) = alpha p_0(w_D) P_0(tau | n)
+ * + (1 - alpha) sum_{lobes of (n, tau)} (q_i / Q) v(w_D; mu_i, kappa_i).  A
+ * cell without lobes of the chain's length (and type) samples p_0 only. */
 mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
                             mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
                             const mpg_params* params, cudaStream_t stream);
@@ -284,20 +315,54 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* scene, const mp
  * q = min(floor(w[r] 2^S), 2^32-1) (0 unless w > 0) to counts[cell[r]][bin(omega)]
  * with 64-bit integer atomics (bit-exact, order independent), then rebuilds the
  * per-cell prefix sums used by the sampler.  omega is [3][R] SoA FP32 (R is the
- * row stride and the upper bound of n); R_dev is a device int32. */
+ * row stride and the upper bound of n); R_dev is a device int32.  Histogram
+ * guides only (a vMF guide is built by mpg_vmf_build). */
 mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell,
                             const float* omega, const float* w, int32_t R, const int32_t* R_dev,
                             int32_t weight_shift, cudaStream_t stream);
-/* Empties the guide (counts and prefix sums to zero) on `stream`, for a new
+/* Empties the guide (counts and prefix sums to zero; a vMF guide: no lobes in
+ * any cell) on `stream`, for a new
  * training pass (Sec. 5.8: the distributions are built from the last training iteration's samples only). */
 mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t stream);
-/* Records of the admissible chains of a batch for mpg_guide_update: compacts
- * (cell, w_D = unit(x_1 - x_D), w = contrib/A_L) of chains with contrib > 0 into
- * cell_out[B], omega_out[3][B] and w_out[B] (capacity B, record order
- * unspecified) and writes the record count to *R_dev (device int32). */
+/* Records of the admissible chains of a batch for mpg_guide_update and
+ * mpg_vmf_build: compacts (cell, w_D = unit(x_1 - x_D), w = contrib/A_L, and
+ * when k_out / tau_out are not NULL the chain's length and types) of chains
+ * with contrib > 0 into cell_out[B], omega_out[3][B], w_out[B], k_out[B] and
+ * tau_out[B] (capacity B) in chain order, and writes the record count to
+ * *R_dev (device int32). */
 mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* scene, const mpg_chains* chains,
                              const float* contrib, uint32_t* cell_out, float* omega_out,
-                             float* w_out, int32_t* R_dev, cudaStream_t stream);
+                             float* w_out, uint8_t* k_out, uint8_t* tau_out, int32_t* R_dev,
+                             cudaStream_t stream);
+
+/* Sec. 5.5 -- vMF mixture guide from the records of the last pass (Eq. vMF):
+ * record r < n (n = *R_dev when R_dev is not NULL, else R) with cell[r],
+ * direction omega[.][r] (SoA [3][R], R the row stride), weight w[r] (Eq.
+ * eq_weight), length k[r] (1..8) and types tau[r] (< 2^k) becomes a lobe with
+ * mu = omega, kappa = sigma^-2 where sigma is the angle to the nearest other
+ * direction of the same cell, length and types (pi when there is none, at
+ * least 1e-6), and weight q = min(floor(w 2^S), 2^32-1).  Lobes are sorted by
+ * (cell, n, tau) keeping the record order (a stable radix sort), so a build
+ * from the same records is bit-identical; cell_start, lobe_key, lobe and
+ * lobe_prefix are overwritten.  Records with a cell, length or type out of
+ * range are left out and flag the context error (reported by mpg_ctx_sync).
+ * R must not exceed guide->capacity. */
+mpg_status mpg_vmf_build(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell, const float* omega,
+                         const float* w, const uint8_t* k, const uint8_t* tau, int32_t R,
+                         const int32_t* R_dev, int32_t weight_shift, cudaStream_t stream);
+
+/* Sec. 5.5 -- chain lengths by the defensive one-sample mixture
+ * P(n) = alpha P_0(n) + (1 - alpha) P_e(n | cell), P_e(n | cell) = W(n) / W the
+ * weight fraction of the cell's lobes of length n (guide of kind
+ * MPG_GUIDE_VMF; NULL, or a cell without lobes => P_0 alone).  P_0 is given
+ * by the integer weights p0_weights[n-1], n = 1..8 (host array, sum > 0).
+ * Draws use Philox4x32-10 counter (b + rng_offset, 0, 2); writes k_out[b] and
+ * pn_out[b] = P(k_out[b]) for the B chains of `chains` (which supplies Q, spq
+ * and cell), to be used as chains->k and chains->pn. */
+mpg_status mpg_sample_lengths(mpg_ctx* ctx, const mpg_guide* guide, const mpg_chains* chains,
+                              const uint32_t* p0_weights, uint64_t rng_seed, uint64_t rng_offset,
+                              const mpg_params* params, uint8_t* k_out, float* pn_out,
+                              cudaStream_t stream);
 
 /* S11 -- adjoint (the configuration's differentiable form, built on the
  * continuity of the specular manifold, Sec. 5.2): accumulates

@@ -73,6 +73,8 @@ struct mpg_ctx {
   int fp64_cap = 0;
   int* d_list[2] = {nullptr, nullptr};
   unsigned* d_nbest = nullptr;
+  uint32_t* d_rec = nullptr;     // per-tile counts of the ordered record compaction
+  int rec_cap = 0;
   uint2* d_pairs = nullptr;      // [8B] converged trial walks of the parallel rounds (chain, trial)
   int* d_npairs = nullptr;       // [MAXK+1] pair counts per chain length
   int bern_cap = 0;
@@ -287,12 +289,27 @@ DChains to_dev(const mpg_chains* c) {
 
 mpg_status check_guide(const mpg_guide* g, DGuide& out) {
   if (!g) return fail(MPG_ERR_INVALID_ARG, "guide is NULL");
+  out = DGuide{};
+  if (g->kind == MPG_GUIDE_VMF) {
+    if (g->n_cells <= 0 || g->n_cells > (1 << 20) || g->capacity < 0 || !aligned16(g->cell_start) ||
+        !aligned16(g->lobe_key) || !aligned16(g->lobe) || !aligned16(g->lobe_prefix) || !aligned16(g->scratch))
+      return fail(MPG_ERR_INVALID_ARG, "invalid vMF guide (cells %d, capacity %d)", g->n_cells, g->capacity);
+    out.kind = MPG_GUIDE_VMF;
+    out.n_cells = g->n_cells;
+    out.cell_start = g->cell_start;
+    out.lobe_key = g->lobe_key;
+    out.lobe = reinterpret_cast<const float4*>(g->lobe);
+    out.lobe_prefix = g->lobe_prefix;
+    return MPG_OK;
+  }
+  if (g->kind != MPG_GUIDE_HISTOGRAM) return fail(MPG_ERR_INVALID_ARG, "unknown guide kind %d", g->kind);
   if (g->n_cells <= 0 || g->n_theta <= 0 || g->n_phi < 2 || (g->n_phi & 1) || !aligned16(g->counts) ||
       !aligned16(g->cdf) || !g->cos_theta || !g->phi_cos || !g->phi_sin)
     return fail(MPG_ERR_INVALID_ARG, "invalid guide (cells %d, theta %d, phi %d)", g->n_cells, g->n_theta, g->n_phi);
   out.n_cells = g->n_cells; out.n_theta = g->n_theta; out.n_phi = g->n_phi; out.bins = g->n_theta * g->n_phi;
   out.counts = g->counts; out.cdf = g->cdf; out.cos_theta = g->cos_theta; out.phi_cos = g->phi_cos;
   out.phi_sin = g->phi_sin;
+  out.kind = MPG_GUIDE_HISTOGRAM;
   return MPG_OK;
 }
 
@@ -463,6 +480,7 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
   cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero); cudaFree(c->d_fp64); cudaFree(c->d_fp64_count);
   cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest); cudaFree(c->d_pairs); cudaFree(c->d_npairs);
+  cudaFree(c->d_rec);
   cudaFree(c->t_x); cudaFree(c->t_surf); cudaFree(c->t_prim); cudaFree(c->t_bary); cudaFree(c->t_status);
   cudaFree(c->t_iters);
   for (int i = 0; i < MAXK; ++i) {
@@ -484,6 +502,9 @@ mpg_status mpg_ctx_sync(mpg_ctx* c, cudaStream_t st) {
   if (err) {
     CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
     if (err & ERR_BVH_STACK) return fail(MPG_ERR_LIMIT, "BVH traversal stack overflow (device flag %d)", err);
+    if (err & ERR_VMF_RECORD)
+      return fail(MPG_ERR_INVALID_ARG, "device-side argument error (flag %d): vMF record with a cell, length or "
+                  "types out of range (left out)", err);
     return fail(MPG_ERR_INVALID_ARG, "device-side argument error (flag %d): guide cell out of range", err);
   }
   return MPG_OK;
@@ -894,6 +915,8 @@ mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t
   DGuide g;
   mpg_status s;
   if ((s = check_guide(guide, g))) return s;
+  if (g.kind != MPG_GUIDE_HISTOGRAM)
+    return fail(MPG_ERR_INVALID_ARG, "mpg_guide_update fills histogram guides; vMF guides are built by mpg_vmf_build");
   if (R < 0 || shift < 0 || shift > 60 || (R > 0 && (!aligned16(cell) || !aligned16(omega) || !aligned16(w))))
     return fail(MPG_ERR_INVALID_ARG, "invalid records (R %d, shift %d)", R, shift);
   CUDA_TRY(cudaSetDevice(ctx->device));
@@ -909,6 +932,10 @@ mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t st
   mpg_status s;
   if ((s = check_guide(guide, g))) return s;
   CUDA_TRY(cudaSetDevice(ctx->device));
+  if (g.kind == MPG_GUIDE_VMF) {  // no lobes in any cell
+    CUDA_TRY(cudaMemsetAsync(guide->cell_start, 0, sizeof(uint32_t) * ((size_t)guide->n_cells + 1), st));
+    return MPG_OK;
+  }
   const size_t bytes = sizeof(uint64_t) * (size_t)guide->n_cells * (size_t)guide->n_theta * (size_t)guide->n_phi;
   CUDA_TRY(cudaMemsetAsync(guide->counts, 0, bytes, st));
   CUDA_TRY(cudaMemsetAsync(guide->cdf, 0, bytes, st));
@@ -916,18 +943,80 @@ mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t st
 }
 
 mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* contrib,
-                             uint32_t* cell_out, float* omega_out, float* w_out, int32_t* R_dev, cudaStream_t st) {
+                             uint32_t* cell_out, float* omega_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
+                             int32_t* R_dev, cudaStream_t st) {
   if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
   mpg_status s;
   if ((s = check_chains(chains, false))) return s;
-  if (!aligned16(contrib) || !aligned16(cell_out) || !aligned16(omega_out) || !aligned16(w_out) || !R_dev)
+  if (!aligned16(contrib) || !aligned16(cell_out) || !aligned16(omega_out) || !aligned16(w_out) || !R_dev ||
+      (k_out && !aligned16(k_out)) || (tau_out && !aligned16(tau_out)))
     return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
   CUDA_TRY(cudaSetDevice(ctx->device));
   DChains c = to_dev(chains);
-  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] {
-    launch_guide_records(c, contrib, 1.0f / sc->S.L.area, cell_out, omega_out, w_out, R_dev, ctx->sms, st);
+  const int tiles = rec_tiles(c.B);
+  if (ctx->rec_cap < tiles) {
+    if (ctx->capturing) return capture_grow_error();
+    if (ctx->d_rec) cudaFree(ctx->d_rec);
+    ctx->d_rec = nullptr;
+    CUDA_TRY(cudaMalloc(&ctx->d_rec, sizeof(uint32_t) * (size_t)tiles));
+    ctx->rec_cap = tiles;
+  }
+  timed(ctx, MPG_KERNEL_AUX, st, tiles ? 3 : 0, [&] {
+    launch_guide_records_ordered(c, contrib, 1.0f / sc->S.L.area, ctx->d_rec, cell_out, omega_out, w_out, k_out,
+                                 tau_out, R_dev, st);
   });
   LAUNCH_CHECK("guide records");
+  return MPG_OK;
+}
+
+mpg_status mpg_vmf_build(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell, const float* omega,
+                         const float* w, const uint8_t* k, const uint8_t* tau, int32_t R, const int32_t* R_dev,
+                         int32_t weight_shift, cudaStream_t st) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  mpg_status s;
+  DGuide g;
+  if ((s = check_guide(guide, g))) return s;
+  if (g.kind != MPG_GUIDE_VMF) return fail(MPG_ERR_INVALID_ARG, "mpg_vmf_build needs a guide of kind MPG_GUIDE_VMF");
+  if (R < 0 || R > guide->capacity)
+    return fail(MPG_ERR_INVALID_ARG, "record count %d outside [0, capacity %d]", R, guide->capacity);
+  if (R > 0 && (!aligned16(cell) || !aligned16(omega) || !aligned16(w) || !aligned16(k) || !aligned16(tau)))
+    return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
+  if (weight_shift < 0 || weight_shift > 32) return fail(MPG_ERR_INVALID_ARG, "weight_shift %d outside [0, 32]", weight_shift);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  timed(ctx, MPG_KERNEL_AUX, st, vmf_build_launches(R, g.n_cells), [&] {
+    launch_vmf_build(g, guide->scratch, cell, omega, w, k, tau, R, R_dev, weight_shift, ctx->d_err, ctx->sms, st);
+  });
+  LAUNCH_CHECK("vMF build");
+  return MPG_OK;
+}
+
+mpg_status mpg_sample_lengths(mpg_ctx* ctx, const mpg_guide* guide, const mpg_chains* chains,
+                              const uint32_t* p0_weights, uint64_t rng_seed, uint64_t rng_offset,
+                              const mpg_params* P, uint8_t* k_out, float* pn_out, cudaStream_t st) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  if (!chains || chains->B < 0 || chains->Q < 0 || chains->spq <= 0 || (int64_t)chains->Q * chains->spq != chains->B)
+    return fail(MPG_ERR_INVALID_ARG, "invalid chain batch sizes");
+  if (chains->B == 0) return MPG_OK;
+  mpg_status s;
+  if ((s = check_params(P))) return s;
+  if (!p0_weights) return fail(MPG_ERR_INVALID_ARG, "p0_weights is NULL");
+  uint64_t W0 = 0;
+  for (int n = 0; n < MAXK; ++n) W0 += p0_weights[n];
+  if (W0 == 0) return fail(MPG_ERR_INVALID_ARG, "the P_0 weights sum to zero");
+  if (!aligned16(k_out) || !aligned16(pn_out))
+    return fail(MPG_ERR_INVALID_ARG, "k_out and pn_out must be non-NULL 16-byte aligned device arrays");
+  DGuide g;
+  if (guide) {
+    if ((s = check_guide(guide, g))) return s;
+    if (g.kind != MPG_GUIDE_VMF) return fail(MPG_ERR_INVALID_ARG, "sampled lengths need a vMF guide (or NULL)");
+  }
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
+  timed(ctx, MPG_KERNEL_SEED, st, 1, [&] {
+    launch_sample_lengths(guide ? &g : nullptr, chains->cell, chains->B, chains->spq, p0_weights, key, rng_offset,
+                          P->alpha, dctx(ctx, MPG_KERNEL_SEED), k_out, pn_out, ctx->sms, st);
+  });
+  LAUNCH_CHECK("sample lengths");
   return MPG_OK;
 }
 

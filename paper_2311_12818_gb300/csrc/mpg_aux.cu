@@ -148,31 +148,6 @@ void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* ome
 }
 
 // Records (cell, w_D, w = contrib / A_L) of chains with a contribution.
-__global__ void k_guide_records(DChains c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
-                                float* w_out, int* R) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c.B; b += gridDim.x * blockDim.x) {
-    float cb = contrib[b];
-    if (!(cb > 0.0f)) continue;
-    int q = b / c.spq;
-    float3 xD = make_float3(c.xD[q], c.xD[c.Q + q], c.xD[2 * c.Q + q]);
-    float3 x1 = make_float3(c.x[b], c.x[(size_t)c.B + b], c.x[2 * (size_t)c.B + b]);
-    float3 w = unit(x1 - xD);
-    int r = atomicAdd(R, 1);
-    cell_out[r] = c.cell ? c.cell[q] : 0u;
-    om_out[r] = w.x;
-    om_out[c.B + r] = w.y;
-    om_out[2 * (size_t)c.B + r] = w.z;
-    w_out[r] = cb * inv_area;
-  }
-}
-
-void launch_guide_records(const DChains& c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
-                          float* w_out, int* R, int sms, cudaStream_t st) {
-  cudaMemsetAsync(R, 0, sizeof(int), st);
-  int grid = min(sms * 8, (c.B + 255) / 256 + 1);
-  k_guide_records<<<grid, 256, 0, st>>>(c, contrib, inv_area, cell_out, om_out, w_out, R);
-}
-
 // ---------------------------------------------------------------------------
 // End of a Bernoulli trial round
 // ---------------------------------------------------------------------------

@@ -10,8 +10,19 @@ void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, i
 void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, cudaStream_t st);
 void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* omega, const float* w, int R,
                          const int* R_dev, int shift, int* err, int sms, cudaStream_t st);
-void launch_guide_records(const DChains& c, const float* contrib, float inv_area, uint32_t* cell_out, float* om_out,
-                          float* w_out, int* R, int sms, cudaStream_t st);
+// Guide records in chain order (mpg_vmf.cu): tile_scratch holds rec_tiles(B) counts.
+int rec_tiles(int B);
+void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
+                                  uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
+                                  int* R, cudaStream_t st);
+// vMF lobe build and chain-length sampler (mpg_vmf.cu).
+int vmf_build_launches(int R, int n_cells);
+void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, const float* omega, const float* w,
+                      const uint8_t* k, const uint8_t* tau, int R, const int* R_dev, int shift, int* err, int sms,
+                      cudaStream_t st);
+void launch_sample_lengths(const DGuide* g, const uint32_t* cell, int B, int spq, const uint32_t* p0w, uint2 key,
+                           uint64_t offset, float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms,
+                           cudaStream_t st);
 void launch_trace(const DScene& S, const float* o, const float* d, int n, float tmin, float tmax, float* t, int* surf,
                   int* prim, float* bary, int* err, unsigned long long* stats, bool st_on, int sms, cudaStream_t st);
 double run_fp32_peak(float* scratch, int sms, cudaStream_t st);

@@ -30,7 +30,7 @@ enum { MAT_MIRROR = 0, MAT_DIELECTRIC = 1 };
 enum { LIGHT_POINT = 0, LIGHT_RECT = 1 };
 enum { TARGET_SPHERE = 0, TARGET_RECT = 1 };
 enum { ST_INVALID = 0, ST_CONVERGED = 1, ST_FAILED = 2, ST_LIMIT = 3, ST_SEEDED = 255 };
-enum { ERR_BVH_STACK = 1 };
+enum { ERR_BVH_STACK = 1, ERR_GUIDE_CELL = 2, ERR_VMF_RECORD = 4 };
 
 // ---------------------------------------------------------------------------
 // Scene description passed by value (kernel parameter space).
@@ -78,6 +78,11 @@ struct DGuide {
   const float* cos_theta;
   const float* phi_cos;
   const float* phi_sin;
+  int kind;                     // MPG_GUIDE_HISTOGRAM or MPG_GUIDE_VMF
+  const uint32_t* cell_start;   // vMF: [n_cells+1]
+  const uint32_t* lobe_key;     // vMF: (n << 8) | tau
+  const float4* lobe;           // vMF: (mu, kappa)
+  const uint64_t* lobe_prefix;  // vMF: cell-local inclusive prefix sums of the quantised weights
 };
 
 // Per-thread work counters (flushed once per warp).
@@ -749,6 +754,101 @@ __device__ __forceinline__ float p0_pdf(const DScene& S, float3 xD, float3 w) {
   return S.n_tg > 0 ? sum / (float)S.n_tg : 0.0f;
 }
 
+// floor(r * total / 2^32) in exact integer arithmetic.
+__device__ __forceinline__ uint64_t scaled_target(uint32_t r, uint64_t total) {
+  uint64_t lo = (uint64_t)r * total, hi = __umul64hi((uint64_t)r, total);
+  return (hi << 32) | (lo >> 32);
+}
+
+__device__ __forceinline__ uint64_t ldg64(const uint64_t* p) {
+  return __ldg(reinterpret_cast<const unsigned long long*>(p));
+}
+
+// ---------------------------------------------------------------------------
+// vMF mixture guide (Sec. 5.5, Eq. vMF).  The lobes of a cell are contiguous
+// and ordered by key (n << 8) | tau, so the lobes of one length, or of one
+// length and type, are a sub-range found by binary search; the cell-local
+// prefix sums of the integer weights make every discrete choice exact.
+// ---------------------------------------------------------------------------
+// Uniform in (0, 1]: the 24-bit draw of u01 shifted up by one step.
+__device__ __forceinline__ float u01c(uint32_t r) { return (float)((r >> 8) + 1u) * (1.0f / 16777216.0f); }
+
+// First lobe in [a, b) whose key is >= key.
+__device__ __forceinline__ uint32_t lobe_bound(const DGuide& g, uint32_t a, uint32_t b, uint32_t key) {
+  while (a < b) {
+    uint32_t m = (a + b) >> 1;
+    if (__ldg(g.lobe_key + m) < key) a = m + 1; else b = m;
+  }
+  return a;
+}
+
+// Weight of the lobes of the cell before lobe i.
+__device__ __forceinline__ uint64_t lobe_cum(const DGuide& g, uint32_t cs, uint32_t i) {
+  return i > cs ? ldg64(g.lobe_prefix + i - 1) : 0ull;
+}
+
+// Lobes of a cell with klo <= key < khi: [a, b), the weight before a, and the range's weight.
+struct VmfRange {
+  uint32_t cs, a, b;
+  uint64_t base, total;
+};
+__device__ __forceinline__ VmfRange vmf_range(const DGuide& g, uint32_t cell, uint32_t klo, uint32_t khi) {
+  VmfRange r;
+  r.cs = __ldg(g.cell_start + cell);
+  uint32_t ce = __ldg(g.cell_start + cell + 1);
+  r.a = lobe_bound(g, r.cs, ce, klo);
+  r.b = lobe_bound(g, r.a, ce, khi);
+  r.base = lobe_cum(g, r.cs, r.a);
+  r.total = lobe_cum(g, r.cs, r.b) - r.base;
+  return r;
+}
+
+// The lobe whose weight interval holds target: first i in [a, b) whose
+// prefix sum exceeds base + target (total > 0, target < total).
+__device__ __forceinline__ uint32_t vmf_search(const DGuide& g, const VmfRange& r, uint64_t target) {
+  uint32_t a = r.a, b = r.b - 1;
+  while (a < b) {
+    uint32_t m = (a + b) >> 1;
+    if (ldg64(g.lobe_prefix + m) - r.base > target) b = m; else a = m + 1;
+  }
+  return a;
+}
+
+// Draw from the lobe (mu, kappa): t = 1 - mu.w has density
+// kappa e^{-kappa t} / (1 - e^{-2 kappa}) on [0, 2], inverted with u1 in
+// (0, 1]; the azimuth 2 pi u2 is taken in the Duff et al. frame of mu.
+__device__ __forceinline__ float3 vmf_sample(float4 L, float u1, float u2) {
+  float3 mu = make_float3(L.x, L.y, L.z);
+  float t = -logf(fmaf(1.0f - u1, expf(-2.0f * L.w), u1)) / L.w;
+  t = fminf(fmaxf(t, 0.0f), 2.0f);
+  float ct = 1.0f - t, st = sqrtf(fmaxf(0.0f, t * (2.0f - t)));
+  float3 e1, e2;
+  onb(mu, e1, e2);
+  float sp, cp;
+  sincospif(2.0f * u2, &sp, &cp);
+  return mu * ct + (e1 * cp + e2 * sp) * st;
+}
+
+// v(w; mu, kappa) (Eq. vMF) as kappa / (2 pi (1 - e^{-2 kappa})) e^{-kappa |w - mu|^2 / 2}:
+// |w - mu|^2 / 2 = 1 - mu.w for unit vectors, without the cancellation of 1 - mu.w.
+__device__ __forceinline__ float vmf_pdf(float4 L, float3 w) {
+  float3 d = w - make_float3(L.x, L.y, L.z);
+  return L.w / (6.28318530717958647f * -expm1f(-2.0f * L.w)) * expf(-0.5f * L.w * dot(d, d));
+}
+
+// Mixture density of the lobes of key kt within the range r, weights q_i / total.
+static __device__ __noinline__ float vmf_mix_pdf(const DGuide& g, VmfRange r, uint32_t kt, float3 w) {
+  uint32_t a = lobe_bound(g, r.a, r.b, kt), b = lobe_bound(g, a, r.b, kt + 1);
+  uint64_t prev = lobe_cum(g, r.cs, a);
+  float sum = 0.0f;
+  for (uint32_t i = a; i < b; ++i) {
+    uint64_t c = ldg64(g.lobe_prefix + i);
+    sum = fmaf((float)(c - prev), vmf_pdf(__ldg(g.lobe + i), w), sum);
+    prev = c;
+  }
+  return sum / (float)r.total;
+}
+
 // Draw seed `trial` of chain idx and deduce its vertices.  Returns validity;
 // fills ch (first k vertices), tau and pdf.
 template <int K, bool kStats>
@@ -759,26 +859,49 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   if (kStats) cnt.seeds++;
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
-  tau_out = tau;
-  // a Bernoulli trial must sample the chain's own types: when it drew others it
-  // has failed already, before any ray is cast
-  if (need_tau_in && tau != tau_in) return false;
+  const bool vmf = g != nullptr && g->kind == MPG_GUIDE_VMF;
+  if (!vmf) {
+    tau_out = tau;
+    // a Bernoulli trial must sample the chain's own types: when it drew others it
+    // has failed already, before any ray is cast
+    if (need_tau_in && tau != tau_in) return false;
+  }
   uint4 r0 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 0u), key);
   uint64_t total = 0;
   bool use_guide = g != nullptr;
   const uint64_t* cdf = nullptr;
+  VmfRange vr = {};
   if (use_guide && cell >= (uint32_t)g->n_cells) {  // bad cell index: flag it, sample p_0 only
     atomicOr(err, 2);
     use_guide = false;
   }
-  if (use_guide) {
+  if (use_guide && vmf) {
+    // the guided component draws (w, tau) given n, or w given n and tau when
+    // the types are fixed
+    uint32_t klo = ((uint32_t)K << 8) | (tau_random ? 0u : tau_in);
+    uint32_t khi = tau_random ? ((uint32_t)(K + 1) << 8) : klo + 1;
+    vr = vmf_range(*g, cell, klo, khi);
+    total = vr.total;
+    use_guide = total > 0;
+  } else if (use_guide) {
     cdf = g->cdf + (size_t)cell * g->bins;
     total = __ldg(reinterpret_cast<const unsigned long long*>(cdf + g->bins - 1));
     use_guide = total > 0;
   }
   bool pick_p0 = !use_guide || u01(r0.x) < P.alpha;
+  uint32_t li = 0;
+  if (vmf) {
+    if (!pick_p0) {
+      li = vmf_search(*g, vr, scaled_target(r0.y, total));
+      tau = __ldg(g->lobe_key + li) & 255u;
+    }
+    tau_out = tau;
+    if (need_tau_in && tau != tau_in) return false;
+  }
   float3 w;
-  if (pick_p0) {
+  if (!pick_p0 && vmf) {
+    w = vmf_sample(__ldg(g->lobe + li), u01c(r0.z), u01(r0.w));
+  } else if (pick_p0) {
     if (S.n_tg == 0) return false;
     int ti = min((int)(u01(r1.x) * (float)S.n_tg), S.n_tg - 1);
     const DTarget& tg = S.tg[ti];
@@ -822,6 +945,11 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   if (dot(w, e.nD) <= 0.0f) return false;
   pdf = 0.0f;
   if (!want_pdf) {
+  } else if (vmf) {
+    // joint density of (w, tau) given n: p_0 draws the types uniformly
+    float p0 = p0_pdf(S, e.xD, w);
+    if (tau_random) p0 = ldexpf(p0, -K);
+    pdf = use_guide ? P.alpha * p0 + (1.0f - P.alpha) * vmf_mix_pdf(*g, vr, ((uint32_t)K << 8) | tau, w) : p0;
   } else if (use_guide) {
     float p0 = p0_pdf(S, e.xD, w);
     int bin = guide_bin(*g, w);

@@ -54,7 +54,12 @@ class mpg_chains(C.Structure):
 class mpg_guide(C.Structure):
     _fields_ = [("n_cells", C.c_int32), ("n_theta", C.c_int32), ("n_phi", C.c_int32),
                 ("counts", C.c_void_p), ("cdf", C.c_void_p), ("cos_theta", C.c_void_p),
-                ("phi_cos", C.c_void_p), ("phi_sin", C.c_void_p)]
+                ("phi_cos", C.c_void_p), ("phi_sin", C.c_void_p), ("kind", C.c_int32), ("capacity", C.c_int32),
+                ("cell_start", C.c_void_p), ("lobe_key", C.c_void_p), ("lobe", C.c_void_p),
+                ("lobe_prefix", C.c_void_p), ("scratch", C.c_void_p)]
+
+
+GUIDE_HISTOGRAM, GUIDE_VMF = 0, 1
 
 
 STAT_FIELDS = ["newton_steps", "thomas_rows", "full_evals", "c_evals", "ray_casts", "sphere_tests",
@@ -73,7 +78,8 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
-           "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune"]
+           "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
+           "mpg_sample_lengths"]
 
 _lib = None
 
@@ -109,7 +115,10 @@ def lib():
         L.mpg_chain_contribution.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                              C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
-        L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp]
+        L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp, vp, vp]
+        L.mpg_vmf_build.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, vp, vp, i32, vp, i32, vp]
+        L.mpg_sample_lengths.argtypes = [vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), vp, u64, u64,
+                                         C.POINTER(mpg_params), vp, vp, vp]
         L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp]
         L.mpg_trace_rays.argtypes = [vp, vp, vp, vp, i32, f32, f32, vp, vp, vp, vp, vp]
         L.mpg_fp32_peak.argtypes = [vp, C.POINTER(C.c_double), vp]
@@ -247,10 +256,37 @@ class Guide:
 
     def struct(self):
         return mpg_guide(self.n_cells, self.n_theta, self.n_phi, self.counts.data_ptr(), self.cdf.data_ptr(),
-                         self.cos_theta.data_ptr(), self.phi_cos.data_ptr(), self.phi_sin.data_ptr())
+                         self.cos_theta.data_ptr(), self.phi_cos.data_ptr(), self.phi_sin.data_ptr(),
+                         GUIDE_HISTOGRAM, 0, None, None, None, None, None)
 
     def clear(self, ctx, stream=None):
         mpg_guide_clear(ctx, self, stream)
+
+
+class VmfGuide:
+    """vMF mixture guide (Sec. 5.5) in device memory: up to `capacity` lobes,
+    cell_start [n_cells+1], lobe_key [capacity] ((n << 8) | tau), lobe
+    [capacity, 4] (mu, kappa), lobe_prefix [capacity] (cell-local prefix sums
+    of the quantised weights), and the build scratch; filled by mpg_vmf_build."""
+
+    def __init__(self, n_cells, capacity, device="cuda"):
+        self.n_cells, self.capacity = n_cells, capacity
+        cap = max(capacity, 1)
+        self.cell_start = torch.zeros(n_cells + 1, dtype=torch.int32, device=device)
+        self.lobe_key = torch.zeros(cap, dtype=torch.int32, device=device)
+        self.lobe = torch.zeros((cap, 4), dtype=torch.float32, device=device)
+        self.lobe_prefix = torch.zeros(cap, dtype=torch.int64, device=device)
+        words = 4 * cap + 256 * ((cap + 1023) // 1024) + 64
+        self.scratch = torch.zeros(words, dtype=torch.int32, device=device)
+
+    def struct(self):
+        return mpg_guide(self.n_cells, 0, 0, None, None, None, None, None, GUIDE_VMF, self.capacity,
+                         self.cell_start.data_ptr(), self.lobe_key.data_ptr(), self.lobe.data_ptr(),
+                         self.lobe_prefix.data_ptr(), self.scratch.data_ptr())
+
+    @property
+    def n_lobes(self):
+        return int(self.cell_start[-1].item())
 
 
 class Chains:
@@ -428,17 +464,48 @@ def mpg_guide_update(ctx, guide, cell, omega, w, R=None, R_dev=None, weight_shif
                                   weight_shift, _stream(stream)))
 
 
-def mpg_guide_records(ctx, scene, chains, contrib, out=None, stream=None):
-    """Records (cell [B] int32, omega [3, B], w [B], count [1] int32) of chains with contrib > 0."""
+def mpg_guide_records(ctx, scene, chains, contrib, out=None, with_types=False, stream=None):
+    """Records of chains with contrib > 0, in chain order: (cell [B] int32,
+    omega [3, B], w [B], count [4] int32 (entry 0)), or with_types (or a
+    six-tensor `out`): (cell, omega, w, k [B] uint8, tau [B] uint8, count)."""
     B = chains.B
     if out is None:
-        out = (torch.zeros(B, dtype=torch.int32, device="cuda"), torch.zeros((3, B), dtype=torch.float32, device="cuda"),
-               torch.zeros(B, dtype=torch.float32, device="cuda"), torch.zeros(4, dtype=torch.int32, device="cuda"))
-    cell, om, w, R = out
+        out = [torch.zeros(B, dtype=torch.int32, device="cuda"), torch.zeros((3, B), dtype=torch.float32, device="cuda"),
+               torch.zeros(B, dtype=torch.float32, device="cuda")]
+        if with_types:
+            out += [torch.zeros(B, dtype=torch.uint8, device="cuda"), torch.zeros(B, dtype=torch.uint8, device="cuda")]
+        out = tuple(out + [torch.zeros(4, dtype=torch.int32, device="cuda")])
+    if len(out) == 6:
+        cell, om, w, k, tau, R = out
+    else:
+        (cell, om, w, R), k, tau = out, None, None
     cs = chains.struct()
     _check(lib().mpg_guide_records(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(cell), _ptr(om), _ptr(w),
-                                   _ptr(R), _stream(stream)))
-    return cell, om, w, R
+                                   _ptr(k), _ptr(tau), _ptr(R), _stream(stream)))
+    return out
+
+
+def mpg_vmf_build(ctx, guide, cell, omega, w, k, tau, R=None, R_dev=None, weight_shift=16, stream=None):
+    """Lobes of the vMF guide from records: cell [R] int32, omega [3, R], w [R],
+    k [R] uint8, tau [R] uint8 (device tensors; R_dev a device count <= R)."""
+    R = int(cell.numel()) if R is None else R
+    gs = guide.struct()
+    _check(lib().mpg_vmf_build(ctx.h, C.byref(gs), _ptr(cell), _ptr(omega), _ptr(w), _ptr(k), _ptr(tau), R,
+                               _ptr(R_dev), weight_shift, _stream(stream)))
+
+
+def mpg_sample_lengths(ctx, guide, chains, p0_weights, params, rng_seed, rng_offset=0, out=None, stream=None):
+    """Chain lengths and P(n) from the mixture of P_0 (integer weights
+    p0_weights[n-1]) and the vMF guide (or None): returns (k [B] uint8, pn [B] f32)."""
+    B = chains.B
+    k, pn = out if out is not None else (torch.zeros(B, dtype=torch.uint8, device="cuda"),
+                                         torch.zeros(B, dtype=torch.float32, device="cuda"))
+    w = (C.c_uint32 * 8)(*[int(x) for x in p0_weights])
+    cs = chains.struct()
+    gs = guide.struct() if guide is not None else None
+    _check(lib().mpg_sample_lengths(ctx.h, C.byref(gs) if gs is not None else None, C.byref(cs), w, rng_seed,
+                                    rng_offset, C.byref(params), _ptr(k), _ptr(pn), _stream(stream)))
+    return k, pn
 
 
 def mpg_walk_adjoint(ctx, scene, chains, T, contrib, dL_dE, dL_dtheta, stream=None):
