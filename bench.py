@@ -744,6 +744,15 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
         st = ctx.stats()
         per = steps + 2
         fl = algorithmic_flops(st, F) / per
+        # per-family launch time (events around each launch on its stream; the
+        # per-length streams overlap) in an uncaptured pass of the same step
+        ctx.profile(reset=True)
+        ctx.set_profile(True)
+        step(9 << 32)
+        ctx.sync()
+        ctx.set_profile(False)
+        fam = {mpg.KERNEL_NAMES[kind]: ctx.profile(kind)[0] for kind in range(len(mpg.KERNEL_NAMES))}
+        ctx.profile(reset=True)
         c = res.contrib
         adm = int((c > 0).sum().item())
         return {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
@@ -752,7 +761,7 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
                 "admissible_per_step": adm, "capped_per_step": int(res.capped.sum().item()),
                 "mean_E": float(res.E.double().mean().item()),
                 "mean_E_std_err": float(res.E.double().std().item() / np.sqrt(wl.Q)),
-                "graph_kernels": gr.kernels()}
+                "graph_kernels": gr.kernels(), "family_ms_uncaptured": fam}
     out["p0_step"] = measure(False)
     out["vmf_step"] = measure(True)
     out["admissible_chains_per_ms"] = {k: out[k]["admissible_per_step"] / out[k]["ms_per_step"]

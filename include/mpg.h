@@ -161,6 +161,8 @@ typedef struct mpg_guide {
   float* lobe;             /* vMF: [capacity][4] mu_x, mu_y, mu_z, kappa           */
   uint64_t* lobe_prefix;   /* vMF: [capacity] inclusive prefix sums of the
                               quantised weights within the cell                    */
+  float* lobe_coef;        /* vMF: [capacity] q_i kappa_i / (2 pi (1 - e^{-2 kappa_i})),
+                              the lobe's factor in the mixture density             */
   uint32_t* scratch;       /* vMF: MPG_VMF_SCRATCH_WORDS(capacity) build scratch   */
 } mpg_guide;
 
@@ -343,8 +345,9 @@ mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* scene, const mpg_cha
  * direction of the same cell, length and types (pi when there is none, at
  * least 1e-6), and weight q = min(floor(w 2^S), 2^32-1).  Lobes are sorted by
  * (cell, n, tau) keeping the record order (a stable radix sort), so a build
- * from the same records is bit-identical; cell_start, lobe_key, lobe and
- * lobe_prefix are overwritten.  Records with a cell, length or type out of
+ * from the same records is bit-identical; cell_start, lobe_key, lobe,
+ * lobe_prefix and lobe_coef are overwritten.  The work scales with the record
+ * count (*R_dev), not with R.  Records with a cell, length or type out of
  * range are left out and flag the context error (reported by mpg_ctx_sync).
  * R must not exceed guide->capacity. */
 mpg_status mpg_vmf_build(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t* cell, const float* omega,

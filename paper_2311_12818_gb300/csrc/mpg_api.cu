@@ -292,7 +292,8 @@ mpg_status check_guide(const mpg_guide* g, DGuide& out) {
   out = DGuide{};
   if (g->kind == MPG_GUIDE_VMF) {
     if (g->n_cells <= 0 || g->n_cells > (1 << 20) || g->capacity < 0 || !aligned16(g->cell_start) ||
-        !aligned16(g->lobe_key) || !aligned16(g->lobe) || !aligned16(g->lobe_prefix) || !aligned16(g->scratch))
+        !aligned16(g->lobe_key) || !aligned16(g->lobe) || !aligned16(g->lobe_prefix) || !aligned16(g->lobe_coef) ||
+        !aligned16(g->scratch))
       return fail(MPG_ERR_INVALID_ARG, "invalid vMF guide (cells %d, capacity %d)", g->n_cells, g->capacity);
     out.kind = MPG_GUIDE_VMF;
     out.n_cells = g->n_cells;
@@ -300,6 +301,7 @@ mpg_status check_guide(const mpg_guide* g, DGuide& out) {
     out.lobe_key = g->lobe_key;
     out.lobe = reinterpret_cast<const float4*>(g->lobe);
     out.lobe_prefix = g->lobe_prefix;
+    out.lobe_coef = g->lobe_coef;
     return MPG_OK;
   }
   if (g->kind != MPG_GUIDE_HISTOGRAM) return fail(MPG_ERR_INVALID_ARG, "unknown guide kind %d", g->kind);

@@ -83,6 +83,7 @@ struct DGuide {
   const uint32_t* lobe_key;     // vMF: (n << 8) | tau
   const float4* lobe;           // vMF: (mu, kappa)
   const uint64_t* lobe_prefix;  // vMF: cell-local inclusive prefix sums of the quantised weights
+  const float* lobe_coef;       // vMF: q_i kappa_i / (2 pi (1 - e^{-2 kappa_i}))
 };
 
 // Per-thread work counters (flushed once per warp).
@@ -829,22 +830,19 @@ __device__ __forceinline__ float3 vmf_sample(float4 L, float u1, float u2) {
   return mu * ct + (e1 * cp + e2 * sp) * st;
 }
 
-// v(w; mu, kappa) (Eq. vMF) as kappa / (2 pi (1 - e^{-2 kappa})) e^{-kappa |w - mu|^2 / 2}:
-// |w - mu|^2 / 2 = 1 - mu.w for unit vectors, without the cancellation of 1 - mu.w.
-__device__ __forceinline__ float vmf_pdf(float4 L, float3 w) {
-  float3 d = w - make_float3(L.x, L.y, L.z);
-  return L.w / (6.28318530717958647f * -expm1f(-2.0f * L.w)) * expf(-0.5f * L.w * dot(d, d));
-}
-
 // Mixture density of the lobes of key kt within the range r, weights q_i / total.
+// The lobe density (Eq. vMF) kappa / (4 pi sinh kappa) e^{kappa mu.w} is written
+// kappa / (2 pi (1 - e^{-2 kappa})) e^{-kappa |w - mu|^2 / 2} (|w - mu|^2 / 2 =
+// 1 - mu.w for unit vectors, without its cancellation), so the sum is
+// sum_i coef_i e^{-kappa_i |w - mu_i|^2 / 2} / total with the lobe factors
+// coef_i = q_i kappa_i / (2 pi (1 - e^{-2 kappa_i})) formed once by the build.
 static __device__ __noinline__ float vmf_mix_pdf(const DGuide& g, VmfRange r, uint32_t kt, float3 w) {
   uint32_t a = lobe_bound(g, r.a, r.b, kt), b = lobe_bound(g, a, r.b, kt + 1);
-  uint64_t prev = lobe_cum(g, r.cs, a);
   float sum = 0.0f;
   for (uint32_t i = a; i < b; ++i) {
-    uint64_t c = ldg64(g.lobe_prefix + i);
-    sum = fmaf((float)(c - prev), vmf_pdf(__ldg(g.lobe + i), w), sum);
-    prev = c;
+    float4 L = __ldg(g.lobe + i);
+    float3 d = w - make_float3(L.x, L.y, L.z);
+    sum = fmaf(__ldg(g.lobe_coef + i), expf(-0.5f * L.w * dot(d, d)), sum);
   }
   return sum / (float)r.total;
 }

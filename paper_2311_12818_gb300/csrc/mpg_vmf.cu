@@ -58,6 +58,44 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_exclusive(uint32_t* a, in
   if (total && t == SCAN_THREADS - 1) *total = (int)run;
 }
 
+// Exclusive scan of the digit-major tile counts cnt[d * tiles + t] over the
+// tiles that hold records (t < used, the others take no part), by one CTA:
+// the virtual index v = d * used + t runs over 256 * used entries.
+__global__ void __launch_bounds__(SCAN_THREADS) k_radix_scan(uint32_t* cnt, int tiles, int R, const int* R_dev) {
+  __shared__ uint32_t warp_sum[SCAN_THREADS / 32];
+  const int nr = R_dev ? min(max(*R_dev, 0), R) : R;
+  const int used = (nr + 4 * 256 - 1) / (4 * 256);
+  const int n = 256 * used;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int chunk = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int i0 = min(n, t * chunk), i1 = min(n, i0 + chunk);
+  auto at = [&](int v) -> uint32_t& { return cnt[(size_t)(v / used) * tiles + v % used]; };
+  uint32_t s = 0;
+  for (int i = i0; i < i1; ++i) s += at(i);
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t v = warp_sum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(FULL, v, o);
+      if (lane >= o) v += y;
+    }
+    warp_sum[lane] = v;
+  }
+  __syncthreads();
+  uint32_t run = x - s + (wid > 0 ? warp_sum[wid - 1] : 0u);
+  for (int i = i0; i < i1; ++i) {
+    uint32_t v = at(i);
+    at(i) = run;
+    run += v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Guide records in chain order (count per tile, scan, write)
 // ---------------------------------------------------------------------------
@@ -118,8 +156,14 @@ __global__ void __launch_bounds__(TILE_THREADS) k_rec_write(DChains c, const flo
 // Stable LSD radix sort of (key, value) pairs, 8 bits per pass
 // ---------------------------------------------------------------------------
 // Digit counts of each tile, stored digit-major: cnt[d * tiles + tile].
-__global__ void __launch_bounds__(TILE_THREADS) k_radix_hist(const uint32_t* keys, int n, int shift, uint32_t* cnt) {
+// Number of records to sort: the device count when given, else R.
+__device__ __forceinline__ int sort_count(int R, const int* R_dev) { return R_dev ? min(max(*R_dev, 0), R) : R; }
+
+__global__ void __launch_bounds__(TILE_THREADS) k_radix_hist(const uint32_t* keys, int R, const int* R_dev, int shift,
+                                                             uint32_t* cnt) {
   __shared__ uint32_t h[256];
+  const int n = sort_count(R, R_dev);
+  if (blockIdx.x * RADIX_TILE >= n) return;  // past the records: this tile takes no part
   h[threadIdx.x] = 0;
   __syncthreads();
   for (int r = 0; r < RADIX_TILE / TILE_THREADS; ++r) {
@@ -134,11 +178,13 @@ __global__ void __launch_bounds__(TILE_THREADS) k_radix_hist(const uint32_t* key
 // tile the items go in index order (rounds of 256, warps in order, lanes in
 // order: match-any ranks within a warp, per-warp digit counts across warps).
 __global__ void __launch_bounds__(TILE_THREADS) k_radix_scatter(const uint32_t* kin, const uint32_t* vin,
-                                                                uint32_t* kout, uint32_t* vout, int n, int shift,
-                                                                const uint32_t* off) {
+                                                                uint32_t* kout, uint32_t* vout, int R,
+                                                                const int* R_dev, int shift, const uint32_t* off) {
   constexpr int NW = TILE_THREADS / 32;
   __shared__ uint32_t base[256];
   __shared__ uint32_t wc[NW][256];
+  const int n = sort_count(R, R_dev);
+  if (blockIdx.x * RADIX_TILE >= n) return;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
   base[t] = off[(size_t)t * gridDim.x + blockIdx.x];
   for (int r = 0; r < RADIX_TILE / TILE_THREADS; ++r) {
@@ -173,30 +219,29 @@ __global__ void __launch_bounds__(TILE_THREADS) k_radix_scatter(const uint32_t* 
 // ---------------------------------------------------------------------------
 // Lobe build
 // ---------------------------------------------------------------------------
-// Group key of each record, cell << 11 | (n - 1) << 8 | tau (cell, then
-// length, then types); records past the count and invalid records get
-// n_cells << 11 and sort after every valid one.
+// Group key of each of the n records, cell << 11 | (n - 1) << 8 | tau (cell,
+// then length, then types); invalid records get n_cells << 11 and sort after
+// every valid one.  Entries past the record count are not sorted or read.
 __global__ void k_vmf_keys(const uint32_t* cell, const uint8_t* k, const uint8_t* tau, int R, const int* R_dev,
                            int n_cells, uint32_t* keys, uint32_t* vals, int* err) {
-  const int n = R_dev ? min(max(*R_dev, 0), R) : R;
+  const int n = sort_count(R, R_dev);
   const uint32_t past = (uint32_t)n_cells << 11;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     uint32_t key = past;
-    if (i < n) {
-      uint32_t c = cell[i], kk = k[i], tt = tau[i];
-      if (c < (uint32_t)n_cells && kk >= 1 && kk <= MAXK && tt < (1u << kk)) key = (c << 11) | ((kk - 1) << 8) | tt;
-      else atomicOr(err, 4);
-    }
+    uint32_t c = cell[i], kk = k[i], tt = tau[i];
+    if (c < (uint32_t)n_cells && kk >= 1 && kk <= MAXK && tt < (1u << kk)) key = (c << 11) | ((kk - 1) << 8) | tt;
+    else atomicOr(err, 4);
     keys[i] = key;
     vals[i] = (uint32_t)i;
   }
 }
 
 // cell_start[c] = first sorted key >= c << 11, c = 0..n_cells (the last is the lobe count).
-__global__ void k_vmf_cells(const uint32_t* keys, int R, int n_cells, uint32_t* cell_start) {
+__global__ void k_vmf_cells(const uint32_t* keys, int R, const int* R_dev, int n_cells, uint32_t* cell_start) {
+  const int n = sort_count(R, R_dev);
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= n_cells; c += gridDim.x * blockDim.x) {
     uint32_t want = (uint32_t)c << 11;
-    int a = 0, b = R;
+    int a = 0, b = n;
     while (a < b) {
       int m = (a + b) >> 1;
       if (keys[m] < want) a = m + 1; else b = m;
@@ -290,9 +335,24 @@ __global__ void __launch_bounds__(TILE_THREADS) k_vmf_kappa(const uint32_t* keys
   }
 }
 
-__global__ void k_vmf_kappa_store(const uint32_t* cell_start, int n_cells, const float* kap, float4* lobe) {
+// Stores kappa into the lobes and the density coefficient of each lobe,
+// q_i kappa_i / (2 pi (1 - e^{-2 kappa_i})), so that the mixture density is
+// sum_i coef_i e^{-kappa_i |w - mu_i|^2 / 2} / Q.
+__global__ void k_vmf_kappa_store(const uint32_t* cell_start, int n_cells, const float* kap,
+                                  const uint64_t* prefix, float4* lobe, float* coef) {
   const int L = (int)cell_start[n_cells];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) lobe[i].w = kap[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+    const float k = kap[i];
+    lobe[i].w = k;
+    // the cell of lobe i: the last c with cell_start[c] <= i
+    int a = 0, b = n_cells;
+    while (b - a > 1) {
+      int m = (a + b) >> 1;
+      if ((int)cell_start[m] <= i) a = m; else b = m;
+    }
+    const uint64_t q = prefix[i] - ((uint32_t)i > cell_start[a] ? prefix[i - 1] : 0ull);
+    coef[i] = (float)q * (k / (6.28318530717958647f * -expm1f(-2.0f * k)));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -381,7 +441,7 @@ void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, 
     cudaMemsetAsync(cell_start, 0, sizeof(uint32_t) * (size_t)(g.n_cells + 1), st);
     return;
   }
-  const int tiles = (R + RADIX_TILE - 1) / RADIX_TILE;
+  const int tiles = (R + RADIX_TILE - 1) / RADIX_TILE;  // tiles past the record count return at once
   uint32_t* ka = scratch;
   uint32_t* va = ka + R;
   uint32_t* kb = va + R;
@@ -391,20 +451,21 @@ void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, 
   k_vmf_keys<<<grid, 256, 0, st>>>(cell, k, tau, R, R_dev, g.n_cells, ka, va, err);
   const int bits = 32 - __builtin_clz((unsigned)g.n_cells << 11);
   for (int shift = 0; shift < bits; shift += 8) {
-    k_radix_hist<<<tiles, TILE_THREADS, 0, st>>>(ka, R, shift, cnt);
-    k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(cnt, 256 * tiles, nullptr);
-    k_radix_scatter<<<tiles, TILE_THREADS, 0, st>>>(ka, va, kb, vb, R, shift, cnt);
+    k_radix_hist<<<tiles, TILE_THREADS, 0, st>>>(ka, R, R_dev, shift, cnt);
+    k_radix_scan<<<1, SCAN_THREADS, 0, st>>>(cnt, tiles, R, R_dev);
+    k_radix_scatter<<<tiles, TILE_THREADS, 0, st>>>(ka, va, kb, vb, R, R_dev, shift, cnt);
     std::swap(ka, kb);
     std::swap(va, vb);
   }
-  k_vmf_cells<<<(g.n_cells + 256) / 256, 256, 0, st>>>(ka, R, g.n_cells, cell_start);
+  k_vmf_cells<<<(g.n_cells + 256) / 256, 256, 0, st>>>(ka, R, R_dev, g.n_cells, cell_start);
   k_vmf_lobes<<<grid, 256, 0, st>>>(va, cell_start, g.n_cells, omega, w, k, tau, R, shift,
                                     const_cast<uint32_t*>(g.lobe_key), const_cast<float4*>(g.lobe),
                                     const_cast<uint64_t*>(g.lobe_prefix));
   k_vmf_prefix<<<g.n_cells, TILE_THREADS, 0, st>>>(cell_start, const_cast<uint64_t*>(g.lobe_prefix));
   float* kap = reinterpret_cast<float*>(kb);  // the sort's other key buffer is free now
   k_vmf_kappa<<<grid, TILE_THREADS, 0, st>>>(ka, cell_start, g.n_cells, g.lobe, kap);
-  k_vmf_kappa_store<<<grid, 256, 0, st>>>(cell_start, g.n_cells, kap, const_cast<float4*>(g.lobe));
+  k_vmf_kappa_store<<<grid, 256, 0, st>>>(cell_start, g.n_cells, kap, g.lobe_prefix, const_cast<float4*>(g.lobe),
+                                          const_cast<float*>(g.lobe_coef));
 }
 
 void launch_sample_lengths(const DGuide* g, const uint32_t* cell, int B, int spq, const uint32_t* p0w, uint2 key,

@@ -56,7 +56,7 @@ class mpg_guide(C.Structure):
                 ("counts", C.c_void_p), ("cdf", C.c_void_p), ("cos_theta", C.c_void_p),
                 ("phi_cos", C.c_void_p), ("phi_sin", C.c_void_p), ("kind", C.c_int32), ("capacity", C.c_int32),
                 ("cell_start", C.c_void_p), ("lobe_key", C.c_void_p), ("lobe", C.c_void_p),
-                ("lobe_prefix", C.c_void_p), ("scratch", C.c_void_p)]
+                ("lobe_prefix", C.c_void_p), ("lobe_coef", C.c_void_p), ("scratch", C.c_void_p)]
 
 
 GUIDE_HISTOGRAM, GUIDE_VMF = 0, 1
@@ -257,7 +257,7 @@ class Guide:
     def struct(self):
         return mpg_guide(self.n_cells, self.n_theta, self.n_phi, self.counts.data_ptr(), self.cdf.data_ptr(),
                          self.cos_theta.data_ptr(), self.phi_cos.data_ptr(), self.phi_sin.data_ptr(),
-                         GUIDE_HISTOGRAM, 0, None, None, None, None, None)
+                         GUIDE_HISTOGRAM, 0, None, None, None, None, None, None)
 
     def clear(self, ctx, stream=None):
         mpg_guide_clear(ctx, self, stream)
@@ -267,7 +267,8 @@ class VmfGuide:
     """vMF mixture guide (Sec. 5.5) in device memory: up to `capacity` lobes,
     cell_start [n_cells+1], lobe_key [capacity] ((n << 8) | tau), lobe
     [capacity, 4] (mu, kappa), lobe_prefix [capacity] (cell-local prefix sums
-    of the quantised weights), and the build scratch; filled by mpg_vmf_build."""
+    of the quantised weights), lobe_coef [capacity] (density factors), and the
+    build scratch; filled by mpg_vmf_build."""
 
     def __init__(self, n_cells, capacity, device="cuda"):
         self.n_cells, self.capacity = n_cells, capacity
@@ -276,13 +277,14 @@ class VmfGuide:
         self.lobe_key = torch.zeros(cap, dtype=torch.int32, device=device)
         self.lobe = torch.zeros((cap, 4), dtype=torch.float32, device=device)
         self.lobe_prefix = torch.zeros(cap, dtype=torch.int64, device=device)
+        self.lobe_coef = torch.zeros(cap, dtype=torch.float32, device=device)
         words = 4 * cap + 256 * ((cap + 1023) // 1024) + 64
         self.scratch = torch.zeros(words, dtype=torch.int32, device=device)
 
     def struct(self):
         return mpg_guide(self.n_cells, 0, 0, None, None, None, None, None, GUIDE_VMF, self.capacity,
                          self.cell_start.data_ptr(), self.lobe_key.data_ptr(), self.lobe.data_ptr(),
-                         self.lobe_prefix.data_ptr(), self.scratch.data_ptr())
+                         self.lobe_prefix.data_ptr(), self.lobe_coef.data_ptr(), self.scratch.data_ptr())
 
     @property
     def n_lobes(self):
