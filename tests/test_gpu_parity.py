@@ -155,14 +155,31 @@ def test_mirror_sphere_parity(M, ctx):
     assert abs(E_g.sum() - E_o.sum()) / E_o.sum() < 1e-3
 
 
+def _chains_from_oracle(M, wl, o, status):
+    """Device chains holding the oracle's chains (rounded to FP32) with the
+    given status: the oracle's results as inputs of a CUDA stage."""
+    ch = M.Chains(wl)
+    ch.x.copy_(torch.as_tensor(np.ascontiguousarray(o["x"].transpose(1, 2, 0)).astype(np.float32)))
+    ch.surf.copy_(torch.as_tensor(np.ascontiguousarray(o["surf"].T).astype(np.int32)))
+    ch.prim.copy_(torch.as_tensor(np.ascontiguousarray(o["prim"].T).astype(np.int32)))
+    ch.bary.copy_(torch.as_tensor(np.ascontiguousarray(o["bary"].transpose(1, 2, 0)).astype(np.float32)))
+    ch.tau.copy_(torch.as_tensor(o["tau"].astype(np.uint8)))
+    ch.status.copy_(torch.as_tensor(status.astype(np.uint8)))
+    return ch
+
+
 def test_walk_parity_from_identical_seeds(M, ctx):
-    """The GPU's own FP32 seeds walked by the oracle in FP64: isolates the walk."""
+    """The oracle's seeds (rounded to FP32) walked on the GPU, against the
+    oracle's FP64 walk of the same seeds: isolates the walk."""
     wl = I.glass_sphere(n=32, spq=16)
-    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
     osc = O.Scene(wl)
-    seeds = dict(x=gs["x"].copy(), surf=gs["surf"].copy(), prim=gs["prim"].copy(), bary=gs["bary"].copy(),
-                 tau=gs["tau"].copy(), valid=(gs["status"] != 0).astype(np.uint8))
+    seeds = O.sample_seeds(wl, osc)
     ow = O.walk(wl, osc, seeds)
+    sc = M.Scene(ctx, wl)
+    ch = _chains_from_oracle(M, wl, seeds, np.where(seeds["valid"] == 1, M.CHAIN_SEEDED, M.CHAIN_INVALID))
+    M.mpg_manifold_walk(ctx, sc, ch, _params(M, wl))
+    ctx.sync()
+    gw = ch.aos()
     _compare_walk(wl, gw, ow)
     assert np.quantile(np.abs(gw["iters"].astype(int) - ow["iters"].astype(int))[ow["status"] == 1], 0.99) <= 1
 
@@ -334,21 +351,26 @@ def test_edge_cases(M, ctx):
 
 
 def test_water_adjoint_matches_oracle(M, ctx):
-    """K7 against the oracle's IFT gradient at the same converged chains and
-    weights dL/dE[q]/spq * contrib/T (gradients within 1e-2 relative)."""
+    """K7 against the oracle's IFT gradient at the oracle's converged chains
+    and weights dL/dE[q]/spq * contrib/T, given to the GPU as inputs (rounded
+    to FP32); gradients within 1e-2 relative."""
     wl = I.water(n=48, spq=4, grid=128)
-    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    adm = con["admissible"] == 1
+    T = np.where(adm, con["T"], 0.0)
+    contrib = np.where(adm, wl.light_area * T * N / wl.pn, 0.0)
     dLdE = I.upstream_grad(wl.Q).astype(np.float32)
-    g = torch.zeros(wl.hf_heights.size, dtype=torch.float32, device="cuda")
-    M.mpg_walk_adjoint(ctx, sc, ch, out.T, out.contrib, torch.as_tensor(dLdE, device="cuda"), g)
-    ctx.sync()
-    gch = ch.aos()
-    T = out.T.cpu().numpy().astype(np.float64)
-    contrib = out.contrib.cpu().numpy().astype(np.float64)
     q = np.arange(wl.B) // wl.spq
-    w = np.where(T > 0, dLdE[q] / wl.spq * contrib / np.maximum(T, 1e-30), 0.0)
+    T32, c32 = T.astype(np.float32), contrib.astype(np.float32)
+    w = np.where(T32 > 0, dLdE[q] / wl.spq * c32.astype(np.float64) / np.maximum(T32, 1e-30), 0.0)
     assert (w > 0).sum() > 1000
-    g_o, okf = O.adjoint(wl, O.Scene(wl), gch, w)
+    g_o, okf = O.adjoint(wl, osc, ow, w)
+    sc = M.Scene(ctx, wl)
+    ch = _chains_from_oracle(M, wl, ow, np.where(adm, M.CHAIN_CONVERGED, M.CHAIN_FAILED))
+    g = torch.zeros(wl.hf_heights.size, dtype=torch.float32, device="cuda")
+    M.mpg_walk_adjoint(ctx, sc, ch, torch.as_tensor(T32, device="cuda"), torch.as_tensor(c32, device="cuda"),
+                       torch.as_tensor(dLdE, device="cuda"), g)
+    ctx.sync()
     g_g = g.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(g_o) > 0
     assert np.linalg.norm(g_g - g_o) <= 1e-2 * np.linalg.norm(g_o)
