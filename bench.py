@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -464,7 +464,9 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     - mixed: the mixed-length batch (k = 1..8, 2^22 chains) plain (one launch
       per k), batched (one graph replay) and batched with the autotuned schedule;
     - adjoint: the adjoint of the water irradiance with respect to the heights;
-    - vmf: the vMF mixture guide with sampled chain lengths on the mixed batch."""
+    - vmf: the vMF mixture guide with sampled chain lengths on the mixed batch;
+    - repeats: four Bernoulli estimates per chain in rendering (R x 4) or in
+      training and rendering (TR x 4) on the guided glass-sphere step."""
     import numpy as np
     from paper_2311_12818_gb300 import inputs as I
     from paper_2311_12818_gb300 import mpg
@@ -486,6 +488,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
     if "vmf" in parts:
         out["vmf_guide"] = part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
+    if "repeats" in parts:
+        out["repeated_estimates"] = part_repeats(ctx, dev, flush, torch, stream, steps)
     if "mixed_group" in parts and parts == ("mixed_group",):
         out["mixed_group"] = part_mixed_group(ctx, dev, flush, torch, stream, steps)
     return out
@@ -766,6 +770,65 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
     out["vmf_step"] = measure(True)
     out["admissible_chains_per_ms"] = {k: out[k]["admissible_per_step"] / out[k]["ms_per_step"]
                                        for k in ("p0_step", "vmf_step")}
+    return out
+
+
+def part_repeats(ctx, dev, flush, torch, stream, steps):
+    """The repeated reciprocal-probability estimate of the paper's performance
+    analysis on the benchmark's guided glass-sphere step: one estimate per
+    chain, four in rendering only (R x 4), four in training and rendering
+    (TR x 4).  Per configuration: a p_0 training pass builds the histogram
+    guide, the guided step replays a captured graph (ms, converged walks/s),
+    and two independent guided steps give the per-point variance of E as half
+    the mean squared difference of their images."""
+    import dataclasses
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.glass_sphere()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    rec = (torch.zeros(wl.B, dtype=torch.int32, device=dev), torch.zeros((3, wl.B), dtype=torch.float32, device=dev),
+           torch.zeros(wl.B, dtype=torch.float32, device=dev), torch.zeros(4, dtype=torch.int32, device=dev))
+    g = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+
+    def params(r):
+        return mpg.params_from(dataclasses.replace(wl.params, bern_repeats=r), walk_mode=mpg.WALK_BATCHED,
+                               k_uniform=2)
+    out = {"workload": "glass_sphere_k2 guided, 1,048,576 chains per step; histogram guide from a p_0 pass"}
+    for name, r_train, r_render in (("single", 1, 1), ("R_x4", 1, 4), ("TR_x4", 4, 4)):
+        Pt, Pr = params(r_train), params(r_render)
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, Pt, wl.rng_seed, 1 << 40)
+        mpg.mpg_manifold_walk(ctx, sc, ch, Pt)
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, Pt, wl.rng_seed, 1 << 40, out=res)
+        mpg.mpg_guide_records(ctx, sc, ch, res.contrib, out=rec)
+        mpg.mpg_guide_clear(ctx, g)
+        mpg.mpg_guide_update(ctx, g, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
+
+        def step(o, P=Pr):
+            mpg.mpg_sample_seeds(ctx, sc, g, ch, P, wl.rng_seed, o)
+            mpg.mpg_manifold_walk(ctx, sc, ch, P)
+            mpg.mpg_chain_contribution(ctx, sc, g, ch, P, wl.rng_seed, o, out=res)
+        images = []
+        for o in (5 << 32, 6 << 32):
+            step(o)
+            ctx.sync()
+            images.append(res.E.double().clone())
+        var = float(((images[0] - images[1]) ** 2).mean().item() / 2)
+        gr = mpg.Graph(ctx, rng_advance=wl.B)
+        with gr:
+            step(7 << 32)
+        ctx.reset_stats()
+        ms = timed_loop(lambda i: gr.launch(), steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        per = steps + 2
+        out[name] = {"train_repeats": r_train, "render_repeats": r_render, "ms_per_step": ms,
+                     "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+                     "trials_per_step": st["trials"] / per, "mean_E": float(images[0].mean().item()),
+                     "per_point_variance_of_E": var}
+    for name in ("R_x4", "TR_x4"):
+        out[name]["variance_vs_single"] = out[name]["per_point_variance_of_E"] / out["single"]["per_point_variance_of_E"]
+        out[name]["time_vs_single"] = out[name]["ms_per_step"] / out["single"]["ms_per_step"]
     return out
 
 

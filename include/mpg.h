@@ -109,6 +109,14 @@ typedef struct mpg_params {
                            memory.  Same per-vertex arithmetic; the compiler may
                            contract products differently in the two forms, so
                            results agree to FP32 rounding, not bit for bit    */
+  int32_t bern_repeats; /* Bernoulli: independent reciprocal-probability
+                           estimates averaged per chain (0 or 1 = one; up to 64;
+                           the paper's repeated estimation, Sec. 6 performance
+                           analysis).  Repeat j draws trial t from counter
+                           (b + offset, t | j << 24, block), so repeat 0 is the
+                           single estimate; trials[b] is the sum of the N_j,
+                           <1/P> = trials[b] / (repeats P(n)), capped is set when
+                           any repeat ran out of trials                        */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
@@ -305,7 +313,9 @@ mpg_status mpg_manifold_walk_noalloc(const mpg_scene* scene, mpg_chains* chains,
  * distance test), N = trial index, <1/P> = N / P(n) (capped at max_trials,
  * `capped` set).  Writes contrib[b] = A_L T <1/P> (A_L = light area, 1 for a
  * point light) and the irradiance estimate E[q] = sum_b contrib / spq
- * (Eq. ThroughputMC).  Outputs may be NULL except E; all are [B] unless noted. */
+ * (Eq. ThroughputMC).  Outputs may be NULL except E; all are [B] unless noted.
+ * Chains whose geometry term is formed in FP64 are first polished in FP64;
+ * their x, prim and bary are updated in place with the polished vertices. */
 mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
                                   const mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
                                   const mpg_params* params, float* G, float* kappa, float* T,

@@ -1642,21 +1642,27 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
     ChainIO target;
     load_chain(S, b, k[b], tau[b], xD, xL, x, surf, nullptr, nullptr, spq, target);
     V3d xd = load3(xD + 3 * (size_t)q), nd = load3(nD + 3 * (size_t)q), xl = load3(xL + 3 * (size_t)b);
-    for (int t = 1; t <= P.max_trials; ++t) {
-      SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, xd, nd,
-                                cell ? cell[q] : 0u, xl, k[b], tau[b], tau_random != 0, rng_seed,
-                                (uint64_t)b + rng_offset, (uint32_t)t, P);
-      if (!sd.valid) continue;
-      int it = 0;
-      if (walk_chain(S, sd.ch, nd, P, it) != ST_CONVERGED) continue;
-      if (trial_walks) trial_walks[b]++;
-      if (same_solution(sd.ch, target, P.dedup_eps)) {
-        N[b] = (uint32_t)t;
-        return;
+    const int repeats = P.bern_repeats > 1 ? P.bern_repeats : 1;
+    for (int rep = 0; rep < repeats; ++rep) {
+      bool hit = false;
+      for (int t = 1; t <= P.max_trials && !hit; ++t) {
+        SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, xd, nd,
+                                  cell ? cell[q] : 0u, xl, k[b], tau[b], tau_random != 0, rng_seed,
+                                  (uint64_t)b + rng_offset, (uint32_t)t | ((uint32_t)rep << 24), P);
+        if (!sd.valid) continue;
+        int it = 0;
+        if (walk_chain(S, sd.ch, nd, P, it) != ST_CONVERGED) continue;
+        if (trial_walks) trial_walks[b]++;
+        if (same_solution(sd.ch, target, P.dedup_eps)) {
+          N[b] += (uint32_t)t;
+          hit = true;
+        }
+      }
+      if (!hit) {
+        N[b] += (uint32_t)P.max_trials;
+        capped[b] = 1;
       }
     }
-    N[b] = (uint32_t)P.max_trials;
-    capped[b] = 1;
   });
   return 0;
 }

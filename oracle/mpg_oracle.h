@@ -37,6 +37,7 @@ typedef struct orc_params {
   int32_t max_trials;  /* Bernoulli trial cap */
   int32_t weight_shift;/* histogram quantisation shift S */
   double alpha;        /* defensive mixture weight of p_0 */
+  int32_t bern_repeats;/* independent Bernoulli estimates per chain (<= 1: one) */
 } orc_params;
 
 /* vMF mixture guide (Sec. 5.5): one lobe per sample of the last pass.  The
@@ -94,7 +95,10 @@ int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
 
 /* Bernoulli trials for admissible chains: N[b] = index of the first trial
  * that walks to the same solution, capped[b] = 1 when max_trials ran out,
- * trial_walks[b] (may be NULL) = trial walks that converged. */
+ * trial_walks[b] (may be NULL) = trial walks that converged.  With
+ * bern_repeats = r > 1 the estimate is repeated r times independently (repeat
+ * j draws trial t with trial counter t | j << 24) and N[b] is the sum of the
+ * r trial counts, so <1/P(x | n)> = N[b] / r; capped when any repeat capped. */
 int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
                       const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,

@@ -26,7 +26,8 @@ _u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 class orc_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("max_halvings", C.c_int32),
                 ("ray_eps", C.c_double), ("sing_eps", C.c_double), ("dedup_eps", C.c_double),
-                ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_double)]
+                ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_double),
+                ("bern_repeats", C.c_int32)]
 
 
 class orc_vmf(C.Structure):
@@ -100,7 +101,7 @@ def _c(a, dt):
 
 def params(p) -> orc_params:
     return orc_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps,
-                      p.max_trials, p.weight_shift, p.alpha)
+                      p.max_trials, p.weight_shift, p.alpha, int(getattr(p, "bern_repeats", 1)))
 
 
 def default_threads():
@@ -329,9 +330,13 @@ def adjoint(wl, scene, chains, weight, threads=None):
     return g, okf
 
 
+def _repeats(wl):
+    return max(1, int(getattr(wl.params, "bern_repeats", 1)))
+
+
 def irradiance(wl, T, N, admissible):
-    """E(x_D) = (1/M) sum_seeds A_L T <1/P>, <1/P> = N / P(n)   (Eq. ThroughputMC; Sec. 5.8)."""
-    c = np.where(admissible.astype(bool), wl.light_area * T * N.astype(np.float64) / wl.pn, 0.0)
+    """E(x_D) = (1/M) sum_seeds A_L T <1/P>, <1/P> = N / (repeats P(n))   (Eq. ThroughputMC; Sec. 5.8)."""
+    c = np.where(admissible.astype(bool), wl.light_area * T * N.astype(np.float64) / (_repeats(wl) * wl.pn), 0.0)
     return c.reshape(wl.Q, wl.spq).sum(axis=1) / wl.spq
 
 
@@ -343,7 +348,7 @@ def records(wl, chains, T, N, admissible, with_types=False):
     x1 = chains["x"][idx, 0, :]
     d = x1 - wl.xD[q]
     om = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
-    w = (T[idx] * N[idx].astype(np.float64) / wl.pn[idx]).astype(np.float32)
+    w = (T[idx] * N[idx].astype(np.float64) / (_repeats(wl) * wl.pn[idx])).astype(np.float32)
     if with_types:
         return (wl.cell[q].astype(np.uint32), om, w, wl.k[idx].astype(np.uint8),
                 chains["tau"][idx].astype(np.uint8))

@@ -73,6 +73,8 @@ struct mpg_ctx {
   int fp64_cap = 0;
   int* d_list[2] = {nullptr, nullptr};
   unsigned* d_nbest = nullptr;
+  uint32_t* d_nsum = nullptr;    // [B] sum of N over Bernoulli repeats when the caller keeps no trials
+  int nsum_cap = 0;
   uint32_t* d_rec = nullptr;     // per-tile counts of the ordered record compaction
   int rec_cap = 0;
   uint2* d_pairs = nullptr;      // [8B] converged trial walks of the parallel rounds (chain, trial)
@@ -273,7 +275,8 @@ mpg_status check_params(const mpg_params* p) {
       p->block_threads < 0 || p->block_threads > 128 || (p->block_threads % 32) != 0 || !(p->stall_tol >= 0.0f) ||
       !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
       p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
-      p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 3)
+      p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 3 ||
+      p->bern_repeats < 0 || p->bern_repeats > 64 || (p->bern_repeats > 1 && p->max_trials >= (1 << 24)))
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -390,7 +393,8 @@ void timed(mpg_ctx* ctx, int kind, cudaStream_t st, int n, F fn) {
 }
 
 DCtx dctx(mpg_ctx* ctx, int kind) {
-  return DCtx{ctx->d_err, ctx->stats_on ? ctx->d_stats + 16 * kind : nullptr, ctx->capturing ? ctx->cap_rng : nullptr};
+  return DCtx{ctx->d_err, ctx->stats_on ? ctx->d_stats + 16 * kind : nullptr, ctx->capturing ? ctx->cap_rng : nullptr,
+              0u};
 }
 
 // Runs fn(K, stream) for each planned K, on forked streams when concurrent.
@@ -482,7 +486,7 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   cudaFree(c->d_base); cudaFree(c->d_cursor); cudaFree(c->d_scratch);
   cudaFree(c->d_queue); cudaFree(c->d_nlist); cudaFree(c->d_zero); cudaFree(c->d_fp64); cudaFree(c->d_fp64_count);
   cudaFree(c->d_list[0]); cudaFree(c->d_list[1]); cudaFree(c->d_nbest); cudaFree(c->d_pairs); cudaFree(c->d_npairs);
-  cudaFree(c->d_rec);
+  cudaFree(c->d_rec); cudaFree(c->d_nsum);
   cudaFree(c->t_x); cudaFree(c->t_surf); cudaFree(c->t_prim); cudaFree(c->t_bary); cudaFree(c->t_status);
   cudaFree(c->t_iters);
   for (int i = 0; i < MAXK; ++i) {
@@ -791,7 +795,17 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     ctx->fp64_cap = c.B;
   }
   CUDA_TRY(cudaMemsetAsync(ctx->d_fp64_count, 0, sizeof(int) * (MAXK + 1), st));
-  DOut o{G, kappa, T, trials, capped, contrib, ctx->d_fp64, nullptr, nullptr};
+  const int repeats = std::max(1, P->bern_repeats);
+  if (repeats > 1 && !trials && ctx->nsum_cap < c.B) {  // the repeats' sum of N needs a home
+    if (ctx->capturing) return capture_grow_error();
+    cudaFree(ctx->d_nsum);
+    ctx->d_nsum = nullptr;
+    ctx->nsum_cap = 0;
+    CUDA_TRY(cudaMalloc(&ctx->d_nsum, sizeof(uint32_t) * (size_t)c.B));
+    ctx->nsum_cap = c.B;
+  }
+  DOut o{G, kappa, T, (repeats > 1 && !trials) ? ctx->d_nsum : trials, capped, contrib, ctx->d_fp64, nullptr, nullptr,
+         0, repeats};
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
   int block = block_of(P);
   if (plan.w.order) {
@@ -858,51 +872,62 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     const int* base = plan.w.base ? plan.w.base : ctx->d_zero;
     int* q = ctx->d_queue + 32 * K;
     int small_grid = ctx->sms * 4;
-    timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-      launch_trial_init(K, sc->S, c, plan.w, o, lists[0], base, counts[0], ctx->d_nbest, small_grid, s2);
-    });
-    int cur = 0;
-    for (int t = 1; t <= T1; ++t) {
-      int nxt = 1 - cur;
-      cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
-      DWork tw{lists[cur], base, counts[cur]};
+    for (int rep = 0; rep < repeats; ++rep) {  // independent estimates, trial counters t | rep << 24
+      DOut oR = o;
+      oR.rep = rep;
+      DCtx dcr = dcb;
+      dcr.trial_base = (uint32_t)rep << 24;
+      if (rep > 0) {  // this length's list lengths and queue counters start from zero again
+        cudaMemsetAsync(q, 0, sizeof(int) * 32, s2);
+        cudaMemsetAsync(counts[0] + K, 0, sizeof(int), s2);
+        cudaMemsetAsync(counts[1] + K, 0, sizeof(int), s2);
+      }
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-        launch_trial_seed(K, sc->S, guide ? &g : nullptr, c, tc, lists[cur], base, counts[cur], key, rng_offset, *P,
-                          dcb, t, grid_of(ctx, P, 5, K, block, c.B, true), block, s2);
+        launch_trial_init(K, sc->S, c, plan.w, oR, lists[0], base, counts[0], ctx->d_nbest, small_grid, s2);
       });
-      // trial walks run the walk kernel and are tallied with the walk family
-      timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
-        launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t,
-                      grid_of(ctx, P, walk_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
-      });
-      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
-        launch_trial_check(K, sc->S, c, tc, o, lists[cur], base, counts[cur], t, t == T1, *P, lists[nxt], counts[nxt],
-                           ctx->d_nbest, small_grid, s2);
-      });
-      cur = nxt;
-    }
-    long long TB = P->trial_batch > 0 ? P->trial_batch : 64;
-    int t0 = T1 + 1;
-    // 64-bit queue counter of the parallel rounds (two int slots, 8-byte aligned)
-    int* q64 = q + 10;
-    for (int r = 0; t0 <= P->max_trials; ++r) {
-      TB = std::min<long long>(TB, (long long)P->max_trials - t0 + 1);  // the last round reaches the cap
-      int t_end = t0 + (int)TB - 1;
-      int nxt = 1 - cur;
-      cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
-      cudaMemsetAsync(ctx->d_npairs + K, 0, sizeof(int), s2);
-      cudaMemsetAsync(q64, 0, sizeof(unsigned long long), s2);
-      DPairs pr{ctx->d_pairs, ctx->d_npairs + K, plan.w.count ? plan.w.count + K : nullptr, c.B};
-      timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
-        launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcb, q64,
-                          lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, (int)TB, pr,
-                          grid_of(ctx, P, round_which(P), K, round_block(P), c.B, true), round_block(P), s2);
-        launch_bern_finish(sc->S, c, o, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
-                           lists[nxt], counts[nxt] + K, pr, dcb.stats, ctx->sms, s2);
-      });
-      t0 = t_end + 1;
-      TB *= 4;
-      cur = nxt;
+      int cur = 0;
+      for (int t = 1; t <= T1; ++t) {
+        int nxt = 1 - cur;
+        cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
+        DWork tw{lists[cur], base, counts[cur]};
+        timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
+          launch_trial_seed(K, sc->S, guide ? &g : nullptr, c, tc, lists[cur], base, counts[cur], key, rng_offset, *P,
+                            dcr, t, grid_of(ctx, P, 5, K, block, c.B, true), block, s2);
+        });
+        // trial walks run the walk kernel and are tallied with the walk family
+        timed(ctx, MPG_KERNEL_WALK, s2, 1, [&] {
+          launch_walk_p(K, ctx->stats_on, sc->S, tc, tw, *P, dcw, q + t,
+                        grid_of(ctx, P, walk_which(P), K, walk_block(P), c.B, true), walk_block(P), s2);
+        });
+        timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {
+          launch_trial_check(K, sc->S, c, tc, oR, lists[cur], base, counts[cur], t, t == T1, *P, lists[nxt], counts[nxt],
+                             ctx->d_nbest, small_grid, s2);
+        });
+        cur = nxt;
+      }
+      long long TB = P->trial_batch > 0 ? P->trial_batch : 64;
+      int t0 = T1 + 1;
+      // 64-bit queue counter of the parallel rounds (two int slots, 8-byte aligned)
+      int* q64 = q + 10;
+      for (int r = 0; t0 <= P->max_trials; ++r) {
+        TB = std::min<long long>(TB, (long long)P->max_trials - t0 + 1);  // the last round reaches the cap
+        int t_end = t0 + (int)TB - 1;
+        int nxt = 1 - cur;
+        cudaMemsetAsync(counts[nxt] + K, 0, sizeof(int), s2);
+        cudaMemsetAsync(ctx->d_npairs + K, 0, sizeof(int), s2);
+        cudaMemsetAsync(q64, 0, sizeof(unsigned long long), s2);
+        DPairs pr{ctx->d_pairs, ctx->d_npairs + K, plan.w.count ? plan.w.count + K : nullptr, c.B};
+        timed(ctx, MPG_KERNEL_BERNOULLI, s2, 2, [&] {
+          launch_bern_round(K, ctx->stats_on, sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dcr, q64,
+                            lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t0, (int)TB, pr,
+                            grid_of(ctx, P, round_which(P), K, round_block(P), c.B, true), round_block(P), s2);
+          launch_bern_finish(sc->S, c, oR, lists[cur], counts[cur] + K, base + K, ctx->d_nbest, t_end, P->max_trials,
+                             lists[nxt], counts[nxt] + K, pr, dcb.stats, ctx->sms, s2);
+        });
+        t0 = t_end + 1;
+        TB *= 4;
+        cur = nxt;
+      }
     }
   });
   if (s) return s;

@@ -176,11 +176,7 @@ __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, co
     bool cap = !hit && t_end >= max_trials;
     if (hit && stats) atomicAdd(stats + 10, 1ull);  // the walk of trial N converged
     if (hit || cap) {
-      uint32_t N = hit ? nb : (uint32_t)max_trials;
-      if (o.trials) o.trials[b] = N;
-      if (o.capped) o.capped[b] = cap ? 1 : 0;
-      float pn = c.pn ? c.pn[b] : 1.0f;
-      o.contrib[b] = area * o.T[b] * (float)N / pn;
+      bern_write(area, c, o, b, o.T[b], hit ? nb : (uint32_t)max_trials, cap);
     } else {
       Nx[atomicAdd(n_next, 1)] = b;
     }

@@ -41,13 +41,32 @@ struct DOut {
   int* fp64_list;        // chains queued for the FP64 geometry term
   int* fp64_count;       // length of this chain length's queue
   const int* fp64_base;  // start of this chain length's region of fp64_list
+  int rep = 0;           // Bernoulli estimate being formed (0 .. repeats-1)
+  int repeats = 1;       // independent estimates averaged per chain
 };
 
 struct DCtx {
   int* err;                          // device error word
   unsigned long long* stats;         // [16] counters of the kernel family (mpg_stats layout)
   const unsigned long long* rng_add; // NULL, or a device counter added to rng offsets (captured graphs)
+  uint32_t trial_base;               // Bernoulli repeat j draws trial t as t | trial_base (= j << 24)
 };
+
+// Final outputs of a chain's Bernoulli estimate: N trials (capped when the
+// cap ran out).  Repeat j > 0 adds its N to the previous repeats' sum in
+// trials[b] (which then must not be NULL) and ORs its cap flag; contrib is
+// the running mean, A_L T (sum N) / (repeats P(n)), final after the last.
+__device__ __forceinline__ void bern_write(float area, const DChains& c, const DOut& o, int b, float T, uint32_t N,
+                                           bool cap) {
+  if (o.rep > 0) {
+    N += o.trials[b];
+    cap = cap || (o.capped && o.capped[b]);
+  }
+  if (o.trials) o.trials[b] = N;
+  if (o.capped) o.capped[b] = cap ? 1 : 0;
+  float pn = c.pn ? c.pn[b] : 1.0f;
+  o.contrib[b] = (T > 0.0f && N > 0) ? area * T * (float)N / ((float)o.repeats * pn) : 0.0f;
+}
 
 // Trial walks of a parallel Bernoulli round that converged to another
 // solution, as (chain, trial) pairs; the round's finish counts those below the

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
     int b = item<K>(w, c, i);
     if (b < 0) continue;
     float T = o.T[b];
-    uint32_t N = 0;
+    uint32_t N = 0;  // summed over the repeats
     bool cap = false;
     if (T > 0.0f) {
       Chain<K> target;
@@ -220,34 +220,37 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
       Ends e = load_ends(c, b);
       int q = b / c.spq;
       uint32_t cell = c.cell ? c.cell[q] : 0u;
-      cap = true;
-      for (int tr = 1; tr <= P.max_trials; ++tr) {
-        t.trials++;
-        Chain<K> ch;
-        uint32_t tau;
-        float pdf;
-        Ends et = e;
-        if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                              (uint64_t)b + offset, (uint32_t)tr, P, ch, tau, pdf, ctx.err, t.c, false, true))
-          continue;
-        if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
-        et.tau = tau;
-        int it;
-        int st = walk<K, kS>(S, ch, et, P, it, ctx.err, t.c);
-        t.walks++;
-        t.conv += st == ST_CONVERGED;
-        if (st == ST_CONVERGED && same_solution<K>(ch, target, eps2)) {
-          N = (uint32_t)tr;
-          cap = false;
-          break;
+      for (int rep = 0; rep < o.repeats; ++rep) {
+        bool cap_r = true;
+        for (int tr = 1; tr <= P.max_trials; ++tr) {
+          t.trials++;
+          Chain<K> ch;
+          uint32_t tau;
+          float pdf;
+          Ends et = e;
+          if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
+                                (uint64_t)b + offset, (uint32_t)tr | ((uint32_t)rep << 24), P, ch, tau, pdf, ctx.err,
+                                t.c, false, true))
+            continue;
+          if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
+          et.tau = tau;
+          int it;
+          int st = walk<K, kS>(S, ch, et, P, it, ctx.err, t.c);
+          t.walks++;
+          t.conv += st == ST_CONVERGED;
+          if (st == ST_CONVERGED && same_solution<K>(ch, target, eps2)) {
+            N += (uint32_t)tr;
+            cap_r = false;
+            break;
+          }
         }
+        if (cap_r) N += (uint32_t)P.max_trials;
+        cap = cap || cap_r;
       }
-      if (cap) N = (uint32_t)P.max_trials;
     }
-    if (o.trials) o.trials[b] = N;
-    if (o.capped) o.capped[b] = cap ? 1 : 0;
-    float pn = c.pn ? c.pn[b] : 1.0f;
-    o.contrib[b] = T > 0.0f ? S.L.area * T * (float)N / pn : 0.0f;
+    DOut one = o;  // the sum over all repeats is written at once
+    one.rep = 0;
+    bern_write(S.L.area, c, one, b, T, N, cap);
   }
   if (kS) flush(t, ctx.stats);
 }

@@ -370,15 +370,6 @@ __global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S
 // the same as in a sequential loop over t.
 // ---------------------------------------------------------------------------
 
-// Final outputs of one chain.
-__device__ __forceinline__ void bern_write(const DScene& S, const DChains& c, const DOut& o, int b, float T, uint32_t N,
-                                           bool cap) {
-  if (o.trials) o.trials[b] = N;
-  if (o.capped) o.capped[b] = cap ? 1 : 0;
-  float pn = c.pn ? c.pn[b] : 1.0f;
-  o.contrib[b] = (T > 0.0f && N > 0) ? S.L.area * T * (float)N / pn : 0.0f;
-}
-
 // Chains of this length with a contribution enter the rounds; the others get
 // their final (zero) outputs.
 template <int K>
@@ -392,7 +383,7 @@ __global__ void __launch_bounds__(256) k_trial_init(const __grid_constant__ DSce
       list[base[K] + atomicAdd(n_list + K, 1)] = b;
       nbest[b] = 0xffffffffu;  // no success yet
     } else {
-      bern_write(S, c, o, b, 0.0f, 0, false);
+      bern_write(S.L.area, c, o, b, 0.0f, 0, false);
     }
   }
 }
@@ -416,8 +407,8 @@ __global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DSce
     float pdf;
     tl.trials++;
     bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[b / c.spq] : 0u, e.tau,
-                               P.tau_random != 0, key, (uint64_t)b + offset, (uint32_t)t, P, ch, tau, pdf, ctx.err,
-                               tl.c, false, true) &&
+                               P.tau_random != 0, key, (uint64_t)b + offset, (uint32_t)t | ctx.trial_base, P, ch, tau,
+                               pdf, ctx.err, tl.c, false, true) &&
               tau == e.tau;
     if (ok) store_chain<K>(tc, b, ch);
     tc.status[b] = ok ? ST_SEEDED : ST_INVALID;
@@ -444,9 +435,9 @@ __global__ void __launch_bounds__(256) k_trial_check(const __grid_constant__ DSc
       hit = same_solution<K>(a, ref, eps2);
     }
     if (hit) {
-      bern_write(S, c, o, b, o.T[b], (uint32_t)t, false);
+      bern_write(S.L.area, c, o, b, o.T[b], (uint32_t)t, false);
     } else if (t >= P.max_trials) {
-      bern_write(S, c, o, b, o.T[b], (uint32_t)P.max_trials, true);
+      bern_write(S.L.area, c, o, b, o.T[b], (uint32_t)P.max_trials, true);
     } else {
       next[base[K] + atomicAdd(n_next + K, 1)] = b;
       if (last) nbest[b] = 0xffffffffu;
@@ -498,7 +489,7 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
         float pdf;
         uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
         if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                             (uint64_t)bb + offset, (uint32_t)tt, P, L.ch, tau, pdf, ctx.err, t.c, false, true) &&
+                             (uint64_t)bb + offset, (uint32_t)tt | ctx.trial_base, P, L.ch, tau, pdf, ctx.err, t.c, false, true) &&
             tau == e.tau) {
           b = bb;
           tr = tt;
@@ -594,7 +585,7 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
       uint32_t tau;
       float pdf;
       drawn = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
-                               (uint64_t)bb + offset, (uint32_t)tt, P, ch, tau, pdf, ctx.err, j == 0 ? t.c : dummy,
+                               (uint64_t)bb + offset, (uint32_t)tt | ctx.trial_base, P, ch, tau, pdf, ctx.err, j == 0 ? t.c : dummy,
                                false, true) &&
               tau == e.tau;
     }

@@ -90,6 +90,7 @@ class Params:
     weight_shift: int = 16       # histogram weight quantisation q = floor(w * 2^S)
     stall_tol: float = 2e-5      # FP32 walks only: stalled line search within this |C| counts as converged
     fp64_tol: float = 1e-4       # FP32 G recomputed in FP64 when its two reciprocal forms differ by more
+    bern_repeats: int = 1        # independent Bernoulli estimates averaged per chain
 
 
 @dataclasses.dataclass

@@ -394,3 +394,40 @@ def test_autograd_function_gradient(M, ctx):
     M.mpg_walk_adjoint(ctx, fn.last_scene, fn.last_chains, fn.last_out.T, fn.last_out.contrib, dLdE, g2)
     ctx.sync()
     assert torch.allclose(h.grad, g2, rtol=1e-4, atol=1e-6 * g2.abs().max().item())
+
+
+@pytest.mark.parametrize("mode", ["batched", "plain"])
+def test_repeated_bernoulli_estimates(M, ctx, mode):
+    """Four independent Bernoulli estimates per chain (trial counters
+    t | j << 24): the summed trial counts equal the oracle's where both sides
+    walked the same chains, contributions use their mean, and the sum needs no
+    caller-kept trial array."""
+    wl = I.glass_sphere(n=32, spq=16)
+    wl = dataclasses.replace(wl, params=dataclasses.replace(wl.params, bern_repeats=4))
+    P = _params(M, wl, mode=M.WALK_PLAIN if mode == "plain" else M.WALK_BATCHED)
+    assert P.bern_repeats == 4
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    both = _compare_walk(wl, gw, ow)
+    G = out.G.cpu().numpy()
+    ab = (G > 0) & (con["admissible"] == 1) & both
+    assert ab.sum() > 1000
+    gN = out.trials.cpu().numpy().astype(np.int64)
+    assert np.all(gN[G > 0] >= 4)
+    # the per-estimate bar (equal trial counts on >= 99.9 % of the chains both
+    # sides walked alike) compounds over four independent estimates: the sum
+    # matches only when all four do, >= 1 - 4 x 0.001
+    assert (gN[ab] == N[ab]).mean() >= 1 - 4 * 0.001
+    T = out.T.cpu().numpy().astype(np.float64)
+    c = out.contrib.cpu().numpy()
+    assert np.allclose(c[G > 0], (wl.light_area * T * gN / (4 * wl.pn))[G > 0], rtol=1e-6)
+    # without a caller-kept trial array the library keeps the sum itself.
+    # (The first call polished its FP64-queued chains in place, so both runs
+    # compared here start from the chains as the first call left them.)
+    ref = M.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 0)
+    res = M.Contribution.empty(wl.B, wl.Q)
+    res.trials = None
+    M.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 0, out=res)
+    ctx.sync()
+    assert torch.equal(res.contrib, ref.contrib)
+    assert torch.equal(ref.trials, out.trials)
