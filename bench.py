@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -466,7 +466,9 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     - adjoint: the adjoint of the water irradiance with respect to the heights;
     - vmf: the vMF mixture guide with sampled chain lengths on the mixed batch;
     - repeats: four Bernoulli estimates per chain in rendering (R x 4) or in
-      training and rendering (TR x 4) on the guided glass-sphere step."""
+      training and rendering (TR x 4) on the guided glass-sphere step;
+    - progressive: the online training schedule and rendering of a
+      64-seed-per-point budget on the glass sphere, as one captured graph."""
     import numpy as np
     from paper_2311_12818_gb300 import inputs as I
     from paper_2311_12818_gb300 import mpg
@@ -490,6 +492,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["vmf_guide"] = part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "repeats" in parts:
         out["repeated_estimates"] = part_repeats(ctx, dev, flush, torch, stream, steps)
+    if "progressive" in parts:
+        out["progressive"] = part_progressive(ctx, dev, flush, torch, stream, max(2, steps // 5))
     if "mixed_group" in parts and parts == ("mixed_group",):
         out["mixed_group"] = part_mixed_group(ctx, dev, flush, torch, stream, steps)
     return out
@@ -829,6 +833,59 @@ def part_repeats(ctx, dev, flush, torch, stream, steps):
     for name in ("R_x4", "TR_x4"):
         out[name]["variance_vs_single"] = out[name]["per_point_variance_of_E"] / out["single"]["per_point_variance_of_E"]
         out[name]["time_vs_single"] = out[name]["ms_per_step"] / out["single"]["ms_per_step"]
+    return out
+
+
+def part_progressive(ctx, dev, flush, torch, stream, steps):
+    """Online training and rendering (Sec. 5.8) of the glass-sphere image with
+    a budget of 64 seeds per receiver point (256 x 256 points): training
+    iterations of 1, 2, 4 and 12 seeds per point, each building the next guide
+    from its own records, then 45 seeds per point of rendering; the whole
+    schedule is one captured graph.  Two replays at independent random numbers
+    give the per-point variance of the image (half the mean squared
+    difference), against the same for 64 seeds per point from p_0 alone."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    from paper_2311_12818_gb300 import progressive as PG
+    out = {"workload": "glass_sphere_k2, 256 x 256 points, 64 seeds per point in total"}
+
+    def variance(a, b):
+        return float(((a - b) ** 2).mean().item() / 2)
+    for kind in ("histogram", "vmf"):
+        pr = PG.Progressive(ctx, PG.glass_sphere_stages(n=256), total_spp=64, guide=kind, device=dev)
+        pr.run(0)
+        ctx.sync()
+        gr = pr.capture(offset=1 << 44, advance=1 << 40)
+        ctx.reset_stats()
+        ms = timed_loop(lambda i: gr.launch(), steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        per = steps + 2
+        gr.launch()
+        ctx.sync()
+        a = pr.image.double().clone()
+        gr.launch()
+        ctx.sync()
+        out[kind] = {"plan_spp": pr.plan, "render_spp": pr.render_spp, "chains": pr.total_chains(),
+                     "ms_per_schedule": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+                     "graph_kernels": gr.kernels(), "mean_E": float(a.mean().item()),
+                     "per_point_variance_of_E": variance(a, pr.image.double())}
+        del gr, pr
+    wl = I.glass_sphere(n=256, spq=64)
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, k_uniform=2)
+    imgs = []
+    for o in (1 << 44, (1 << 44) + (1 << 40)):
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, o)
+        mpg.mpg_manifold_walk(ctx, sc, ch, P)
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, o, out=res)
+        ctx.sync()
+        imgs.append(res.E.double().clone())
+    out["p0_only"] = {"spp": 64, "chains": wl.B, "mean_E": float(imgs[0].mean().item()),
+                      "per_point_variance_of_E": variance(imgs[0], imgs[1])}
+    for kind in ("histogram", "vmf"):
+        out[kind]["variance_vs_p0_only"] = out[kind]["per_point_variance_of_E"] / out["p0_only"]["per_point_variance_of_E"]
     return out
 
 

@@ -441,6 +441,20 @@ mpg_status mpg_graph_launch(mpg_graph* graph, cudaStream_t stream);
 mpg_status mpg_graph_kernels(const mpg_graph* graph, int64_t* count);
 void mpg_graph_destroy(mpg_graph* graph);
 
+/* Sample schedule of the progressive training (Sec. 5.8, online training and
+ * rendering), in seeds per receiver point: training iterations of first_spp,
+ * 2 first_spp, 4 first_spp, ... seeds; training never uses more than
+ * floor(train_fraction * total_spp) seeds (an iteration that would pass it is
+ * cut there); after an iteration a new one starts only while less than half
+ * of the training budget is used, otherwise the current iteration continues
+ * until the training budget is spent.  Writes the iterations' seed counts to
+ * iter_spp[0 .. *n_iters) (room for max_iters) and the rendering budget
+ * total_spp - (training seeds) to *render_spp.  Each iteration's guide is
+ * built from its own samples only, and training samples are not splatted
+ * into the image.  Host-only: no device or context. */
+mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_fraction, int32_t max_iters,
+                             int32_t* iter_spp, int32_t* n_iters, int32_t* render_spp);
+
 /* Autotuner of the batched schedule (block_threads, ctas_per_sm, walk_group,
  * refill_every, trial_sync_rounds, trial_batch, fp64_k).  Times candidate
  * schedules by running the step seeds -> walk -> contribution on the given

@@ -7,6 +7,7 @@ stated, array-of-structures: x[B, 8, 3], surf/prim[B, 8], bary[B, 8, 2].
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 
 import numpy as np
@@ -189,6 +190,30 @@ class VmfGuide:
         return orc_guide(None, self.n_cells, 0, 0, None, None, None, C.addressof(self._v))
 
 
+def training_plan(total_spp, first_spp=1, train_fraction=0.3):
+    """Seeds per point of the training iterations and of rendering, following
+    the online training of Sec. 5.8 step by step: the sample count doubles
+    each iteration; training stops as soon as train_fraction of the budget is
+    used; when an iteration ends, a new one starts if less than half of the
+    training budget is used, else the current one continues until training
+    ends.  Returns (iteration counts, rendering count)."""
+    budget = math.floor(train_fraction * total_spp)
+    iters = []
+    used, size = 0, first_spp
+    while used < budget:
+        take = min(size, budget - used)          # stop immediately at the training budget
+        iters.append(take)
+        used += take
+        if used >= budget:
+            break
+        if used < budget / 2:                    # start a new, doubled iteration
+            size *= 2
+        else:                                    # continue the current iteration
+            iters[-1] += budget - used
+            used = budget
+    return iters, total_spp - used
+
+
 def sample_lengths(wl, guide, p0w, rng_offset=0):
     """Chain lengths and P(n) from the defensive mixture of P_0 (integer weights
     p0w[n-1]) and the vMF guide's P_e(n | cell) (Sec. 5.5)."""
@@ -364,3 +389,35 @@ def run(wl, guide=None, threads=None, max_trials=None):
     N, capped = bernoulli(wl, sc, ch, con["admissible"], guide, threads=threads, max_trials=max_trials)
     E = irradiance(wl, con["T"], N, con["admissible"])
     return dict(scene=sc, seeds=seeds, chains=ch, contrib=con, N=N, capped=capped, E=E)
+
+
+def progressive(make_workload, total_spp, first_spp=1, train_fraction=0.3, guide="histogram", threads=None):
+    """Online training and rendering (Sec. 5.8) in the oracle: each training
+    iteration samples from the guide of the previous one (p_0 first) and its
+    records alone build the next guide; the rendering stage's irradiance is
+    the image.  Stage i draws its random numbers at offset i * 2^36.
+    Returns (plan, render spp, per-stage dicts, image)."""
+    from paper_2311_12818_gb300 import inputs as I
+    plan, render = training_plan(total_spp, first_spp, train_fraction)
+    wls = [make_workload(s, i) for i, s in enumerate(plan + [render])]
+    sc = Scene(wls[0])
+    g = None
+    stages = []
+    for i, wl in enumerate(wls):
+        o = i << 36
+        seeds = sample_seeds(wl, sc, g, threads=threads, rng_offset=o)
+        ch = walk(wl, sc, seeds, threads=threads)
+        con = contribution(wl, sc, ch, threads=threads)
+        N, capped = bernoulli(wl, sc, ch, con["admissible"], g, threads=threads, rng_offset=o)
+        stages.append(dict(wl=wl, seeds=seeds, chains=ch, contrib=con, N=N, guide=g))
+        if i == len(plan):
+            break
+        cell, om, w, k, tau = records(wl, ch, con["T"], N, con["admissible"], with_types=True)
+        if guide == "histogram":
+            g = Guide(wl.n_cells, I.guide_edges())
+            g.update(cell, om, w, wl.params.weight_shift)
+        else:
+            g = VmfGuide(wl.n_cells).build(cell, om, w, k, tau, wl.params.weight_shift)
+    last = stages[-1]
+    image = irradiance(last["wl"], last["contrib"]["T"], last["N"], last["contrib"]["admissible"])
+    return plan, render, stages, image

@@ -1220,6 +1220,32 @@ void mpg_graph_destroy(mpg_graph* g) {
 // ---------------------------------------------------------------------------
 // Autotuner of the batched schedule.
 // ---------------------------------------------------------------------------
+mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_fraction, int32_t max_iters,
+                             int32_t* iter_spp, int32_t* n_iters, int32_t* render_spp) {
+  if (total_spp < 0 || first_spp < 1 || !(train_fraction >= 0.0f && train_fraction <= 1.0f) || max_iters < 0 ||
+      !n_iters || !render_spp || (max_iters > 0 && !iter_spp))
+    return fail(MPG_ERR_INVALID_ARG, "invalid training plan arguments");
+  const int64_t budget = (int64_t)std::floor((double)train_fraction * (double)total_spp);
+  int64_t used = 0, next = first_spp;
+  int n = 0;
+  while (used < budget) {
+    if (n == max_iters) return fail(MPG_ERR_LIMIT, "training plan needs more than %d iterations", max_iters);
+    const int64_t cur = std::min(next, budget - used);  // cut at the training budget
+    iter_spp[n++] = (int32_t)cur;
+    used += cur;
+    if (used >= budget) break;
+    if (2 * used < budget) {  // less than half of the training budget used: a new iteration
+      next *= 2;
+    } else {  // otherwise the current iteration continues until the budget is spent
+      iter_spp[n - 1] += (int32_t)(budget - used);
+      used = budget;
+    }
+  }
+  *n_iters = n;
+  *render_spp = (int32_t)(total_spp - used);
+  return MPG_OK;
+}
+
 mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guide, mpg_chains* chains,
                         uint64_t rng_seed, uint64_t rng_offset, const mpg_params* in, int32_t repeats,
                         mpg_params* out, double* best_ms, cudaStream_t st) {

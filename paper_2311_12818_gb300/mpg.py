@@ -80,7 +80,7 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
-           "mpg_sample_lengths"]
+           "mpg_sample_lengths", "mpg_training_plan"]
 
 _lib = None
 
@@ -118,6 +118,7 @@ def lib():
         L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
         L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_vmf_build.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, vp, vp, i32, vp, i32, vp]
+        L.mpg_training_plan.argtypes = [i32, i32, f32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.mpg_sample_lengths.argtypes = [vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), vp, u64, u64,
                                          C.POINTER(mpg_params), vp, vp, vp]
         L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp]
@@ -496,6 +497,15 @@ def mpg_vmf_build(ctx, guide, cell, omega, w, k, tau, R=None, R_dev=None, weight
     gs = guide.struct()
     _check(lib().mpg_vmf_build(ctx.h, C.byref(gs), _ptr(cell), _ptr(omega), _ptr(w), _ptr(k), _ptr(tau), R,
                                _ptr(R_dev), weight_shift, _stream(stream)))
+
+
+def mpg_training_plan(total_spp, first_spp=1, train_fraction=0.3, max_iters=32):
+    """Seeds per point of each training iteration and of the rendering stage
+    (Sec. 5.8, online training): returns (list of iteration counts, render count)."""
+    it = (C.c_int32 * max_iters)()
+    n, r = C.c_int32(), C.c_int32()
+    _check(lib().mpg_training_plan(total_spp, first_spp, train_fraction, max_iters, it, C.byref(n), C.byref(r)))
+    return [int(it[i]) for i in range(n.value)], int(r.value)
 
 
 def mpg_sample_lengths(ctx, guide, chains, p0_weights, params, rng_seed, rng_offset=0, out=None, stream=None):
