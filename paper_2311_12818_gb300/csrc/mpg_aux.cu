@@ -1,6 +1,7 @@
 // Small kernels around the hot path: k-bucketing of the work list, the
-// per-point irradiance reduction, the guide histogram (update, prefix sums,
-// records), a standalone ray batch and an FP32 peak probe.
+// per-point irradiance reduction, the guide histogram (update, prefix sums;
+// the records are compacted in mpg_vmf.cu), the end of a Bernoulli round, a
+// standalone ray batch and the FP32 / FP64 peak probes.
 #include "mpg_aux.cuh"
 
 namespace mpg {
