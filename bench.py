@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -467,6 +467,7 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     - vmf: the vMF mixture guide with sampled chain lengths on the mixed batch;
     - repeats: four Bernoulli estimates per chain in rendering (R x 4) or in
       training and rendering (TR x 4) on the guided glass-sphere step;
+    - selective: the guided glass-sphere step with selective activation;
     - progressive: the online training schedule and rendering of a
       64-seed-per-point budget on the glass sphere, as one captured graph."""
     import numpy as np
@@ -492,6 +493,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["vmf_guide"] = part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "repeats" in parts:
         out["repeated_estimates"] = part_repeats(ctx, dev, flush, torch, stream, steps)
+    if "selective" in parts:
+        out["selective_activation"] = part_selective(ctx, dev, flush, torch, stream, steps)
     if "progressive" in parts:
         out["progressive"] = part_progressive(ctx, dev, flush, torch, stream, max(2, steps // 5))
     if "mixed_group" in parts and parts == ("mixed_group",):
@@ -833,6 +836,54 @@ def part_repeats(ctx, dev, flush, torch, stream, steps):
     for name in ("R_x4", "TR_x4"):
         out[name]["variance_vs_single"] = out[name]["per_point_variance_of_E"] / out["single"]["per_point_variance_of_E"]
         out[name]["time_vs_single"] = out[name]["ms_per_step"] / out["single"]["ms_per_step"]
+    return out
+
+
+def part_selective(ctx, dev, flush, torch, stream, steps):
+    """Selective activation (Sec. 5.8) on the benchmark's guided glass-sphere
+    step: points whose guide cell holds no weight after the p_0 training pass
+    draw no seed.  Step time and active fraction with and without it; the
+    image of the active points is unchanged (same seeds)."""
+    import dataclasses
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.glass_sphere()
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    g = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, k_uniform=2)
+    mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40)
+    mpg.mpg_manifold_walk(ctx, sc, ch, P)
+    mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40, out=res)
+    rec = mpg.mpg_guide_records(ctx, sc, ch, res.contrib)
+    mpg.mpg_guide_update(ctx, g, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[3], weight_shift=wl.params.weight_shift)
+    ctx.sync()
+    active_cells = (g.counts.sum(dim=1) > 0).cpu()
+    active = float(active_cells[torch.as_tensor(wl.cell.astype("int64"))].float().mean().item())
+    out = {"workload": "glass_sphere_k2 guided, 1,048,576 chains", "active_point_fraction": active}
+    images = {}
+    for name, sel in (("off", 0), ("on", 1)):
+        Ps = mpg.params_from(dataclasses.replace(wl.params, selective=sel), walk_mode=mpg.WALK_BATCHED, k_uniform=2)
+
+        def step(o, Ps=Ps):
+            mpg.mpg_sample_seeds(ctx, sc, g, ch, Ps, wl.rng_seed, o)
+            mpg.mpg_manifold_walk(ctx, sc, ch, Ps)
+            mpg.mpg_chain_contribution(ctx, sc, g, ch, Ps, wl.rng_seed, o, out=res)
+        step(3 << 32)
+        ctx.sync()
+        images[name] = res.E.clone()
+        gr = mpg.Graph(ctx, rng_advance=wl.B)
+        with gr:
+            step(3 << 32)
+        ctx.reset_stats()
+        ms = timed_loop(lambda i: gr.launch(), steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        out[name] = {"ms_per_step": ms, "seeds_per_step": st["seeds"] / (steps + 2),
+                     "converged_per_step": st["converged"] / (steps + 2)}
+    pts = torch.as_tensor(active_cells.numpy()[wl.cell.astype("int64")], device=dev)
+    out["image_equal_on_active_points"] = bool(torch.equal(images["off"][pts], images["on"][pts]))
+    out["on"]["time_vs_off"] = out["on"]["ms_per_step"] / out["off"]["ms_per_step"]
     return out
 
 

@@ -111,12 +111,18 @@ typedef struct mpg_params {
                            results agree to FP32 rounding, not bit for bit    */
   int32_t bern_repeats; /* Bernoulli: independent reciprocal-probability
                            estimates averaged per chain (0 or 1 = one; up to 64;
-                           the paper's repeated estimation, Sec. 6 performance
-                           analysis).  Repeat j draws trial t from counter
+                           the paper's repeated estimation, Sec. 6.5
+                           performance analysis).  Repeat j draws trial t from counter
                            (b + offset, t | j << 24, block), so repeat 0 is the
                            single estimate; trials[b] is the sum of the N_j,
                            <1/P> = trials[b] / (repeats P(n)), capped is set when
                            any repeat ran out of trials                        */
+  int32_t selective;    /* selective activation (Sec. 5.8): with a guide, seeds
+                           of receiver points whose cell holds no samples (no
+                           histogram weight; no lobes) are not drawn -- the
+                           chain is MPG_CHAIN_INVALID at once and contributes
+                           nothing; the paper hands such points to path
+                           tracing, which this library does not do          */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */

@@ -922,6 +922,7 @@ static SeedDraw sample_seed(const Scene& S, const orc_guide* g, const GuideCDF* 
   philox4x32_10(c0, key, r0);
   philox4x32_10(c1, key, r1);
   uint8_t tau = tau_random ? (uint8_t)(r1[1] & ((1u << k) - 1u)) : tau_in;
+  sd.tau = tau;  // the guided vMF component may replace it below
   uint64_t total = 0;
   const orc_vmf* vm = g ? g->vmf : nullptr;
   LobeRange lr;
@@ -934,9 +935,12 @@ static SeedDraw sample_seed(const Scene& S, const orc_guide* g, const GuideCDF* 
     lr = lobe_range(*vm, cell, klo, khi);
     total = lr.total;
     use_guide = total > 0;
+    // selective activation (Sec. 5.8): no sample in the cell, no seed
+    if (prm.selective && vm->cell_start[cell] == vm->cell_start[cell + 1]) return sd;
   } else {
     use_guide = g && g->counts && cdf;
     if (use_guide) total = cdf->cdf[(size_t)cell * cdf->bins + cdf->bins - 1];
+    if (prm.selective && use_guide && total == 0) return sd;  // selective activation
     use_guide = use_guide && total > 0;
   }
   bool pick_p0 = !use_guide || u01(r0[0]) < prm.alpha;

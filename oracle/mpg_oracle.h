@@ -38,6 +38,7 @@ typedef struct orc_params {
   int32_t weight_shift;/* histogram quantisation shift S */
   double alpha;        /* defensive mixture weight of p_0 */
   int32_t bern_repeats;/* independent Bernoulli estimates per chain (<= 1: one) */
+  int32_t selective;   /* selective activation: with a guide, no seed in a cell without samples */
 } orc_params;
 
 /* vMF mixture guide (Sec. 5.5): one lobe per sample of the last pass.  The

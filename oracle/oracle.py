@@ -28,7 +28,7 @@ class orc_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("max_halvings", C.c_int32),
                 ("ray_eps", C.c_double), ("sing_eps", C.c_double), ("dedup_eps", C.c_double),
                 ("max_trials", C.c_int32), ("weight_shift", C.c_int32), ("alpha", C.c_double),
-                ("bern_repeats", C.c_int32)]
+                ("bern_repeats", C.c_int32), ("selective", C.c_int32)]
 
 
 class orc_vmf(C.Structure):
@@ -102,7 +102,8 @@ def _c(a, dt):
 
 def params(p) -> orc_params:
     return orc_params(p.tol, p.max_iter, p.max_halvings, p.ray_eps, p.sing_eps, p.dedup_eps,
-                      p.max_trials, p.weight_shift, p.alpha, int(getattr(p, "bern_repeats", 1)))
+                      p.max_trials, p.weight_shift, p.alpha, int(getattr(p, "bern_repeats", 1)),
+                      int(getattr(p, "selective", 0)))
 
 
 def default_threads():

@@ -276,7 +276,8 @@ mpg_status check_params(const mpg_params* p) {
       !(p->fp64_tol >= 0.0f) || p->fp64_k < 0 || p->fp64_k > 6 || p->ctas_per_sm < 0 || p->ctas_per_sm > 64 ||
       p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
       p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 3 ||
-      p->bern_repeats < 0 || p->bern_repeats > 64 || (p->bern_repeats > 1 && p->max_trials >= (1 << 24)))
+      p->bern_repeats < 0 || p->bern_repeats > 64 || (p->bern_repeats > 1 && p->max_trials >= (1 << 24)) ||
+      p->selective < 0 || p->selective > 1)
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }

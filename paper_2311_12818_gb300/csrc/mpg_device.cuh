@@ -857,9 +857,9 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   if (kStats) cnt.seeds++;
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
+  tau_out = tau;  // the guided vMF component may replace it below
   const bool vmf = g != nullptr && g->kind == MPG_GUIDE_VMF;
   if (!vmf) {
-    tau_out = tau;
     // a Bernoulli trial must sample the chain's own types: when it drew others it
     // has failed already, before any ray is cast
     if (need_tau_in && tau != tau_in) return false;
@@ -874,6 +874,8 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     use_guide = false;
   }
   if (use_guide && vmf) {
+    // selective activation: a cell without any lobe is not sampled at all
+    if (P.selective && __ldg(g->cell_start + cell) == __ldg(g->cell_start + cell + 1)) return false;
     // the guided component draws (w, tau) given n, or w given n and tau when
     // the types are fixed
     uint32_t klo = ((uint32_t)K << 8) | (tau_random ? 0u : tau_in);
@@ -885,6 +887,7 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     cdf = g->cdf + (size_t)cell * g->bins;
     total = __ldg(reinterpret_cast<const unsigned long long*>(cdf + g->bins - 1));
     use_guide = total > 0;
+    if (P.selective && !use_guide) return false;  // selective activation: an empty cell is not sampled
   }
   bool pick_p0 = !use_guide || u01(r0.x) < P.alpha;
   uint32_t li = 0;

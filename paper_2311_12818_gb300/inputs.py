@@ -91,6 +91,7 @@ class Params:
     stall_tol: float = 2e-5      # FP32 walks only: stalled line search within this |C| counts as converged
     fp64_tol: float = 1e-4       # FP32 G recomputed in FP64 when its two reciprocal forms differ by more
     bern_repeats: int = 1        # independent Bernoulli estimates averaged per chain
+    selective: int = 0           # selective activation: no seeds where the guide's cell is empty
 
 
 @dataclasses.dataclass

@@ -38,7 +38,7 @@ class mpg_params(C.Structure):
                 ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float),
                 ("fp64_k", C.c_int32), ("ctas_per_sm", C.c_int32), ("refill_every", C.c_int32),
                 ("trial_sync_rounds", C.c_int32), ("trial_batch", C.c_int32), ("walk_group", C.c_int32),
-                ("bern_repeats", C.c_int32)]
+                ("bern_repeats", C.c_int32), ("selective", C.c_int32)]
 
 SCHEDULE_FIELDS = ["block_threads", "ctas_per_sm", "refill_every", "trial_sync_rounds", "trial_batch", "fp64_k",
                    "walk_group"]
@@ -162,6 +162,7 @@ def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_
                    p.weight_shift, p.alpha, walk_mode, block_threads, int(bool(tau_random)), k_uniform,
                    p.stall_tol, p.fp64_tol)
     P.bern_repeats = int(getattr(p, "bern_repeats", 1))
+    P.selective = int(getattr(p, "selective", 0))
     for f, v in schedule.items():
         if f not in SCHEDULE_FIELDS:
             raise TypeError("unknown schedule field %r" % f)

@@ -431,3 +431,42 @@ def test_repeated_bernoulli_estimates(M, ctx, mode):
     ctx.sync()
     assert torch.equal(res.contrib, ref.contrib)
     assert torch.equal(ref.trials, out.trials)
+
+
+@pytest.mark.parametrize("kind", ["histogram", "vmf"])
+def test_selective_activation(M, ctx, kind):
+    """Selective activation (Sec. 5.8): seeds of points whose guide cell is
+    empty are not drawn; all other seeds are those drawn without it, on both
+    sides.  The guide holds the oracle's records of every other cell."""
+    wl = I.glass_sphere(n=32, spq=4)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    cell, om, w, k, tau = O.records(wl, ow, con["T"], N, con["admissible"], with_types=True)
+    keep = (cell % 2) == 0
+    recs = (cell[keep], om[keep], w[keep], k[keep], tau[keep])
+    dev = (torch.as_tensor(recs[0].astype(np.int32), device="cuda"),
+           torch.as_tensor(np.ascontiguousarray(recs[1].T), device="cuda"), torch.as_tensor(recs[2], device="cuda"),
+           torch.as_tensor(recs[3], device="cuda"), torch.as_tensor(recs[4], device="cuda"))
+    if kind == "histogram":
+        og = O.Guide(wl.n_cells, I.guide_edges())
+        og.update(recs[0], recs[1], recs[2], wl.params.weight_shift)
+        gg = M.Guide(wl.n_cells, I.guide_edges())
+        M.mpg_guide_update(ctx, gg, dev[0], dev[1], dev[2], weight_shift=wl.params.weight_shift)
+        cells = np.nonzero(og.counts.sum(axis=1) > 0)[0]
+    else:
+        og = O.VmfGuide(wl.n_cells).build(*recs, wl.params.weight_shift)
+        gg = M.VmfGuide(wl.n_cells, recs[0].size)
+        M.mpg_vmf_build(ctx, gg, *dev, weight_shift=wl.params.weight_shift)
+        cells = np.nonzero(np.diff(og.cell_start) > 0)[0]
+    on = dataclasses.replace(wl, params=dataclasses.replace(wl.params, selective=1))
+    P = _params(M, on)
+    assert P.selective == 1
+    sc = M.Scene(ctx, on)
+    ch = M.Chains(on)
+    M.mpg_sample_seeds(ctx, sc, gg, ch, P, on.rng_seed, 77)
+    ctx.sync()
+    gs = ch.aos()
+    os2 = O.sample_seeds(on, O.Scene(on), og, rng_offset=77)
+    active = np.isin(np.repeat(wl.cell, wl.spq), cells)
+    assert 0.2 < active.mean() < 0.8
+    assert not (gs["status"] != 0)[~active].any() and not os2["valid"][~active].any()
+    _compare_seeds(on, gs, os2)

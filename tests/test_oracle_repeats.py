@@ -1,5 +1,5 @@
 """Pin of the repeated reciprocal-probability estimate (the paper's R x 4 /
-TR x 4 variants, Sec. 6): r independent Bernoulli estimates per chain are
+TR x 4 variants, Sec. 6.5): r independent Bernoulli estimates per chain are
 averaged, so on a single-solution configuration N / r keeps the mean 1/P of
 the geometric trial count and its variance falls to (1 - P) / (r P^2)."""
 import dataclasses
