@@ -1544,23 +1544,24 @@ int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const d
                          uint64_t rng_seed, uint64_t rng_offset, uint32_t trial,
                          const orc_params* prm, double* x, int32_t* surf, int32_t* prim,
                          double* bary, uint8_t* tau_out, double* pdf, uint8_t* valid,
-                         int32_t n_threads) {
+                         int32_t n_threads, const uint32_t* chain_cell) {
   if (!scene || !prm || Q < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   orc_params P = default_check(prm);
   GuideCDF cdf;
   bool g_ok = guide && (guide->counts || guide->vmf);
   if (g_ok && !guide->vmf) guide_cdf(*guide, cdf);
-  if (g_ok && guide->vmf && cell)
-    for (int q = 0; q < Q; ++q)
-      if ((int)cell[q] >= guide->vmf->n_cells) return -3;
   int B = Q * spq;
+  auto cell_of = [&](int b) { return chain_cell ? chain_cell[b] : (cell ? cell[b / spq] : 0u); };
+  if (g_ok && guide->vmf)
+    for (int b = 0; b < B; ++b)
+      if ((int)cell_of(b) >= guide->vmf->n_cells) return -3;
   for (int b = 0; b < B; ++b)
     if (k[b] < 1 || k[b] > MAXK) return -2;
   parallel_for(B, n_threads, [&](int b) {
     int q = b / spq;
     SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, load3(xD + 3 * (size_t)q),
-                              load3(nD + 3 * (size_t)q), cell ? cell[q] : 0u, load3(xL + 3 * (size_t)b),
+                              load3(nD + 3 * (size_t)q), cell_of(b), load3(xL + 3 * (size_t)b),
                               k[b], tau[b], tau_random != 0, rng_seed, (uint64_t)b + rng_offset, trial, P);
     valid[b] = sd.valid ? 1 : 0;
     pdf[b] = sd.valid ? sd.pdf : 0.0;
@@ -1626,17 +1627,19 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
-                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads) {
+                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads,
+                      const uint32_t* chain_cell) {
   if (!scene || !prm || Q < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   orc_params P = *prm;
   GuideCDF cdf;
   bool g_ok = guide && (guide->counts || guide->vmf);
   if (g_ok && !guide->vmf) guide_cdf(*guide, cdf);
-  if (g_ok && guide->vmf && cell)
-    for (int q = 0; q < Q; ++q)
-      if ((int)cell[q] >= guide->vmf->n_cells) return -3;
   int B = Q * spq;
+  auto cell_of = [&](int b) { return chain_cell ? chain_cell[b] : (cell ? cell[b / spq] : 0u); };
+  if (g_ok && guide->vmf)
+    for (int b = 0; b < B; ++b)
+      if ((int)cell_of(b) >= guide->vmf->n_cells) return -3;
   parallel_for(B, n_threads, [&](int b) {
     N[b] = 0;
     capped[b] = 0;
@@ -1651,7 +1654,7 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
       bool hit = false;
       for (int t = 1; t <= P.max_trials && !hit; ++t) {
         SeedDraw sd = sample_seed(S, g_ok ? guide : nullptr, g_ok ? &cdf : nullptr, xd, nd,
-                                  cell ? cell[q] : 0u, xl, k[b], tau[b], tau_random != 0, rng_seed,
+                                  cell_of(b), xl, k[b], tau[b], tau_random != 0, rng_seed,
                                   (uint64_t)b + rng_offset, (uint32_t)t | ((uint32_t)rep << 24), P);
         if (!sd.valid) continue;
         int it = 0;
@@ -1728,17 +1731,17 @@ int32_t orc_vmf_build(int32_t n_cells, int32_t R, const uint32_t* cell, const fl
 
 int32_t orc_sample_lengths(const orc_guide* guide, int32_t Q, const uint32_t* cell, int32_t spq,
                            const uint32_t* p0w, uint64_t rng_seed, uint64_t rng_offset,
-                           const orc_params* prm, uint8_t* k_out, double* pn_out) {
+                           const orc_params* prm, uint8_t* k_out, double* pn_out, const uint32_t* chain_cell) {
   if (Q < 0 || spq <= 0 || !p0w || !prm) return -1;
   uint64_t W0 = 0;
   for (int n = 1; n <= MAXK; ++n) W0 += p0w[n - 1];
   if (W0 == 0) return -2;
   const orc_vmf* vm = guide ? guide->vmf : nullptr;
   uint32_t key[2] = {(uint32_t)rng_seed, (uint32_t)(rng_seed >> 32)};
-  for (int q = 0; q < Q; ++q) {
-    uint32_t c = cell ? cell[q] : 0u;
+  for (size_t b = 0; b < (size_t)Q * spq; ++b) {
+    uint32_t c = chain_cell ? chain_cell[b] : (cell ? cell[b / spq] : 0u);
     if (vm && (int)c >= vm->n_cells) return -3;
-    // W(n) of the cell, n = 1..8
+    // W(n) of the chain's cell, n = 1..8
     uint64_t We[MAXK + 1] = {0}, Wc = 0;
     if (vm) {
       for (int n = 1; n <= MAXK; ++n) {
@@ -1746,26 +1749,23 @@ int32_t orc_sample_lengths(const orc_guide* guide, int32_t Q, const uint32_t* ce
         Wc += We[n];
       }
     }
-    for (int s = 0; s < spq; ++s) {
-      size_t b = (size_t)q * spq + s;
-      uint64_t idx = (uint64_t)b + rng_offset;
-      uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), 0u, 2u}, r[4];
-      philox4x32_10(ctr, key, r);
-      bool pick_p0 = Wc == 0 || u01(r[0]) < prm->alpha;
-      const uint64_t* Wt = pick_p0 ? nullptr : We;
-      uint64_t total = pick_p0 ? W0 : Wc;
-      uint64_t target = scaled_target(r[1], total);
-      int n = 1;
-      uint64_t acc = 0;
-      for (; n <= MAXK; ++n) {
-        acc += Wt ? Wt[n] : p0w[n - 1];
-        if (acc > target) break;
-      }
-      n = std::min(n, MAXK);
-      double P0 = (double)p0w[n - 1] / (double)W0;
-      k_out[b] = (uint8_t)n;
-      pn_out[b] = Wc == 0 ? P0 : prm->alpha * P0 + (1.0 - prm->alpha) * (double)We[n] / (double)Wc;
+    uint64_t idx = (uint64_t)b + rng_offset;
+    uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), 0u, 2u}, r[4];
+    philox4x32_10(ctr, key, r);
+    bool pick_p0 = Wc == 0 || u01(r[0]) < prm->alpha;
+    const uint64_t* Wt = pick_p0 ? nullptr : We;
+    uint64_t total = pick_p0 ? W0 : Wc;
+    uint64_t target = scaled_target(r[1], total);
+    int n = 1;
+    uint64_t acc = 0;
+    for (; n <= MAXK; ++n) {
+      acc += Wt ? Wt[n] : p0w[n - 1];
+      if (acc > target) break;
     }
+    n = std::min(n, MAXK);
+    double P0 = (double)p0w[n - 1] / (double)W0;
+    k_out[b] = (uint8_t)n;
+    pn_out[b] = Wc == 0 ? P0 : prm->alpha * P0 + (1.0 - prm->alpha) * (double)We[n] / (double)Wc;
   }
   return 0;
 }

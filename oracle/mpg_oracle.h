@@ -71,14 +71,17 @@ int32_t orc_intersect(void* scene, int32_t n, const double* o, const double* d, 
                       double tmax, int32_t brute, double* t, int32_t* surf, int32_t* prim,
                       double* bary);
 
-/* Seed chains (trial index `trial`, 0 for the first draw). */
+/* Seed chains (trial index `trial`, 0 for the first draw).  The guide cell of
+ * chain b is chain_cell[b] when chain_cell is not NULL (a spatial tree's
+ * leaf), else cell[b / spq]; the same holds for orc_bernoulli and
+ * orc_sample_lengths. */
 int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
                          const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
                          const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                          uint64_t rng_seed, uint64_t rng_offset, uint32_t trial,
                          const orc_params* prm, double* x, int32_t* surf, int32_t* prim,
                          double* bary, uint8_t* tau_out, double* pdf, uint8_t* valid,
-                         int32_t n_threads);
+                         int32_t n_threads, const uint32_t* chain_cell);
 
 /* Manifold walk in place on chains with valid[b] != 0. */
 int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
@@ -105,7 +108,8 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
-                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads);
+                      uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads,
+                      const uint32_t* chain_cell);
 
 /* Histogram bin of each direction (theta-major index), and the update
  * counts[cell][bin] += q(w), q = min(floor(w 2^S), 2^32-1) (0 unless w > 0). */
@@ -129,7 +133,8 @@ int32_t orc_vmf_build(int32_t n_cells, int32_t R, const uint32_t* cell, const fl
  * of P_0(n), n = 1..8. */
 int32_t orc_sample_lengths(const orc_guide* guide, int32_t Q, const uint32_t* cell, int32_t spq,
                            const uint32_t* p0w, uint64_t rng_seed, uint64_t rng_offset,
-                           const orc_params* prm, uint8_t* k_out, double* pn_out);
+                           const orc_params* prm, uint8_t* k_out, double* pn_out,
+                           const uint32_t* chain_cell);
 
 /* vMF lobe density (Eq. vMF) and inverse-CDF draw, exposed for the tests. */
 double orc_vmf_pdf(const double* mu, double kappa, const double* w);

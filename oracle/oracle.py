@@ -58,7 +58,7 @@ def lib():
         L.orc_sample_seeds.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
                                        C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64,
                                        C.c_uint64, C.c_uint32, C.POINTER(orc_params), _f64p, _i32p,
-                                       _i32p, _f64p, _u8p, _f64p, _u8p, C.c_int32]
+                                       _i32p, _f64p, _u8p, _f64p, _u8p, C.c_int32, C.c_void_p]
         L.orc_walk.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p,
                                C.POINTER(orc_params), _u8p, _f64p, _i32p, _i32p, _f64p, _u8p, _u8p,
                                C.c_int32]
@@ -68,7 +68,7 @@ def lib():
         L.orc_bernoulli.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
                                     C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64, C.c_uint64,
                                     C.POINTER(orc_params), _f64p, _i32p, _u8p, _u32p, _u8p, C.c_void_p,
-                                    C.c_int32]
+                                    C.c_int32, C.c_void_p]
         L.orc_guide_bin.argtypes = [C.POINTER(orc_guide), C.c_int32, _f32p, _i32p]
         L.orc_guide_update.argtypes = [C.POINTER(orc_guide), _u64p, C.c_int32, _u32p, _f32p, _f32p,
                                        C.c_int32]
@@ -81,7 +81,7 @@ def lib():
         L.orc_vmf_build.argtypes = [C.c_int32, C.c_int32, _u32p, _f32p, _f32p, _u8p, _u8p, C.c_int32, _u32p,
                                     _u32p, _f64p, _u64p]
         L.orc_sample_lengths.argtypes = [C.c_void_p, C.c_int32, _u32p, C.c_int32, _u32p, C.c_uint64, C.c_uint64,
-                                         C.POINTER(orc_params), _u8p, _f64p]
+                                         C.POINTER(orc_params), _u8p, _f64p, C.c_void_p]
         L.orc_vmf_pdf.argtypes = [_f64p, C.c_double, _f64p]
         L.orc_vmf_pdf.restype = C.c_double
         L.orc_vmf_sample.argtypes = [_f64p, C.c_double, C.c_double, C.c_double, _f64p]
@@ -215,15 +215,17 @@ def training_plan(total_spp, first_spp=1, train_fraction=0.3):
     return iters, total_spp - used
 
 
-def sample_lengths(wl, guide, p0w, rng_offset=0):
+def sample_lengths(wl, guide, p0w, rng_offset=0, chain_cell=None):
     """Chain lengths and P(n) from the defensive mixture of P_0 (integer weights
     p0w[n-1]) and the vMF guide's P_e(n | cell) (Sec. 5.5)."""
+    cc = _cells(chain_cell)
     k = np.zeros(wl.B, np.uint8)
     pn = np.zeros(wl.B)
     g = guide.struct() if guide is not None else None
     P = params(wl.params)
     rc = lib().orc_sample_lengths(C.byref(g) if g is not None else None, wl.Q, _c(wl.cell, np.uint32), wl.spq,
-                                  _c(p0w, np.uint32), wl.rng_seed, rng_offset, C.byref(P), k, pn)
+                                  _c(p0w, np.uint32), wl.rng_seed, rng_offset, C.byref(P), k, pn,
+                                  None if cc is None else cc.ctypes.data)
     assert rc == 0, rc
     return k, pn
 
@@ -247,8 +249,14 @@ def intersect(scene, o, d, tmin=1e-4, tmax=np.inf, brute=False):
     return t, surf, prim, bary
 
 
-def sample_seeds(wl, scene, guide=None, trial=0, threads=None, rng_offset=0):
+def _cells(chain_cell):
+    """Per-chain guide cells (uint32, kept alive by the caller) or None."""
+    return None if chain_cell is None else _c(chain_cell, np.uint32)
+
+
+def sample_seeds(wl, scene, guide=None, trial=0, threads=None, rng_offset=0, chain_cell=None):
     B = wl.B
+    cc = _cells(chain_cell)
     out = dict(x=np.zeros((B, MAXK, 3)), surf=np.zeros((B, MAXK), np.int32),
                prim=np.zeros((B, MAXK), np.int32), bary=np.zeros((B, MAXK, 2)),
                tau=np.zeros(B, np.uint8), pdf=np.zeros(B), valid=np.zeros(B, np.uint8))
@@ -259,7 +267,7 @@ def sample_seeds(wl, scene, guide=None, trial=0, threads=None, rng_offset=0):
                                 wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(wl.tau, np.uint8),
                                 int(wl.tau_random), wl.rng_seed, rng_offset, trial, C.byref(P),
                                 out["x"], out["surf"], out["prim"], out["bary"], out["tau"], out["pdf"],
-                                out["valid"], threads or default_threads())
+                                out["valid"], threads or default_threads(), None if cc is None else cc.ctypes.data)
     assert rc == 0, rc
     return out
 
@@ -294,8 +302,9 @@ def contribution(wl, scene, chains, threads=None):
 
 
 def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offset=0, max_trials=None,
-              trial_walks=None):
+              trial_walks=None, chain_cell=None):
     B = wl.B
+    cc = _cells(chain_cell)
     N = np.zeros(B, np.uint32)
     capped = np.zeros(B, np.uint8)
     tw = None if trial_walks is None else trial_walks.ctypes.data
@@ -310,7 +319,7 @@ def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offse
                              wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8),
                              _c(chains["tau"], np.uint8), int(wl.tau_random), wl.rng_seed, rng_offset,
                              C.byref(P), chains["x"], chains["surf"], _c(admissible, np.uint8), N,
-                             capped, tw, threads or default_threads())
+                             capped, tw, threads or default_threads(), None if cc is None else cc.ctypes.data)
     assert rc == 0, rc
     return N, capped
 
