@@ -142,6 +142,8 @@ typedef struct mpg_chains {
   float* pdf;           /* [B] solid-angle density of the seed direction           */
   uint8_t* status;      /* [B] MPG_CHAIN_* (valid seed => INVALID until walked)    */
   uint8_t* iters;       /* [B] Newton steps taken                                  */
+  const uint32_t* chain_cell; /* [B] guide cell of each chain (a spatial tree's leaf,
+                           mpg_stree_query), or NULL => cell[b / spq]             */
 } mpg_chains;
 
 /* Guide kinds (mpg_guide.kind). */
@@ -344,14 +346,15 @@ mpg_status mpg_guide_update(mpg_ctx* ctx, const mpg_guide* guide, const uint32_t
 mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t stream);
 /* Records of the admissible chains of a batch for mpg_guide_update and
  * mpg_vmf_build: compacts (cell, w_D = unit(x_1 - x_D), w = contrib/A_L, and
- * when k_out / tau_out are not NULL the chain's length and types) of chains
- * with contrib > 0 into cell_out[B], omega_out[3][B], w_out[B], k_out[B] and
- * tau_out[B] (capacity B) in chain order, and writes the record count to
- * *R_dev (device int32). */
+ * when k_out / tau_out / chain_out are not NULL the chain's length, types and
+ * index) of chains with contrib > 0 into cell_out[B], omega_out[3][B],
+ * w_out[B], k_out[B], tau_out[B] and chain_out[B] (capacity B) in chain
+ * order, and writes the record count to *R_dev (device int32).  The cell is
+ * the chain's (chain_cell when set). */
 mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* scene, const mpg_chains* chains,
                              const float* contrib, uint32_t* cell_out, float* omega_out,
-                             float* w_out, uint8_t* k_out, uint8_t* tau_out, int32_t* R_dev,
-                             cudaStream_t stream);
+                             float* w_out, uint8_t* k_out, uint8_t* tau_out, int32_t* chain_out,
+                             int32_t* R_dev, cudaStream_t stream);
 
 /* Sec. 5.5 -- vMF mixture guide from the records of the last pass (Eq. vMF):
  * record r < n (n = *R_dev when R_dev is not NULL, else R) with cell[r],
@@ -446,6 +449,49 @@ mpg_status mpg_graph_launch(mpg_graph* graph, cudaStream_t stream);
 /* Kernel launches inside one replay (of every context recorded). */
 mpg_status mpg_graph_kernels(const mpg_graph* graph, int64_t* count);
 void mpg_graph_destroy(mpg_graph* graph);
+
+/* Sec. 5.6 -- spatial tree of the guide samples: a binary tree over the
+ * 6-D positions (x_D, x_L) of the records of a pass, whose leaves stand for
+ * the neighbourhood S(x_D, x_L) of the guiding distribution.  A node holding
+ * more than T = floor(c sqrt(|S|)) of its own samples (c = 1 in the paper) is
+ * split at the midpoint of its box along the axis of largest extent relative
+ * to the root box (first such axis on ties; boxes and midpoints in FP64 from
+ * the FP32 positions), samples below the midpoint going left; floor(eps k)
+ * samples of each child nearest to the plane (k = the node's own samples;
+ * eps = 0.1 in the paper; ties by record index) are copied into the other
+ * child (spatial filtering) and are not passed on when that child splits in
+ * turn; depth at most 48.  Leaves are numbered depth-first, left first; a
+ * leaf's members are its own samples and the copies it received, ascending by
+ * record index.
+ * mpg_stree_build reads the record count (*R_dev, else R) and the records'
+ * chain indices (rec_chain, from mpg_guide_records) back to the host,
+ * gathers their positions from `chains` on the device, builds the tree on the
+ * host and uploads it (library-owned; synchronous). */
+typedef struct mpg_stree mpg_stree;
+mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,
+                           const int32_t* R_dev, float epsilon, float c, mpg_stree** out, cudaStream_t stream);
+/* Sizes of a tree: samples, nodes, leaves and leaf members (own + copies). */
+mpg_status mpg_stree_info(const mpg_stree* tree, int32_t* n_samples, int32_t* n_nodes, int32_t* n_leaves,
+                          int32_t* n_members);
+/* Host copies of the tree (for checks): per node axis (-1 for a leaf), split,
+ * left child (the leaf index for a leaf) and right child [n_nodes]; per member
+ * its leaf and record index [n_members].  Any pointer may be NULL. */
+mpg_status mpg_stree_export(const mpg_stree* tree, int32_t* axis, double* split, int32_t* left, int32_t* right,
+                            int32_t* member_leaf, int32_t* member_rec);
+/* Guide records of the leaves: member m of leaf j becomes a record with cell
+ * j and the direction, weight, length and types of its record in the input
+ * (arrays of capacity R_in, omega SoA [3][R_in]); written in member order to
+ * the outputs (capacity R_out >= n_members, omega [3][R_out]) with the count in
+ * *R_out_dev.  A guide built from them has n_cells = n_leaves. */
+mpg_status mpg_stree_records(mpg_ctx* ctx, const mpg_stree* tree, const float* omega, const float* w,
+                             const uint8_t* k, const uint8_t* tau, int32_t R_in, uint32_t* cell_out,
+                             float* omega_out, float* w_out, uint8_t* k_out, uint8_t* tau_out, int32_t R_out,
+                             int32_t* R_out_dev, cudaStream_t stream);
+/* Leaf of each chain of a batch by descending the tree with (x_D, x_L) (FP64
+ * comparisons): chain_cell[b], to be set as chains->chain_cell. */
+mpg_status mpg_stree_query(mpg_ctx* ctx, const mpg_stree* tree, const mpg_chains* chains, uint32_t* chain_cell,
+                           cudaStream_t stream);
+void mpg_stree_destroy(mpg_stree* tree);
 
 /* Sample schedule of the progressive training (Sec. 5.8, online training and
  * rendering), in seeds per receiver point: training iterations of first_spp,

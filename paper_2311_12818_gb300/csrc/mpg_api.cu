@@ -263,6 +263,7 @@ mpg_status check_chains(const mpg_chains* c, bool need_walk_state) {
   for (int i = 0; i < 11; ++i)
     if (!aligned16(req[i])) return fail(MPG_ERR_INVALID_ARG, "chains.%s is NULL or not 16-byte aligned", names[i]);
   if (need_walk_state && !aligned16(c->pdf)) return fail(MPG_ERR_INVALID_ARG, "chains.pdf is NULL or unaligned");
+  if (c->chain_cell && !aligned16(c->chain_cell)) return fail(MPG_ERR_INVALID_ARG, "chains.chain_cell is not 16-byte aligned");
   return MPG_OK;
 }
 
@@ -287,7 +288,7 @@ DChains to_dev(const mpg_chains* c) {
   d.B = c->B; d.Q = c->Q; d.spq = c->spq;
   d.xD = c->xD; d.nD = c->nD; d.cell = c->cell; d.xL = c->xL; d.k = c->k; d.pn = c->pn; d.tau = c->tau;
   d.x = c->x; d.surf = c->surf; d.prim = c->prim; d.bary = c->bary; d.pdf = c->pdf;
-  d.status = c->status; d.iters = c->iters;
+  d.status = c->status; d.iters = c->iters; d.chain_cell = c->chain_cell;
   return d;
 }
 
@@ -972,12 +973,12 @@ mpg_status mpg_guide_clear(mpg_ctx* ctx, const mpg_guide* guide, cudaStream_t st
 
 mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains* chains, const float* contrib,
                              uint32_t* cell_out, float* omega_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
-                             int32_t* R_dev, cudaStream_t st) {
+                             int32_t* chain_out, int32_t* R_dev, cudaStream_t st) {
   if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
   mpg_status s;
   if ((s = check_chains(chains, false))) return s;
   if (!aligned16(contrib) || !aligned16(cell_out) || !aligned16(omega_out) || !aligned16(w_out) || !R_dev ||
-      (k_out && !aligned16(k_out)) || (tau_out && !aligned16(tau_out)))
+      (k_out && !aligned16(k_out)) || (tau_out && !aligned16(tau_out)) || (chain_out && !aligned16(chain_out)))
     return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
   CUDA_TRY(cudaSetDevice(ctx->device));
   DChains c = to_dev(chains);
@@ -991,7 +992,7 @@ mpg_status mpg_guide_records(mpg_ctx* ctx, const mpg_scene* sc, const mpg_chains
   }
   timed(ctx, MPG_KERNEL_AUX, st, tiles ? 3 : 0, [&] {
     launch_guide_records_ordered(c, contrib, 1.0f / sc->S.L.area, ctx->d_rec, cell_out, omega_out, w_out, k_out,
-                                 tau_out, R_dev, st);
+                                 tau_out, chain_out, R_dev, st);
   });
   LAUNCH_CHECK("guide records");
   return MPG_OK;
@@ -1041,8 +1042,8 @@ mpg_status mpg_sample_lengths(mpg_ctx* ctx, const mpg_guide* guide, const mpg_ch
   CUDA_TRY(cudaSetDevice(ctx->device));
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
   timed(ctx, MPG_KERNEL_SEED, st, 1, [&] {
-    launch_sample_lengths(guide ? &g : nullptr, chains->cell, chains->B, chains->spq, p0_weights, key, rng_offset,
-                          P->alpha, dctx(ctx, MPG_KERNEL_SEED), k_out, pn_out, ctx->sms, st);
+    launch_sample_lengths(guide ? &g : nullptr, to_dev(chains), p0_weights, key, rng_offset, P->alpha,
+                          dctx(ctx, MPG_KERNEL_SEED), k_out, pn_out, ctx->sms, st);
   });
   LAUNCH_CHECK("sample lengths");
   return MPG_OK;
@@ -1221,6 +1222,141 @@ void mpg_graph_destroy(mpg_graph* g) {
 // ---------------------------------------------------------------------------
 // Autotuner of the batched schedule.
 // ---------------------------------------------------------------------------
+struct mpg_stree {
+  int device = 0;
+  StreeHost h;
+  int* d_axis = nullptr;
+  int* d_left = nullptr;
+  int* d_right = nullptr;
+  int* d_member_leaf = nullptr;
+  int* d_member_rec = nullptr;
+  double* d_split = nullptr;
+};
+
+void mpg_stree_destroy(mpg_stree* t) {
+  if (!t) return;
+  cudaSetDevice(t->device);
+  cudaFree(t->d_axis); cudaFree(t->d_left); cudaFree(t->d_right); cudaFree(t->d_split);
+  cudaFree(t->d_member_leaf); cudaFree(t->d_member_rec);
+  delete t;
+}
+
+mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,
+                           const int32_t* R_dev, float epsilon, float c, mpg_stree** out, cudaStream_t st) {
+  if (!ctx || !out) return fail(MPG_ERR_INVALID_ARG, "ctx or out is NULL");
+  *out = nullptr;
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (R < 0 || (R > 0 && !aligned16(rec_chain)) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f))
+    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (R %d, epsilon %g, c %g)", R, epsilon, c);
+  if (ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "mpg_stree_build is synchronous and cannot be captured");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  int n = R;
+  if (R_dev) {
+    CUDA_TRY(cudaMemcpyAsync(&n, R_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    n = std::min(std::max(n, 0), R);
+  }
+  std::vector<int> idx(n);
+  if (n > 0) {
+    CUDA_TRY(cudaMemcpyAsync(idx.data(), rec_chain, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  for (int i = 0; i < n; ++i)
+    if (idx[i] < 0 || idx[i] >= chains->B)
+      return fail(MPG_ERR_INVALID_ARG, "record %d names chain %d outside the batch", i, idx[i]);
+  std::vector<float> pos((size_t)6 * n);
+  if (n > 0) {
+    float* d_pos = nullptr;
+    CUDA_TRY(cudaMalloc(&d_pos, sizeof(float) * pos.size()));
+    launch_stree_gather(to_dev(chains), rec_chain, n, d_pos, st);
+    cudaError_t e = cudaMemcpyAsync(pos.data(), d_pos, sizeof(float) * pos.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d_pos);
+    if (e != cudaSuccess) return fail(MPG_ERR_CUDA, "tree positions: %s", cudaGetErrorString(e));
+    ctx->launches += 1;
+  }
+  mpg_stree* t = new mpg_stree;
+  t->device = ctx->device;
+  stree_build(pos.data(), n, (double)epsilon, (double)c, t->h);
+  auto upload = [](auto** d, const auto& h) {
+    const size_t bytes = sizeof(h[0]) * h.size();
+    cudaError_t e = cudaMalloc((void**)d, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(*d, h.data(), bytes, cudaMemcpyHostToDevice);
+    return e;
+  };
+  cudaError_t e = upload(&t->d_axis, t->h.axis);
+  if (e == cudaSuccess) e = upload(&t->d_left, t->h.left);
+  if (e == cudaSuccess) e = upload(&t->d_right, t->h.right);
+  if (e == cudaSuccess) e = upload(&t->d_split, t->h.split);
+  if (e == cudaSuccess) e = upload(&t->d_member_leaf, t->h.member_leaf);
+  if (e == cudaSuccess) e = upload(&t->d_member_rec, t->h.member_rec);
+  if (e != cudaSuccess) {
+    mpg_stree_destroy(t);
+    return fail(MPG_ERR_CUDA, "tree upload: %s", cudaGetErrorString(e));
+  }
+  *out = t;
+  return MPG_OK;
+}
+
+mpg_status mpg_stree_info(const mpg_stree* t, int32_t* n_samples, int32_t* n_nodes, int32_t* n_leaves,
+                          int32_t* n_members) {
+  if (!t) return fail(MPG_ERR_INVALID_ARG, "tree is NULL");
+  if (n_samples) *n_samples = t->h.n_samples;
+  if (n_nodes) *n_nodes = (int32_t)t->h.axis.size();
+  if (n_leaves) *n_leaves = t->h.n_leaves;
+  if (n_members) *n_members = (int32_t)t->h.member_rec.size();
+  return MPG_OK;
+}
+
+mpg_status mpg_stree_export(const mpg_stree* t, int32_t* axis, double* split, int32_t* left, int32_t* right,
+                            int32_t* member_leaf, int32_t* member_rec) {
+  if (!t) return fail(MPG_ERR_INVALID_ARG, "tree is NULL");
+  if (axis) std::copy(t->h.axis.begin(), t->h.axis.end(), axis);
+  if (split) std::copy(t->h.split.begin(), t->h.split.end(), split);
+  if (left) std::copy(t->h.left.begin(), t->h.left.end(), left);
+  if (right) std::copy(t->h.right.begin(), t->h.right.end(), right);
+  if (member_leaf) std::copy(t->h.member_leaf.begin(), t->h.member_leaf.end(), member_leaf);
+  if (member_rec) std::copy(t->h.member_rec.begin(), t->h.member_rec.end(), member_rec);
+  return MPG_OK;
+}
+
+mpg_status mpg_stree_records(mpg_ctx* ctx, const mpg_stree* t, const float* omega, const float* w, const uint8_t* k,
+                             const uint8_t* tau, int32_t R_in, uint32_t* cell_out, float* omega_out, float* w_out,
+                             uint8_t* k_out, uint8_t* tau_out, int32_t R_out, int32_t* R_out_dev, cudaStream_t st) {
+  if (!ctx || !t) return fail(MPG_ERR_INVALID_ARG, "ctx or tree is NULL");
+  const int M = (int)t->h.member_rec.size();
+  if (R_out < M || R_in < t->h.n_samples)
+    return fail(MPG_ERR_INVALID_ARG, "record arrays too small (R_in %d < %d samples or R_out %d < %d members)", R_in,
+                t->h.n_samples, R_out, M);
+  if (!R_out_dev || (M > 0 && (!aligned16(omega) || !aligned16(w) || !aligned16(k) || !aligned16(tau) ||
+                               !aligned16(cell_out) || !aligned16(omega_out) || !aligned16(w_out) ||
+                               !aligned16(k_out) || !aligned16(tau_out))))
+    return fail(MPG_ERR_INVALID_ARG, "record arrays must be non-NULL 16-byte aligned device arrays");
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] {
+    launch_stree_records(t->d_member_leaf, t->d_member_rec, M, omega, w, k, tau, R_in, cell_out, omega_out, w_out,
+                         k_out, tau_out, R_out, R_out_dev, ctx->sms, st);
+  });
+  LAUNCH_CHECK("tree records");
+  return MPG_OK;
+}
+
+mpg_status mpg_stree_query(mpg_ctx* ctx, const mpg_stree* t, const mpg_chains* chains, uint32_t* chain_cell,
+                           cudaStream_t st) {
+  if (!ctx || !t) return fail(MPG_ERR_INVALID_ARG, "ctx or tree is NULL");
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (!aligned16(chain_cell)) return fail(MPG_ERR_INVALID_ARG, "chain_cell must be a 16-byte aligned device array");
+  if (chains->B == 0) return MPG_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] {
+    launch_stree_query(t->d_axis, t->d_split, t->d_left, t->d_right, to_dev(chains), chain_cell, ctx->sms, st);
+  });
+  LAUNCH_CHECK("tree query");
+  return MPG_OK;
+}
+
 mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_fraction, int32_t max_iters,
                              int32_t* iter_spp, int32_t* n_iters, int32_t* render_spp) {
   if (total_spp < 0 || first_spp < 1 || !(train_fraction >= 0.0f && train_fraction <= 1.0f) || max_iters < 0 ||

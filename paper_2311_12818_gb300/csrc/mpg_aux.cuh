@@ -1,9 +1,22 @@
 // Declarations of the auxiliary kernels' host launchers.
 #pragma once
 
+#include <vector>
+
 #include "mpg_kernels.cuh"
 
 namespace mpg {
+
+// Spatial tree of the guide samples, host side (mpg_stree.cu): per node the
+// split axis (-1 for a leaf), split value, children (the leaf index in `left`
+// for a leaf); per leaf member its leaf and record, leaf-major, ascending
+// records within a leaf.
+struct StreeHost {
+  std::vector<int> axis, left, right, member_leaf, member_rec;
+  std::vector<double> split;
+  int n_leaves = 0, n_samples = 0;
+};
+void stree_build(const float* pos /* [6][n] host */, int n, double eps, double c, StreeHost& t);
 
 void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
                    int* order, int sms, cudaStream_t st);
@@ -14,15 +27,22 @@ void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* ome
 int rec_tiles(int B);
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
                                   uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
-                                  int* R, cudaStream_t st);
+                                  int* chain_out, int* R, cudaStream_t st);
 // vMF lobe build and chain-length sampler (mpg_vmf.cu).
 int vmf_build_launches(int R, int n_cells);
 void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, const float* omega, const float* w,
                       const uint8_t* k, const uint8_t* tau, int R, const int* R_dev, int shift, int* err, int sms,
                       cudaStream_t st);
-void launch_sample_lengths(const DGuide* g, const uint32_t* cell, int B, int spq, const uint32_t* p0w, uint2 key,
-                           uint64_t offset, float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms,
-                           cudaStream_t st);
+void launch_sample_lengths(const DGuide* g, const DChains& c, const uint32_t* p0w, uint2 key, uint64_t offset,
+                           float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms, cudaStream_t st);
+// Spatial tree of the guide samples (mpg_stree.cu).
+void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st);
+void launch_stree_records(const int* member_leaf, const int* member_rec, int M, const float* omega, const float* w,
+                          const uint8_t* k, const uint8_t* tau, int R_in, uint32_t* cell_out, float* omega_out,
+                          float* w_out, uint8_t* k_out, uint8_t* tau_out, int R_out, int* R_out_dev, int sms,
+                          cudaStream_t st);
+void launch_stree_query(const int* axis, const double* split, const int* left, const int* right, const DChains& c,
+                        uint32_t* chain_cell, int sms, cudaStream_t st);
 void launch_trace(const DScene& S, const float* o, const float* d, int n, float tmin, float tmax, float* t, int* surf,
                   int* prim, float* bary, int* err, unsigned long long* stats, bool st_on, int sms, cudaStream_t st);
 double run_fp32_peak(float* scratch, int sms, cudaStream_t st);

@@ -22,7 +22,13 @@ struct DChains {
   float* pdf;
   uint8_t* status;
   uint8_t* iters;
+  const uint32_t* chain_cell;  // per-chain guide cell, or NULL
 };
+
+// Guide cell of chain b: its own (a spatial tree's leaf) or its receiver point's.
+__device__ __forceinline__ uint32_t cell_of(const DChains& c, int b) {
+  return c.chain_cell ? c.chain_cell[b] : (c.cell ? c.cell[b / c.spq] : 0u);
+}
 
 // Optional k-bucketed work list: chains order[base[K] .. base[K]+count[K]).
 struct DWork {

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
     uint32_t tau;
     float pdf;
     int q = b / c.spq;
-    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[q] : 0u, e.tau, P.tau_random != 0,
+    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0,
                                key, (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c);
     if (!ok) {
 #pragma unroll
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
       load_chain<K>(c, b, target);
       Ends e = load_ends(c, b);
       int q = b / c.spq;
-      uint32_t cell = c.cell ? c.cell[q] : 0u;
+      uint32_t cell = cell_of(c, b);
       for (int rep = 0; rep < o.repeats; ++rep) {
         bool cap_r = true;
         for (int tr = 1; tr <= P.max_trials; ++tr) {

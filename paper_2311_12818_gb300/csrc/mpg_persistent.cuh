@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(128) k_trial_seed(const __grid_constant__ DSce
     uint32_t tau;
     float pdf;
     tl.trials++;
-    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, c.cell ? c.cell[b / c.spq] : 0u, e.tau,
+    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau,
                                P.tau_random != 0, key, (uint64_t)b + offset, (uint32_t)t | ctx.trial_base, P, ch, tau,
                                pdf, ctx.err, tl.c, false, true) &&
               tau == e.tau;
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
         Ends e = load_ends(c, bb);
         uint32_t tau;
         float pdf;
-        uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
+        uint32_t cell = cell_of(c, bb);
         if (draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
                              (uint64_t)bb + offset, (uint32_t)tt | ctx.trial_base, P, L.ch, tau, pdf, ctx.err, t.c, false, true) &&
             tau == e.tau) {
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
     if (take) {
       if (j == 0) t.trials++;
       e = load_ends(c, bb);
-      uint32_t cell = c.cell ? c.cell[bb / c.spq] : 0u;
+      uint32_t cell = cell_of(c, bb);
       uint32_t tau;
       float pdf;
       drawn = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,

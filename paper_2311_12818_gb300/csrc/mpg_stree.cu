@@ -1,0 +1,175 @@
+// Spatial tree of the guide samples (Sec. 5.6): the host build of the binary
+// tree over the samples' (x_D, x_L), and the device kernels around it --
+// gathering the samples' positions, turning the leaves' members into guide
+// records, and the per-chain leaf query.  The tree is built on the host once
+// per training pass (the paper's tree is a host structure too); the queries
+// run on the GPU for every chain.
+#include <algorithm>
+#include <cmath>
+
+#include "mpg_aux.cuh"
+
+namespace mpg {
+
+namespace {
+constexpr int STREE_MAX_DEPTH = 48;
+
+struct Builder {
+  const float* pos;  // [6][n]
+  int n;
+  double eps;
+  int T;
+  double root_ext[6];
+  StreeHost& t;
+
+  double at(int i, int a) const { return (double)pos[(size_t)a * n + i]; }
+
+  int node() {
+    t.axis.push_back(-1);
+    t.split.push_back(0.0);
+    t.left.push_back(-1);
+    t.right.push_back(-1);
+    return (int)t.axis.size() - 1;
+  }
+
+  // The m samples of `side` nearest to the plane x = mid (ties: lower index).
+  std::vector<int> nearest(const std::vector<int>& side, int a, double mid, size_t m) const {
+    std::vector<std::pair<double, int>> d;
+    d.reserve(side.size());
+    for (int s : side) d.push_back({std::fabs(at(s, a) - mid), s});
+    m = std::min(m, d.size());
+    std::partial_sort(d.begin(), d.begin() + m, d.end());
+    std::vector<int> out;
+    for (size_t j = 0; j < m; ++j) out.push_back(d[j].second);
+    return out;
+  }
+
+  int build(const std::vector<int>& own, const std::vector<int>& copies, const double* lo, const double* hi,
+            int depth) {
+    const int i = node();
+    int a = 0;
+    double best = -1.0;
+    for (int ax = 0; ax < 6; ++ax) {  // largest extent relative to the root box, first on ties
+      double rel = root_ext[ax] > 0.0 ? (hi[ax] - lo[ax]) / root_ext[ax] : 0.0;
+      if (rel > best) { best = rel; a = ax; }
+    }
+    if ((int)own.size() <= T || depth >= STREE_MAX_DEPTH || !(best > 0.0)) {
+      const int leaf = t.n_leaves++;
+      t.left[i] = leaf;
+      std::vector<int> mem(own);
+      mem.insert(mem.end(), copies.begin(), copies.end());
+      std::sort(mem.begin(), mem.end());
+      mem.erase(std::unique(mem.begin(), mem.end()), mem.end());
+      for (int r : mem) {
+        t.member_leaf.push_back(leaf);
+        t.member_rec.push_back(r);
+      }
+      return i;
+    }
+    const double mid = 0.5 * (lo[a] + hi[a]);
+    std::vector<int> L, R;
+    for (int s : own) (at(s, a) < mid ? L : R).push_back(s);  // own is ascending, so are L and R
+    const size_t m = (size_t)std::floor(eps * (double)own.size());
+    std::vector<int> to_right = nearest(L, a, mid, m), to_left = nearest(R, a, mid, m);
+    t.axis[i] = a;
+    t.split[i] = mid;
+    double hl[6], lr[6];
+    std::copy(hi, hi + 6, hl);
+    std::copy(lo, lo + 6, lr);
+    hl[a] = mid;
+    lr[a] = mid;
+    const int l = build(L, to_left, lo, hl, depth + 1);
+    t.left[i] = l;
+    const int r = build(R, to_right, lr, hi, depth + 1);
+    t.right[i] = r;
+    return i;
+  }
+};
+
+__global__ void k_stree_gather(DChains c, const int* rec_chain, int n, float* pos) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int b = rec_chain[i];
+    const int q = b / c.spq;
+    pos[i] = c.xD[q];
+    pos[(size_t)n + i] = c.xD[c.Q + q];
+    pos[2 * (size_t)n + i] = c.xD[2 * c.Q + q];
+    pos[3 * (size_t)n + i] = c.xL[b];
+    pos[4 * (size_t)n + i] = c.xL[(size_t)c.B + b];
+    pos[5 * (size_t)n + i] = c.xL[2 * (size_t)c.B + b];
+  }
+}
+
+__global__ void k_stree_records(const int* member_leaf, const int* member_rec, int M, const float* omega,
+                                const float* w, const uint8_t* k, const uint8_t* tau, int R_in, uint32_t* cell_out,
+                                float* omega_out, float* w_out, uint8_t* k_out, uint8_t* tau_out, int R_out,
+                                int* R_out_dev) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *R_out_dev = M;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < M; m += gridDim.x * blockDim.x) {
+    const int r = member_rec[m];
+    cell_out[m] = (uint32_t)member_leaf[m];
+    omega_out[m] = omega[r];
+    omega_out[R_out + m] = omega[R_in + r];
+    omega_out[2 * (size_t)R_out + m] = omega[2 * (size_t)R_in + r];
+    w_out[m] = w[r];
+    k_out[m] = k[r];
+    tau_out[m] = tau[r];
+  }
+}
+
+// Descend from the root by (x_D, x_L); the comparisons are the build's, in FP64.
+__global__ void k_stree_query(const int* axis, const double* split, const int* left, const int* right, DChains c,
+                              uint32_t* chain_cell) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c.B; b += gridDim.x * blockDim.x) {
+    const int q = b / c.spq;
+    double p[6] = {(double)c.xD[q], (double)c.xD[c.Q + q], (double)c.xD[2 * c.Q + q],
+                   (double)c.xL[b], (double)c.xL[(size_t)c.B + b], (double)c.xL[2 * (size_t)c.B + b]};
+    int i = 0;
+    for (int d = 0; d <= STREE_MAX_DEPTH && axis[i] >= 0; ++d) {
+      const int a = axis[i];
+      double x = a == 0 ? p[0] : a == 1 ? p[1] : a == 2 ? p[2] : a == 3 ? p[3] : a == 4 ? p[4] : p[5];
+      i = x < split[i] ? left[i] : right[i];
+    }
+    chain_cell[b] = (uint32_t)left[i];
+  }
+}
+}  // namespace
+
+void stree_build(const float* pos, int n, double eps, double c, StreeHost& t) {
+  t = StreeHost{};
+  t.n_samples = n;
+  Builder B{pos, n, eps, std::max(1, (int)std::floor(c * std::sqrt((double)n))), {}, t};
+  double lo[6], hi[6];
+  for (int a = 0; a < 6; ++a) {
+    lo[a] = hi[a] = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double x = B.at(i, a);
+      if (i == 0 || x < lo[a]) lo[a] = x;
+      if (i == 0 || x > hi[a]) hi[a] = x;
+    }
+    B.root_ext[a] = hi[a] - lo[a];
+  }
+  std::vector<int> all(n);
+  for (int i = 0; i < n; ++i) all[i] = i;
+  B.build(all, {}, lo, hi, 0);
+}
+
+void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st) {
+  if (n > 0) k_stree_gather<<<std::min(1024, (n + 255) / 256), 256, 0, st>>>(c, rec_chain, n, pos);
+}
+
+void launch_stree_records(const int* member_leaf, const int* member_rec, int M, const float* omega, const float* w,
+                          const uint8_t* k, const uint8_t* tau, int R_in, uint32_t* cell_out, float* omega_out,
+                          float* w_out, uint8_t* k_out, uint8_t* tau_out, int R_out, int* R_out_dev, int sms,
+                          cudaStream_t st) {
+  const int grid = std::max(1, std::min(sms * 8, (M + 255) / 256));
+  k_stree_records<<<grid, 256, 0, st>>>(member_leaf, member_rec, M, omega, w, k, tau, R_in, cell_out, omega_out,
+                                        w_out, k_out, tau_out, R_out, R_out_dev);
+}
+
+void launch_stree_query(const int* axis, const double* split, const int* left, const int* right, const DChains& c,
+                        uint32_t* chain_cell, int sms, cudaStream_t st) {
+  const int grid = std::max(1, std::min(sms * 8, (c.B + 255) / 256));
+  k_stree_query<<<grid, 256, 0, st>>>(axis, split, left, right, c, chain_cell);
+}
+
+}  // namespace mpg

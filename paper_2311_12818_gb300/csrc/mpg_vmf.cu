@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(TILE_THREADS) k_rec_count(const float* contrib
 
 __global__ void __launch_bounds__(TILE_THREADS) k_rec_write(DChains c, const float* contrib, float inv_area,
                                                             const uint32_t* offs, uint32_t* cell_out, float* om_out,
-                                                            float* w_out, uint8_t* k_out, uint8_t* tau_out) {
+                                                            float* w_out, uint8_t* k_out, uint8_t* tau_out,
+                                                            int* chain_out) {
   __shared__ int wcount[TILE_THREADS / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int run = (int)offs[blockIdx.x];
@@ -139,13 +140,14 @@ __global__ void __launch_bounds__(TILE_THREADS) k_rec_write(DChains c, const flo
       float3 xD = make_float3(c.xD[q], c.xD[c.Q + q], c.xD[2 * c.Q + q]);
       float3 x1 = make_float3(c.x[b], c.x[(size_t)c.B + b], c.x[2 * (size_t)c.B + b]);
       float3 w = unit(x1 - xD);
-      cell_out[o] = c.cell ? c.cell[q] : 0u;
+      cell_out[o] = cell_of(c, b);
       om_out[o] = w.x;
       om_out[c.B + o] = w.y;
       om_out[2 * (size_t)c.B + o] = w.z;
       w_out[o] = contrib[b] * inv_area;
       if (k_out) k_out[o] = c.k[b];
       if (tau_out) tau_out[o] = c.tau[b];
+      if (chain_out) chain_out[o] = b;
     }
     run += all;
     __syncthreads();
@@ -363,13 +365,13 @@ struct P0Table {
   uint64_t total;
 };
 
-__global__ void k_sample_lengths(DGuide g, int has_guide, const uint32_t* cell, int B, int spq, P0Table p0,
-                                 uint2 key, uint64_t offset, float alpha, DCtx ctx, uint8_t* k_out, float* pn_out) {
+__global__ void k_sample_lengths(DGuide g, int has_guide, DChains ch, P0Table p0, uint2 key, uint64_t offset,
+                                 float alpha, DCtx ctx, uint8_t* k_out, float* pn_out) {
   offset = rng_offset(offset, ctx);
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < ch.B; b += gridDim.x * blockDim.x) {
     uint64_t idx = (uint64_t)b + offset;
     uint4 r = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), 0u, 2u), key);
-    uint32_t c = cell ? cell[b / spq] : 0u;
+    uint32_t c = cell_of(ch, b);
     uint32_t cs = 0, ce = 0;
     uint64_t Wc = 0;
     if (has_guide) {
@@ -415,7 +417,7 @@ int rec_tiles(int B) { return (B + REC_TILE - 1) / REC_TILE; }
 
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
                                   uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
-                                  int* R, cudaStream_t st) {
+                                  int* chain_out, int* R, cudaStream_t st) {
   const int tiles = rec_tiles(c.B);
   if (tiles == 0) {
     cudaMemsetAsync(R, 0, sizeof(int), st);
@@ -424,7 +426,7 @@ void launch_guide_records_ordered(const DChains& c, const float* contrib, float 
   k_rec_count<<<tiles, TILE_THREADS, 0, st>>>(contrib, c.B, tile_scratch);
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(tile_scratch, tiles, R);
   k_rec_write<<<tiles, TILE_THREADS, 0, st>>>(c, contrib, inv_area, tile_scratch, cell_out, om_out, w_out, k_out,
-                                              tau_out);
+                                              tau_out, chain_out);
 }
 
 int vmf_build_launches(int R, int n_cells) {
@@ -468,9 +470,8 @@ void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, 
                                           const_cast<float*>(g.lobe_coef));
 }
 
-void launch_sample_lengths(const DGuide* g, const uint32_t* cell, int B, int spq, const uint32_t* p0w, uint2 key,
-                           uint64_t offset, float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms,
-                           cudaStream_t st) {
+void launch_sample_lengths(const DGuide* g, const DChains& c, const uint32_t* p0w, uint2 key, uint64_t offset,
+                           float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms, cudaStream_t st) {
   P0Table t;
   t.total = 0;
   for (int n = 0; n < MAXK; ++n) {
@@ -478,8 +479,8 @@ void launch_sample_lengths(const DGuide* g, const uint32_t* cell, int B, int spq
     t.total += p0w[n];
   }
   DGuide gg = g ? *g : DGuide{};
-  const int grid = std::max(1, std::min(sms * 8, (B + 255) / 256));
-  k_sample_lengths<<<grid, 256, 0, st>>>(gg, g != nullptr, cell, B, spq, t, key, offset, alpha, ctx, k_out, pn_out);
+  const int grid = std::max(1, std::min(sms * 8, (c.B + 255) / 256));
+  k_sample_lengths<<<grid, 256, 0, st>>>(gg, g != nullptr, c, t, key, offset, alpha, ctx, k_out, pn_out);
 }
 
 }  // namespace mpg

@@ -49,7 +49,7 @@ class mpg_chains(C.Structure):
                 ("xD", C.c_void_p), ("nD", C.c_void_p), ("cell", C.c_void_p), ("xL", C.c_void_p),
                 ("k", C.c_void_p), ("pn", C.c_void_p), ("tau", C.c_void_p), ("x", C.c_void_p),
                 ("surf", C.c_void_p), ("prim", C.c_void_p), ("bary", C.c_void_p), ("pdf", C.c_void_p),
-                ("status", C.c_void_p), ("iters", C.c_void_p)]
+                ("status", C.c_void_p), ("iters", C.c_void_p), ("chain_cell", C.c_void_p)]
 
 
 class mpg_guide(C.Structure):
@@ -80,7 +80,8 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
-           "mpg_sample_lengths", "mpg_training_plan"]
+           "mpg_sample_lengths", "mpg_training_plan", "mpg_stree_build", "mpg_stree_info", "mpg_stree_export",
+           "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy"]
 
 _lib = None
 
@@ -116,9 +117,16 @@ def lib():
         L.mpg_chain_contribution.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                              C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_guide_update.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, i32, vp, i32, vp]
-        L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp, vp, vp]
+        L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_vmf_build.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.mpg_training_plan.argtypes = [i32, i32, f32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.mpg_stree_build.argtypes = [vp, C.POINTER(mpg_chains), vp, i32, vp, f32, f32, C.POINTER(vp), vp]
+        L.mpg_stree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+        L.mpg_stree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.mpg_stree_records.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp]
+        L.mpg_stree_query.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp]
+        L.mpg_stree_destroy.argtypes = [vp]
+        L.mpg_stree_destroy.restype = None
         L.mpg_sample_lengths.argtypes = [vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), vp, u64, u64,
                                          C.POINTER(mpg_params), vp, vp, vp]
         L.mpg_walk_adjoint.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp]
@@ -135,7 +143,7 @@ def lib():
         L.mpg_autotune.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                    C.POINTER(mpg_params), i32, C.POINTER(mpg_params), C.POINTER(C.c_double), vp]
         for n in EXPORTS[2:]:
-            if n not in ("mpg_ctx_destroy", "mpg_scene_destroy", "mpg_graph_destroy"):
+            if n not in ("mpg_ctx_destroy", "mpg_scene_destroy", "mpg_graph_destroy", "mpg_stree_destroy"):
                 getattr(L, n).restype = i32
         _lib = L
     return _lib
@@ -316,12 +324,14 @@ class Chains:
         self.pdf = torch.zeros(B, **f32)
         self.status = torch.zeros(B, dtype=torch.uint8, device=device)
         self.iters = torch.zeros(B, dtype=torch.uint8, device=device)
+        self.chain_cell = None  # [B] int32 per-chain guide cells (a tree's leaves), or None
 
     def struct(self):
         return mpg_chains(self.B, self.Q, self.spq, self.xD.data_ptr(), self.nD.data_ptr(), self.cell.data_ptr(),
                           self.xL.data_ptr(), self.k.data_ptr(), self.pn.data_ptr(), self.tau.data_ptr(),
                           self.x.data_ptr(), self.surf.data_ptr(), self.prim.data_ptr(), self.bary.data_ptr(),
-                          self.pdf.data_ptr(), self.status.data_ptr(), self.iters.data_ptr())
+                          self.pdf.data_ptr(), self.status.data_ptr(), self.iters.data_ptr(),
+                          None if self.chain_cell is None else self.chain_cell.data_ptr())
 
     def aos(self):
         """Host copy in the oracle's array-of-structures layout (tests)."""
@@ -470,25 +480,84 @@ def mpg_guide_update(ctx, guide, cell, omega, w, R=None, R_dev=None, weight_shif
                                   weight_shift, _stream(stream)))
 
 
-def mpg_guide_records(ctx, scene, chains, contrib, out=None, with_types=False, stream=None):
+def mpg_guide_records(ctx, scene, chains, contrib, out=None, with_types=False, with_chain=False, stream=None):
     """Records of chains with contrib > 0, in chain order: (cell [B] int32,
-    omega [3, B], w [B], count [4] int32 (entry 0)), or with_types (or a
-    six-tensor `out`): (cell, omega, w, k [B] uint8, tau [B] uint8, count)."""
+    omega [3, B], w [B], count [4] int32 (entry 0)); with_types (or a
+    six-tensor `out`): (cell, omega, w, k [B] uint8, tau [B] uint8, count);
+    with_chain (or seven tensors): (cell, omega, w, k, tau, chain [B] int32, count)."""
     B = chains.B
     if out is None:
         out = [torch.zeros(B, dtype=torch.int32, device="cuda"), torch.zeros((3, B), dtype=torch.float32, device="cuda"),
                torch.zeros(B, dtype=torch.float32, device="cuda")]
-        if with_types:
+        if with_types or with_chain:
             out += [torch.zeros(B, dtype=torch.uint8, device="cuda"), torch.zeros(B, dtype=torch.uint8, device="cuda")]
+        if with_chain:
+            out += [torch.zeros(B, dtype=torch.int32, device="cuda")]
         out = tuple(out + [torch.zeros(4, dtype=torch.int32, device="cuda")])
-    if len(out) == 6:
+    chain = None
+    if len(out) == 7:
+        cell, om, w, k, tau, chain, R = out
+    elif len(out) == 6:
         cell, om, w, k, tau, R = out
     else:
         (cell, om, w, R), k, tau = out, None, None
     cs = chains.struct()
     _check(lib().mpg_guide_records(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(cell), _ptr(om), _ptr(w),
-                                   _ptr(k), _ptr(tau), _ptr(R), _stream(stream)))
+                                   _ptr(k), _ptr(tau), _ptr(chain), _ptr(R), _stream(stream)))
     return out
+
+
+class STree:
+    """Spatial tree of the guide samples (Sec. 5.6; mpg_stree_*): built from
+    the records of a pass (their chain indices) over those chains' (x_D, x_L)."""
+
+    def __init__(self, ctx, chains, rec_chain, R=None, R_dev=None, epsilon=0.1, c=1.0, stream=None):
+        self.ctx = ctx
+        R = int(rec_chain.numel()) if R is None else R
+        h = C.c_void_p()
+        cs = chains.struct()
+        _check(lib().mpg_stree_build(ctx.h, C.byref(cs), _ptr(rec_chain), R, _ptr(R_dev), epsilon, c, C.byref(h),
+                                     _stream(stream)))
+        self.h = h
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().mpg_stree_info(self.h, *[C.byref(x) for x in v]))
+        self.n_samples, self.n_nodes, self.n_leaves, self.n_members = (x.value for x in v)
+
+    def export(self):
+        """Host arrays: axis, split, left, right [n_nodes]; member_leaf, member_rec [n_members]."""
+        n, m = self.n_nodes, self.n_members
+        ax, lf, rt = (np.zeros(n, np.int32) for _ in range(3))
+        sp = np.zeros(n, np.float64)
+        ml, mr = np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
+        _check(lib().mpg_stree_export(self.h, ax.ctypes.data, sp.ctypes.data, lf.ctypes.data, rt.ctypes.data,
+                                      ml.ctypes.data, mr.ctypes.data))
+        return ax, sp, lf, rt, ml[:m], mr[:m]
+
+    def records(self, rec, R_in, out=None, stream=None):
+        """Guide records of the leaves from records (cell, omega, w, k, tau, ...)
+        of capacity R_in: (cell, omega, w, k, tau, count), n_members of them."""
+        M = max(self.n_members, 1)
+        if out is None:
+            out = (torch.zeros(M, dtype=torch.int32, device="cuda"), torch.zeros((3, M), dtype=torch.float32, device="cuda"),
+                   torch.zeros(M, dtype=torch.float32, device="cuda"), torch.zeros(M, dtype=torch.uint8, device="cuda"),
+                   torch.zeros(M, dtype=torch.uint8, device="cuda"), torch.zeros(4, dtype=torch.int32, device="cuda"))
+        cell, om, w, k, tau, R = out
+        _check(lib().mpg_stree_records(self.ctx.h, self.h, _ptr(rec[1]), _ptr(rec[2]), _ptr(rec[3]), _ptr(rec[4]),
+                                       R_in, _ptr(cell), _ptr(om), _ptr(w), _ptr(k), _ptr(tau), om.shape[1], _ptr(R),
+                                       _stream(stream)))
+        return out
+
+    def query(self, chains, out=None, stream=None):
+        """Leaf of each chain (int32 [B]), for chains.chain_cell."""
+        out = out if out is not None else torch.zeros(chains.B, dtype=torch.int32, device="cuda")
+        cs = chains.struct()
+        _check(lib().mpg_stree_query(self.ctx.h, self.h, C.byref(cs), _ptr(out), _stream(stream)))
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().mpg_stree_destroy(self.h)
+            self.h = None
 
 
 def mpg_vmf_build(ctx, guide, cell, omega, w, k, tau, R=None, R_dev=None, weight_shift=16, stream=None):

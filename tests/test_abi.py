@@ -63,5 +63,5 @@ def test_params_struct_layout_matches_header():
     assert fields == [f for f, _ in mpg.mpg_params._fields_]
     body = src[src.index("typedef struct mpg_chains"):src.index("} mpg_chains;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    fields = re.findall(r"\b([a-zA-Z]+)[;,]", body.replace("B, Q, spq", "B; Q; spq"))
+    fields = re.findall(r"\b([a-zA-Z_]+)[;,]", body.replace("B, Q, spq", "B; Q; spq"))
     assert fields == [f for f, _ in mpg.mpg_chains._fields_]
