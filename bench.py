@@ -902,24 +902,31 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
 
     def variance(a, b):
         return float(((a - b) ** 2).mean().item() / 2)
-    for kind in ("histogram", "vmf"):
+    for kind in ("histogram", "vmf", "vmf_tree"):
         pr = PG.Progressive(ctx, PG.glass_sphere_stages(n=256), total_spp=64, guide=kind, device=dev)
         pr.run(0)
         ctx.sync()
-        gr = pr.capture(offset=1 << 44, advance=1 << 40)
+        if kind == "vmf_tree":  # host tree builds: timed uncaptured, wall clock
+            run = lambda i: pr.run((1 << 44) + (i << 40))  # noqa: E731
+            gr = None
+        else:
+            gr = pr.capture(offset=1 << 44, advance=1 << 40)
+            run = lambda i: gr.launch()  # noqa: E731
         ctx.reset_stats()
-        ms = timed_loop(lambda i: gr.launch(), steps, 2, flush, stream, torch)
+        ms = timed_loop(run, steps, 2, flush, stream, torch)
         st = ctx.stats()
         per = steps + 2
-        gr.launch()
+        run(100)
         ctx.sync()
         a = pr.image.double().clone()
-        gr.launch()
+        run(101)
         ctx.sync()
         out[kind] = {"plan_spp": pr.plan, "render_spp": pr.render_spp, "chains": pr.total_chains(),
                      "ms_per_schedule": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
-                     "graph_kernels": gr.kernels(), "mean_E": float(a.mean().item()),
-                     "per_point_variance_of_E": variance(a, pr.image.double())}
+                     "graph_kernels": gr.kernels() if gr is not None else None, "captured": gr is not None,
+                     "mean_E": float(a.mean().item()), "per_point_variance_of_E": variance(a, pr.image.double())}
+        if kind == "vmf_tree":
+            out[kind]["leaves_last_training_iteration"] = pr.trees[(len(pr.plan) - 1) % 2].n_leaves
         del gr, pr
     wl = I.glass_sphere(n=256, spq=64)
     sc = mpg.Scene(ctx, wl)
@@ -935,7 +942,7 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
         imgs.append(res.E.double().clone())
     out["p0_only"] = {"spp": 64, "chains": wl.B, "mean_E": float(imgs[0].mean().item()),
                       "per_point_variance_of_E": variance(imgs[0], imgs[1])}
-    for kind in ("histogram", "vmf"):
+    for kind in ("histogram", "vmf", "vmf_tree"):
         out[kind]["variance_vs_p0_only"] = out[kind]["per_point_variance_of_E"] / out["p0_only"]["per_point_variance_of_E"]
     return out
 

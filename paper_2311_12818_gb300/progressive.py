@@ -4,11 +4,13 @@ rendering) on the CUDA path.
 The sample schedule comes from mpg_training_plan: training iterations whose
 seed counts per receiver point double, then the rendering stage.  Iteration i
 samples from the guide built by iteration i - 1 (p_0 for the first), and its
-own records build the next guide (histogram or vMF mixture); only the
-rendering stage's contributions form the image.  Every stage is a chain batch
-of its own (receiver points x its seeds per point, light-side points from the
-workload generator), so the whole schedule is a fixed sequence of library
-calls that can be recorded once as a CUDA graph and replayed."""
+own records build the next guide (histogram or vMF mixture over receiver
+cells, or a vMF mixture over the leaves of a spatial tree of its samples);
+only the rendering stage's contributions form the image.  Every stage is a
+chain batch of its own (receiver points x its seeds per point, light-side
+points from the workload generator), so with cell guides the whole schedule
+is a fixed sequence of library calls that can be recorded once as a CUDA
+graph and replayed."""
 from __future__ import annotations
 
 import dataclasses
@@ -26,8 +28,12 @@ class Progressive:
 
     def __init__(self, ctx, make_workload, total_spp, first_spp=1, train_fraction=0.3, guide="histogram",
                  train_repeats=1, render_repeats=1, device="cuda"):
-        if guide not in ("histogram", "vmf"):
-            raise ValueError("guide must be 'histogram' or 'vmf'")
+        """guide: 'histogram' or 'vmf' (one guide cell per receiver cell), or
+        'vmf_tree' (the vMF mixture over the leaves of a spatial tree of each
+        iteration's samples, Sec. 5.6; its host build is synchronous, so that
+        schedule is not recorded as a graph)."""
+        if guide not in ("histogram", "vmf", "vmf_tree"):
+            raise ValueError("guide must be 'histogram', 'vmf' or 'vmf_tree'")
         self.ctx, self.kind = ctx, guide
         self.plan, self.render_spp = mpg.mpg_training_plan(total_spp, first_spp, train_fraction)
         if self.render_spp < 1:
@@ -48,9 +54,12 @@ class Progressive:
         cap = max(wl.B for wl in self.workloads[:-1]) if self.plan else 1
         if guide == "histogram":
             self.guides = [mpg.Guide(wl0.n_cells, I.guide_edges(), device=device) for _ in range(2)]
-        else:
+        elif guide == "vmf":
             self.guides = [mpg.VmfGuide(wl0.n_cells, cap, device=device) for _ in range(2)]
-        self.records = [mpg.mpg_guide_records(ctx, self.scene, ch, res.contrib, with_types=True)
+        else:
+            self.guides = [None, None]  # sized per iteration by its tree
+        self.trees = [None, None]
+        self.records = [mpg.mpg_guide_records(ctx, self.scene, ch, res.contrib, with_chain=True)
                         for ch, res in zip(self.chains[:-1], self.results[:-1])]
 
     def guide_of(self, stage):
@@ -64,6 +73,8 @@ class Progressive:
         for i, (wl, ch, res, P) in enumerate(zip(self.workloads, self.chains, self.results, self.params)):
             g = self.guide_of(i)
             o = offset + (i << 36)
+            if self.kind == "vmf_tree":  # each chain samples the leaf of its (x_D, x_L)
+                ch.chain_cell = None if i == 0 else self.trees[(i - 1) % 2].query(ch, stream=stream)
             mpg.mpg_sample_seeds(ctx, sc, g, ch, P, wl.rng_seed, o, stream=stream)
             mpg.mpg_manifold_walk(ctx, sc, ch, P, stream=stream)
             mpg.mpg_chain_contribution(ctx, sc, g, ch, P, wl.rng_seed, o, out=res, stream=stream)
@@ -75,11 +86,18 @@ class Progressive:
             nxt = self.guides[i % 2]
             if self.kind == "histogram":
                 mpg.mpg_guide_clear(ctx, nxt, stream=stream)
-                mpg.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[5],
+                mpg.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[6],
                                      weight_shift=wl.params.weight_shift, stream=stream)
-            else:
-                mpg.mpg_vmf_build(ctx, nxt, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[5],
+            elif self.kind == "vmf":
+                mpg.mpg_vmf_build(ctx, nxt, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[6],
                                   weight_shift=wl.params.weight_shift, stream=stream)
+            else:
+                tree = mpg.STree(ctx, ch, rec[5], R=wl.B, R_dev=rec[6], stream=stream)
+                leaf_rec = tree.records(rec, wl.B, stream=stream)
+                nxt = mpg.VmfGuide(tree.n_leaves, max(tree.n_members, 1))
+                mpg.mpg_vmf_build(ctx, nxt, *leaf_rec[:5], R=leaf_rec[0].numel(), R_dev=leaf_rec[5],
+                                  weight_shift=wl.params.weight_shift, stream=stream)
+                self.trees[i % 2], self.guides[i % 2] = tree, nxt
         return self.results[-1]
 
     @property
@@ -89,6 +107,8 @@ class Progressive:
 
     def capture(self, offset=0, advance=0):
         """The whole schedule as one graph (run() once first to size the buffers)."""
+        if self.kind == "vmf_tree":
+            raise ValueError("the tree's host build cannot be recorded: run the schedule uncaptured")
         g = mpg.Graph(self.ctx, rng_advance=advance)
         with g:
             self.run(offset, stream=g.stream)

@@ -68,10 +68,10 @@ def test_progressive_schedule_matches_oracle(M, ctx, guide):
         nxt = pr.guides[i % 2]
         if guide == "histogram":
             M.mpg_guide_clear(ctx, nxt)
-            M.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[5],
+            M.mpg_guide_update(ctx, nxt, rec[0], rec[1], rec[2], R=wl.B, R_dev=rec[6],
                                weight_shift=wl.params.weight_shift)
         else:
-            M.mpg_vmf_build(ctx, nxt, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[5],
+            M.mpg_vmf_build(ctx, nxt, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[6],
                             weight_shift=wl.params.weight_shift)
     ctx.sync()
     for i, st in enumerate(stages):
