@@ -21,6 +21,9 @@ struct Builder {
   int T;
   double root_ext[6];
   StreeHost& t;
+  std::vector<int> idx;                       // sample indices; a node owns a contiguous range
+  std::vector<float> X[6];                    // the samples' coordinates, permuted with idx
+  std::vector<double> dist;                   // selection scratch
 
   double at(int i, int a) const { return (double)pos[(size_t)a * n + i]; }
 
@@ -32,20 +35,31 @@ struct Builder {
     return (int)t.axis.size() - 1;
   }
 
-  // The m samples of `side` nearest to the plane x = mid (ties: lower index).
-  std::vector<int> nearest(const std::vector<int>& side, int a, double mid, size_t m) const {
-    std::vector<std::pair<double, int>> d;
-    d.reserve(side.size());
-    for (int s : side) d.push_back({std::fabs(at(s, a) - mid), s});
-    m = std::min(m, d.size());
-    std::partial_sort(d.begin(), d.begin() + m, d.end());
-    std::vector<int> out;
-    for (size_t j = 0; j < m; ++j) out.push_back(d[j].second);
+  // The m samples of idx[b, e) nearest to the plane x = mid (ties: lower
+  // index), as a set: the m-th smallest distance by linear-time selection,
+  // then every sample below it and, at it, the lowest indices.
+  std::vector<int> nearest(size_t b, size_t e, int a, double mid, size_t m) {
+    m = std::min(m, e - b);
+    if (m == 0) return {};
+    const float* x = X[a].data();
+    dist.resize(e - b);
+    for (size_t j = b; j < e; ++j) dist[j - b] = std::fabs((double)x[j] - mid);
+    std::nth_element(dist.begin(), dist.begin() + (m - 1), dist.end());
+    const double thr = dist[m - 1];
+    std::vector<int> out, tie;
+    out.reserve(m);
+    for (size_t j = b; j < e; ++j) {
+      const double d = std::fabs((double)x[j] - mid);
+      if (d < thr) out.push_back(idx[j]);
+      else if (d == thr) tie.push_back(idx[j]);
+    }
+    std::sort(tie.begin(), tie.end());
+    for (size_t j = 0; out.size() < m; ++j) out.push_back(tie[j]);
     return out;
   }
 
-  int build(const std::vector<int>& own, const std::vector<int>& copies, const double* lo, const double* hi,
-            int depth) {
+  // Node over the own samples idx[b, e) and the copies it received.
+  int build(size_t b, size_t e, const std::vector<int>& copies, const double* lo, const double* hi, int depth) {
     const int i = node();
     int a = 0;
     double best = -1.0;
@@ -53,10 +67,11 @@ struct Builder {
       double rel = root_ext[ax] > 0.0 ? (hi[ax] - lo[ax]) / root_ext[ax] : 0.0;
       if (rel > best) { best = rel; a = ax; }
     }
-    if ((int)own.size() <= T || depth >= STREE_MAX_DEPTH || !(best > 0.0)) {
+    const size_t k = e - b;
+    if ((int)k <= T || depth >= STREE_MAX_DEPTH || !(best > 0.0)) {
       const int leaf = t.n_leaves++;
       t.left[i] = leaf;
-      std::vector<int> mem(own);
+      std::vector<int> mem(idx.begin() + b, idx.begin() + e);
       mem.insert(mem.end(), copies.begin(), copies.end());
       std::sort(mem.begin(), mem.end());
       mem.erase(std::unique(mem.begin(), mem.end()), mem.end());
@@ -67,10 +82,18 @@ struct Builder {
       return i;
     }
     const double mid = 0.5 * (lo[a] + hi[a]);
-    std::vector<int> L, R;
-    for (int s : own) (at(s, a) < mid ? L : R).push_back(s);  // own is ascending, so are L and R
-    const size_t m = (size_t)std::floor(eps * (double)own.size());
-    std::vector<int> to_right = nearest(L, a, mid, m), to_left = nearest(R, a, mid, m);
+    // in-place partition without branches, coordinates moved along: [b, j)
+    // below the plane, [j, e) not
+    size_t j = b;
+    float* xa = X[a].data();
+    for (size_t p = b; p < e; ++p) {
+      const bool left = (double)xa[p] < mid;
+      std::swap(idx[p], idx[j]);
+      for (int c = 0; c < 6; ++c) std::swap(X[c][p], X[c][j]);
+      j += left;
+    }
+    const size_t m = (size_t)std::floor(eps * (double)k);
+    std::vector<int> to_right = nearest(b, j, a, mid, m), to_left = nearest(j, e, a, mid, m);
     t.axis[i] = a;
     t.split[i] = mid;
     double hl[6], lr[6];
@@ -78,9 +101,9 @@ struct Builder {
     std::copy(lo, lo + 6, lr);
     hl[a] = mid;
     lr[a] = mid;
-    const int l = build(L, to_left, lo, hl, depth + 1);
+    const int l = build(b, j, to_left, lo, hl, depth + 1);
     t.left[i] = l;
-    const int r = build(R, to_right, lr, hi, depth + 1);
+    const int r = build(j, e, to_right, lr, hi, depth + 1);
     t.right[i] = r;
     return i;
   }
@@ -137,7 +160,7 @@ __global__ void k_stree_query(const int* axis, const double* split, const int* l
 void stree_build(const float* pos, int n, double eps, double c, StreeHost& t) {
   t = StreeHost{};
   t.n_samples = n;
-  Builder B{pos, n, eps, std::max(1, (int)std::floor(c * std::sqrt((double)n))), {}, t};
+  Builder B{pos, n, eps, std::max(1, (int)std::floor(c * std::sqrt((double)n))), {}, t, {}, {}};
   double lo[6], hi[6];
   for (int a = 0; a < 6; ++a) {
     lo[a] = hi[a] = 0.0;
@@ -148,9 +171,11 @@ void stree_build(const float* pos, int n, double eps, double c, StreeHost& t) {
     }
     B.root_ext[a] = hi[a] - lo[a];
   }
-  std::vector<int> all(n);
-  for (int i = 0; i < n; ++i) all[i] = i;
-  B.build(all, {}, lo, hi, 0);
+  B.idx.resize(n);
+  for (int i = 0; i < n; ++i) B.idx[i] = i;
+  for (int a = 0; a < 6; ++a) B.X[a].assign(pos + (size_t)a * n, pos + (size_t)(a + 1) * n);
+  B.dist.reserve(n);
+  B.build(0, (size_t)n, {}, lo, hi, 0);
 }
 
 void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st) {
