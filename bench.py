@@ -995,12 +995,19 @@ def oracle_step(wl, threads):
 
 
 def cpu_baseline(wl_full):
+    """The oracle on all host cores (the whole workload) and on one core (a
+    64 x 64-point sample of it, same extent and seeds per point)."""
     threads = os.cpu_count() or 1
     wl = cpu_sample()
     dt, conv = oracle_step(wl, threads)
+    w1 = cpu_sample(n=64)
+    dt1, conv1 = oracle_step(w1, 1)
     return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "the whole workload (%d chains), one guided step after an untimed training pass, %.1f s"
-                      % (wl.B, dt)}
+                      % (wl.B, dt),
+            "single_core": {"value": conv1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": "64 x 64 receiver points x 16 seeds (%d chains), one guided step, %.1f s"
+                                      % (w1.B, dt1)}}
 
 
 def run_reference(args, rank, world):
