@@ -314,3 +314,38 @@ WORKLOADS = {
     "water": water,
     "mixed": mixed,
 }
+
+
+def synthetic_guide_records(wl: Workload, per_cell: int = 512, seed: int = 0x4D50470014):
+    """Seeded synthetic guide records for a workload (for tests at sizes where
+    no training pass is run): per receiver cell, `per_cell` records with a
+    receiver point of the cell, a direction from it toward a random point
+    within 1.2 radii of a random sphere seed target (or on a rectangle
+    target), a log-uniform weight in [1e-6, 1e-1], a length drawn like the
+    workload's (the geometric law for the mixed batch) and random types.
+    Returns (cell [R] u32, omega [R, 3] f32, w [R] f32, k [R] u8, tau [R] u8)."""
+    rng = np.random.default_rng(seed)
+    cells = np.unique(wl.cell)
+    R = cells.size * per_cell
+    cell = np.repeat(cells, per_cell).astype(np.uint32)
+    pts = np.empty((R, 3))
+    for j, c in enumerate(cells):
+        q = np.nonzero(wl.cell == c)[0]
+        pts[j * per_cell:(j + 1) * per_cell] = wl.xD[rng.choice(q, per_cell)]
+    tg = wl.targets[rng.integers(0, wl.targets.shape[0], R)]
+    off = rng.normal(size=(R, 3))
+    off /= np.linalg.norm(off, axis=1, keepdims=True)
+    aim = np.where((tg[:, 0] == TARGET_SPHERE)[:, None],
+                   tg[:, 1:4] + off * (1.2 * tg[:, 4:5]) * rng.random((R, 1)),
+                   tg[:, 1:4] + (2 * rng.random((R, 1)) - 1) * tg[:, 5:8] + (2 * rng.random((R, 1)) - 1) * tg[:, 8:11])
+    d = aim - pts
+    om = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    w = np.exp(rng.uniform(math.log(1e-6), math.log(1e-1), R)).astype(np.float32)
+    if (wl.k == wl.k[0]).all():
+        k = np.full(R, wl.k[0], np.uint8)
+    else:
+        k = (rng.choice(MAXK, size=R, p=GEOMETRIC_K_PMF) + 1).astype(np.uint8)
+    tau = (rng.integers(0, 256, R) & ((1 << k.astype(np.int64)) - 1)).astype(np.uint8)
+    if not wl.tau_random:
+        tau = np.full(R, wl.tau[0], np.uint8)
+    return cell, om, w, k, tau

@@ -68,7 +68,7 @@ def _oracle_block(sub, guide, off):
     return seeds, ch, cp["T"], adm.astype(bool), N
 
 
-def _compare_blocks(M, wl, ch, res, guide_o, off):
+def _compare_blocks(M, wl, ch, res, guide_o, off, block=None):
     st = ch.status.cpu().numpy()
     x = ch.x.permute(2, 0, 1).double().cpu().numpy()
     surf = ch.surf.T.contiguous().cpu().numpy()
@@ -78,7 +78,7 @@ def _compare_blocks(M, wl, ch, res, guide_o, off):
     flags, same_T, same_N, rel_T, rel_E, dx = [], [], [], [], [], []
     for b0 in _starts(wl):
         sl = slice(b0, b0 + BLOCK)
-        sub = _block(wl, b0, BLOCK)
+        sub = _block(wl, b0, BLOCK) if block is None else block(b0)
         seeds, och, oT, oadm, oN = _oracle_block(sub, guide_o, off + b0)
         g1, o1 = st[sl] == 1, och["status"] == 1
         flags.append(g1 == o1)
@@ -199,3 +199,50 @@ def test_mixed_batch_full_size_captured_step(M, ctx):
     st = ch.status.cpu().numpy()
     for kk in range(1, 9):
         assert ((k == kk) & (st == 1)).sum() > 0
+
+
+def test_mixed_vmf_full_size_captured_step(M, ctx):
+    """The vMF-guided mixed batch (4,194,304 chains, sampled lengths, guided
+    seeds and trials) replayed from its captured graph, as the benchmark's vMF
+    measurement runs it.  The guide is built on both sides from the same seeded
+    synthetic records (no training pass at this size); the oracle redraws the
+    blocks' lengths itself, which must equal the GPU's bit for bit."""
+    from test_gpu_vmf import _compare_guides, _dev_records
+    wl = I.mixed()
+    recs = I.synthetic_guide_records(wl)
+    og = O.VmfGuide(wl.n_cells).build(*recs, wl.params.weight_shift)
+    gg = M.VmfGuide(wl.n_cells, recs[0].size)
+    M.mpg_vmf_build(ctx, gg, *_dev_records(recs), weight_shift=wl.params.weight_shift)
+    ctx.sync()
+    _compare_guides(og, gg)
+    sc = M.Scene(ctx, wl)
+    ch = M.Chains(wl)
+    P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, tau_random=True)
+    res = M.Contribution.empty(wl.B, wl.Q)
+    p0w = I.GEOMETRIC_K_WEIGHTS
+
+    def step(off):
+        M.mpg_sample_lengths(ctx, gg, ch, p0w, P, wl.rng_seed, off, out=(ch.k, ch.pn))
+        M.mpg_sample_seeds(ctx, sc, gg, ch, P, wl.rng_seed, off)
+        M.mpg_manifold_walk(ctx, sc, ch, P)
+        M.mpg_chain_contribution(ctx, sc, gg, ch, P, wl.rng_seed, off, out=res)
+
+    off = 9 * wl.B
+    step(off)
+    ctx.sync()
+    g = M.Graph(ctx, rng_advance=wl.B)
+    with g:
+        step(off)
+    g.launch()
+    ctx.sync()
+    k_gpu = ch.k.cpu().numpy()
+
+    def block(b0):
+        sub = _block(wl, b0, BLOCK)
+        ok, opn = O.sample_lengths(sub, og, p0w, rng_offset=off + b0)
+        assert np.array_equal(ok, k_gpu[b0:b0 + BLOCK])
+        return dataclasses.replace(sub, k=ok, pn=opn)
+
+    _compare_blocks(M, wl, ch, res, og, off, block=block)
+    for kk in range(1, 9):
+        assert ((k_gpu == kk) & (ch.status.cpu().numpy() == 1)).sum() > 0
