@@ -454,7 +454,7 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group")
 
 
 def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
@@ -468,6 +468,7 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
     - repeats: four Bernoulli estimates per chain in rendering (R x 4) or in
       training and rendering (TR x 4) on the guided glass-sphere step;
     - selective: the guided glass-sphere step with selective activation;
+    - glossy: product importance sampling with a glossy separator (mixed batch);
     - progressive: the online training schedule and rendering of a
       64-seed-per-point budget on the glass sphere, as one captured graph."""
     import numpy as np
@@ -493,6 +494,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
         out["vmf_guide"] = part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "repeats" in parts:
         out["repeated_estimates"] = part_repeats(ctx, dev, flush, torch, stream, steps)
+    if "glossy" in parts:
+        out["glossy_separator"] = part_glossy(ctx, dev, flush, torch, stream, steps)
     if "selective" in parts:
         out["selective_activation"] = part_selective(ctx, dev, flush, torch, stream, steps)
     if "progressive" in parts:
@@ -836,6 +839,64 @@ def part_repeats(ctx, dev, flush, torch, stream, steps):
     for name in ("R_x4", "TR_x4"):
         out[name]["variance_vs_single"] = out[name]["per_point_variance_of_E"] / out["single"]["per_point_variance_of_E"]
         out[name]["time_vs_single"] = out[name]["ms_per_step"] / out["single"]["ms_per_step"]
+    return out
+
+
+def part_glossy(ctx, dev, flush, torch, stream, steps):
+    """Glossy separators (Sec. 5.7) on the mixed batch: the receivers carry a
+    normalised Phong lobe (exponent 20) around the mirror direction of rays
+    from a camera at (0, -3, 1).  A p_0 pass gives the records; one histogram
+    guide takes their weights as they are (Eq. eq_weight), the other multiplied
+    by the separator's BSDF (product importance sampling, Eq. eq_weight_pis).
+    Per guide: the guided step's time, and the per-point variance of the
+    radiance toward the camera from two independent steps."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    wl = I.mixed()
+    cam, e = (0.0, -3.0, 1.0), 20.0
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=True, k_uniform=0)
+    mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40)
+    mpg.mpg_manifold_walk(ctx, sc, ch, P)
+    mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40, out=res)
+    rec = mpg.mpg_guide_records(ctx, sc, ch, res.contrib, with_chain=True)
+    guides = {}
+    tree = mpg.STree(ctx, ch, rec[5], R=wl.B, R_dev=rec[6])  # over the p_0 pass's samples
+    for name in ("plain_weights", "product_weights"):
+        w = rec[2].clone()
+        if name == "product_weights":
+            mpg.mpg_records_bsdf(ctx, ch, rec[5], rec[1], w, cam, e, R=wl.B, R_dev=rec[6])
+        g = mpg.Guide(wl.n_cells, I.guide_edges(), device=dev)
+        mpg.mpg_guide_update(ctx, g, rec[0], rec[1], w, R=wl.B, R_dev=rec[6], weight_shift=wl.params.weight_shift)
+        guides["cell_histogram_" + name] = (g, None)
+        lr = tree.records((rec[0], rec[1], w, rec[3], rec[4]), wl.B)
+        v = mpg.VmfGuide(tree.n_leaves, max(tree.n_members, 1))
+        mpg.mpg_vmf_build(ctx, v, *lr[:5], R=lr[0].numel(), R_dev=lr[5], weight_shift=wl.params.weight_shift)
+        guides["tree_vmf_" + name] = (v, tree)
+    leaves = tree.query(ch)
+    out = {"workload": "mixed_k1to8, 4,194,304 chains; Phong separator (exponent %g), camera at %s; tree of %d "
+                       "leaves" % (e, cam, tree.n_leaves)}
+    for name, (g, t) in guides.items():
+        def step(o, g=g, t=t):
+            ch.chain_cell = leaves if t is not None else None
+            mpg.mpg_sample_seeds(ctx, sc, g, ch, P, wl.rng_seed, o)
+            mpg.mpg_manifold_walk(ctx, sc, ch, P)
+            mpg.mpg_chain_contribution(ctx, sc, g, ch, P, wl.rng_seed, o, out=res)
+        imgs = []
+        for o in (5 << 36, 6 << 36):
+            step(o)
+            _, L = mpg.mpg_separator_bsdf(ctx, ch, res.contrib, cam, e)
+            ctx.sync()
+            imgs.append(L.double().clone())
+        ms = timed_loop(lambda i: step((7 << 36) + i * wl.B), max(2, steps // 5), 1, flush, stream, torch)
+        out[name] = {"ms_per_step": ms, "mean_radiance": float(imgs[0].mean().item()),
+                     "per_point_variance": float(((imgs[0] - imgs[1]) ** 2).mean().item() / 2)}
+    ch.chain_cell = None
+    for kind in ("cell_histogram_", "tree_vmf_"):
+        out[kind + "product_over_plain_variance"] = (out[kind + "product_weights"]["per_point_variance"]
+                                                     / out[kind + "plain_weights"]["per_point_variance"])
     return out
 
 

@@ -493,6 +493,24 @@ mpg_status mpg_stree_query(mpg_ctx* ctx, const mpg_stree* tree, const mpg_chains
                            cudaStream_t stream);
 void mpg_stree_destroy(mpg_stree* tree);
 
+/* Sec. 5.7 -- glossy separators.  The receiver's BSDF is a normalised Phong
+ * lobe rho(w_i, w) = (e + 2) / (2 pi) max(0, r.w)^e around the mirror
+ * direction r = w_i - 2 (w_i.n_D) n_D of the camera ray w_i = unit(x_D -
+ * camera) (camera: host float[3]; exponent e > 0).
+ * mpg_separator_bsdf: the radiance estimate toward the camera, radiance[b] =
+ * rho(w_i, w_D) contrib[b] with w_D = unit(x_1 - x_D) (0 where contrib is 0),
+ * and L[q] = sum over the point's seeds / spq.
+ * mpg_records_bsdf: product importance sampling with the separator's BSDF
+ * (Eq. eq_weight_pis): for the records r < n (n = *R_dev, else R) of
+ * mpg_guide_records (chain index, omega SoA [3][R], weight), w[r] *=
+ * rho(w_i(x_D of the record's chain), omega_r), in place, before the guide
+ * update or build. */
+mpg_status mpg_separator_bsdf(mpg_ctx* ctx, const mpg_chains* chains, const float* contrib, const float* camera,
+                              float exponent, float* radiance, float* L, cudaStream_t stream);
+mpg_status mpg_records_bsdf(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, const float* omega,
+                            float* w, int32_t R, const int32_t* R_dev, const float* camera, float exponent,
+                            cudaStream_t stream);
+
 /* Sample schedule of the progressive training (Sec. 5.8, online training and
  * rendering), in seeds per receiver point: training iterations of first_spp,
  * 2 first_spp, 4 first_spp, ... seeds; training never uses more than

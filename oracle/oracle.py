@@ -431,3 +431,41 @@ def progressive(make_workload, total_spp, first_spp=1, train_fraction=0.3, guide
     last = stages[-1]
     image = irradiance(last["wl"], last["contrib"]["T"], last["N"], last["contrib"]["admissible"])
     return plan, render, stages, image
+
+
+def phong(w_i, n, w, exponent):
+    """Separator BSDF of the glossy-separator extension (Sec. 5.7): a
+    normalised Phong lobe (e + 2) / (2 pi) max(0, r.w)^e around the mirror
+    direction r = w_i - 2 (w_i.n) n of the incoming camera ray w_i (unit,
+    toward x_D), for unit directions w leaving x_D.  Arrays [m, 3]."""
+    w_i, n, w = (np.atleast_2d(np.asarray(a, np.float64)) for a in (w_i, n, w))
+    r = w_i - 2.0 * np.sum(w_i * n, axis=1, keepdims=True) * n
+    c = np.maximum(np.sum(r * w, axis=1), 0.0)
+    return (exponent + 2.0) / (2.0 * math.pi) * c ** exponent
+
+
+def camera_rays(wl, camera):
+    """Unit directions from the camera position to each receiver point [Q, 3]."""
+    d = wl.xD - np.asarray(camera, np.float64)[None, :]
+    return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def separator_radiance(wl, chains, contrib, camera, exponent):
+    """Radiance toward the camera at each receiver point: (1/M) sum over its
+    seeds of rho(w_i, w_D) times the chain's contribution, w_D = unit(x_1 - x_D).
+    Returns (per-chain weighted contributions [B], per-point radiance [Q])."""
+    q = np.arange(wl.B) // wl.spq
+    d = chains["x"][:, 0, :] - wl.xD[q]
+    nrm = np.linalg.norm(d, axis=1, keepdims=True)
+    w_D = d / np.where(nrm > 0, nrm, 1.0)
+    rho = phong(camera_rays(wl, camera)[q], wl.nD[q], w_D, exponent)
+    c = np.where(contrib > 0, rho * contrib, 0.0)
+    return c, c.reshape(wl.Q, wl.spq).sum(axis=1) / wl.spq
+
+
+def records_bsdf(wl, chain, omega, w, camera, exponent):
+    """Product importance sampling weights (Eq. eq_weight_pis): each record's
+    weight times the separator BSDF at its receiver point toward its direction."""
+    q = np.asarray(chain, np.int64) // wl.spq
+    rho = phong(camera_rays(wl, camera)[q], wl.nD[q], np.asarray(omega, np.float64), exponent)
+    return (np.asarray(w, np.float64) * rho).astype(np.float32)

@@ -1357,6 +1357,41 @@ mpg_status mpg_stree_query(mpg_ctx* ctx, const mpg_stree* t, const mpg_chains* c
   return MPG_OK;
 }
 
+mpg_status mpg_separator_bsdf(mpg_ctx* ctx, const mpg_chains* chains, const float* contrib, const float* camera,
+                              float exponent, float* radiance, float* L, cudaStream_t st) {
+  if (!ctx || !camera) return fail(MPG_ERR_INVALID_ARG, "ctx or camera is NULL");
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (!(exponent > 0.0f) || !aligned16(contrib) || !aligned16(radiance) || !aligned16(L))
+    return fail(MPG_ERR_INVALID_ARG, "invalid separator BSDF arguments (exponent %g, arrays)", exponent);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  DChains c = to_dev(chains);
+  timed(ctx, MPG_KERNEL_AUX, st, 2, [&] {
+    launch_separator_bsdf(c, contrib, make_float3(camera[0], camera[1], camera[2]), exponent, radiance, ctx->sms, st);
+    launch_irradiance(radiance, c.Q, c.spq, L, ctx->sms, st);
+  });
+  LAUNCH_CHECK("separator BSDF");
+  return MPG_OK;
+}
+
+mpg_status mpg_records_bsdf(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, const float* omega,
+                            float* w, int32_t R, const int32_t* R_dev, const float* camera, float exponent,
+                            cudaStream_t st) {
+  if (!ctx || !camera) return fail(MPG_ERR_INVALID_ARG, "ctx or camera is NULL");
+  mpg_status s;
+  if ((s = check_chains(chains, false))) return s;
+  if (R < 0 || !(exponent > 0.0f) || (R > 0 && (!aligned16(rec_chain) || !aligned16(omega) || !aligned16(w))))
+    return fail(MPG_ERR_INVALID_ARG, "invalid record arguments (R %d, exponent %g)", R, exponent);
+  if (R == 0) return MPG_OK;
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  timed(ctx, MPG_KERNEL_AUX, st, 1, [&] {
+    launch_records_bsdf(to_dev(chains), rec_chain, omega, w, R, R_dev, make_float3(camera[0], camera[1], camera[2]),
+                        exponent, ctx->sms, st);
+  });
+  LAUNCH_CHECK("record BSDF weights");
+  return MPG_OK;
+}
+
 mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_fraction, int32_t max_iters,
                              int32_t* iter_spp, int32_t* n_iters, int32_t* render_spp) {
   if (total_spp < 0 || first_spp < 1 || !(train_fraction >= 0.0f && train_fraction <= 1.0f) || max_iters < 0 ||

@@ -150,6 +150,56 @@ void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* ome
 
 // Records (cell, w_D, w = contrib / A_L) of chains with a contribution.
 // ---------------------------------------------------------------------------
+// Glossy separators (Sec. 5.7): a normalised Phong lobe around the mirror
+// direction of the camera ray, applied to the contributions (radiance) and to
+// the guide records' weights (product importance sampling, Eq. eq_weight_pis)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float phong_rho(float3 w_i, float3 n, float3 w, float e) {
+  const float3 r = w_i - n * (2.0f * dot(w_i, n));
+  return (e + 2.0f) * 0.15915494309189535f * powf(fmaxf(dot(r, w), 0.0f), e);
+}
+
+__device__ __forceinline__ float3 receiver_at(const float* a, int Q, int q) {
+  return make_float3(a[q], a[Q + q], a[2 * Q + q]);
+}
+
+__global__ void k_separator_bsdf(DChains c, const float* contrib, float3 cam, float e, float* radiance) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c.B; b += gridDim.x * blockDim.x) {
+    const float cb = contrib[b];
+    float out = 0.0f;
+    if (cb > 0.0f) {
+      const int q = b / c.spq;
+      const float3 xD = receiver_at(c.xD, c.Q, q);
+      const float3 x1 = make_float3(c.x[b], c.x[(size_t)c.B + b], c.x[2 * (size_t)c.B + b]);
+      out = phong_rho(unit(xD - cam), receiver_at(c.nD, c.Q, q), unit(x1 - xD), e) * cb;
+    }
+    radiance[b] = out;
+  }
+}
+
+__global__ void k_records_bsdf(DChains c, const int* rec_chain, const float* omega, float* w, int R, const int* R_dev,
+                               float3 cam, float e) {
+  const int n = R_dev ? min(max(*R_dev, 0), R) : R;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const int q = rec_chain[r] / c.spq;
+    const float3 xD = receiver_at(c.xD, c.Q, q);
+    const float3 om = make_float3(omega[r], omega[R + r], omega[2 * (size_t)R + r]);
+    w[r] *= phong_rho(unit(xD - cam), receiver_at(c.nD, c.Q, q), om, e);
+  }
+}
+
+void launch_separator_bsdf(const DChains& c, const float* contrib, float3 cam, float e, float* radiance, int sms,
+                           cudaStream_t st) {
+  k_separator_bsdf<<<std::max(1, std::min(sms * 8, (c.B + 255) / 256)), 256, 0, st>>>(c, contrib, cam, e, radiance);
+}
+
+void launch_records_bsdf(const DChains& c, const int* rec_chain, const float* omega, float* w, int R, const int* R_dev,
+                         float3 cam, float e, int sms, cudaStream_t st) {
+  k_records_bsdf<<<std::max(1, std::min(sms * 8, (R + 255) / 256)), 256, 0, st>>>(c, rec_chain, omega, w, R, R_dev,
+                                                                                  cam, e);
+}
+
+// ---------------------------------------------------------------------------
 // End of a Bernoulli trial round
 // ---------------------------------------------------------------------------
 __global__ void k_bern_finish(float area, DChains c, DOut o, const int* list, const int* n_list, const int* base,

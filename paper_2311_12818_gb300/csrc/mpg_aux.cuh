@@ -35,6 +35,11 @@ void launch_vmf_build(const DGuide& g, uint32_t* scratch, const uint32_t* cell, 
                       cudaStream_t st);
 void launch_sample_lengths(const DGuide* g, const DChains& c, const uint32_t* p0w, uint2 key, uint64_t offset,
                            float alpha, DCtx ctx, uint8_t* k_out, float* pn_out, int sms, cudaStream_t st);
+// Glossy separators (mpg_aux.cu).
+void launch_separator_bsdf(const DChains& c, const float* contrib, float3 cam, float e, float* radiance, int sms,
+                           cudaStream_t st);
+void launch_records_bsdf(const DChains& c, const int* rec_chain, const float* omega, float* w, int R, const int* R_dev,
+                         float3 cam, float e, int sms, cudaStream_t st);
 // Spatial tree of the guide samples (mpg_stree.cu).
 void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st);
 void launch_stree_records(const int* member_leaf, const int* member_rec, int M, const float* omega, const float* w,

@@ -81,7 +81,7 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
            "mpg_sample_lengths", "mpg_training_plan", "mpg_stree_build", "mpg_stree_info", "mpg_stree_export",
-           "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy"]
+           "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy", "mpg_separator_bsdf", "mpg_records_bsdf"]
 
 _lib = None
 
@@ -126,6 +126,8 @@ def lib():
         L.mpg_stree_records.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp]
         L.mpg_stree_query.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp]
         L.mpg_stree_destroy.argtypes = [vp]
+        L.mpg_separator_bsdf.argtypes = [vp, C.POINTER(mpg_chains), vp, C.POINTER(f32), f32, vp, vp, vp]
+        L.mpg_records_bsdf.argtypes = [vp, C.POINTER(mpg_chains), vp, vp, vp, i32, vp, C.POINTER(f32), f32, vp]
         L.mpg_stree_destroy.restype = None
         L.mpg_sample_lengths.argtypes = [vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), vp, u64, u64,
                                          C.POINTER(mpg_params), vp, vp, vp]
@@ -505,6 +507,27 @@ def mpg_guide_records(ctx, scene, chains, contrib, out=None, with_types=False, w
     _check(lib().mpg_guide_records(ctx.h, scene.h, C.byref(cs), _ptr(contrib), _ptr(cell), _ptr(om), _ptr(w),
                                    _ptr(k), _ptr(tau), _ptr(chain), _ptr(R), _stream(stream)))
     return out
+
+
+def mpg_separator_bsdf(ctx, chains, contrib, camera, exponent, out=None, stream=None):
+    """Radiance toward the camera through the glossy separator (Sec. 5.7):
+    (per-chain weighted contributions [B], per-point radiance [Q])."""
+    rad, L = out if out is not None else (torch.zeros(chains.B, dtype=torch.float32, device="cuda"),
+                                          torch.zeros(chains.Q, dtype=torch.float32, device="cuda"))
+    cam = (C.c_float * 3)(*[float(v) for v in camera])
+    cs = chains.struct()
+    _check(lib().mpg_separator_bsdf(ctx.h, C.byref(cs), _ptr(contrib), cam, float(exponent), _ptr(rad), _ptr(L),
+                                    _stream(stream)))
+    return rad, L
+
+
+def mpg_records_bsdf(ctx, chains, rec_chain, omega, w, camera, exponent, R=None, R_dev=None, stream=None):
+    """Product importance sampling weights (Eq. eq_weight_pis), in place on w."""
+    R = int(w.numel()) if R is None else R
+    cam = (C.c_float * 3)(*[float(v) for v in camera])
+    cs = chains.struct()
+    _check(lib().mpg_records_bsdf(ctx.h, C.byref(cs), _ptr(rec_chain), _ptr(omega), _ptr(w), R, _ptr(R_dev), cam,
+                                  float(exponent), _stream(stream)))
 
 
 class STree:

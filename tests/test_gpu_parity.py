@@ -470,3 +470,34 @@ def test_selective_activation(M, ctx, kind):
     assert 0.2 < active.mean() < 0.8
     assert not (gs["status"] != 0)[~active].any() and not os2["valid"][~active].any()
     _compare_seeds(on, gs, os2)
+
+
+def test_glossy_separator(M, ctx):
+    """Glossy separators (Sec. 5.7): the radiance through the separator's
+    Phong lobe and the product importance sampling weights (Eq.
+    eq_weight_pis) on the oracle's chains and records, against the oracle."""
+    wl = I.mixed(nx=64, ny=32, spq=8)
+    cam, e = (0.0, -3.0, 1.0), 20.0
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    adm = con["admissible"] == 1
+    contrib = np.where(adm, wl.light_area * con["T"] * N / wl.pn, 0.0).astype(np.float32)
+    oc, oL = O.separator_radiance(wl, ow, contrib.astype(np.float64), cam, e)
+    ch = _chains_from_oracle(M, wl, ow, np.where(adm, M.CHAIN_CONVERGED, M.CHAIN_FAILED))
+    rad, L = M.mpg_separator_bsdf(ctx, ch, torch.as_tensor(contrib, device="cuda"), cam, e)
+    ctx.sync()
+    rad, L = rad.cpu().numpy().astype(np.float64), L.cpu().numpy().astype(np.float64)
+    big = oc > 1e-6 * oc.max()
+    assert big.sum() > 100 and np.all(rad[~adm] == 0)
+    assert np.quantile(np.abs(rad[big] - oc[big]) / oc[big], 0.999) < 1e-4
+    assert np.allclose(L, oL, rtol=1e-4, atol=1e-6 * oL.max())
+    cell, om, w = O.records(wl, ow, con["T"], N, con["admissible"])
+    chain = np.nonzero(adm)[0]
+    wo = O.records_bsdf(wl, chain, om, w, cam, e).astype(np.float64)
+    gw = torch.as_tensor(w, device="cuda")
+    M.mpg_records_bsdf(ctx, ch, torch.as_tensor(chain.astype(np.int32), device="cuda"),
+                       torch.as_tensor(np.ascontiguousarray(om.T), device="cuda"), gw, cam, e)
+    ctx.sync()
+    gw = gw.cpu().numpy().astype(np.float64)
+    big = wo > 1e-6 * wo.max()
+    assert big.sum() > 100
+    assert np.quantile(np.abs(gw[big] - wo[big]) / wo[big], 0.999) < 1e-4
