@@ -6,7 +6,11 @@
  * between two separators x_D and x_L, Newton manifold walks on the specular
  * constraints, the contribution T = kappa G L_o of each admissible chain, its
  * reciprocal probability by Bernoulli trials, the guide-histogram update, and
- * the adjoint of the receiver irradiance with respect to surface parameters.
+ * the adjoint of the receiver irradiance with respect to surface parameters;
+ * and around it the paper's guiding machinery: the vMF mixture with sampled
+ * chain lengths and types, the spatial tree of the guide samples, glossy
+ * separators with product importance sampling, repeated reciprocal estimates,
+ * selective activation and the online training schedule.
  *
  * Conventions for every entry point:
  *   - Return value: MPG_OK (0) or a negative mpg_status.  The message of the
