@@ -1,10 +1,13 @@
 """Multi-process helpers: one process per GPU, chains partitioned across ranks.
 
 Chains are independent, so the walk, contribution and trials need no
-collective.  Two things cross ranks:
+collective.  Three things cross ranks:
   - the guide histograms of a training pass (each rank adds its own records;
     the pass's guide is the sum).  Counts are integers, so the sum is exact and
     independent of the reduction order: every rank ends with the same bits.
+  - the records of a pass for the vMF guide (and its spatial tree): lobes are
+    built from all records, so the ranks' records are gathered in rank order
+    and every rank builds the same guide from the same concatenation.
   - the job's throughput: units processed on all ranks over the slowest rank's
     time.
 """
@@ -39,3 +42,26 @@ def job_throughput(t_ms: float, units: float, device="cpu", group=None):
     dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
     dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
     return float(t.item()), float(u.item())
+
+
+def allgather_records(arrays, counts=None, group=None):
+    """Concatenation in rank order of every rank's records: `arrays` is a list
+    of tensors whose first dimension indexes the records (the same dtypes and
+    trailing shapes on every rank), `counts` the number of valid leading
+    records per rank (default: all).  Returns the gathered tensors; a stable
+    build from them is then identical on every rank."""
+    n = int(arrays[0].shape[0]) if counts is None else int(counts)
+    mine = torch.tensor([n], dtype=torch.int64, device=arrays[0].device)
+    world = dist.get_world_size(group)
+    sizes = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(sizes, mine, group=group)
+    sizes = [int(x.item()) for x in sizes]
+    top = max(sizes)
+    out = []
+    for a in arrays:
+        pad = torch.zeros((top,) + tuple(a.shape[1:]), dtype=a.dtype, device=a.device)
+        pad[:n] = a[:n]
+        parts = [torch.zeros_like(pad) for _ in range(world)]
+        dist.all_gather(parts, pad, group=group)
+        out.append(torch.cat([p[:sz] for p, sz in zip(parts, sizes)]))
+    return out
