@@ -6,6 +6,7 @@
 // run on the GPU for every chain.
 #include <algorithm>
 #include <cmath>
+#include <future>
 
 #include "mpg_aux.cuh"
 
@@ -13,19 +14,50 @@ namespace mpg {
 
 namespace {
 constexpr int STREE_MAX_DEPTH = 48;
+constexpr int STREE_PAR_DEPTH = 4;  // subtrees below this depth are built on threads of their own
 
-struct Builder {
+// What every part of one build shares: the samples and the index array whose
+// disjoint ranges the parts partition in place.
+struct Shared {
   const float* pos;  // [6][n]
   int n;
   double eps;
   int T;
   double root_ext[6];
-  StreeHost& t;
-  std::vector<int> idx;                       // sample indices; a node owns a contiguous range
-  std::vector<float> X[6];                    // the samples' coordinates, permuted with idx
-  std::vector<double> dist;                   // selection scratch
+  std::vector<int> idx;     // sample indices; a node owns a contiguous range
+  std::vector<float> X[6];  // the samples' coordinates, permuted with idx
+};
 
-  double at(int i, int a) const { return (double)pos[(size_t)a * n + i]; }
+// Appends part `p` (nodes, leaves and members numbered from 0) to `t`;
+// returns the index its root node gets.
+int splice(StreeHost& t, const StreeHost& p) {
+  const int off = (int)t.axis.size(), leaf0 = t.n_leaves;
+  for (size_t j = 0; j < p.axis.size(); ++j) {
+    const bool leaf = p.axis[j] < 0;
+    t.axis.push_back(p.axis[j]);
+    t.split.push_back(p.split[j]);
+    t.left.push_back(leaf ? p.left[j] + leaf0 : p.left[j] + off);
+    t.right.push_back(leaf ? -1 : p.right[j] + off);
+  }
+  for (size_t m = 0; m < p.member_rec.size(); ++m) {
+    t.member_leaf.push_back(p.member_leaf[m] + leaf0);
+    t.member_rec.push_back(p.member_rec[m]);
+  }
+  t.n_leaves += p.n_leaves;
+  return off;
+}
+
+struct Builder {
+  Shared& sh;
+  StreeHost& t;
+  std::vector<double> dist;  // selection scratch
+  const std::vector<float>* X;
+  std::vector<int>& idx;
+  const double eps;
+  const int T;
+  const double* root_ext;
+
+  Builder(Shared& s, StreeHost& out) : sh(s), t(out), X(s.X), idx(s.idx), eps(s.eps), T(s.T), root_ext(s.root_ext) {}
 
   int node() {
     t.axis.push_back(-1);
@@ -85,11 +117,12 @@ struct Builder {
     // in-place partition without branches, coordinates moved along: [b, j)
     // below the plane, [j, e) not
     size_t j = b;
-    float* xa = X[a].data();
+    std::vector<float>* Xs = sh.X;
+    const float* xa = Xs[a].data();
     for (size_t p = b; p < e; ++p) {
       const bool left = (double)xa[p] < mid;
       std::swap(idx[p], idx[j]);
-      for (int c = 0; c < 6; ++c) std::swap(X[c][p], X[c][j]);
+      for (int c = 0; c < 6; ++c) std::swap(Xs[c][p], Xs[c][j]);
       j += left;
     }
     const size_t m = (size_t)std::floor(eps * (double)k);
@@ -101,6 +134,19 @@ struct Builder {
     std::copy(lo, lo + 6, lr);
     hl[a] = mid;
     lr[a] = mid;
+    if (depth < STREE_PAR_DEPTH && k > 4096) {
+      // the two subtrees on two threads, each into a part of its own, then
+      // appended in the order the sequential build numbers them
+      StreeHost pl, pr;
+      auto left = std::async(std::launch::async, [&] { Builder(sh, pl).build(b, j, to_left, lo, hl, depth + 1); });
+      Builder(sh, pr).build(j, e, to_right, lr, hi, depth + 1);
+      left.get();
+      const int l = splice(t, pl);
+      t.left[i] = l;
+      const int r = splice(t, pr);
+      t.right[i] = r;
+      return i;
+    }
     const int l = build(b, j, to_left, lo, hl, depth + 1);
     t.left[i] = l;
     const int r = build(j, e, to_right, lr, hi, depth + 1);
@@ -160,22 +206,25 @@ __global__ void k_stree_query(const int* axis, const double* split, const int* l
 void stree_build(const float* pos, int n, double eps, double c, StreeHost& t) {
   t = StreeHost{};
   t.n_samples = n;
-  Builder B{pos, n, eps, std::max(1, (int)std::floor(c * std::sqrt((double)n))), {}, t, {}, {}};
+  Shared sh;
+  sh.pos = pos;
+  sh.n = n;
+  sh.eps = eps;
+  sh.T = std::max(1, (int)std::floor(c * std::sqrt((double)n)));
   double lo[6], hi[6];
   for (int a = 0; a < 6; ++a) {
     lo[a] = hi[a] = 0.0;
     for (int i = 0; i < n; ++i) {
-      double x = B.at(i, a);
+      double x = (double)pos[(size_t)a * n + i];
       if (i == 0 || x < lo[a]) lo[a] = x;
       if (i == 0 || x > hi[a]) hi[a] = x;
     }
-    B.root_ext[a] = hi[a] - lo[a];
+    sh.root_ext[a] = hi[a] - lo[a];
   }
-  B.idx.resize(n);
-  for (int i = 0; i < n; ++i) B.idx[i] = i;
-  for (int a = 0; a < 6; ++a) B.X[a].assign(pos + (size_t)a * n, pos + (size_t)(a + 1) * n);
-  B.dist.reserve(n);
-  B.build(0, (size_t)n, {}, lo, hi, 0);
+  sh.idx.resize(n);
+  for (int i = 0; i < n; ++i) sh.idx[i] = i;
+  for (int a = 0; a < 6; ++a) sh.X[a].assign(pos + (size_t)a * n, pos + (size_t)(a + 1) * n);
+  Builder(sh, t).build(0, (size_t)n, {}, lo, hi, 0);
 }
 
 void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st) {
