@@ -84,3 +84,30 @@ def test_coincident_samples_end_at_the_depth_limit():
         i = t.left[i] if p[0, t.axis[i]] < t.split[i] else t.right[i]
         depth += 1
     assert depth == MAX_DEPTH
+
+
+def test_per_chain_cells_equal_point_cells_when_they_agree():
+    """Seeds, sampled lengths and trials take a chain's own cell when given;
+    with every chain on its point's cell the results are those of the
+    per-point path."""
+    from oracle import oracle as O
+    from paper_2311_12818_gb300 import inputs as I
+    wl = I.mixed(nx=32, ny=16, spq=8)
+    recs = I.synthetic_guide_records(wl, per_cell=64)
+    g = O.VmfGuide(wl.n_cells).build(*recs, wl.params.weight_shift)
+    cc = np.repeat(wl.cell, wl.spq).astype(np.uint32)
+    k1, p1 = O.sample_lengths(wl, g, I.GEOMETRIC_K_WEIGHTS, rng_offset=5)
+    k2, p2 = O.sample_lengths(wl, g, I.GEOMETRIC_K_WEIGHTS, rng_offset=5, chain_cell=cc)
+    assert np.array_equal(k1, k2) and np.array_equal(p1, p2)
+    sc = O.Scene(wl)
+    a = O.sample_seeds(wl, sc, g, rng_offset=5)
+    b = O.sample_seeds(wl, sc, g, rng_offset=5, chain_cell=cc)
+    assert all(np.array_equal(a[f], b[f]) for f in ("x", "surf", "tau", "pdf", "valid"))
+    # and a different cell for some chains changes exactly their draws' guide
+    cc2 = cc.copy()
+    cc2[::7] = (cc2[::7] + 1) % wl.n_cells
+    c = O.sample_seeds(wl, sc, g, rng_offset=5, chain_cell=cc2)
+    same = np.ones(wl.B, bool)
+    same[::7] = False
+    assert np.array_equal(a["pdf"][same], c["pdf"][same])
+    assert not np.array_equal(a["pdf"][~same], c["pdf"][~same])
