@@ -59,3 +59,28 @@ def test_radiance_estimate_unbiased_with_product_weights():
         contrib = np.where(k2["admissible"] == 1, wl.light_area * k2["T"] * N2 / wl.pn, 0.0)
         c, L = O.separator_radiance(wl, c2, contrib, cam, e)
         assert abs(L[0] - L_true) < 4 * c.std() / math.sqrt(M) + 1e-12
+
+
+def test_product_weights_and_radiance_on_the_mirror_direction():
+    """A direction along the mirror of the camera ray about the receiver normal
+    gets the lobe's peak (e + 2) / (2 pi); one perpendicular to it gets zero --
+    for the records' product weights and for the chains' radiance alike."""
+    wl = I.glass_sphere(n=4, spq=2)
+    cam, e = (0.3, -2.0, 1.0), 30.0
+    xD, nD = wl.xD, wl.nD
+    wi = (xD - np.array(cam)) / np.linalg.norm(xD - np.array(cam), axis=1, keepdims=True)
+    r = wi - 2 * np.sum(wi * nD, axis=1, keepdims=True) * nD   # mirror of the camera ray
+    perp = np.cross(r, [0.0, 0.0, 1.0])
+    perp /= np.linalg.norm(perp, axis=1, keepdims=True)
+    chain = np.arange(wl.B)
+    q = chain // wl.spq
+    om = np.where((chain % 2 == 0)[:, None], r[q], perp[q]).astype(np.float32)
+    w = np.full(wl.B, 0.5, np.float32)
+    got = O.records_bsdf(wl, chain, om, w, cam, e)
+    peak = (e + 2) / (2 * math.pi)
+    assert np.allclose(got[0::2], 0.5 * peak, rtol=1e-5) and np.all(got[1::2] < 1e-12)
+    x = np.zeros((wl.B, I.MAXK, 3))
+    x[:, 0, :] = xD[q] + 2.0 * om.astype(np.float64)
+    c, L = O.separator_radiance(wl, dict(x=x), np.ones(wl.B), cam, e)
+    assert np.allclose(c[0::2], peak, rtol=1e-5) and np.all(c[1::2] < 1e-12)
+    assert np.allclose(L, peak / 2, rtol=1e-5)
