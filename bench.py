@@ -274,6 +274,12 @@ def run_ours(args, rank, world, local):
     from paper_2311_12818_gb300 import dist as D
     t_ms, conv_all = D.job_throughput(t_ms, float(conv), device=dev)  # max time, summed walks
     value = conv_all / (t_ms * 1e-3)
+    # irradiance throughput: receiver points and admissible contributions (the
+    # records of each context's last timed step) per second, all ranks
+    contrib_step = sum(int(bf["rec"][3][0].item()) for bf in bufs) / len(bufs)
+    irr = {"shading_points_per_s": world * Q * steps_run / (t_ms * 1e-3),
+           "contributions_per_s": world * contrib_step * steps_run / (t_ms * 1e-3),
+           "contributions_per_step": contrib_step}
 
     # ---- attribution: the same steps uncaptured, each launch bracketed by
     # CUDA events on its own stream (per-family time, counters and flops)
@@ -374,7 +380,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "clocks": clk,
-        "detail": {"converged_per_step": conv / steps_run, "walks_per_step": total["walks"] / steps_run,
+        "detail": {"irradiance_throughput": irr,
+                   "converged_per_step": conv / steps_run, "walks_per_step": total["walks"] / steps_run,
                    "trials_per_step": total["trials"] / steps_run,
                    "fp64_geometry_terms_per_step": total["ggt_fp64"] / steps_run,
                    "step_ms": [round(x, 4) for x in step_ms],
