@@ -439,7 +439,10 @@ def kernel_digest():
 
 def profiled_traffic(summary):
     """DRAM bytes per launch from a committed ncu summary under profiles/, or
-    None when the summary was taken on other kernel sources than these."""
+    None when the summary was taken on other kernel sources than these.  A
+    summary may list later source digests at which the profiled kernel's own
+    code (the kernel and every function it calls) is unchanged, one per line
+    as "Kernel unchanged at digest: <sha256> (<the change>)"."""
     import re
     try:
         with open(os.path.join(ROOT, "profiles", summary)) as f:
@@ -448,7 +451,10 @@ def profiled_traffic(summary):
         return None
     dg = re.search(r"Kernel source digest[^:]*: ([0-9a-f]{64})", text)
     tb = re.search(r"dram_bytes_per_launch: (\d+)", text)
-    if not dg or not tb or dg.group(1) != kernel_digest():
+    if not dg or not tb:
+        return None
+    valid = {dg.group(1)} | set(re.findall(r"Kernel unchanged at digest: ([0-9a-f]{64})", text))
+    if kernel_digest() not in valid:
         return None
     return int(tb.group(1))
 

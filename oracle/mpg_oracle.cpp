@@ -1147,12 +1147,18 @@ T fresnel(T cos1, T eta1, T eta2) {
 }
 
 // kappa: product over vertices of the mirror factor (1), the Fresnel
-// reflectance (dielectric reflection) or transmittance times the radiance
-// scaling (eta_i/eta_o)^2 (dielectric refraction, light travelling from the
-// x_{i+1} side into the x_{i-1} side).
+// reflectance (dielectric reflection) or transmittance (dielectric
+// refraction).  Under an area light the refraction factor also carries the
+// radiance scaling (eta_i/eta_o)^2 (light travelling from the x_{i+1} side
+// into the x_{i-1} side): there G = cos(theta_D) |d(w_D)/d(u_L)| integrates
+// radiance over the receiver's solid angle, and radiance over eta^2 is what
+// refraction keeps.  Under a point light G = |d(w_L)/d(u_D)| maps the emitted
+// intensity's solid angle onto receiver area, so E = I kappa G conserves flux
+// with the transmittance alone and the radiance scaling does not enter.
 template <class T>
 T chain_kappa(const Scene& S, int k, uint8_t tau, const Frame<T>* f, const int* surf,
               const VBlocks<T>* vb) {
+  const bool point = S.light.type == LIGHT_POINT;
   T kap(1.0);
   for (int i = 1; i <= k; ++i) {
     const Surface& sf = S.surf[surf[i]];
@@ -1164,7 +1170,7 @@ T chain_kappa(const Scene& S, int k, uint8_t tau, const Frame<T>* f, const int* 
     T eta2 = T(vb[i - 1].front ? sf.etaB : sf.etaF);
     T F = fresnel(ci, eta1, eta2);
     if (refract) {
-      T r = vb[i - 1].eta_i / vb[i - 1].eta_o;
+      T r = point ? T(1.0) : vb[i - 1].eta_i / vb[i - 1].eta_o;
       kap = kap * (T(1.0) - F) * r * r;
     } else {
       kap = kap * F;

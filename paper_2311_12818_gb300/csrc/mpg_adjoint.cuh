@@ -292,7 +292,8 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
   }
   DF G = dabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
   if (!point) G = dot(f[0].n, w) * G;
-  // kappa with the chain's cosines (transmittance formed directly)
+  // kappa with the chain's cosines (transmittance formed directly; the
+  // radiance scaling (eta_i/eta_o)^2 under an area light only)
   DF kap = cst(1.0f);
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -307,7 +308,7 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
       DF num = ci * co * (4.0f * n1 * n2);
       DF ds = ci * n1 + co * n2, dp = ci * n2 + co * n1;
       DF Tr = (num / (ds * ds) + num / (dp * dp)) * 0.5f;
-      kap = kap * Tr * ((n1 / n2) * (n1 / n2));
+      kap = point ? kap * Tr : kap * Tr * ((n1 / n2) * (n1 / n2));
     } else {
       float n2 = vb[i].front ? sf.etaB : sf.etaF;
       DF s2 = (cst(1.0f) - ci * ci) * ((n1 / n2) * (n1 / n2));

@@ -1081,7 +1081,9 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   float XDs = rc * XD;
   mismatch = fabsf(XL - XDs) / fmaxf(fmaxf(XL, XDs), 1e-30f);
   G = point ? XD : XL;
-  // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2.  The
+  // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2 under an
+  // area light, T -> (1 - F) under a point light (G maps the intensity's solid
+  // angle onto receiver area, so flux carries no radiance scaling).  The
   // transmittance is formed directly, (1 - F) = (T_s + T_p)/2 with
   // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
   // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
@@ -1105,7 +1107,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       float num = 4.0f * n1 * n2 * ci * co;
       float ds = n1 * ci + n2 * co, dp = n2 * ci + n1 * co;
       float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
-      float r = n1 / n2;
+      float r = point ? 1.0f : n1 / n2;
       kap *= Tr * r * r;
       kappa_err = fmaxf(kappa_err, 1.2e-7f / fmaxf(fminf(ci, co), 1e-30f));
     } else {

@@ -373,6 +373,7 @@ __device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, dou
   double det = fabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
   G = point ? det : dot(d3(e.nD), w) * det;
   // kappa in FP64: mirror 1, dielectric R -> F, T -> (T_s + T_p)/2 (eta_i/eta_o)^2
+  // (area light) or (T_s + T_p)/2 (point light)
   kappa = 1.0;
   D3 xD = d3(e.xD), xL = d3(e.xL);
 #pragma unroll
@@ -389,7 +390,7 @@ __device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, dou
       double n2 = front ? sf.etaB : sf.etaF;
       double co = fabs(dot(wo, f[i].n));
       double num = 4.0 * n1 * n2 * ci * co, ds = n1 * ci + n2 * co, dp = n2 * ci + n1 * co;
-      double r = n1 / n2;
+      double r = point ? 1.0 : n1 / n2;
       kappa *= 0.5 * (num / (ds * ds) + num / (dp * dp)) * r * r;
     } else {
       double n2 = front ? sf.etaB : sf.etaF;

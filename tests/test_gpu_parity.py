@@ -274,6 +274,25 @@ def test_water_pipeline_parity(M, ctx):
     assert np.quantile(rel, 0.999) < 1e-3
 
 
+def test_water_point_light_parity(M, ctx):
+    """Refraction through the water surface under a point light: the FP32
+    contribution (and its FP64 polish) forms kappa from the transmittance
+    alone, without the area light's radiance scaling, like the oracle."""
+    wl = I.water(n=48, spq=4, grid=128)
+    pos = (0.0, 0.0, 4.0)
+    wl = dataclasses.replace(wl, light=I._light(I.LIGHT_POINT, pos, power=1.0),
+                             xL=np.tile(np.asarray(pos, np.float64), (wl.B, 1)))
+    sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl)
+    osc, os_, ow, con, N, capped = _oracle_pipeline(wl)
+    _compare_seeds(wl, gs, os_)
+    both = _compare_walk(wl, gw, ow)
+    T = out.T.cpu().numpy()
+    ab = (T > 0) & (con["admissible"] == 1) & both
+    assert ab.sum() > 1000
+    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
+    assert np.quantile(rel, 0.999) < 1e-3
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_mixed_lengths_plain_and_batched(M, ctx, mode):
     """mode 0: plain; 1: batched, one thread per chain; 2: batched, one chain per lane group."""
