@@ -474,6 +474,14 @@ void mpg_graph_destroy(mpg_graph* graph);
 typedef struct mpg_stree mpg_stree;
 mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,
                            const int32_t* R_dev, float epsilon, float c, mpg_stree** out, cudaStream_t stream);
+/* The same tree from host positions: pos [6][n] host FP32 (x_D then x_L,
+ * coordinate-major; borrowed, read during the call), record r at column r.
+ * Built on the host with no device copy and no CUDA call, so it needs no
+ * GPU; mpg_stree_info and mpg_stree_export work on it, mpg_stree_records and
+ * mpg_stree_query reject it (MPG_ERR_INVALID_ARG).  Errors: pos NULL with
+ * n > 0, n < 0, epsilon outside [0, 0.5), c <= 0 or a non-finite position
+ * (MPG_ERR_INVALID_ARG). */
+mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, mpg_stree** out);
 /* Sizes of a tree: samples, nodes, leaves and leaf members (own + copies). */
 mpg_status mpg_stree_info(const mpg_stree* tree, int32_t* n_samples, int32_t* n_nodes, int32_t* n_leaves,
                           int32_t* n_members);

@@ -1235,6 +1235,10 @@ struct mpg_stree {
 
 void mpg_stree_destroy(mpg_stree* t) {
   if (!t) return;
+  if (t->device < 0) {  // host-only tree
+    delete t;
+    return;
+  }
   cudaSetDevice(t->device);
   cudaFree(t->d_axis); cudaFree(t->d_left); cudaFree(t->d_right); cudaFree(t->d_split);
   cudaFree(t->d_member_leaf); cudaFree(t->d_member_rec);
@@ -1299,6 +1303,20 @@ mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t
   return MPG_OK;
 }
 
+mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, mpg_stree** out) {
+  if (!out) return fail(MPG_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 0 || (n > 0 && !pos) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f))
+    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (n %d, epsilon %g, c %g)", n, epsilon, c);
+  for (size_t i = 0; i < (size_t)6 * n; ++i)
+    if (!std::isfinite(pos[i])) return fail(MPG_ERR_INVALID_ARG, "position %zu is not finite", i);
+  mpg_stree* t = new mpg_stree;
+  t->device = -1;
+  stree_build(pos, n, (double)epsilon, (double)c, t->h);
+  *out = t;
+  return MPG_OK;
+}
+
 mpg_status mpg_stree_info(const mpg_stree* t, int32_t* n_samples, int32_t* n_nodes, int32_t* n_leaves,
                           int32_t* n_members) {
   if (!t) return fail(MPG_ERR_INVALID_ARG, "tree is NULL");
@@ -1324,6 +1342,7 @@ mpg_status mpg_stree_export(const mpg_stree* t, int32_t* axis, double* split, in
 mpg_status mpg_stree_records(mpg_ctx* ctx, const mpg_stree* t, const float* omega, const float* w, const uint8_t* k,
                              const uint8_t* tau, int32_t R_in, uint32_t* cell_out, float* omega_out, float* w_out,
                              uint8_t* k_out, uint8_t* tau_out, int32_t R_out, int32_t* R_out_dev, cudaStream_t st) {
+  if (t && t->device < 0) return fail(MPG_ERR_INVALID_ARG, "the tree has no device copy (built from host positions)");
   if (!ctx || !t) return fail(MPG_ERR_INVALID_ARG, "ctx or tree is NULL");
   const int M = (int)t->h.member_rec.size();
   if (R_out < M || R_in < t->h.n_samples)
@@ -1344,6 +1363,7 @@ mpg_status mpg_stree_records(mpg_ctx* ctx, const mpg_stree* t, const float* omeg
 
 mpg_status mpg_stree_query(mpg_ctx* ctx, const mpg_stree* t, const mpg_chains* chains, uint32_t* chain_cell,
                            cudaStream_t st) {
+  if (t && t->device < 0) return fail(MPG_ERR_INVALID_ARG, "the tree has no device copy (built from host positions)");
   if (!ctx || !t) return fail(MPG_ERR_INVALID_ARG, "ctx or tree is NULL");
   mpg_status s;
   if ((s = check_chains(chains, false))) return s;

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libmpg.so")
 
 MAXK = 8
 MPG_OK = 0
+MPG_ERR_INVALID_ARG, MPG_ERR_CUDA, MPG_ERR_OOM, MPG_ERR_LIMIT, MPG_ERR_UNSUPPORTED = -1, -2, -3, -4, -5
 CHAIN_INVALID, CHAIN_CONVERGED, CHAIN_FAILED, CHAIN_LIMIT, CHAIN_SEEDED = 0, 1, 2, 3, 255
 WALK_PLAIN, WALK_BATCHED = 0, 1
 
@@ -80,7 +81,7 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
-           "mpg_sample_lengths", "mpg_training_plan", "mpg_stree_build", "mpg_stree_info", "mpg_stree_export",
+           "mpg_sample_lengths", "mpg_training_plan", "mpg_stree_build", "mpg_stree_build_host", "mpg_stree_info", "mpg_stree_export",
            "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy", "mpg_separator_bsdf", "mpg_records_bsdf"]
 
 _lib = None
@@ -121,6 +122,7 @@ def lib():
         L.mpg_vmf_build.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.mpg_training_plan.argtypes = [i32, i32, f32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.mpg_stree_build.argtypes = [vp, C.POINTER(mpg_chains), vp, i32, vp, f32, f32, C.POINTER(vp), vp]
+        L.mpg_stree_build_host.argtypes = [vp, i32, f32, f32, C.POINTER(vp)]
         L.mpg_stree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.mpg_stree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.mpg_stree_records.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp]
@@ -541,6 +543,22 @@ class STree:
         cs = chains.struct()
         _check(lib().mpg_stree_build(ctx.h, C.byref(cs), _ptr(rec_chain), R, _ptr(R_dev), epsilon, c, C.byref(h),
                                      _stream(stream)))
+        self._adopt(h)
+
+    @classmethod
+    def from_host(cls, pos, epsilon=0.1, c=1.0):
+        """The tree of host positions pos [n, 6] (x_D, x_L) with no device copy
+        (mpg_stree_build_host; needs no GPU): info and export only."""
+        pos = np.ascontiguousarray(np.asarray(pos, np.float32).reshape(-1, 6).T)
+        h = C.c_void_p()
+        _check(lib().mpg_stree_build_host(pos.ctypes.data if pos.size else None, pos.shape[1], epsilon, c,
+                                          C.byref(h)))
+        t = cls.__new__(cls)
+        t.ctx = None
+        t._adopt(h)
+        return t
+
+    def _adopt(self, h):
         self.h = h
         v = [C.c_int32() for _ in range(4)]
         _check(lib().mpg_stree_info(self.h, *[C.byref(x) for x in v]))
