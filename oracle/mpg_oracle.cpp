@@ -1034,12 +1034,20 @@ static void chain_frames(const Scene& S, const ChainIO& ch, const V3d& nD, Frame
   f[ch.k + 1] = light_frame(S.light, ch.v[ch.k + 1].p);
 }
 
-static void eval_chain(const Scene& S, const ChainIO& ch, const V3d& nD, EvalOut& ev) {
+// off (may be NULL): offset normals of a glossy chain, [k][2] tangential
+// components in each vertex's (s, t) frame; the constraint becomes
+// C_i = (h.s, h.t) - off_i (Sec. 5.7, glossy chains).  The Jacobian blocks do
+// not change.
+static void eval_chain(const Scene& S, const ChainIO& ch, const V3d& nD, EvalOut& ev,
+                       const double* off = nullptr) {
   chain_frames(S, ch, nD, ev.f);
   int surf[MAXK + 2];
   for (int i = 0; i <= ch.k + 1; ++i) surf[i] = ch.v[i].surf;
   ev.ok = chain_blocks<double>(S, ch.k, ch.tau, ev.f, surf, ev.vb);
   if (!ev.ok) return;
+  if (off)
+    for (int i = 0; i < ch.k; ++i)
+      for (int c = 0; c < 2; ++c) ev.vb[i].C[c] -= off[2 * i + c];
   ev.cmax = 0.0;
   ev.cnorm2 = 0.0;
   for (int i = 0; i < ch.k; ++i)
@@ -1099,11 +1107,12 @@ static bool propose(const Scene& S, const ChainIO& ch, const Frame<double>* f, c
   return true;
 }
 
-static int walk_chain(const Scene& S, ChainIO& ch, const V3d& nD, const orc_params& prm, int& iters) {
+static int walk_chain(const Scene& S, ChainIO& ch, const V3d& nD, const orc_params& prm, int& iters,
+                      const double* off = nullptr) {
   EvalOut ev;
   for (int it = 0;; ++it) {
     iters = it;
-    eval_chain(S, ch, nD, ev);
+    eval_chain(S, ch, nD, ev, off);
     if (!ev.ok) return ST_FAILED;
     if (ev.cmax < prm.tol) return ST_CONVERGED;
     if (it >= prm.max_iter) return ST_LIMIT;
@@ -1117,7 +1126,7 @@ static int walk_chain(const Scene& S, ChainIO& ch, const V3d& nD, const orc_para
       ChainIO cand;
       if (!propose(S, ch, ev.f, du, beta, cand)) continue;
       EvalOut ec;
-      eval_chain(S, cand, nD, ec);
+      eval_chain(S, cand, nD, ec, off);
       if (ec.ok && ec.cnorm2 < ev.cnorm2) {
         ch = cand;
         accepted = true;
@@ -1478,6 +1487,138 @@ static bool chain_adjoint(const Scene& S, const ChainIO& ch, const V3d& nD, std:
 
 using namespace orc;
 
+// ---------------------------------------------------------------------------
+// Glossy chains (Sec. 5.7): offset normals.  Every vertex of a glossy chain
+// is a rough interface with an isotropic Beckmann microfacet distribution of
+// roughness alpha.  An offset normal m_i is drawn per vertex before the walk;
+// its tangential components o_i = (m_i.s, m_i.t) in the vertex's shading frame
+// are the constraint's targets (C_i = o_i), and the walk then finds the
+// chains whose half-vectors are the drawn normals, as in the specular case.
+// The estimate of one found chain is the path integrand in area measure over
+// the density of the offsets in the constraint's coordinates:
+//   W = L_e prod_i [f_i |n_i.l_i|] prod_j [geometric factors]
+//       / (|det dC/du| prod_i p(o_i)),
+// dC/du the 2k x 2k Jacobian in orthonormal area coordinates of the surfaces,
+// f_i the microfacet BSDF (Walter et al. 2007: reflection
+// F D G2 / (4 |l.n||v.n|); transmission |l.m||v.m| / (|l.n||v.n|) *
+// eta_v^2 (1 - F) D G2 / (eta_l l.m + eta_v v.m)^2), l toward the light and
+// v toward the receiver, G2 the separable Smith term.  Drawing m with density
+// D(m) (m.n) in solid angle gives o the density D(m) on the unit disk, since
+// the disk's area element is (m.n) times the solid angle.
+// ---------------------------------------------------------------------------
+static double beckmann_D(double cos_m, double alpha) {
+  if (!(cos_m > 0.0)) return 0.0;
+  double c2 = cos_m * cos_m, t2 = (1.0 - c2) / c2;
+  return std::exp(-t2 / (alpha * alpha)) / (PI * alpha * alpha * c2 * c2);
+}
+
+// Smith masking of one direction with cosine c to the macro normal and
+// cosine cm to the microfacet normal (Beckmann, exact Lambda with erf).
+static double smith_G1(double c, double cm, double alpha) {
+  if (!(c * cm > 0.0)) return 0.0;
+  double ac = std::fabs(c);
+  if (ac >= 1.0) return 1.0;
+  double tan_t = std::sqrt(1.0 - ac * ac) / ac;
+  double a = 1.0 / (alpha * tan_t);
+  double lambda = 0.5 * (std::erf(a) - 1.0) + std::exp(-a * a) / (2.0 * a * std::sqrt(PI));
+  return 1.0 / (1.0 + lambda);
+}
+
+// Offset (tangential components) of a normal drawn with density D(m) (m.n):
+// tan^2(theta) = -alpha^2 log(1 - u1), phi = 2 pi u2.
+static void beckmann_offset(double alpha, double u1, double u2, double o[2]) {
+  double t2 = -alpha * alpha * std::log(1.0 - u1);
+  double c = 1.0 / std::sqrt(1.0 + t2), s = std::sqrt(t2) * c;
+  double phi = 2.0 * PI * u2;
+  o[0] = s * std::cos(phi);
+  o[1] = s * std::sin(phi);
+}
+
+// Determinant of a dense n x n matrix by Gaussian elimination with partial
+// pivoting (a different route from the block Thomas sweep).
+static double dense_det(int n, std::vector<double> A) {
+  double det = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r) if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return 0.0;
+    if (piv != c) {
+      for (int q = 0; q < n; ++q) std::swap(A[c * n + q], A[piv * n + q]);
+      det = -det;
+    }
+    det *= A[c * n + c];
+    for (int r = c + 1; r < n; ++r) {
+      double f = A[r * n + c] / A[c * n + c];
+      for (int q = c; q < n; ++q) A[r * n + q] -= f * A[c * n + q];
+    }
+  }
+  return det;
+}
+
+struct GlossyTerms {
+  double detJ = 0.0;    // |det dC/du|
+  double bsdf = 1.0;    // prod_i f_i |n_i.l_i| / D(m_i)  (the BSDF's D divided out)
+  double geom = 1.0;    // receiver cosine, area-measure factors, light factor
+  double dens = 1.0;    // prod_i D(m_i): the offsets' density on the disk
+  double W = 0.0;       // the estimate L_e bsdf geom / detJ (D cancels against dens)
+};
+
+// Terms of one converged glossy chain (alpha > 0) or, with alpha = 0, of the
+// specular limit (D and G2 dropped: the terms then reproduce kappa G).
+static bool glossy_terms(const Scene& S, const ChainIO& ch, const EvalOut& ev, double alpha, GlossyTerms& gt) {
+  const int k = ch.k;
+  std::vector<double> J((size_t)4 * k * k, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int r = 0; r < 2; ++r)
+      for (int c = 0; c < 2; ++c) {
+        J[(size_t)(2 * i + r) * 2 * k + 2 * i + c] = ev.vb[i].B[r][c];
+        if (i > 0) J[(size_t)(2 * i + r) * 2 * k + 2 * (i - 1) + c] = ev.vb[i].A[r][c];
+        if (i < k - 1) J[(size_t)(2 * i + r) * 2 * k + 2 * (i + 1) + c] = ev.vb[i].Cc[r][c];
+      }
+  gt.detJ = std::fabs(dense_det(2 * k, J));
+  if (!(gt.detJ > 0.0)) return false;
+  gt.bsdf = gt.geom = gt.dens = 1.0;
+  for (int i = 1; i <= k; ++i) {
+    const Surface& sf = S.surf[ch.v[i].surf];
+    const Frame<double>& f = ev.f[i];
+    const VBlocks<double>& vb = ev.vb[i - 1];
+    V3d v = normalize(ch.v[i - 1].p - f.p), l = normalize(ch.v[i + 1].p - f.p);
+    double cv = dot(v, f.n), cl = dot(l, f.n);
+    bool refract = (ch.tau >> (i - 1)) & 1;
+    double ev_ = vb.eta_i, el = vb.eta_o;  // indices on the receiver and light sides
+    V3d m = normalize(v * ev_ + l * el);
+    if (dot(m, f.n) < 0.0) m = -m;
+    double vm = dot(v, m), lm = dot(l, m), mn = dot(m, f.n);
+    double F = 1.0;
+    if (sf.mat != MAT_MIRROR) {
+      double e2 = vb.front ? sf.etaB : sf.etaF;
+      F = fresnel<double>(std::fabs(vm), ev_, e2);
+    }
+    double G2 = alpha > 0.0 ? smith_G1(cv, vm, alpha) * smith_G1(cl, lm, alpha) : 1.0;
+    double fhat;  // f_i / D(m_i)
+    if (refract) {
+      double den = ev_ * vm + el * lm;
+      fhat = std::fabs(lm) * std::fabs(vm) / (std::fabs(cl) * std::fabs(cv)) * ev_ * ev_ * (1.0 - F) * G2 /
+             (den * den);
+    } else {
+      fhat = F * G2 / (4.0 * std::fabs(cl) * std::fabs(cv));
+    }
+    gt.bsdf *= fhat * std::fabs(cl);
+    if (alpha > 0.0) gt.dens *= beckmann_D(mn, alpha);
+    // area measure at x_i: |cos| to the surface's geometric normal over d^2
+    V3d ng = normalize(cross(f.dpdu, f.dpdv));
+    double d = norm(ch.v[i - 1].p - f.p);
+    gt.geom *= std::fabs(dot(ng, v)) / (d * d);
+  }
+  V3d w0 = normalize(ch.v[1].p - ch.v[0].p);
+  gt.geom *= std::fabs(dot(ev.f[0].n, w0));
+  double dL = norm(ch.v[k + 1].p - ch.v[k].p);
+  V3d wL = (ch.v[k].p - ch.v[k + 1].p) / dL;
+  gt.geom *= (S.light.type == LIGHT_POINT ? 1.0 : std::fabs(dot(S.light.n, wL))) / (dL * dL);
+  gt.W = S.light.power * gt.bsdf * gt.geom / gt.detJ;
+  return true;
+}
+
 extern "C" {
 
 void* orc_scene_create(const double* surfaces, int32_t n_surf, const double* hf_desc,
@@ -1581,7 +1722,7 @@ int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const d
 int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
                  const double* xL, const uint8_t* k, const uint8_t* tau, const orc_params* prm,
                  const uint8_t* valid, double* x, int32_t* surf, int32_t* prim, double* bary,
-                 uint8_t* status, uint8_t* iters, int32_t n_threads) {
+                 uint8_t* status, uint8_t* iters, int32_t n_threads, const double* offset) {
   if (!scene || !prm || B < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   orc_params P = *prm;
@@ -1590,7 +1731,8 @@ int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const do
     ChainIO ch;
     load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
     int it = 0;
-    int st = walk_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), P, it);
+    int st = walk_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), P, it,
+                        offset ? offset + (size_t)b * 2 * MAXK : nullptr);
     status[b] = (uint8_t)st;
     iters[b] = (uint8_t)it;
     store_chain(ch, b, x, surf, prim, bary);
@@ -1634,7 +1776,7 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
                       uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads,
-                      const uint32_t* chain_cell) {
+                      const uint32_t* chain_cell, const double* offset) {
   if (!scene || !prm || Q < 0 || spq <= 0) return -1;
   const Scene& S = *(Scene*)scene;
   orc_params P = *prm;
@@ -1664,7 +1806,8 @@ int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const doub
                                   (uint64_t)b + rng_offset, (uint32_t)t | ((uint32_t)rep << 24), P);
         if (!sd.valid) continue;
         int it = 0;
-        if (walk_chain(S, sd.ch, nd, P, it) != ST_CONVERGED) continue;
+        if (walk_chain(S, sd.ch, nd, P, it, offset ? offset + (size_t)b * 2 * MAXK : nullptr) != ST_CONVERGED)
+          continue;
         if (trial_walks) trial_walks[b]++;
         if (same_solution(sd.ch, target, P.dedup_eps)) {
           N[b] += (uint32_t)t;
@@ -1947,5 +2090,55 @@ int32_t orc_unit_flops(double* out) {
   return 0;
 }
 
+
+
+// Offset normals of glossy chains: for chain b (global index b + rng_offset)
+// and vertex i < k[b], one Philox block with counter (index, i, 4) gives the
+// two uniforms of the Beckmann draw; vertices i >= k[b] get zero offsets.
+int32_t orc_sample_offsets(int32_t B, const uint8_t* k, double alpha, uint64_t rng_seed, uint64_t rng_offset,
+                           double* offset) {
+  if (B < 0 || !(alpha > 0.0)) return -1;
+  uint32_t key[2] = {(uint32_t)rng_seed, (uint32_t)(rng_seed >> 32)};
+  for (int b = 0; b < B; ++b) {
+    uint64_t idx = (uint64_t)b + rng_offset;
+    for (int i = 0; i < MAXK; ++i) {
+      double* o = offset + ((size_t)b * MAXK + i) * 2;
+      o[0] = o[1] = 0.0;
+      if (i >= k[b]) continue;
+      uint32_t ctr[4] = {(uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)i, 4u}, r[4];
+      philox4x32_10(ctr, key, r);
+      beckmann_offset(alpha, u01(r[0]), u01(r[1]), o);
+    }
+  }
+  return 0;
+}
+
+// Terms of converged glossy chains: out [B][5] = |det dC/du|, the BSDF
+// product with D divided out, the geometric factors, the offsets' density and
+// the estimate W; admissible[b] as for orc_contribution.  alpha = 0 gives the
+// specular limit.
+int32_t orc_glossy(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD, const double* xL,
+                   const uint8_t* k, const uint8_t* tau, const double* x, const int32_t* surf, const int32_t* prim,
+                   const double* bary, const uint8_t* status, const orc_params* prm, const double* offset,
+                   double alpha, double* out, uint8_t* admissible, int32_t n_threads) {
+  if (!scene || !prm || B < 0 || spq <= 0 || !(alpha >= 0.0)) return -1;
+  const Scene& S = *(Scene*)scene;
+  parallel_for(B, n_threads, [&](int b) {
+    for (int j = 0; j < 5; ++j) out[(size_t)b * 5 + j] = 0.0;
+    admissible[b] = 0;
+    if (status[b] != ST_CONVERGED) return;
+    ChainIO ch;
+    load_chain(S, b, k[b], tau[b], xD, xL, x, surf, prim, bary, spq, ch);
+    EvalOut ev;
+    eval_chain(S, ch, load3(nD + 3 * (size_t)(b / spq)), ev, offset ? offset + (size_t)b * 2 * MAXK : nullptr);
+    if (!ev.ok || !admissible_chain(S, ch, ev, prm->ray_eps)) return;
+    GlossyTerms gt;
+    if (!glossy_terms(S, ch, ev, alpha, gt)) return;
+    admissible[b] = 1;
+    double* o = out + (size_t)b * 5;
+    o[0] = gt.detJ; o[1] = gt.bsdf; o[2] = gt.geom; o[3] = gt.dens; o[4] = gt.W;
+  });
+  return 0;
+}
 
 }  // extern "C"

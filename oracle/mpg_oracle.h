@@ -83,11 +83,13 @@ int32_t orc_sample_seeds(void* scene, const orc_guide* guide, int32_t Q, const d
                          double* bary, uint8_t* tau_out, double* pdf, uint8_t* valid,
                          int32_t n_threads, const uint32_t* chain_cell);
 
-/* Manifold walk in place on chains with valid[b] != 0. */
+/* Manifold walk in place on chains with valid[b] != 0.  offset (may be NULL):
+ * offset normals of glossy chains, [B][8][2] tangential components per vertex;
+ * the walk then solves C_i = off_i (Sec. 5.7, glossy chains). */
 int32_t orc_walk(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD,
                  const double* xL, const uint8_t* k, const uint8_t* tau, const orc_params* prm,
                  const uint8_t* valid, double* x, int32_t* surf, int32_t* prim, double* bary,
-                 uint8_t* status, uint8_t* iters, int32_t n_threads);
+                 uint8_t* status, uint8_t* iters, int32_t n_threads, const double* offset);
 
 /* Admissibility, generalized geometry term, kappa, T = kappa G L_o. */
 int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
@@ -102,14 +104,17 @@ int32_t orc_contribution(void* scene, int32_t B, int32_t spq, const double* xD,
  * trial_walks[b] (may be NULL) = trial walks that converged.  With
  * bern_repeats = r > 1 the estimate is repeated r times independently (repeat
  * j draws trial t with trial counter t | j << 24) and N[b] is the sum of the
- * r trial counts, so <1/P(x | n)> = N[b] / r; capped when any repeat capped. */
+ * r trial counts, so <1/P(x | n)> = N[b] / r; capped when any repeat capped.
+ * offset (may be NULL): the offset normals of glossy chains ([B][8][2], as for
+ * orc_walk); every trial of chain b walks with chain b's offsets, so N[b]
+ * estimates 1/P(x | n, offsets). */
 int32_t orc_bernoulli(void* scene, const orc_guide* guide, int32_t Q, const double* xD,
                       const double* nD, const uint32_t* cell, int32_t spq, const double* xL,
                       const uint8_t* k, const uint8_t* tau, int32_t tau_random,
                       uint64_t rng_seed, uint64_t rng_offset, const orc_params* prm,
                       const double* x, const int32_t* surf, const uint8_t* admissible,
                       uint32_t* N, uint8_t* capped, uint32_t* trial_walks, int32_t n_threads,
-                      const uint32_t* chain_cell);
+                      const uint32_t* chain_cell, const double* offset);
 
 /* Histogram bin of each direction (theta-major index), and the update
  * counts[cell][bin] += q(w), q = min(floor(w 2^S), 2^32-1) (0 unless w > 0). */
@@ -159,6 +164,24 @@ int32_t orc_adjoint(void* scene, int32_t B, int32_t spq, const double* xD, const
                     const uint8_t* k, const uint8_t* tau, const double* x, const int32_t* surf,
                     const int32_t* prim, const double* bary, const double* weight, double* dL_dtheta,
                     double* dT_out, int32_t n_threads);
+
+/* Glossy chains (Sec. 5.7): offset normals drawn from an isotropic Beckmann
+ * distribution of roughness alpha > 0, [B][8][2] tangential components per
+ * vertex (zero beyond k[b]); chain b uses Philox counter (b + rng_offset,
+ * vertex, 4). */
+int32_t orc_sample_offsets(int32_t B, const uint8_t* k, double alpha, uint64_t rng_seed, uint64_t rng_offset,
+                           double* offset);
+
+/* Terms of converged glossy chains walked with `offset` (may be NULL):
+ * out [B][5] = |det dC/du| (orthonormal area coordinates), the microfacet
+ * BSDF product with D divided out, the geometric factors, the offsets'
+ * density prod D(m_i) on the disk, and the estimate W = L_e bsdf geom / det;
+ * admissible[b] as for orc_contribution.  alpha = 0: the specular limit
+ * (no D, no shadowing), whose W equals kappa G L_e. */
+int32_t orc_glossy(void* scene, int32_t B, int32_t spq, const double* xD, const double* nD, const double* xL,
+                   const uint8_t* k, const uint8_t* tau, const double* x, const int32_t* surf, const int32_t* prim,
+                   const double* bary, const uint8_t* status, const orc_params* prm, const double* offset,
+                   double alpha, double* out, uint8_t* admissible, int32_t n_threads);
 
 /* Philox4x32-10 block: out = philox(ctr[4], key[2]). */
 void orc_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out);

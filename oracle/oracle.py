@@ -61,14 +61,18 @@ def lib():
                                        _i32p, _f64p, _u8p, _f64p, _u8p, C.c_int32, C.c_void_p]
         L.orc_walk.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p,
                                C.POINTER(orc_params), _u8p, _f64p, _i32p, _i32p, _f64p, _u8p, _u8p,
-                               C.c_int32]
+                               C.c_int32, C.c_void_p]
         L.orc_contribution.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p,
                                        _u8p, _f64p, _i32p, _i32p, _f64p, _u8p,
                                        C.POINTER(orc_params), _f64p, _f64p, _f64p, _u8p, C.c_int32]
         L.orc_bernoulli.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, _f64p, _f64p, _u32p,
                                     C.c_int32, _f64p, _u8p, _u8p, C.c_int32, C.c_uint64, C.c_uint64,
                                     C.POINTER(orc_params), _f64p, _i32p, _u8p, _u32p, _u8p, C.c_void_p,
-                                    C.c_int32, C.c_void_p]
+                                    C.c_int32, C.c_void_p, C.c_void_p]
+        L.orc_sample_offsets.argtypes = [C.c_int32, _u8p, C.c_double, C.c_uint64, C.c_uint64, _f64p]
+        L.orc_glossy.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _f64p, _f64p, _f64p, _u8p, _u8p, _f64p, _i32p,
+                                 _i32p, _f64p, _u8p, C.POINTER(orc_params), C.c_void_p, C.c_double, _f64p, _u8p,
+                                 C.c_int32]
         L.orc_guide_bin.argtypes = [C.POINTER(orc_guide), C.c_int32, _f32p, _i32p]
         L.orc_guide_update.argtypes = [C.POINTER(orc_guide), _u64p, C.c_int32, _u32p, _f32p, _f32p,
                                        C.c_int32]
@@ -90,7 +94,7 @@ def lib():
         L.orc_philox.restype = None
         for name in ("orc_intersect", "orc_sample_seeds", "orc_walk", "orc_contribution",
                      "orc_bernoulli", "orc_guide_bin", "orc_guide_update", "orc_constraint",
-                     "orc_shoot", "orc_vmf_build", "orc_sample_lengths"):
+                     "orc_shoot", "orc_vmf_build", "orc_sample_lengths", "orc_sample_offsets", "orc_glossy"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -272,8 +276,17 @@ def sample_seeds(wl, scene, guide=None, trial=0, threads=None, rng_offset=0, cha
     return out
 
 
-def walk(wl, scene, seeds, threads=None):
-    """Walk the seeds in place (copies); returns dict with x/surf/prim/bary/status/iters."""
+def _offsets(offset, B):
+    if offset is None:
+        return None
+    o = np.ascontiguousarray(offset, np.float64)
+    assert o.shape == (B, MAXK, 2), o.shape
+    return o
+
+
+def walk(wl, scene, seeds, threads=None, offset=None):
+    """Walk the seeds in place (copies); returns dict with x/surf/prim/bary/status/iters.
+    offset [B, 8, 2]: offset normals of glossy chains (Sec. 5.7), or None."""
     B = wl.B
     ch = {n: seeds[n].copy() for n in ("x", "surf", "prim", "bary")}
     status = np.zeros(B, np.uint8)
@@ -282,7 +295,8 @@ def walk(wl, scene, seeds, threads=None):
     rc = lib().orc_walk(scene.h, B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64),
                         _c(wl.xL, np.float64), _c(wl.k, np.uint8), _c(seeds["tau"], np.uint8),
                         C.byref(P), _c(seeds["valid"], np.uint8), ch["x"], ch["surf"], ch["prim"],
-                        ch["bary"], status, iters, threads or default_threads())
+                        ch["bary"], status, iters, threads or default_threads(),
+                        None if (o := _offsets(offset, B)) is None else o.ctypes.data)
     assert rc == 0, rc
     ch.update(status=status, iters=iters, tau=seeds["tau"].copy())
     return ch
@@ -302,7 +316,7 @@ def contribution(wl, scene, chains, threads=None):
 
 
 def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offset=0, max_trials=None,
-              trial_walks=None, chain_cell=None):
+              trial_walks=None, chain_cell=None, offset=None):
     B = wl.B
     cc = _cells(chain_cell)
     N = np.zeros(B, np.uint32)
@@ -319,9 +333,37 @@ def bernoulli(wl, scene, chains, admissible, guide=None, threads=None, rng_offse
                              wl.spq, _c(wl.xL, np.float64), _c(wl.k, np.uint8),
                              _c(chains["tau"], np.uint8), int(wl.tau_random), wl.rng_seed, rng_offset,
                              C.byref(P), chains["x"], chains["surf"], _c(admissible, np.uint8), N,
-                             capped, tw, threads or default_threads(), None if cc is None else cc.ctypes.data)
+                             capped, tw, threads or default_threads(), None if cc is None else cc.ctypes.data,
+                             None if (o := _offsets(offset, B)) is None else o.ctypes.data)
     assert rc == 0, rc
     return N, capped
+
+
+def sample_offsets(wl, alpha, rng_offset=0):
+    """Offset normals of glossy chains (Sec. 5.7): [B, 8, 2] tangential
+    components drawn from a Beckmann distribution of roughness alpha."""
+    out = np.zeros((wl.B, MAXK, 2))
+    rc = lib().orc_sample_offsets(wl.B, _c(wl.k, np.uint8), float(alpha), wl.rng_seed, rng_offset, out)
+    assert rc == 0, rc
+    return out
+
+
+def glossy(wl, scene, chains, offset=None, alpha=0.0, threads=None):
+    """Terms of converged glossy chains (Sec. 5.7): |det dC/du|, the BSDF
+    product with D divided out, the geometric factors, the offsets' density,
+    the estimate W (alpha = 0: the specular limit) and admissibility."""
+    B = wl.B
+    out = np.zeros((B, 5))
+    adm = np.zeros(B, np.uint8)
+    P = params(wl.params)
+    o = _offsets(offset, B)
+    rc = lib().orc_glossy(scene.h, B, wl.spq, _c(wl.xD, np.float64), _c(wl.nD, np.float64), _c(wl.xL, np.float64),
+                          _c(wl.k, np.uint8), _c(chains["tau"], np.uint8), _c(chains["x"], np.float64),
+                          _c(chains["surf"], np.int32), _c(chains["prim"], np.int32), _c(chains["bary"], np.float64),
+                          _c(chains["status"], np.uint8), C.byref(P), None if o is None else o.ctypes.data,
+                          float(alpha), out, adm, threads or default_threads())
+    assert rc == 0, rc
+    return dict(detJ=out[:, 0], bsdf=out[:, 1], geom=out[:, 2], dens=out[:, 3], W=out[:, 4], admissible=adm)
 
 
 def constraint(wl, scene, chains):

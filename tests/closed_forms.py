@@ -105,3 +105,83 @@ def flat_interface_G(hD, hL, thD, thL, etaD, etaL):
     dthL = etaD * math.cos(thD) / (etaL * math.cos(thL))
     drho = hD / math.cos(thD) ** 2 + hL / math.cos(thL) ** 2 * dthL
     return math.cos(thD) * math.sin(thD) / (rho * drho)
+
+
+# --- rough interfaces (microfacet BSDFs, Walter et al. 2007) -----------------
+
+def beckmann_D(cos_m, alpha):
+    """Isotropic Beckmann normal distribution (solid-angle density of m times
+    m.n integrates to one over the hemisphere)."""
+    cos_m = np.asarray(cos_m, np.float64)
+    c2 = np.clip(cos_m, 1e-300, None) ** 2
+    return np.where(cos_m > 0, np.exp(-(1 - c2) / c2 / alpha ** 2) / (math.pi * alpha ** 2 * c2 ** 2), 0.0)
+
+
+def smith_G1(c, cm, alpha):
+    """Smith masking for the Beckmann distribution, exact Lambda (erf form)."""
+    c, cm = np.asarray(c, np.float64), np.asarray(cm, np.float64)
+    ac = np.clip(np.abs(c), 1e-300, 1.0)
+    tan_t = np.sqrt(np.clip(1 - ac ** 2, 0, None)) / ac
+    a = np.minimum(1.0 / (alpha * np.clip(tan_t, 1e-300, None)), 1e8)  # Lambda is 0 to double precision beyond
+    from scipy.special import erf
+    lam = 0.5 * (erf(a) - 1) + np.exp(-a * a) / (2 * a * math.sqrt(math.pi))
+    g = np.where(tan_t > 0, 1 / (1 + lam), 1.0)
+    return np.where(c * cm > 0, g, 0.0)
+
+
+def fresnel_vec(cos1, eta1, eta2):
+    cos1 = np.abs(np.asarray(cos1, np.float64))
+    s2 = (eta1 / eta2) ** 2 * (1 - cos1 ** 2)
+    c2 = np.sqrt(np.clip(1 - s2, 0, None))
+    rs = (eta1 * cos1 - eta2 * c2) / (eta1 * cos1 + eta2 * c2)
+    rp = (eta2 * cos1 - eta1 * c2) / (eta2 * cos1 + eta1 * c2)
+    return np.where(s2 >= 1, 1.0, 0.5 * (rs * rs + rp * rp))
+
+
+def rough_plane_irradiance(xD, nD, xL, light_n, alpha, eta_v, eta_other, refract, half_extent, n_r=400, n_phi=256,
+                           r_max=4.0, centre=None):
+    """Irradiance at x_D from one bounce off (refract=False) or through
+    (refract=True) the rough plane z = 0, |x|, |y| <= half_extent, normal +z:
+    the area integral over x_1 of
+        f(l, v) |n.l| * |n.v| / d_D^2 * |n_D.w_D| * L(x_L -> x_1)
+    with L = |n_L.l| / d_L^2 per unit emitter area (light_n given) or 1 / d_L^2
+    (point light, light_n None), by Gauss-Legendre in r (r = r_max u^2 around
+    `centre`) and the periodic trapezoid rule in phi.  eta_v: index on the
+    receiver's side, eta_other: index on the far side of the interface (the
+    light's side when refract)."""
+    eta_l = eta_other if refract else eta_v
+    xD, xL, nD = (np.asarray(a, np.float64) for a in (xD, xL, nD))
+    c = np.asarray(centre if centre is not None else xD[:2], np.float64)
+    u, wu = np.polynomial.legendre.leggauss(n_r)
+    u = 0.5 * (u + 1)
+    wu = 0.5 * wu
+    r = r_max * u * u
+    wr = wu * 2 * r_max * u * r  # dr = 2 r_max u du, area element r dr dphi
+    phi = np.arange(n_phi) * (2 * math.pi / n_phi)
+    R, P = np.meshgrid(r, phi, indexing="ij")
+    W = np.broadcast_to(wr[:, None] * (2 * math.pi / n_phi), R.shape)
+    X = np.stack([c[0] + R * np.cos(P), c[1] + R * np.sin(P), np.zeros_like(R)], -1)
+    inside = (np.abs(X[..., 0]) <= half_extent) & (np.abs(X[..., 1]) <= half_extent)
+    n = np.array([0.0, 0.0, 1.0])
+    dv, dl = xD - X, xL - X
+    d0, dL = np.linalg.norm(dv, axis=-1), np.linalg.norm(dl, axis=-1)
+    v, l = dv / d0[..., None], dl / dL[..., None]
+    cv, cl = v @ n, l @ n
+    m = eta_v * v + eta_l * l
+    m = m / np.linalg.norm(m, axis=-1)[..., None]
+    m = np.where((m @ n)[..., None] < 0, -m, m)
+    vm, lm, mn = (v * m).sum(-1), (l * m).sum(-1), m @ n
+    D = beckmann_D(mn, alpha)
+    G2 = smith_G1(cv, vm, alpha) * smith_G1(cl, lm, alpha)
+    F = fresnel_vec(vm, eta_v, eta_other)
+    if refract:
+        den = eta_l * lm + eta_v * vm
+        f = np.abs(lm) * np.abs(vm) / (np.abs(cl) * np.abs(cv)) * eta_v ** 2 * (1 - F) * D * G2 / den ** 2
+        ok = cv * cl < 0
+    else:
+        f = F * D * G2 / (4 * np.abs(cl) * np.abs(cv))
+        ok = cv * cl > 0
+    wD = -v
+    Lin = (np.abs(l @ np.asarray(light_n, np.float64)) if light_n is not None else 1.0) / dL ** 2
+    val = f * np.abs(cl) * np.abs(cv) / d0 ** 2 * np.abs(wD @ nD) * Lin
+    return float(np.sum(np.where(inside & ok, val, 0.0) * W))
