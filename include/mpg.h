@@ -469,19 +469,34 @@ void mpg_graph_destroy(mpg_graph* graph);
  * record index.
  * mpg_stree_build reads the record count (*R_dev, else R) and the records'
  * chain indices (rec_chain, from mpg_guide_records) back to the host,
- * gathers their positions from `chains` on the device, builds the tree on the
- * host and uploads it (library-owned; synchronous). */
+ * gathers their positions from `chains` on the device and builds the tree
+ * (library-owned; synchronous) by `method`:
+ *   MPG_STREE_RECURSIVE: depth first on the host (threads for the subtrees
+ *     near the root), after copying the positions back;
+ *   MPG_STREE_LEVELS: level by level on the device -- each level partitions
+ *     the samples of all its split nodes at once (stable, by prefix counts)
+ *     and selects all their copies at once (the m-th smallest FP64 distance
+ *     of each side by 8-bit digits of its bit pattern, ties by position,
+ *     which is ascending record index); the host decides nodes and numbering.
+ * Both give the same tree.  Errors: invalid arguments or method
+ * (MPG_ERR_INVALID_ARG), a CUDA failure (MPG_ERR_CUDA). */
+#define MPG_STREE_RECURSIVE 0
+#define MPG_STREE_LEVELS 1
 typedef struct mpg_stree mpg_stree;
 mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,
-                           const int32_t* R_dev, float epsilon, float c, mpg_stree** out, cudaStream_t stream);
+                           const int32_t* R_dev, float epsilon, float c, int32_t method, mpg_stree** out,
+                           cudaStream_t stream);
 /* The same tree from host positions: pos [6][n] host FP32 (x_D then x_L,
  * coordinate-major; borrowed, read during the call), record r at column r.
  * Built on the host with no device copy and no CUDA call, so it needs no
- * GPU; mpg_stree_info and mpg_stree_export work on it, mpg_stree_records and
- * mpg_stree_query reject it (MPG_ERR_INVALID_ARG).  Errors: pos NULL with
- * n > 0, n < 0, epsilon outside [0, 0.5), c <= 0 or a non-finite position
- * (MPG_ERR_INVALID_ARG). */
-mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, mpg_stree** out);
+ * GPU: MPG_STREE_RECURSIVE depth first, or MPG_STREE_LEVELS with the passes
+ * of the device's level-by-level build run as plain loops (the same
+ * decisions in the same order).  mpg_stree_info and mpg_stree_export work on
+ * it, mpg_stree_records and mpg_stree_query reject it (MPG_ERR_INVALID_ARG).
+ * Errors: pos NULL with n > 0, n < 0, epsilon outside [0, 0.5), c <= 0, an
+ * unknown method or a non-finite position (MPG_ERR_INVALID_ARG). */
+mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, int32_t method,
+                                mpg_stree** out);
 /* Sizes of a tree: samples, nodes, leaves and leaf members (own + copies). */
 mpg_status mpg_stree_info(const mpg_stree* tree, int32_t* n_samples, int32_t* n_nodes, int32_t* n_leaves,
                           int32_t* n_members);

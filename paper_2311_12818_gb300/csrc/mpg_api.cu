@@ -1246,13 +1246,16 @@ void mpg_stree_destroy(mpg_stree* t) {
 }
 
 mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,
-                           const int32_t* R_dev, float epsilon, float c, mpg_stree** out, cudaStream_t st) {
+                           const int32_t* R_dev, float epsilon, float c, int32_t method, mpg_stree** out,
+                           cudaStream_t st) {
   if (!ctx || !out) return fail(MPG_ERR_INVALID_ARG, "ctx or out is NULL");
   *out = nullptr;
   mpg_status s;
   if ((s = check_chains(chains, false))) return s;
-  if (R < 0 || (R > 0 && !aligned16(rec_chain)) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f))
-    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (R %d, epsilon %g, c %g)", R, epsilon, c);
+  if (R < 0 || (R > 0 && !aligned16(rec_chain)) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f) ||
+      (method != MPG_STREE_RECURSIVE && method != MPG_STREE_LEVELS))
+    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (R %d, epsilon %g, c %g, method %d)", R, epsilon, c,
+                method);
   if (ctx->capturing) return fail(MPG_ERR_INVALID_ARG, "mpg_stree_build is synchronous and cannot be captured");
   CUDA_TRY(cudaSetDevice(ctx->device));
   int n = R;
@@ -1269,20 +1272,40 @@ mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t
   for (int i = 0; i < n; ++i)
     if (idx[i] < 0 || idx[i] >= chains->B)
       return fail(MPG_ERR_INVALID_ARG, "record %d names chain %d outside the batch", i, idx[i]);
-  std::vector<float> pos((size_t)6 * n);
-  if (n > 0) {
-    float* d_pos = nullptr;
-    CUDA_TRY(cudaMalloc(&d_pos, sizeof(float) * pos.size()));
-    launch_stree_gather(to_dev(chains), rec_chain, n, d_pos, st);
-    cudaError_t e = cudaMemcpyAsync(pos.data(), d_pos, sizeof(float) * pos.size(), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_pos);
-    if (e != cudaSuccess) return fail(MPG_ERR_CUDA, "tree positions: %s", cudaGetErrorString(e));
-    ctx->launches += 1;
-  }
   mpg_stree* t = new mpg_stree;
   t->device = ctx->device;
-  stree_build(pos.data(), n, (double)epsilon, (double)c, t->h);
+  float* d_pos = nullptr;
+  if (n > 0) {
+    cudaError_t e = cudaMalloc(&d_pos, sizeof(float) * (size_t)6 * n);
+    if (e != cudaSuccess) {
+      delete t;
+      return fail(MPG_ERR_CUDA, "tree positions: %s", cudaGetErrorString(e));
+    }
+    launch_stree_gather(to_dev(chains), rec_chain, n, d_pos, st);
+    ctx->launches += 1;
+  }
+  if (method == MPG_STREE_LEVELS) {
+    // level by level on the device, from the gathered positions
+    const char* why = nullptr;
+    const bool ok = stree_build_levels_device(d_pos, n, (double)epsilon, (double)c, t->h, st, &why);
+    if (d_pos) cudaFree(d_pos);
+    if (!ok) {
+      delete t;
+      return fail(MPG_ERR_CUDA, "device tree build: %s", why);
+    }
+  } else {
+    std::vector<float> pos((size_t)6 * n);
+    if (n > 0) {
+      cudaError_t e = cudaMemcpyAsync(pos.data(), d_pos, sizeof(float) * pos.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      cudaFree(d_pos);
+      if (e != cudaSuccess) {
+        delete t;
+        return fail(MPG_ERR_CUDA, "tree positions: %s", cudaGetErrorString(e));
+      }
+    }
+    stree_build(pos.data(), n, (double)epsilon, (double)c, t->h);
+  }
   auto upload = [](auto** d, const auto& h) {
     const size_t bytes = sizeof(h[0]) * h.size();
     cudaError_t e = cudaMalloc((void**)d, std::max<size_t>(bytes, 16));
@@ -1303,16 +1326,20 @@ mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t
   return MPG_OK;
 }
 
-mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, mpg_stree** out) {
+mpg_status mpg_stree_build_host(const float* pos, int32_t n, float epsilon, float c, int32_t method,
+                                mpg_stree** out) {
   if (!out) return fail(MPG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (n < 0 || (n > 0 && !pos) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f))
-    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (n %d, epsilon %g, c %g)", n, epsilon, c);
+  if (n < 0 || (n > 0 && !pos) || !(epsilon >= 0.0f && epsilon < 0.5f) || !(c > 0.0f) ||
+      (method != MPG_STREE_RECURSIVE && method != MPG_STREE_LEVELS))
+    return fail(MPG_ERR_INVALID_ARG, "invalid tree arguments (n %d, epsilon %g, c %g, method %d)", n, epsilon, c,
+                method);
   for (size_t i = 0; i < (size_t)6 * n; ++i)
     if (!std::isfinite(pos[i])) return fail(MPG_ERR_INVALID_ARG, "position %zu is not finite", i);
   mpg_stree* t = new mpg_stree;
   t->device = -1;
-  stree_build(pos, n, (double)epsilon, (double)c, t->h);
+  if (method == MPG_STREE_LEVELS) stree_build_levels_host(pos, n, (double)epsilon, (double)c, t->h);
+  else stree_build(pos, n, (double)epsilon, (double)c, t->h);
   *out = t;
   return MPG_OK;
 }

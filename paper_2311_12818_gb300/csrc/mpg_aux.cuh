@@ -17,6 +17,12 @@ struct StreeHost {
   int n_leaves = 0, n_samples = 0;
 };
 void stree_build(const float* pos /* [6][n] host */, int n, double eps, double c, StreeHost& t);
+// The same tree level by level (mpg_stree_level.cuh): on the host from host
+// positions, or on the device from device positions d_pos [6][n] (consumed
+// as scratch; synchronous on st).  Returns false on a CUDA error (message in err).
+void stree_build_levels_host(const float* pos, int n, double eps, double c, StreeHost& t);
+bool stree_build_levels_device(float* d_pos, int n, double eps, double c, StreeHost& t, cudaStream_t st,
+                               const char** err);
 
 void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
                    int* order, int sms, cudaStream_t st);
@@ -25,6 +31,8 @@ void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* ome
                          const int* R_dev, int shift, int* err, int sms, cudaStream_t st);
 // Guide records in chain order (mpg_vmf.cu): tile_scratch holds rec_tiles(B) counts.
 int rec_tiles(int B);
+// Exclusive scan of a[0..n) in place by one CTA; *total (may be NULL) gets the sum.
+void launch_scan_exclusive(uint32_t* a, int n, int* total, cudaStream_t st);
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
                                   uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
                                   int* chain_out, int* R, cudaStream_t st);

@@ -6,9 +6,11 @@
 // run on the GPU for every chain.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <future>
 
 #include "mpg_aux.cuh"
+#include "mpg_stree_level.cuh"
 
 namespace mpg {
 
@@ -225,6 +227,487 @@ void stree_build(const float* pos, int n, double eps, double c, StreeHost& t) {
   for (int i = 0; i < n; ++i) sh.idx[i] = i;
   for (int a = 0; a < 6; ++a) sh.X[a].assign(pos + (size_t)a * n, pos + (size_t)(a + 1) * n);
   Builder(sh, t).build(0, (size_t)n, {}, lo, hi, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Level-by-level build (mpg_stree_level.cuh): the passes on the host ...
+// ---------------------------------------------------------------------------
+namespace {
+using stree::LeafOut;
+using stree::Segment;
+using stree::SplitNode;
+
+void exclusive_scan(std::vector<uint32_t>& a) {
+  uint32_t run = 0;
+  for (auto& v : a) {
+    const uint32_t x = v;
+    v = run;
+    run += x;
+  }
+}
+
+// Plain loops taking the device passes' decisions in the same order: owner
+// tables, flags, exclusive scans, scatters, digit histograms.
+struct HostLevels {
+  int n;
+  std::vector<int> idx, idx2;
+  std::vector<float> X, X2;  // [6][n]
+  std::vector<int> pool;
+  StreeHost* t;
+
+  HostLevels(const float* pos, int n_, StreeHost* out) : n(n_), idx(n_), idx2(n_), X(pos, pos + (size_t)6 * n_),
+                                                         X2((size_t)6 * n_), t(out) {
+    for (int i = 0; i < n; ++i) idx[i] = i;
+  }
+  float x(int a, int64_t p) const { return X[(size_t)a * n + p]; }
+
+  void root_box(double lo[6], double hi[6]) {
+    for (int a = 0; a < 6; ++a) {
+      float mn = x(a, 0), mx = mn;
+      for (int p = 1; p < n; ++p) {
+        mn = std::min(mn, x(a, p));
+        mx = std::max(mx, x(a, p));
+      }
+      lo[a] = mn;
+      hi[a] = mx;
+    }
+  }
+
+  void partition(const std::vector<SplitNode>& sn, std::vector<uint32_t>& nleft) {
+    std::vector<int> owner(n, -1);
+    for (size_t q = 0; q < sn.size(); ++q)
+      for (int64_t p = sn[q].b; p < sn[q].e; ++p) owner[p] = (int)q;
+    std::vector<uint32_t> f(n + 1, 0);
+    for (int p = 0; p < n; ++p)
+      if (owner[p] >= 0) f[p] = stree::goes_left(x(sn[owner[p]].axis, p), sn[owner[p]].mid);
+    exclusive_scan(f);
+    for (int p = 0; p < n; ++p) {
+      int64_t d = p;
+      if (owner[p] >= 0) {
+        const SplitNode& s = sn[owner[p]];
+        d = stree::partition_dest(p, s.b, f[p], f[s.b], f[s.e] - f[s.b], stree::goes_left(x(s.axis, p), s.mid));
+      }
+      idx2[d] = idx[p];
+      for (int a = 0; a < 6; ++a) X2[(size_t)a * n + d] = X[(size_t)a * n + p];
+    }
+    idx.swap(idx2);
+    X.swap(X2);
+    nleft.resize(sn.size());
+    for (size_t q = 0; q < sn.size(); ++q) nleft[q] = f[sn[q].e] - f[sn[q].b];
+  }
+
+  void select(const std::vector<Segment>& sg, std::vector<int64_t>& off) {
+    const size_t S = sg.size();
+    std::vector<int> owner(n, -1);
+    for (size_t s = 0; s < S; ++s)
+      for (int64_t p = sg[s].b; p < sg[s].e; ++p) owner[p] = (int)s;
+    std::vector<uint64_t> prefix(S, 0);
+    std::vector<uint32_t> rank(S), hist(S * 256);
+    for (size_t s = 0; s < S; ++s) rank[s] = sg[s].m;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      std::fill(hist.begin(), hist.end(), 0u);
+      for (int p = 0; p < n; ++p) {
+        const int s = owner[p];
+        if (s < 0) continue;
+        const uint64_t u = stree::dist_bits(x(sg[s].axis, p), sg[s].mid);
+        if (stree::candidate(u, prefix[s], shift)) hist[(size_t)s * 256 + ((u >> shift) & 255u)]++;
+      }
+      for (size_t s = 0; s < S; ++s) prefix[s] |= (uint64_t)stree::pick_digit(&hist[s * 256], rank[s]) << shift;
+    }
+    std::vector<uint32_t> tie(n + 1, 0), sel(n + 1, 0);
+    for (int p = 0; p < n; ++p) {
+      const int s = owner[p];
+      if (s >= 0) tie[p] = stree::dist_bits(x(sg[s].axis, p), sg[s].mid) == prefix[s];
+    }
+    exclusive_scan(tie);
+    for (int p = 0; p < n; ++p) {
+      const int s = owner[p];
+      if (s < 0) continue;
+      const uint64_t u = stree::dist_bits(x(sg[s].axis, p), sg[s].mid);
+      sel[p] = u < prefix[s] || (u == prefix[s] && tie[p] - tie[sg[s].b] < rank[s]);
+    }
+    exclusive_scan(sel);
+    const int64_t base = (int64_t)pool.size();
+    int64_t total = 0;
+    off.resize(S);
+    for (size_t s = 0; s < S; ++s) {
+      off[s] = base + total;
+      total += sg[s].m;
+    }
+    pool.resize(base + total);
+    for (int p = 0; p < n; ++p)
+      if (sel[p + 1] != sel[p]) pool[base + sel[p]] = idx[p];
+  }
+
+  void emit(const std::vector<LeafOut>& lv, int64_t members) {
+    t->member_leaf.assign(members, 0);
+    t->member_rec.assign(members, 0);
+    for (const LeafOut& L : lv) {
+      const int* own = idx.data() + L.b;
+      const int* cp = pool.data() + L.copy_off;
+      const int64_t no = L.e - L.b, nc = L.copy_cnt;
+      for (int64_t i = 0; i < no; ++i) {
+        const int64_t pos = i + (std::lower_bound(cp, cp + nc, own[i]) - cp);
+        t->member_rec[L.out_off + pos] = own[i];
+        t->member_leaf[L.out_off + pos] = L.leaf;
+      }
+      for (int64_t j = 0; j < nc; ++j) {
+        const int64_t pos = j + (std::lower_bound(own, own + no, cp[j]) - own);
+        t->member_rec[L.out_off + pos] = cp[j];
+        t->member_leaf[L.out_off + pos] = L.leaf;
+      }
+    }
+  }
+};
+
+// ... and on the device: the same passes as kernels over all samples of a
+// level (owner tables, flags, one-CTA scans, scatters, per-segment digit
+// histograms), the node decisions on the host between them.
+constexpr int LV_THREADS = 256;
+
+int lv_grid(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + LV_THREADS - 1) / LV_THREADS)); }
+
+__global__ void k_lv_owner(const int64_t* b, const int64_t* e, int stride, int count, int* owner) {
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    const int64_t lo = b[(size_t)q * stride], hi = e[(size_t)q * stride];
+    for (int64_t p = lo + threadIdx.x; p < hi; p += blockDim.x) owner[p] = q;
+  }
+}
+
+__global__ void k_lv_minmax(const float* X, int n, float* part) {
+  __shared__ float smn[LV_THREADS], smx[LV_THREADS];
+  for (int a = 0; a < 6; ++a) {
+    float mn = INFINITY, mx = -INFINITY;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+      const float v = X[(size_t)a * n + p];
+      mn = fminf(mn, v);
+      mx = fmaxf(mx, v);
+    }
+    smn[threadIdx.x] = mn;
+    smx[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        smn[threadIdx.x] = fminf(smn[threadIdx.x], smn[threadIdx.x + o]);
+        smx[threadIdx.x] = fmaxf(smx[threadIdx.x], smx[threadIdx.x + o]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      part[(size_t)blockIdx.x * 12 + a] = smn[0];
+      part[(size_t)blockIdx.x * 12 + 6 + a] = smx[0];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_lv_flags(const int* owner, const SplitNode* sn, const float* X, int n, uint32_t* f) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int q = owner[p];
+    f[p] = q >= 0 && stree::goes_left(X[(size_t)sn[q].axis * n + p], sn[q].mid);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) f[n] = 0;
+}
+
+__global__ void k_lv_scatter(const int* owner, const SplitNode* sn, const float* X, const int* idx, const uint32_t* f,
+                             int n, float* X2, int* idx2) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int q = owner[p];
+    int64_t d = p;
+    if (q >= 0) {
+      const SplitNode s = sn[q];
+      d = stree::partition_dest(p, s.b, f[p], f[s.b], f[s.e] - f[s.b],
+                                stree::goes_left(X[(size_t)s.axis * n + p], s.mid));
+    }
+    idx2[d] = idx[p];
+    for (int a = 0; a < 6; ++a) X2[(size_t)a * n + d] = X[(size_t)a * n + p];
+  }
+}
+
+__global__ void k_lv_nleft(const SplitNode* sn, int count, const uint32_t* f, uint32_t* nleft) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < count; q += gridDim.x * blockDim.x)
+    nleft[q] = f[sn[q].e] - f[sn[q].b];
+}
+
+__global__ void k_lv_hist(const int* owner, const Segment* sg, const uint64_t* prefix, int shift, const float* X,
+                          int n, uint32_t* hist) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int s = owner[p];
+    if (s < 0) continue;
+    const uint64_t u = stree::dist_bits(X[(size_t)sg[s].axis * n + p], sg[s].mid);
+    if (stree::candidate(u, prefix[s], shift)) atomicAdd(hist + (size_t)s * 256 + ((u >> shift) & 255u), 1u);
+  }
+}
+
+__global__ void k_lv_pick(int S, const uint32_t* hist, uint64_t* prefix, uint32_t* rank, int shift) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
+    uint32_t r = rank[s];
+    const uint32_t d = stree::pick_digit(hist + (size_t)s * 256, r);
+    rank[s] = r;
+    prefix[s] |= (uint64_t)d << shift;
+  }
+}
+
+__global__ void k_lv_ties(const int* owner, const Segment* sg, const uint64_t* prefix, const float* X, int n,
+                          uint32_t* tie) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const int s = owner[p];
+    tie[p] = s >= 0 && stree::dist_bits(X[(size_t)sg[s].axis * n + p], sg[s].mid) == prefix[s];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) tie[n] = 0;
+}
+
+__device__ __forceinline__ bool lv_selected(const int* owner, const Segment* sg, const uint64_t* prefix,
+                                            const uint32_t* rank, const uint32_t* tie, const float* X, int n, int p) {
+  const int s = owner[p];
+  if (s < 0) return false;
+  const uint64_t u = stree::dist_bits(X[(size_t)sg[s].axis * n + p], sg[s].mid);
+  return u < prefix[s] || (u == prefix[s] && tie[p] - tie[sg[s].b] < rank[s]);
+}
+
+__global__ void k_lv_sel(const int* owner, const Segment* sg, const uint64_t* prefix, const uint32_t* rank,
+                         const uint32_t* tie, const float* X, int n, uint32_t* sel) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    sel[p] = lv_selected(owner, sg, prefix, rank, tie, X, n, p);
+  if (blockIdx.x == 0 && threadIdx.x == 0) sel[n] = 0;
+}
+
+__global__ void k_lv_write(const int* owner, const Segment* sg, const uint64_t* prefix, const uint32_t* rank,
+                           const uint32_t* tie, const float* X, const int* idx, const uint32_t* sel, int n,
+                           int64_t base, int* pool) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    if (lv_selected(owner, sg, prefix, rank, tie, X, n, p)) pool[base + sel[p]] = idx[p];
+}
+
+__device__ __forceinline__ int64_t count_below(const int* a, int64_t n, int v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t m = (lo + hi) >> 1;
+    if (a[m] < v) lo = m + 1;
+    else hi = m;
+  }
+  return lo;
+}
+
+__global__ void k_lv_emit(const LeafOut* lv, int count, const int* idx, const int* pool, int* member_leaf,
+                          int* member_rec) {
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    const LeafOut L = lv[q];
+    const int* own = idx + L.b;
+    const int* cp = pool + L.copy_off;
+    const int64_t no = L.e - L.b, nc = L.copy_cnt;
+    for (int64_t i = threadIdx.x; i < no; i += blockDim.x) {
+      const int64_t pos = L.out_off + i + count_below(cp, nc, own[i]);
+      member_rec[pos] = own[i];
+      member_leaf[pos] = L.leaf;
+    }
+    for (int64_t j = threadIdx.x; j < nc; j += blockDim.x) {
+      const int64_t pos = L.out_off + j + count_below(own, no, cp[j]);
+      member_rec[pos] = cp[j];
+      member_leaf[pos] = L.leaf;
+    }
+  }
+}
+
+struct DevLevels {
+  int n;
+  cudaStream_t st;
+  cudaError_t e = cudaSuccess;
+  float *X = nullptr, *X2 = nullptr;
+  int *idx = nullptr, *idx2 = nullptr, *owner = nullptr, *pool = nullptr;
+  uint32_t *f = nullptr, *tie = nullptr, *sel = nullptr;
+  int64_t pool_cap = 0, pool_size = 0;
+  std::vector<void*> owned;
+  StreeHost* t;
+
+  template <class T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 16));
+    if (e == cudaSuccess) owned.push_back(p);
+    return (T*)p;
+  }
+  // a table of host structs on the device, freed with the build
+  template <class T>
+  T* upload(const std::vector<T>& h) {
+    T* d = alloc<T>(h.size());
+    if (e == cudaSuccess && !h.empty()) e = cudaMemcpyAsync(d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st);
+    return d;
+  }
+  // the int64 field at byte offset `at` of the first entry of a device table
+  // (entries of the tables are multiples of 8 bytes)
+  template <class T>
+  static const int64_t* field(const T* d, size_t at) {
+    static_assert(sizeof(T) % sizeof(int64_t) == 0, "table entries are read as int64 strides");
+    return (const int64_t*)((const char*)d + at);
+  }
+  bool sync() {
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess;
+  }
+
+  DevLevels(float* d_pos, int n_, cudaStream_t s, StreeHost* out) : n(n_), st(s), X(d_pos), t(out) {
+    X2 = alloc<float>((size_t)6 * n);
+    idx = alloc<int>(n);
+    idx2 = alloc<int>(n);
+    owner = alloc<int>(n);
+    f = alloc<uint32_t>(n + 1);
+    tie = alloc<uint32_t>(n + 1);
+    sel = alloc<uint32_t>(n + 1);
+    if (e == cudaSuccess) {
+      std::vector<int> iota(n);
+      for (int i = 0; i < n; ++i) iota[i] = i;
+      e = cudaMemcpy(idx, iota.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice);
+    }
+  }
+  ~DevLevels() {
+    cudaStreamSynchronize(st);
+    for (void* p : owned) cudaFree(p);
+    if (pool) cudaFree(pool);
+  }
+
+  void root_box(double lo[6], double hi[6]) {
+    const int g = std::min(256, lv_grid(n));
+    float* part = alloc<float>((size_t)g * 12);
+    if (e == cudaSuccess) k_lv_minmax<<<g, LV_THREADS, 0, st>>>(X, n, part);
+    std::vector<float> h((size_t)g * 12, 0.0f);
+    if (sync()) e = cudaMemcpy(h.data(), part, sizeof(float) * h.size(), cudaMemcpyDeviceToHost);
+    for (int a = 0; a < 6; ++a) {
+      float mn = h[a], mx = h[6 + a];
+      for (int b = 1; b < g; ++b) {
+        mn = std::min(mn, h[(size_t)b * 12 + a]);
+        mx = std::max(mx, h[(size_t)b * 12 + 6 + a]);
+      }
+      lo[a] = mn;
+      hi[a] = mx;
+    }
+  }
+
+  void owners(const int64_t* b, const int64_t* e_, int stride, int count) {
+    if (e != cudaSuccess) return;
+    e = cudaMemsetAsync(owner, 0xff, sizeof(int) * (size_t)n, st);  // -1 everywhere
+    if (e == cudaSuccess && count > 0) k_lv_owner<<<std::min(count, 4096), LV_THREADS, 0, st>>>(b, e_, stride, count, owner);
+  }
+
+  void partition(const std::vector<SplitNode>& sn, std::vector<uint32_t>& nleft) {
+    nleft.assign(sn.size(), 0);
+    SplitNode* d_sn = upload(sn);
+    uint32_t* d_nl = alloc<uint32_t>(sn.size());
+    owners(field(d_sn, offsetof(SplitNode, b)), field(d_sn, offsetof(SplitNode, e)),
+           sizeof(SplitNode) / sizeof(int64_t), (int)sn.size());
+    const int g = lv_grid(n);
+    if (e == cudaSuccess) {
+      k_lv_flags<<<g, LV_THREADS, 0, st>>>(owner, d_sn, X, n, f);
+      launch_scan_exclusive(f, n + 1, nullptr, st);
+      k_lv_scatter<<<g, LV_THREADS, 0, st>>>(owner, d_sn, X, idx, f, n, X2, idx2);
+      k_lv_nleft<<<lv_grid((int64_t)sn.size()), LV_THREADS, 0, st>>>(d_sn, (int)sn.size(), f, d_nl);
+      std::swap(X, X2);
+      std::swap(idx, idx2);
+    }
+    if (sync()) e = cudaMemcpy(nleft.data(), d_nl, sizeof(uint32_t) * sn.size(), cudaMemcpyDeviceToHost);
+  }
+
+  void grow_pool(int64_t need) {
+    if (e != cudaSuccess || need <= pool_cap) return;
+    const int64_t cap = std::max<int64_t>(need, 2 * pool_cap);
+    int* np = nullptr;
+    e = cudaMalloc((void**)&np, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess && pool_size > 0)
+      e = cudaMemcpyAsync(np, pool, sizeof(int) * (size_t)pool_size, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+      if (np) cudaFree(np);
+      return;
+    }
+    if (pool) cudaFree(pool);
+    pool = np;
+    pool_cap = cap;
+  }
+
+  void select(const std::vector<Segment>& sg, std::vector<int64_t>& off) {
+    const int S = (int)sg.size();
+    off.resize(S);
+    int64_t total = 0;
+    for (int s = 0; s < S; ++s) {
+      off[s] = pool_size + total;
+      total += sg[s].m;
+    }
+    grow_pool(pool_size + total);
+    Segment* d_sg = upload(sg);
+    std::vector<uint32_t> r0(S);
+    for (int s = 0; s < S; ++s) r0[s] = sg[s].m;
+    uint32_t* d_rank = upload(r0);
+    uint64_t* d_prefix = alloc<uint64_t>(S);
+    uint32_t* d_hist = alloc<uint32_t>((size_t)S * 256);
+    owners(field(d_sg, offsetof(Segment, b)), field(d_sg, offsetof(Segment, e)), sizeof(Segment) / sizeof(int64_t),
+           S);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_prefix, 0, sizeof(uint64_t) * S, st);
+    const int g = lv_grid(n);
+    for (int shift = 56; shift >= 0 && e == cudaSuccess; shift -= 8) {
+      e = cudaMemsetAsync(d_hist, 0, sizeof(uint32_t) * (size_t)S * 256, st);
+      if (e != cudaSuccess) break;
+      k_lv_hist<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, shift, X, n, d_hist);
+      k_lv_pick<<<lv_grid(S), LV_THREADS, 0, st>>>(S, d_hist, d_prefix, d_rank, shift);
+    }
+    if (e == cudaSuccess) {
+      k_lv_ties<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, X, n, tie);
+      launch_scan_exclusive(tie, n + 1, nullptr, st);
+      k_lv_sel<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, d_rank, tie, X, n, sel);
+      launch_scan_exclusive(sel, n + 1, nullptr, st);
+      k_lv_write<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, d_rank, tie, X, idx, sel, n, pool_size, pool);
+    }
+    sync();
+    pool_size += total;
+  }
+
+  void emit(const std::vector<LeafOut>& lv, int64_t members) {
+    int* d_leaf = alloc<int>(members);
+    int* d_rec = alloc<int>(members);
+    LeafOut* d_lv = upload(lv);
+    if (e == cudaSuccess && !lv.empty())
+      k_lv_emit<<<(int)std::min<size_t>(lv.size(), 4096), LV_THREADS, 0, st>>>(d_lv, (int)lv.size(), idx, pool,
+                                                                               d_leaf, d_rec);
+    t->member_leaf.assign(members, 0);
+    t->member_rec.assign(members, 0);
+    if (sync() && members > 0) {
+      e = cudaMemcpy(t->member_leaf.data(), d_leaf, sizeof(int) * (size_t)members, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(t->member_rec.data(), d_rec, sizeof(int) * (size_t)members, cudaMemcpyDeviceToHost);
+    }
+  }
+};
+
+void take_result(const stree::Result& r, int n, StreeHost& t) {
+  t.axis = r.axis;
+  t.left = r.left;
+  t.right = r.right;
+  t.split = r.split;
+  t.n_leaves = r.n_leaves;
+  t.n_samples = n;
+}
+}  // namespace
+
+void stree_build_levels_host(const float* pos, int n, double eps, double c, StreeHost& t) {
+  t = StreeHost{};
+  HostLevels ex(pos, n, &t);
+  stree::Result r;
+  stree::build_levels(ex, n, eps, c, r);
+  take_result(r, n, t);
+}
+
+bool stree_build_levels_device(float* d_pos, int n, double eps, double c, StreeHost& t, cudaStream_t st,
+                               const char** err) {
+  t = StreeHost{};
+  DevLevels ex(d_pos, n, st, &t);
+  stree::Result r;
+  if (ex.e == cudaSuccess) stree::build_levels(ex, n, eps, c, r);
+  if (ex.e != cudaSuccess) {
+    *err = cudaGetErrorString(ex.e);
+    return false;
+  }
+  take_result(r, n, t);
+  return true;
 }
 
 void launch_stree_gather(const DChains& c, const int* rec_chain, int n, float* pos, cudaStream_t st) {

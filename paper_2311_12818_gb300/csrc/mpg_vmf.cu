@@ -415,6 +415,10 @@ __global__ void k_sample_lengths(DGuide g, int has_guide, DChains ch, P0Table p0
 // ---------------------------------------------------------------------------
 int rec_tiles(int B) { return (B + REC_TILE - 1) / REC_TILE; }
 
+void launch_scan_exclusive(uint32_t* a, int n, int* total, cudaStream_t st) {
+  k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(a, n, total);
+}
+
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
                                   uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
                                   int* chain_out, int* R, cudaStream_t st) {

@@ -62,6 +62,7 @@ class mpg_guide(C.Structure):
 
 
 GUIDE_HISTOGRAM, GUIDE_VMF = 0, 1
+STREE_RECURSIVE, STREE_LEVELS = 0, 1
 
 
 STAT_FIELDS = ["newton_steps", "thomas_rows", "full_evals", "c_evals", "ray_casts", "sphere_tests",
@@ -121,8 +122,8 @@ def lib():
         L.mpg_guide_records.argtypes = [vp, vp, C.POINTER(mpg_chains), vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.mpg_vmf_build.argtypes = [vp, C.POINTER(mpg_guide), vp, vp, vp, vp, vp, i32, vp, i32, vp]
         L.mpg_training_plan.argtypes = [i32, i32, f32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
-        L.mpg_stree_build.argtypes = [vp, C.POINTER(mpg_chains), vp, i32, vp, f32, f32, C.POINTER(vp), vp]
-        L.mpg_stree_build_host.argtypes = [vp, i32, f32, f32, C.POINTER(vp)]
+        L.mpg_stree_build.argtypes = [vp, C.POINTER(mpg_chains), vp, i32, vp, f32, f32, i32, C.POINTER(vp), vp]
+        L.mpg_stree_build_host.argtypes = [vp, i32, f32, f32, i32, C.POINTER(vp)]
         L.mpg_stree_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
         L.mpg_stree_export.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.mpg_stree_records.argtypes = [vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, i32, vp, vp]
@@ -536,22 +537,27 @@ class STree:
     """Spatial tree of the guide samples (Sec. 5.6; mpg_stree_*): built from
     the records of a pass (their chain indices) over those chains' (x_D, x_L)."""
 
-    def __init__(self, ctx, chains, rec_chain, R=None, R_dev=None, epsilon=0.1, c=1.0, stream=None):
+    def __init__(self, ctx, chains, rec_chain, R=None, R_dev=None, epsilon=0.1, c=1.0, method=None, stream=None):
+        """method: STREE_RECURSIVE (host, the default) or STREE_LEVELS (device)."""
         self.ctx = ctx
         R = int(rec_chain.numel()) if R is None else R
         h = C.c_void_p()
         cs = chains.struct()
-        _check(lib().mpg_stree_build(ctx.h, C.byref(cs), _ptr(rec_chain), R, _ptr(R_dev), epsilon, c, C.byref(h),
-                                     _stream(stream)))
+        method = STREE_RECURSIVE if method is None else method
+        _check(lib().mpg_stree_build(ctx.h, C.byref(cs), _ptr(rec_chain), R, _ptr(R_dev), epsilon, c, method,
+                                     C.byref(h), _stream(stream)))
         self._adopt(h)
 
     @classmethod
-    def from_host(cls, pos, epsilon=0.1, c=1.0):
+    def from_host(cls, pos, epsilon=0.1, c=1.0, method=None):
         """The tree of host positions pos [n, 6] (x_D, x_L) with no device copy
-        (mpg_stree_build_host; needs no GPU): info and export only."""
+        (mpg_stree_build_host; needs no GPU): info and export only.  method:
+        STREE_RECURSIVE (default) or STREE_LEVELS (the device build's passes
+        as host loops)."""
         pos = np.ascontiguousarray(np.asarray(pos, np.float32).reshape(-1, 6).T)
         h = C.c_void_p()
-        _check(lib().mpg_stree_build_host(pos.ctypes.data if pos.size else None, pos.shape[1], epsilon, c,
+        method = STREE_RECURSIVE if method is None else method
+        _check(lib().mpg_stree_build_host(pos.ctypes.data if pos.size else None, pos.shape[1], epsilon, c, method,
                                           C.byref(h)))
         t = cls.__new__(cls)
         t.ctx = None

@@ -52,14 +52,19 @@ def _dev(recs):
             torch.as_tensor(w, device="cuda"), torch.as_tensor(k, device="cuda"), torch.as_tensor(tau, device="cuda"))
 
 
+LEVELS_PENDING = pytest.mark.skip(reason="the device level build has not yet run on a GPU")
+
+
+@pytest.mark.parametrize("method", ["recursive", pytest.param("levels", marks=LEVELS_PENDING)])
 @pytest.mark.parametrize("which", ["glass", "mixed"])
-def test_tree_build_query_and_guide_match_oracle(M, ctx, which):
+def test_tree_build_query_and_guide_match_oracle(M, ctx, which, method):
     wl = I.glass_sphere(n=32, spq=16) if which == "glass" else I.mixed(nx=64, ny=32, spq=8)
     idx, recs = _training(wl)
     assert idx.size > 300
     ot = STree(positions(wl, idx))
     ch = M.Chains(wl)
-    gt = M.STree(ctx, ch, torch.as_tensor(idx.astype(np.int32), device="cuda"))
+    gt = M.STree(ctx, ch, torch.as_tensor(idx.astype(np.int32), device="cuda"),
+                 method=M.STREE_LEVELS if method == "levels" else M.STREE_RECURSIVE)
     ax, sp, lf, rt, ml, mr = gt.export()
     assert gt.n_samples == idx.size and gt.n_leaves == ot.n_leaves > 4
     assert np.array_equal(ax, ot.axis) and np.array_equal(sp, ot.split)
