@@ -431,11 +431,23 @@ __global__ void k_lv_nleft(const SplitNode* sn, int count, const uint32_t* f, ui
 
 __global__ void k_lv_hist(const int* owner, const Segment* sg, const uint64_t* prefix, int shift, const float* X,
                           int n, uint32_t* hist) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    const int s = owner[p];
-    if (s < 0) continue;
-    const uint64_t u = stree::dist_bits(X[(size_t)sg[s].axis * n + p], sg[s].mid);
-    if (stree::candidate(u, prefix[s], shift)) atomicAdd(hist + (size_t)s * 256 + ((u >> shift) & 255u), 1u);
+  // Every lane of a warp runs the same iterations (the loop test uses the
+  // warp's first index), so the whole warp takes part in the match: lanes
+  // counting into the same bin add once (the top digits of a segment's
+  // distances mostly share one bin).
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p - lane < n; p += stride) {
+    unsigned bin = 0xffffffffu;
+    if (p < n) {
+      const int s = owner[p];
+      if (s >= 0) {
+        const uint64_t u = stree::dist_bits(X[(size_t)sg[s].axis * n + p], sg[s].mid);
+        if (stree::candidate(u, prefix[s], shift)) bin = (unsigned)s * 256u + (unsigned)((u >> shift) & 255u);
+      }
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, bin);
+    if (bin != 0xffffffffu && lane == __ffs(peers) - 1) atomicAdd(hist + bin, (uint32_t)__popc(peers));
   }
 }
 
