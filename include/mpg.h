@@ -300,9 +300,13 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* c
  * forbids cudaMalloc (it synchronises the device and can stall the frame),
  * codes whose device memory is owned by their own pool allocator, and
  * callers that cannot touch the runtime allocator while another thread holds a
- * global-mode stream capture.  Same inputs, outputs and results as
- * mpg_manifold_walk with walk_mode MPG_WALK_BATCHED on the current device, with
- * no context: work counters and launch timing are not kept.
+ * global-mode stream capture.  Same inputs, outputs and results (bit for
+ * bit) as mpg_manifold_walk with walk_mode MPG_WALK_BATCHED and the same
+ * schedule (walk_group, block_threads, ctas_per_sm, refill_every) on the
+ * current device, with no context: work counters and launch timing are not
+ * kept.  Unlike mpg_manifold_walk it waits for `stream` before returning, to
+ * read the device-side error word it clears at the start of every call: a
+ * BVH traversal stack overflow returns MPG_ERR_LIMIT.
  * Scratch: a fixed device array inside the library (about 4 MiB plus the
  * counters, held by every GPU that loads the library until the process exits),
  * so one call takes at most 1,048,576 chains; larger batches are rejected with

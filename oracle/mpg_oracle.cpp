@@ -2068,8 +2068,11 @@ int32_t orc_unit_flops(double* out) {
   Frame<C> ff[3] = {fp, f, fn};
   double gg = run([&] { C G; chain_ggt<C>(1, false, ff, v8, 0.0, G); });
   out[10] = gg - g1;
+  // The ray tests take a unit direction as input: it is normalised once per
+  // ray (or is unit by construction), outside the counted test.
   C r0[2];
-  out[11] = run([&] { sphere_roots<C>(V3<C>(0.1, 0.2, -1.5), normalize(V3<C>(0.0, 0.1, 1.0)), c, C(1.0), r0); });
+  const V3<C> d_sph = normalize(V3<C>(0.0, 0.1, 1.0)), d_tri = normalize(V3<C>(0.0, 0.0, 1.0));
+  out[11] = run([&] { sphere_roots<C>(V3<C>(0.1, 0.2, -1.5), d_sph, c, C(1.0), r0); });
   out[12] = run([&] {  // plane t, hit point and two in-rectangle projections
     V3<C> o(0.1, 0.2, 1.0), d(0.0, 0.1, -1.0), n(0.0, 0.0, 1.0), ex(1.0, 0.0, 0.0), ey(0.0, 1.0, 0.0);
     C t = dot(c - o, n) / dot(d, n);
@@ -2077,7 +2080,7 @@ int32_t orc_unit_flops(double* out) {
     dot(q, ex); dot(q, ey); dot(ex, ex); dot(ey, ey);
   });
   C tt, bb1, bb2;
-  out[13] = run([&] { tri_hit<C>(V3<C>(0.01, 0.005, -1.0), normalize(V3<C>(0.0, 0.0, 1.0)), P0, P1, P2, tt, bb1, bb2); });
+  out[13] = run([&] { tri_hit<C>(V3<C>(0.01, 0.005, -1.0), d_tri, P0, P1, P2, tt, bb1, bb2); });
   out[14] = 12.0;  // 6 subtractions and 6 divisions (or reciprocal products) of the slab test
   out[15] = run([&] {
     V3<C> wi = normalize(fp.p - f.p);

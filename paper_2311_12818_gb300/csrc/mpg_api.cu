@@ -355,11 +355,12 @@ mpg_status make_plan(mpg_ctx* ctx, const mpg_chains* c, const mpg_params* p, int
     CUDA_TRY(cudaMalloc(&ctx->d_order, sizeof(int) * (size_t)c->B));
     ctx->order_cap = c->B;
   }
+  cudaError_t be = cudaSuccess;
   timed(ctx, MPG_KERNEL_AUX, st, 3, [&] {
-    launch_bucket(c->k, c->status, status_filter, c->B, ctx->d_count, ctx->d_base, ctx->d_cursor, ctx->d_order,
-                  ctx->sms, st);
+    be = launch_bucket(c->k, c->status, status_filter, c->B, ctx->d_count, ctx->d_base, ctx->d_cursor, ctx->d_order,
+                       ctx->sms, st);
   });
-  LAUNCH_CHECK("bucket");
+  if (be != cudaSuccess) return fail(MPG_ERR_CUDA, "bucket: %s", cudaGetErrorString(be));
   plan.w = DWork{ctx->d_order, ctx->d_base, ctx->d_count};
   plan.concurrent = true;
   return MPG_OK;
@@ -1658,24 +1659,37 @@ extern "C" mpg_status mpg_manifold_walk_noalloc(const mpg_scene* sc, mpg_chains*
   if ((s = noalloc_scratch(device, &scr))) return s;
   int sms = 1;
   CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-  // what must start at zero: the queue counters and the bucket sizes
+  // what must start at zero: the queue counters, the bucket sizes and the
+  // device error word (a previous call's flag must not leak into this one)
   CUDA_TRY(cudaMemsetAsync(scr->queue, 0, sizeof(scr->queue), st));
+  CUDA_TRY(cudaMemsetAsync(&scr->err, 0, sizeof(int), st));
   DChains c = to_dev(chains);
   DWork w{nullptr, nullptr, nullptr};
   int k_lo = 1, k_hi = MAXK;
   if (P->k_uniform >= 1) {
     k_lo = k_hi = P->k_uniform;
   } else {
-    launch_bucket(c.k, c.status, ST_SEEDED, c.B, scr->count, scr->base, scr->cursor, scr->order, sms, st);
+    CUDA_TRY(launch_bucket(c.k, c.status, ST_SEEDED, c.B, scr->count, scr->base, scr->cursor, scr->order, sms, st));
     w = DWork{scr->order, scr->base, scr->count};
   }
   DCtx dc{&scr->err, nullptr};
-  int block = block_of(P);
+  // the schedule of mpg_manifold_walk's batched mode: the walk form the
+  // caller picked (one thread or one lane group per chain), its block size
+  // and resident CTAs per SM, clamped by ctas_per_sm
+  const int which = walk_which(P), block = walk_block(P);
   for (int K = k_lo; K <= k_hi; ++K) {
-    int per_sm = blocks_per_sm(4, K, false, block);
+    int per_sm = blocks_per_sm(which, K, false, block);
+    if (P->ctas_per_sm > 0) per_sm = std::min(per_sm, P->ctas_per_sm);
     int grid = std::max(1, std::min(sms * per_sm, (c.B + block - 1) / block));
     launch_walk_p(K, false, sc->S, c, w, *P, dc, scr->queue + 16 * K, grid, block, st);
   }
   LAUNCH_CHECK("walk (no-alloc)");
+  // Device-side failures (a BVH traversal stack overflow) are read back here:
+  // the call waits for `stream` and reports them like mpg_ctx_sync.
+  int err = 0;
+  CUDA_TRY(cudaMemcpyAsync(&err, &scr->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (err & ERR_BVH_STACK) return fail(MPG_ERR_LIMIT, "BVH traversal stack overflow (device flag %d)", err);
+  if (err) return fail(MPG_ERR_INVALID_ARG, "device-side argument error (flag %d)", err);
   return MPG_OK;
 }

@@ -55,13 +55,15 @@ __global__ void k_bucket_scatter(const uint8_t* k, const uint8_t* status, int fi
   }
 }
 
-void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
-                   int* order, int sms, cudaStream_t st) {
-  cudaMemsetAsync(count, 0, sizeof(int) * (MAXK + 1), st);
+cudaError_t launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base,
+                          int* cursor, int* order, int sms, cudaStream_t st) {
+  const cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (MAXK + 1), st);
+  if (e != cudaSuccess) return e;  // the counting kernels need zeroed counts
   int grid = min(sms * 4, (B + 255) / 256 + 1);
   k_bucket_count<<<grid, 256, 0, st>>>(k, status, filter, B, count);
   k_bucket_scan<<<1, 32, 0, st>>>(count, base, cursor);
   k_bucket_scatter<<<grid, 256, 0, st>>>(k, status, filter, B, cursor, order);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -24,8 +24,10 @@ void stree_build_levels_host(const float* pos, int n, double eps, double c, Stre
 bool stree_build_levels_device(float* d_pos, int n, double eps, double c, StreeHost& t, cudaStream_t st,
                                const char** err);
 
-void launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base, int* cursor,
-                   int* order, int sms, cudaStream_t st);
+// Counting sort of the chains with status `filter` (any status when < 0) by
+// length into order[]; returns the first CUDA error of its calls.
+cudaError_t launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base,
+                          int* cursor, int* order, int sms, cudaStream_t st);
 void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, cudaStream_t st);
 void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* omega, const float* w, int R,
                          const int* R_dev, int shift, int* err, int sms, cudaStream_t st);

@@ -640,6 +640,11 @@ struct DevLevels {
   void select(const std::vector<Segment>& sg, std::vector<int64_t>& off) {
     const int S = (int)sg.size();
     off.resize(S);
+    // k_lv_hist keys a bin as segment * 256 + digit in 32 bits with 2^32 - 1
+    // meaning "no bin": fewer than 2^24 segments per level keep the two apart
+    // (a level has at most 2 sqrt(n) segments, each split node holding more
+    // than sqrt(n) samples)
+    if (S >= (1 << 24)) e = cudaErrorInvalidValue;
     int64_t total = 0;
     for (int s = 0; s < S; ++s) {
       off[s] = pool_size + total;

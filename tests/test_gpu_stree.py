@@ -52,10 +52,7 @@ def _dev(recs):
             torch.as_tensor(w, device="cuda"), torch.as_tensor(k, device="cuda"), torch.as_tensor(tau, device="cuda"))
 
 
-LEVELS_PENDING = pytest.mark.skip(reason="the device level build has not yet run on a GPU")
-
-
-@pytest.mark.parametrize("method", ["recursive", pytest.param("levels", marks=LEVELS_PENDING)])
+@pytest.mark.parametrize("method", ["recursive", "levels"])
 @pytest.mark.parametrize("which", ["glass", "mixed"])
 def test_tree_build_query_and_guide_match_oracle(M, ctx, which, method):
     wl = I.glass_sphere(n=32, spq=16) if which == "glass" else I.mixed(nx=64, ny=32, spq=8)
@@ -114,3 +111,23 @@ def test_tree_build_query_and_guide_match_oracle(M, ctx, which, method):
     assert ab.sum() > 200
     gN = out.trials.cpu().numpy().astype(np.int64)
     assert (gN[ab] == N[ab]).mean() >= 0.999
+
+
+@pytest.mark.parametrize("n_samples", [1000, 600_000])
+def test_level_build_on_device_equals_recursive_build(M, ctx, n_samples):
+    """The device's level-by-level build and the depth-first build give the
+    same tree (nodes, splits, leaf members) on the benchmark workload's
+    positions: a small sample set, then one of the size a training pass of
+    the full glass-sphere batch gives.  The depth-first build is the one
+    checked against the oracle's tree above."""
+    wl = I.glass_sphere()
+    ch = M.Chains(wl)
+    rng = np.random.default_rng(0x4D50470015 + n_samples)
+    idx = np.sort(rng.choice(wl.B, n_samples, replace=False)).astype(np.int32)
+    rc = torch.as_tensor(idx, device="cuda")
+    a = M.STree(ctx, ch, rc, method=M.STREE_RECURSIVE).export()
+    b = M.STree(ctx, ch, rc, method=M.STREE_LEVELS).export()
+    ctx.sync()
+    assert a[0].size > 10
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
