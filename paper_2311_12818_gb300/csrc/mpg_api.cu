@@ -500,6 +500,7 @@ void mpg_ctx_destroy(mpg_ctx* c) {
   for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   delete c;
+  (void)cudaGetLastError();  // a failure here must not surface in a later call's launch check
 }
 
 mpg_status mpg_ctx_sync(mpg_ctx* c, cudaStream_t st) {
@@ -711,6 +712,7 @@ void mpg_scene_destroy(mpg_scene* sc) {
   cudaSetDevice(sc->device);
   for (void* p : sc->allocs) cudaFree(p);
   delete sc;
+  (void)cudaGetLastError();  // a failure here must not surface in a later call's launch check
 }
 
 mpg_status mpg_scene_info(const mpg_scene* sc, int32_t h, int32_t* n_nodes, int32_t* n_tris) {
@@ -1108,6 +1110,7 @@ mpg_status mpg_fp64_peak(mpg_ctx* ctx, double* flops, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 struct mpg_graph {
   mpg_ctx* ctx = nullptr;
+  int device = 0;  // kept apart from ctx: the context may be destroyed first
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long* counter = nullptr;
@@ -1166,6 +1169,7 @@ mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t st, mpg_graph** out) {
   cudaError_t e = cudaStreamEndCapture(st, &graph);
   mpg_graph* g = new mpg_graph();
   g->ctx = ctx;
+  g->device = ctx->device;
   g->counter = ctx->cap_rng;
   g->kernels = ctx->launches - ctx->cap_launch0 + 1;
   ctx->launches = ctx->cap_launch0;
@@ -1199,7 +1203,7 @@ mpg_status mpg_graph_end(mpg_ctx* ctx, cudaStream_t st, mpg_graph** out) {
 
 mpg_status mpg_graph_launch(mpg_graph* g, cudaStream_t st) {
   if (!g || !g->exec) return fail(MPG_ERR_INVALID_ARG, "graph is NULL");
-  CUDA_TRY(cudaSetDevice(g->ctx->device));
+  CUDA_TRY(cudaSetDevice(g->device));
   CUDA_TRY(cudaGraphLaunch(g->exec, st));
   g->ctx->launches += g->kernels;
   return MPG_OK;
@@ -1213,11 +1217,12 @@ mpg_status mpg_graph_kernels(const mpg_graph* g, int64_t* count) {
 
 void mpg_graph_destroy(mpg_graph* g) {
   if (!g) return;
-  cudaSetDevice(g->ctx->device);
+  cudaSetDevice(g->device);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   cudaFree(g->counter);
   delete g;
+  (void)cudaGetLastError();  // a failure here must not surface in a later call's launch check
 }
 
 // ---------------------------------------------------------------------------
@@ -1244,6 +1249,7 @@ void mpg_stree_destroy(mpg_stree* t) {
   cudaFree(t->d_axis); cudaFree(t->d_left); cudaFree(t->d_right); cudaFree(t->d_split);
   cudaFree(t->d_member_leaf); cudaFree(t->d_member_rec);
   delete t;
+  (void)cudaGetLastError();  // a failure here must not surface in a later call's launch check
 }
 
 mpg_status mpg_stree_build(mpg_ctx* ctx, const mpg_chains* chains, const int32_t* rec_chain, int32_t R,

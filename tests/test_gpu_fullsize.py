@@ -75,7 +75,7 @@ def _compare_blocks(M, wl, ch, res, guide_o, off, block=None):
     T = res.T.cpu().numpy()
     N = res.trials.cpu().numpy().astype(np.int64)
     E = res.E.cpu().numpy()
-    flags, same_T, same_N, rel_T, rel_E, dx = [], [], [], [], [], []
+    flags, same_T, same_N, rel_T, rel_E, dx, worst = [], [], [], [], [], [], []
     for b0 in _starts(wl):
         sl = slice(b0, b0 + BLOCK)
         sub = _block(wl, b0, BLOCK) if block is None else block(b0)
@@ -91,6 +91,7 @@ def _compare_blocks(M, wl, ch, res, guide_o, off, block=None):
         same_T.append(gadm == oadm)
         ab = gadm & oadm
         rel_T.append(np.abs(T[sl][ab] - oT[ab]) / oT[ab])
+        worst.append((rel_T[-1].max(initial=0.0), b0, np.nonzero(ab)[0][np.argmax(rel_T[-1])] if ab.any() else -1))
         same_N.append(N[sl][ab] == oN[ab])
         # irradiance of the points whose every chain agrees in admissibility and N
         ok = ((gadm == oadm) & ((N[sl] == oN) | ~oadm)).reshape(-1, wl.spq).all(axis=1)
@@ -103,7 +104,8 @@ def _compare_blocks(M, wl, ch, res, guide_o, off, block=None):
     assert flags.mean() >= 0.999, flags.mean()
     assert max(dx) < 1e-4 * wl.scene_scale, max(dx)
     assert same_T.mean() >= 0.999, same_T.mean()
-    assert rel_T.size > 200 and np.quantile(rel_T, 0.999) < 1e-3
+    # T of every chain both sides admit (the maximum, no quantile)
+    assert rel_T.size > 200 and rel_T.max() < 1e-3, max(worst)
     assert same_N.mean() >= 0.999, same_N.mean()
     assert rel_E.size > 50 and rel_E.max() < 1e-3
     # whole batch: E is the per-point mean of the contributions
@@ -246,3 +248,104 @@ def test_mixed_vmf_full_size_captured_step(M, ctx):
     _compare_blocks(M, wl, ch, res, og, off, block=block)
     for kk in range(1, 9):
         assert ((k_gpu == kk) & (ch.status.cpu().numpy() == 1)).sum() > 0
+
+
+def _put_block(M, ch, b0, o, status):
+    """Chains [b0, b0 + n) of the device batch set to the oracle's chains
+    (rounded to FP32) with the given status."""
+    n = status.size
+    sl = slice(b0, b0 + n)
+    ch.x[:, :, sl] = torch.as_tensor(np.ascontiguousarray(o["x"].transpose(1, 2, 0)).astype(np.float32), device="cuda")
+    ch.surf[:, sl] = torch.as_tensor(np.ascontiguousarray(o["surf"].T).astype(np.int32), device="cuda")
+    ch.prim[:, sl] = torch.as_tensor(np.ascontiguousarray(o["prim"].T).astype(np.int32), device="cuda")
+    ch.bary[:, :, sl] = torch.as_tensor(np.ascontiguousarray(o["bary"].transpose(1, 2, 0)).astype(np.float32),
+                                        device="cuda")
+    ch.tau[sl] = torch.as_tensor(o["tau"].astype(np.uint8), device="cuda")
+    ch.status[sl] = torch.as_tensor(status.astype(np.uint8), device="cuda")
+
+
+def test_water_full_size_captured_step_and_adjoint(M, ctx):
+    """The water heightfield at its full size (512 x 512 points x 4 seeds =
+    1,048,576 chains, BVH traversal), batched and replayed from a captured
+    graph, compared block by block with the oracle; then the adjoint of the
+    irradiance with respect to the 128 x 128 heights over the whole batch
+    (the launch the benchmark times): linear in the upstream gradient over
+    the whole batch, and equal to the oracle's implicit-function gradient on
+    receiver-aligned blocks of the oracle's chains placed in that batch."""
+    wl = I.water()
+    sc = M.Scene(ctx, wl)
+    ch = M.Chains(wl)
+    P = M.params_from(wl.params, walk_mode=M.WALK_BATCHED, k_uniform=0)
+    res = M.Contribution.empty(wl.B, wl.Q)
+
+    def step(off):
+        M.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, off)
+        M.mpg_manifold_walk(ctx, sc, ch, P)
+        M.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, off, out=res)
+
+    off = 5 * wl.B
+    step(off)
+    ctx.sync()
+    g = M.Graph(ctx, rng_advance=wl.B)
+    with g:
+        step(off)
+    g.launch()
+    ctx.sync()
+    _compare_blocks(M, wl, ch, res, None, off)
+    st = ch.status.cpu().numpy()
+    # one refraction converges for most points; the RT / TR chains need a
+    # crest to bounce off and converge rarely
+    assert ((wl.k == 1) & (st == 1)).sum() > 0.3 * (wl.k == 1).sum()
+    # adjoint over the whole batch, and over the two halves of the receiver points
+    dLdE = torch.as_tensor(I.upstream_grad(wl.Q), dtype=torch.float32, device="cuda")
+    n_h = wl.hf_heights.size
+    g_all = torch.zeros(n_h, dtype=torch.float32, device="cuda")
+    M.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE, g_all)
+    half = torch.zeros_like(dLdE)
+    half[: wl.Q // 2] = dLdE[: wl.Q // 2]
+    g_a, g_b = torch.zeros_like(g_all), torch.zeros_like(g_all)
+    M.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, half, g_a)
+    M.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE - half, g_b)
+    ctx.sync()
+    g_all = g_all.cpu().numpy().astype(np.float64)
+    assert np.isfinite(g_all).all() and np.count_nonzero(g_all) > 0.5 * n_h
+    assert np.linalg.norm(g_a.cpu().numpy() + g_b.cpu().numpy() - g_all) <= 1e-4 * np.linalg.norm(g_all)
+    # receiver-aligned blocks of the oracle's chains inside the full batch
+    osc = O.Scene(wl)
+    q = np.arange(wl.B) // wl.spq
+    T_in = np.zeros(wl.B, np.float32)
+    c_in = np.zeros(wl.B, np.float32)
+    up = np.zeros(wl.Q, np.float32)
+    dl = I.upstream_grad(wl.Q).astype(np.float32)
+    g_o = np.zeros(n_h)
+    for b0 in _starts(wl):
+        sub = _block(wl, b0, BLOCK)
+        sseeds = O.sample_seeds(sub, osc, None, rng_offset=off + b0)
+        och = O.walk(sub, osc, sseeds)
+        con = O.contribution(sub, osc, och)
+        oN, _ = O.bernoulli(sub, osc, och, con["admissible"], None, rng_offset=off + b0)
+        tight = dataclasses.replace(sub, params=dataclasses.replace(sub.params, tol=1e-12))
+        conv = dict(x=och["x"], surf=och["surf"], prim=och["prim"], bary=och["bary"], tau=och["tau"],
+                    valid=(och["status"] == 1).astype(np.uint8))
+        pol = O.walk(tight, osc, conv)
+        pol["status"] = np.where(pol["status"] == 1, och["status"], 0).astype(np.uint8)
+        cp = O.contribution(sub, osc, pol)
+        adm = (con["admissible"] == 1) & (cp["admissible"] == 1)
+        T = np.where(adm, cp["T"], 0.0)
+        contrib = np.where(adm, sub.light_area * T * oN / sub.pn, 0.0)
+        T32, c32 = T.astype(np.float32), contrib.astype(np.float32)
+        sq = np.arange(BLOCK) // wl.spq
+        w = np.where(T32 > 0, dl[b0 // wl.spq + sq] / wl.spq * c32.astype(np.float64) / np.maximum(T32, 1e-30), 0.0)
+        gb, _ = O.adjoint(sub, osc, och, w)
+        g_o += gb
+        _put_block(M, ch, b0, och, np.where(adm, M.CHAIN_CONVERGED, M.CHAIN_FAILED))
+        T_in[b0:b0 + BLOCK], c_in[b0:b0 + BLOCK] = T32, c32
+        up[b0 // wl.spq: (b0 + BLOCK) // wl.spq] = dl[b0 // wl.spq: (b0 + BLOCK) // wl.spq]
+    assert np.count_nonzero(T_in) > 1000
+    g_gpu = torch.zeros(n_h, dtype=torch.float32, device="cuda")
+    M.mpg_walk_adjoint(ctx, sc, ch, torch.as_tensor(T_in, device="cuda"), torch.as_tensor(c_in, device="cuda"),
+                       torch.as_tensor(up, device="cuda"), g_gpu)
+    ctx.sync()
+    g_gpu = g_gpu.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g_o) > 0
+    assert np.linalg.norm(g_gpu - g_o) <= 1e-2 * np.linalg.norm(g_o), np.linalg.norm(g_gpu - g_o) / np.linalg.norm(g_o)

@@ -60,16 +60,34 @@ def _oracle_pipeline(wl, guide=None):
     ch = O.walk(wl, sc, seeds)
     con = O.contribution(wl, sc, ch)
     N, capped = O.bernoulli(wl, sc, ch, con["admissible"], guide)
+    return sc, seeds, ch, _polished(wl, sc, ch, con), N, capped
+
+
+def _polished(wl, sc, ch, con):
+    """Contribution of the oracle's converged chains after polishing them to
+    max|C| < 1e-12; admissibility stays that of the walk at the tolerance."""
     tight = dataclasses.replace(wl, params=dataclasses.replace(wl.params, tol=1e-12))
     conv = dict(x=ch["x"], surf=ch["surf"], prim=ch["prim"], bary=ch["bary"], tau=ch["tau"],
                 valid=(ch["status"] == 1).astype(np.uint8))
     pol = O.walk(tight, sc, conv)
     pol["status"] = np.where(pol["status"] == 1, ch["status"], 0).astype(np.uint8)
     cp = O.contribution(wl, sc, pol)
-    # flags and trial counts stay those of the walk at the tolerance
-    con = dict(G=cp["G"], kappa=cp["kappa"], T=cp["T"],
-               admissible=(con["admissible"] & (cp["admissible"] | (ch["status"] != 1))).astype(np.uint8))
-    return sc, seeds, ch, con, N, capped
+    return dict(G=cp["G"], kappa=cp["kappa"], T=cp["T"],
+                admissible=(con["admissible"] & (cp["admissible"] | (ch["status"] != 1))).astype(np.uint8))
+
+
+def _assert_T_max(wl, T_g, T_o, ab, bar=1e-3):
+    """T of every chain both sides admit within `bar` relative (the maximum,
+    no quantile); on failure the message lists the worst chains."""
+    idx = np.nonzero(ab)[0]
+    rel = np.abs(T_g[idx] - T_o[idx]) / T_o[idx]
+    if rel.size and rel.max() >= bar:
+        worst = np.argsort(rel)[::-1][:8]
+        rows = ["b=%d k=%d rel=%.3e T_gpu=%.6e T_oracle=%.6e" % (idx[j], wl.k[idx[j]], rel[j], T_g[idx[j]], T_o[idx[j]])
+                for j in worst]
+        raise AssertionError("T beyond %.0e on %d of %d chains:\n%s" % (bar, int((rel >= bar).sum()), rel.size,
+                                                                        "\n".join(rows)))
+    return rel
 
 
 def _seed_valid(st):
@@ -208,8 +226,7 @@ def test_glass_sphere_guided_parity_and_histogram_bit_exact(M, ctx):
     G = out.G.cpu().numpy()
     ab = (G > 0) & (con2["admissible"] == 1) & both
     assert ab.sum() > 1000
-    rel = np.abs(out.T.cpu().numpy()[ab] - con2["T"][ab]) / con2["T"][ab]
-    assert np.quantile(rel, 0.999) < 1e-3
+    _assert_T_max(wl, out.T.cpu().numpy(), con2["T"], ab)
     gN = out.trials.cpu().numpy().astype(np.int64)
     assert (gN[ab] == N2[ab]).mean() >= 0.999
 
@@ -270,8 +287,7 @@ def test_water_pipeline_parity(M, ctx):
     T = out.T.cpu().numpy()
     ab = (T > 0) & (con["admissible"] == 1) & both
     assert ab.sum() > 1000
-    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
-    assert np.quantile(rel, 0.999) < 1e-3
+    _assert_T_max(wl, T, con["T"], ab)
 
 
 def test_water_point_light_parity(M, ctx):
@@ -289,8 +305,7 @@ def test_water_point_light_parity(M, ctx):
     T = out.T.cpu().numpy()
     ab = (T > 0) & (con["admissible"] == 1) & both
     assert ab.sum() > 1000
-    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
-    assert np.quantile(rel, 0.999) < 1e-3
+    _assert_T_max(wl, T, con["T"], ab)
 
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
@@ -305,8 +320,7 @@ def test_mixed_lengths_plain_and_batched(M, ctx, mode):
     T = out.T.cpu().numpy()
     assert ((T > 0) == (con["admissible"] == 1)).mean() >= 0.999
     ab = (T > 0) & (con["admissible"] == 1)
-    rel = np.abs(T[ab] - con["T"][ab]) / con["T"][ab]
-    assert np.quantile(rel, 0.999) < 1e-3
+    _assert_T_max(wl, T, con["T"], ab)
     for kk in range(1, 9):
         assert ((gw["status"] == 1) & (wl.k == kk)).sum() >= 0
 
@@ -507,7 +521,8 @@ def test_glossy_separator(M, ctx):
     rad, L = rad.cpu().numpy().astype(np.float64), L.cpu().numpy().astype(np.float64)
     big = oc > 1e-6 * oc.max()
     assert big.sum() > 100 and np.all(rad[~adm] == 0)
-    assert np.quantile(np.abs(rad[big] - oc[big]) / oc[big], 0.999) < 1e-4
+    rr = np.abs(rad[big] - oc[big]) / oc[big]
+    assert np.quantile(rr, 0.999) < 1e-4 and rr.max() < 1e-3
     assert np.allclose(L, oL, rtol=1e-4, atol=1e-6 * oL.max())
     cell, om, w = O.records(wl, ow, con["T"], N, con["admissible"])
     chain = np.nonzero(adm)[0]
@@ -519,4 +534,5 @@ def test_glossy_separator(M, ctx):
     gw = gw.cpu().numpy().astype(np.float64)
     big = wo > 1e-6 * wo.max()
     assert big.sum() > 100
-    assert np.quantile(np.abs(gw[big] - wo[big]) / wo[big], 0.999) < 1e-4
+    rr = np.abs(gw[big] - wo[big]) / wo[big]
+    assert np.quantile(rr, 0.999) < 1e-4 and rr.max() < 1e-3
