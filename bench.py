@@ -397,6 +397,7 @@ def run_ours(args, rank, world, local):
     }
     del graph
     if rank == 0 and not args.no_secondary:
+        line["configs"] = other_configs(args, dev, flush, torch, peak_nominal)
         line["secondary"] = secondary(args, dev, flush, torch, peak_nominal)
     if rank == 0:
         line["cpu_baseline"] = cpu_baseline(wl)
@@ -467,10 +468,46 @@ def measured_hbm():
         return 6800.0, "fallback"
 
 
-PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group")
+PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group",
+         "configs")
+# measured by default beside the headline; "mixed" and "adjoint" are covered
+# by the configuration lines (other_configs) and run only with --part
+DEFAULT_PARTS = ("plain", "k3", "k6", "vmf", "repeats", "progressive", "selective", "glossy")
 
 
-def secondary(args, dev, flush, torch, peak_fp32, parts=PARTS):
+def other_configs(args, dev, flush, torch, peak_fp32):
+    """The other configurations of the benchmark as lines of their own (see
+    config_line): the mirror sphere (k = 1, point light), the water
+    heightfield (BVH, k = 1..2), the mixed-length batch (k = 1..8, 2^22 chains:
+    batched vs plain on identical inputs) and the adjoint on the water scene."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    stream = torch.cuda.current_stream()
+    F = unit_flops()
+    steps = max(3, min(10, args.steps // 4))
+    ctx = mpg.Context(dev.index or 0)
+    out = {}
+    out["mirror_sphere"] = config_line(
+        ctx, dev, flush, torch, stream, I.mirror_sphere(),
+        "mirror_sphere_k1: r=1, point light (0,3,2), 64x64 points x 16 seeds from p_0 = 65,536 chains",
+        steps, args.warmup, F, peak_fp32, cpu_wl=I.mirror_sphere(), cpu_note="the whole workload")
+    out["water"] = config_line(
+        ctx, dev, flush, torch, stream, I.water(),
+        "water_heightfield: 128x128 heights (32,258 triangles, BVH), IOR 1.33, 512x512 floor points x 4 seeds"
+        " = 1,048,576 chains, k = 1 (T) or 2 (RT, TR)",
+        steps, args.warmup, F, peak_fp32, cpu_wl=I.water(n=128, spq=4),
+        cpu_note="1/16 sample: 128x128 floor points over the same extent x 4 seeds")
+    out["mixed"] = config_line(
+        ctx, dev, flush, torch, stream, I.mixed(),
+        "mixed_k1to8: nested spheres + 4 lenses + mirror, 1024x512 points x 8 seeds = 4,194,304 chains,"
+        " k ~ Geometric(0.35) on 1..8, random types",
+        steps, args.warmup, F, peak_fp32, cpu_wl=I.mixed(nx=256, ny=128, spq=8),
+        cpu_note="1/16 sample: 256x128 points over the same extent x 8 seeds")
+    out["adjoint"] = part_adjoint(ctx, dev, flush, torch, stream, steps)
+    return out
+
+
+def secondary(args, dev, flush, torch, peak_fp32, parts=DEFAULT_PARTS):
     """The other configurations, measured beside the headline:
     - k3: the standalone BVH ray batch on the water heightfield (GB/s);
     - k6: the guide-histogram update of one glass-sphere pass (GB/s);
@@ -686,6 +723,179 @@ def part_mixed(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
     best = max(mixed[k]["converged_walks_per_s"] for k in ("batched", "batched_autotuned", "batched_autotuned_2_in_flight"))
     mixed["batched_over_plain"] = best / mixed["plain"]["converged_walks_per_s"]
     return mixed
+
+
+def config_line(ctx, dev, flush, torch, stream, wl, describe, steps, warmup, F, peak_fp32, autotune=True,
+                cpu_wl=None, cpu_note=""):
+    """One configuration measured like the headline: the batched step (seeds
+    -> walk -> contribution with Bernoulli trials -> irradiance) replayed from
+    a captured graph with the autotuned schedule, against the plain mode (one
+    launch per chain length, sequential trial loops, no graph) on identical
+    inputs (the same random-number offsets, so the same seeds and trials);
+    converged walks per second with and without the Bernoulli trial walks;
+    the irradiance throughput; the roofline of the dominant kernel family from
+    per-launch CUDA events of an uncaptured pass of the same steps; the same
+    metric end to end with host inputs; and the oracle on the host cores."""
+    import numpy as np
+    from paper_2311_12818_gb300 import mpg
+    B, Q = wl.B, wl.Q
+    uniform = int(wl.k[0]) if (wl.k == wl.k[0]).all() else 0
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(B, Q, device=dev)
+    base = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=wl.tau_random, k_uniform=uniform)
+    plain = mpg.params_from(wl.params, walk_mode=mpg.WALK_PLAIN, tau_random=wl.tau_random, k_uniform=uniform)
+
+    def step(P, o, s=None):
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, o, stream=s)
+        mpg.mpg_manifold_walk(ctx, sc, ch, P, stream=s)
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, o, out=res, stream=s)
+
+    step(base, 1 << 44)
+    ctx.sync()
+    tune_s, P = None, base
+    if autotune:
+        t0 = time.perf_counter()
+        P, _ = mpg.mpg_autotune(ctx, sc, None, ch, base, wl.rng_seed, 1 << 45, repeats=1)
+        tune_s = time.perf_counter() - t0
+    BASE = 1 << 40
+    offs = [BASE + (warmup + j) * B for j in range(steps)]  # graph replay warmup + j draws here
+    step(P, BASE)
+    ctx.sync()
+    g = mpg.Graph(ctx, rng_advance=B)
+    with g:
+        step(P, BASE, g.stream)
+    for _ in range(warmup):
+        g.launch()
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        ctx.reset_stats()
+        ms, prim = [], 0
+        for j in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(j)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        ctx.sync()
+        return sum(ms) / steps, ctx.stats()
+
+    ms_b, st_b = timed(lambda j: g.launch())
+    n_launch = g.kernels()
+    adm_b = int((res.contrib > 0).sum().item())
+    # plain mode on the same offsets
+    ms_p, st_p = timed(lambda j: step(plain, offs[j]))
+    # attribution: the batched schedule uncaptured at the same offsets, every
+    # launch bracketed by events on its own stream; primary convergences
+    ctx.reset_stats()
+    ctx.profile(reset=True)
+    ctx.set_profile(True)
+    prim_b = 0
+    for j in range(steps):
+        flush.zero_()
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, offs[j])
+        mpg.mpg_manifold_walk(ctx, sc, ch, P)
+        ctx.sync()
+        prim_b += int((ch.status == 1).sum().item())
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, offs[j], out=res)
+    ctx.sync()
+    ctx.set_profile(False)
+    fam = {}
+    for kind, fname in enumerate(mpg.KERNEL_NAMES):
+        fms, nl = ctx.profile(kind)
+        fst = ctx.stats(kind)
+        fam[fname] = dict(ms=fms, launches=nl, flops=algorithmic_flops(fst, F))
+    ctx.profile(reset=True)
+    dom = max((n for n in fam if n not in ("aux", "trace")), key=lambda n: fam[n]["ms"])
+    d = fam[dom]
+    kernels = {"walk": "k_walk_g" if P.walk_group & 1 else "k_walk_p",
+               "bernoulli": "k_bern_round_g" if P.walk_group & 2 else "k_bern_round",
+               "contrib": "k_contrib", "seed": "k_seed"}[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) if d["ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": kernels, "family": dom, "achieved": achieved / 1e12,
+                "peak": peak_fp32 / 1e12, "unit": "TFLOP/s", "frac": achieved / peak_fp32, "traffic": None,
+                "algorithmic_flops_per_launch": d["flops"] / max(1, d["launches"]),
+                "avg_launch_ms": d["ms"] / max(1, d["launches"]),
+                "timing": "per-launch CUDA events in an uncaptured pass of the same steps (family: %d launches)"
+                          % d["launches"]}
+    # end to end: pinned host inputs copied in, the irradiance image read back
+    pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
+    host_in = [(ch.xD, pin(np.ascontiguousarray(wl.xD.T, np.float32))),
+               (ch.nD, pin(np.ascontiguousarray(wl.nD.T, np.float32))), (ch.cell, pin(wl.cell.astype(np.int32))),
+               (ch.xL, pin(np.ascontiguousarray(wl.xL.T, np.float32))), (ch.k, pin(wl.k.astype(np.uint8))),
+               (ch.tau, pin(wl.tau.astype(np.uint8))), (ch.pn, pin(wl.pn.astype(np.float32)))]
+    E_host = torch.empty(Q, dtype=torch.float32).pin_memory()
+
+    def e2e_step(j):
+        for dd, hh in host_in:
+            dd.copy_(hh, non_blocking=True)
+        g.launch()
+        E_host.copy_(res.E, non_blocking=True)
+    n_e2e = max(2, steps // 2)
+    ctx.reset_stats()
+    ms_e = 0.0
+    for j in range(n_e2e):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step(j)
+        b.record(stream)
+        b.synchronize()
+        ms_e += a.elapsed_time(b)
+    ctx.sync()
+    ms_e /= n_e2e
+    e2e_conv = ctx.stats()["converged"] / n_e2e
+    h2d = sum(h.numel() * h.element_size() for _, h in host_in)
+    out = {
+        "workload": describe, "metric": METRIC, "unit": UNIT,
+        "value": st_b["converged"] / steps / (ms_b * 1e-3), "ms_per_step": ms_b, "steps": steps,
+        "warmup": warmup, "chains_per_step": B, "same_inputs_as_plain": True,
+        "primary_converged_walks_per_s": prim_b / steps / (ms_b * 1e-3),
+        "converged_per_step": st_b["converged"] / steps, "primary_converged_per_step": prim_b / steps,
+        "trials_per_step": st_b["trials"] / steps,
+        "irradiance_throughput": {"shading_points_per_s": Q / (ms_b * 1e-3),
+                                  "contributions_per_s": adm_b / (ms_b * 1e-3), "contributions_per_step": adm_b},
+        "fp32_tflops_step": algorithmic_flops(st_b, F) / steps / (ms_b * 1e-3) / 1e12,
+        "fp32_frac_step": algorithmic_flops(st_b, F) / steps / (ms_b * 1e-3) / peak_fp32,
+        "graph_kernels_per_step": n_launch,
+        "schedule": {f: getattr(P, f) for f in mpg.SCHEDULE_FIELDS}, "autotune_s": tune_s,
+        "plain": {"ms_per_step": ms_p, "converged_walks_per_s": st_p["converged"] / steps / (ms_p * 1e-3),
+                  "converged_per_step": st_p["converged"] / steps,
+                  "fp32_frac_step": algorithmic_flops(st_p, F) / steps / (ms_p * 1e-3) / peak_fp32},
+        "roofline": roofline,
+        "families_uncaptured_ms_per_step": {n: f["ms"] / steps for n, f in fam.items() if f["launches"]},
+        "e2e": {"value": e2e_conv / (ms_e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": Q * 4},
+    }
+    out["batched_over_plain"] = out["value"] / out["plain"]["converged_walks_per_s"]
+    if cpu_wl is not None:
+        out["cpu_baseline"] = cpu_line(cpu_wl, cpu_note)
+    del g
+    return out
+
+
+def cpu_line(wl, note):
+    """The oracle (as it stands) on all host cores over a sample workload:
+    seeds -> walk -> contribution -> Bernoulli trials -> irradiance."""
+    import numpy as np
+
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    sc = O.Scene(wl)
+    s = O.sample_seeds(wl, sc, None, threads=threads)
+    c = O.walk(wl, sc, s, threads=threads)
+    k = O.contribution(wl, sc, c, threads=threads)
+    tw = np.zeros(wl.B, np.uint32)
+    N, _ = O.bernoulli(wl, sc, c, k["admissible"], None, threads=threads, trial_walks=tw)
+    O.irradiance(wl, k["T"], N, k["admissible"])
+    dt = time.perf_counter() - t0
+    conv = int((c["status"] == 1).sum() + tw.sum())
+    return {"value": conv / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%s: %d chains, one step, %.1f s" % (note, wl.B, dt)}
 
 
 def part_adjoint(ctx, dev, flush, torch, stream, steps):
@@ -1029,6 +1239,9 @@ def run_part(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     props = torch.cuda.get_device_properties(dev)
     peak = props.multi_processor_count * 128 * 2 * 2070.0 * 1e6
+    if args.part == "configs":
+        print(json.dumps({"part": args.part, **other_configs(args, dev, flush, torch, peak)}))
+        return
     print(json.dumps({"part": args.part, **secondary(args, dev, flush, torch, peak, parts=(args.part,))}))
 
 

@@ -127,6 +127,10 @@ typedef struct mpg_params {
                            chain is MPG_CHAIN_INVALID at once and contributes
                            nothing; the paper hands such points to path
                            tracing, which this library does not do          */
+  float roughness;      /* glossy chains (chains.offset set, Sec. 5.7): the
+                           Beckmann roughness alpha of every vertex, used by
+                           the shadowing term of the estimate (0..1; 0 = the
+                           specular limit of the estimate)                   */
 } mpg_params;
 
 /* Chain batch: B = Q * spq chains of length k[b] <= 8 between x_D[q] and x_L[b]. */
@@ -148,6 +152,11 @@ typedef struct mpg_chains {
   uint8_t* iters;       /* [B] Newton steps taken                                  */
   const uint32_t* chain_cell; /* [B] guide cell of each chain (a spatial tree's leaf,
                            mpg_stree_query), or NULL => cell[b / spq]             */
+  const float* offset;  /* [8][2][B] offset normals of glossy chains
+                           (mpg_sample_offsets), or NULL for specular chains:
+                           the tangential components o_i of a microfacet normal
+                           per vertex in the vertex's shading frame; the walk
+                           then solves C_i = (h.s_i, h.t_i) - o_i (Sec. 5.7)  */
 } mpg_chains;
 
 /* Guide kinds (mpg_guide.kind). */
@@ -239,7 +248,9 @@ mpg_status mpg_ctx_stats(mpg_ctx* ctx, int32_t kind, mpg_stats* out, int32_t res
 /* Work counters on (default) or off; off skips writing them. */
 mpg_status mpg_ctx_set_stats(mpg_ctx* ctx, int32_t on);
 /* Launch timing: when on, every kernel launch of the library is bracketed by
- * CUDA events recorded on the stream it is launched on.  mpg_ctx_profile sums
+ * CUDA events recorded on the stream it is launched on, and the per-length
+ * launches of a batched call run one after another on the call's stream
+ * (instead of on concurrent streams), so each bracket times its kernel alone.  mpg_ctx_profile sums
  * the elapsed times (ms) and counts the launches of a family (kind) since the
  * last reset; it synchronises on the recorded events. */
 mpg_status mpg_ctx_set_profile(mpg_ctx* ctx, int32_t on);
@@ -282,6 +293,17 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guid
                             mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
                             const mpg_params* params, cudaStream_t stream);
 
+/* Sec. 5.7 -- offset normals of glossy chains: for chain b and vertex i <
+ * k[b], a microfacet normal m drawn from the isotropic Beckmann distribution
+ * of roughness alpha with density D(m) (m.n) (tan^2 theta = -alpha^2
+ * log(1 - u1), phi = 2 pi u2, u1 and u2 from Philox4x32-10 counter
+ * (b + rng_offset, i, 4)); offset[(2i + c) B + b] = its tangential components
+ * (sin theta cos phi, sin theta sin phi), zeros for i >= k[b].  Uses B and k
+ * of `chains`; offset is a device array of 16 B floats.  Errors: alpha outside
+ * (0, 1], NULL or unaligned arrays (MPG_ERR_INVALID_ARG). */
+mpg_status mpg_sample_offsets(mpg_ctx* ctx, const mpg_chains* chains, float alpha, uint64_t rng_seed,
+                              uint64_t rng_offset, float* offset, cudaStream_t stream);
+
 /* S2-S6 -- manifold walk (Sec. 3, "Manifold walks"): Newton's method on the
  * generalized half-vector constraints C_i = (h.s_i, h.t_i), h ~ eta_i w_i +
  * eta_o w_o, with the 2k x 2k block-tridiagonal Jacobian solved by a 2x2-block
@@ -290,7 +312,8 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guid
  * centre of spheres and caps, along the normal of rectangles, vertically into
  * heightfields).  Chain visibility is left to mpg_chain_contribution's
  * admissibility test.  Walks every chain whose status is MPG_CHAIN_SEEDED; writes x,
- * surf, prim, bary, status and iters in place. */
+ * surf, prim, bary, status and iters in place.  Glossy chains (chains.offset
+ * set) are walked to C_i = o_i by the plain kernels whatever walk_mode asks. */
 mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* chains,
                              const mpg_params* params, cudaStream_t stream);
 
@@ -315,7 +338,8 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* scene, mpg_chains* c
  * stream capture.  It calls no cudaMalloc, cudaFree or allocating library
  * routine.  Every call shares the array and clears what must start at zero;
  * calls that overlap on the GPU (two streams, or two host threads) race on it.
- * The scene must live on the current device. */
+ * The scene must live on the current device.  Glossy chains (chains.offset
+ * set) are rejected with MPG_ERR_UNSUPPORTED. */
 mpg_status mpg_manifold_walk_noalloc(const mpg_scene* scene, mpg_chains* chains,
                                      const mpg_params* params, cudaStream_t stream);
 
@@ -331,7 +355,14 @@ mpg_status mpg_manifold_walk_noalloc(const mpg_scene* scene, mpg_chains* chains,
  * point light) and the irradiance estimate E[q] = sum_b contrib / spq
  * (Eq. ThroughputMC).  Outputs may be NULL except E; all are [B] unless noted.
  * Chains whose geometry term is formed in FP64 are first polished in FP64;
- * their x, prim and bary are updated in place with the polished vertices. */
+ * their x, prim and bary are updated in place with the polished vertices.
+ * Glossy chains (chains.offset set; plain kernels): T is the estimate
+ * W = L_e prod_i f_i |n_i.l_i| prod(area factors) / (|det dC/du| prod_i p(o_i))
+ * of Sec. 5.7 in FP64 (f the microfacet BSDF of Walter et al. 2007 with the
+ * Beckmann distribution of roughness params.roughness, p(o) = D(m) on the unit
+ * disk, so D cancels; |det dC/du| as the product of the block elimination's
+ * pivot determinants), G and kappa are 0, and the Bernoulli trials walk every
+ * trial seed with the chain's own offsets. */
 mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
                                   const mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
                                   const mpg_params* params, float* G, float* kappa, float* T,

@@ -264,6 +264,7 @@ mpg_status check_chains(const mpg_chains* c, bool need_walk_state) {
     if (!aligned16(req[i])) return fail(MPG_ERR_INVALID_ARG, "chains.%s is NULL or not 16-byte aligned", names[i]);
   if (need_walk_state && !aligned16(c->pdf)) return fail(MPG_ERR_INVALID_ARG, "chains.pdf is NULL or unaligned");
   if (c->chain_cell && !aligned16(c->chain_cell)) return fail(MPG_ERR_INVALID_ARG, "chains.chain_cell is not 16-byte aligned");
+  if (c->offset && !aligned16(c->offset)) return fail(MPG_ERR_INVALID_ARG, "chains.offset is not 16-byte aligned");
   return MPG_OK;
 }
 
@@ -278,7 +279,7 @@ mpg_status check_params(const mpg_params* p) {
       p->refill_every < 0 || p->refill_every > 64 || p->trial_sync_rounds < -1 || p->trial_sync_rounds > 8 ||
       p->trial_batch < 0 || p->trial_batch > 4096 || p->walk_group < 0 || p->walk_group > 3 ||
       p->bern_repeats < 0 || p->bern_repeats > 64 || (p->bern_repeats > 1 && p->max_trials >= (1 << 24)) ||
-      p->selective < 0 || p->selective > 1)
+      p->selective < 0 || p->selective > 1 || !(p->roughness >= 0.0f && p->roughness <= 1.0f))
     return fail(MPG_ERR_INVALID_ARG, "invalid solver parameters");
   return MPG_OK;
 }
@@ -288,7 +289,7 @@ DChains to_dev(const mpg_chains* c) {
   d.B = c->B; d.Q = c->Q; d.spq = c->spq;
   d.xD = c->xD; d.nD = c->nD; d.cell = c->cell; d.xL = c->xL; d.k = c->k; d.pn = c->pn; d.tau = c->tau;
   d.x = c->x; d.surf = c->surf; d.prim = c->prim; d.bary = c->bary; d.pdf = c->pdf;
-  d.status = c->status; d.iters = c->iters; d.chain_cell = c->chain_cell;
+  d.status = c->status; d.iters = c->iters; d.chain_cell = c->chain_cell; d.offset = c->offset;
   return d;
 }
 
@@ -401,9 +402,12 @@ DCtx dctx(mpg_ctx* ctx, int kind) {
 }
 
 // Runs fn(K, stream) for each planned K, on forked streams when concurrent.
+// With launch timing on (mpg_ctx_set_profile), the lengths run one after
+// another on the call's stream, so that each bracketed launch has the GPU to
+// itself and its events time that kernel alone.
 template <class F>
 mpg_status run_plan(mpg_ctx* ctx, const Plan& plan, cudaStream_t st, F fn) {
-  if (!plan.concurrent) {
+  if (!plan.concurrent || ctx->profile) {
     for (int i = 0; i < plan.nK; ++i) fn(plan.K[i], st);
     LAUNCH_CHECK("kernel launch");
     return MPG_OK;
@@ -746,12 +750,31 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* 
   });
 }
 
-mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chains, const mpg_params* P,
+mpg_status mpg_sample_offsets(mpg_ctx* ctx, const mpg_chains* chains, float alpha, uint64_t rng_seed,
+                              uint64_t rng_offset, float* offset, cudaStream_t st) {
+  if (!ctx) return fail(MPG_ERR_INVALID_ARG, "ctx is NULL");
+  if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
+  if (!chains || chains->B <= 0 || !aligned16(chains->k) || !aligned16(offset))
+    return fail(MPG_ERR_INVALID_ARG, "chains (B > 0, k) and offset must be 16-byte aligned device arrays");
+  if (!(alpha > 0.0f && alpha <= 1.0f)) return fail(MPG_ERR_INVALID_ARG, "roughness alpha %g outside (0, 1]", alpha);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  DChains c = to_dev(chains);
+  uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
+  timed(ctx, MPG_KERNEL_SEED, st, 1,
+        [&] { launch_offsets(c, alpha, key, rng_offset, dctx(ctx, MPG_KERNEL_SEED), offset, ctx->sms, st); });
+  LAUNCH_CHECK("offsets");
+  return MPG_OK;
+}
+
+mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chains, const mpg_params* Pin,
                              cudaStream_t st) {
   if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
   if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
   mpg_status s;
-  if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  if ((s = check_chains(chains, false)) || (s = check_params(Pin))) return s;
+  mpg_params Pg = *Pin;
+  if (chains->offset) Pg.walk_mode = MPG_WALK_PLAIN;  // glossy chains: one launch per length, one thread per chain
+  const mpg_params* P = &Pg;
   CUDA_TRY(cudaSetDevice(ctx->device));
   Plan plan;
   if ((s = make_plan(ctx, chains, P, ST_SEEDED, st, plan))) return s;
@@ -775,13 +798,16 @@ mpg_status mpg_manifold_walk(mpg_ctx* ctx, const mpg_scene* sc, mpg_chains* chai
 }
 
 mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* guide, const mpg_chains* chains,
-                                  uint64_t rng_seed, uint64_t rng_offset, const mpg_params* P, float* G, float* kappa,
-                                  float* T, uint32_t* trials, uint8_t* capped, float* contrib, float* E,
+                                  uint64_t rng_seed, uint64_t rng_offset, const mpg_params* Pin, float* G,
+                                  float* kappa, float* T, uint32_t* trials, uint8_t* capped, float* contrib, float* E,
                                   cudaStream_t st) {
   if (!ctx || !sc) return fail(MPG_ERR_INVALID_ARG, "ctx or scene is NULL");
   if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;  // empty batch
   mpg_status s;
-  if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  if ((s = check_chains(chains, false)) || (s = check_params(Pin))) return s;
+  mpg_params Pg = *Pin;
+  if (chains->offset) Pg.walk_mode = MPG_WALK_PLAIN;  // glossy chains: the plain kernels
+  const mpg_params* P = &Pg;
   if (!aligned16(T) || !aligned16(contrib) || !aligned16(E))
     return fail(MPG_ERR_INVALID_ARG, "T, contrib and E must be non-NULL 16-byte aligned device arrays");
   DGuide g;
@@ -855,7 +881,11 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
     DOut oK = o;
     oK.fp64_count = ctx->d_fp64_count + K;
     oK.fp64_base = (plan.w.base ? plan.w.base : ctx->d_zero) + K;
-    timed(ctx, MPG_KERNEL_CONTRIB, s2, 2, [&] {
+    timed(ctx, MPG_KERNEL_CONTRIB, s2, c.offset ? 1 : 2, [&] {
+      if (c.offset) {  // glossy chains: admissibility and the estimate W in FP64
+        launch_glossy(K, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, P, 2, K, 64, c.B, true), s2);
+        return;
+      }
       launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, P, 2, K, block, c.B, true), block,
                      s2);
       launch_contrib64(K, sc->S, c, *P, oK, ctx->sms * 2, s2);
@@ -1655,6 +1685,8 @@ extern "C" mpg_status mpg_manifold_walk_noalloc(const mpg_scene* sc, mpg_chains*
   if (chains && chains->B == 0 && chains->Q == 0) return MPG_OK;
   mpg_status s;
   if ((s = check_chains(chains, false)) || (s = check_params(P))) return s;
+  if (chains->offset)
+    return fail(MPG_ERR_UNSUPPORTED, "mpg_manifold_walk_noalloc walks specular chains only (chains.offset is set)");
   if (chains->B > NOALLOC_MAX_CHAINS)
     return fail(MPG_ERR_INVALID_ARG, "mpg_manifold_walk_noalloc takes at most %d chains per call (got %d)",
                 NOALLOC_MAX_CHAINS, chains->B);

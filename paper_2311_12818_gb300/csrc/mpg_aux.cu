@@ -67,6 +67,44 @@ cudaError_t launch_bucket(const uint8_t* k, const uint8_t* status, int filter, i
 }
 
 // ---------------------------------------------------------------------------
+// Offset normals of glossy chains (Sec. 5.7): for chain b and vertex i < k[b]
+// one Philox4x32-10 block with counter (b + offset, i, 4) gives u1 and u2; the
+// normal is drawn from the Beckmann distribution with density D(m) (m.n):
+// tan^2(theta) = -alpha^2 log(1 - u1), phi = 2 pi u2; its tangential part
+// (sin theta cos phi, sin theta sin phi) is the offset.  Vertices past the
+// chain's length get zeros.
+// ---------------------------------------------------------------------------
+__global__ void k_offsets(const uint8_t* k, int B, float alpha, uint2 key, uint64_t offset, DCtx ctx, float* out) {
+  offset = rng_offset(offset, ctx);
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
+    const int kk = k[b];
+    const uint64_t idx = (uint64_t)b + offset;
+#pragma unroll
+    for (int i = 0; i < MAXK; ++i) {
+      float ox = 0.0f, oy = 0.0f;
+      if (i < kk) {
+        const uint4 r = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)i, 4u), key);
+        const float u1 = u01(r.x), u2 = u01(r.y);
+        const float t2 = -alpha * alpha * logf(1.0f - u1);
+        const float c = 1.0f / sqrtf(1.0f + t2), sn = sqrtf(t2) * c;
+        float sp, cp;
+        sincospif(2.0f * u2, &sp, &cp);
+        ox = sn * cp;
+        oy = sn * sp;
+      }
+      out[(size_t)(2 * i + 0) * B + b] = ox;
+      out[(size_t)(2 * i + 1) * B + b] = oy;
+    }
+  }
+}
+
+void launch_offsets(const DChains& c, float alpha, uint2 key, uint64_t offset, DCtx ctx, float* out, int sms,
+                    cudaStream_t st) {
+  const int grid = max(1, min(sms * 8, (c.B + 255) / 256));
+  k_offsets<<<grid, 256, 0, st>>>(c.k, c.B, alpha, key, offset, ctx, out);
+}
+
+// ---------------------------------------------------------------------------
 // E[q] = (1/spq) sum_j contrib[q*spq + j]   (Eq. ThroughputMC), fixed order.
 // ---------------------------------------------------------------------------
 __global__ void k_irradiance(const float* contrib, int Q, int spq, float* E) {

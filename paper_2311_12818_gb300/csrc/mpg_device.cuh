@@ -505,10 +505,13 @@ struct Ends {
 };
 
 // Full evaluation of all K vertices; fills vb and the tangent bases.
+// off (NULL for specular chains): the offset normals of a glossy chain, one
+// 2-vector of tangential components per vertex; the constraint becomes
+// C_i = (h.s_i, h.t_i) - off_i (Sec. 5.7) and the Jacobian blocks stay.
 template <int K, bool kStats>
 __device__ __forceinline__ bool eval_full(const DScene& S, const Chain<K>& ch, const Ends& e, VB (&vb)[K],
                                           float3 (&tu)[K], float3 (&tv)[K], float& cnorm2, float& cmax,
-                                          bool want_ends, Counters& cnt) {
+                                          bool want_ends, Counters& cnt, const float2* off = nullptr) {
   Frame fr[K];
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -531,6 +534,7 @@ __device__ __forceinline__ bool eval_full(const DScene& S, const Chain<K>& ch, c
     bool wa = i > 0 || want_ends, wc = i < K - 1 || want_ends;
     if (!vertex_blocks(xp, pu, pv, ch.x[i], fr[i], xn, nu, nv, S.s[ch.surf[i]], (e.tau >> i) & 1u, wa, wc, vb[i]))
       return false;
+    if (off) vb[i].C = make_float2(vb[i].C.x - off[i].x, vb[i].C.y - off[i].y);
     cnorm2 = fmaf(vb[i].C.x, vb[i].C.x, fmaf(vb[i].C.y, vb[i].C.y, cnorm2));
     cmax = fmaxf(cmax, fmaxf(fabsf(vb[i].C.x), fabsf(vb[i].C.y)));
   }
@@ -540,7 +544,7 @@ __device__ __forceinline__ bool eval_full(const DScene& S, const Chain<K>& ch, c
 
 template <int K, bool kStats>
 __device__ __forceinline__ bool eval_c(const DScene& S, const Chain<K>& ch, const Ends& e, float& cnorm2,
-                                       Counters& cnt) {
+                                       Counters& cnt, const float2* off = nullptr) {
   cnorm2 = 0.0f;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -549,6 +553,7 @@ __device__ __forceinline__ bool eval_c(const DScene& S, const Chain<K>& ch, cons
     float3 n = vertex_normal(S, ch.surf[i], ch.prim[i], ch.x[i], ch.b1[i], ch.b2[i]);
     float2 C;
     if (!vertex_c(xp, ch.x[i], xn, n, S.s[ch.surf[i]], (e.tau >> i) & 1u, C)) return false;
+    if (off) C = make_float2(C.x - off[i].x, C.y - off[i].y);
     cnorm2 = fmaf(C.x, C.x, fmaf(C.y, C.y, cnorm2));
   }
   if (kStats) cnt.c_evals += K;
@@ -624,13 +629,13 @@ __device__ __forceinline__ bool propose(const DScene& S, const Chain<K>& ch, con
 // the number of Newton steps taken.
 template <int K, bool kStats>
 __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_params& P, int& iters, int* err,
-                    Counters& cnt) {
+                    Counters& cnt, const float2* off = nullptr) {
   VB vb[K];
   float3 tu[K], tv[K];
   float cn2, cmax;
   for (int it = 0;; ++it) {
     iters = it;
-    if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, false, cnt)) return ST_FAILED;
+    if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, false, cnt, off)) return ST_FAILED;
     if (cmax < P.tol) return ST_CONVERGED;
     if (it >= P.max_iter) return cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
     float2 du[K][1];
@@ -646,7 +651,7 @@ __device__ int walk(const DScene& S, Chain<K>& ch, const Ends& e, const mpg_para
       Chain<K> cand;
       if (!propose<K>(S, ch, dstep, beta, cand)) continue;
       float cc2;
-      if (eval_c<K, kStats>(S, cand, e, cc2, cnt) && cc2 < cn2) {
+      if (eval_c<K, kStats>(S, cand, e, cc2, cnt, off) && cc2 < cn2) {
         ch = cand;
         accepted = true;
         break;
@@ -1013,14 +1018,13 @@ __device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 
 // reciprocity eta_D^2 X_L = eta_L^2 |n_L.w_L| X_D, so their relative mismatch
 // estimates the FP32 error of G (out: mismatch); cmax (out) is the chain's
 // FP32 residual.  Returns false for an inadmissible chain.
+// Admissibility of a converged chain: every vertex type matches the sides of
+// its neighbours (refraction crosses the surface, reflection stays on one
+// side), the receiver and an area light face the chain, and every segment is
+// unoccluded.
 template <int K, bool kStats>
-__device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
-                             float& kappa, float& mismatch, float& cmax, float& kappa_err, int* err, Counters& cnt) {
-  VB vb[K];
-  float3 tu[K], tv[K];
-  float cn2;
-  if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, true, cnt)) return false;
-  // vertex types must match the sides of their neighbours
+__device__ __forceinline__ bool admissible(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P,
+                                           int* err, Counters& cnt) {
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     float3 xp = i == 0 ? e.xD : ch.x[i - 1];
@@ -1031,17 +1035,30 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
     if (refract ? !(si * so < 0.0f) : !(si * so > 0.0f)) return false;
   }
   float3 wD = unit(ch.x[0] - e.xD);
-  float cosD = dot(e.nD, wD);
-  if (!(cosD > 0.0f)) return false;
-  bool point = S.L.type == LIGHT_POINT;
+  if (!(dot(e.nD, wD) > 0.0f)) return false;
   float3 wL = unit(ch.x[K - 1] - e.xL);
-  if (!point && !(dot(S.L.n, wL) > 0.0f)) return false;
+  if (S.L.type != LIGHT_POINT && !(dot(S.L.n, wL) > 0.0f)) return false;
   if (!segment_clear<kStats>(S, e.xD, ch.x[0], P.ray_eps, err, cnt)) return false;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     float3 b = i == K - 1 ? e.xL : ch.x[i + 1];
     if (!segment_clear<kStats>(S, ch.x[i], b, P.ray_eps, err, cnt)) return false;
   }
+  return true;
+}
+
+template <int K, bool kStats>
+__device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
+                             float& kappa, float& mismatch, float& cmax, float& kappa_err, int* err, Counters& cnt) {
+  VB vb[K];
+  float3 tu[K], tv[K];
+  float cn2;
+  if (!eval_full<K, kStats>(S, ch, e, vb, tu, tv, cn2, cmax, true, cnt)) return false;
+  if (!admissible<K, kStats>(S, ch, e, P, err, cnt)) return false;
+  float3 wD = unit(ch.x[0] - e.xD);
+  float cosD = dot(e.nD, wD);
+  bool point = S.L.type == LIGHT_POINT;
+  float3 wL = unit(ch.x[K - 1] - e.xL);
   // J Y = -dC/du_end: columns 0,1 light end (block row K-1), 2,3 receiver end (row 0)
   float2 Y[K][4];
 #pragma unroll

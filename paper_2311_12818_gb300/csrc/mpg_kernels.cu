@@ -67,6 +67,13 @@ void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w
 #undef C_
 }
 
+void launch_glossy(int K, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx, int grid,
+                   cudaStream_t st) {
+#define C_(KK) KLaunch<KK>::glossy(S, c, w, P, o, ctx, grid, st)
+  MPG_SWITCH(K, C_)
+#undef C_
+}
+
 void launch_contrib64(int K, const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid,
                       cudaStream_t st) {
 #define C_(KK) KLaunch<KK>::contrib64(S, c, P, o, grid, st)

@@ -23,6 +23,7 @@ struct DChains {
   uint8_t* status;
   uint8_t* iters;
   const uint32_t* chain_cell;  // per-chain guide cell, or NULL
+  const float* offset;         // [8][2][B] offset normals of glossy chains, or NULL (specular)
 };
 
 // Guide cell of chain b: its own (a spatial tree's leaf) or its receiver point's.
@@ -147,8 +148,17 @@ struct KLaunch {
                          const mpg_params& P, DCtx ctx, int* queue, const int* list, const int* n_list,
                          const int* base, unsigned* nbest, int t0, int TB, DPairs pr, int grid, int block,
                          cudaStream_t st);
+  // glossy chains: admissibility and the estimate W (FP64) as T
+  static void glossy(const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx, int grid,
+                     cudaStream_t st);
   static int blocks_per_sm(int which, bool stats, int block);
 };
+
+void launch_glossy(int K, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx, int grid,
+                   cudaStream_t st);
+// Offset normals of glossy chains (Beckmann, roughness alpha), [8][2][B].
+void launch_offsets(const DChains& c, float alpha, uint2 key, uint64_t offset, DCtx ctx, float* out, int sms,
+                    cudaStream_t st);
 
 // Persistent-mode launchers by chain length (dispatch to KLaunch<K>).
 void launch_walk_p(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "mpg_ggt64.cuh"
+#include "mpg_glossy.cuh"
 #include "mpg_kernels.cuh"
 
 namespace mpg {
@@ -55,6 +56,14 @@ __device__ __forceinline__ void store_chain(const DChains& c, int b, const Chain
     c.bary[(2 * i + 0) * B + b] = ch.b1[i];
     c.bary[(2 * i + 1) * B + b] = ch.b2[i];
   }
+}
+
+// Offset normals of glossy chain b (its K vertices' tangential components).
+template <int K>
+__device__ __forceinline__ void load_offsets(const DChains& c, int b, float2 (&off)[K]) {
+  const size_t B = (size_t)c.B;
+#pragma unroll
+  for (int i = 0; i < K; ++i) off[i] = make_float2(c.offset[(2 * i + 0) * B + b], c.offset[(2 * i + 1) * B + b]);
 }
 
 __device__ __forceinline__ Ends load_ends(const DChains& c, int b) {
@@ -110,7 +119,8 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
   if (kS) flush(t, ctx.stats);
 }
 
-template <int K, bool kS>
+// kOff: glossy chains, walked to C_i = o_i with the chain's offset normals.
+template <int K, bool kS, bool kOff>
 __global__ void __launch_bounds__(128) k_walk(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
                                               DCtx ctx) {
   Tally t = {};
@@ -121,8 +131,10 @@ __global__ void __launch_bounds__(128) k_walk(const __grid_constant__ DScene S, 
     Chain<K> ch;
     load_chain<K>(c, b, ch);
     Ends e = load_ends(c, b);
+    float2 off[K];
+    if (kOff) load_offsets<K>(c, b, off);
     int it = 0;
-    int st = walk<K, kS>(S, ch, e, P, it, ctx.err, t.c);
+    int st = walk<K, kS>(S, ch, e, P, it, ctx.err, t.c, kOff ? off : nullptr);
     t.walks++;
     t.conv += st == ST_CONVERGED;
     store_chain<K>(c, b, ch);
@@ -200,7 +212,53 @@ __global__ void __launch_bounds__(64) k_contrib64(const __grid_constant__ DScene
   }
 }
 
+// Glossy contribution: admissibility (as for specular chains) and the
+// estimate W of each converged glossy chain in FP64 after an FP64 polish to
+// C = o (mpg_glossy.cuh), written as T; the polished vertices are written
+// back; G and kappa are not formed for glossy chains (0).
 template <int K, bool kS>
+__global__ void __launch_bounds__(64) k_glossy(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+                                               DOut o, DCtx ctx) {
+  Tally t = {};
+  const int n = n_items<K>(w, c);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int b = item<K>(w, c, i);
+    if (b < 0) continue;
+    float T = 0.f;
+    if (c.status[b] == ST_CONVERGED) {
+      Chain<K> ch;
+      load_chain<K>(c, b, ch);
+      Ends e = load_ends(c, b);
+      float2 off[K];
+      load_offsets<K>(c, b, off);
+      Chain64<K> c64;
+      to64<K>(S, ch, c64);
+      double W;
+      if (admissible<K, kS>(S, ch, e, P, ctx.err, t.c) &&
+          glossy_w64<K>(S, c64, e, off, (double)P.roughness, (double)P.tol, (double)P.sing_eps, W)) {
+        T = (float)W;
+        // the polished vertices replace the FP32 ones (the Bernoulli trials
+        // compare against them)
+#pragma unroll
+        for (int v = 0; v < K; ++v) {
+          ch.x[v] = make_float3((float)c64.x[v].x, (float)c64.x[v].y, (float)c64.x[v].z);
+          ch.prim[v] = c64.prim[v];
+          ch.b1[v] = (float)c64.b1[v];
+          ch.b2[v] = (float)c64.b2[v];
+        }
+        store_chain<K>(c, b, ch);
+      }
+    }
+    if (o.G) o.G[b] = 0.f;
+    if (o.kappa) o.kappa[b] = 0.f;
+    o.T[b] = T;
+  }
+  if (kS) flush(t, ctx.stats);
+}
+
+// kOff: glossy chains; every trial is walked with the chain's own offset
+// normals, so N estimates the reciprocal probability given the offsets.
+template <int K, bool kS, bool kOff>
 __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                    DChains c, DWork w, uint2 key, uint64_t offset, mpg_params P,
                                                    DOut o, DCtx ctx) {
@@ -218,7 +276,8 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
       Chain<K> target;
       load_chain<K>(c, b, target);
       Ends e = load_ends(c, b);
-      int q = b / c.spq;
+      float2 off[K];
+      if (kOff) load_offsets<K>(c, b, off);
       uint32_t cell = cell_of(c, b);
       for (int rep = 0; rep < o.repeats; ++rep) {
         bool cap_r = true;
@@ -235,7 +294,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
           if (tau != e.tau) continue;  // a different type sequence cannot be the same solution
           et.tau = tau;
           int it;
-          int st = walk<K, kS>(S, ch, et, P, it, ctx.err, t.c);
+          int st = walk<K, kS>(S, ch, et, P, it, ctx.err, t.c, kOff ? off : nullptr);
           t.walks++;
           t.conv += st == ST_CONVERGED;
           if (st == ST_CONVERGED && same_solution<K>(ch, target, eps2)) {
@@ -335,7 +394,14 @@ void KLaunch<K>::seed(bool stats, const DScene& S, const DGuide* g, const DChain
 template <int K>
 void KLaunch<K>::walk(bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx, int grid,
                       int block, cudaStream_t st) {
-  kern::k_walk<K, true><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+  if (c.offset) kern::k_walk<K, true, true><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+  else kern::k_walk<K, true, false><<<grid, block, 0, st>>>(S, c, w, P, ctx);
+}
+
+template <int K>
+void KLaunch<K>::glossy(const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o, DCtx ctx, int grid,
+                        cudaStream_t st) {
+  kern::k_glossy<K, true><<<grid, 64, 0, st>>>(S, c, w, P, o, ctx);
 }
 
 template <int K>
@@ -349,16 +415,17 @@ void KLaunch<K>::bernoulli(bool stats, const DScene& S, const DGuide* g, const D
                            uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
                            cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  kern::k_bernoulli<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  if (c.offset) kern::k_bernoulli<K, true, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  else kern::k_bernoulli<K, true, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
 }
 
 template <int K>
 int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   const void* fn;
   if (which == 0) fn = (const void*)kern::k_seed<K, true>;
-  else if (which == 1) fn = (const void*)kern::k_walk<K, true>;
+  else if (which == 1) fn = (const void*)kern::k_walk<K, true, false>;
   else if (which == 2) fn = (const void*)kern::k_contrib<K, true>;
-  else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true>;
+  else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true, false>;
   else if (which == 4) fn = (const void*)kern::k_walk_p<K, true>;
   else if (which == 5) fn = (const void*)kern::k_trial_seed<K, true>;
   else if (which == 7) {

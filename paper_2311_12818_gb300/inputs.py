@@ -92,6 +92,7 @@ class Params:
     fp64_tol: float = 1e-4       # FP32 G recomputed in FP64 when its two reciprocal forms differ by more
     bern_repeats: int = 1        # independent Bernoulli estimates averaged per chain
     selective: int = 0           # selective activation: no seeds where the guide's cell is empty
+    roughness: float = 0.0       # Beckmann roughness of glossy chains (their offsets' distribution)
 
 
 @dataclasses.dataclass

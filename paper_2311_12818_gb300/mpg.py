@@ -39,7 +39,7 @@ class mpg_params(C.Structure):
                 ("k_uniform", C.c_int32), ("stall_tol", C.c_float), ("fp64_tol", C.c_float),
                 ("fp64_k", C.c_int32), ("ctas_per_sm", C.c_int32), ("refill_every", C.c_int32),
                 ("trial_sync_rounds", C.c_int32), ("trial_batch", C.c_int32), ("walk_group", C.c_int32),
-                ("bern_repeats", C.c_int32), ("selective", C.c_int32)]
+                ("bern_repeats", C.c_int32), ("selective", C.c_int32), ("roughness", C.c_float)]
 
 SCHEDULE_FIELDS = ["block_threads", "ctas_per_sm", "refill_every", "trial_sync_rounds", "trial_batch", "fp64_k",
                    "walk_group"]
@@ -50,7 +50,7 @@ class mpg_chains(C.Structure):
                 ("xD", C.c_void_p), ("nD", C.c_void_p), ("cell", C.c_void_p), ("xL", C.c_void_p),
                 ("k", C.c_void_p), ("pn", C.c_void_p), ("tau", C.c_void_p), ("x", C.c_void_p),
                 ("surf", C.c_void_p), ("prim", C.c_void_p), ("bary", C.c_void_p), ("pdf", C.c_void_p),
-                ("status", C.c_void_p), ("iters", C.c_void_p), ("chain_cell", C.c_void_p)]
+                ("status", C.c_void_p), ("iters", C.c_void_p), ("chain_cell", C.c_void_p), ("offset", C.c_void_p)]
 
 
 class mpg_guide(C.Structure):
@@ -83,7 +83,8 @@ EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
            "mpg_graph_launch", "mpg_graph_kernels", "mpg_graph_destroy", "mpg_autotune", "mpg_vmf_build",
            "mpg_sample_lengths", "mpg_training_plan", "mpg_stree_build", "mpg_stree_build_host", "mpg_stree_info", "mpg_stree_export",
-           "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy", "mpg_separator_bsdf", "mpg_records_bsdf"]
+           "mpg_stree_records", "mpg_stree_query", "mpg_stree_destroy", "mpg_separator_bsdf", "mpg_records_bsdf",
+           "mpg_sample_offsets"]
 
 _lib = None
 
@@ -115,6 +116,7 @@ def lib():
         L.mpg_sample_seeds.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                        C.POINTER(mpg_params), vp]
         L.mpg_manifold_walk.argtypes = [vp, vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
+        L.mpg_sample_offsets.argtypes = [vp, C.POINTER(mpg_chains), f32, u64, u64, vp, vp]
         L.mpg_manifold_walk_noalloc.argtypes = [vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
         L.mpg_chain_contribution.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                              C.POINTER(mpg_params), vp, vp, vp, vp, vp, vp, vp, vp]
@@ -176,6 +178,7 @@ def params_from(p, walk_mode=WALK_BATCHED, block_threads=0, tau_random=False, k_
                    p.stall_tol, p.fp64_tol)
     P.bern_repeats = int(getattr(p, "bern_repeats", 1))
     P.selective = int(getattr(p, "selective", 0))
+    P.roughness = float(getattr(p, "roughness", 0.0))
     for f, v in schedule.items():
         if f not in SCHEDULE_FIELDS:
             raise TypeError("unknown schedule field %r" % f)
@@ -330,13 +333,15 @@ class Chains:
         self.status = torch.zeros(B, dtype=torch.uint8, device=device)
         self.iters = torch.zeros(B, dtype=torch.uint8, device=device)
         self.chain_cell = None  # [B] int32 per-chain guide cells (a tree's leaves), or None
+        self.offset = None  # [8, 2, B] float32 offset normals of glossy chains, or None (specular)
 
     def struct(self):
         return mpg_chains(self.B, self.Q, self.spq, self.xD.data_ptr(), self.nD.data_ptr(), self.cell.data_ptr(),
                           self.xL.data_ptr(), self.k.data_ptr(), self.pn.data_ptr(), self.tau.data_ptr(),
                           self.x.data_ptr(), self.surf.data_ptr(), self.prim.data_ptr(), self.bary.data_ptr(),
                           self.pdf.data_ptr(), self.status.data_ptr(), self.iters.data_ptr(),
-                          None if self.chain_cell is None else self.chain_cell.data_ptr())
+                          None if self.chain_cell is None else self.chain_cell.data_ptr(),
+                          None if self.offset is None else self.offset.data_ptr())
 
     def aos(self):
         """Host copy in the oracle's array-of-structures layout (tests)."""
@@ -452,6 +457,17 @@ class Graph:
         if getattr(self, "h", None):
             lib().mpg_graph_destroy(self.h)
             self.h = None
+
+
+def mpg_sample_offsets(ctx, chains, alpha, rng_seed, rng_offset=0, out=None, stream=None):
+    """Offset normals of glossy chains (Sec. 5.7) into out ([8, 2, B] float32,
+    allocated when None); returns it (set it as chains.offset to walk them)."""
+    if out is None:
+        out = torch.zeros((MAXK, 2, chains.B), dtype=torch.float32, device=chains.k.device)
+    cs = chains.struct()
+    _check(lib().mpg_sample_offsets(ctx.h, C.byref(cs), float(alpha), rng_seed, rng_offset, _ptr(out),
+                                    _stream(stream)))
+    return out
 
 
 def mpg_manifold_walk(ctx, scene, chains, params, stream=None):
