@@ -469,10 +469,10 @@ def measured_hbm():
 
 
 PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group",
-         "configs")
+         "configs", "glossy_chains")
 # measured by default beside the headline; "mixed" and "adjoint" are covered
 # by the configuration lines (other_configs) and run only with --part
-DEFAULT_PARTS = ("plain", "k3", "k6", "vmf", "repeats", "progressive", "selective", "glossy")
+DEFAULT_PARTS = ("plain", "k3", "k6", "vmf", "repeats", "progressive", "selective", "glossy", "glossy_chains")
 
 
 def other_configs(args, dev, flush, torch, peak_fp32):
@@ -546,6 +546,8 @@ def secondary(args, dev, flush, torch, peak_fp32, parts=DEFAULT_PARTS):
         out["repeated_estimates"] = part_repeats(ctx, dev, flush, torch, stream, steps)
     if "glossy" in parts:
         out["glossy_separator"] = part_glossy(ctx, dev, flush, torch, stream, steps)
+    if "glossy_chains" in parts:
+        out["glossy_chains"] = part_glossy_chains(ctx, dev, flush, torch, stream, steps, F, peak_fp32)
     if "selective" in parts:
         out["selective_activation"] = part_selective(ctx, dev, flush, torch, stream, steps)
     if "progressive" in parts:
@@ -1123,6 +1125,48 @@ def part_glossy(ctx, dev, flush, torch, stream, steps):
     return out
 
 
+def part_glossy_chains(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
+    """Glossy chains (Sec. 5.7) on the glass sphere with a rough surface
+    (Beckmann alpha = 0.05): seeds, offset normals, walks to C = o and the
+    estimate W with Bernoulli trials walked with the chain's offsets (the
+    plain kernels), beside the specular plain step on the same seeds."""
+    import dataclasses
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    alpha = 0.05
+    wl = I.glass_sphere()
+    wl = dataclasses.replace(wl, params=dataclasses.replace(wl.params, roughness=alpha))
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    res = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    off = torch.zeros((8, 2, wl.B), dtype=torch.float32, device=dev)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_PLAIN, k_uniform=2)
+    out = {"workload": "glass_sphere_k2 with rough interfaces (Beckmann alpha %.2f), 1,048,576 chains, p_0 seeds"
+                       % alpha}
+    for name, glossy in (("specular_plain", False), ("glossy", True)):
+        def step(i, glossy=glossy):
+            ch.offset = None
+            mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B)
+            if glossy:
+                mpg.mpg_sample_offsets(ctx, ch, alpha, wl.rng_seed, i * wl.B, out=off)
+                ch.offset = off
+            mpg.mpg_manifold_walk(ctx, sc, ch, P)
+            mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, i * wl.B, out=res)
+        step(0)
+        ctx.sync()
+        ctx.reset_stats()
+        ms = timed_loop(step, steps, 2, flush, stream, torch)
+        st = ctx.stats()
+        per = steps + 2
+        fl = algorithmic_flops(st, F) / per
+        out[name] = {"ms_per_step": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
+                     "contributions_per_step": int((res.T > 0).sum().item()),
+                     "mean_E": float(res.E.double().mean().item()),
+                     "fp32_tflops": fl / (ms * 1e-3) / 1e12, "fp32_frac": fl / (ms * 1e-3) / peak_fp32}
+    ch.offset = None
+    return out
+
+
 def part_selective(ctx, dev, flush, torch, stream, steps):
     """Selective activation (Sec. 5.8) on the benchmark's guided glass-sphere
     step: points whose guide cell holds no weight after the p_0 training pass
@@ -1186,11 +1230,12 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
 
     def variance(a, b):
         return float(((a - b) ** 2).mean().item() / 2)
-    for kind in ("histogram", "vmf", "vmf_tree"):
-        pr = PG.Progressive(ctx, PG.glass_sphere_stages(n=256), total_spp=64, guide=kind, device=dev)
+    for kind in ("histogram", "vmf", "vmf_tree", "vmf_tree_levels"):
+        pr = PG.Progressive(ctx, PG.glass_sphere_stages(n=256), total_spp=64, guide=kind.replace("_levels", ""),
+                            device=dev, tree_method=mpg.STREE_LEVELS if kind.endswith("_levels") else None)
         pr.run(0)
         ctx.sync()
-        if kind == "vmf_tree":  # host tree builds: timed uncaptured, wall clock
+        if kind.startswith("vmf_tree"):  # tree builds synchronise with the host: timed uncaptured
             run = lambda i: pr.run((1 << 44) + (i << 40))  # noqa: E731
             gr = None
         else:
@@ -1209,8 +1254,10 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
                      "ms_per_schedule": ms, "converged_walks_per_s": st["converged"] / per / (ms * 1e-3),
                      "graph_kernels": gr.kernels() if gr is not None else None, "captured": gr is not None,
                      "mean_E": float(a.mean().item()), "per_point_variance_of_E": variance(a, pr.image.double())}
-        if kind == "vmf_tree":
+        if kind.startswith("vmf_tree"):
             out[kind]["leaves_last_training_iteration"] = pr.trees[(len(pr.plan) - 1) % 2].n_leaves
+            out[kind]["tree_build"] = "level by level on the device" if kind.endswith("_levels") else \
+                "depth first on the host (positions gathered on the device)"
         del gr, pr
     wl = I.glass_sphere(n=256, spq=64)
     sc = mpg.Scene(ctx, wl)
@@ -1226,7 +1273,7 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
         imgs.append(res.E.double().clone())
     out["p0_only"] = {"spp": 64, "chains": wl.B, "mean_E": float(imgs[0].mean().item()),
                       "per_point_variance_of_E": variance(imgs[0], imgs[1])}
-    for kind in ("histogram", "vmf", "vmf_tree"):
+    for kind in ("histogram", "vmf", "vmf_tree", "vmf_tree_levels"):
         out[kind]["variance_vs_p0_only"] = out[kind]["per_point_variance_of_E"] / out["p0_only"]["per_point_variance_of_E"]
     return out
 

@@ -14,7 +14,6 @@ __global__ void __launch_bounds__(64) k_adjoint(const __grid_constant__ DScene S
                                                 const float* contrib, const float* dL_dE, float* dL_dtheta,
                                                 int* skipped) {
   constexpr int NU = 2 * K;
-  constexpr int ND = NU + MAXP * K;
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < c.B; b += gridDim.x * blockDim.x) {
     if (c.k[b] != K) continue;
     float cb = contrib[b], Tb = T[b];
@@ -75,43 +74,59 @@ __global__ void __launch_bounds__(64) k_adjoint(const __grid_constant__ DScene S
         D[i][2 + qq] = (g11 * r2 - g12 * r1) * igd;
       }
     }
-    const int nd = NU + m;
-    float dC[NU][ND], dT[ND];
+    // J = dC/du (NU x NU) and dT/du from the u directions, in chunks of
+    // LANES directions whose indices are compile-time constants (so J stays
+    // in registers); no height lanes are seeded in these chunks.
+    constexpr int NCU = (NU + adj::LANES - 1) / adj::LANES;
+    float J[NU][NU], dTu[NU];
     bool ok = true;
-    for (int d0 = 0; d0 < nd && ok; d0 += adj::LANES) {
-      adj::DF C[NU], Tv;
-      ok = adj::chain_eval<K>(S, ch, e, params, m, D, d0, C, Tv);
-      for (int l = 0; l < adj::LANES && ok; ++l) {
-        int d = d0 + l;
-        if (d >= nd) break;
 #pragma unroll
-        for (int r = 0; r < NU; ++r) dC[r][d] = C[r].d[l];
-        dT[d] = Tv.d[l];
+    for (int cu = 0; cu < NCU; ++cu) {
+      adj::DF C[NU], Tv;
+      ok = ok && adj::chain_eval<K>(S, ch, e, params, 0, D, cu * adj::LANES, C, Tv);
+#pragma unroll
+      for (int l = 0; l < adj::LANES; ++l) {
+        const int d = cu * adj::LANES + l;
+        if (d < NU) {
+#pragma unroll
+          for (int r = 0; r < NU; ++r) J[r][d] = C[r].d[l];
+          dTu[d] = Tv.d[l];
+        }
       }
     }
     if (!ok) { atomicAdd(skipped, 1); continue; }
     // J^T lambda = dT/du by the 2x2-block Thomas sweep on the transposed
     // block-tridiagonal system: its diagonal blocks are B_i^T, its sub- and
-    // super-diagonal blocks Cc_{i-1}^T and A_{i+1}^T (J = dC/du, dC[r][d] for d < 2k).
+    // super-diagonal blocks Cc_{i-1}^T and A_{i+1}^T.
     VB vt[K];
     float2 lam2[K][1];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
       const int r = 2 * i;
-      vt[i].B = make_float4(dC[r][r], dC[r + 1][r], dC[r][r + 1], dC[r + 1][r + 1]);
-      if (i > 0) vt[i].A = make_float4(dC[r - 2][r], dC[r - 1][r], dC[r - 2][r + 1], dC[r - 1][r + 1]);
-      if (i < K - 1) vt[i].Cc = make_float4(dC[r + 2][r], dC[r + 3][r], dC[r + 2][r + 1], dC[r + 3][r + 1]);
-      lam2[i][0] = make_float2(dT[r], dT[r + 1]);
+      vt[i].B = make_float4(J[r][r], J[r + 1][r], J[r][r + 1], J[r + 1][r + 1]);
+      if (i > 0) vt[i].A = make_float4(J[r - 2][r], J[r - 1][r], J[r - 2][r + 1], J[r - 1][r + 1]);
+      if (i < K - 1) vt[i].Cc = make_float4(J[r + 2][r], J[r + 3][r], J[r + 2][r + 1], J[r + 3][r + 1]);
+      lam2[i][0] = make_float2(dTu[r], dTu[r + 1]);
     }
     if (!thomas<K, 1>(vt, lam2, 0.0f)) { atomicAdd(skipped, 1); continue; }
     float lam[NU];
 #pragma unroll
     for (int i = 0; i < K; ++i) { lam[2 * i] = lam2[i][0].x; lam[2 * i + 1] = lam2[i][0].y; }
-    for (int p = 0; p < m; ++p) {
-      float g = dT[NU + p];
+    // dT/dtheta_p - lambda^T dC/dtheta_p for the heights, LANES at a time,
+    // scattered as soon as they are formed (the values of every chunk are
+    // those of the u chunks, so a chain that passed them passes these too)
+    for (int p0 = 0; p0 < m; p0 += adj::LANES) {
+      adj::DF C[NU], Tv;
+      if (!adj::chain_eval<K>(S, ch, e, params, m, D, NU + p0, C, Tv)) break;
 #pragma unroll
-      for (int r = 0; r < NU; ++r) g -= lam[r] * dC[r][NU + p];
-      atomicAdd(dL_dtheta + params[p], scale * g);
+      for (int l = 0; l < adj::LANES; ++l) {
+        const int p = p0 + l;
+        if (p >= m) break;
+        float g = Tv.d[l];
+#pragma unroll
+        for (int r = 0; r < NU; ++r) g -= lam[r] * C[r].d[l];
+        atomicAdd(dL_dtheta + params[p], scale * g);
+      }
     }
   }
 }

@@ -15,7 +15,11 @@
 namespace mpg {
 namespace adj {
 
-constexpr int LANES = 4;
+// Directions carried per dual evaluation.  Two keep a chain's dual state in
+// registers (at four the frames spilled: 346 MB of local-memory writes per
+// launch on the water scene against 35 MB at two), at the price of more
+// evaluations per chain.
+constexpr int LANES = 2;
 
 struct DF {
   float v;
@@ -192,7 +196,12 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
     int id = j * hf.nx + i;
     DF h = cst(__ldg(hf.P + id).z);
     for (int p = 0; p < m; ++p)
-      if (params[p] == id) { int l = lane_of(2 * K + p); if (l >= 0) h.d[l] = 1.0f; }
+      if (params[p] == id) {
+        const int l = lane_of(2 * K + p);
+#pragma unroll
+        for (int q = 0; q < LANES; ++q)  // a constant index keeps the dual in registers
+          if (q == l) h.d[q] = 1.0f;
+      }
     return h;
   };
   FrameD f[K + 2];
@@ -213,8 +222,11 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
     }
     DF u0 = cst(0.f), u1 = cst(0.f);
     int l0 = lane_of(2 * i), l1 = lane_of(2 * i + 1);
-    if (l0 >= 0) u0.d[l0] = 1.0f;
-    if (l1 >= 0) u1.d[l1] = 1.0f;
+#pragma unroll
+    for (int q = 0; q < LANES; ++q) {
+      if (q == l0) u0.d[q] = 1.0f;
+      if (q == l1) u1.d[q] = 1.0f;
+    }
     DF b1 = cst(ch.b1[i]) + u0 * D[i][0] + u1 * D[i][1];
     DF b2 = cst(ch.b2[i]) + u0 * D[i][2] + u1 * D[i][3];
     f[i + 1] = frame_tri(P[0], P[1], P[2], N[0], N[1], N[2], b1, b2);
@@ -276,8 +288,16 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
       R[i][1][c] = Bi[i][2] * r0 + Bi[i][3] * r1;
     }
   }
-  int vi = point ? K : 1;
-  V w = f[vi].p - (point ? f[K + 1].p : f[0].p);
+  // the vertex whose motion moves the measured direction: x_K (point light)
+  // or x_1 (area light); selected by value so that every array index stays a
+  // compile-time constant (a runtime index would move the arrays to memory)
+  const V vp = point ? f[K].p : f[1].p, vdu = point ? f[K].dpdu : f[1].dpdu, vdv = point ? f[K].dpdv : f[1].dpdv;
+  DF Ry[2][2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) Ry[r][c] = point ? R[K - 1][r][c] : R[0][r][c];
+  V w = vp - (point ? f[K + 1].p : f[0].p);
   DF dist = norm(w);
   w = w * (cst(1.0f) / dist);
   V a, b;
@@ -285,7 +305,7 @@ __device__ bool chain_eval(const DScene& S, const Chain<K>& ch, const Ends& e, c
   DF M[2][2];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
-    V dx = f[vi].dpdu * R[vi - 1][0][c] + f[vi].dpdv * R[vi - 1][1][c];
+    V dx = vdu * Ry[0][c] + vdv * Ry[1][c];
     V dw = (dx - w * dot(w, dx)) * (cst(1.0f) / dist);
     M[0][c] = dot(a, dw);
     M[1][c] = dot(b, dw);

@@ -888,7 +888,7 @@ mpg_status mpg_chain_contribution(mpg_ctx* ctx, const mpg_scene* sc, const mpg_g
       }
       launch_contrib(K, ctx->stats_on, sc->S, c, plan.w, *P, oK, dcc, grid_of(ctx, P, 2, K, block, c.B, true), block,
                      s2);
-      launch_contrib64(K, sc->S, c, *P, oK, ctx->sms * 2, s2);
+      launch_contrib64(K, sc->S, c, *P, oK, ctx->sms * 4, s2);
     });
     if (!batched) {
       timed(ctx, MPG_KERNEL_BERNOULLI, s2, 1, [&] {

@@ -852,13 +852,58 @@ static __device__ __noinline__ float vmf_mix_pdf(const DGuide& g, VmfRange r, ui
   return sum / (float)r.total;
 }
 
+// The vMF part of a seed's density left to the caller: the lobes of group kt
+// in range vr, evaluated at w (summed by a whole warp, vmf_sum_warp).
+struct VmfDeferred {
+  bool need;
+  VmfRange vr;
+  uint32_t kt;
+  float3 w;
+};
+
+// Sum over the lobes of each lane's group at its direction, for the lanes
+// with `need`, taken by the whole warp one lane at a time: consecutive lanes
+// read consecutive lobes (coalesced 16-byte loads) and a butterfly reduction
+// adds the partial sums.  Every lane of the warp must call it; returns the
+// lane's sum divided by the cell's total weight (0 without `need`).
+__device__ __forceinline__ float vmf_sum_warp(const DGuide& g, bool need, const VmfDeferred& d) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  uint32_t a = 0, b = 0;
+  if (need) {
+    a = lobe_bound(g, d.vr.a, d.vr.b, d.kt);
+    b = lobe_bound(g, a, d.vr.b, d.kt + 1);
+  }
+  float mine = 0.0f;
+  unsigned m = __ballot_sync(FULL, need);
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const uint32_t sa = __shfl_sync(FULL, a, src), sb = __shfl_sync(FULL, b, src);
+    const float3 w = make_float3(__shfl_sync(FULL, d.w.x, src), __shfl_sync(FULL, d.w.y, src),
+                                 __shfl_sync(FULL, d.w.z, src));
+    float part = 0.0f;
+    for (uint32_t i = sa + (uint32_t)lane; i < sb; i += 32u) {
+      const float4 L = __ldg(g.lobe + i);
+      const float3 dv = w - make_float3(L.x, L.y, L.z);
+      part = fmaf(__ldg(g.lobe_coef + i), expf(-0.5f * L.w * dot(dv, dv)), part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    if (lane == src) mine = part;
+  }
+  return need ? mine / (float)d.vr.total : 0.0f;
+}
+
 // Draw seed `trial` of chain idx and deduce its vertices.  Returns validity;
-// fills ch (first k vertices), tau and pdf.
+// fills ch (first k vertices), tau and pdf.  With `defer` (vMF guide), the sum
+// over the lobes is not formed here: pdf gets the p_0 part alone and defer
+// what the caller needs to add (1 - alpha) vmf_sum_warp(...) to it.
 template <int K, bool kStats>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
                           Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
-                          bool want_pdf = true, bool need_tau_in = false) {
+                          bool want_pdf = true, bool need_tau_in = false, VmfDeferred* defer = nullptr) {
   if (kStats) cnt.seeds++;
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
@@ -955,7 +1000,15 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     // joint density of (w, tau) given n: p_0 draws the types uniformly
     float p0 = p0_pdf(S, e.xD, w);
     if (tau_random) p0 = ldexpf(p0, -K);
-    pdf = use_guide ? P.alpha * p0 + (1.0f - P.alpha) * vmf_mix_pdf(*g, vr, ((uint32_t)K << 8) | tau, w) : p0;
+    if (defer && use_guide) {
+      defer->need = true;
+      defer->vr = vr;
+      defer->kt = ((uint32_t)K << 8) | tau;
+      defer->w = w;
+      pdf = P.alpha * p0;
+    } else {
+      pdf = use_guide ? P.alpha * p0 + (1.0f - P.alpha) * vmf_mix_pdf(*g, vr, ((uint32_t)K << 8) | tau, w) : p0;
+    }
   } else if (use_guide) {
     float p0 = p0_pdf(S, e.xD, w);
     int bin = guide_bin(*g, w);

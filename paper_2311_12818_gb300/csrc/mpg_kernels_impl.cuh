@@ -93,16 +93,30 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
   Tally t = {};
   const int n = n_items<K>(w, c);
   offset = rng_offset(offset, ctx);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int b = item<K>(w, c, i);
-    if (b < 0) continue;
-    Ends e = load_ends(c, b);
+  // with a vMF guide the lobe sum of each seed's density is taken by the whole
+  // warp (vmf_sum_warp), so the loop runs warp-uniformly
+  const bool vmf = has_guide && g.kind == MPG_GUIDE_VMF;
+  const int lane = threadIdx.x & 31;
+  for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += gridDim.x * blockDim.x) {
+    const int i = base + lane;
+    const int b = i < n ? item<K>(w, c, i) : -1;
+    VmfDeferred df;
+    df.need = false;
     Chain<K> ch;
-    uint32_t tau;
-    float pdf;
-    int q = b / c.spq;
-    bool ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0,
-                               key, (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c);
+    uint32_t tau = 0;
+    float pdf = 0.0f;
+    bool ok = false;
+    if (b >= 0) {
+      Ends e = load_ends(c, b);
+      ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0, key,
+                            (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c, true, false,
+                            vmf ? &df : nullptr);
+    }
+    if (vmf) {
+      const float s = vmf_sum_warp(g, ok && df.need, df);
+      if (ok && df.need) pdf += (1.0f - P.alpha) * s;
+    }
+    if (b < 0) continue;
     if (!ok) {
 #pragma unroll
       for (int v = 0; v < K; ++v) {

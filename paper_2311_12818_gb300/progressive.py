@@ -27,11 +27,14 @@ class Progressive:
     is the rendering stage)."""
 
     def __init__(self, ctx, make_workload, total_spp, first_spp=1, train_fraction=0.3, guide="histogram",
-                 train_repeats=1, render_repeats=1, device="cuda"):
+                 train_repeats=1, render_repeats=1, device="cuda", tree_method=None):
         """guide: 'histogram' or 'vmf' (one guide cell per receiver cell), or
         'vmf_tree' (the vMF mixture over the leaves of a spatial tree of each
-        iteration's samples, Sec. 5.6; its host build is synchronous, so that
-        schedule is not recorded as a graph)."""
+        iteration's samples, Sec. 5.6; its build is synchronous -- the host
+        decides the tree's nodes -- so that schedule is not recorded as a
+        graph).  tree_method: mpg.STREE_RECURSIVE (depth first on the host,
+        the default) or mpg.STREE_LEVELS (level by level on the device)."""
+        self.tree_method = mpg.STREE_RECURSIVE if tree_method is None else tree_method
         if guide not in ("histogram", "vmf", "vmf_tree"):
             raise ValueError("guide must be 'histogram', 'vmf' or 'vmf_tree'")
         self.ctx, self.kind = ctx, guide
@@ -92,7 +95,7 @@ class Progressive:
                 mpg.mpg_vmf_build(ctx, nxt, rec[0], rec[1], rec[2], rec[3], rec[4], R=wl.B, R_dev=rec[6],
                                   weight_shift=wl.params.weight_shift, stream=stream)
             else:
-                tree = mpg.STree(ctx, ch, rec[5], R=wl.B, R_dev=rec[6], stream=stream)
+                tree = mpg.STree(ctx, ch, rec[5], R=wl.B, R_dev=rec[6], method=self.tree_method, stream=stream)
                 leaf_rec = tree.records(rec, wl.B, stream=stream)
                 nxt = mpg.VmfGuide(tree.n_leaves, max(tree.n_members, 1))
                 mpg.mpg_vmf_build(ctx, nxt, *leaf_rec[:5], R=leaf_rec[0].numel(), R_dev=leaf_rec[5],
@@ -108,7 +111,7 @@ class Progressive:
     def capture(self, offset=0, advance=0):
         """The whole schedule as one graph (run() once first to size the buffers)."""
         if self.kind == "vmf_tree":
-            raise ValueError("the tree's host build cannot be recorded: run the schedule uncaptured")
+            raise ValueError("the tree build synchronises with the host: run the schedule uncaptured")
         g = mpg.Graph(self.ctx, rng_advance=advance)
         with g:
             self.run(offset, stream=g.stream)
