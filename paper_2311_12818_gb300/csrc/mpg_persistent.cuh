@@ -53,12 +53,16 @@ __device__ __forceinline__ void walk_begin(WalkLane<K>& w) {
 }
 
 // One pass of the walk: Jacobian and Newton direction when the previous
-// attempt was accepted (or at the start), then one reprojection attempt.
-// Same decisions, in the same order, as walk<K>().  In a pass without the
-// evaluation phase (eval_phase false) a lane that needs the Jacobian waits.
+// attempt was accepted (or at the start), then up to `attempts` reprojection
+// attempts of the line search (one per pass while the work queue still holds
+// items; more once it is empty, when the warp's other lanes are mostly idle
+// and a walk between step halvings would otherwise take one pass per
+// halving).  Same decisions, in the same order, as walk<K>().  In a pass
+// without the evaluation phase (eval_phase false) a lane that needs the
+// Jacobian waits.
 template <int K, bool kS>
 __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const mpg_params& P, Counters& cnt,
-                                         bool eval_phase) {
+                                         bool eval_phase, int attempts = 1) {
   if (w.need_eval) {
     if (!eval_phase) return RUNNING;
     VB vb[K];
@@ -76,20 +80,25 @@ __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const 
     w.hv = 0;
     w.need_eval = false;
   }
-  Chain<K> cand;
-  float cc2;
-  if (propose<K>(S, w.ch, w.d, w.beta, cand) && eval_c<K, kS>(S, cand, w.e, cc2, cnt) &&
-      cc2 < w.cn2) {
-    w.ch = cand;
-    w.it++;
-    w.need_eval = true;
-    return RUNNING;
+  for (int a = 0; a < attempts; ++a) {
+    Chain<K> cand;
+    float cc2;
+    if (propose<K>(S, w.ch, w.d, w.beta, cand) && eval_c<K, kS>(S, cand, w.e, cc2, cnt) &&
+        cc2 < w.cn2) {
+      w.ch = cand;
+      w.it++;
+      w.need_eval = true;
+      return RUNNING;
+    }
+    w.hv++;
+    w.beta *= 0.5f;
+    if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   }
-  w.hv++;
-  w.beta *= 0.5f;
-  if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   return RUNNING;
 }
+
+// Line-search attempts per pass once a launch's work queue is empty.
+constexpr int TAIL_ATTEMPTS = 4;
 
 // Phase vote of a warp: the Jacobian evaluation (about four times the work of
 // a line-search attempt) runs when at least as many active lanes need it as
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid
     if (!any && done) break;
     const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b >= 0) {
-      int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase);
+      int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, done ? TAIL_ATTEMPTS : 1);
       if (st != RUNNING) {
         t.walks++;
         t.conv += st == ST_CONVERGED;
@@ -503,7 +512,7 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
     if (!any && done) break;
     const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b < 0) continue;
-    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase);
+    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, done ? TAIL_ATTEMPTS : 1);
     if (st != RUNNING) {
       t.walks++;
       // converged walks of the trial sequence (t <= N) are counted by the
