@@ -218,7 +218,7 @@ struct GroupLane {
 template <int K, int G, bool kS>
 __device__ __forceinline__ int walk_pass_g(const DScene& S, GroupLane<K>& w, const mpg_params& P, Counters& cnt,
                                            bool eval_phase, unsigned gmask, int j, float2* sC, float4* sA, float4* sB,
-                                           float4* sCc) {
+                                           float4* sCc, int attempts = 1) {
   const bool own = j < K;
   if (w.need_eval) {
     if (!eval_phase) return RUNNING;
@@ -261,42 +261,46 @@ __device__ __forceinline__ int walk_pass_g(const DScene& S, GroupLane<K>& w, con
     w.hv = 0;
     w.need_eval = false;
   }
-  float3 cx = w.x;
-  int cprim = w.prim;
-  float cb1 = w.b1, cb2 = w.b2;
-  bool ok = !own || reproject(S, w.surf, w.x + w.d * w.beta, cx, cprim, cb1, cb2);
-  bool accept = false;
-  if (__all_sync(gmask, ok)) {
-    float3 xp = shfl_up3(gmask, cx, G), xn = shfl_down3(gmask, cx, G);
-    if (j == 0) xp = w.e.xD;
-    if (j == K - 1) xn = w.e.xL;
-    float2 C = make_float2(0.f, 0.f);
-    bool okc = true;
-    if (own) {
-      float3 n = vertex_normal(S, w.surf, cprim, cx, cb1, cb2);
-      okc = vertex_c(xp, cx, xn, n, S.s[w.surf], (w.e.tau >> j) & 1u, C);
-    }
-    if (__all_sync(gmask, okc)) {
-      if (kS && j == 0) cnt.c_evals += K;
-      const int leader = (threadIdx.x & 31) & ~(G - 1);
-      float cc2 = 0.0f;
-#pragma unroll
-      for (int i = 0; i < K; ++i) {
-        float cxv = __shfl_sync(gmask, C.x, leader + i), cyv = __shfl_sync(gmask, C.y, leader + i);
-        cc2 = fmaf(cxv, cxv, fmaf(cyv, cyv, cc2));
+  // Every decision below is the same in all lanes of the group, so the
+  // attempts loop keeps the group converged for its shuffles.
+  for (int a = 0; a < attempts; ++a) {
+    float3 cx = w.x;
+    int cprim = w.prim;
+    float cb1 = w.b1, cb2 = w.b2;
+    bool ok = !own || reproject(S, w.surf, w.x + w.d * w.beta, cx, cprim, cb1, cb2);
+    bool accept = false;
+    if (__all_sync(gmask, ok)) {
+      float3 xp = shfl_up3(gmask, cx, G), xn = shfl_down3(gmask, cx, G);
+      if (j == 0) xp = w.e.xD;
+      if (j == K - 1) xn = w.e.xL;
+      float2 C = make_float2(0.f, 0.f);
+      bool okc = true;
+      if (own) {
+        float3 n = vertex_normal(S, w.surf, cprim, cx, cb1, cb2);
+        okc = vertex_c(xp, cx, xn, n, S.s[w.surf], (w.e.tau >> j) & 1u, C);
       }
-      accept = cc2 < w.cn2;
+      if (__all_sync(gmask, okc)) {
+        if (kS && j == 0) cnt.c_evals += K;
+        const int leader = (threadIdx.x & 31) & ~(G - 1);
+        float cc2 = 0.0f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          float cxv = __shfl_sync(gmask, C.x, leader + i), cyv = __shfl_sync(gmask, C.y, leader + i);
+          cc2 = fmaf(cxv, cxv, fmaf(cyv, cyv, cc2));
+        }
+        accept = cc2 < w.cn2;
+      }
     }
+    if (accept) {
+      w.x = cx; w.prim = cprim; w.b1 = cb1; w.b2 = cb2;
+      w.it++;
+      w.need_eval = true;
+      return RUNNING;
+    }
+    w.hv++;
+    w.beta *= 0.5f;
+    if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   }
-  if (accept) {
-    w.x = cx; w.prim = cprim; w.b1 = cb1; w.b2 = cb2;
-    w.it++;
-    w.need_eval = true;
-    return RUNNING;
-  }
-  w.hv++;
-  w.beta *= 0.5f;
-  if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
   return RUNNING;
 }
 
@@ -347,7 +351,8 @@ __global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S
     if (!any && done) break;
     const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
     if (b >= 0) {
-      int st = walk_pass_g<K, G, kS>(S, L, P, t.c, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp], sCc[grp]);
+      int st = walk_pass_g<K, G, kS>(S, L, P, t.c, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp], sCc[grp],
+                                     done ? TAIL_ATTEMPTS : 1);
       if (st != RUNNING) {
         if (j < K) {
           c.x[(3 * j + 0) * Bz + b] = L.x.x;
@@ -463,11 +468,80 @@ __global__ void __launch_bounds__(256) k_trial_check(const __grid_constant__ DSc
 // items above a chain's best success so far are skipped: the speculative work
 // is bounded by the items in flight, not by TB.
 // ---------------------------------------------------------------------------
+// Item filter of the parallel rounds.  Item i is trial tt of chain bb (the
+// trial-major order above).  It is dropped when tt is past the trial cap or
+// not below the chain's best success so far, and -- for seeds whose types are
+// drawn at random from the first counter block (p_0 and histogram guides) --
+// when that draw gives a type sequence other than the chain's: draw_seed
+// fails such a trial before any ray is cast, so it never needs a walking lane.
+struct BernFilter {
+  const int* over;
+  int nl, t0;
+  unsigned* nbest;
+  uint64_t offset;
+  uint32_t trial_base;
+  bool types;  // the type test applies (random types, no vMF guide)
+};
+
+template <int K, bool kS>
+__device__ __forceinline__ bool bern_keep(const DChains& c, const BernFilter& f, uint2 key, const mpg_params& P,
+                                          long long i, Tally& t) {
+  const int bb = f.over[i % f.nl];
+  const int tt = f.t0 + (int)(i / f.nl);
+  if (tt > P.max_trials || (unsigned)tt >= *((volatile unsigned*)(f.nbest + bb))) return false;
+  t.trials++;
+  if (!f.types) return true;
+  const uint64_t idx = (uint64_t)bb + f.offset;
+  const uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), (uint32_t)tt | f.trial_base, 1u), key);
+  if ((r1.y & ((1u << K) - 1u)) == (uint32_t)c.tau[bb]) return true;
+  if (kS) t.c.seeds++;  // the seed was drawn (its types) and failed
+  return false;
+}
+
+// Filter sweeps per pass at most (each takes one item per free pool slot).
+constexpr int POOL_SWEEPS = 8;
+
+// Warp-collective take from a per-warp pool of filtered items (pool[0..np)
+// in shared memory, np warp-uniform).  While the pool holds fewer items than
+// lanes asking (`want`), every lane with a free slot takes one raw item from
+// the queue and filters it, and the survivors are appended; the asking lanes
+// then take items from the top of the pool.  Returns the lane's item or -1.
+// The pool only changes which lane walks which trial and when: the outputs
+// (the smallest successful trial of each chain, and the walks below it) are
+// the same.
+template <int K, bool kS>
+__device__ __forceinline__ long long bern_pool_take(bool want, long long* pool, int& np,
+                                                    unsigned long long* queue64, long long n, bool& done,
+                                                    const DChains& c, const BernFilter& f, uint2 key,
+                                                    const mpg_params& P, Tally& t) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned need = __ballot_sync(FULL, want);
+  const int nneed = __popc(need);
+  for (int s = 0; s < POOL_SWEEPS && np < nneed && !done; ++s) {
+    long long i = take_item64(lane >= np, queue64, n, done);
+    const bool keep = i >= 0 && bern_keep<K, kS>(c, f, key, P, i, t);
+    const unsigned km = __ballot_sync(FULL, keep);
+    if (keep) pool[np + __popc(km & lt)] = i;  // slots np.. (at most 32 - np survivors)
+    np += __popc(km);
+  }
+  __syncwarp();
+  const int give = min(nneed, np);
+  const int rank = __popc(need & lt);
+  long long mine = -1;
+  if (want && rank < give) mine = pool[np - 1 - rank];
+  np -= give;
+  __syncwarp();  // the slots handed out are rewritten by the next sweep
+  return mine;
+}
+
 template <int K, bool kS>
 __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                     DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
                                                     int* queue, const int* list, const int* n_list, const int* base,
                                                     unsigned* nbest, int t0, int TB, DPairs pr) {
+  __shared__ long long pools[4][32];
   Tally t = {};
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
   const int* over = list + *base;
@@ -475,6 +549,10 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
   const long long n = (long long)nl * TB;
   unsigned long long* queue64 = reinterpret_cast<unsigned long long*>(queue);
   offset = rng_offset(offset, ctx);
+  const BernFilter f{over, nl, t0, nbest, offset, ctx.trial_base,
+                     P.tau_random != 0 && !(has_guide && g.kind == MPG_GUIDE_VMF)};
+  long long* pool = pools[threadIdx.x >> 5];
+  int np = 0;
   const int refill = P.refill_every > 1 ? P.refill_every : 1;
   int pass = 0;
   WalkLane<K> L;
@@ -486,13 +564,13 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
   while (true) {
     // idle lanes refill every `refill` passes, or at once when the whole warp is idle
     bool idle_warp = __all_sync(FULL, b < 0);
-    long long i = take_item64(b < 0 && (idle_warp || pass % refill == 0), queue64, n, done);
+    long long i = bern_pool_take<K, kS>(b < 0 && (idle_warp || pass % refill == 0), pool, np, queue64, n, done, c,
+                                        f, key, P, t);
     ++pass;
     if (i >= 0) {
       int bb = over[i % nl];
       int tt = t0 + (int)(i / nl);
-      if (tt <= P.max_trials && (unsigned)tt < *((volatile unsigned*)(nbest + bb))) {
-        t.trials++;
+      if ((unsigned)tt < *((volatile unsigned*)(nbest + bb))) {  // no success below it meanwhile
         Ends e = load_ends(c, bb);
         uint32_t tau;
         float pdf;
@@ -508,11 +586,12 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
         }
       }
     }
+    const bool tail = done && np == 0;
     bool any = __any_sync(FULL, b >= 0);
-    if (!any && done) break;
+    if (!any && tail) break;
     const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b < 0) continue;
-    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, done ? TAIL_ATTEMPTS : 1);
+    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, tail ? TAIL_ATTEMPTS : 1);
     if (st != RUNNING) {
       t.walks++;
       // converged walks of the trial sequence (t <= N) are counted by the
@@ -547,6 +626,7 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
   constexpr int NG = 128 / G;
   __shared__ float2 sC[NG][K];
   __shared__ float4 sA[NG][K], sB[NG][K], sCc[NG][K];
+  __shared__ long long pools[4][32];
   Tally t = {};
   Counters dummy = {};
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
@@ -555,6 +635,10 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
   const long long n = (long long)nl * TB;
   unsigned long long* queue64 = reinterpret_cast<unsigned long long*>(queue);
   offset = rng_offset(offset, ctx);
+  const BernFilter f{over, nl, t0, nbest, offset, ctx.trial_base,
+                     P.tau_random != 0 && !(has_guide && g.kind == MPG_GUIDE_VMF)};
+  long long* pool = pools[threadIdx.x >> 5];
+  int np = 0;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, j = threadIdx.x % G, grp = threadIdx.x / G;
   const int leader = lane & ~(G - 1);
@@ -570,7 +654,8 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
   int pass = 0;
   while (true) {
     bool idle_warp = __all_sync(FULL, b < 0);
-    long long i = take_item64(j == 0 && b < 0 && (idle_warp || pass % refill == 0), queue64, n, done);
+    long long i = bern_pool_take<K, kS>(j == 0 && b < 0 && (idle_warp || pass % refill == 0), pool, np, queue64, n,
+                                        done, c, f, key, P, t);
     i = __shfl_sync(FULL, i, leader);
     ++pass;
     // The leader alone reads the chain's best success (it changes under other
@@ -581,14 +666,13 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
     if (i >= 0) {
       bb = over[i % nl];
       tt = t0 + (int)(i / nl);
-      if (j == 0) take = tt <= P.max_trials && (unsigned)tt < *((volatile unsigned*)(nbest + bb));
+      if (j == 0) take = (unsigned)tt < *((volatile unsigned*)(nbest + bb));  // no success below it meanwhile
     }
     take = __shfl_sync(FULL, take ? 1 : 0, leader) != 0;
     bool drawn = false;
     Chain<K> ch;
     Ends e;
     if (take) {
-      if (j == 0) t.trials++;
       e = load_ends(c, bb);
       uint32_t cell = cell_of(c, bb);
       uint32_t tau;
@@ -615,12 +699,13 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
       L.beta = 1.0f;
       L.need_eval = true;
     }
+    const bool tail = done && np == 0;
     bool any = __any_sync(FULL, b >= 0);
-    if (!any && done) break;
+    if (!any && tail) break;
     const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
     if (b < 0) continue;
     int st = walk_pass_g<K, G, kS>(S, L, P, j == 0 ? t.c : dummy, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp],
-                                   sCc[grp]);
+                                   sCc[grp], tail ? TAIL_ATTEMPTS : 1);
     if (st != RUNNING) {
       if (j == 0) t.walks++;
       if (st == ST_CONVERGED) {
