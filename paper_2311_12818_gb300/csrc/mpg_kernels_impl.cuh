@@ -194,12 +194,18 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
 
 // FP64 polish, G and kappa of the chains k_contrib queued (rare: near caustic
 // folds, grazing transmission, stalled walks, k >= 6).  Writes back the
-// polished vertices and the final G, kappa and T.
+// polished vertices and the final G, kappa and T.  The queue is short (a few
+// thousand chains) and each chain is a long serial FP64 computation with its
+// arrays in local memory, so warps of 32 consecutive chains are dealt to the
+// blocks in turn (the first warp of every block before any second warp): the
+// work spreads over all SMs instead of filling the first few blocks.
 template <int K>
 __global__ void __launch_bounds__(64) k_contrib64(const __grid_constant__ DScene S, DChains c, mpg_params P, DOut o) {
   const int n = *o.fp64_count;
   const int* list = o.fp64_list + *o.fp64_base;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = ((long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x) * 32 + (threadIdx.x & 31);
+  for (long long j = first; j < n; j += stride) {
     int b = list[j];
     Chain<K> ch;
     load_chain<K>(c, b, ch);

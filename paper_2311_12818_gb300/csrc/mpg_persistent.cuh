@@ -1,8 +1,9 @@
 // Persistent work-queue kernels of the batched mode.
 //
 // A thread keeps one chain (or one Bernoulli trial) in registers and advances
-// it by one line-search attempt per pass; every pass re-evaluates only the
-// lanes whose previous attempt was accepted.  A lane whose walk ends takes
+// it by one line-search attempt per pass; each attempt evaluates constraint
+// and Jacobian blocks at its candidate, so every lane of a warp runs the same
+// instructions in a pass whatever state its walk is in.  A lane whose walk ends takes
 // the next item of the launch's queue in the same pass (warp-aggregated
 // atomic), so a warp stays full until the queue is empty instead of waiting
 // for its slowest chain.  All loops are bounded: each pass either consumes a
@@ -21,7 +22,7 @@ constexpr int RUNNING = -1;
 // compiled for: the register need grows with K (about 128 registers at
 // K <= 2, 168 at K <= 4, the 255 maximum beyond), and a tighter bound spills.
 template <int K>
-constexpr int walk_min_ctas() { return K <= 2 ? 5 : K <= 4 ? 3 : 2; }
+constexpr int walk_min_ctas() { return K <= 2 ? 4 : K <= 4 ? 3 : 2; }
 
 // float3 from the previous / next lane of a segment of `width` lanes (the lane
 // itself at the segment's start / end); `mask` holds the segment's lanes.
@@ -41,7 +42,7 @@ struct WalkLane {
   float3 d[K];  // Newton step of each vertex (tangent vector), kept through the halvings
   float cn2, cmax, beta;
   int it, hv;
-  bool need_eval;
+  bool need_eval;  // the walk has not evaluated its seed yet
 };
 
 template <int K>
@@ -52,44 +53,51 @@ __device__ __forceinline__ void walk_begin(WalkLane<K>& w) {
   w.need_eval = true;
 }
 
-// One pass of the walk: Jacobian and Newton direction when the previous
-// attempt was accepted (or at the start), then up to `attempts` reprojection
-// attempts of the line search (one per pass while the work queue still holds
-// items; more once it is empty, when the warp's other lanes are mostly idle
-// and a walk between step halvings would otherwise take one pass per
-// halving).  Same decisions, in the same order, as walk<K>().  In a pass
-// without the evaluation phase (eval_phase false) a lane that needs the
-// Jacobian waits.
+// One pass of the walk in fused form: every attempt evaluates the constraint
+// together with its Jacobian blocks at the candidate, so that each pass runs
+// the same instructions in every lane (a two-phase pass, Jacobian after an
+// accepted step and constraint-only line-search attempts otherwise, leaves the
+// lanes in the other phase waiting).  The first pass of a walk evaluates the seed itself; a candidate is
+// accepted when its |C|^2 is below the current one, and the blocks already
+// evaluated there give the next Newton direction.  The constraint values are
+// those of the two-phase form (vertex_c and vertex_blocks form C with the same
+// operations), so the decisions are the same as walk<K>()'s.  A rejected
+// candidate costs a full evaluation instead of a constraint-only one; the
+// counters record only the constraint evaluation it needed.
 template <int K, bool kS>
-__device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const mpg_params& P, Counters& cnt,
-                                         bool eval_phase, int attempts = 1) {
-  if (w.need_eval) {
-    if (!eval_phase) return RUNNING;
+__device__ __forceinline__ int walk_pass_fused(const DScene& S, WalkLane<K>& w, const mpg_params& P, Counters& cnt,
+                                               int attempts = 1) {
+  for (int a = 0; a < attempts; ++a) {
+    const bool first = w.need_eval;
+    Chain<K> cand;
+    bool ok = true;
+    if (first) cand = w.ch;
+    else ok = propose<K>(S, w.ch, w.d, w.beta, cand);
     VB vb[K];
     float3 tu[K], tv[K];
-    if (!eval_full<K, kS>(S, w.ch, w.e, vb, tu, tv, w.cn2, w.cmax, false, cnt)) return ST_FAILED;
-    if (w.cmax < P.tol) return ST_CONVERGED;
-    if (w.it >= P.max_iter) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
-    float2 du[K][1];
-#pragma unroll
-    for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
-    if (kS) { cnt.newton++; cnt.rows += K; }
-    if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
-    step_vectors<K>(tu, tv, du, w.d);
-    w.beta = 1.0f;
-    w.hv = 0;
-    w.need_eval = false;
-  }
-  for (int a = 0; a < attempts; ++a) {
-    Chain<K> cand;
-    float cc2;
-    if (propose<K>(S, w.ch, w.d, w.beta, cand) && eval_c<K, kS>(S, cand, w.e, cc2, cnt) &&
-        cc2 < w.cn2) {
+    float c2 = 0.0f, cm = 0.0f;
+    ok = ok && eval_full<K, false>(S, cand, w.e, vb, tu, tv, c2, cm, false, cnt);
+    if (ok && (first || c2 < w.cn2)) {
+      if (kS) cnt.full_evals += K;
       w.ch = cand;
-      w.it++;
-      w.need_eval = true;
+      w.it += first ? 0 : 1;
+      w.need_eval = false;
+      w.cn2 = c2;
+      w.cmax = cm;
+      if (cm < P.tol) return ST_CONVERGED;
+      if (w.it >= P.max_iter) return cm < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
+      float2 du[K][1];
+#pragma unroll
+      for (int i = 0; i < K; ++i) du[i][0] = make_float2(-vb[i].C.x, -vb[i].C.y);
+      if (kS) { cnt.newton++; cnt.rows += K; }
+      if (!thomas<K, 1>(vb, du, P.sing_eps)) return ST_FAILED;
+      step_vectors<K>(tu, tv, du, w.d);
+      w.beta = 1.0f;
+      w.hv = 0;
       return RUNNING;
     }
+    if (first) return ST_FAILED;  // the seed chain itself cannot be evaluated
+    if (kS && ok) cnt.c_evals += K;
     w.hv++;
     w.beta *= 0.5f;
     if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
@@ -99,19 +107,6 @@ __device__ __forceinline__ int walk_pass(const DScene& S, WalkLane<K>& w, const 
 
 // Line-search attempts per pass once a launch's work queue is empty.
 constexpr int TAIL_ATTEMPTS = 4;
-
-// Phase vote of a warp: the Jacobian evaluation (about four times the work of
-// a line-search attempt) runs when at least as many active lanes need it as
-// are between halvings; otherwise the pass runs the line-search attempts only
-// and the lanes that need the Jacobian wait for the next evaluation pass.
-// Without it, a lane whose last step was rejected idles through the other
-// lanes' evaluation in every pass.
-__device__ __forceinline__ bool eval_vote(bool active, bool need_eval) {
-  const unsigned FULL = 0xffffffffu;
-  unsigned e = __ballot_sync(FULL, active && need_eval);
-  unsigned l = __ballot_sync(FULL, active && !need_eval);
-  return __popc(e) >= __popc(l);
-}
 
 // Warp-aggregated take of one queue item per lane that asks for one.  Returns
 // the lane's item index (or -1) and sets `done` (warp-uniform) once the queue
@@ -176,9 +171,8 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid
     }
     bool any = __any_sync(FULL, b >= 0);
     if (!any && done) break;
-    const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b >= 0) {
-      int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, done ? TAIL_ATTEMPTS : 1);
+      int st = walk_pass_fused<K, kS>(S, L, P, t.c, done ? TAIL_ATTEMPTS : 1);
       if (st != RUNNING) {
         t.walks++;
         t.conv += st == ST_CONVERGED;
@@ -198,7 +192,7 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid
 // neighbours' positions and tangent bases come by shuffles within the group,
 // and each lane stages its vertex's 2x2 blocks and constraint in shared
 // memory, where every lane of the group reads all of them and runs the same
-// block Thomas sweep.  Per vertex the arithmetic is that of walk_pass() and
+// block Thomas sweep.  Per vertex the arithmetic is that of walk_pass_fused() and
 // the sums over vertices are taken in the same order (the compiler may still
 // contract some products differently, so the two forms agree to FP32
 // rounding); the group form cuts the latency of a pass by up to K, at the
@@ -215,88 +209,78 @@ struct GroupLane {
   bool need_eval;
 };
 
+// One pass of the group walk (the group form of walk_pass_fused): every attempt
+// reprojects the group's vertices, evaluates frames, blocks and constraint at
+// the candidate and stages them, so that all groups of a warp run the same
+// instructions in each pass; an accepted candidate's blocks give the next
+// Newton direction.  Per vertex the arithmetic and the decisions are those
+// of walk_pass_fused.
 template <int K, int G, bool kS>
-__device__ __forceinline__ int walk_pass_g(const DScene& S, GroupLane<K>& w, const mpg_params& P, Counters& cnt,
-                                           bool eval_phase, unsigned gmask, int j, float2* sC, float4* sA, float4* sB,
-                                           float4* sCc, int attempts = 1) {
+__device__ __forceinline__ int walk_pass_g_fused(const DScene& S, GroupLane<K>& w, const mpg_params& P, Counters& cnt,
+                                                 unsigned gmask, int j, float2* sC, float4* sA, float4* sB,
+                                                 float4* sCc, int attempts = 1) {
   const bool own = j < K;
-  if (w.need_eval) {
-    if (!eval_phase) return RUNNING;
-    Frame fr = {};
-    if (own) fr = vertex_frame(S, w.surf, w.prim, w.x, w.b1, w.b2);
-    float3 tu = fr.dpdu, tv = fr.dpdv;
-    float3 xp = shfl_up3(gmask, w.x, G), xn = shfl_down3(gmask, w.x, G);
-    float3 pu = shfl_up3(gmask, tu, G), pv = shfl_up3(gmask, tv, G);
-    float3 nu = shfl_down3(gmask, tu, G), nv = shfl_down3(gmask, tv, G);
-    if (j == 0) xp = w.e.xD;
-    if (j == K - 1) xn = w.e.xL;
-    VB vb;
-    bool ok = !own || vertex_blocks(xp, pu, pv, w.x, fr, xn, nu, nv, S.s[w.surf], (w.e.tau >> j) & 1u, j > 0,
-                                    j < K - 1, vb);
-    if (!__all_sync(gmask, ok)) return ST_FAILED;
-    if (own) { sC[j] = vb.C; sA[j] = vb.A; sB[j] = vb.B; sCc[j] = vb.Cc; }
-    __syncwarp(gmask);
-    VB blk[K];
-    float2 du[K][1];
-    float cn2 = 0.0f, cmax = 0.0f;
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-      blk[i].C = sC[i]; blk[i].A = sA[i]; blk[i].B = sB[i]; blk[i].Cc = sCc[i];
-      cn2 = fmaf(blk[i].C.x, blk[i].C.x, fmaf(blk[i].C.y, blk[i].C.y, cn2));
-      cmax = fmaxf(cmax, fmaxf(fabsf(blk[i].C.x), fabsf(blk[i].C.y)));
-      du[i][0] = make_float2(-blk[i].C.x, -blk[i].C.y);
-    }
-    __syncwarp(gmask);  // the staging area is rewritten by the next evaluation
-    if (kS && j == 0) cnt.full_evals += K;
-    w.cn2 = cn2;
-    w.cmax = cmax;
-    if (cmax < P.tol) return ST_CONVERGED;
-    if (w.it >= P.max_iter) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
-    if (kS && j == 0) { cnt.newton++; cnt.rows += K; }
-    if (!thomas<K, 1>(blk, du, P.sing_eps)) return ST_FAILED;
-#pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (i == j) w.d = tu * du[i][0].x + tv * du[i][0].y;
-    w.beta = 1.0f;
-    w.hv = 0;
-    w.need_eval = false;
-  }
-  // Every decision below is the same in all lanes of the group, so the
-  // attempts loop keeps the group converged for its shuffles.
   for (int a = 0; a < attempts; ++a) {
+    const bool first = w.need_eval;  // the same in every lane of the group
     float3 cx = w.x;
     int cprim = w.prim;
     float cb1 = w.b1, cb2 = w.b2;
-    bool ok = !own || reproject(S, w.surf, w.x + w.d * w.beta, cx, cprim, cb1, cb2);
-    bool accept = false;
-    if (__all_sync(gmask, ok)) {
+    bool ok = true;
+    if (!first && own) ok = reproject(S, w.surf, w.x + w.d * w.beta, cx, cprim, cb1, cb2);
+    ok = __all_sync(gmask, ok);
+    bool evaluated = false, accept = false;
+    VB blk[K];
+    float2 du[K][1];
+    float cn2 = 0.0f, cmax = 0.0f;
+    float3 tu = make_float3(0.f, 0.f, 0.f), tv = tu;
+    if (ok) {
+      Frame fr = {};
+      if (own) fr = vertex_frame(S, w.surf, cprim, cx, cb1, cb2);
+      tu = fr.dpdu;
+      tv = fr.dpdv;
       float3 xp = shfl_up3(gmask, cx, G), xn = shfl_down3(gmask, cx, G);
+      float3 pu = shfl_up3(gmask, tu, G), pv = shfl_up3(gmask, tv, G);
+      float3 nu = shfl_down3(gmask, tu, G), nv = shfl_down3(gmask, tv, G);
       if (j == 0) xp = w.e.xD;
       if (j == K - 1) xn = w.e.xL;
-      float2 C = make_float2(0.f, 0.f);
-      bool okc = true;
-      if (own) {
-        float3 n = vertex_normal(S, w.surf, cprim, cx, cb1, cb2);
-        okc = vertex_c(xp, cx, xn, n, S.s[w.surf], (w.e.tau >> j) & 1u, C);
-      }
-      if (__all_sync(gmask, okc)) {
-        if (kS && j == 0) cnt.c_evals += K;
-        const int leader = (threadIdx.x & 31) & ~(G - 1);
-        float cc2 = 0.0f;
+      VB vb;
+      bool okb = !own || vertex_blocks(xp, pu, pv, cx, fr, xn, nu, nv, S.s[w.surf], (w.e.tau >> j) & 1u, j > 0,
+                                       j < K - 1, vb);
+      if (__all_sync(gmask, okb)) {
+        if (own) { sC[j] = vb.C; sA[j] = vb.A; sB[j] = vb.B; sCc[j] = vb.Cc; }
+        __syncwarp(gmask);
 #pragma unroll
         for (int i = 0; i < K; ++i) {
-          float cxv = __shfl_sync(gmask, C.x, leader + i), cyv = __shfl_sync(gmask, C.y, leader + i);
-          cc2 = fmaf(cxv, cxv, fmaf(cyv, cyv, cc2));
+          blk[i].C = sC[i]; blk[i].A = sA[i]; blk[i].B = sB[i]; blk[i].Cc = sCc[i];
+          cn2 = fmaf(blk[i].C.x, blk[i].C.x, fmaf(blk[i].C.y, blk[i].C.y, cn2));
+          cmax = fmaxf(cmax, fmaxf(fabsf(blk[i].C.x), fabsf(blk[i].C.y)));
+          du[i][0] = make_float2(-blk[i].C.x, -blk[i].C.y);
         }
-        accept = cc2 < w.cn2;
+        __syncwarp(gmask);  // the staging area is rewritten by the next evaluation
+        evaluated = true;
+        accept = first || cn2 < w.cn2;
       }
     }
     if (accept) {
+      if (kS && j == 0) cnt.full_evals += K;
       w.x = cx; w.prim = cprim; w.b1 = cb1; w.b2 = cb2;
-      w.it++;
-      w.need_eval = true;
+      w.it += first ? 0 : 1;
+      w.need_eval = false;
+      w.cn2 = cn2;
+      w.cmax = cmax;
+      if (cmax < P.tol) return ST_CONVERGED;
+      if (w.it >= P.max_iter) return cmax < P.stall_tol ? ST_CONVERGED : ST_LIMIT;
+      if (kS && j == 0) { cnt.newton++; cnt.rows += K; }
+      if (!thomas<K, 1>(blk, du, P.sing_eps)) return ST_FAILED;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i == j) w.d = tu * du[i][0].x + tv * du[i][0].y;
+      w.beta = 1.0f;
+      w.hv = 0;
       return RUNNING;
     }
+    if (first) return ST_FAILED;  // the seed chain itself cannot be evaluated
+    if (kS && j == 0 && evaluated) cnt.c_evals += K;
     w.hv++;
     w.beta *= 0.5f;
     if (w.hv > P.max_halvings) return w.cmax < P.stall_tol ? ST_CONVERGED : ST_FAILED;
@@ -349,10 +333,9 @@ __global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S
     }
     bool any = __any_sync(FULL, b >= 0);
     if (!any && done) break;
-    const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
     if (b >= 0) {
-      int st = walk_pass_g<K, G, kS>(S, L, P, t.c, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp], sCc[grp],
-                                     done ? TAIL_ATTEMPTS : 1);
+      int st = walk_pass_g_fused<K, G, kS>(S, L, P, t.c, gmask, j, sC[grp], sA[grp], sB[grp], sCc[grp],
+                                           done ? TAIL_ATTEMPTS : 1);
       if (st != RUNNING) {
         if (j < K) {
           c.x[(3 * j + 0) * Bz + b] = L.x.x;
@@ -589,9 +572,8 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
     const bool tail = done && np == 0;
     bool any = __any_sync(FULL, b >= 0);
     if (!any && tail) break;
-    const bool eval_phase = eval_vote(b >= 0, L.need_eval);
     if (b < 0) continue;
-    int st = walk_pass<K, kS>(S, L, P, t.c, eval_phase, tail ? TAIL_ATTEMPTS : 1);
+    int st = walk_pass_fused<K, kS>(S, L, P, t.c, tail ? TAIL_ATTEMPTS : 1);
     if (st != RUNNING) {
       t.walks++;
       // converged walks of the trial sequence (t <= N) are counted by the
@@ -702,10 +684,9 @@ __global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DS
     const bool tail = done && np == 0;
     bool any = __any_sync(FULL, b >= 0);
     if (!any && tail) break;
-    const bool eval_phase = eval_vote(b >= 0 && j == 0, L.need_eval);
     if (b < 0) continue;
-    int st = walk_pass_g<K, G, kS>(S, L, P, j == 0 ? t.c : dummy, eval_phase, gmask, j, sC[grp], sA[grp], sB[grp],
-                                   sCc[grp], tail ? TAIL_ATTEMPTS : 1);
+    int st = walk_pass_g_fused<K, G, kS>(S, L, P, j == 0 ? t.c : dummy, gmask, j, sC[grp], sA[grp], sB[grp],
+                                         sCc[grp], tail ? TAIL_ATTEMPTS : 1);
     if (st != RUNNING) {
       if (j == 0) t.walks++;
       if (st == ST_CONVERGED) {
