@@ -407,4 +407,227 @@ __device__ bool polish_ggt64(const DScene& S, Chain64<K>& ch, const Ends& e, dou
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// The same FP64 polish and geometry term with one chain per group of G >= K
+// lanes: lane j owns vertex j (frame, blocks and constraint of that vertex;
+// the neighbours' positions and tangents come by shuffles within the group),
+// the blocks are staged in shared memory, and every lane of the group runs the
+// same block Thomas sweep over them.  The serial per-chain work of
+// polish_ggt64 is K frames and block rows per evaluation; here each lane
+// evaluates one, so a chain costs about 1/K of the instructions in sequence
+// and its arrays stay in registers.  Decisions and arithmetic per vertex are
+// those of polish_ggt64 (the product of the kappa factors is taken in
+// another order).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ D3 shfl_d3(unsigned mask, D3 v, int src, int width) {
+  return D3{__shfl_sync(mask, v.x, src, width), __shfl_sync(mask, v.y, src, width), __shfl_sync(mask, v.z, src, width)};
+}
+__device__ __forceinline__ D3 shfl_up_d3(unsigned mask, D3 v, int width) {
+  return D3{__shfl_up_sync(mask, v.x, 1, width), __shfl_up_sync(mask, v.y, 1, width), __shfl_up_sync(mask, v.z, 1, width)};
+}
+__device__ __forceinline__ D3 shfl_down_d3(unsigned mask, D3 v, int width) {
+  return D3{__shfl_down_sync(mask, v.x, 1, width), __shfl_down_sync(mask, v.y, 1, width),
+            __shfl_down_sync(mask, v.z, 1, width)};
+}
+
+// Staged blocks of one vertex: A, B, Cc (row-major 2x2) and the constraint.
+struct VS64 {
+  double A[4], B[4], Cc[4], C[2];
+};
+
+// Own vertex j of a group: frame, blocks and constraint at the group's chain;
+// false in every lane of the group when any vertex fails.  cmax is the
+// group's maximum |C|.  The blocks are staged in sv[j].
+template <int K, int G>
+__device__ __forceinline__ bool chain64_g(const DScene& S, int j, unsigned gmask, int surf, int prim, D3 x, double b1,
+                                         double b2, const Ends& e, Frame64& f, VS64* sv, double& cmax) {
+  const bool own = j < K;
+  if (own) f = frame64_at(S, surf, prim, x, b1, b2);
+  D3 xp = shfl_up_d3(gmask, f.p, G), xn = shfl_down_d3(gmask, f.p, G);
+  D3 pu = shfl_up_d3(gmask, f.dpdu, G), pv = shfl_up_d3(gmask, f.dpdv, G);
+  D3 nu = shfl_down_d3(gmask, f.dpdu, G), nv = shfl_down_d3(gmask, f.dpdv, G);
+  if (j == 0) {
+    xp = d3(e.xD);
+    onb(d3(e.nD), pu, pv);
+  }
+  if (j == K - 1) {
+    xn = d3(e.xL);
+    nu = d3(S.L.exu);
+    nv = d3(S.L.eyu);
+  }
+  bool ok = true;
+  double c0 = 0.0, c1 = 0.0;
+  if (own) {
+    const DSurf& sf = S.s[surf];
+    const bool refract = (e.tau >> j) & 1u;
+    VB64 vb;
+    ok = blocks64(xp, pu, pv, f, xn, nu, nv, sf, refract, vb) && constraint64(xp, f, xn, sf, refract, c0, c1);
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { sv[j].A[q] = vb.A[q]; sv[j].B[q] = vb.B[q]; sv[j].Cc[q] = vb.Cc[q]; }
+      sv[j].C[0] = c0;
+      sv[j].C[1] = c1;
+    }
+  }
+  if (!__all_sync(gmask, ok)) return false;
+  double m = fmax(fabs(c0), fabs(c1));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(gmask, m, o, G));
+  cmax = m;
+  __syncwarp(gmask);  // the staged blocks are read by every lane of the group
+  return true;
+}
+
+// thomas64 over staged blocks (every lane of a group runs it alike).
+template <int K, int M>
+__device__ __forceinline__ bool thomas64_s(const VS64* vb, double (&R)[K][2][M], double sing_eps) {
+  double Binv[K][4];
+  double Bp[4] = {vb[0].B[0], vb[0].B[1], vb[0].B[2], vb[0].B[3]};
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    if (i > 0) {
+      const double* Ai = vb[i].A;
+      double Lm[4] = {Ai[0] * Binv[i - 1][0] + Ai[1] * Binv[i - 1][2], Ai[0] * Binv[i - 1][1] + Ai[1] * Binv[i - 1][3],
+                      Ai[2] * Binv[i - 1][0] + Ai[3] * Binv[i - 1][2], Ai[2] * Binv[i - 1][1] + Ai[3] * Binv[i - 1][3]};
+      const double* Cp = vb[i - 1].Cc;
+      Bp[0] = vb[i].B[0] - (Lm[0] * Cp[0] + Lm[1] * Cp[2]);
+      Bp[1] = vb[i].B[1] - (Lm[0] * Cp[1] + Lm[1] * Cp[3]);
+      Bp[2] = vb[i].B[2] - (Lm[2] * Cp[0] + Lm[3] * Cp[2]);
+      Bp[3] = vb[i].B[3] - (Lm[2] * Cp[1] + Lm[3] * Cp[3]);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        double r0 = R[i - 1][0][c], r1 = R[i - 1][1][c];
+        R[i][0][c] -= Lm[0] * r0 + Lm[1] * r1;
+        R[i][1][c] -= Lm[2] * r0 + Lm[3] * r1;
+      }
+    }
+    double det = Bp[0] * Bp[3] - Bp[1] * Bp[2];
+    double mx = fmax(fmax(fabs(Bp[0]), fabs(Bp[1])), fmax(fabs(Bp[2]), fabs(Bp[3])));
+    if (!(fabs(det) > sing_eps * mx * mx)) return false;
+    double id = 1.0 / det;
+    Binv[i][0] = Bp[3] * id; Binv[i][1] = -Bp[1] * id; Binv[i][2] = -Bp[2] * id; Binv[i][3] = Bp[0] * id;
+  }
+#pragma unroll
+  for (int i = K - 1; i >= 0; --i) {
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      double r0 = R[i][0][c], r1 = R[i][1][c];
+      if (i < K - 1) {
+        const double* Cc = vb[i].Cc;
+        r0 -= Cc[0] * R[i + 1][0][c] + Cc[1] * R[i + 1][1][c];
+        r1 -= Cc[2] * R[i + 1][0][c] + Cc[3] * R[i + 1][1][c];
+      }
+      R[i][0][c] = Binv[i][0] * r0 + Binv[i][1] * r1;
+      R[i][1][c] = Binv[i][2] * r0 + Binv[i][3] * r1;
+    }
+  }
+  return true;
+}
+
+
+// polish_ggt64 in group form.  Lane j < K holds vertex j in (x, prim, b1, b2)
+// and gets the polished vertex back; G and kappa come back in every lane of
+// the group.  The staging area sv holds K vertices and is private to the group.
+template <int K, int G>
+__device__ bool polish_ggt64_g(const DScene& S, int j, unsigned gmask, int surf, int& prim, D3& x, double& b1,
+                               double& b2, const Ends& e, double tol, double sing_eps, int steps, VS64* sv, double& G64,
+                               double& kappa) {
+  const bool own = j < K;
+  Frame64 f;
+  f.p = f.n = f.dpdu = f.dpdv = f.dndu = f.dndv = D3{0.0, 0.0, 0.0};
+  double cmax;
+  if (!chain64_g<K, G>(S, j, gmask, surf, prim, x, b1, b2, e, f, sv, cmax)) return false;
+  for (int it = 0; it < steps && cmax >= 1e-3 * tol; ++it) {
+    double R[K][2][1];
+#pragma unroll
+    for (int i = 0; i < K; ++i) { R[i][0][0] = -sv[i].C[0]; R[i][1][0] = -sv[i].C[1]; }
+    if (!thomas64_s<K, 1>(sv, R, sing_eps)) break;
+    double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i == j) { r0 = R[i][0][0]; r1 = R[i][1][0]; }
+    D3 cx = x;
+    int cprim = prim;
+    double cb1 = b1, cb2 = b2;
+    bool ok = !own || reproject64(S, surf, x + f.dpdu * r0 + f.dpdv * r1, cx, cprim, cb1, cb2);
+    if (!__all_sync(gmask, ok)) break;
+    __syncwarp(gmask);  // every lane has read the staged blocks of the current chain
+    Frame64 fc = f;
+    double cn;
+    // a failed or worse candidate leaves the staging area overwritten: the
+    // loop ends then, and only the current vertices and frame are used below
+    const bool ev = chain64_g<K, G>(S, j, gmask, surf, cprim, cx, cb1, cb2, e, fc, sv, cn);
+    if (!ev || !(cn < cmax)) {
+      // restore the staged blocks of the current chain for the geometry term
+      // (the same evaluation as before this attempt, so the same values)
+      chain64_g<K, G>(S, j, gmask, surf, prim, x, b1, b2, e, f, sv, cmax);
+      break;
+    }
+    x = cx; prim = cprim; b1 = cb1; b2 = cb2;
+    f = fc;
+    cmax = cn;
+  }
+  if (!(cmax < tol)) return false;
+  const bool point = S.L.type == LIGHT_POINT;
+  double R[K][2][2];
+#pragma unroll
+  for (int i = 0; i < K; ++i) R[i][0][0] = R[i][0][1] = R[i][1][0] = R[i][1][1] = 0.0;
+  const double* E = point ? sv[0].A : sv[K - 1].Cc;
+  const int row = point ? 0 : K - 1;
+  R[row][0][0] = -E[0]; R[row][0][1] = -E[1]; R[row][1][0] = -E[2]; R[row][1][1] = -E[3];
+  if (!thomas64_s<K, 2>(sv, R, sing_eps)) return false;
+  const int vi = point ? K - 1 : 0;
+  // the frame of vertex vi, from its lane
+  D3 pv = shfl_d3(gmask, f.p, vi, G), du = shfl_d3(gmask, f.dpdu, vi, G), dv = shfl_d3(gmask, f.dpdv, vi, G);
+  D3 anchor = point ? d3(e.xL) : d3(e.xD);
+  D3 w = pv - anchor;
+  double dist = len(w);
+  w = w * (1.0 / dist);
+  D3 a, b;
+  onb(w, a, b);
+  double M[2][2];
+  for (int c = 0; c < 2; ++c) {
+    D3 dx = du * R[vi][0][c] + dv * R[vi][1][c];
+    D3 dw = (dx - w * dot(w, dx)) * (1.0 / dist);
+    M[0][c] = dot(a, dw);
+    M[1][c] = dot(b, dw);
+  }
+  double det = fabs(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
+  G64 = point ? det : dot(d3(e.nD), w) * det;
+  // kappa: each lane its vertex's factor (as polish_ggt64), multiplied over the group
+  double kf = 1.0;
+  D3 xp = shfl_up_d3(gmask, f.p, G), xn = shfl_down_d3(gmask, f.p, G);
+  if (j == 0) xp = d3(e.xD);
+  if (j == K - 1) xn = d3(e.xL);
+  if (own) {
+    const DSurf& sf = S.s[surf];
+    if (sf.mat != MAT_MIRROR) {
+      D3 wi = unit(xp - f.p), wo = unit(xn - f.p);
+      double ci = fabs(dot(wi, f.n));
+      bool front = dot(wi, f.n) > 0.0;
+      double n1 = front ? sf.etaF : sf.etaB;
+      double n2 = front ? sf.etaB : sf.etaF;
+      if ((e.tau >> j) & 1u) {
+        double co = fabs(dot(wo, f.n));
+        double num = 4.0 * n1 * n2 * ci * co, ds = n1 * ci + n2 * co, dp = n2 * ci + n1 * co;
+        double r = point ? 1.0 : n1 / n2;
+        kf = 0.5 * (num / (ds * ds) + num / (dp * dp)) * r * r;
+      } else {
+        double s2 = (n1 / n2) * (n1 / n2) * (1.0 - ci * ci);
+        double F = 1.0;
+        if (s2 < 1.0) {
+          double c2 = sqrt(1.0 - s2);
+          double rs = (n1 * ci - n2 * c2) / (n1 * ci + n2 * c2), rp = (n2 * ci - n1 * c2) / (n2 * ci + n1 * c2);
+          F = 0.5 * (rs * rs + rp * rp);
+        }
+        kf = F;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) kf *= __shfl_xor_sync(gmask, kf, o, G);
+  kappa = kf;
+  return true;
+}
+
 }  // namespace mpg

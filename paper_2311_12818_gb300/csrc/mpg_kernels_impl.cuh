@@ -232,6 +232,58 @@ __global__ void __launch_bounds__(64) k_contrib64(const __grid_constant__ DScene
   }
 }
 
+// k_contrib64 with one chain per group of G >= K lanes (polish_ggt64_g): the
+// FP64 queue of long chains is short, and each chain's serial FP64 work shrinks
+// by about K; groups are dealt to the blocks in turn as in k_contrib64.
+template <int K, int G>
+__global__ void __launch_bounds__(64) k_contrib64_g(const __grid_constant__ DScene S, DChains c, mpg_params P, DOut o) {
+  static_assert(G >= K && G <= 32 && (G & (G - 1)) == 0, "group of a power of two >= K lanes");
+  constexpr int NG = 64 / G;
+  __shared__ VS64 sv[NG][K];
+  const int n = *o.fp64_count;
+  const int* list = o.fp64_list + *o.fp64_base;
+  const int lane = threadIdx.x & 31, j = threadIdx.x % G, grp = threadIdx.x / G;
+  const int leader = lane & ~(G - 1);
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << leader;
+  const size_t Bz = (size_t)c.B;
+  for (long long q = (long long)grp * gridDim.x + blockIdx.x; q < n; q += (long long)gridDim.x * NG) {
+    const int b = list[q];
+    const Ends e = load_ends(c, b);
+    int surf = 0, prim = 0;
+    D3 x = D3{0.0, 0.0, 0.0};
+    double b1 = 0.0, b2 = 0.0;
+    if (j < K) {
+      surf = c.surf[j * Bz + b];
+      prim = c.prim[j * Bz + b];
+      b1 = c.bary[(2 * j + 0) * Bz + b];
+      b2 = c.bary[(2 * j + 1) * Bz + b];
+      x = D3{(double)c.x[(3 * j + 0) * Bz + b], (double)c.x[(3 * j + 1) * Bz + b], (double)c.x[(3 * j + 2) * Bz + b]};
+      const DSurf& sf = S.s[surf];
+      if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) x = d3(sf.c) + unit(x - d3(sf.c)) * (double)sf.r;
+    }
+    double g, k64;
+    float G32 = 0.f, kap = 0.f;
+    if (polish_ggt64_g<K, G>(S, j, gmask, surf, prim, x, b1, b2, e, (double)P.tol, (double)P.sing_eps, 3, sv[grp], g,
+                             k64)) {
+      G32 = (float)g;
+      kap = (float)k64;
+      if (j < K) {
+        c.x[(3 * j + 0) * Bz + b] = (float)x.x;
+        c.x[(3 * j + 1) * Bz + b] = (float)x.y;
+        c.x[(3 * j + 2) * Bz + b] = (float)x.z;
+        c.prim[j * Bz + b] = prim;
+        c.bary[(2 * j + 0) * Bz + b] = (float)b1;
+        c.bary[(2 * j + 1) * Bz + b] = (float)b2;
+      }
+    }
+    if (j == 0) {
+      if (o.G) o.G[b] = G32;
+      if (o.kappa) o.kappa[b] = kap;
+      o.T[b] = kap * G32 * S.L.power;
+    }
+  }
+}
+
 // Glossy contribution: admissibility (as for specular chains) and the
 // estimate W of each converged glossy chain in FP64 after an FP64 polish to
 // C = o (mpg_glossy.cuh), written as T; the polished vertices are written
@@ -361,7 +413,10 @@ void KLaunch<K>::walk_g(bool stats, const DScene& S, const DChains& c, DWork w, 
 
 template <int K>
 void KLaunch<K>::contrib64(const DScene& S, const DChains& c, const mpg_params& P, DOut o, int grid, cudaStream_t st) {
-  kern::k_contrib64<K><<<grid, 64, 0, st>>>(S, c, P, o);
+  // one chain per lane group from three vertices on (K <= 2: a thread per chain)
+  constexpr int G = K <= 2 ? 1 : K <= 4 ? 4 : 8;
+  if constexpr (G == 1) kern::k_contrib64<K><<<grid, 64, 0, st>>>(S, c, P, o);
+  else kern::k_contrib64_g<K, G><<<grid, 64, 0, st>>>(S, c, P, o);
 }
 
 template <int K>
