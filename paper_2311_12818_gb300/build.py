@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT = os.path.join(HERE, "libmpg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["mpg_kernels.cu", "mpg_aux.cu", "mpg_api.cu", "mpg_adjoint.cu", "mpg_vmf.cu", "mpg_stree.cu"] + ["mpg_k%d.cu" % k for k in range(1, 9)]
+SOURCES = ["mpg_kernels.cu", "mpg_aux.cu", "mpg_api.cu", "mpg_adjoint.cu", "mpg_vmf.cu", "mpg_stree.cu", "mpg_seed_all.cu"] + ["mpg_k%d.cu" % k for k in range(1, 9)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 division at <= 2 ulp (hardware reciprocal) instead of the IEEE-rounded
 # sequence; square roots stay IEEE; FP64 and denormals are untouched.

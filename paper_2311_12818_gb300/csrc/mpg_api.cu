@@ -735,12 +735,20 @@ mpg_status mpg_sample_seeds(mpg_ctx* ctx, const mpg_scene* sc, const mpg_guide* 
   DGuide g;
   if (guide && (s = check_guide(guide, g))) return s;
   CUDA_TRY(cudaSetDevice(ctx->device));
-  Plan plan;
-  mpg_params Pn = *P;
-  if ((s = make_plan(ctx, chains, &Pn, -1, st, plan))) return s;
   DChains c = to_dev(chains);
   uint2 key = make_uint2((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32));
   DCtx dc = dctx(ctx, MPG_KERNEL_SEED);
+  if (P->walk_mode == MPG_WALK_BATCHED) {
+    // one launch over the batch in chain order, every length at once
+    const int grid = std::max(1, std::min((chains->B + 127) / 128, ctx->sms * 16));
+    timed(ctx, MPG_KERNEL_SEED, st, 1,
+          [&] { launch_seed_all(sc->S, guide ? &g : nullptr, c, key, rng_offset, *P, dc, grid, st); });
+    LAUNCH_CHECK("seed");
+    return MPG_OK;
+  }
+  Plan plan;
+  mpg_params Pn = *P;
+  if ((s = make_plan(ctx, chains, &Pn, -1, st, plan))) return s;
   int block = block_of(P);
   return run_plan(ctx, plan, st, [&](int K, cudaStream_t s2) {
     timed(ctx, MPG_KERNEL_SEED, s2, 1, [&] {

@@ -895,15 +895,16 @@ __device__ __forceinline__ float vmf_sum_warp(const DGuide& g, bool need, const 
   return need ? mine / (float)d.vr.total : 0.0f;
 }
 
-// Draw seed `trial` of chain idx and deduce its vertices.  Returns validity;
-// fills ch (first k vertices), tau and pdf.  With `defer` (vMF guide), the sum
-// over the lobes is not formed here: pdf gets the p_0 part alone and defer
-// what the caller needs to add (1 - alpha) vmf_sum_warp(...) to it.
-template <int K, bool kStats>
-__device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
-                          bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
-                          Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
-                          bool want_pdf = true, bool need_tau_in = false, VmfDeferred* defer = nullptr) {
+// First part of a seed draw for a chain of K vertices (K at run time): the
+// mixture component, the types tau and the direction w from x_D with its
+// density pdf; false when the draw fails before any ray is cast.  tau_out is
+// set on every path (the guided vMF component may replace the drawn types).
+template <bool kStats>
+__device__ __forceinline__ bool draw_dir(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell,
+                                         uint32_t tau_in, bool tau_random, uint2 key, uint64_t idx, uint32_t trial,
+                                         const mpg_params& P, int K, float3& w, uint32_t& tau_out, float& pdf,
+                                         int* err, Counters& cnt, bool want_pdf, bool need_tau_in,
+                                         VmfDeferred* defer) {
   if (kStats) cnt.seeds++;
   uint4 r1 = philox(make_uint4((uint32_t)idx, (uint32_t)(idx >> 32), trial, 1u), key);
   uint32_t tau = tau_random ? (r1.y & ((1u << K) - 1u)) : tau_in;
@@ -949,7 +950,6 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
     tau_out = tau;
     if (need_tau_in && tau != tau_in) return false;
   }
-  float3 w;
   if (!pick_p0 && vmf) {
     w = vmf_sample(__ldg(g->lobe + li), u01c(r0.z), u01(r0.w));
   } else if (pick_p0) {
@@ -1020,6 +1020,24 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   } else {
     pdf = p0_pdf(S, e.xD, w);
   }
+  return true;
+}
+
+// Draw seed `trial` of chain idx and deduce its vertices (Eq. deduction).
+// Returns validity; fills ch (first K vertices), tau and pdf.  With `defer`
+// (vMF guide), the sum over the lobes is not formed here: pdf gets the p_0
+// part alone and defer what the caller needs to add (1 - alpha)
+// vmf_sum_warp(...) to it.
+template <int K, bool kStats>
+__device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
+                          bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
+                          Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
+                          bool want_pdf = true, bool need_tau_in = false, VmfDeferred* defer = nullptr) {
+  float3 w;
+  if (!draw_dir<kStats>(S, g, e, cell, tau_in, tau_random, key, idx, trial, P, K, w, tau_out, pdf, err, cnt, want_pdf,
+                        need_tau_in, defer))
+    return false;
+  const uint32_t tau = tau_out;
   float3 o = e.xD, d = w;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
@@ -1112,18 +1130,32 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   float cosD = dot(e.nD, wD);
   bool point = S.L.type == LIGHT_POINT;
   float3 wL = unit(ch.x[K - 1] - e.xL);
-  // J Y = -dC/du_end: columns 0,1 light end (block row K-1), 2,3 receiver end (row 0)
-  float2 Y[K][4];
+  // J Y = -dC/du_end: columns 0,1 light end (block row K-1), 2,3 receiver end
+  // (row 0); column 4 the Newton step -J^-1 C the chain is still away from the
+  // solution (its size bounds the error of the converged vertices).
+  float2 Y[K][5];
 #pragma unroll
-  for (int i = 0; i < K; ++i)
+  for (int i = 0; i < K; ++i) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) Y[i][c] = make_float2(0.f, 0.f);
+    Y[i][4] = make_float2(-vb[i].C.x, -vb[i].C.y);
+  }
   Y[K - 1][0] = make_float2(-vb[K - 1].Cc.x, -vb[K - 1].Cc.z);
   Y[K - 1][1] = make_float2(-vb[K - 1].Cc.y, -vb[K - 1].Cc.w);
   Y[0][2] = make_float2(-vb[0].A.x, -vb[0].A.z);
   Y[0][3] = make_float2(-vb[0].A.y, -vb[0].A.w);
   if (kStats) cnt.ggt += 2 * K;
-  if (!thomas<K, 4>(vb, Y, P.sing_eps)) return false;
+  if (!thomas<K, 5>(vb, Y, P.sing_eps)) return false;
+  // direction error of the converged chain: the largest remaining vertex
+  // displacement over the shortest segment
+  float dx2 = 0.0f, dmin = len(ch.x[0] - e.xD);
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    float3 d = tu[i] * Y[i][4].x + tv[i] * Y[i][4].y;
+    dx2 = fmaxf(dx2, dot(d, d));
+    dmin = fminf(dmin, len((i == K - 1 ? e.xL : ch.x[i + 1]) - ch.x[i]));
+  }
+  const float dir_err = fmaxf(1.2e-7f, 2.0f * sqrtf(dx2) / fmaxf(dmin, 1e-30f));
   float X[2];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -1158,9 +1190,12 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
   // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
   // near total internal reflection.
-  // kappa_err (out): FP32 relative error estimate of the transmittances.  The
-  // cosines come from the chain's own unit directions (absolute error ~1e-7),
-  // and T_s, T_p scale like the smaller cosine at grazing incidence or exit.
+  // kappa_err (out): relative error estimate of the transmittances.  The
+  // cosines come from the chain's own unit directions, whose error is the
+  // larger of FP32 rounding (~1e-7) and the remaining Newton step over the
+  // shortest segment (dir_err: near grazing or a caustic a small residual C
+  // can leave the vertices well off the solution); T_s, T_p scale like the
+  // smaller cosine at grazing incidence or exit.
   float kap = 1.0f;
   kappa_err = 0.0f;
 #pragma unroll
@@ -1179,7 +1214,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
       float r = point ? 1.0f : n1 / n2;
       kap *= Tr * r * r;
-      kappa_err = fmaxf(kappa_err, 1.2e-7f / fmaxf(fminf(ci, co), 1e-30f));
+      kappa_err = fmaxf(kappa_err, dir_err / fmaxf(fminf(ci, co), 1e-30f));
     } else {
       float e2 = vb[i].front ? sf.etaB : sf.etaF;
       kap *= fresnel(ci, vb[i].ei, e2);

@@ -104,6 +104,10 @@ __host__ __device__ __forceinline__ int fp64_k_of(const mpg_params& P) { return 
 
 void launch_seed(int K, bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                  uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st);
+// Seeds of every chain of a batch in one launch, whatever its length
+// (mpg_seed_all.cu; batched mode).
+void launch_seed_all(const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
+                     const mpg_params& P, DCtx ctx, int grid, cudaStream_t st);
 void launch_walk(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DCtx ctx,
                  int grid, int block, cudaStream_t st);
 void launch_contrib(int K, bool stats, const DScene& S, const DChains& c, DWork w, const mpg_params& P, DOut o,

@@ -335,8 +335,13 @@ def test_plain_and_batched_agree(M, ctx):
         sc, ch, gs, gw, out = _gpu_pipeline(M, ctx, wl, P=P)
         res.append((gs, gw, out.T.cpu().numpy(), out.trials.cpu().numpy(), out.E.cpu().numpy()))
     (s0, w0, T0, N0, E0), (s1, w1, T1, N1, E1) = res
-    assert np.array_equal(s0["status"], s1["status"])      # the seed kernel is shared
-    assert np.array_equal(s0["x"], s1["x"])
+    # the batched mode seeds every length in one launch, the plain mode one
+    # launch per length: the same draws (same counters), FP32 rounding apart
+    assert (s0["status"] == s1["status"]).mean() >= 0.999
+    ok = (s0["status"] != 0) & (s1["status"] != 0)
+    same = ok & (s0["surf"] == s1["surf"]).all(axis=1)  # unused rows hold the same fill on both sides
+    assert same.sum() >= 0.999 * ok.sum() and ok.sum() > 1000
+    assert np.abs(s0["x"][same] - s1["x"][same]).max() < 1e-4 * wl.scene_scale
     _compare_walk(wl, w0, w1)
     both = (T0 > 0) & (T1 > 0)
     assert ((T0 > 0) == (T1 > 0)).mean() >= 0.999
