@@ -595,7 +595,9 @@ mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_f
  * input parameters with the fastest schedule, and in *best_ms its time.
  * Coordinate descent over one group at a time (tile shape, walk form, refill
  * cadence, Bernoulli rounds, FP64 split); each candidate is timed `repeats`
- * times (minimum).
+ * times (minimum) and replaces the best one only when more than 3 % faster.
+ * The result is then timed three more times against the input schedule,
+ * alternately, and the input schedule is returned if it is the faster. 
  * The outputs of the step go to scratch the call allocates and frees.
  * Synchronous; walk_mode must be MPG_WALK_BATCHED. */
 mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,

@@ -1120,7 +1120,8 @@ __device__ __forceinline__ bool admissible(const DScene& S, const Chain<K>& ch, 
 
 template <int K, bool kStats>
 __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
-                             float& kappa, float& mismatch, float& cmax, float& kappa_err, int* err, Counters& cnt) {
+                             float& kappa, float& mismatch, float& cmax, float& kappa_err, float& step_err, int* err,
+                             Counters& cnt) {
   VB vb[K];
   float3 tu[K], tv[K];
   float cn2;
@@ -1155,7 +1156,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
     dx2 = fmaxf(dx2, dot(d, d));
     dmin = fminf(dmin, len((i == K - 1 ? e.xL : ch.x[i + 1]) - ch.x[i]));
   }
-  const float dir_err = fmaxf(1.2e-7f, 2.0f * sqrtf(dx2) / fmaxf(dmin, 1e-30f));
+  const float dir_err = 2.0f * sqrtf(dx2) / fmaxf(dmin, 1e-30f);
   float X[2];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
@@ -1190,14 +1191,17 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   // T_s = 4 n1 n2 c1 c2/(n1 c1 + n2 c2)^2 and T_p = 4 n1 n2 c1 c2/(n2 c1 + n1 c2)^2,
   // c2 the refracted cosine of the converged chain: 1 - F would cancel in FP32
   // near total internal reflection.
-  // kappa_err (out): relative error estimate of the transmittances.  The
-  // cosines come from the chain's own unit directions, whose error is the
-  // larger of FP32 rounding (~1e-7) and the remaining Newton step over the
-  // shortest segment (dir_err: near grazing or a caustic a small residual C
-  // can leave the vertices well off the solution); T_s, T_p scale like the
-  // smaller cosine at grazing incidence or exit.
+  // kappa_err, step_err (out): relative error estimates of the
+  // transmittances, which scale like the smaller cosine at grazing incidence
+  // or exit.  The cosines come from the chain's own unit directions: their
+  // FP32 rounding (~1e-7) gives kappa_err; the remaining Newton step over the
+  // shortest segment (dir_err: near grazing a residual C below the tolerance
+  // can still leave the vertices off the solution) gives step_err, a bound
+  // rather than an estimate (the largest vertex step, over the shortest
+  // segment, doubled).
   float kap = 1.0f;
   kappa_err = 0.0f;
+  step_err = 0.0f;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
     const DSurf& sf = S.s[ch.surf[i]];
@@ -1214,7 +1218,9 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       float Tr = 0.5f * (num / (ds * ds) + num / (dp * dp));
       float r = point ? 1.0f : n1 / n2;
       kap *= Tr * r * r;
-      kappa_err = fmaxf(kappa_err, dir_err / fmaxf(fminf(ci, co), 1e-30f));
+      const float ic = 1.0f / fmaxf(fminf(ci, co), 1e-30f);
+      kappa_err = fmaxf(kappa_err, 1.2e-7f * ic);
+      step_err = fmaxf(step_err, dir_err * ic);
     } else {
       float e2 = vb[i].front ? sf.etaB : sf.etaF;
       kap *= fresnel(ci, vb[i].ei, e2);

@@ -172,14 +172,16 @@ __global__ void __launch_bounds__(128) k_contrib(const __grid_constant__ DScene 
       Chain<K> ch;
       load_chain<K>(c, b, ch);
       Ends e = load_ends(c, b);
-      float mismatch = 0.0f, cmax = 0.0f, kerr = 0.0f;
-      adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, kerr, ctx.err, t.c);
+      float mismatch = 0.0f, cmax = 0.0f, kerr = 0.0f, serr = 0.0f;
+      adm = contribution<K, kS>(S, ch, e, P, G, kap, mismatch, cmax, kerr, serr, ctx.err, t.c);
       // Escalate to FP64 where FP32 is not enough: long chains, a geometry term
       // whose two reciprocal FP32 evaluations disagree, a transmittance at a
-      // grazing cosine, or a walk that stopped at the FP32 resolution of C.
-      // The chain is queued for k_contrib64, which polishes it and recomputes
-      // G and kappa in FP64.
-      if (adm && (K >= fp64_k_of(P) || mismatch > P.fp64_tol || kerr > P.fp64_tol || !(cmax < P.tol)) && o.fp64_list) {
+      // grazing cosine (FP32 rounding, or the walk's remaining step: that bound
+      // is allowed five times fp64_tol), or a walk that stopped at the FP32
+      // resolution of C.  The chain is queued for k_contrib64, which polishes
+      // it and recomputes G and kappa in FP64.
+      if (adm && (K >= fp64_k_of(P) || mismatch > P.fp64_tol || kerr > P.fp64_tol || serr > 5.0f * P.fp64_tol ||
+                  !(cmax < P.tol)) && o.fp64_list) {
         o.fp64_list[*o.fp64_base + atomicAdd(o.fp64_count, 1)] = b;
         t.c.ggt64++;
       }
