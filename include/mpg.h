@@ -272,6 +272,21 @@ mpg_status mpg_scene_create(mpg_ctx* ctx, const double* surfaces, int32_t n_surf
 void mpg_scene_destroy(mpg_scene* scene);
 /* Number of BVH nodes and triangles of heightfield h (for reports). */
 mpg_status mpg_scene_info(const mpg_scene* scene, int32_t h, int32_t* n_nodes, int32_t* n_tris);
+/* New heights of heightfield h, on the device: `heights` is a device array of
+ * nx * ny floats (row-major, as hf_heights of mpg_scene_create), read only.
+ * Recomputes the vertex positions and interpolation normals with the scene
+ * builder's formulas and FP64 operations (so a scene built on the host from
+ * the same FP32 heights has the same arrays), the leaf-ordered triangles, and
+ * refits the boxes of the BVH bottom up while keeping its shape.  The
+ * heightfield's parameters are what the adjoint (mpg_walk_adjoint, Sec. 5.2)
+ * differentiates, so a gradient loop changes them without leaving the device.
+ * Asynchronous on `stream`; calls on the scene queued after it on that stream
+ * see the new surface, calls already running on other streams must be
+ * finished first (the caller orders them).  Errors: MPG_ERR_INVALID_ARG for
+ * a NULL or unaligned pointer or no heightfield h, MPG_ERR_CUDA for a launch
+ * failure. */
+mpg_status mpg_scene_set_heights(mpg_ctx* ctx, mpg_scene* scene, int32_t h, const float* heights,
+                                 cudaStream_t stream);
 
 /* S1 -- seed chains (Eq. deduction; Sec. 5.4 initialisation p_0; Sec. 5.5
  * guided sampling with the one-sample defensive mixture alpha p_0 + (1-alpha) p_e).

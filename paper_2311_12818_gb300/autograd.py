@@ -31,7 +31,13 @@ class _Fn(torch.autograd.Function):
 class HeightfieldIrradiance:
     """E = f(heights): seeds -> manifold walk -> contribution (with Bernoulli
     trials) on a workload whose scene has one heightfield; heights is a flat
-    CUDA tensor of the grid heights (row-major)."""
+    CUDA float32 tensor of the grid heights (row-major).
+
+    The first call builds the scene (mesh and BVH on the host, from these
+    heights); every later call replaces the heights on the device
+    (mpg_scene_set_heights: positions, normals, triangles and a refit of the
+    BVH boxes), so a gradient loop never copies the heights to the host.  The
+    chain buffers are allocated once and reused; each call returns its own E."""
 
     def __init__(self, ctx, workload, params=None):
         self.ctx = ctx
@@ -42,11 +48,14 @@ class HeightfieldIrradiance:
         self.last_scene = self.last_chains = self.last_out = None
 
     def _forward(self, heights):
-        h = heights.detach().double().cpu().numpy().ravel()
-        wl = dataclasses.replace(self.wl, hf_heights=h)
-        self.last_scene = mpg.Scene(self.ctx, wl)
-        self.last_chains = mpg.Chains(wl)
-        self.last_out = mpg.run(self.ctx, self.last_scene, self.last_chains, wl, params=self.params)
+        h = heights.detach().float().contiguous().view(-1)
+        if self.last_scene is None:
+            wl = dataclasses.replace(self.wl, hf_heights=h.cpu().numpy().astype(np.float64))
+            self.last_scene = mpg.Scene(self.ctx, wl)
+            self.last_chains = mpg.Chains(wl)
+        else:
+            self.last_scene.set_heights(h)
+        self.last_out = mpg.run(self.ctx, self.last_scene, self.last_chains, self.wl, params=self.params)
         return self.last_out.E
 
     def __call__(self, heights):

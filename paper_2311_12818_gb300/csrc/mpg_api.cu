@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "mpg_aux.cuh"
@@ -104,6 +105,12 @@ struct mpg_scene {
   DScene S;
   std::vector<void*> allocs;
   std::vector<int> n_nodes, n_tris;
+  // per heightfield, for height updates on the device (mpg_scene_set_heights):
+  // the grid's extent in FP64, each node's parent and number of inner
+  // children, and a counter per node for the bottom-up refit
+  std::vector<std::array<double, 4>> hf_extent;
+  std::vector<const int*> hf_parent, hf_ninner;
+  std::vector<int*> hf_count;
   int device = 0;
 };
 
@@ -663,6 +670,25 @@ mpg_status mpg_scene_create(mpg_ctx* ctx, const double* surfaces, int32_t n_surf
     }
     sc->n_nodes.push_back(H.n_nodes);
     sc->n_tris.push_back(nt);
+    // the tree's shape for the refit: nodes are numbered parents first
+    std::vector<int> parent(H.n_nodes, -1), ninner(H.n_nodes, 0);
+    for (int v = 0; v < H.n_nodes; ++v) {
+      int4 ch;
+      memcpy(&ch, &bb.nodes[4 * (size_t)v + 3], sizeof(int4));
+      if (ch.z == 0) { parent[ch.x] = v; ninner[v]++; }
+      if (ch.w == 0) { parent[ch.y] = v; ninner[v]++; }
+    }
+    const int* dp = nullptr;
+    const int* dn = nullptr;
+    const int* dc = nullptr;
+    if ((st = upload(sc, parent, &dp)) || (st = upload(sc, ninner, &dn)) || (st = upload(sc, ninner, &dc))) {
+      mpg_scene_destroy(sc);
+      return st;
+    }
+    sc->hf_extent.push_back({d[2], d[3], d[4], d[5]});
+    sc->hf_parent.push_back(dp);
+    sc->hf_ninner.push_back(dn);
+    sc->hf_count.push_back(const_cast<int*>(dc));
   }
   for (int s = 0; s < n_surf; ++s) {
     const double* r = surfaces + 24 * s;
@@ -717,6 +743,19 @@ void mpg_scene_destroy(mpg_scene* sc) {
   for (void* p : sc->allocs) cudaFree(p);
   delete sc;
   (void)cudaGetLastError();  // a failure here must not surface in a later call's launch check
+}
+
+mpg_status mpg_scene_set_heights(mpg_ctx* ctx, mpg_scene* sc, int32_t h, const float* heights, cudaStream_t st) {
+  if (!ctx || !sc || !aligned16(heights)) return fail(MPG_ERR_INVALID_ARG, "ctx, scene or heights NULL or unaligned");
+  if (h < 0 || h >= (int)sc->n_nodes.size()) return fail(MPG_ERR_INVALID_ARG, "no heightfield %d", h);
+  CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaError_t e = cudaSuccess;
+  timed(ctx, MPG_KERNEL_AUX, st, 3, [&] {
+    e = launch_hf_update(sc->S.hf[h], sc->hf_extent[h].data(), heights, sc->n_tris[h], sc->hf_parent[h],
+                         sc->hf_ninner[h], sc->hf_count[h], st);
+  });
+  if (e != cudaSuccess) return fail(MPG_ERR_CUDA, "heightfield update: %s", cudaGetErrorString(e));
+  return MPG_OK;
 }
 
 mpg_status mpg_scene_info(const mpg_scene* sc, int32_t h, int32_t* n_nodes, int32_t* n_tris) {

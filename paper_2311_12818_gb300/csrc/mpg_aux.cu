@@ -396,3 +396,124 @@ double run_fp32_peak(float* scratch, int sms, cudaStream_t st) {
 }
 
 }  // namespace mpg
+
+// ---------------------------------------------------------------------------
+// Heightfield heights replaced on the device (mpg_scene_set_heights)
+// ---------------------------------------------------------------------------
+namespace mpg {
+
+// Vertex positions and interpolation normals of the grid: the same formulas,
+// in the same FP64 operations, as the scene builder on the host (central
+// differences inside, one-sided on the border; explicit round-to-nearest
+// operations so that nothing is contracted into a fused multiply-add), so the
+// two give the same FP32 arrays.
+__global__ void k_hf_mesh(int nx, int ny, double x0, double y0, double dx, double dy, const float* __restrict__ h,
+                          float4* P, float4* N) {
+  const int n = nx * ny;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int i = v % nx, j = v / nx;
+    auto H = [&](int a, int b) { return (double)h[(size_t)b * nx + a]; };
+    double gx, gy;
+    if (i == 0) gx = __ddiv_rn(__dsub_rn(H(1, j), H(0, j)), dx);
+    else if (i == nx - 1) gx = __ddiv_rn(__dsub_rn(H(nx - 1, j), H(nx - 2, j)), dx);
+    else gx = __ddiv_rn(__dsub_rn(H(i + 1, j), H(i - 1, j)), __dmul_rn(2.0, dx));
+    if (j == 0) gy = __ddiv_rn(__dsub_rn(H(i, 1), H(i, 0)), dy);
+    else if (j == ny - 1) gy = __ddiv_rn(__dsub_rn(H(i, ny - 1), H(i, ny - 2)), dy);
+    else gy = __ddiv_rn(__dsub_rn(H(i, j + 1), H(i, j - 1)), __dmul_rn(2.0, dy));
+    const double l = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy)), 1.0));
+    P[v] = make_float4((float)__dadd_rn(x0, __dmul_rn((double)i, dx)), (float)__dadd_rn(y0, __dmul_rn((double)j, dy)),
+                       h[v], 0.0f);
+    N[v] = make_float4((float)__ddiv_rn(-gx, l), (float)__ddiv_rn(-gy, l), (float)__ddiv_rn(1.0, l), 0.0f);
+  }
+}
+
+// Leaf-ordered triangles (v0 with the triangle id in w, e1, e2) from the new
+// positions; the id already in slot s's w gives the triangle.
+__global__ void k_hf_tris(int nx, int n_tris, const float4* __restrict__ P, float4* tris) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_tris; s += gridDim.x * blockDim.x) {
+    const int t = __float_as_int(tris[3 * (size_t)s].w);
+    const int quad = t / 2, tt = t % 2, i = quad % (nx - 1), j = quad / (nx - 1);
+    const int v00 = j * nx + i, v1 = tt == 0 ? v00 + 1 : v00 + nx + 1, v2 = tt == 0 ? v00 + nx + 1 : v00 + nx;
+    const float4 a = P[v00], b = P[v1], c = P[v2];
+    tris[3 * (size_t)s + 0] = make_float4(a.x, a.y, a.z, __int_as_float(t));
+    tris[3 * (size_t)s + 1] = make_float4(__fsub_rn(b.x, a.x), __fsub_rn(b.y, a.y), __fsub_rn(b.z, a.z), 0.f);
+    tris[3 * (size_t)s + 2] = make_float4(__fsub_rn(c.x, a.x), __fsub_rn(c.y, a.y), __fsub_rn(c.z, a.z), 0.f);
+  }
+}
+
+struct Box3 {
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ void grow(Box3& b, float x, float y, float z) {
+  b.lo[0] = fminf(b.lo[0], x); b.hi[0] = fmaxf(b.hi[0], x);
+  b.lo[1] = fminf(b.lo[1], y); b.hi[1] = fmaxf(b.hi[1], y);
+  b.lo[2] = fminf(b.lo[2], z); b.hi[2] = fmaxf(b.hi[2], z);
+}
+
+// Box of one child of a node: over the grid vertices of its triangles (a
+// leaf; as the host builder) or over the two boxes stored in the child node
+// (read through L2: another thread wrote them).
+__device__ __forceinline__ Box3 child_box(const float4* nodes, const float4* tris, const float4* P, int nx, int idx,
+                                          int count) {
+  Box3 b = {{INFINITY, INFINITY, INFINITY}, {-INFINITY, -INFINITY, -INFINITY}};
+  if (count > 0) {
+    for (int s = idx; s < idx + count; ++s) {
+      const int t = __float_as_int(tris[3 * (size_t)s].w);
+      const int quad = t / 2, tt = t % 2, i = quad % (nx - 1), j = quad / (nx - 1);
+      const int v00 = j * nx + i, v1 = tt == 0 ? v00 + 1 : v00 + nx + 1, v2 = tt == 0 ? v00 + nx + 1 : v00 + nx;
+      const float4 p0 = P[v00], p1 = P[v1], p2 = P[v2];
+      grow(b, p0.x, p0.y, p0.z);
+      grow(b, p1.x, p1.y, p1.z);
+      grow(b, p2.x, p2.y, p2.z);
+    }
+    return b;
+  }
+  const float4 na = __ldcg(nodes + 4 * (size_t)idx), nb = __ldcg(nodes + 4 * (size_t)idx + 1),
+               nc = __ldcg(nodes + 4 * (size_t)idx + 2);
+  b.lo[0] = fminf(na.x, nb.x); b.hi[0] = fmaxf(na.y, nb.y);
+  b.lo[1] = fminf(na.z, nb.z); b.hi[1] = fmaxf(na.w, nb.w);
+  b.lo[2] = fminf(nc.x, nc.z); b.hi[2] = fmaxf(nc.y, nc.w);
+  return b;
+}
+
+// Bottom-up refit in one launch: a node whose children are all leaves starts
+// at once; a node with inner children is taken by the thread that finishes
+// its last inner child (counter per node).  No thread waits on another.
+__global__ void k_hf_refit(int n_nodes, int nx, float4* nodes, const float4* __restrict__ tris,
+                           const float4* __restrict__ P, const int* __restrict__ parent,
+                           const int* __restrict__ ninner, int* count) {
+  for (int v0 = blockIdx.x * blockDim.x + threadIdx.x; v0 < n_nodes; v0 += gridDim.x * blockDim.x) {
+    if (ninner[v0] != 0) continue;
+    int v = v0;
+    while (true) {
+      const int4 ch = __ldcg(reinterpret_cast<const int4*>(nodes + 4 * (size_t)v + 3));
+      const Box3 L = child_box(nodes, tris, P, nx, ch.x, ch.z), R = child_box(nodes, tris, P, nx, ch.y, ch.w);
+      nodes[4 * (size_t)v + 0] = make_float4(L.lo[0], L.hi[0], L.lo[1], L.hi[1]);
+      nodes[4 * (size_t)v + 1] = make_float4(R.lo[0], R.hi[0], R.lo[1], R.hi[1]);
+      nodes[4 * (size_t)v + 2] = make_float4(L.lo[2], L.hi[2], R.lo[2], R.hi[2]);
+      __threadfence();
+      const int p = parent[v];
+      if (p < 0) break;
+      if (atomicAdd(count + p, 1) + 1 < ninner[p]) break;  // the sibling subtree is not done yet
+      __threadfence();
+      v = p;
+    }
+  }
+}
+
+cudaError_t launch_hf_update(DHF H, const double* extent, const float* heights, int n_tris, const int* parent,
+                             const int* ninner, int* count, cudaStream_t st) {
+  const double dx = (extent[2] - extent[0]) / (H.nx - 1), dy = (extent[3] - extent[1]) / (H.ny - 1);
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)H.n_nodes, st);
+  if (e != cudaSuccess) return e;
+  const int nv = H.nx * H.ny;
+  k_hf_mesh<<<(nv + 255) / 256, 256, 0, st>>>(H.nx, H.ny, extent[0], extent[1], dx, dy, heights,
+                                               const_cast<float4*>(H.P), const_cast<float4*>(H.N));
+  k_hf_tris<<<(n_tris + 255) / 256, 256, 0, st>>>(H.nx, n_tris, H.P, const_cast<float4*>(H.tris));
+  k_hf_refit<<<(H.n_nodes + 127) / 128, 128, 0, st>>>(H.n_nodes, H.nx, const_cast<float4*>(H.nodes), H.tris, H.P,
+                                                       parent, ninner, count);
+  return cudaGetLastError();
+}
+
+}  // namespace mpg

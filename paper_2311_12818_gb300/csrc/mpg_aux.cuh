@@ -29,6 +29,12 @@ bool stree_build_levels_device(float* d_pos, int n, double eps, double c, StreeH
 cudaError_t launch_bucket(const uint8_t* k, const uint8_t* status, int filter, int B, int* count, int* base,
                           int* cursor, int* order, int sms, cudaStream_t st);
 void launch_irradiance(const float* contrib, int Q, int spq, float* E, int sms, cudaStream_t st);
+// New heights of a heightfield on the device: vertex positions and normals,
+// the leaf-ordered triangles and a bottom-up refit of the BVH boxes (the tree's
+// shape is kept).  `extent` = (x0, y0, x1, y1); parent / ninner describe the
+// tree; count is scratch of one int per node.  Returns the first CUDA error.
+cudaError_t launch_hf_update(DHF H, const double* extent, const float* heights, int n_tris, const int* parent,
+                             const int* ninner, int* count, cudaStream_t st);
 void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* omega, const float* w, int R,
                          const int* R_dev, int shift, int* err, int sms, cudaStream_t st);
 // Guide records in chain order (mpg_vmf.cu): tile_scratch holds rec_tiles(B) counts.

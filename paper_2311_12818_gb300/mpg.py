@@ -77,7 +77,7 @@ class mpg_stats(C.Structure):
 
 
 EXPORTS = ["mpg_last_error", "mpg_version", "mpg_ctx_create", "mpg_ctx_destroy", "mpg_ctx_sync",
-           "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info",
+           "mpg_ctx_stats", "mpg_ctx_set_stats", "mpg_ctx_set_profile", "mpg_ctx_profile", "mpg_ctx_launches", "mpg_scene_create", "mpg_scene_destroy", "mpg_scene_info", "mpg_scene_set_heights",
            "mpg_sample_seeds", "mpg_manifold_walk", "mpg_chain_contribution", "mpg_guide_update",
            "mpg_guide_records", "mpg_walk_adjoint", "mpg_trace_rays", "mpg_fp32_peak",
            "mpg_manifold_walk_noalloc", "mpg_fp64_peak", "mpg_guide_clear", "mpg_graph_begin", "mpg_graph_join", "mpg_graph_end",
@@ -113,6 +113,7 @@ def lib():
         L.mpg_scene_destroy.restype = None
         L.mpg_graph_destroy.restype = None
         L.mpg_scene_info.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.mpg_scene_set_heights.argtypes = [vp, vp, i32, vp, vp]
         L.mpg_sample_seeds.argtypes = [vp, vp, C.POINTER(mpg_guide), C.POINTER(mpg_chains), u64, u64,
                                        C.POINTER(mpg_params), vp]
         L.mpg_manifold_walk.argtypes = [vp, vp, C.POINTER(mpg_chains), C.POINTER(mpg_params), vp]
@@ -256,6 +257,13 @@ class Scene:
         n, t = C.c_int32(), C.c_int32()
         _check(lib().mpg_scene_info(self.h, h, C.byref(n), C.byref(t)))
         return n.value, t.value
+
+    def set_heights(self, heights, h=0, stream=None):
+        """mpg_scene_set_heights: heightfield h takes the heights of a CUDA
+        float32 tensor (nx * ny, row-major), on the device."""
+        if not (heights.is_cuda and heights.dtype == torch.float32 and heights.is_contiguous()):
+            raise TypeError("heights must be a contiguous CUDA float32 tensor")
+        _check(lib().mpg_scene_set_heights(self.ctx.h, self.h, h, _ptr(heights), _stream(stream)))
 
     def __del__(self):
         if getattr(self, "h", None):
