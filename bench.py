@@ -460,6 +460,18 @@ def profiled_traffic(summary):
     return int(tb.group(1))
 
 
+def profiled_fraction(summary):
+    """The executed-FP32 fraction a committed ncu summary states ('= F of the
+    derived 80.5 TFLOP/s'), or None when it was taken on other kernel sources
+    (same digest rule as profiled_traffic)."""
+    import re
+    if profiled_traffic(summary) is None:
+        return None
+    with open(os.path.join(ROOT, "profiles", summary)) as f:
+        m = re.search(r"= ([0-9.]+) of the derived", f.read())
+    return float(m.group(1)) if m else None
+
+
 def measured_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -917,7 +929,11 @@ def part_adjoint(ctx, dev, flush, torch, stream, steps):
         mpg.mpg_walk_adjoint(ctx, sc, ch, res.T, res.contrib, dLdE, gr)
     ms = timed_loop(adj, steps, 2, flush, stream, torch)
     return {"workload": "water_heightfield: 128x128 heights, 512x512 points x 4 = 1,048,576 chains",
-            "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3)}
+            "differentiated_chains": n_adj, "ms": ms, "chains_per_s": n_adj / (ms * 1e-3),
+            "roofline": {"bound": "alu", "kernel": "k_adjoint<1>",
+                         "executed_fp32_frac": profiled_fraction("k_adjoint__water_1M.md"),
+                         "source": "executed FP32 flops (ncu per-opcode counts, FFMA = 2) over the ncu duration of one"
+                                   " launch, profiles/k_adjoint__water_1M.md; null when the kernels changed since"}}
 
 
 def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
