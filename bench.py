@@ -481,6 +481,7 @@ def measured_hbm():
 
 
 PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group",
+         "mixed_step",
          "configs", "glossy_chains")
 # measured by default beside the headline; "mixed" and "adjoint" are covered
 # by the configuration lines (other_configs) and run only with --part
@@ -1305,7 +1306,40 @@ def run_part(args):
     if args.part == "configs":
         print(json.dumps({"part": args.part, **other_configs(args, dev, flush, torch, peak)}))
         return
+    if args.part == "mixed_step":
+        print(json.dumps({"part": args.part, **part_mixed_step(args, dev, torch)}))
+        return
     print(json.dumps({"part": args.part, **secondary(args, dev, flush, torch, peak, parts=(args.part,))}))
+
+
+def part_mixed_step(args, dev, torch):
+    """Uncaptured steps of the mixed-length batch (4 n x 2 n receiver points x 8
+    seeds; n = 256 is the full configuration) with the schedule the autotuner
+    usually picks for it (lane-group walks and rounds, refills every 4 passes,
+    one synchronous round, first parallel batch of 16): a short program whose
+    launches ncu can list or capture one by one."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    ctx = mpg.Context(dev.index or 0)
+    wl = I.mixed(nx=4 * args.n, ny=2 * args.n)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, tau_random=wl.tau_random, walk_group=3,
+                        refill_every=4, trial_sync_rounds=1, trial_batch=16)
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    out = mpg.Contribution.empty(wl.B, wl.Q, device=dev)
+    ms = []
+    for j in range(max(2, args.steps)):
+        o = (1 << 40) + j * wl.B
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, o)
+        mpg.mpg_manifold_walk(ctx, sc, ch, P)
+        mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, o, out=out)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.sync()
+    return {"chains": wl.B, "ms_per_step_uncaptured": ms}
 
 
 def cpu_sample(n=256, spq=16):

@@ -809,15 +809,32 @@ __device__ __forceinline__ VmfRange vmf_range(const DGuide& g, uint32_t cell, ui
   return r;
 }
 
+// The bin of an inverse-CDF draw: the smallest i in [0, n) with
+// cdf[i] - base > target (cdf non-decreasing, target < cdf[n - 1] - base).  Eight-way search: each round loads
+// seven pivots at once, so a draw over 4,096 bins waits on four rounds of
+// loads instead of the twelve dependent loads of a binary search (inside the
+// walk kernels a drawing lane stalls its whole warp for that wait).  The
+// result is the binary search's.
+__device__ __forceinline__ int cdf_search(const uint64_t* cdf, int n, uint64_t target, uint64_t base = 0) {
+  int lo = 0;
+  while (n > 1) {
+    const int step = (n + 7) >> 3;
+    int j = 0;
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      const int m = lo + q * step;  // first index of part q
+      if (m < lo + n && __ldg(reinterpret_cast<const unsigned long long*>(cdf + m - 1)) - base <= target) j = q;
+    }
+    lo += j * step;
+    n = min(step, n - j * step);
+  }
+  return lo;
+}
+
 // The lobe whose weight interval holds target: first i in [a, b) whose
 // prefix sum exceeds base + target (total > 0, target < total).
 __device__ __forceinline__ uint32_t vmf_search(const DGuide& g, const VmfRange& r, uint64_t target) {
-  uint32_t a = r.a, b = r.b - 1;
-  while (a < b) {
-    uint32_t m = (a + b) >> 1;
-    if (ldg64(g.lobe_prefix + m) - r.base > target) b = m; else a = m + 1;
-  }
-  return a;
+  return r.a + (uint32_t)cdf_search(g.lobe_prefix + r.a, (int)(r.b - r.a), target, r.base);
 }
 
 // Draw from the lobe (mu, kappa): t = 1 - mu.w has density
@@ -979,12 +996,7 @@ __device__ __forceinline__ bool draw_dir(const DScene& S, const DGuide* g, const
     uint64_t r = r0.y;
     uint64_t lo = r * total, hi = __umul64hi(r, total);
     uint64_t target = (hi << 32) | (lo >> 32);
-    int a = 0, b = g->bins - 1;
-    while (a < b) {
-      int mid = (a + b) >> 1;
-      uint64_t c = __ldg(reinterpret_cast<const unsigned long long*>(cdf + mid));
-      if (c > target) b = mid; else a = mid + 1;
-    }
+    const int a = cdf_search(cdf, g->bins, target);
     int it = a / g->n_phi, ip = a % g->n_phi;
     float clo = __ldg(g->cos_theta + it), chi = __ldg(g->cos_theta + it + 1);
     float ct = clo + u01(r0.z) * (chi - clo);
