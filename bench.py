@@ -481,7 +481,7 @@ def measured_hbm():
 
 
 PARTS = ("plain", "k3", "k6", "mixed", "adjoint", "vmf", "repeats", "progressive", "selective", "glossy", "mixed_group",
-         "mixed_step",
+         "mixed_step", "stree",
          "configs", "glossy_chains")
 # measured by default beside the headline; "mixed" and "adjoint" are covered
 # by the configuration lines (other_configs) and run only with --part
@@ -1249,7 +1249,7 @@ def part_progressive(ctx, dev, flush, torch, stream, steps):
         return float(((a - b) ** 2).mean().item() / 2)
     for kind in ("histogram", "vmf", "vmf_tree", "vmf_tree_levels"):
         pr = PG.Progressive(ctx, PG.glass_sphere_stages(n=256), total_spp=64, guide=kind.replace("_levels", ""),
-                            device=dev, tree_method=mpg.STREE_LEVELS if kind.endswith("_levels") else None)
+                            device=dev, tree_method=mpg.STREE_LEVELS if kind.endswith("_levels") else mpg.STREE_RECURSIVE)
         pr.run(0)
         ctx.sync()
         if kind.startswith("vmf_tree"):  # tree builds synchronise with the host: timed uncaptured
@@ -1309,6 +1309,9 @@ def run_part(args):
     if args.part == "mixed_step":
         print(json.dumps({"part": args.part, **part_mixed_step(args, dev, torch)}))
         return
+    if args.part == "stree":
+        print(json.dumps({"part": args.part, **part_stree(args, dev, torch)}))
+        return
     print(json.dumps({"part": args.part, **secondary(args, dev, flush, torch, peak, parts=(args.part,))}))
 
 
@@ -1340,6 +1343,41 @@ def part_mixed_step(args, dev, torch):
         ms.append(a.elapsed_time(b))
     ctx.sync()
     return {"chains": wl.B, "ms_per_step_uncaptured": ms}
+
+
+def part_stree(args, dev, torch):
+    """The spatial tree (Sec. 5.6) over the records of one p_0 pass of the
+    glass sphere (n x n points x 16 seeds): the level-by-level device build and
+    the depth-first host build timed, and the query of every chain's leaf."""
+    from paper_2311_12818_gb300 import inputs as I
+    from paper_2311_12818_gb300 import mpg
+    ctx = mpg.Context(dev.index or 0)
+    wl = I.glass_sphere(n=args.n)
+    P = mpg.params_from(wl.params, walk_mode=mpg.WALK_BATCHED, k_uniform=2)
+    sc = mpg.Scene(ctx, wl)
+    ch = mpg.Chains(wl, device=dev)
+    mpg.mpg_sample_seeds(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40)
+    mpg.mpg_manifold_walk(ctx, sc, ch, P)
+    res = mpg.mpg_chain_contribution(ctx, sc, None, ch, P, wl.rng_seed, 1 << 40)
+    rec = mpg.mpg_guide_records(ctx, sc, ch, res.contrib, with_chain=True)
+    ctx.sync()
+    out = {"chains": wl.B, "records": int(rec[6][0].item())}
+    for name, method in (("levels", mpg.STREE_LEVELS), ("recursive", mpg.STREE_RECURSIVE)):
+        ms = []
+        for _ in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = mpg.STree(ctx, ch, rec[5], R=wl.B, R_dev=rec[6], method=method)
+            torch.cuda.synchronize()
+            ms.append((time.perf_counter() - t0) * 1e3)
+        out[name] = {"build_ms": ms, "leaves": tree.n_leaves, "members": tree.n_members}
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    tree.query(ch)
+    b.record()
+    b.synchronize()
+    out["query_ms"] = a.elapsed_time(b)
+    return out
 
 
 def cpu_sample(n=256, spq=16):

@@ -41,6 +41,9 @@ void launch_guide_update(const DGuide& g, const uint32_t* cell, const float* ome
 int rec_tiles(int B);
 // Exclusive scan of a[0..n) in place by one CTA; *total (may be NULL) gets the sum.
 void launch_scan_exclusive(uint32_t* a, int n, int* total, cudaStream_t st);
+// The same over many CTAs for long arrays; sums holds scan_tiles(n) values.
+int scan_tiles(int n);
+void launch_scan_exclusive_tiled(uint32_t* a, int n, uint32_t* sums, cudaStream_t st);
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,
                                   uint32_t* cell_out, float* om_out, float* w_out, uint8_t* k_out, uint8_t* tau_out,
                                   int* chain_out, int* R, cudaStream_t st);

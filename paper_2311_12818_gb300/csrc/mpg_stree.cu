@@ -527,7 +527,7 @@ struct DevLevels {
   cudaError_t e = cudaSuccess;
   float *X = nullptr, *X2 = nullptr;
   int *idx = nullptr, *idx2 = nullptr, *owner = nullptr, *pool = nullptr;
-  uint32_t *f = nullptr, *tie = nullptr, *sel = nullptr;
+  uint32_t *f = nullptr, *tie = nullptr, *sel = nullptr, *scan_sums = nullptr;
   int64_t pool_cap = 0, pool_size = 0;
   std::vector<void*> owned;
   StreeHost* t;
@@ -567,6 +567,7 @@ struct DevLevels {
     f = alloc<uint32_t>(n + 1);
     tie = alloc<uint32_t>(n + 1);
     sel = alloc<uint32_t>(n + 1);
+    scan_sums = alloc<uint32_t>(scan_tiles(n + 1) + 1);
     if (e == cudaSuccess) {
       std::vector<int> iota(n);
       for (int i = 0; i < n; ++i) iota[i] = i;
@@ -611,7 +612,7 @@ struct DevLevels {
     const int g = lv_grid(n);
     if (e == cudaSuccess) {
       k_lv_flags<<<g, LV_THREADS, 0, st>>>(owner, d_sn, X, n, f);
-      launch_scan_exclusive(f, n + 1, nullptr, st);
+      launch_scan_exclusive_tiled(f, n + 1, scan_sums, st);
       k_lv_scatter<<<g, LV_THREADS, 0, st>>>(owner, d_sn, X, idx, f, n, X2, idx2);
       k_lv_nleft<<<lv_grid((int64_t)sn.size()), LV_THREADS, 0, st>>>(d_sn, (int)sn.size(), f, d_nl);
       std::swap(X, X2);
@@ -669,9 +670,9 @@ struct DevLevels {
     }
     if (e == cudaSuccess) {
       k_lv_ties<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, X, n, tie);
-      launch_scan_exclusive(tie, n + 1, nullptr, st);
+      launch_scan_exclusive_tiled(tie, n + 1, scan_sums, st);
       k_lv_sel<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, d_rank, tie, X, n, sel);
-      launch_scan_exclusive(sel, n + 1, nullptr, st);
+      launch_scan_exclusive_tiled(sel, n + 1, scan_sums, st);
       k_lv_write<<<g, LV_THREADS, 0, st>>>(owner, d_sg, d_prefix, d_rank, tie, X, idx, sel, n, pool_size, pool);
     }
     sync();

@@ -58,6 +58,74 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_exclusive(uint32_t* a, in
   if (total && t == SCAN_THREADS - 1) *total = (int)run;
 }
 
+// Exclusive scan of a long array over many CTAs: tiles of SCAN_TILE values,
+// their sums (k_scan_tile_sums), the one-CTA scan of the sums, then every tile
+// scanned with its offset (k_scan_tile_apply).  Loads and stores of a tile go
+// through shared memory, coalesced; the one-CTA kernel above reads a thread's
+// contiguous chunk and is kept for short arrays.
+constexpr int SCAN_TILE_THREADS = 256, SCAN_PER = 16, SCAN_TILE = SCAN_TILE_THREADS * SCAN_PER;
+
+__global__ void __launch_bounds__(SCAN_TILE_THREADS) k_scan_tile_sums(const uint32_t* a, int n, uint32_t* sums) {
+  __shared__ uint32_t ws[SCAN_TILE_THREADS / 32];
+  const int base = blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    const int i = base + j * SCAN_TILE_THREADS + threadIdx.x;
+    if (i < n) s += a[i];
+  }
+  s = __reduce_add_sync(FULL, s);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int w = 0; w < SCAN_TILE_THREADS / 32; ++w) t += ws[w];
+    sums[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_TILE_THREADS) k_scan_tile_apply(uint32_t* a, int n, const uint32_t* offs) {
+  __shared__ uint32_t tile[SCAN_TILE];
+  __shared__ uint32_t ws[SCAN_TILE_THREADS / 32];
+  const int base = blockIdx.x * SCAN_TILE;
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    const int k = j * SCAN_TILE_THREADS + threadIdx.x, i = base + k;
+    tile[k] = i < n ? a[i] : 0u;
+  }
+  __syncthreads();
+  // each thread scans its SCAN_PER consecutive values
+  uint32_t v[SCAN_PER], s = 0;
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    v[j] = tile[threadIdx.x * SCAN_PER + j];
+    s += v[j];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int w = 0; w < wid; ++w) before += ws[w];
+  uint32_t run = offs[blockIdx.x] + before + x - s;
+  __syncthreads();  // every thread has read its values from the tile
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    tile[threadIdx.x * SCAN_PER + j] = run;
+    run += v[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < SCAN_PER; ++j) {
+    const int k = j * SCAN_TILE_THREADS + threadIdx.x, i = base + k;
+    if (i < n) a[i] = tile[k];
+  }
+}
+
 // Exclusive scan of the digit-major tile counts cnt[d * tiles + t] over the
 // tiles that hold records (t < used, the others take no part), by one CTA:
 // the virtual index v = d * used + t runs over 256 * used entries.
@@ -417,6 +485,19 @@ int rec_tiles(int B) { return (B + REC_TILE - 1) / REC_TILE; }
 
 void launch_scan_exclusive(uint32_t* a, int n, int* total, cudaStream_t st) {
   k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(a, n, total);
+}
+
+int scan_tiles(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+void launch_scan_exclusive_tiled(uint32_t* a, int n, uint32_t* sums, cudaStream_t st) {
+  const int tiles = scan_tiles(n);
+  if (tiles <= 1) {
+    k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(a, n, nullptr);
+    return;
+  }
+  k_scan_tile_sums<<<tiles, SCAN_TILE_THREADS, 0, st>>>(a, n, sums);
+  k_scan_exclusive<<<1, SCAN_THREADS, 0, st>>>(sums, tiles, nullptr);
+  k_scan_tile_apply<<<tiles, SCAN_TILE_THREADS, 0, st>>>(a, n, sums);
 }
 
 void launch_guide_records_ordered(const DChains& c, const float* contrib, float inv_area, uint32_t* tile_scratch,

@@ -562,12 +562,14 @@ class STree:
     the records of a pass (their chain indices) over those chains' (x_D, x_L)."""
 
     def __init__(self, ctx, chains, rec_chain, R=None, R_dev=None, epsilon=0.1, c=1.0, method=None, stream=None):
-        """method: STREE_RECURSIVE (host, the default) or STREE_LEVELS (device)."""
+        """method: STREE_LEVELS (level by level on the device, the default: the
+        same tree as the depth-first build, faster in the progressive schedule)
+        or STREE_RECURSIVE (depth first on the host)."""
         self.ctx = ctx
         R = int(rec_chain.numel()) if R is None else R
         h = C.c_void_p()
         cs = chains.struct()
-        method = STREE_RECURSIVE if method is None else method
+        method = STREE_LEVELS if method is None else method
         _check(lib().mpg_stree_build(ctx.h, C.byref(cs), _ptr(rec_chain), R, _ptr(R_dev), epsilon, c, method,
                                      C.byref(h), _stream(stream)))
         self._adopt(h)

@@ -32,9 +32,10 @@ class Progressive:
         'vmf_tree' (the vMF mixture over the leaves of a spatial tree of each
         iteration's samples, Sec. 5.6; its build is synchronous -- the host
         decides the tree's nodes -- so that schedule is not recorded as a
-        graph).  tree_method: mpg.STREE_RECURSIVE (depth first on the host,
-        the default) or mpg.STREE_LEVELS (level by level on the device)."""
-        self.tree_method = mpg.STREE_RECURSIVE if tree_method is None else tree_method
+        graph).  tree_method: mpg.STREE_LEVELS (level by level on the device,
+        the default) or mpg.STREE_RECURSIVE (depth first on the host): the
+        same tree."""
+        self.tree_method = mpg.STREE_LEVELS if tree_method is None else tree_method
         if guide not in ("histogram", "vmf", "vmf_tree"):
             raise ValueError("guide must be 'histogram', 'vmf' or 'vmf_tree'")
         self.ctx, self.kind = ctx, guide
