@@ -303,6 +303,12 @@ def run_ours(args, rank, world, local):
         ms, n = ctx.profile(k)
         st = ctx.stats(k)
         fam[name] = dict(ms=ms, launches=n, stats=st, flops=algorithmic_flops(st, F))
+    # first walks alone: one more uncaptured step, its statuses read after the walk
+    c0, bf0 = ctxs[0], bufs[0]
+    mpg.mpg_sample_seeds(c0, bf0["sc"], guide, bf0["ch"], P, wl.rng_seed, off + 7777 * B * world)
+    mpg.mpg_manifold_walk(c0, bf0["sc"], bf0["ch"], P)
+    c0.sync()
+    primary_per_step = int((bf0["ch"].status == 1).sum().item())
 
     # ---- end to end through the public API with host buffers
     pin = lambda a: torch.as_tensor(a).pin_memory()  # noqa: E731
@@ -382,6 +388,8 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "detail": {"irradiance_throughput": irr,
                    "converged_per_step": conv / steps_run, "walks_per_step": total["walks"] / steps_run,
+                   "primary_converged_per_step": primary_per_step,
+                   "primary_converged_walks_per_s": world * primary_per_step * steps_run / (t_ms * 1e-3),
                    "trials_per_step": total["trials"] / steps_run,
                    "fp64_geometry_terms_per_step": total["ggt_fp64"] / steps_run,
                    "step_ms": [round(x, 4) for x in step_ms],
