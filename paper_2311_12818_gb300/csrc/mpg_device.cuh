@@ -1093,14 +1093,6 @@ __device__ __forceinline__ bool segment_clear(const DScene& S, float3 a, float3 
   return h.surf < 0;
 }
 
-// Admissibility, G (IFT; FP64 determinant for K >= 6), kappa.  Returns false
-// for an inadmissible chain.
-// Admissibility, G (implicit function theorem) and kappa in FP32.  G is
-// formed twice from one 4-column Thomas sweep: X_L = cos_D |det d(w_D)/d(u_L)|
-// (light end moved) and X_D = |det d(w_L)/d(u_D)| (receiver moved).  By
-// reciprocity eta_D^2 X_L = eta_L^2 |n_L.w_L| X_D, so their relative mismatch
-// estimates the FP32 error of G (out: mismatch); cmax (out) is the chain's
-// FP32 residual.  Returns false for an inadmissible chain.
 // Admissibility of a converged chain: every vertex type matches the sides of
 // its neighbours (refraction crosses the surface, reflection stays on one
 // side), the receiver and an area light face the chain, and every segment is
@@ -1130,6 +1122,14 @@ __device__ __forceinline__ bool admissible(const DScene& S, const Chain<K>& ch, 
   return true;
 }
 
+// Admissibility, G (implicit function theorem) and kappa in FP32.  G is
+// formed twice from one Thomas sweep (with the remaining Newton step as a
+// fifth column): X_L = cos_D |det d(w_D)/d(u_L)| (light end moved) and
+// X_D = |det d(w_L)/d(u_D)| (receiver moved).  By reciprocity
+// eta_D^2 X_L = eta_L^2 |n_L.w_L| X_D, so their relative mismatch estimates
+// the FP32 error of G (out: mismatch; on heightfield chains the determinant's
+// conditioning instead, see below); cmax (out) is the chain's FP32 residual.
+// Returns false for an inadmissible chain.
 template <int K, bool kStats>
 __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e, const mpg_params& P, float& G,
                              float& kappa, float& mismatch, float& cmax, float& kappa_err, float& step_err, int* err,
@@ -1169,7 +1169,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
     dmin = fminf(dmin, len((i == K - 1 ? e.xL : ch.x[i + 1]) - ch.x[i]));
   }
   const float dir_err = 2.0f * sqrtf(dx2) / fmaxf(dmin, 1e-30f);
-  float X[2];
+  float X[2], cond[2];
 #pragma unroll
   for (int side = 0; side < 2; ++side) {
     int vi = side == 0 ? 0 : K - 1;
@@ -1188,6 +1188,7 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
       M[1][c] = dot(b, dw);
     }
     X[side] = fabsf(M[0][0] * M[1][1] - M[0][1] * M[1][0]);
+    cond[side] = (fabsf(M[0][0] * M[1][1]) + fabsf(M[0][1] * M[1][0])) / fmaxf(X[side], 1e-30f);
   }
   float XL = cosD * X[0], XD = X[1];
   float3 nl = point ? cross(S.L.exu, S.L.eyu) : S.L.n;
@@ -1196,6 +1197,16 @@ __device__ bool contribution(const DScene& S, const Chain<K>& ch, const Ends& e,
   float XDs = rc * XD;
   mismatch = fabsf(XL - XDs) / fmaxf(fmaxf(XL, XDs), 1e-30f);
   G = point ? XD : XL;
+  // With interpolated shading normals (heightfield vertices) the normal field
+  // is not the surface's, the two ends' terms are not reciprocal, and their
+  // mismatch (1e-4 to 1e-3 on the water scene) measures the interpolation
+  // rather than rounding.  There the estimate is the cancellation in the
+  // determinant instead: entries good to about 1e-6 relative after the
+  // solve, times (|m00 m11| + |m01 m10|) / |det m|.
+  bool shading = false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) shading = shading || S.s[ch.surf[i]].type == SURF_HEIGHTFIELD;
+  if (shading) mismatch = 1e-6f * cond[point ? 1 : 0];
   // kappa: mirror 1; dielectric R -> F, T -> (1 - F)(eta_i/eta_o)^2 under an
   // area light, T -> (1 - F) under a point light (G maps the intensity's solid
   // angle onto receiver area, so flux carries no radiance scaling).  The
