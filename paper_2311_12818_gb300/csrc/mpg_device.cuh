@@ -186,8 +186,12 @@ __device__ __forceinline__ bool tri_hit(float3 o, float3 d, float3 v0, float3 e1
   return t > tmin && t < tmax;
 }
 
+// Kept out of line: inlined into every ray cast it made the kernels that
+// cast rays over analytic scenes too large for the instruction cache (the
+// mixed batch's one-launch seed kernel took 4.1 ms per step inlined, 1.4 ms
+// out of line; the water scene's BVH-heavy kernels pay the calls, about 8 %).
 template <bool kStats>
-__device__ __forceinline__ void hf_intersect(const DHF& H, float3 o, float3 d, float tmin, float& tbest,
+__device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, float tmin, float& tbest,
                                              Hit& best, int* err, Counters& cnt) {
   float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
   int stack[BVH_STACK];
