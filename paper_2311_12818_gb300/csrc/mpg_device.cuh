@@ -802,7 +802,7 @@ struct VmfRange {
   uint32_t cs, a, b;
   uint64_t base, total;
 };
-__device__ __forceinline__ VmfRange vmf_range(const DGuide& g, uint32_t cell, uint32_t klo, uint32_t khi) {
+static __device__ __noinline__ VmfRange vmf_range(const DGuide& g, uint32_t cell, uint32_t klo, uint32_t khi) {
   VmfRange r;
   r.cs = __ldg(g.cell_start + cell);
   uint32_t ce = __ldg(g.cell_start + cell + 1);
@@ -835,16 +835,19 @@ __device__ __forceinline__ int cdf_search(const uint64_t* cdf, int n, uint64_t t
   return lo;
 }
 
+// The vMF guide's pieces of a seed draw (vmf_range, vmf_search, vmf_sample,
+// vmf_mix_pdf) are kept out of line, like the BVH traversal: they run only
+// with a vMF guide, and inlined they enlarge every kernel that draws seeds.
 // The lobe whose weight interval holds target: first i in [a, b) whose
 // prefix sum exceeds base + target (total > 0, target < total).
-__device__ __forceinline__ uint32_t vmf_search(const DGuide& g, const VmfRange& r, uint64_t target) {
+static __device__ __noinline__ uint32_t vmf_search(const DGuide& g, const VmfRange& r, uint64_t target) {
   return r.a + (uint32_t)cdf_search(g.lobe_prefix + r.a, (int)(r.b - r.a), target, r.base);
 }
 
 // Draw from the lobe (mu, kappa): t = 1 - mu.w has density
 // kappa e^{-kappa t} / (1 - e^{-2 kappa}) on [0, 2], inverted with u1 in
 // (0, 1]; the azimuth 2 pi u2 is taken in the Duff et al. frame of mu.
-__device__ __forceinline__ float3 vmf_sample(float4 L, float u1, float u2) {
+static __device__ __noinline__ float3 vmf_sample(float4 L, float u1, float u2) {
   float3 mu = make_float3(L.x, L.y, L.z);
   float t = -logf(fmaf(1.0f - u1, expf(-2.0f * L.w), u1)) / L.w;
   t = fminf(fmaxf(t, 0.0f), 2.0f);
