@@ -952,7 +952,9 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
     step draws n from alpha P_0 + (1 - alpha) P_e(n | cell) and (w_D, tau)
     from alpha p_0 + (1 - alpha) p_e, walks and forms the contributions with
     Bernoulli trials from the same mixture.  Both steps replay captured
-    graphs with the library's default schedule."""
+    graphs, each with the schedule the library's autotuner picks for it (the
+    default schedule walks every length in the one-thread form, which at k >= 3
+    takes about three times as long on this batch)."""
     import numpy as np
     from paper_2311_12818_gb300 import inputs as I
     from paper_2311_12818_gb300 import mpg
@@ -990,14 +992,17 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
 
     def measure(guided):
         ch, res = (chv, resv) if guided else (ch0, res0)
+        gg = g if guided else None
+        if guided:
+            mpg.mpg_sample_lengths(ctx, g, ch, p0w, P, wl.rng_seed, 0, out=(ch.k, ch.pn))
+        Ps, _ = mpg.mpg_autotune(ctx, sc, gg, ch, P, wl.rng_seed, 1 << 45, repeats=1)
 
         def step(o, s=None):
-            gg = g if guided else None
             if guided:
-                mpg.mpg_sample_lengths(ctx, g, ch, p0w, P, wl.rng_seed, o, out=(ch.k, ch.pn), stream=s)
-            mpg.mpg_sample_seeds(ctx, sc, gg, ch, P, wl.rng_seed, o, stream=s)
-            mpg.mpg_manifold_walk(ctx, sc, ch, P, stream=s)
-            mpg.mpg_chain_contribution(ctx, sc, gg, ch, P, wl.rng_seed, o, out=res, stream=s)
+                mpg.mpg_sample_lengths(ctx, g, ch, p0w, Ps, wl.rng_seed, o, out=(ch.k, ch.pn), stream=s)
+            mpg.mpg_sample_seeds(ctx, sc, gg, ch, Ps, wl.rng_seed, o, stream=s)
+            mpg.mpg_manifold_walk(ctx, sc, ch, Ps, stream=s)
+            mpg.mpg_chain_contribution(ctx, sc, gg, ch, Ps, wl.rng_seed, o, out=res, stream=s)
         step(0)
         torch.cuda.synchronize()
         gr = mpg.Graph(ctx, rng_advance=wl.B)
@@ -1025,7 +1030,8 @@ def part_vmf(ctx, dev, flush, torch, stream, steps, F, peak_fp32):
                 "admissible_per_step": adm, "capped_per_step": int(res.capped.sum().item()),
                 "mean_E": float(res.E.double().mean().item()),
                 "mean_E_std_err": float(res.E.double().std().item() / np.sqrt(wl.Q)),
-                "graph_kernels": gr.kernels(), "family_ms_uncaptured": fam}
+                "graph_kernels": gr.kernels(), "family_ms_uncaptured": fam,
+                "schedule": {f: getattr(Ps, f) for f in mpg.SCHEDULE_FIELDS}}
     out["p0_step"] = measure(False)
     out["vmf_step"] = measure(True)
     out["admissible_chains_per_ms"] = {k: out[k]["admissible_per_step"] / out[k]["ms_per_step"]

@@ -307,8 +307,12 @@ __device__ __forceinline__ float3 hit_point(const DScene& S, float3 o, float3 d,
 // ---------------------------------------------------------------------------
 // Local frames
 // ---------------------------------------------------------------------------
+// Unit shading normal n, tangent basis (dpdu, dpdv) of the surface, and the
+// shape operator in the constraint's frame (s, t) = onb(n): W = (s.dn/du,
+// s.dn/dv, t.dn/du, t.dn/dv), row-major.
 struct Frame {
-  float3 n, dpdu, dpdv, dndu, dndv;
+  float3 n, dpdu, dpdv;
+  float4 W;
 };
 
 // Unit shading normal only (constraint-only evaluations).
@@ -327,16 +331,15 @@ __device__ __forceinline__ Frame vertex_frame(const DScene& S, int surf, int pri
   Frame f;
   const DSurf& sf = S.s[surf];
   if (sf.type == SURF_SPHERE || sf.type == SURF_CAP) {
+    // (dpdu, dpdv) = (s, t) and dn = da / r: W = I / r
     f.n = unit(p - sf.c);
     onb(f.n, f.dpdu, f.dpdv);
     float ir = 1.0f / sf.r;
-    f.dndu = f.dpdu * ir;
-    f.dndv = f.dpdv * ir;
+    f.W = make_float4(ir, 0.f, 0.f, ir);
   } else if (sf.type == SURF_RECT) {
     f.n = sf.axis;
     onb(f.n, f.dpdu, f.dpdv);
-    f.dndu = make_float3(0.f, 0.f, 0.f);
-    f.dndv = f.dndu;
+    f.W = make_float4(0.f, 0.f, 0.f, 0.f);
   } else {
     // n = normalize(sum b_j N_j); a tangent move a changes the barycentrics by
     // the solution of a = db1 e1 + db2 e2.
@@ -353,6 +356,8 @@ __device__ __forceinline__ Frame vertex_frame(const DScene& S, int surf, int pri
     float g11 = dot(e1, e1), g12 = dot(e1, e2), g22 = dot(e2, e2);
     float igd = 1.0f / (g11 * g22 - g12 * g12);
     float3 dN1 = N1 - N0, dN2 = N2 - N0;
+    float3 s, t;
+    onb(f.n, s, t);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       float3 a = q == 0 ? f.dpdu : f.dpdv;
@@ -360,7 +365,8 @@ __device__ __forceinline__ Frame vertex_frame(const DScene& S, int surf, int pri
       float db1 = (g22 * r1 - g12 * r2) * igd, db2 = (g11 * r2 - g12 * r1) * igd;
       float3 dN = dN1 * db1 + dN2 * db2;
       float3 dn = (dN - f.n * dot(f.n, dN)) * il;
-      if (q == 0) f.dndu = dn; else f.dndv = dn;
+      if (q == 0) { f.W.x = dot(s, dn); f.W.z = dot(t, dn); }
+      else { f.W.y = dot(s, dn); f.W.w = dot(t, dn); }
     }
   }
   return f;
@@ -425,21 +431,30 @@ __device__ __forceinline__ bool vertex_blocks(float3 xp, float3 tpu, float3 tpv,
   // The derivative of C along dh is (s.dh, t.dh) with dh = (I - h h^T) dht / L;
   // fold the projection into the row vectors: s' = (s - h (h.s)) / L.
   float3 sp = (s - h * o.C.x) * iL, tp = (t - h * o.C.y) * iL;
-  // d(w)/d(y) a = (a - w (w.a)) / d for w = (y - x)/|y - x|.
-  auto Pi = [&](float3 a) { return (a - wi * dot(wi, a)) * idi; };
-  auto Po = [&](float3 a) { return (a - wo * dot(wo, a)) * ido; };
-  float3 piu = Pi(f.dpdu) * o.ei, piv = Pi(f.dpdv) * o.ei;
-  float3 pou = Po(f.dpdu) * o.eo, pov = Po(f.dpdv) * o.eo;
-  float3 bu = -(piu + pou), bv = -(piv + pov);
-  o.B = make_float4(dot(sp, bu) - hn * dot(s, f.dndu), dot(sp, bv) - hn * dot(s, f.dndv),
-                    dot(tp, bu) - hn * dot(t, f.dndu), dot(tp, bv) - hn * dot(t, f.dndv));
+  // d(w)/d(y) a = (a - w (w.a)) / d for w = (y - x)/|y - x|, so moving x_{i-1}
+  // by a changes ht by ei (a - wi (wi.a)) / di, and a row r of the derivative
+  // gives r.dht = ai (r.a) - ai (r.wi) (wi.a) with ai = ei / di (likewise
+  // ao = eo / dO for x_{i+1}); moving x itself changes ht by minus both.  The
+  // blocks are formed from these dot products, the scale factors kept scalar.
+  const float ai = o.ei * idi, ao = o.eo * ido, aa = ai + ao;
+  const float spi = ai * dot(sp, wi), tpi = ai * dot(tp, wi);
+  const float spo = ao * dot(sp, wo), tpo = ao * dot(tp, wo);
+  {
+    const float wiu = dot(wi, f.dpdu), wiv = dot(wi, f.dpdv), wou = dot(wo, f.dpdu), wov = dot(wo, f.dpdv);
+    o.B = make_float4(fmaf(spi, wiu, fmaf(spo, wou, -aa * dot(sp, f.dpdu))) - hn * f.W.x,
+                      fmaf(spi, wiv, fmaf(spo, wov, -aa * dot(sp, f.dpdv))) - hn * f.W.y,
+                      fmaf(tpi, wiu, fmaf(tpo, wou, -aa * dot(tp, f.dpdu))) - hn * f.W.z,
+                      fmaf(tpi, wiv, fmaf(tpo, wov, -aa * dot(tp, f.dpdv))) - hn * f.W.w);
+  }
   if (want_a) {
-    float3 au = Pi(tpu) * o.ei, av = Pi(tpv) * o.ei;
-    o.A = make_float4(dot(sp, au), dot(sp, av), dot(tp, au), dot(tp, av));
+    const float wiu = dot(wi, tpu), wiv = dot(wi, tpv);
+    o.A = make_float4(fmaf(ai, dot(sp, tpu), -spi * wiu), fmaf(ai, dot(sp, tpv), -spi * wiv),
+                      fmaf(ai, dot(tp, tpu), -tpi * wiu), fmaf(ai, dot(tp, tpv), -tpi * wiv));
   }
   if (want_c) {
-    float3 cu = Po(tnu) * o.eo, cv = Po(tnv) * o.eo;
-    o.Cc = make_float4(dot(sp, cu), dot(sp, cv), dot(tp, cu), dot(tp, cv));
+    const float wou = dot(wo, tnu), wov = dot(wo, tnv);
+    o.Cc = make_float4(fmaf(ao, dot(sp, tnu), -spo * wou), fmaf(ao, dot(sp, tnv), -spo * wov),
+                       fmaf(ao, dot(tp, tnu), -tpo * wou), fmaf(ao, dot(tp, tnv), -tpo * wov));
   }
   return true;
 }
