@@ -71,6 +71,23 @@ struct DScene {
   DLight L;
 };
 
+// The scene copied to shared memory at the start of a walk kernel.  The walk
+// indexes the surface table by each lane's own surface id; read from the
+// kernel's parameter (constant) space, such loads are served one distinct
+// address of the warp at a time, from shared memory in one pass (bank
+// conflicts apart).  The walk kernels (persistent, or one long walk loop per
+// thread) use it; the short seed and contribution kernels and the adjoint,
+// launched over many blocks, read the parameter space directly (there the
+// copy per block cost more than it saved).  Every thread of the block must
+// call it, before any thread returns.
+__device__ __forceinline__ const DScene& scene_in_smem(const DScene& S, DScene& sm) {
+  static_assert(sizeof(DScene) % 4 == 0, "copied as 32-bit words");
+  for (int i = threadIdx.x; i < (int)(sizeof(DScene) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&sm)[i] = reinterpret_cast<const int*>(&S)[i];
+  __syncthreads();
+  return sm;
+}
+
 struct DGuide {
   int n_cells, n_theta, n_phi, bins;
   const uint64_t* counts;

@@ -144,8 +144,10 @@ __device__ __forceinline__ long long take_item64(bool want, unsigned long long* 
 // Walk (K2): one lane per chain, refilled from the bucket's queue.
 // ---------------------------------------------------------------------------
 template <int K, bool kS>
-__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_walk_p(const __grid_constant__ DScene S_, DChains c, DWork w, mpg_params P,
                                                 DCtx ctx, int* queue) {
+  __shared__ DScene s_scene;
+  const DScene& S = scene_in_smem(S_, s_scene);
   Tally t = {};
   const int n = n_items<K>(w, c);
   WalkLane<K> L;
@@ -289,8 +291,10 @@ __device__ __forceinline__ int walk_pass_g_fused(const DScene& S, GroupLane<K>& 
 }
 
 template <int K, int G, bool kS>
-__global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
+__global__ void __launch_bounds__(128) k_walk_g(const __grid_constant__ DScene S_, DChains c, DWork w, mpg_params P,
                                                 DCtx ctx, int* queue) {
+  __shared__ DScene s_scene;
+  const DScene& S = scene_in_smem(S_, s_scene);
   static_assert(G >= K && G <= 32 && (G & (G - 1)) == 0, "group of a power of two >= K lanes");
   constexpr int NG = 128 / G;
   __shared__ float2 sC[NG][K];
@@ -520,10 +524,12 @@ __device__ __forceinline__ long long bern_pool_take(bool want, long long* pool, 
 }
 
 template <int K, bool kS>
-__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __grid_constant__ DScene S, DGuide g, int has_guide,
+__global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __grid_constant__ DScene S_, DGuide g, int has_guide,
                                                     DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
                                                     int* queue, const int* list, const int* n_list, const int* base,
                                                     unsigned* nbest, int t0, int TB, DPairs pr) {
+  __shared__ DScene s_scene;
+  const DScene& S = scene_in_smem(S_, s_scene);
   __shared__ long long pools[4][32];
   Tally t = {};
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
@@ -600,10 +606,12 @@ __global__ void __launch_bounds__(128, walk_min_ctas<K>()) k_bern_round(const __
 // and the same-solution test is taken per vertex in FP64 and combined over the
 // group -- the decisions of k_bern_round.
 template <int K, int G, bool kS>
-__global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DScene S, DGuide g, int has_guide,
+__global__ void __launch_bounds__(128) k_bern_round_g(const __grid_constant__ DScene S_, DGuide g, int has_guide,
                                                       DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx,
                                                       int* queue, const int* list, const int* n_list, const int* base,
                                                       unsigned* nbest, int t0, int TB, DPairs pr) {
+  __shared__ DScene s_scene;
+  const DScene& S = scene_in_smem(S_, s_scene);
   static_assert(G >= K && G <= 32 && (G & (G - 1)) == 0, "group of a power of two >= K lanes");
   constexpr int NG = 128 / G;
   __shared__ float2 sC[NG][K];
