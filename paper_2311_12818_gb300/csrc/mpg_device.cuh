@@ -75,11 +75,12 @@ struct DScene {
 // indexes the surface table by each lane's own surface id; read from the
 // kernel's parameter (constant) space, such loads are served one distinct
 // address of the warp at a time, from shared memory in one pass (bank
-// conflicts apart).  The walk kernels (persistent, or one long walk loop per
-// thread) use it; the short seed and contribution kernels and the adjoint,
-// launched over many blocks, read the parameter space directly (there the
-// copy per block cost more than it saved).  Every thread of the block must
-// call it, before any thread returns.
+// conflicts apart).  The persistent kernels of the batched mode (a few
+// blocks per SM) use it; the kernels launched with one block per 128 chains
+// (seeds, contributions, the adjoint and the plain mode's walk and trial
+// loops) read the parameter space directly: there the copy per block cost
+// more than it saved.  Every thread of the block must call it, before any
+// thread returns.
 __device__ __forceinline__ const DScene& scene_in_smem(const DScene& S, DScene& sm) {
   static_assert(sizeof(DScene) % 4 == 0, "copied as 32-bit words");
   for (int i = threadIdx.x; i < (int)(sizeof(DScene) / 4); i += blockDim.x)

@@ -135,10 +135,8 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
 
 // kOff: glossy chains, walked to C_i = o_i with the chain's offset normals.
 template <int K, bool kS, bool kOff>
-__global__ void __launch_bounds__(128) k_walk(const __grid_constant__ DScene S_, DChains c, DWork w, mpg_params P,
+__global__ void __launch_bounds__(128) k_walk(const __grid_constant__ DScene S, DChains c, DWork w, mpg_params P,
                                               DCtx ctx) {
-  __shared__ DScene s_scene;
-  const DScene& S = scene_in_smem(S_, s_scene);
   Tally t = {};
   const int n = n_items<K>(w, c);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -335,11 +333,9 @@ __global__ void __launch_bounds__(64) k_glossy(const __grid_constant__ DScene S,
 // kOff: glossy chains; every trial is walked with the chain's own offset
 // normals, so N estimates the reciprocal probability given the offsets.
 template <int K, bool kS, bool kOff>
-__global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S_, DGuide g, int has_guide,
+__global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                    DChains c, DWork w, uint2 key, uint64_t offset, mpg_params P,
                                                    DOut o, DCtx ctx) {
-  __shared__ DScene s_scene;
-  const DScene& S = scene_in_smem(S_, s_scene);
   Tally t = {};
   const int n = n_items<K>(w, c);
   const double eps2 = (double)P.dedup_eps * (double)P.dedup_eps;
