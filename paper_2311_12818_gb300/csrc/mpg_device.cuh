@@ -254,7 +254,10 @@ __device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, floa
   }
 }
 
-template <bool kStats>
+// kHF: the scene may hold heightfields.  Without them the BVH branch and its
+// call are compiled out: the call alone costs a kernel its register budget
+// (the plain mode's trial loop went from 168 registers to 128 and spills).
+template <bool kStats, bool kHF = true>
 __device__ Hit intersect(const DScene& S, float3 o, float3 d, float tmin, float tmax, int* err, Counters& cnt) {
   Hit best;
   best.t = -1.0f; best.surf = -1; best.prim = -1; best.b1 = best.b2 = 0.0f;
@@ -286,7 +289,7 @@ __device__ Hit intersect(const DScene& S, float3 o, float3 d, float tmin, float 
       float3 q = o + d * t - sf.c;
       if (fabsf(dot(q, sf.ex)) > sf.ex2 || fabsf(dot(q, sf.ey)) > sf.ey2) continue;
       tbest = t; best.t = t; best.surf = s; best.prim = -1;
-    } else {
+    } else if (kHF) {
       hf_intersect<kStats>(S.hf[sf.hf], o, d, tmin, tbest, best, err, cnt);
     }
   }
@@ -1080,7 +1083,7 @@ __device__ __forceinline__ bool draw_dir(const DScene& S, const DGuide* g, const
 // (vMF guide), the sum over the lobes is not formed here: pdf gets the p_0
 // part alone and defer what the caller needs to add (1 - alpha)
 // vmf_sum_warp(...) to it.
-template <int K, bool kStats>
+template <int K, bool kStats, bool kHF = true>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
                           Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
@@ -1093,7 +1096,7 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   float3 o = e.xD, d = w;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    Hit h = intersect<kStats>(S, o, d, P.ray_eps, 3.0e38f, err, cnt);
+    Hit h = intersect<kStats, kHF>(S, o, d, P.ray_eps, 3.0e38f, err, cnt);
     if (h.surf < 0) return false;
     ch.x[i] = hit_point(S, o, d, h);
     ch.surf[i] = h.surf;

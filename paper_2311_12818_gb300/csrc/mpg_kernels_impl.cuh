@@ -87,7 +87,8 @@ __device__ __forceinline__ int n_items(const DWork& w, const DChains& c) {
   return w.order ? w.count[K] : c.B;
 }
 
-template <int K, bool kS>
+// kHF: the scene may hold heightfields (intersect's BVH branch compiled in).
+template <int K, bool kS, bool kHF>
 __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, DGuide g, int has_guide, DChains c,
                                               DWork w, uint2 key, uint64_t offset, mpg_params P, DCtx ctx) {
   Tally t = {};
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
     bool ok = false;
     if (b >= 0) {
       Ends e = load_ends(c, b);
-      ok = draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0, key,
+      ok = draw_seed<K, kS, kHF>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0, key,
                             (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c, true, false,
                             vmf ? &df : nullptr);
     }
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(64) k_glossy(const __grid_constant__ DScene S,
 
 // kOff: glossy chains; every trial is walked with the chain's own offset
 // normals, so N estimates the reciprocal probability given the offsets.
-template <int K, bool kS, bool kOff>
+template <int K, bool kS, bool kOff, bool kHF>
 __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                    DChains c, DWork w, uint2 key, uint64_t offset, mpg_params P,
                                                    DOut o, DCtx ctx) {
@@ -361,7 +362,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
           uint32_t tau;
           float pdf;
           Ends et = e;
-          if (!draw_seed<K, kS>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
+          if (!draw_seed<K, kS, kHF>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
                                 (uint64_t)b + offset, (uint32_t)tr | ((uint32_t)rep << 24), P, ch, tau, pdf, ctx.err,
                                 t.c, false, true))
             continue;
@@ -465,7 +466,8 @@ template <int K>
 void KLaunch<K>::seed(bool stats, const DScene& S, const DGuide* g, const DChains& c, DWork w, uint2 key,
                       uint64_t offset, const mpg_params& P, DCtx ctx, int grid, int block, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  kern::k_seed<K, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
+  if (S.n_hf > 0) kern::k_seed<K, true, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
+  else kern::k_seed<K, true, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, ctx);
 }
 
 template <int K>
@@ -492,17 +494,24 @@ void KLaunch<K>::bernoulli(bool stats, const DScene& S, const DGuide* g, const D
                            uint64_t offset, const mpg_params& P, DOut o, DCtx ctx, int grid, int block,
                            cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (c.offset) kern::k_bernoulli<K, true, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
-  else kern::k_bernoulli<K, true, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  const bool hf = S.n_hf > 0;
+  if (c.offset && hf)
+    kern::k_bernoulli<K, true, true, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  else if (c.offset)
+    kern::k_bernoulli<K, true, true, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  else if (hf)
+    kern::k_bernoulli<K, true, false, true><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
+  else
+    kern::k_bernoulli<K, true, false, false><<<grid, block, 0, st>>>(S, gg, g != nullptr, c, w, key, offset, P, o, ctx);
 }
 
 template <int K>
 int KLaunch<K>::blocks_per_sm(int which, bool stats, int block) {
   const void* fn;
-  if (which == 0) fn = (const void*)kern::k_seed<K, true>;
+  if (which == 0) fn = (const void*)kern::k_seed<K, true, true>;
   else if (which == 1) fn = (const void*)kern::k_walk<K, true, false>;
   else if (which == 2) fn = (const void*)kern::k_contrib<K, true>;
-  else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true, false>;
+  else if (which == 3) fn = (const void*)kern::k_bernoulli<K, true, false, true>;
   else if (which == 4) fn = (const void*)kern::k_walk_p<K, true>;
   else if (which == 5) fn = (const void*)kern::k_trial_seed<K, true>;
   else if (which == 7) {
