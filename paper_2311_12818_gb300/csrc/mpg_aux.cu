@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(128) k_trace(const __grid_constant__ DScene S,
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float3 oo = make_float3(o[i], o[n + i], o[2 * (size_t)n + i]);
     float3 dd = unit(make_float3(d[i], d[n + i], d[2 * (size_t)n + i]));
-    Hit h = intersect<kS>(S, oo, dd, tmin, tmax, err, cnt);
+    Hit h = intersect<kS, BVH_INLINE>(S, oo, dd, tmin, tmax, err, cnt);
     t[i] = h.surf >= 0 ? h.t : -1.0f;
     surf[i] = h.surf;
     prim[i] = h.prim;

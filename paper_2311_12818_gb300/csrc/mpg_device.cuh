@@ -204,13 +204,10 @@ __device__ __forceinline__ bool tri_hit(float3 o, float3 d, float3 v0, float3 e1
   return t > tmin && t < tmax;
 }
 
-// Kept out of line: inlined into every ray cast it made the kernels that
-// cast rays over analytic scenes too large for the instruction cache (the
-// mixed batch's one-launch seed kernel took 4.1 ms per step inlined, 1.4 ms
-// out of line; the water scene's BVH-heavy kernels pay the calls, about 8 %).
+// BVH traversal of a heightfield's triangles (closest hit below tbest).
 template <bool kStats>
-__device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, float tmin, float& tbest,
-                                             Hit& best, int* err, Counters& cnt) {
+__device__ __forceinline__ void hf_traverse(const DHF& H, float3 o, float3 d, float tmin, float& tbest, Hit& best,
+                                            int* err, Counters& cnt) {
   float3 inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
   int stack[BVH_STACK];
   int sp = 0;
@@ -254,10 +251,25 @@ __device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, floa
   }
 }
 
-// kHF: the scene may hold heightfields.  Without them the BVH branch and its
-// call are compiled out: the call alone costs a kernel its register budget
-// (the plain mode's trial loop went from 168 registers to 128 and spills).
-template <bool kStats, bool kHF = true>
+// The traversal kept out of line: inlined into every ray cast it made the
+// kernels that cast rays over analytic scenes too large for the instruction
+// cache (the mixed batch's one-launch seed kernel took 4.1 ms per step
+// inlined, 1.4 ms out of line; the water scene's BVH-heavy kernels pay the
+// calls, about 8 %).
+template <bool kStats>
+__device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, float tmin, float& tbest, Hit& best,
+                                          int* err, Counters& cnt) {
+  hf_traverse<kStats>(H, o, d, tmin, tbest, best, err, cnt);
+}
+
+// How a ray cast reaches the heightfields' BVHs: BVH_NONE, the scene holds
+// none (the branch compiled out; a call alone costs a kernel registers: the
+// plain mode's trial loop has 168 registers without it, 128 and spills with
+// it); BVH_CALL, the out-of-line traversal; BVH_INLINE, the traversal inlined
+// (the ray-batch kernel, whose loop is the traversal).
+enum { BVH_NONE = 0, BVH_CALL = 1, BVH_INLINE = 2 };
+
+template <bool kStats, int kBVH = BVH_CALL>
 __device__ Hit intersect(const DScene& S, float3 o, float3 d, float tmin, float tmax, int* err, Counters& cnt) {
   Hit best;
   best.t = -1.0f; best.surf = -1; best.prim = -1; best.b1 = best.b2 = 0.0f;
@@ -289,8 +301,10 @@ __device__ Hit intersect(const DScene& S, float3 o, float3 d, float tmin, float 
       float3 q = o + d * t - sf.c;
       if (fabsf(dot(q, sf.ex)) > sf.ex2 || fabsf(dot(q, sf.ey)) > sf.ey2) continue;
       tbest = t; best.t = t; best.surf = s; best.prim = -1;
-    } else if (kHF) {
+    } else if (kBVH == BVH_CALL) {
       hf_intersect<kStats>(S.hf[sf.hf], o, d, tmin, tbest, best, err, cnt);
+    } else if (kBVH == BVH_INLINE) {
+      hf_traverse<kStats>(S.hf[sf.hf], o, d, tmin, tbest, best, err, cnt);
     }
   }
   return best;
@@ -1083,7 +1097,7 @@ __device__ __forceinline__ bool draw_dir(const DScene& S, const DGuide* g, const
 // (vMF guide), the sum over the lobes is not formed here: pdf gets the p_0
 // part alone and defer what the caller needs to add (1 - alpha)
 // vmf_sum_warp(...) to it.
-template <int K, bool kStats, bool kHF = true>
+template <int K, bool kStats, int kBVH = BVH_CALL>
 __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint32_t cell, uint32_t tau_in,
                           bool tau_random, uint2 key, uint64_t idx, uint32_t trial, const mpg_params& P,
                           Chain<K>& ch, uint32_t& tau_out, float& pdf, int* err, Counters& cnt,
@@ -1096,7 +1110,7 @@ __device__ bool draw_seed(const DScene& S, const DGuide* g, const Ends& e, uint3
   float3 o = e.xD, d = w;
 #pragma unroll
   for (int i = 0; i < K; ++i) {
-    Hit h = intersect<kStats, kHF>(S, o, d, P.ray_eps, 3.0e38f, err, cnt);
+    Hit h = intersect<kStats, kBVH>(S, o, d, P.ray_eps, 3.0e38f, err, cnt);
     if (h.surf < 0) return false;
     ch.x[i] = hit_point(S, o, d, h);
     ch.surf[i] = h.surf;

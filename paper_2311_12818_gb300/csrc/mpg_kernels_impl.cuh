@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(128) k_seed(const __grid_constant__ DScene S, 
     bool ok = false;
     if (b >= 0) {
       Ends e = load_ends(c, b);
-      ok = draw_seed<K, kS, kHF>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0, key,
+      ok = draw_seed<K, kS, kHF ? BVH_CALL : BVH_NONE>(S, has_guide ? &g : nullptr, e, cell_of(c, b), e.tau, P.tau_random != 0, key,
                             (uint64_t)b + offset, 0u, P, ch, tau, pdf, ctx.err, t.c, true, false,
                             vmf ? &df : nullptr);
     }
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScen
           uint32_t tau;
           float pdf;
           Ends et = e;
-          if (!draw_seed<K, kS, kHF>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
+          if (!draw_seed<K, kS, kHF ? BVH_CALL : BVH_NONE>(S, has_guide ? &g : nullptr, e, cell, e.tau, P.tau_random != 0, key,
                                 (uint64_t)b + offset, (uint32_t)tr | ((uint32_t)rep << 24), P, ch, tau, pdf, ctx.err,
                                 t.c, false, true))
             continue;
