@@ -266,7 +266,10 @@ __device__ __noinline__ void hf_intersect(const DHF& H, float3 o, float3 d, floa
 // none (the branch compiled out; a call alone costs a kernel registers: the
 // plain mode's trial loop has 168 registers without it, 128 and spills with
 // it); BVH_CALL, the out-of-line traversal; BVH_INLINE, the traversal inlined
-// (the ray-batch kernel, whose loop is the traversal).
+// (the ray-batch kernel, whose loop is the traversal).  The batched seed
+// kernel keeps the call whatever the scene: without it the compiler gives it
+// 80 registers against 64, and at the lower occupancy its dependent loads
+// take longer than the spills it saves.
 enum { BVH_NONE = 0, BVH_CALL = 1, BVH_INLINE = 2 };
 
 template <bool kStats, int kBVH = BVH_CALL>

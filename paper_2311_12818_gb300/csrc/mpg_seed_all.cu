@@ -18,8 +18,7 @@
 namespace mpg {
 namespace kern {
 
-// kBVH: BVH_NONE for scenes without heightfields, else BVH_CALL.
-template <bool kS, int kBVH>
+template <bool kS>
 __global__ void __launch_bounds__(128) k_seed_all(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                   DChains c, uint2 key, uint64_t offset, mpg_params P, DCtx ctx) {
   Tally t = {};
@@ -46,7 +45,7 @@ __global__ void __launch_bounds__(128) k_seed_all(const __grid_constant__ DScene
       // Eq. deduction with k at run time, each vertex stored as it is found
       float3 o = e.xD, d = w;
       for (int i = 0; ok && i < k; ++i) {
-        Hit h = intersect<kS, kBVH>(S, o, d, P.ray_eps, 3.0e38f, ctx.err, t.c);
+        Hit h = intersect<kS>(S, o, d, P.ray_eps, 3.0e38f, ctx.err, t.c);
         if (h.surf < 0) { ok = false; break; }
         const float3 x = hit_point(S, o, d, h);
         c.x[(3 * i + 0) * B + b] = x.x;
@@ -93,8 +92,7 @@ __global__ void __launch_bounds__(128) k_seed_all(const __grid_constant__ DScene
 void launch_seed_all(const DScene& S, const DGuide* g, const DChains& c, uint2 key, uint64_t offset,
                      const mpg_params& P, DCtx ctx, int grid, cudaStream_t st) {
   DGuide gg = g ? *g : DGuide{};
-  if (S.n_hf > 0) kern::k_seed_all<true, BVH_CALL><<<grid, 128, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx);
-  else kern::k_seed_all<true, BVH_NONE><<<grid, 128, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx);
+  kern::k_seed_all<true><<<grid, 128, 0, st>>>(S, gg, g != nullptr, c, key, offset, P, ctx);
 }
 
 }  // namespace mpg
