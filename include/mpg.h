@@ -612,9 +612,12 @@ mpg_status mpg_training_plan(int32_t total_spp, int32_t first_spp, float train_f
  * cadence, Bernoulli rounds, FP64 split); each candidate is timed `repeats`
  * times (minimum) and replaces the best one only when more than 3 % faster.
  * The result is then timed three more times against the input schedule,
- * alternately, and the input schedule is returned if it is the faster. 
- * The outputs of the step go to scratch the call allocates and frees.
- * Synchronous; walk_mode must be MPG_WALK_BATCHED. */
+ * alternately, and the input schedule is returned if it is the faster.
+ * The default schedule walks every length with one thread per chain; on
+ * batches with chains of length 3 and more the lane-group form (walk_group)
+ * is usually faster (the mixed k = 1..8 batch: about 2.5 times), which this
+ * call finds.  The outputs of the step go to scratch the call allocates and
+ * frees.  Synchronous; walk_mode must be MPG_WALK_BATCHED. */
 mpg_status mpg_autotune(mpg_ctx* ctx, const mpg_scene* scene, const mpg_guide* guide,
                         mpg_chains* chains, uint64_t rng_seed, uint64_t rng_offset,
                         const mpg_params* in, int32_t repeats, mpg_params* out,
