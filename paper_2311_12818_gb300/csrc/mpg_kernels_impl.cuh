@@ -333,6 +333,7 @@ __global__ void __launch_bounds__(64) k_glossy(const __grid_constant__ DScene S,
 
 // kOff: glossy chains; every trial is walked with the chain's own offset
 // normals, so N estimates the reciprocal probability given the offsets.
+// kHF: the scene may hold heightfields (as for k_seed).
 template <int K, bool kS, bool kOff, bool kHF>
 __global__ void __launch_bounds__(128) k_bernoulli(const __grid_constant__ DScene S, DGuide g, int has_guide,
                                                    DChains c, DWork w, uint2 key, uint64_t offset, mpg_params P,
